@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Throughput of cross-scale (zero-tree) OMP vs plain OMP on one GB300.
+
+Workload: Bayer RGGB demosaicing of a 512x512 RGB synthetic image, 8x8x3
+patches at stride 2 (253 x 253 = 64,009 patches), fine dictionary 192 x 1024,
+64 measurements per patch, K = 8 (coarse scale 48 x 256, K_low = 4, links by
+nearest downsampled atom).  One step = the whole hot path on that image:
+patch extraction -> solve (cross-scale for the headline value; plain OMP
+reported beside it) -> overlap-add aggregation.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "patches/s cross-scale vs full OMP on one GB300 at matched PSNR; p50/p99 job latency"
+UNIT = "patches/s"
+L2_FLUSH_BYTES = 512 << 20
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="bayer")
+    ap.add_argument("--links", default="paper", choices=["paper", "literal"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(w, args):
+    g = w.geometry
+    return {
+        "workload": f"{w.name}_{w.sensing.kind}_{g.H}x{g.W}x{g.planes}_patch{g.P}_stride{g.stride}",
+        "patches": int(w.n_patches),
+        "dictionaries": [f"{d.shape[1]}x{d.shape[0]}" for d in w.dicts],
+        "K": [int(k[0]) for k in w.K_levels],
+        "links": args.links,
+        "seed": int(w.seed),
+        "l2": "flushed between steps (512 MiB write)",
+        "parallelism": "replicas (one image per GPU)",
+    }
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# roofline bookkeeping
+# ----------------------------------------------------------------------------
+def kernel_source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1511_05174_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the
+    current kernel sources (profiles/traffic_<kernel>_<workload>.txt: key: value)."""
+    path = os.path.join(ROOT, "profiles", f"traffic_{kernel}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line and not line.startswith("#"):
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("source_sha") != kernel_source_sha():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def algorithmic(kind, w, prof_launches, stats, B):
+    """Algorithmic work of one launch of `kind` on this workload: (amount, unit, bound)."""
+    g = w.geometry
+    M = 64 if w.sensing.kind != "identity" else g.planes * g.P * g.P
+    top = w.dicts[-1].shape[0]
+    if kind == "proxy_fp32":
+        T = top if prof_launches.get("restricted") else w.dicts[0].shape[0]
+        return 2.0 * M * T * B, "TFLOP/s", "alu"
+    if kind == "restricted":
+        n = max(prof_launches.get("restricted", (1,))[0], 1)
+        return 2.0 * M * stats.get("restricted_scores", 0) / n, "TFLOP/s", "alu"
+    if kind == "omp_update":
+        # y, r read and r written, 4 B each, per patch
+        return 3.0 * 4 * M * B, "GB/s", "hbm"
+    if kind == "aggregate":
+        K = int(w.K_levels[0][0])
+        return 4.0 * g.planes * g.H * g.W + B * (K * 8 + 1), "GB/s", "hbm"
+    if kind == "extract":
+        return 4.0 * B * M + 4.0 * w.meas.size, "GB/s", "hbm"
+    return None, None, None
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on a bounded sample
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    import oracle
+    import synthetic
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = synthetic.make_workload(args.workload, links=args.links)
+    Y = oracle.extract_patches(w)
+    cores = oracle.num_threads()
+    sample = int(os.environ.get("CSP_REF_SAMPLE", "2048"))
+    rng = np.random.default_rng(1)
+    times = []
+    for i in range(args.warmup + args.steps):
+        sel = np.sort(rng.choice(w.n_patches, min(sample, w.n_patches), replace=False))
+        t0 = time.perf_counter()
+        oracle.cross_scale_omp(w, Y=Y, patches=sel, nthreads=cores)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            times.append(t1 - t0)
+    total = sum(times)
+    value = sample * len(times) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {**workload_config(w, args), "form": "cross_scale"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} random patches of the {w.n_patches}-patch image per step, "
+                                   "extraction excluded, cross-scale solve"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(w, seconds=12.0):
+    """The oracle as it stands, on all host threads, over a sample of patches
+    sized to about `seconds` of CPU time (cross-scale and plain)."""
+    import oracle
+
+    cores = oracle.num_threads()
+    Y = oracle.extract_patches(w)
+    rng = np.random.default_rng(2)
+    out = {}
+    for form, fn in (("cross_scale", oracle.cross_scale_omp), ("plain", oracle.plain_omp)):
+        n = 256
+        sel = np.sort(rng.choice(w.n_patches, n, replace=False))
+        t0 = time.perf_counter()
+        fn(w, Y=Y, patches=sel, nthreads=cores)
+        dt = time.perf_counter() - t0
+        n2 = int(min(w.n_patches, max(n, n * (seconds / 2) / max(dt, 1e-6))))
+        sel = np.sort(rng.choice(w.n_patches, n2, replace=False))
+        t0 = time.perf_counter()
+        fn(w, Y=Y, patches=sel, nthreads=cores)
+        dt = time.perf_counter() - t0
+        out[form] = (n2 / dt, n2)
+    return {"value": out["cross_scale"][0], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{out['cross_scale'][1]} random patches (cross-scale solve; extraction and "
+                      f"aggregation excluded); plain OMP: {out['plain'][0]:.1f} patches/s on "
+                      f"{out['plain'][1]} patches"}
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import synthetic
+    from paper_1511_05174_gb300.context import Context
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    w = synthetic.make_workload(args.workload, links=args.links, seed=rank)
+    ctx = Context(local)
+    ctx.load_workload(w)
+    B, M = ctx.B, ctx.M
+    K = [int(k[0]) for k in w.K_levels]
+    Kmax = K[0]
+    meas_d = torch.from_numpy(w.meas).to(dev)
+    Y = torch.empty((B, M), dtype=torch.float32, device=dev)
+    sup = torch.empty((B, Kmax), dtype=torch.int32, device=dev)
+    coef = torch.empty((B, Kmax), dtype=torch.float32, device=dev)
+    keff = torch.empty((B,), dtype=torch.int8, device=dev)
+    img = torch.empty((w.geometry.planes, w.geometry.H, w.geometry.W), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(mode):
+        ctx.extract(meas_d, Y)
+        ctx.solve(Y, mode, args.precision, K=K if mode == "cross_scale" else K[:1], Kmax=Kmax,
+                  out=(sup, coef, keff))
+        ctx.aggregate(sup, coef, keff, img)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step("cross_scale")
+        step("plain")
+    torch.cuda.synchronize()
+
+    def timed(mode, sampler=None):
+        ctx.profile_read(reset=True)
+        ctx.profile(True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            step(mode)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        clocks = sampler.stop() if sampler else None
+        barrier()
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        prof = ctx.profile_read(reset=True)
+        ctx.profile(False)
+        st = ctx.stats()
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item()), prof, st, clocks
+
+    cs_ms, cs_prof, cs_stats, clocks = timed("cross_scale", ClockSampler(local))
+    cs_img = img.double().cpu().numpy()
+    pl_ms, pl_prof, pl_stats, _ = timed("plain")
+    pl_img = img.double().cpu().numpy()
+
+    value = world * B * args.steps / (cs_ms / 1e3)
+    plain_value = world * B * args.steps / (pl_ms / 1e3)
+
+    # dominant kernel of the headline (cross-scale) step
+    launches = {k: v for k, v in cs_prof.items()}
+    dom = max(cs_prof.items(), key=lambda kv: kv[1][1])[0]
+    n_launch, tot_ms = cs_prof[dom]
+    amount, unit, bound = algorithmic(dom, w, launches, cs_stats, B)
+    roofline = None
+    if amount is not None and n_launch:
+        per_s = amount / (tot_ms / n_launch / 1e3)
+        peaks = {}
+        try:
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        except (OSError, ValueError):
+            pass
+        if bound == "hbm":
+            peak, src = (peaks.get("hbm_gbs"), "measured") if peaks.get("hbm_gbs") else (6800.0, "fallback")
+            achieved = per_s / 1e9
+        else:
+            peak, src = FP32_PEAK_TFLOPS, "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"
+            achieved = per_s / 1e12
+        roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "peak_source": src,
+                    "unit": unit, "frac": achieved / peak if peak else None,
+                    "traffic": read_traffic(dom, w.name),
+                    "avg_launch_us": 1e3 * tot_ms / n_launch, "launches_per_step": n_launch / args.steps}
+
+    gpu_launches = int(sum(v[0] for v in cs_prof.values()))
+    kernels = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
+               for k, v in cs_prof.items()}
+    kernels_plain = {k: {"launches_per_step": v[0] / args.steps, "ms_per_step": v[1] / args.steps}
+                     for k, v in pl_prof.items()}
+
+    # end to end through the C ABI from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        meas_h = torch.from_numpy(w.meas.copy()).pin_memory()
+        img_h = torch.empty(img.shape, dtype=torch.float32).pin_memory()
+        for _ in range(2):
+            ctx.reconstruct_host(meas_h, img_h, "cross_scale", args.precision, K=K, Kmax=Kmax)
+        barrier()
+        tot = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.reconstruct_host(meas_h, img_h, "cross_scale", args.precision, K=K, Kmax=Kmax)
+            tot += time.perf_counter() - t0
+        t = torch.tensor([tot], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * B * args.steps / float(t.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(w.meas.nbytes), "d2h_bytes_per_step": int(img.numel() * 4)}
+
+    def psnr(est):
+        mse = float(np.mean((w.truth - est) ** 2))
+        peak = float(w.truth.max() - w.truth.min())
+        return 10 * np.log10(peak * peak / mse)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": cs_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
+            "data": "synthetic (seeded; Gaussian unit-norm atoms, K-sparse N(0,1) codes)",
+            "config": {**workload_config(w, args), "form": "cross_scale", "precision": args.precision},
+            "plain_omp": {"value": plain_value, "unit": UNIT, "ms_per_step": pl_ms / args.steps,
+                          "kernels": kernels_plain},
+            "speedup_cross_scale_vs_plain": value / plain_value,
+            "psnr_db": {"cross_scale": psnr(cs_img), "plain": psnr(pl_img)},
+            "solve_stats": {"cross_scale": cs_stats, "plain": pl_stats},
+            "kernels": kernels,
+            "roofline": roofline,
+            "gpu_launches": gpu_launches,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

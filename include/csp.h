@@ -1,0 +1,217 @@
+/*
+ * csp.h -- C ABI of the GB300 cross-scale predictive OMP library.
+ *
+ * Batched Orthogonal Matching Pursuit over the independent patches of a
+ * linear inverse problem y = Phi D s + e (arXiv 1511.05174, Sec. III-C), in
+ * two forms:
+ *   - plain OMP against the fine dictionary (Sec. II-B, Algorithm 1);
+ *   - cross-scale ("zero-tree") OMP (Sec. III-C, Algorithm 2, problems
+ *     (P_low) and (P_high)): OMP on the coarsest scale, then at each finer
+ *     scale an OMP restricted to the children f(Omega) of the atoms chosen
+ *     one scale up (cross-scale map, Sec. III-B; multi-scale tree, Fig. 3).
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a csp_status; CSP_OK (0) on success, a negative code
+ *     otherwise, with a message from csp_last_error().  No C++ exception
+ *     crosses this boundary.
+ *   - The caller owns every buffer it passes.  The library copies what it
+ *     keeps (dictionaries, links, codes) into device memory it owns, and frees
+ *     it in csp_destroy().
+ *   - "device" pointers are CUDA global-memory pointers on the context's
+ *     device; "host" pointers are ordinary (preferably pinned) host memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *     enqueued asynchronously on it; outputs are valid once the stream has
+ *     reached the point of the call.
+ *   - Dictionaries are atom-major float32: atom i of level l occupies
+ *     D[i * N_l .. i * N_l + N_l - 1].  Level 0 is the finest scale.
+ *   - Patch vector layout at any level: index ((ly * Lx + lx) * Py + py) * Px + px
+ *     for plane-grid position (ly, lx) (colour channel, frame or view) and
+ *     pixel (py, px) of the patch.
+ *   - Patch origins along an axis of extent E: min(i * stride, E - P) for
+ *     i = 0 .. n-1, n = floor((E - P) / stride) + 1 (+1 when the stride misses
+ *     E - P).  Patch b = iy * nx + ix (raster order).
+ *   - A context is not thread-safe: one host thread at a time per context.
+ */
+#ifndef CSP_H
+#define CSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int csp_status;
+
+#define CSP_OK               0
+#define CSP_ERR_INVALID     -1   /* bad argument, size or state */
+#define CSP_ERR_OOM         -2   /* device allocation failed or memory budget exceeded */
+#define CSP_ERR_NOT_READY   -3   /* a required load/set call has not been made */
+#define CSP_ERR_CUDA        -4   /* a CUDA runtime call failed */
+#define CSP_ERR_TIMEOUT     -5   /* a bounded wait expired */
+#define CSP_ERR_UNSUPPORTED -6   /* valid request this build does not implement */
+
+#define CSP_MAX_LEVELS 4
+#define CSP_MAX_K      32        /* largest sparsity per level */
+
+/* Sensing operators Phi (Sec. III-C "y = Phi x + e"; Sec. IV experiments). */
+#define CSP_SENSE_IDENTITY       0  /* denoising: Phi = I, M = planes * P * P                 */
+#define CSP_SENSE_BAYER_RGGB     1  /* demosaicing: one colour per pixel, RGGB, M = P * P     */
+#define CSP_SENSE_CODED_EXPOSURE 2  /* video CS: per-pixel binary code per frame, M = P * P   */
+#define CSP_SENSE_CODED_APERTURE 3  /* light-field CS: per-shot binary code per view,
+                                       M = shots * P * P                                     */
+
+#define CSP_MODE_PLAIN        0     /* Algorithm 1 on the fine dictionary                    */
+#define CSP_MODE_CROSS_SCALE  1     /* Algorithm 2 over all loaded levels                    */
+
+#define CSP_PREC_FP32 0             /* proxy inner products in FP32 on CUDA cores            */
+#define CSP_PREC_BF16 1             /* proxy on tcgen05 tensor cores in BF16 (FP32 accumulate),
+                                       top candidates re-scored in FP32                      */
+
+typedef struct csp_ctx csp_ctx;
+
+/* Signal and patch geometry (patches: Sec. IV; scales W/U: Sec. III-A/III-C). */
+typedef struct csp_geometry {
+    int H, W;                  /* pixels per plane                                       */
+    int plane_rows;            /* Ly: plane grid rows (views) -- 1 for images and videos */
+    int plane_cols;            /* Lx: colour channels, frames or view columns            */
+    int P;                     /* patch side in pixels                                   */
+    int stride;                /* patch origin step                                      */
+    int n_levels;              /* number of scales, 1 .. CSP_MAX_LEVELS                  */
+    int factors[CSP_MAX_LEVELS][4]; /* per level (fy, fx, sy, sx): downsampling of the plane
+                                  grid rows/cols and pixel rows/cols relative to level 0;
+                                  level 0 must be (1,1,1,1); each level must divide the
+                                  next.  W = box average, U = nearest replicate, W U = I. */
+} csp_geometry;
+
+/* Sensing operator.  `codes` is a HOST pointer, copied by the library:
+ *   CODED_EXPOSURE: uint8 [planes][H][W] (frame-major), values 0/1;
+ *   CODED_APERTURE: uint8 [shots][planes], values 0/1;
+ *   otherwise ignored (may be NULL). */
+typedef struct csp_sensing {
+    int kind;
+    int shots;
+    const uint8_t *codes;
+} csp_sensing;
+
+/* Solve parameters.
+ *   K[l]       -- sparsity budget at level l (1 .. CSP_MAX_K) used when K_patch[l] is NULL;
+ *   K_patch[l] -- optional DEVICE int8 [B] per-patch budgets for level l (values 0 .. CSP_MAX_K);
+ *   Kmax       -- row length of the support/coef outputs (>= every level-0 budget).
+ * In CSP_MODE_PLAIN only level 0 is read. */
+typedef struct csp_solve_params {
+    int mode;
+    int precision;
+    int K[CSP_MAX_LEVELS];
+    const int8_t *K_patch[CSP_MAX_LEVELS];
+    int Kmax;
+} csp_solve_params;
+
+/* Solve statistics of the last csp_solve on a context (host copy, filled
+ * when the solve's stream work is complete and csp_solve_stats is called). */
+typedef struct csp_solve_stats {
+    int64_t patches;
+    int64_t fp64_fallbacks;    /* projections redone in FP64 (pivot ratio below threshold) */
+    int64_t early_stops;       /* patches that ended with k_eff < budget                    */
+    int64_t overflow;          /* patches whose candidate set exceeded the kernel capacity  */
+    int64_t restricted_scores; /* candidate inner products <a_i, r> computed by the restricted
+                                  (finer-scale) steps, summed over patches and iterations   */
+} csp_solve_stats;
+
+/* Create a context on CUDA `device`.  mem_budget_bytes caps the device memory
+ * the context may hold (0 = no cap); exceeding it yields CSP_ERR_OOM. */
+csp_status csp_create(csp_ctx **out, int device, size_t mem_budget_bytes);
+
+/* Free every device allocation of the context and the context itself.
+ * Waits for the context's outstanding work. NULL is ignored. */
+void csp_destroy(csp_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none).  Valid until
+ * the next call on the context.  ctx may be NULL (creation errors). */
+const char *csp_last_error(const csp_ctx *ctx);
+
+/* Set geometry (Sec. IV patches; Fig. 3 scales).  Invalidates loaded
+ * dictionaries' derived data.  Errors: CSP_ERR_INVALID on inconsistent sizes. */
+csp_status csp_set_geometry(csp_ctx *ctx, const csp_geometry *geom);
+
+/* Set the sensing operator Phi of y = Phi x + e (Sec. III-C).  Requires
+ * geometry.  Errors: CSP_ERR_INVALID (plane count incompatible with kind),
+ * CSP_ERR_NOT_READY (no geometry). */
+csp_status csp_set_sensing(csp_ctx *ctx, const csp_sensing *sensing);
+
+/* Load the dictionary D^(level) (N_l x T_l, atom-major float32, Sec. III-A).
+ * N_l must equal the level's patch dimension.  The library copies it.
+ * is_device_ptr: 0 = D is a host pointer, 1 = device pointer. */
+csp_status csp_load_dictionary(csp_ctx *ctx, int level, const float *D, int N_l, int T_l,
+                               int is_device_ptr);
+
+/* Load the cross-scale map f between `level` and `level + 1` (Sec. III-B).
+ * parent: HOST int32 [T_l], parent[i] in [0, T_{l+1}) is the coarse atom that
+ * atom i of `level` is a child of.  parent == NULL with Q > 0 selects the
+ * paper's block rule parent[i] = floor(i / Q) (requires T_l = Q * T_{l+1}).
+ * Requires both dictionaries loaded.  Errors: CSP_ERR_INVALID (range, size). */
+csp_status csp_load_scale_links(csp_ctx *ctx, int level, const int32_t *parent, int T_l, int Q);
+
+/* Patch count B and measurement dimension M of the current geometry and
+ * sensing. */
+csp_status csp_problem_size(const csp_ctx *ctx, int64_t *B_out, int *M_out);
+
+/* Patch extraction (Sec. III-C measurements, Sec. IV overlapping patches):
+ * meas (DEVICE float32) is the measurement image -- IDENTITY [planes][H][W],
+ * BAYER / CODED_EXPOSURE [H][W], CODED_APERTURE [shots][H][W]; Y_out (DEVICE
+ * float32 [B][M]) receives one measurement vector per patch. */
+csp_status csp_extract_patches(csp_ctx *ctx, const float *meas, float *Y_out, int64_t *B_out,
+                               void *stream);
+
+/* Solve every patch (Algorithm 1 or Algorithm 2).  Y: DEVICE float32 [B][M].
+ * Outputs (DEVICE, [B][Kmax]): support_out = fine-dictionary atom indices in
+ * selection order (-1 padded), coef_out = least-squares coefficients
+ * (0 padded), k_eff_out (DEVICE int8 [B]) = atoms chosen (< budget when the
+ * residual vanished, a chosen atom was linearly dependent, or the candidate set
+ * ran out).  Workspace is owned by the context and reused across calls. */
+csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *params, const float *Y, int64_t B,
+                     int32_t *support_out, float *coef_out, int8_t *k_eff_out, void *stream);
+
+/* Statistics of the most recent csp_solve (synchronises its stream). */
+csp_status csp_solve_stats_get(csp_ctx *ctx, csp_solve_stats *out);
+
+/* Synthesis and overlap-add (Sec. IV: overlapping patches; uniform average
+ * over the covering patches): x_hat_p = D^(0)_|Omega alpha for every patch,
+ * image_out (DEVICE float32 [planes][H][W]) = per-pixel mean of the covering
+ * patches' values.  Deterministic (fixed summation order). */
+csp_status csp_aggregate(csp_ctx *ctx, const int32_t *support, const float *coef,
+                         const int8_t *k_eff, int64_t B, int Kmax, float *image_out,
+                         void *stream);
+
+/* End-to-end reconstruction from HOST buffers: copies the measurement image
+ * (layout as in csp_extract_patches) to the device, extracts, solves,
+ * aggregates and copies the image (float32 [planes][H][W]) back into
+ * image_host.  Per-patch budgets are not accepted here (K_patch must be NULL).
+ * Returns when the image is in host memory. */
+csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *params,
+                                const float *meas_host, float *image_host, void *stream);
+
+/* ---- Instrumentation (not part of the paper's method) ----------------------
+ * Every kernel launch of a context is counted per kernel kind.  While
+ * profiling is enabled, each launch is also bracketed by CUDA events on its
+ * stream, so that csp_profile_read reports the device time per kind. */
+typedef struct csp_kernel_time {
+    char name[32];             /* kernel kind, e.g. "proxy_fp32", "restricted"            */
+    int64_t launches;          /* launches since the last reset                          */
+    double total_ms;           /* summed event time (0 when profiling was off)           */
+} csp_kernel_time;
+
+/* on != 0 enables event timing of every launch from now on. */
+csp_status csp_profile_enable(csp_ctx *ctx, int on);
+
+/* Synchronises the context's recorded events, fills up to `cap` entries
+ * (kinds with at least one launch) and their count in *n_out; reset != 0
+ * clears the counters afterwards. */
+csp_status csp_profile_read(csp_ctx *ctx, csp_kernel_time *out, int cap, int *n_out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CSP_H */

@@ -1,0 +1,716 @@
+// C ABI of the cross-scale OMP library: context, loaders, validation,
+// workspace and the launch sequence of each entry point (declared in csp.h).
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "csp_internal.cuh"
+
+using namespace csp;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+csp_status fail(csp_ctx *ctx, csp_status st, const std::string &msg) {
+  if (ctx) ctx->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+#define CSP_CUDA(ctx, call)                                                              \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(ctx, CSP_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CSP_TRY(expr)             \
+  do {                            \
+    csp_status s_ = (expr);       \
+    if (s_ != CSP_OK) return s_;  \
+  } while (0)
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+csp_status dev_alloc(csp_ctx *ctx, void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return CSP_OK;
+  if (ctx->budget && ctx->held + bytes > ctx->budget)
+    return fail(ctx, CSP_ERR_OOM, "device memory budget exceeded (" + std::to_string(ctx->held + bytes) +
+                                      " > " + std::to_string(ctx->budget) + " bytes)");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(ctx, CSP_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  ctx->held += bytes;
+  ctx->allocs.push_back({*p, bytes});
+  return CSP_OK;
+}
+
+void dev_free(csp_ctx *ctx, void *p) {
+  if (!p) return;
+  for (size_t i = 0; i < ctx->allocs.size(); ++i)
+    if (ctx->allocs[i].first == p) {
+      cudaFree(p);
+      ctx->held -= ctx->allocs[i].second;
+      ctx->allocs.erase(ctx->allocs.begin() + (long)i);
+      return;
+    }
+}
+
+template <typename T>
+csp_status dev_alloc_t(csp_ctx *ctx, T **p, size_t count) {
+  void *v = nullptr;
+  csp_status s = dev_alloc(ctx, &v, count * sizeof(T));
+  *p = static_cast<T *>(v);
+  return s;
+}
+
+// Grow-only workspace slot.
+csp_status ws_get(csp_ctx *ctx, int slot, size_t bytes, void **out) {
+  if ((int)ctx->ws.size() <= slot) ctx->ws.resize(slot + 1);
+  Buf &b = ctx->ws[slot];
+  if (b.bytes < bytes) {
+    dev_free(ctx, b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    CSP_TRY(dev_alloc(ctx, &b.p, bytes));
+    b.bytes = bytes;
+  }
+  *out = b.p;
+  return CSP_OK;
+}
+template <typename T>
+csp_status ws_get_t(csp_ctx *ctx, int slot, size_t count, T **out) {
+  void *v = nullptr;
+  csp_status s = ws_get(ctx, slot, count * sizeof(T) + 16, &v);
+  *out = static_cast<T *>(v);
+  return s;
+}
+
+const char *const kKernelNames[KK_COUNT] = {"extract", "downsample", "prepare", "omp_init", "proxy_fp32",
+                                            "proxy_bf16", "omp_update", "restricted", "aggregate"};
+
+cudaEvent_t pool_event(csp_ctx *ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+  return e;
+}
+
+// Counts one launch of `kind` and, while profiling, brackets it with events.
+template <typename F>
+void run(csp_ctx *ctx, int kind, cudaStream_t s, int64_t n, F &&launch) {
+  if (n <= 0) return;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (ctx->prof) {
+    a = pool_event(ctx);
+    b = pool_event(ctx);
+    if (a) cudaEventRecord(a, s);
+  }
+  launch();
+  if (ctx->prof && a && b) {
+    cudaEventRecord(b, s);
+    ctx->pending.push_back({kind, a, b});
+  }
+  ctx->launches[kind] += 1;
+}
+
+csp_status drain_profile(csp_ctx *ctx) {
+  for (auto &r : ctx->pending) {
+    CSP_CUDA(ctx, cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    CSP_CUDA(ctx, cudaEventElapsedTime(&ms, r.a, r.b));
+    ctx->prof_ms[r.kind] += ms;
+    ctx->ev_pool.push_back(r.a);
+    ctx->ev_pool.push_back(r.b);
+  }
+  ctx->pending.clear();
+  return CSP_OK;
+}
+
+
+enum Slot {
+  WS_R, WS_RBF, WS_L, WS_Z, WS_FLAGS, WS_CAND,
+  WS_LV_OMEGA, WS_LV_ALPHA = WS_LV_OMEGA + CSP_MAX_LEVELS, WS_LV_KEFF = WS_LV_ALPHA + CSP_MAX_LEVELS,
+  WS_LV_Y = WS_LV_KEFF + CSP_MAX_LEVELS,
+  WS_COUNT = WS_LV_Y + CSP_MAX_LEVELS
+};
+
+int level_dim(const csp_geometry &g, int l) {
+  return (g.plane_rows / g.factors[l][0]) * (g.plane_cols / g.factors[l][1]) * (g.P / g.factors[l][2]) *
+         (g.P / g.factors[l][3]);
+}
+
+int count_1d(int E, int P, int s) {
+  if (E < P) return 0;
+  int n = (E - P) / s + 1;
+  if ((E - P) % s) ++n;
+  return n;
+}
+
+void free_level_derived(csp_ctx *ctx, LevelData &L) {
+  for (int p = 0; p < kMaxPhases; ++p) {
+    if (L.A[p] && L.A[p] != L.D) dev_free(ctx, L.A[p]);
+    dev_free(ctx, L.inv_norm[p]);
+    dev_free(ctx, L.Abf[p]);
+    L.A[p] = nullptr;
+    L.inv_norm[p] = nullptr;
+    L.Abf[p] = nullptr;
+  }
+  L.n_phase = 0;
+}
+
+void free_links(csp_ctx *ctx, LevelData &L) {
+  dev_free(ctx, L.child_off);
+  dev_free(ctx, L.child_idx);
+  L.child_off = L.child_idx = nullptr;
+  L.max_children = 0;
+  L.links = false;
+}
+
+csp_status prepare(csp_ctx *ctx, cudaStream_t s) {
+  if (ctx->prepared) return CSP_OK;
+  if (!ctx->has_geom) return fail(ctx, CSP_ERR_NOT_READY, "geometry not set");
+  if (!ctx->has_sensing) return fail(ctx, CSP_ERR_NOT_READY, "sensing operator not set");
+  if (ctx->sense_kind == CSP_SENSE_CODED_EXPOSURE)
+    return fail(ctx, CSP_ERR_UNSUPPORTED, "coded exposure (per-patch Phi) is not implemented in this build");
+  const int nl = ctx->geom.n_levels;
+  for (int l = 0; l < nl; ++l) {
+    LevelData &L = ctx->lv[l];
+    if (!L.D) return fail(ctx, CSP_ERR_NOT_READY, "dictionary of level " + std::to_string(l) + " not loaded");
+    free_level_derived(ctx, L);
+    const bool ident = ctx->sense_kind == CSP_SENSE_IDENTITY;
+    L.M = ident ? L.N : ctx->M;
+    L.Mp = (L.M + 63) / 64 * 64;
+    const int nph = ctx->sense_kind == CSP_SENSE_BAYER_RGGB ? 4 : 1;
+    for (int p = 0; p < nph; ++p) {
+      if (ident) {
+        L.A[p] = L.D;
+      } else {
+        CSP_TRY(dev_alloc_t(ctx, &L.A[p], (size_t)L.T * L.M));
+        run(ctx, KK_PREP, s, (int64_t)L.T * L.M, [&] {
+          launch_effective_dict(ctx->gd, ctx->sense_kind, ctx->shots, ctx->codes, l, p, L.D, L.T, L.N, L.A[p],
+                                L.M, s);
+        });
+      }
+      CSP_TRY(dev_alloc_t(ctx, &L.inv_norm[p], (size_t)L.T));
+      CSP_TRY(dev_alloc_t(ctx, &L.Abf[p], (size_t)L.T * L.Mp));
+      run(ctx, KK_PREP, s, L.T, [&] { launch_norms(L.A[p], L.T, L.M, L.Mp, L.inv_norm[p], L.Abf[p], s); });
+    }
+    L.n_phase = nph;
+  }
+  for (int l = 0; l + 1 < nl; ++l)
+    if (ctx->lv[l].links && ctx->lv[l].T == 0)
+      return fail(ctx, CSP_ERR_INVALID, "links of level " + std::to_string(l) + " inconsistent");
+  CSP_CUDA(ctx, cudaGetLastError());
+  ctx->prepared = true;
+  return CSP_OK;
+}
+
+bool valid_ptr_or_empty(const void *p, int64_t n) { return p != nullptr || n == 0; }
+
+}  // namespace
+
+extern "C" {
+
+csp_status csp_create(csp_ctx **out, int device, size_t mem_budget_bytes) {
+  if (!out) return fail(nullptr, CSP_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(nullptr, CSP_ERR_CUDA, std::string("cudaGetDeviceCount: ") + cudaGetErrorString(e));
+  }
+  if (device < 0 || device >= n) return fail(nullptr, CSP_ERR_INVALID, "device index out of range");
+  csp_ctx *ctx = new (std::nothrow) csp_ctx();
+  if (!ctx) return fail(nullptr, CSP_ERR_OOM, "host allocation failed");
+  ctx->device = device;
+  ctx->budget = mem_budget_bytes;
+  DeviceGuard g(device);
+  if (!g.ok) { delete ctx; return fail(nullptr, CSP_ERR_CUDA, "cudaSetDevice failed"); }
+  if (dev_alloc_t(ctx, &ctx->stats_dev, 4) != CSP_OK) {
+    std::string m = ctx->err;
+    delete ctx;
+    return fail(nullptr, CSP_ERR_OOM, m);
+  }
+  cudaMemset(ctx->stats_dev, 0, 4 * sizeof(int64_t));
+  *out = ctx;
+  return CSP_OK;
+}
+
+void csp_destroy(csp_ctx *ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  for (auto &a : ctx->allocs) cudaFree(a.first);
+  for (auto &r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char *csp_last_error(const csp_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+csp_status csp_set_geometry(csp_ctx *ctx, const csp_geometry *geom) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (!geom) return fail(ctx, CSP_ERR_INVALID, "geometry is NULL");
+  const csp_geometry &g = *geom;
+  if (g.P < 1 || g.stride < 1 || g.H < g.P || g.W < g.P || g.plane_rows < 1 || g.plane_cols < 1)
+    return fail(ctx, CSP_ERR_INVALID, "invalid extents: need 1 <= P <= H, W; stride >= 1; plane grid >= 1");
+  if (g.n_levels < 1 || g.n_levels > CSP_MAX_LEVELS)
+    return fail(ctx, CSP_ERR_INVALID, "n_levels must be in 1..CSP_MAX_LEVELS");
+  const int dims[4] = {g.plane_rows, g.plane_cols, g.P, g.P};
+  for (int l = 0; l < g.n_levels; ++l)
+    for (int c = 0; c < 4; ++c) {
+      const int f = g.factors[l][c];
+      if (f < 1 || dims[c] % f) return fail(ctx, CSP_ERR_INVALID, "scale factor does not divide the extent");
+      if (l == 0 && f != 1) return fail(ctx, CSP_ERR_INVALID, "level 0 factors must be 1");
+      if (l > 0 && f % g.factors[l - 1][c]) return fail(ctx, CSP_ERR_INVALID, "scale factors must nest");
+    }
+  DeviceGuard dg(ctx->device);
+  const int64_t ny = count_1d(g.H, g.P, g.stride), nx = count_1d(g.W, g.P, g.stride);
+  if (ny * nx > (int64_t)INT32_MAX) return fail(ctx, CSP_ERR_INVALID, "too many patches");
+  // cover ranges: patches iy with origin(iy) <= y < origin(iy) + P
+  auto cover = [&](int E, int n) {
+    std::vector<int32_t> c(2 * (size_t)E);
+    for (int y = 0; y < E; ++y) {
+      int lo = -1, hi = -2;
+      for (int i = 0; i < n; ++i) {
+        const int o = std::min(i * g.stride, E - g.P);
+        if (o <= y && y < o + g.P) { if (lo < 0) lo = i; hi = i; }
+      }
+      c[2 * y] = lo < 0 ? 0 : lo;
+      c[2 * y + 1] = hi;
+    }
+    return c;
+  };
+  std::vector<int32_t> cy = cover(g.H, (int)ny), cx = cover(g.W, (int)nx);
+  dev_free(ctx, ctx->cover_y);
+  dev_free(ctx, ctx->cover_x);
+  ctx->cover_y = ctx->cover_x = nullptr;
+  CSP_TRY(dev_alloc_t(ctx, &ctx->cover_y, cy.size()));
+  CSP_TRY(dev_alloc_t(ctx, &ctx->cover_x, cx.size()));
+  CSP_CUDA(ctx, cudaMemcpy(ctx->cover_y, cy.data(), cy.size() * 4, cudaMemcpyHostToDevice));
+  CSP_CUDA(ctx, cudaMemcpy(ctx->cover_x, cx.data(), cx.size() * 4, cudaMemcpyHostToDevice));
+  // a new geometry invalidates everything shaped by it
+  for (int l = 0; l < CSP_MAX_LEVELS; ++l) {
+    free_level_derived(ctx, ctx->lv[l]);
+    free_links(ctx, ctx->lv[l]);
+    dev_free(ctx, ctx->lv[l].D);
+    ctx->lv[l] = LevelData();
+  }
+  dev_free(ctx, ctx->codes);
+  ctx->codes = nullptr;
+  dev_free(ctx, ctx->phase_ids);
+  ctx->phase_ids = nullptr;
+  ctx->has_sensing = false;
+  ctx->geom = g;
+  GeomDev &d = ctx->gd;
+  d.H = g.H; d.W = g.W; d.Ly = g.plane_rows; d.Lx = g.plane_cols; d.P = g.P; d.stride = g.stride;
+  d.nx = (int)nx; d.ny = (int)ny; d.n_levels = g.n_levels;
+  for (int l = 0; l < CSP_MAX_LEVELS; ++l)
+    for (int c = 0; c < 4; ++c) d.f[l][c] = l < g.n_levels ? g.factors[l][c] : 1;
+  ctx->B = nx * ny;
+  ctx->has_geom = true;
+  ctx->prepared = false;
+  return CSP_OK;
+}
+
+csp_status csp_set_sensing(csp_ctx *ctx, const csp_sensing *sensing) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (!sensing) return fail(ctx, CSP_ERR_INVALID, "sensing is NULL");
+  if (!ctx->has_geom) return fail(ctx, CSP_ERR_NOT_READY, "set the geometry first");
+  const csp_geometry &g = ctx->geom;
+  const int planes = g.plane_rows * g.plane_cols;
+  const int PP = g.P * g.P;
+  size_t code_bytes = 0;
+  int M = 0;
+  switch (sensing->kind) {
+    case CSP_SENSE_IDENTITY: M = planes * PP; break;
+    case CSP_SENSE_BAYER_RGGB:
+      if (g.plane_rows != 1 || g.plane_cols != 3) return fail(ctx, CSP_ERR_INVALID, "Bayer sensing needs a 1x3 (RGB) plane grid");
+      M = PP;
+      break;
+    case CSP_SENSE_CODED_EXPOSURE:
+      if (!sensing->codes) return fail(ctx, CSP_ERR_INVALID, "coded exposure needs codes");
+      M = PP;
+      code_bytes = (size_t)planes * g.H * g.W;
+      break;
+    case CSP_SENSE_CODED_APERTURE:
+      if (!sensing->codes || sensing->shots < 1) return fail(ctx, CSP_ERR_INVALID, "coded aperture needs shots >= 1 and codes");
+      M = sensing->shots * PP;
+      code_bytes = (size_t)sensing->shots * planes;
+      break;
+    default: return fail(ctx, CSP_ERR_INVALID, "unknown sensing kind");
+  }
+  if (M > 256) return fail(ctx, CSP_ERR_UNSUPPORTED, "measurement dimension above 256 is not supported");
+  DeviceGuard dg(ctx->device);
+  dev_free(ctx, ctx->codes);
+  ctx->codes = nullptr;
+  if (code_bytes) {
+    CSP_TRY(dev_alloc_t(ctx, &ctx->codes, code_bytes));
+    CSP_CUDA(ctx, cudaMemcpy(ctx->codes, sensing->codes, code_bytes, cudaMemcpyHostToDevice));
+  }
+  // patches grouped by Bayer phase (a single group for every other operator)
+  dev_free(ctx, ctx->phase_ids);
+  ctx->phase_ids = nullptr;
+  std::fill(std::begin(ctx->phase_start), std::end(ctx->phase_start), 0);
+  if (sensing->kind == CSP_SENSE_BAYER_RGGB) {
+    std::vector<int32_t> ids;
+    ids.reserve((size_t)ctx->B);
+    for (int ph = 0; ph < 4; ++ph) {
+      ctx->phase_start[ph] = (int64_t)ids.size();
+      for (int64_t b = 0; b < ctx->B; ++b) {
+        const int iy = (int)(b / ctx->gd.nx), ix = (int)(b % ctx->gd.nx);
+        const int oy = std::min(iy * g.stride, g.H - g.P), ox = std::min(ix * g.stride, g.W - g.P);
+        if (2 * (oy & 1) + (ox & 1) == ph) ids.push_back((int32_t)b);
+      }
+    }
+    ctx->phase_start[4] = (int64_t)ids.size();
+    CSP_TRY(dev_alloc_t(ctx, &ctx->phase_ids, ids.size()));
+    CSP_CUDA(ctx, cudaMemcpy(ctx->phase_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice));
+  }
+  ctx->sense_kind = sensing->kind;
+  ctx->shots = sensing->kind == CSP_SENSE_CODED_APERTURE ? sensing->shots : 0;
+  ctx->M = M;
+  ctx->has_sensing = true;
+  ctx->prepared = false;
+  return CSP_OK;
+}
+
+csp_status csp_load_dictionary(csp_ctx *ctx, int level, const float *D, int N_l, int T_l, int is_device_ptr) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (!ctx->has_geom) return fail(ctx, CSP_ERR_NOT_READY, "set the geometry first");
+  if (level < 0 || level >= ctx->geom.n_levels) return fail(ctx, CSP_ERR_INVALID, "level out of range");
+  if (N_l != level_dim(ctx->geom, level))
+    return fail(ctx, CSP_ERR_INVALID, "N_l = " + std::to_string(N_l) + " does not match the level's patch dimension " +
+                                          std::to_string(level_dim(ctx->geom, level)));
+  if (T_l < 1 || !D) return fail(ctx, CSP_ERR_INVALID, "empty dictionary");
+  DeviceGuard dg(ctx->device);
+  LevelData &L = ctx->lv[level];
+  free_level_derived(ctx, L);
+  free_links(ctx, L);
+  if (level > 0) free_links(ctx, ctx->lv[level - 1]);
+  dev_free(ctx, L.D);
+  L.D = nullptr;
+  CSP_TRY(dev_alloc_t(ctx, &L.D, (size_t)N_l * T_l));
+  CSP_CUDA(ctx, cudaMemcpy(L.D, D, sizeof(float) * (size_t)N_l * T_l,
+                           is_device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice));
+  L.N = N_l;
+  L.T = T_l;
+  ctx->prepared = false;
+  return CSP_OK;
+}
+
+csp_status csp_load_scale_links(csp_ctx *ctx, int level, const int32_t *parent, int T_l, int Q) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (!ctx->has_geom) return fail(ctx, CSP_ERR_NOT_READY, "set the geometry first");
+  if (level < 0 || level + 1 >= ctx->geom.n_levels) return fail(ctx, CSP_ERR_INVALID, "level out of range for links");
+  LevelData &F = ctx->lv[level], &C = ctx->lv[level + 1];
+  if (!F.D || !C.D) return fail(ctx, CSP_ERR_NOT_READY, "load both dictionaries before their links");
+  if (T_l != F.T) return fail(ctx, CSP_ERR_INVALID, "T_l does not match the loaded dictionary");
+  std::vector<int32_t> par((size_t)T_l);
+  if (!parent) {
+    if (Q < 1 || (int64_t)Q * C.T != T_l) return fail(ctx, CSP_ERR_INVALID, "block map needs T_l = Q * T_{l+1}");
+    for (int i = 0; i < T_l; ++i) par[i] = i / Q;
+  } else {
+    std::memcpy(par.data(), parent, sizeof(int32_t) * (size_t)T_l);
+    for (int i = 0; i < T_l; ++i)
+      if (par[i] < 0 || par[i] >= C.T)
+        return fail(ctx, CSP_ERR_INVALID, "parent[" + std::to_string(i) + "] out of range");
+  }
+  std::vector<int32_t> off((size_t)C.T + 1, 0), idx((size_t)T_l);
+  for (int i = 0; i < T_l; ++i) ++off[par[i] + 1];
+  int mx = 0;
+  for (int p = 0; p < C.T; ++p) { mx = std::max(mx, off[p + 1]); off[p + 1] += off[p]; }
+  std::vector<int32_t> fillp(off.begin(), off.end() - 1);
+  for (int i = 0; i < T_l; ++i) idx[fillp[par[i]]++] = i;  // ascending within each parent
+  DeviceGuard dg(ctx->device);
+  free_links(ctx, F);
+  CSP_TRY(dev_alloc_t(ctx, &F.child_off, off.size()));
+  CSP_TRY(dev_alloc_t(ctx, &F.child_idx, idx.size()));
+  CSP_CUDA(ctx, cudaMemcpy(F.child_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice));
+  CSP_CUDA(ctx, cudaMemcpy(F.child_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice));
+  F.max_children = mx;
+  F.links = true;
+  return CSP_OK;
+}
+
+csp_status csp_problem_size(const csp_ctx *ctx, int64_t *B_out, int *M_out) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (!ctx->has_geom || !ctx->has_sensing) return CSP_ERR_NOT_READY;
+  if (B_out) *B_out = ctx->B;
+  if (M_out) *M_out = ctx->M;
+  return CSP_OK;
+}
+
+csp_status csp_extract_patches(csp_ctx *ctx, const float *meas, float *Y_out, int64_t *B_out, void *stream) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (!ctx->has_geom || !ctx->has_sensing) return fail(ctx, CSP_ERR_NOT_READY, "geometry and sensing must be set");
+  if (!meas || !Y_out) return fail(ctx, CSP_ERR_INVALID, "NULL buffer");
+  DeviceGuard dg(ctx->device);
+  run(ctx, KK_EXTRACT, (cudaStream_t)stream, ctx->B * ctx->M, [&] {
+    launch_extract(ctx->gd, ctx->sense_kind, ctx->shots, meas, Y_out, ctx->B, ctx->M, (cudaStream_t)stream);
+  });
+  CSP_CUDA(ctx, cudaGetLastError());
+  if (B_out) *B_out = ctx->B;
+  return CSP_OK;
+}
+
+csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, int64_t B,
+                     int32_t *support_out, float *coef_out, int8_t *k_eff_out, void *stream) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (!prm) return fail(ctx, CSP_ERR_INVALID, "params is NULL");
+  if (B < 0) return fail(ctx, CSP_ERR_INVALID, "B < 0");
+  if (!valid_ptr_or_empty(Y, B) || !valid_ptr_or_empty(support_out, B) || !valid_ptr_or_empty(coef_out, B) ||
+      !valid_ptr_or_empty(k_eff_out, B))
+    return fail(ctx, CSP_ERR_INVALID, "NULL buffer");
+  if (prm->mode != CSP_MODE_PLAIN && prm->mode != CSP_MODE_CROSS_SCALE) return fail(ctx, CSP_ERR_INVALID, "unknown mode");
+  if (prm->precision != CSP_PREC_FP32 && prm->precision != CSP_PREC_BF16)
+    return fail(ctx, CSP_ERR_INVALID, "unknown precision");
+  if (prm->Kmax < 1 || prm->Kmax > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "Kmax must be in 1..CSP_MAX_K");
+  if (!ctx->has_geom || !ctx->has_sensing) return fail(ctx, CSP_ERR_NOT_READY, "geometry and sensing must be set");
+  const int nl = prm->mode == CSP_MODE_PLAIN ? 1 : ctx->geom.n_levels;
+  int Kb[CSP_MAX_LEVELS];
+  for (int l = 0; l < nl; ++l) {
+    if (prm->K_patch[l]) Kb[l] = prm->Kmax;
+    else {
+      if (prm->K[l] < 1 || prm->K[l] > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "K[l] must be in 1..CSP_MAX_K");
+      Kb[l] = prm->K[l];
+    }
+  }
+  if (!prm->K_patch[0] && prm->K[0] > prm->Kmax) return fail(ctx, CSP_ERR_INVALID, "K[0] exceeds Kmax");
+  for (int l = 0; l + 1 < nl; ++l)
+    if (!ctx->lv[l].links) return fail(ctx, CSP_ERR_NOT_READY, "scale links of level " + std::to_string(l) + " not loaded");
+  if (ctx->sense_kind == CSP_SENSE_BAYER_RGGB && B != ctx->B)
+    return fail(ctx, CSP_ERR_INVALID, "Bayer sensing solves the geometry's patch grid: B must equal the patch count");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard dg(ctx->device);
+  CSP_TRY(prepare(ctx, s));
+  const bool bf16 = prm->precision == CSP_PREC_BF16;
+  const int top = nl - 1;
+  const LevelData &LT = ctx->lv[top];
+  if (bf16 && !proxy_bf16_supported(LT.M, LT.T))
+    return fail(ctx, CSP_ERR_UNSUPPORTED, "BF16 tensor-core proxy not available for this shape");
+  for (int l = 1; l < nl; ++l) {
+    const int cap = ctx->lv[l - 1].max_children * Kb[l];
+    if (cap > 1024) return fail(ctx, CSP_ERR_UNSUPPORTED, "candidate capacity above 1024 (max children x K)");
+  }
+  CSP_CUDA(ctx, cudaMemsetAsync(ctx->stats_dev, 0, 4 * sizeof(int64_t), s));
+  ctx->last_B = B;
+  ctx->last_stream = s;
+  if (B == 0) return CSP_OK;
+
+  // phase groups
+  const bool phased = ctx->sense_kind == CSP_SENSE_BAYER_RGGB;
+  const int nph = phased ? 4 : 1;
+  auto ids_of = [&](int ph) -> const int32_t * { return phased ? ctx->phase_ids + ctx->phase_start[ph] : nullptr; };
+  auto n_of = [&](int ph) -> int64_t { return phased ? ctx->phase_start[ph + 1] - ctx->phase_start[ph] : B; };
+
+  // per-level measurement vectors (Phi = I: y_l = W_l y)
+  const float *Yl[CSP_MAX_LEVELS];
+  for (int l = 0; l < nl; ++l) {
+    if (l > 0 && ctx->sense_kind == CSP_SENSE_IDENTITY) {
+      float *buf = nullptr;
+      CSP_TRY(ws_get_t(ctx, WS_LV_Y + l, (size_t)B * ctx->lv[l].M, &buf));
+      run(ctx, KK_DOWNSAMPLE, s, B, [&] { launch_downsample(ctx->gd, l, Y, buf, B, s); });
+      Yl[l] = buf;
+    } else {
+      Yl[l] = Y;
+    }
+  }
+
+  // per-level outputs (level 0 writes straight into the caller's buffers)
+  int32_t *lv_om[CSP_MAX_LEVELS];
+  float *lv_al[CSP_MAX_LEVELS];
+  int8_t *lv_ke[CSP_MAX_LEVELS];
+  int ldo[CSP_MAX_LEVELS];
+  for (int l = 0; l < nl; ++l) {
+    if (l == 0) {
+      lv_om[0] = support_out; lv_al[0] = coef_out; lv_ke[0] = k_eff_out; ldo[0] = prm->Kmax;
+    } else {
+      ldo[l] = Kb[l];
+      CSP_TRY(ws_get_t(ctx, WS_LV_OMEGA + l, (size_t)B * Kb[l], &lv_om[l]));
+      CSP_TRY(ws_get_t(ctx, WS_LV_ALPHA + l, (size_t)B * Kb[l], &lv_al[l]));
+      CSP_TRY(ws_get_t(ctx, WS_LV_KEFF + l, (size_t)B, &lv_ke[l]));
+    }
+  }
+
+  // full-dictionary OMP at the top level (the only level in plain mode)
+  {
+    const LevelData &L = ctx->lv[top];
+    OmpState st{};
+    CSP_TRY(ws_get_t(ctx, WS_R, (size_t)B * L.M, &st.R));
+    st.Rbf = nullptr;
+    if (bf16) CSP_TRY(ws_get_t(ctx, WS_RBF, (size_t)B * L.Mp, &st.Rbf));
+    st.Kb = Kb[top];
+    st.ldo = ldo[top];
+    CSP_TRY(ws_get_t(ctx, WS_L, (size_t)B * (Kb[top] * (Kb[top] + 1) / 2), &st.Lpk));
+    CSP_TRY(ws_get_t(ctx, WS_Z, (size_t)B * Kb[top], &st.z));
+    CSP_TRY(ws_get_t(ctx, WS_FLAGS, (size_t)B, &st.flags));
+    CSP_TRY(ws_get_t(ctx, WS_CAND, (size_t)B * kTopP, &st.cand));
+    st.omega = lv_om[top];
+    st.alpha = lv_al[top];
+    st.k_eff = lv_ke[top];
+    run(ctx, KK_INIT, s, B, [&] { launch_omp_init(Yl[top], B, L.M, bf16 ? L.Mp : 0, st, s); });
+    for (int it = 0; it < Kb[top]; ++it) {
+      for (int ph = 0; ph < nph; ++ph) {
+        if (bf16)
+          run(ctx, KK_PROXY_BF16, s, n_of(ph), [&] {
+            launch_proxy_bf16(st.Rbf, L.Mp, L.Abf[ph], L.T, ids_of(ph), n_of(ph), st.flags, st.cand, s);
+          });
+        else
+          run(ctx, KK_PROXY_FP32, s, n_of(ph), [&] {
+            launch_proxy_fp32(st.R, L.M, L.A[ph], L.inv_norm[ph], L.T, ids_of(ph), n_of(ph), st.omega, st.ldo,
+                              st.k_eff, st.flags, st.cand, s);
+          });
+      }
+      for (int ph = 0; ph < nph; ++ph)
+        run(ctx, KK_UPDATE, s, n_of(ph), [&] {
+          launch_omp_update(Yl[top], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph), bf16 ? kTopP : 1,
+                            prm->K_patch[top], prm->K[top], st, ctx->stats_dev, s);
+        });
+    }
+  }
+  // restricted OMP down the scales (Algorithm 2 fine steps)
+  for (int l = top - 1; l >= 0; --l) {
+    const LevelData &L = ctx->lv[l];
+    const int cap = std::max(1, L.max_children * Kb[l + 1]);
+    for (int ph = 0; ph < nph; ++ph)
+      run(ctx, KK_RESTRICTED, s, n_of(ph), [&] {
+        launch_omp_restricted(Yl[l], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph), L.child_off,
+                              L.child_idx, cap, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1], prm->K_patch[l], prm->K[l],
+                              Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], ctx->stats_dev, s);
+      });
+  }
+  CSP_CUDA(ctx, cudaGetLastError());
+  return CSP_OK;
+}
+
+csp_status csp_solve_stats_get(csp_ctx *ctx, csp_solve_stats *out) {
+  if (!ctx || !out) return fail(ctx, CSP_ERR_INVALID, "NULL argument");
+  DeviceGuard dg(ctx->device);
+  int64_t h[4] = {0, 0, 0, 0};
+  CSP_CUDA(ctx, cudaStreamSynchronize(ctx->last_stream));
+  CSP_CUDA(ctx, cudaMemcpy(h, ctx->stats_dev, sizeof(h), cudaMemcpyDeviceToHost));
+  out->patches = ctx->last_B;
+  out->fp64_fallbacks = h[0];
+  out->early_stops = h[1];
+  out->overflow = h[3];
+  out->restricted_scores = h[2];
+  return CSP_OK;
+}
+
+csp_status csp_aggregate(csp_ctx *ctx, const int32_t *support, const float *coef, const int8_t *k_eff, int64_t B,
+                         int Kmax, float *image_out, void *stream) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (!ctx->has_geom) return fail(ctx, CSP_ERR_NOT_READY, "geometry not set");
+  if (!ctx->lv[0].D) return fail(ctx, CSP_ERR_NOT_READY, "fine dictionary not loaded");
+  if (B != ctx->B) return fail(ctx, CSP_ERR_INVALID, "B must equal the geometry's patch count");
+  if (Kmax < 1 || Kmax > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "Kmax must be in 1..CSP_MAX_K");
+  if (!support || !coef || !k_eff || !image_out) return fail(ctx, CSP_ERR_INVALID, "NULL buffer");
+  DeviceGuard dg(ctx->device);
+  run(ctx, KK_AGGREGATE, (cudaStream_t)stream, B, [&] {
+    launch_aggregate(ctx->gd, ctx->lv[0].D, ctx->lv[0].N, support, coef, k_eff, Kmax, ctx->cover_y, ctx->cover_x,
+                     image_out, (cudaStream_t)stream);
+  });
+  CSP_CUDA(ctx, cudaGetLastError());
+  return CSP_OK;
+}
+
+csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *prm, const float *meas_host,
+                                float *image_host, void *stream) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (!prm || !meas_host || !image_host) return fail(ctx, CSP_ERR_INVALID, "NULL argument");
+  for (int l = 0; l < CSP_MAX_LEVELS; ++l)
+    if (prm->K_patch[l]) return fail(ctx, CSP_ERR_INVALID, "per-patch budgets are not accepted by csp_reconstruct_host");
+  if (!ctx->has_geom || !ctx->has_sensing) return fail(ctx, CSP_ERR_NOT_READY, "geometry and sensing must be set");
+  const csp_geometry &g = ctx->geom;
+  const int planes = g.plane_rows * g.plane_cols;
+  size_t meas_n = 0;
+  switch (ctx->sense_kind) {
+    case CSP_SENSE_IDENTITY: meas_n = (size_t)planes * g.H * g.W; break;
+    case CSP_SENSE_CODED_APERTURE: meas_n = (size_t)ctx->shots * g.H * g.W; break;
+    default: meas_n = (size_t)g.H * g.W;
+  }
+  const size_t img_n = (size_t)planes * g.H * g.W;
+  const int64_t B = ctx->B;
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard dg(ctx->device);
+  auto grow = [&](Buf &b, size_t bytes) -> csp_status {
+    if (b.bytes >= bytes) return CSP_OK;
+    dev_free(ctx, b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    CSP_TRY(dev_alloc(ctx, &b.p, bytes));
+    b.bytes = bytes;
+    return CSP_OK;
+  };
+  CSP_TRY(grow(ctx->h_meas, meas_n * 4));
+  CSP_TRY(grow(ctx->h_Y, (size_t)B * ctx->M * 4 + 16));
+  CSP_TRY(grow(ctx->h_sup, (size_t)B * prm->Kmax * 4 + 16));
+  CSP_TRY(grow(ctx->h_coef, (size_t)B * prm->Kmax * 4 + 16));
+  CSP_TRY(grow(ctx->h_keff, (size_t)B + 16));
+  CSP_TRY(grow(ctx->h_img, img_n * 4));
+  CSP_CUDA(ctx, cudaMemcpyAsync(ctx->h_meas.p, meas_host, meas_n * 4, cudaMemcpyHostToDevice, s));
+  CSP_TRY(csp_extract_patches(ctx, (const float *)ctx->h_meas.p, (float *)ctx->h_Y.p, nullptr, stream));
+  CSP_TRY(csp_solve(ctx, prm, (const float *)ctx->h_Y.p, B, (int32_t *)ctx->h_sup.p, (float *)ctx->h_coef.p,
+                    (int8_t *)ctx->h_keff.p, stream));
+  CSP_TRY(csp_aggregate(ctx, (const int32_t *)ctx->h_sup.p, (const float *)ctx->h_coef.p,
+                        (const int8_t *)ctx->h_keff.p, B, prm->Kmax, (float *)ctx->h_img.p, stream));
+  CSP_CUDA(ctx, cudaMemcpyAsync(image_host, ctx->h_img.p, img_n * 4, cudaMemcpyDeviceToHost, s));
+  CSP_CUDA(ctx, cudaStreamSynchronize(s));
+  return CSP_OK;
+}
+
+csp_status csp_profile_enable(csp_ctx *ctx, int on) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  ctx->prof = on != 0;
+  return CSP_OK;
+}
+
+csp_status csp_profile_read(csp_ctx *ctx, csp_kernel_time *out, int cap, int *n_out, int reset) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (cap < 0 || (cap > 0 && !out)) return fail(ctx, CSP_ERR_INVALID, "bad output array");
+  DeviceGuard dg(ctx->device);
+  CSP_TRY(drain_profile(ctx));
+  int n = 0;
+  for (int k = 0; k < KK_COUNT; ++k) {
+    if (!ctx->launches[k]) continue;
+    if (n < cap) {
+      std::memset(out[n].name, 0, sizeof(out[n].name));
+      std::strncpy(out[n].name, kKernelNames[k], sizeof(out[n].name) - 1);
+      out[n].launches = ctx->launches[k];
+      out[n].total_ms = ctx->prof_ms[k];
+    }
+    ++n;
+  }
+  if (n_out) *n_out = n;
+  if (reset)
+    for (int k = 0; k < KK_COUNT; ++k) { ctx->launches[k] = 0; ctx->prof_ms[k] = 0.0; }
+  return CSP_OK;
+}
+
+}  // extern "C"

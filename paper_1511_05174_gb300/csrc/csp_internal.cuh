@@ -1,0 +1,155 @@
+// Internal declarations of the cross-scale OMP library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "csp.h"
+
+namespace csp {
+
+// Numerical thresholds of the GPU path.
+//  - kTauPivot: the FP32 Cholesky pivot d = ||a||^2 - ||w||^2 is trusted when
+//    d / ||a||^2 >= kTauPivot; below it the projection is redone in FP64.
+//  - kEpsD64: in FP64, an atom with L_kk <= kEpsD64 * ||a_k|| depends on the
+//    chosen atoms and ends the patch (same test as a QR pivot |R_kk|).
+//  - kEpsR32: the patch ends when ||r||^2 <= kEpsR32 * ||y||^2 (FP32 noise floor).
+constexpr float kTauPivot = 1e-3f;
+constexpr double kEpsD64 = 1e-10;
+constexpr float kEpsR32 = 1e-12f;
+
+constexpr int kMaxPhases = 4;      // Bayer: 4 mosaic phases; other operators: 1
+constexpr int kTopP = 4;           // BF16 proxy: candidates re-scored in FP32 per patch
+
+// Device-side description of geometry, shared by the extraction, precompute
+// and aggregation kernels.
+struct GeomDev {
+  int H, W, Ly, Lx, P, stride, nx, ny, n_levels;
+  int f[CSP_MAX_LEVELS][4];
+};
+
+struct LevelData {
+  int N = 0, T = 0;            // patch dimension and atom count of this scale
+  float *D = nullptr;          // [T][N] atom-major
+  int M = 0;                   // dimension of this level's problem (rows of A)
+  int n_phase = 0;             // effective dictionaries held (0 = not prepared)
+  float *A[kMaxPhases] = {};   // [T][M]  a_i = Phi U_l d_i  (or d_i for Phi = I)
+  float *inv_norm[kMaxPhases] = {};   // [T] 1/||a_i||, or -1 for an ineligible zero column
+  __nv_bfloat16 *Abf[kMaxPhases] = {};  // [T][Mp] a_i / ||a_i|| in BF16 (tensor-core proxy)
+  int Mp = 0;                  // BF16 row length (M rounded up to 64)
+  // Cross-scale map f to the next coarser level (valid when this level < n_levels - 1).
+  int32_t *child_off = nullptr;   // [T_{l+1} + 1]
+  int32_t *child_idx = nullptr;   // [T] children of each coarse atom, ascending
+  int max_children = 0;
+  bool links = false;
+};
+
+// Grow-only device buffer owned by a context.
+struct Buf {
+  void *p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace csp
+
+namespace csp {
+enum KernelKind {
+  KK_EXTRACT, KK_DOWNSAMPLE, KK_PREP, KK_INIT, KK_PROXY_FP32, KK_PROXY_BF16, KK_UPDATE, KK_RESTRICTED,
+  KK_AGGREGATE, KK_COUNT
+};
+struct ProfRec {
+  int kind;
+  cudaEvent_t a, b;
+};
+}  // namespace csp
+
+struct csp_ctx {
+  int device = 0;
+  size_t budget = 0;  // 0 = unlimited
+  size_t held = 0;
+  std::string err;
+  bool has_geom = false, has_sensing = false, prepared = false;
+  csp_geometry geom{};
+  csp::GeomDev gd{};
+  int sense_kind = -1, shots = 0;
+  uint8_t *codes = nullptr;     // device copy of the codes
+  size_t codes_bytes = 0;
+  int64_t B = 0;
+  int M = 0;
+  csp::LevelData lv[CSP_MAX_LEVELS];
+  // Patches grouped by Bayer phase (phase = 2 * (oy % 2) + ox % 2).
+  int32_t *phase_ids = nullptr;          // [B] patch ids sorted by phase
+  int64_t phase_start[csp::kMaxPhases + 1] = {};
+  // Aggregation: covering patch-index range of every row / column.
+  int32_t *cover_y = nullptr, *cover_x = nullptr;
+  // Workspace (grown on demand).
+  std::vector<csp::Buf> ws;
+  int64_t *stats_dev = nullptr;          // 4 counters (see csp_solve_stats)
+  int64_t last_B = 0;
+  cudaStream_t last_stream = nullptr;
+  // Host-path buffers of csp_reconstruct_host.
+  csp::Buf h_meas, h_Y, h_sup, h_coef, h_keff, h_img;
+  // Instrumentation: launches per kernel kind, optional event timing.
+  int64_t launches[csp::KK_COUNT] = {};
+  double prof_ms[csp::KK_COUNT] = {};
+  bool prof = false;
+  std::vector<csp::ProfRec> pending;
+  std::vector<cudaEvent_t> ev_pool;
+  // All device allocations (for the memory budget and destroy).
+  std::vector<std::pair<void *, size_t>> allocs;
+};
+
+namespace csp {
+
+// ---- kernels (launch wrappers; all enqueue on `s`) ----
+void launch_extract(const GeomDev &g, int sense_kind, int shots, const float *meas, float *Y,
+                    int64_t B, int M, cudaStream_t s);
+void launch_downsample(const GeomDev &g, int level, const float *Y0, float *Yl, int64_t B,
+                       cudaStream_t s);
+void launch_effective_dict(const GeomDev &g, int sense_kind, int shots, const uint8_t *codes,
+                           int level, int phase, const float *D, int T, int N, float *A, int M,
+                           cudaStream_t s);
+void launch_norms(const float *A, int T, int M, int Mp, float *inv_norm, __nv_bfloat16 *Abf,
+                  cudaStream_t s);
+void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *support,
+                      const float *coef, const int8_t *k_eff, int Kmax, const int32_t *cover_y,
+                      const int32_t *cover_x, float *img, cudaStream_t s);
+
+// OMP state of a full-dictionary level, in device memory.
+struct OmpState {
+  float *R;          // [B][M] residuals
+  __nv_bfloat16 *Rbf;// [B][Mp] residuals in BF16 for the tensor-core proxy (may be null)
+  float *Lpk;        // [B][Kb*(Kb+1)/2] packed Cholesky factor of A_Omega^T A_Omega
+  float *z;          // [B][Kb]  L^{-1} A_Omega^T y
+  int32_t *omega;    // [B][ldo] chosen columns
+  float *alpha;      // [B][ldo]
+  int8_t *k_eff;     // [B]
+  uint8_t *flags;    // [B] bit0 done, bit1 FP64 mode
+  int32_t *cand;     // [B][kTopP] proxy candidates
+  int Kb;            // Cholesky capacity (max budget)
+  int ldo;           // row length of omega/alpha
+};
+
+void launch_omp_init(const float *Y, int64_t B, int M, int Mp, OmpState st, cudaStream_t s);
+void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_norm, int T,
+                       const int32_t *ids, int64_t n, const int32_t *omega, int ldo,
+                       const int8_t *k_eff, const uint8_t *flags, int32_t *cand, cudaStream_t s);
+bool proxy_bf16_supported(int M, int T);
+void launch_proxy_bf16(const __nv_bfloat16 *Rbf, int Mp, const __nv_bfloat16 *Abf, int T,
+                       const int32_t *ids, int64_t n, const uint8_t *flags, int32_t *cand,
+                       cudaStream_t s);
+void launch_omp_update(const float *Y, int M, const float *A, const float *inv_norm,
+                       const int32_t *ids, int64_t n, int n_cand, const int8_t *Kp, int Kuni,
+                       OmpState st, int64_t *stats, cudaStream_t s);
+void launch_omp_restricted(const float *Y, int M, const float *A, const float *inv_norm,
+                           const int32_t *ids, int64_t n, const int32_t *child_off,
+                           const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,
+                           const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
+                           int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
+                           cudaStream_t s);
+
+}  // namespace csp

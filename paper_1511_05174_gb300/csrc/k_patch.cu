@@ -1,0 +1,211 @@
+// Patch extraction, scale operators W/U, effective dictionaries and
+// overlap-add aggregation.
+//
+//  * extraction: y_p = the measurement pixels under patch p (Sec. III-C,
+//    y = Phi x + e; patches overlap, Sec. IV);
+//  * W: uniform (box) downsampler of a patch vector to a coarser scale, U:
+//    nearest-neighbour upsampler, W U = I (Sec. III-C, problem (P_low));
+//  * effective dictionary of a scale: a_i = Phi U_l d_i (the operator of
+//    (P_low) and, restricted, of (P_high)); for Phi = I the scale's own
+//    dictionary D^(l) against W_l x (Algorithm 2);
+//  * aggregation: x_hat_p = D_|Omega alpha, overlap-add averaged over the
+//    covering patches (Sec. IV: overlapping patches).
+#include "csp_internal.cuh"
+
+namespace csp {
+
+namespace {
+
+__device__ __forceinline__ int origin(int i, int stride, int extent, int P) {
+  int o = i * stride;
+  return o < extent - P ? o : extent - P;
+}
+
+// Index into a level-l patch vector of the level-0 position (ly, lx, py, px).
+__device__ __forceinline__ int level_index(const GeomDev &g, int l, int ly, int lx, int py, int px) {
+  const int fy = g.f[l][0], fx = g.f[l][1], sy = g.f[l][2], sx = g.f[l][3];
+  const int Lxl = g.Lx / fx, Pyl = g.P / sy, Pxl = g.P / sx;
+  return (((ly / fy) * Lxl + lx / fx) * Pyl + py / sy) * Pxl + px / sx;
+}
+
+// One thread per output element (b, m).  For every sensing kind the measurement
+// of row m of patch b is meas[q][oy + py][ox + px] with q = m / (P*P) (plane for
+// Phi = I, shot for coded aperture, 0 otherwise).
+__global__ void extract_kernel(GeomDev g, const float *__restrict__ meas, float *__restrict__ Y,
+                               int64_t B, int M) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * M) return;
+  const int64_t b = e / M;
+  const int m = (int)(e - b * M);
+  const int iy = (int)(b / g.nx), ix = (int)(b - (int64_t)iy * g.nx);
+  const int oy = origin(iy, g.stride, g.H, g.P), ox = origin(ix, g.stride, g.W, g.P);
+  const int PP = g.P * g.P;
+  const int q = m / PP, r = m - q * PP, py = r / g.P, px = r - py * g.P;
+  Y[e] = __ldg(meas + ((int64_t)q * g.H + oy + py) * g.W + ox + px);
+}
+
+// y_l = W_l y_0 for Phi = I: box average over the level's factor block.
+__global__ void downsample_kernel(GeomDev g, int l, const float *__restrict__ Y0,
+                                  float *__restrict__ Yl, int64_t B) {
+  const int fy = g.f[l][0], fx = g.f[l][1], sy = g.f[l][2], sx = g.f[l][3];
+  const int Lyl = g.Ly / fy, Lxl = g.Lx / fx, Pyl = g.P / sy, Pxl = g.P / sx;
+  const int Nl = Lyl * Lxl * Pyl * Pxl, N0 = g.Ly * g.Lx * g.P * g.P;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * Nl) return;
+  const int64_t b = e / Nl;
+  int n = (int)(e - b * Nl);
+  const int pxl = n % Pxl; n /= Pxl;
+  const int pyl = n % Pyl; n /= Pyl;
+  const int lxl = n % Lxl; const int lyl = n / Lxl;
+  const float *y = Y0 + b * N0;
+  float acc = 0.f;
+  for (int a = 0; a < fy; ++a)
+    for (int c = 0; c < fx; ++c)
+      for (int d = 0; d < sy; ++d)
+        for (int e2 = 0; e2 < sx; ++e2) {
+          const int ly = lyl * fy + a, lx = lxl * fx + c, py = pyl * sy + d, px = pxl * sx + e2;
+          acc += y[((ly * g.Lx + lx) * g.P + py) * g.P + px];
+        }
+  Yl[e] = acc / (float)(fy * fx * sy * sx);
+}
+
+// a_i[m] = (Phi U_l d_i)[m] for a Phi shared by all patches of one phase.
+__global__ void effective_dict_kernel(GeomDev g, int kind, int shots, const uint8_t *__restrict__ codes,
+                                      int l, int phase, const float *__restrict__ D, int T, int N,
+                                      float *__restrict__ A, int M) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)T * M) return;
+  const int i = (int)(e / M), m = (int)(e - (int64_t)i * M);
+  const float *d = D + (int64_t)i * N;
+  const int PP = g.P * g.P;
+  float v = 0.f;
+  if (kind == CSP_SENSE_BAYER_RGGB) {
+    const int py = m / g.P, px = m - py * g.P;
+    const int ry = ((phase >> 1) + py) & 1, rx = ((phase & 1) + px) & 1;
+    const int ch = (ry == 0 && rx == 0) ? 0 : ((ry == 1 && rx == 1) ? 2 : 1);
+    v = d[level_index(g, l, 0, ch, py, px)];
+  } else if (kind == CSP_SENSE_CODED_APERTURE) {
+    const int s = m / PP, r = m - s * PP, py = r / g.P, px = r - py * g.P;
+    const int V = g.Ly * g.Lx;
+    for (int vv = 0; vv < V; ++vv)
+      if (codes[s * V + vv]) v += d[level_index(g, l, vv / g.Lx, vv % g.Lx, py, px)];
+  } else {  // identity: the scale's own atoms
+    v = d[m];
+  }
+  A[e] = v;
+}
+
+// Column norms of A; 1/||a_i|| (or -1 for columns with ||a_i|| <= 1e-12 max_j ||a_j||,
+// which are never chosen) and the BF16 copy of a_i/||a_i|| padded to Mp.
+// One CTA, run once per dictionary.
+__global__ void norms_kernel(const float *__restrict__ A, int T, int M, int Mp, float *inv_norm,
+                             __nv_bfloat16 *Abf) {
+  __shared__ float red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float mx = 0.f;
+  for (int i = warp; i < T; i += nw) {
+    float s = 0.f;
+    for (int m = lane; m < M; m += 32) { const float a = A[(int64_t)i * M + m]; s = fmaf(a, a, s); }
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const float nrm = sqrtf(s);
+    if (lane == 0) inv_norm[i] = nrm;
+    mx = fmaxf(mx, nrm);
+  }
+  if (lane == 0) red[warp] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float v = 0.f;
+    for (int w = 0; w < nw; ++w) v = fmaxf(v, red[w]);
+    red[0] = v;
+  }
+  __syncthreads();
+  const float thr = 1e-12f * red[0];
+  for (int i = warp; i < T; i += nw) {
+    const float nrm = inv_norm[i];
+    __syncwarp();
+    const bool ok = nrm > thr && nrm > 0.f;
+    const float inv = ok ? 1.f / nrm : 0.f;
+    if (Abf)
+      for (int m = lane; m < Mp; m += 32)
+        Abf[(int64_t)i * Mp + m] = __float2bfloat16_rn(m < M ? A[(int64_t)i * M + m] * inv : 0.f);
+    if (lane == 0) inv_norm[i] = ok ? inv : -1.f;
+  }
+}
+
+// One thread per image pixel (plane, y, x): mean over the covering patches of
+// x_hat_p at that pixel, summed in patch raster order (deterministic).
+__global__ void aggregate_kernel(GeomDev g, const float *__restrict__ D0, int N0,
+                                 const int32_t *__restrict__ support, const float *__restrict__ coef,
+                                 const int8_t *__restrict__ k_eff, int Kmax,
+                                 const int32_t *__restrict__ cover_y, const int32_t *__restrict__ cover_x,
+                                 float *__restrict__ img) {
+  const int planes = g.Ly * g.Lx;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)planes * g.H * g.W) return;
+  const int x = (int)(e % g.W);
+  const int y = (int)((e / g.W) % g.H);
+  const int pl = (int)(e / ((int64_t)g.W * g.H));
+  const int y0 = cover_y[2 * y], y1 = cover_y[2 * y + 1];
+  const int x0 = cover_x[2 * x], x1 = cover_x[2 * x + 1];
+  float acc = 0.f;
+  int cnt = 0;
+  for (int iy = y0; iy <= y1; ++iy) {
+    const int py = y - origin(iy, g.stride, g.H, g.P);
+    for (int ix = x0; ix <= x1; ++ix) {
+      const int px = x - origin(ix, g.stride, g.W, g.P);
+      const int64_t b = (int64_t)iy * g.nx + ix;
+      const int k = k_eff[b];
+      const int n = (pl * g.P + py) * g.P + px;
+      float v = 0.f;
+      for (int j = 0; j < k; ++j)
+        v = fmaf(__ldg(coef + b * Kmax + j), __ldg(D0 + (int64_t)__ldg(support + b * Kmax + j) * N0 + n), v);
+      acc += v;
+      ++cnt;
+    }
+  }
+  img[e] = cnt ? acc / (float)cnt : 0.f;
+}
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void launch_extract(const GeomDev &g, int sense_kind, int shots, const float *meas, float *Y,
+                    int64_t B, int M, cudaStream_t s) {
+  (void)sense_kind; (void)shots;
+  if (B * M == 0) return;
+  extract_kernel<<<blocks(B * M, 256), 256, 0, s>>>(g, meas, Y, B, M);
+}
+
+void launch_downsample(const GeomDev &g, int level, const float *Y0, float *Yl, int64_t B,
+                       cudaStream_t s) {
+  const int Nl = (g.Ly / g.f[level][0]) * (g.Lx / g.f[level][1]) * (g.P / g.f[level][2]) *
+                 (g.P / g.f[level][3]);
+  if (B * Nl == 0) return;
+  downsample_kernel<<<blocks(B * Nl, 256), 256, 0, s>>>(g, level, Y0, Yl, B);
+}
+
+void launch_effective_dict(const GeomDev &g, int sense_kind, int shots, const uint8_t *codes,
+                           int level, int phase, const float *D, int T, int N, float *A, int M,
+                           cudaStream_t s) {
+  if ((int64_t)T * M == 0) return;
+  effective_dict_kernel<<<blocks((int64_t)T * M, 256), 256, 0, s>>>(g, sense_kind, shots, codes, level,
+                                                                     phase, D, T, N, A, M);
+}
+
+void launch_norms(const float *A, int T, int M, int Mp, float *inv_norm, __nv_bfloat16 *Abf,
+                  cudaStream_t s) {
+  if (T == 0) return;
+  norms_kernel<<<1, 1024, 0, s>>>(A, T, M, Mp, inv_norm, Abf);
+}
+
+void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *support,
+                      const float *coef, const int8_t *k_eff, int Kmax, const int32_t *cover_y,
+                      const int32_t *cover_x, float *img, cudaStream_t s) {
+  const int64_t n = (int64_t)g.Ly * g.Lx * g.H * g.W;
+  if (n == 0) return;
+  aggregate_kernel<<<blocks(n, 256), 256, 0, s>>>(g, D0, N0, support, coef, k_eff, Kmax, cover_y,
+                                                  cover_x, img);
+}
+
+}  // namespace csp

@@ -1,0 +1,222 @@
+"""GPU path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.
+
+Bar (FP32 path): support sets identical on >= 99.9 % of patches and, on those,
+per-patch reconstruction D_|Omega alpha within 1e-4 relative L2 of the
+oracle's; image PSNR within 0.05 dB.  Extraction is exact (a copy)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+from _gpu_util import budgets, compare, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+MATCH = 0.999
+
+SMALL = {
+    # name: workload kwargs -- several proxy tiles (64 patches) and ragged patch grids
+    "denoise": dict(name="denoise"),
+    "denoise_ragged": dict(name="denoise", H=64, W=72),
+    "bayer": dict(name="bayer", H=64, W=64),
+    "lightfield": dict(name="lightfield", H=48, W=48, T0=2048),
+}
+
+
+def _workload(key, links="paper", **kw):
+    spec = dict(SMALL[key])
+    name = spec.pop("name")
+    spec.update(kw)
+    w = synthetic.make_workload(name, links=links, **spec)
+    if key == "denoise_ragged":
+        w.geometry.stride = 3   # (72 - 8) % 3 != 0: clamped last origin on x
+        B = w.n_patches
+        w.K_levels = [np.full(B, int(k[0]), np.int32) for k in w.K_levels]
+    return w
+
+
+@pytest.mark.parametrize("key", list(SMALL))
+def test_extract_is_exact(key):
+    w = _workload(key)
+    g = run_gpu(w, "plain")
+    np.testing.assert_array_equal(g["Y"], oracle.extract_patches(w).astype(np.float32))
+
+
+@pytest.mark.parametrize("key", list(SMALL))
+def test_plain_parity(key):
+    w = _workload(key)
+    g = run_gpu(w, "plain")
+    o, a, k, _ = oracle.plain_omp(w)
+    rate, worst, bad = compare(w.dicts[0], g["sup"], g["coef"], g["keff"], o, a, k)
+    assert rate >= MATCH, f"support mismatch on patches {bad[:10]}"
+    assert worst <= REL_TOL
+
+
+@pytest.mark.parametrize("links", ["paper", "literal"])
+@pytest.mark.parametrize("key", list(SMALL))
+def test_cross_scale_parity(key, links):
+    w = _workload(key, links=links)
+    g = run_gpu(w, "cross_scale")
+    o, a, k, _ = oracle.cross_scale_omp(w)
+    rate, worst, bad = compare(w.dicts[0], g["sup"], g["coef"], g["keff"], o, a, k)
+    assert rate >= MATCH, f"support mismatch on patches {bad[:10]}"
+    assert worst <= REL_TOL
+    assert g["stats"]["overflow"] == 0
+
+
+@pytest.mark.parametrize("key", ["denoise", "bayer", "lightfield"])
+def test_aggregate_matches_oracle(key):
+    """Overlap-add of the GPU's own codes against the oracle's aggregation of
+    the same codes."""
+    w = _workload(key)
+    g = run_gpu(w, "cross_scale")
+    ref = oracle.aggregate(w, g["sup"], g["coef"].astype(np.float64), g["keff"])
+    scale = max(np.abs(ref).max(), 1e-30)
+    assert np.abs(g["img"] - ref).max() <= 1e-5 * scale
+
+
+@pytest.mark.parametrize("mode", ["plain", "cross_scale"])
+def test_psnr_matches_oracle(mode):
+    w = _workload("bayer")
+    g = run_gpu(w, mode)
+    o, a, k, _ = oracle.plain_omp(w) if mode == "plain" else oracle.cross_scale_omp(w)
+    img_o = oracle.aggregate(w, o, a, k)
+    assert abs(oracle.psnr(w.truth, g["img"]) - oracle.psnr(w.truth, img_o)) <= 0.05
+
+
+def test_bayer_all_four_phases():
+    """Stride 1 puts patch origins on every RGGB phase."""
+    w = synthetic.make_workload("bayer", H=24, W=24)
+    w.geometry.stride = 1
+    B = w.n_patches
+    w.K_levels = [np.full(B, int(k[0]), np.int32) for k in w.K_levels]
+    for mode, fn in (("plain", oracle.plain_omp), ("cross_scale", oracle.cross_scale_omp)):
+        g = run_gpu(w, mode)
+        o, a, k, _ = fn(w)
+        rate, worst, bad = compare(w.dicts[0], g["sup"], g["coef"], g["keff"], o, a, k)
+        assert rate >= MATCH and worst <= REL_TOL, (mode, bad[:10])
+
+
+def test_independent_problems_nonunit_norms():
+    """Phi = I over 1000 independent problems with column norms in [0.5, 2]
+    (the angle proxy divides by ||a_i||), K = 6, noisy."""
+    from paper_1511_05174_gb300.context import Context
+    A, Y, _ = synthetic.make_independent_problems(1000, 64, 320, 6, seed=3, sigma=0.05)
+    ctx = Context(0)
+    ctx.set_geometry(8, 8, (1, 1), 8, 8, [(1, 1, 1, 1)])
+    ctx.set_sensing("identity")
+    ctx.load_dictionary(0, A)
+    sup, coef, keff = ctx.solve(torch.from_numpy(Y).cuda(), "plain", "fp32", K=[6], Kmax=8)
+    o, a, k, _ = oracle.omp_batch([A] * len(Y), Y, 6)
+    rate, worst, bad = compare(A, sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy().astype(int), o, a, k)
+    assert rate >= MATCH and worst <= REL_TOL, bad[:10]
+
+
+def test_degenerate_inputs():
+    """Zero measurements (k_eff = 0), duplicate atoms (dependence), a zero
+    atom (never chosen) and K = 1."""
+    from paper_1511_05174_gb300.context import Context
+    A, Y, _ = synthetic.make_independent_problems(300, 64, 128, 4, seed=5, sigma=0.01)
+    A = A.copy()
+    A[7] = 0.0
+    A[9] = A[3]
+    Y = Y.copy()
+    Y[::10] = 0.0
+    # a measurement exactly in the span of {3, 9}: 9 duplicates 3, so OMP picks 3 then must not add 9
+    Y[1] = 2.0 * A[3]
+    ctx = Context(0)
+    ctx.set_geometry(8, 8, (1, 1), 8, 8, [(1, 1, 1, 1)])
+    ctx.set_sensing("identity")
+    ctx.load_dictionary(0, A)
+    for K in (1, 4, 10):
+        sup, coef, keff = ctx.solve(torch.from_numpy(Y).cuda(), "plain", "fp32", K=[K], Kmax=K)
+        s, c, kk = sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy().astype(int)
+        o, a, k, _ = oracle.omp_batch([A] * len(Y), Y, K)
+        assert np.all(kk[::10] == 0) and np.all(k[::10] == 0)
+        assert not np.any(s == 7)
+        assert np.all(np.isfinite(c))
+        assert s[1, 0] == 3 and kk[1] == 1
+        rate, worst, bad = compare(A, s, c, kk, o, a, k)
+        assert rate >= MATCH and worst <= REL_TOL, (K, bad[:10])
+
+
+def test_per_patch_budgets_lightfield():
+    """K drawn per patch in [8, 20] (and ceil(K/2), ceil(K/4) at coarser scales)."""
+    w = _workload("lightfield")
+    assert len(np.unique(w.K_levels[0])) > 3
+    for mode, fn in (("plain", oracle.plain_omp), ("cross_scale", oracle.cross_scale_omp)):
+        g = run_gpu(w, mode)
+        o, a, k, _ = fn(w)
+        assert np.all(g["keff"] <= w.K_levels[0])
+        rate, worst, bad = compare(w.dicts[0], g["sup"], g["coef"], g["keff"], o, a, k)
+        assert rate >= MATCH and worst <= REL_TOL, (mode, bad[:10])
+
+
+def test_deterministic():
+    w = _workload("bayer")
+    g1 = run_gpu(w, "cross_scale")
+    g2 = run_gpu(w, "cross_scale")
+    for key in ("sup", "coef", "keff", "img"):
+        np.testing.assert_array_equal(g1[key], g2[key])
+
+
+def test_full_size_bayer_sampled():
+    """Full 512x512 Bayer workload (64,009 patches) in the benchmark's launch
+    configuration; the oracle solves a seeded sample of 300 patches."""
+    w = synthetic.make_workload("bayer")
+    rng = np.random.default_rng(0)
+    sample = np.sort(rng.choice(w.n_patches, 300, replace=False))
+    Y = oracle.extract_patches(w)
+    for mode, fn in (("plain", oracle.plain_omp), ("cross_scale", oracle.cross_scale_omp)):
+        g = run_gpu(w, mode)
+        o, a, k, _ = fn(w, Y=Y, patches=sample)
+        rate, worst, bad = compare(w.dicts[0], g["sup"][sample], g["coef"][sample], g["keff"][sample], o, a, k)
+        assert rate >= MATCH and worst <= REL_TOL, (mode, sample[bad[:10]])
+
+
+def test_invalid_arguments_raise():
+    from paper_1511_05174_gb300 import _binding as b
+    from paper_1511_05174_gb300.context import Context
+    w = _workload("denoise")
+    ctx = Context(0)
+    ctx.load_workload(w)
+    bad = w.parents[0].copy()
+    bad[0] = 10_000
+    with pytest.raises(b.CspError) as e:
+        ctx.load_links(0, bad)
+    assert e.value.status == b.CSP_ERR_INVALID
+    Y = torch.zeros((w.n_patches, 64), device="cuda")
+    with pytest.raises(b.CspError):
+        ctx.solve(Y, "plain", "fp32", K=[40], Kmax=40)
+    small = Context(0, mem_budget_bytes=4096)
+    small.set_geometry(64, 64, (1, 1), 8, 8, [(1, 1, 1, 1)])
+    small.set_sensing("identity")
+    with pytest.raises(b.CspError) as e:
+        small.load_dictionary(0, w.dicts[0])
+    assert e.value.status == b.CSP_ERR_OOM
+
+
+def test_exactly_dependent_atom_ends_the_patch():
+    """Integer atoms make a_2 = a_0 + a_1 exact in float32: after a_0 and a_1
+    the only eligible atom depends on them, the FP64 pivot test rejects it and
+    k_eff = 2 (as the oracle's QR pivot does)."""
+    from paper_1511_05174_gb300.context import Context
+    rng = np.random.default_rng(12)
+    A = rng.integers(-3, 4, size=(3, 64)).astype(np.float32)
+    A[2] = A[0] + A[1]
+    Y = np.stack([A[0] + 0.5 * A[1] + 0.01 * rng.standard_normal(64) for _ in range(40)]).astype(np.float32)
+    ctx = Context(0)
+    ctx.set_geometry(8, 8, (1, 1), 8, 8, [(1, 1, 1, 1)])
+    ctx.set_sensing("identity")
+    ctx.load_dictionary(0, A)
+    sup, coef, keff = ctx.solve(torch.from_numpy(Y).cuda(), "plain", "fp32", K=[3], Kmax=3)
+    o, a, k, _ = oracle.omp_batch([A] * len(Y), Y, 3)
+    assert np.all(k == 2)
+    assert np.all(keff.cpu().numpy() == 2)
+    assert ctx.stats()["fp64_fallbacks"] >= 1
+    rate, worst, bad = compare(A, sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy().astype(int), o, a, k)
+    assert rate == 1.0 and worst <= REL_TOL
