@@ -153,8 +153,9 @@ def read_traffic(kernel: str, workload: str):
         return None
 
 
-def algorithmic(kind, w, prof_launches, stats, B):
-    """Algorithmic work of one launch of `kind` on this workload: (amount, unit, bound)."""
+def algorithmic(kind, w, prof_launches, stats, B, steps):
+    """Algorithmic work of one launch of `kind` on this workload: (amount, unit, bound).
+    `stats` are the solve statistics of one step."""
     g = w.geometry
     M = 64 if w.sensing.kind != "identity" else g.planes * g.P * g.P
     top = w.dicts[-1].shape[0]
@@ -162,8 +163,8 @@ def algorithmic(kind, w, prof_launches, stats, B):
         T = top if prof_launches.get("restricted") else w.dicts[0].shape[0]
         return 2.0 * M * T * B, "TFLOP/s", "alu"
     if kind == "restricted":
-        n = max(prof_launches.get("restricted", (1,))[0], 1)
-        return 2.0 * M * stats.get("restricted_scores", 0) / n, "TFLOP/s", "alu"
+        per_step = max(prof_launches.get("restricted", (1,))[0] / steps, 1.0)
+        return 2.0 * M * stats.get("restricted_scores", 0) / per_step, "TFLOP/s", "alu"
     if kind == "omp_update":
         # y, r read and r written, 4 B each, per patch
         return 3.0 * 4 * M * B, "GB/s", "hbm"
@@ -330,7 +331,7 @@ def main():
     launches = {k: v for k, v in cs_prof.items()}
     dom = max(cs_prof.items(), key=lambda kv: kv[1][1])[0]
     n_launch, tot_ms = cs_prof[dom]
-    amount, unit, bound = algorithmic(dom, w, launches, cs_stats, B)
+    amount, unit, bound = algorithmic(dom, w, launches, cs_stats, B, args.steps)
     roofline = None
     if amount is not None and n_launch:
         per_s = amount / (tot_ms / n_launch / 1e3)

@@ -204,6 +204,9 @@ csp_status prepare(csp_ctx *ctx, cudaStream_t s) {
     const bool ident = ctx->sense_kind == CSP_SENSE_IDENTITY;
     L.M = ident ? L.N : ctx->M;
     L.Mp = (L.M + 63) / 64 * 64;
+    if (!omp_dims_supported(L.M))
+      return fail(ctx, CSP_ERR_UNSUPPORTED, "problem dimension " + std::to_string(L.M) +
+                                                " of level " + std::to_string(l) + " must be a multiple of 4, <= 256");
     const int nph = ctx->sense_kind == CSP_SENSE_BAYER_RGGB ? 4 : 1;
     for (int p = 0; p < nph; ++p) {
       if (ident) {

@@ -139,6 +139,7 @@ void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_n
                        const int32_t *ids, int64_t n, const int32_t *omega, int ldo,
                        const int8_t *k_eff, const uint8_t *flags, int32_t *cand, cudaStream_t s);
 bool proxy_bf16_supported(int M, int T);
+bool omp_dims_supported(int M);  // M % 4 == 0 and M <= 256
 void launch_proxy_bf16(const __nv_bfloat16 *Rbf, int Mp, const __nv_bfloat16 *Abf, int T,
                        const int32_t *ids, int64_t n, const uint8_t *flags, int32_t *cand,
                        cudaStream_t s);

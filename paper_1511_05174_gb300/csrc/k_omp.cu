@@ -13,14 +13,24 @@
 // kTauPivot the factor is rebuilt from scratch in FP64 for that patch, which
 // also decides linear dependence (L_kk <= kEpsD64 ||a_k||) like a QR pivot.
 //
+// Work decomposition: a GROUP of G lanes (G = 4, 8 or 16) solves one patch;
+// a warp holds 32 / G patches.  Lane s of a group owns the float4 chunks
+// j = s, s + G, s + 2G, ... of every M-vector (y, r, columns), so the group
+// reads each column row as contiguous 16 G-byte segments and reduces a dot
+// product with log2(G) shuffles.  Loops whose trip counts differ between the
+// patches of a warp run to the warp maximum with per-group predicates, so all
+// shuffles execute in converged control flow.  The triangular factor, z, the
+// Gram column and alpha live in per-group shared memory.
+//
 // Kernels:
 //   proxy_fp32_kernel      full-dictionary proxy, FP32 CUDA-core GEMM of a tile of
 //                          64 residuals against all atoms, fused |.|/norm, mask and
 //                          argmax (one candidate per patch)
-//   omp_update_kernel      one warp per patch: (re-score candidates in FP32,) merge,
-//                          projection and residue; state in global memory
-//   omp_restricted_kernel  one warp per patch, all iterations of the restricted OMP
-//                          over the children f(Omega_up) of the coarser support
+//   omp_update_kernel      one iteration for every patch: (re-score the proxy's
+//                          candidates in FP32,) merge, projection, residue; state
+//                          kept in global memory between launches
+//   omp_restricted_kernel  all iterations of the restricted OMP over the children
+//                          f(Omega_up) of the coarser support (Algorithm 2 fine step)
 #include "csp_internal.cuh"
 
 namespace csp {
@@ -29,26 +39,9 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }
+__host__ __device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }
+__host__ __device__ __forceinline__ int up16(int bytes) { return (bytes + 15) & ~15; }
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
-    v = w > v ? w : v;
-  }
-  return v;
-}
 // Packed argmax key: larger score first, then lower index.  0 = no candidate.
 __device__ __forceinline__ unsigned long long pack_key(float score, int idx) {
   return ((unsigned long long)__float_as_uint(score) << 32) | (0xffffffffu - (unsigned)idx);
@@ -57,192 +50,232 @@ __device__ __forceinline__ int key_idx(unsigned long long k) {
   return (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
 }
 
-// ---------------------------------------------------------------------------
-// Shared projection step: append column q to the support of one patch.
-//
-// Lanes hold y, r and a_q over m = lane + 32 t.  L (packed), z, omega and alpha
-// live in global or shared memory (generic pointers).  Returns 1 when q was
-// appended (alpha, r, rsq updated), 0 when q depends on the chosen columns
-// (nothing changes; the patch ends).
-// ---------------------------------------------------------------------------
-template <int MPL>
-__device__ int omp_append(int lane, int M, const float *__restrict__ A, int q,
-                          const float (&aq)[MPL], const float (&yv)[MPL], float (&rv)[MPL], int k,
-                          int32_t *omega, float *alpha, float *L, float *z, uint8_t &fl,
-                          double *L64, float &rsq, int64_t *stats) {
-  if (!(fl & 2)) {
-    // Gram column v_j = <a_{omega_j}, a_q>, lane j keeps v_j.
-    float vj = 0.f;
-    for (int j = 0; j < k; ++j) {
-      const float *aj = A + (int64_t)omega[j] * M;
-      float p = 0.f;
+// ---- group reductions (every lane of the warp must call them together) ----
+template <int G>
+__device__ __forceinline__ float gsum(float v) {
 #pragma unroll
-      for (int t = 0; t < MPL; ++t) {
-        const int m = lane + 32 * t;
-        if (m < M) p = fmaf(__ldg(aj + m), aq[t], p);
-      }
-      p = warp_sum(p);
-      if (lane == j) vj = p;
-    }
-    float aa = 0.f;
+  for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+template <int G>
+__device__ __forceinline__ unsigned long long gmax(unsigned long long v) {
 #pragma unroll
-    for (int t = 0; t < MPL; ++t) aa = fmaf(aq[t], aq[t], aa);
-    aa = warp_sum(aa);
-    // w = L^{-1} v (column-oriented forward substitution across lanes)
-    for (int i = 0; i < k; ++i) {
-      const float wi = __shfl_sync(kFull, vj, i) / L[tri(i) + i];
-      if (lane == i) vj = wi;
-      else if (lane > i && lane < k) vj = fmaf(-L[tri(lane) + i], wi, vj);
-    }
-    const float ww = warp_sum(lane < k ? vj * vj : 0.f);
-    const float d = aa - ww;
-    if (d >= kTauPivot * aa && aa > 0.f) {
-      const float lkk = sqrtf(d);
-      float bq = 0.f;
-#pragma unroll
-      for (int t = 0; t < MPL; ++t) bq = fmaf(aq[t], yv[t], bq);
-      bq = warp_sum(bq);
-      const float zprev = (lane < k) ? z[lane] : 0.f;
-      const float zz = warp_sum(lane < k ? vj * zprev : 0.f);
-      const float zk = (bq - zz) / lkk;
-      __syncwarp();
-      if (lane < k) L[tri(k) + lane] = vj;
-      if (lane == 0) { L[tri(k) + k] = lkk; z[k] = zk; omega[k] = q; }
-      __syncwarp();
-      // alpha = L^{-T} z (column-oriented back substitution; lane i ends with alpha_i)
-      float acc = (lane < k) ? zprev : (lane == k ? zk : 0.f);
-      for (int j = k; j >= 0; --j) {
-        const float aj = __shfl_sync(kFull, acc, j) / L[tri(j) + j];
-        if (lane == j) acc = aj;
-        else if (lane < j) acc = fmaf(-L[tri(j) + lane], aj, acc);
-      }
-      if (lane <= k) alpha[lane] = acc;
-      // residue r = y - A_Omega alpha
-      float r2 = 0.f;
-#pragma unroll
-      for (int t = 0; t < MPL; ++t) rv[t] = yv[t];
-      for (int j = 0; j <= k; ++j) {
-        const float aj = __shfl_sync(kFull, acc, j);
-        if (j == k) {
-#pragma unroll
-          for (int t = 0; t < MPL; ++t) rv[t] = fmaf(-aj, aq[t], rv[t]);
-        } else {
-          const float *col = A + (int64_t)omega[j] * M;
-#pragma unroll
-          for (int t = 0; t < MPL; ++t) {
-            const int m = lane + 32 * t;
-            if (m < M) rv[t] = fmaf(-aj, __ldg(col + m), rv[t]);
-          }
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < MPL; ++t) r2 = fmaf(rv[t], rv[t], r2);
-      rsq = warp_sum(r2);
-      __syncwarp();
-      return 1;
-    }
-    // Low pivot ratio: switch this patch to FP64 projections for good.
-    fl |= 2;
-    if (lane == 0 && stats) atomicAdd((unsigned long long *)&stats[0], 1ull);
+  for (int o = G / 2; o; o >>= 1) {
+    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
+    v = w > v ? w : v;
   }
-  // FP64 path: rebuild the Cholesky factor of A_S^T A_S for S = omega[0..k-1] + q,
-  // entry by entry (all lanes compute the same scalars; lane 0 stores).
+  return v;
+}
+
+__device__ __forceinline__ float dot4(const float4 &a, const float4 &b) {
+  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+}
+
+// Chunks j = s + G t (t < NCH) of a 16-byte aligned row of nv float4; zeros past nv.
+template <int G, int NCH>
+__device__ __forceinline__ void load_chunks(float4 (&v)[NCH], const float *__restrict__ row, int nv, int s,
+                                            bool on) {
+  const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+  for (int t = 0; t < NCH; ++t) {
+    const int j = s + G * t;
+    v[t] = (on && j < nv) ? __ldg(r4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+template <int NCH>
+__device__ __forceinline__ float dotc(const float4 (&a)[NCH], const float4 (&b)[NCH]) {
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int t = 0; t < NCH; ++t) {
+    if (t & 1) s1 += dot4(a[t], b[t]);
+    else s0 += dot4(a[t], b[t]);
+  }
+  return s0 + s1;
+}
+
+// ---------------------------------------------------------------------------
+// Per-group shared-memory block.
+// ---------------------------------------------------------------------------
+struct GrpSmem {
+  double *L64;   // [tri(Kb+1)] FP64 factor (fallback path)
+  float *L;      // [tri(Kb)]   packed lower factor
+  float *Linv;   // [Kb]        1 / L_jj
+  float *z;      // [Kb]
+  float *V;      // [Kb+1]      Gram column / back-substitution accumulator
+  float *W;      // [Kb+1]      w = L^{-1} v, then alpha
+  int *om;       // [Kb]        chosen atoms
+  int *cs;       // [cap]       candidate atoms (restricted kernel)
+  float *invn;   // [cap]       their 1/||a|| (-1 once chosen or ineligible)
+  int *misc;     // [4]
+};
+
+__host__ __device__ inline int grp_smem_bytes(int Kb, int cap) {
+  return up16(8 * tri(Kb + 1)) + up16(4 * tri(Kb)) + 2 * up16(4 * Kb) + 2 * up16(4 * (Kb + 1)) +
+         up16(4 * Kb) + 2 * up16(4 * cap) + 16;
+}
+
+__device__ inline GrpSmem carve(char *p, int Kb, int cap) {
+  GrpSmem S;
+  S.L64 = reinterpret_cast<double *>(p); p += up16(8 * tri(Kb + 1));
+  S.L = reinterpret_cast<float *>(p); p += up16(4 * tri(Kb));
+  S.Linv = reinterpret_cast<float *>(p); p += up16(4 * Kb);
+  S.z = reinterpret_cast<float *>(p); p += up16(4 * Kb);
+  S.V = reinterpret_cast<float *>(p); p += up16(4 * (Kb + 1));
+  S.W = reinterpret_cast<float *>(p); p += up16(4 * (Kb + 1));
+  S.om = reinterpret_cast<int *>(p); p += up16(4 * Kb);
+  S.cs = reinterpret_cast<int *>(p); p += up16(4 * cap);
+  S.invn = reinterpret_cast<float *>(p); p += up16(4 * cap);
+  S.misc = reinterpret_cast<int *>(p);
+  return S;
+}
+
+// FP64 projection from scratch, run by one lane: Cholesky of A_S^T A_S for
+// S = om[0..k-1] + q with entries accumulated in FP64 from the FP32 columns,
+// then z = L^{-1} A_S^T y and alpha = L^{-T} z (into S.W).  Returns false when
+// q depends on the chosen columns.
+__device__ bool fp64_projection(const float *__restrict__ A, int M, const float *__restrict__ y,
+                                const GrpSmem &S, int k, int q) {
+  double *L64 = S.L64;
   for (int i = 0; i <= k; ++i) {
-    const float *ci = (i < k) ? A + (int64_t)omega[i] * M : nullptr;
+    const float *ci = A + (int64_t)(i < k ? S.om[i] : q) * M;
     for (int j = 0; j <= i; ++j) {
-      const float *cj = (j < k) ? A + (int64_t)omega[j] * M : nullptr;
+      const float *cj = A + (int64_t)(j < k ? S.om[j] : q) * M;
       double g = 0.0;
-#pragma unroll
-      for (int t = 0; t < MPL; ++t) {
-        const int m = lane + 32 * t;
-        if (m < M) {
-          const double u = ci ? (double)__ldg(ci + m) : (double)aq[t];
-          const double v = cj ? (double)__ldg(cj + m) : (double)aq[t];
-          g = fma(u, v, g);
-        }
-      }
-      g = warp_sum_d(g);
-      double s = g;
-      for (int p = 0; p < j; ++p) s -= L64[tri(i) + p] * L64[tri(j) + p];
-      double val;
+      for (int m = 0; m < M; ++m) g = fma((double)ci[m], (double)cj[m], g);
+      double r = g;
+      for (int p = 0; p < j; ++p) r -= L64[tri(i) + p] * L64[tri(j) + p];
       if (j < i) {
-        val = s / L64[tri(j) + j];
+        L64[tri(i) + j] = r / L64[tri(j) + j];
       } else {
-        if (i == k && !(s > kEpsD64 * kEpsD64 * g)) return 0;  // dependent column
-        val = sqrt(s > 0.0 ? s : 0.0);
+        if (i == k && !(r > kEpsD64 * kEpsD64 * g)) return false;
+        L64[tri(i) + i] = sqrt(r > 0.0 ? r : 0.0);
       }
-      __syncwarp();
-      if (lane == 0) L64[tri(i) + j] = val;
-      __syncwarp();
     }
   }
-  // z = L^{-1} A_S^T y, alpha = L^{-T} z, serially in FP64 (identical on all lanes).
   double zb[CSP_MAX_K + 1];
   for (int i = 0; i <= k; ++i) {
-    const float *ci = (i < k) ? A + (int64_t)omega[i] * M : nullptr;
+    const float *ci = A + (int64_t)(i < k ? S.om[i] : q) * M;
     double bi = 0.0;
-#pragma unroll
-    for (int t = 0; t < MPL; ++t) {
-      const int m = lane + 32 * t;
-      if (m < M) bi = fma(ci ? (double)__ldg(ci + m) : (double)aq[t], (double)yv[t], bi);
-    }
-    bi = warp_sum_d(bi);
+    for (int m = 0; m < M; ++m) bi = fma((double)ci[m], (double)y[m], bi);
     for (int p = 0; p < i; ++p) bi -= L64[tri(i) + p] * zb[p];
     zb[i] = bi / L64[tri(i) + i];
   }
   for (int i = k; i >= 0; --i) {
-    double s = zb[i];
-    for (int j = i + 1; j <= k; ++j) s -= L64[tri(j) + i] * zb[j];
-    zb[i] = s / L64[tri(i) + i];  // zb now holds alpha_i for indices >= i
+    double r = zb[i];
+    for (int j = i + 1; j <= k; ++j) r -= L64[tri(j) + i] * zb[j];
+    zb[i] = r / L64[tri(i) + i];
+  }
+  for (int i = 0; i <= k; ++i) S.W[i] = (float)zb[i];
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// Group projection step.  `act`: this group appends atom q as its k-th column
+// (S.om[0..k-1] chosen; S.L/Linv/z valid unless fl has bit 1).  Lanes hold
+// their chunks of y and r.  On success alpha is in S.W[0..k], r and rsq are
+// updated, S.om[k] = q, and the FP32 factor gained row k.  Returns whether q
+// was appended (false: q depends on the chosen columns).  Warp-collective.
+// ---------------------------------------------------------------------------
+template <int G, int NCH>
+__device__ bool grp_append(bool act, int s, int M, const float *__restrict__ A,
+                           const float *__restrict__ yrow, int q, int k, const float4 (&yv)[NCH],
+                           float4 (&rv)[NCH], const GrpSmem &S, uint8_t &fl, float &rsq,
+                           int64_t *stats) {
+  const int nv = M >> 2;
+  float4 aq[NCH];
+  load_chunks<G, NCH>(aq, A + (int64_t)q * M, nv, s, act);
+  const float aa = gsum<G>(dotc<NCH>(aq, aq));
+  const float bq = gsum<G>(dotc<NCH>(aq, yv));
+  const int kw = __reduce_max_sync(kFull, act ? k : 0);
+  // Gram column V[j] = <a_{om_j}, a_q>
+  for (int j = 0; j < kw; ++j) {
+    const bool o = act && j < k;
+    float4 c[NCH];
+    load_chunks<G, NCH>(c, A + (int64_t)(o ? S.om[j] : 0) * M, nv, s, o);
+    const float v = gsum<G>(dotc<NCH>(c, aq));
+    if (o && s == 0) S.V[j] = v;
   }
   __syncwarp();
-  if (lane == 0) omega[k] = q;
-  if (lane <= k) {
-    double a = 0.0;
-    for (int i = 0; i <= k; ++i) if (i == lane) a = zb[i];
-    alpha[lane] = (float)a;
+  const bool f32 = act && !(fl & 2);
+  // W = L^{-1} V, column-oriented: step i finalises W_i and updates V_j, j > i
+  for (int i = 0; i < kw; ++i) {
+    if (f32 && i < k) {
+      const float wi = S.V[i] * S.Linv[i];
+      if (s == 0) S.W[i] = wi;
+      for (int j = i + 1 + s; j < k; j += G) S.V[j] = fmaf(-S.L[tri(j) + i], wi, S.V[j]);
+    }
+    __syncwarp();
   }
-  __syncwarp();
-  double rr[MPL];
-#pragma unroll
-  for (int t = 0; t < MPL; ++t) rr[t] = (double)yv[t];
-  for (int j = 0; j <= k; ++j) {
-    const float *col = (j < k) ? A + (int64_t)omega[j] * M : nullptr;
-#pragma unroll
-    for (int t = 0; t < MPL; ++t) {
-      const int m = lane + 32 * t;
-      if (m < M) rr[t] -= zb[j] * (col ? (double)__ldg(col + m) : (double)aq[t]);
+  float ww = 0.f, zz = 0.f;
+  if (f32)
+    for (int j = s; j < k; j += G) {
+      ww = fmaf(S.W[j], S.W[j], ww);
+      zz = fmaf(S.W[j], S.z[j], zz);
+    }
+  ww = gsum<G>(ww);
+  zz = gsum<G>(zz);
+  const float d = aa - ww;
+  const bool ok32 = f32 && aa > 0.f && d >= kTauPivot * aa;
+  if (f32 && !ok32) {
+    fl |= 2;
+    if (s == 0 && stats) atomicAdd((unsigned long long *)&stats[0], 1ull);
+  }
+  if (ok32) {
+    const float lkk = sqrtf(d), il = 1.f / lkk;
+    for (int j = s; j < k; j += G) S.L[tri(k) + j] = S.W[j];
+    if (s == 0) {
+      S.L[tri(k) + k] = lkk;
+      S.Linv[k] = il;
+      S.z[k] = (bq - zz) * il;
     }
   }
-  float r2 = 0.f;
-#pragma unroll
-  for (int t = 0; t < MPL; ++t) {
-    const int m = lane + 32 * t;
-    rv[t] = (m < M) ? (float)rr[t] : 0.f;
-    r2 = fmaf(rv[t], rv[t], r2);
+  __syncwarp();
+  // back substitution alpha = L^{-T} z (accumulator V; alpha into W)
+  if (ok32)
+    for (int i = s; i <= k; i += G) S.V[i] = S.z[i];
+  __syncwarp();
+  for (int j = kw; j >= 0; --j) {
+    if (ok32 && j <= k) {
+      const float aj = S.V[j] * S.Linv[j];
+      if (s == 0) S.W[j] = aj;
+      for (int i = s; i < j; i += G) S.V[i] = fmaf(-S.L[tri(j) + i], aj, S.V[i]);
+    }
+    __syncwarp();
   }
-  rsq = warp_sum(r2);
-  return 1;
-}
-
-template <int MPL>
-__device__ __forceinline__ void load_vec(float (&v)[MPL], const float *__restrict__ p, int M, int lane) {
+  // FP64 rebuild for the groups that need it (rare; one lane per group)
+  const bool go64 = act && !ok32;
+  if (go64 && s == 0) S.misc[0] = fp64_projection(A, M, yrow, S, k, q) ? 1 : 0;
+  __syncwarp();
+  const bool appended = ok32 || (go64 && S.misc[0] != 0);
+  // residue r = y - A_Omega alpha
+  if (appended) {
 #pragma unroll
-  for (int t = 0; t < MPL; ++t) {
-    const int m = lane + 32 * t;
-    v[t] = (m < M) ? __ldg(p + m) : 0.f;
+    for (int t = 0; t < NCH; ++t) rv[t] = yv[t];
   }
-}
-
-template <int MPL>
-__device__ __forceinline__ float dot_vec(const float (&v)[MPL], const float *__restrict__ p, int M, int lane) {
-  float s = 0.f;
+  for (int j = 0; j <= kw; ++j) {
+    const bool o = appended && j <= k;
+    if (o) {
+      const float aj = S.W[j];
+      float4 c[NCH];
+      if (j < k) load_chunks<G, NCH>(c, A + (int64_t)S.om[j] * M, nv, s, true);
 #pragma unroll
-  for (int t = 0; t < MPL; ++t) {
-    const int m = lane + 32 * t;
-    if (m < M) s = fmaf(__ldg(p + m), v[t], s);
+      for (int t = 0; t < NCH; ++t) {
+        const float4 col = (j < k) ? c[t] : aq[t];
+        rv[t].x = fmaf(-aj, col.x, rv[t].x);
+        rv[t].y = fmaf(-aj, col.y, rv[t].y);
+        rv[t].z = fmaf(-aj, col.z, rv[t].z);
+        rv[t].w = fmaf(-aj, col.w, rv[t].w);
+      }
+    }
   }
-  return warp_sum(s);
+  const float r2 = gsum<G>(dotc<NCH>(rv, rv));
+  if (appended) {
+    rsq = r2;
+    if (s == 0) S.om[k] = q;
+  }
+  __syncwarp();
+  return appended;
 }
 
 // ---------------------------------------------------------------------------
@@ -362,111 +395,136 @@ proxy_fp32_kernel(const float *__restrict__ R, int M, const float *__restrict__ 
 }
 
 // ---------------------------------------------------------------------------
-// Update: one warp per patch of the id list.
+// Update: one iteration of every patch of the id list (one group per patch).
 // ---------------------------------------------------------------------------
-template <int MPL>
-__global__ void __launch_bounds__(256)
+constexpr int GRP_WARPS = 4;
+
+template <int G, int NCH>
+__global__ void __launch_bounds__(GRP_WARPS * 32)
 omp_update_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                   const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
                   int n_cand, const int8_t *__restrict__ Kp, int Kuni, OmpState st, int64_t *stats) {
-  extern __shared__ __align__(16) double smem64[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t wi = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
-  if (wi >= n) return;
-  const int64_t b = ids ? ids[wi] : wi;
-  uint8_t fl = st.flags[b];
-  if (fl & 1) return;
-  const int k = st.k_eff[b];
-  int Kb = Kp ? (int)Kp[b] : Kuni;
-  Kb = Kb < st.Kb ? Kb : st.Kb;
-  int32_t *om = st.omega + b * st.ldo;
-  float *al = st.alpha + b * st.ldo;
-  if (k >= Kb) {
-    if (lane == 0) st.flags[b] = fl | 1;
-    return;
+  constexpr int NG = 32 / G;
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
+  const int64_t wbase = ((int64_t)blockIdx.x * GRP_WARPS + wib) * NG;
+  if (wbase >= n) return;  // whole warp
+  const int64_t wi = wbase + g;
+  const bool valid = wi < n;
+  const int64_t b = valid ? (ids ? ids[wi] : wi) : 0;
+  const GrpSmem S = carve(smem_raw + (size_t)(wib * NG + g) * grp_smem_bytes(st.Kb, 0), st.Kb, 0);
+  const int nv = M >> 2;
+  uint8_t fl = valid ? st.flags[b] : 1;
+  const int k = valid ? st.k_eff[b] : 0;
+  int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
+  Kpb = Kpb < st.Kb ? Kpb : st.Kb;
+  bool act = !(fl & 1) && k < Kpb;
+  if (valid && !(fl & 1) && k >= Kpb && s == 0) st.flags[b] = fl | 1;
+  int32_t *om_g = st.omega + b * st.ldo;
+  const float *yrow = Y + b * M;
+  float4 yv[NCH], rv[NCH];
+  load_chunks<G, NCH>(yv, yrow, nv, s, act);
+  load_chunks<G, NCH>(rv, st.R + b * M, nv, s, act);
+  const float ysq = gsum<G>(dotc<NCH>(yv, yv));
+  const float rsq0 = gsum<G>(dotc<NCH>(rv, rv));
+  if (act && rsq0 <= kEpsR32 * ysq) {
+    act = false;
+    if (s == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
   }
-  float yv[MPL], rv[MPL];
-  load_vec<MPL>(yv, Y + b * M, M, lane);
-  load_vec<MPL>(rv, st.R + b * M, M, lane);
-  const float ysq = warp_sum([&] { float s = 0.f;
-#pragma unroll
-    for (int t = 0; t < MPL; ++t) s = fmaf(yv[t], yv[t], s); return s; }());
-  float rsq0 = 0.f;
-#pragma unroll
-  for (int t = 0; t < MPL; ++t) rsq0 = fmaf(rv[t], rv[t], rsq0);
-  rsq0 = warp_sum(rsq0);
-  if (rsq0 <= kEpsR32 * ysq) {
-    if (lane == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
-    return;
-  }
-  // Candidate choice: the FP32 proxy's argmax, or the best of the re-scored top candidates.
+  // stage the chosen atoms
+  if (act)
+    for (int j = s; j < k; j += G) S.om[j] = om_g[j];
+  __syncwarp();
+  // candidate: the proxy's argmax, or the best of its re-scored top candidates
   const int32_t *cb = st.cand + b * kTopP;
   int q = -1;
   if (n_cand <= 1) {
-    q = cb[0];
+    q = act ? cb[0] : -1;
   } else {
     unsigned long long best = 0ull;
     for (int c = 0; c < n_cand; ++c) {
-      const int a = cb[c];
-      if (a < 0) continue;
-      const float inv = __ldg(inv_norm + a);
-      if (!(inv > 0.f)) continue;
-      const bool chosen = __any_sync(kFull, lane < k && om[lane] == a);
-      if (chosen) continue;
-      const float s = fabsf(dot_vec<MPL>(rv, A + (int64_t)a * M, M, lane)) * inv;
-      const unsigned long long key = pack_key(s, a);
-      best = key > best ? key : best;
+      const int a = act ? cb[c] : -1;
+      bool ok = a >= 0 && __ldg(inv_norm + a) > 0.f;
+      bool dup = false;
+      if (ok)
+        for (int j = s; j < k; j += G) dup |= (S.om[j] == a);
+      const unsigned bal = __ballot_sync(kFull, dup);
+      ok = ok && ((bal >> (g * G)) & ((G == 32) ? 0xffffffffu : ((1u << G) - 1u))) == 0u;
+      float4 c4[NCH];
+      load_chunks<G, NCH>(c4, A + (int64_t)(ok ? a : 0) * M, nv, s, ok);
+      const float sc = gsum<G>(dotc<NCH>(c4, rv));
+      if (ok) {
+        const unsigned long long key = pack_key(fabsf(sc) * __ldg(inv_norm + a), a);
+        best = key > best ? key : best;
+      }
     }
     q = best ? key_idx(best) : -1;
   }
-  if (q < 0) {
-    if (lane == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
+  if (act && q < 0) {
+    act = false;
+    if (s == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
+  }
+  float *L_g = st.Lpk + b * tri(st.Kb);
+  float *z_g = st.z + b * st.Kb;
+  if (act && !(fl & 2)) {
+    for (int e = s; e < tri(k); e += G) S.L[e] = L_g[e];
+    for (int j = s; j < k; j += G) {
+      S.z[j] = z_g[j];
+      S.Linv[j] = 1.f / L_g[tri(j) + j];
+    }
+  }
+  __syncwarp();
+  float rsq = rsq0;
+  const bool ok = grp_append<G, NCH>(act, s, M, A, yrow, act ? q : 0, k, yv, rv, S, fl, rsq, stats);
+  if (act && !ok) {
+    if (s == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
     return;
   }
-  float aq[MPL];
-  load_vec<MPL>(aq, A + (int64_t)q * M, M, lane);
-  double *L64 = smem64 + (size_t)wib * tri(st.Kb + 1);
-  float rsq = 0.f;
-  const int ok = omp_append<MPL>(lane, M, A, q, aq, yv, rv, k, om, al, st.Lpk + b * tri(st.Kb),
-                                 st.z + b * st.Kb, fl, L64, rsq, stats);
-  if (!ok) {
-    if (lane == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
-    return;
-  }
+  if (!act) return;
+  // write back
+  if (!(fl & 2))
+    for (int j = s; j <= k; j += G) L_g[tri(k) + j] = S.L[tri(k) + j];
+  for (int j = s; j <= k; j += G) st.alpha[b * st.ldo + j] = S.W[j];
+  float4 *R4 = reinterpret_cast<float4 *>(st.R + b * M);
 #pragma unroll
-  for (int t = 0; t < MPL; ++t) {
-    const int m = lane + 32 * t;
-    if (m < M) st.R[b * M + m] = rv[t];
+  for (int t = 0; t < NCH; ++t) {
+    const int j = s + G * t;
+    if (j < nv) R4[j] = rv[t];
   }
   if (st.Rbf) {
     const int Mp = (M + 63) / 64 * 64;
-    for (int t = 0; t < (Mp + 31) / 32; ++t) {
-      const int m = lane + 32 * t;
-      float v = 0.f;
+    __nv_bfloat16 *rb = st.Rbf + b * Mp;
 #pragma unroll
-      for (int u = 0; u < MPL; ++u) if (u == t) v = rv[u];
-      if (m < Mp) st.Rbf[b * Mp + m] = __float2bfloat16_rn(m < M ? v : 0.f);
+    for (int t = 0; t < NCH; ++t) {
+      const int j = s + G * t;
+      if (j < nv) {
+        rb[4 * j + 0] = __float2bfloat16_rn(rv[t].x);
+        rb[4 * j + 1] = __float2bfloat16_rn(rv[t].y);
+        rb[4 * j + 2] = __float2bfloat16_rn(rv[t].z);
+        rb[4 * j + 3] = __float2bfloat16_rn(rv[t].w);
+      }
     }
   }
-  if (lane == 0) {
+  if (s == 0) {
+    if (!(fl & 2)) z_g[k] = S.z[k];
+    om_g[k] = q;
     st.k_eff[b] = (int8_t)(k + 1);
     uint8_t nf = fl;
-    if (k + 1 >= Kb) nf |= 1;
+    if (k + 1 >= Kpb) nf |= 1;
     if (rsq <= kEpsR32 * ysq) nf |= 1;
-    if ((nf & 1) && k + 1 < Kb) atomicAdd((unsigned long long *)&stats[1], 1ull);
+    if ((nf & 1) && k + 1 < Kpb) atomicAdd((unsigned long long *)&stats[1], 1ull);
     st.flags[b] = nf;
   }
 }
 
 // ---------------------------------------------------------------------------
-// Restricted OMP (fine step of Algorithm 2): one warp per patch, all iterations.
-// Candidates C = children of the coarser support (disjoint lists, since every
-// fine atom has one parent), proxy over C only, projection as above.
+// Restricted OMP (fine step of Algorithm 2), all iterations, one group per
+// patch.  Candidates C = children of the coarser support (disjoint lists:
+// every finer atom has one parent); the proxy scores only C, two candidates
+// per group and pass, rows read from the L2-resident effective dictionary.
 // ---------------------------------------------------------------------------
-constexpr int RS_WARPS = 4;
-
-template <int MPL>
-__global__ void __launch_bounds__(RS_WARPS * 32)
+template <int G, int NCH>
+__global__ void __launch_bounds__(GRP_WARPS * 32)
 omp_restricted_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                       const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
                       const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx,
@@ -474,113 +532,121 @@ omp_restricted_kernel(const float *__restrict__ Y, int M, const float *__restric
                       const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                       int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
                       int8_t *__restrict__ k_eff, int64_t *stats) {
-  extern __shared__ __align__(16) double smem64[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  // per-warp shared layout: L64 | L | z | alpha | r | omega | cand
-  const int n64 = tri(Kb + 1);
-  const int nf = tri(Kb) + 2 * Kb + M;
-  const int per_warp_bytes = ((n64 * 8 + nf * 4 + (Kb + cap) * 4) + 15) / 16 * 16;
-  char *base = reinterpret_cast<char *>(smem64) + (size_t)wib * per_warp_bytes;
-  double *L64 = reinterpret_cast<double *>(base);
-  float *Ls = reinterpret_cast<float *>(base + n64 * 8);
-  float *zs = Ls + tri(Kb);
-  float *as = zs + Kb;
-  float *rs = as + Kb;
-  int32_t *oms = reinterpret_cast<int32_t *>(rs + M);
-  int32_t *cs = oms + Kb;
-
-  const int64_t wi = (int64_t)blockIdx.x * RS_WARPS + wib;
-  if (wi >= n) return;
-  const int64_t b = ids ? ids[wi] : wi;
-  int Kpb = Kp ? (int)Kp[b] : Kuni;
+  constexpr int NG = 32 / G;
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
+  const int64_t wbase = ((int64_t)blockIdx.x * GRP_WARPS + wib) * NG;
+  if (wbase >= n) return;  // whole warp
+  const int64_t wi = wbase + g;
+  const bool valid = wi < n;
+  const int64_t b = valid ? (ids ? ids[wi] : wi) : 0;
+  const GrpSmem S = carve(smem_raw + (size_t)(wib * NG + g) * grp_smem_bytes(Kb, cap), Kb, cap);
+  const int nv = M >> 2;
+  int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
   Kpb = Kpb < Kb ? Kpb : Kb;
 
   // candidate set f(Omega_up)
   int nc = 0;
-  const int kup = keff_up[b];
-  bool overflow = false;
-  for (int j = 0; j < kup; ++j) {
-    const int p = omega_up[b * ldo_up + j];
-    const int s = child_off[p], e = child_off[p + 1];
-    for (int i = lane; i < e - s; i += 32)
-      if (nc + i < cap) cs[nc + i] = child_idx[s + i];
-    nc += e - s;
+  if (valid) {
+    const int kup = keff_up[b];
+    for (int j = 0; j < kup; ++j) {
+      const int p = omega_up[b * ldo_up + j];
+      const int c0 = child_off[p], c1 = child_off[p + 1];
+      for (int i = s; i < c1 - c0; i += G)
+        if (nc + i < cap) {
+          const int a = child_idx[c0 + i];
+          S.cs[nc + i] = a;
+          S.invn[nc + i] = __ldg(inv_norm + a);
+        }
+      nc += c1 - c0;
+    }
+    if (nc > cap) {
+      if (s == 0) atomicAdd((unsigned long long *)&stats[3], 1ull);
+      nc = cap;
+    }
   }
-  if (nc > cap) { overflow = true; nc = cap; }
-  if (overflow && lane == 0) atomicAdd((unsigned long long *)&stats[3], 1ull);
   __syncwarp();
-
-  float yv[MPL], rv[MPL];
-  load_vec<MPL>(yv, Y + b * M, M, lane);
+  const float *yrow = Y + b * M;
+  float4 yv[NCH], rv[NCH];
+  load_chunks<G, NCH>(yv, yrow, nv, s, valid);
 #pragma unroll
-  for (int t = 0; t < MPL; ++t) {
-    rv[t] = yv[t];
-    const int m = lane + 32 * t;
-    if (m < M) rs[m] = yv[t];
-  }
-  float ysq = 0.f;
-#pragma unroll
-  for (int t = 0; t < MPL; ++t) ysq = fmaf(yv[t], yv[t], ysq);
-  ysq = warp_sum(ysq);
+  for (int t = 0; t < NCH; ++t) rv[t] = yv[t];
+  const float ysq = gsum<G>(dotc<NCH>(yv, yv));
   float rsq = ysq;
-  unsigned sel = 0u;  // bit t: candidate slot lane + 32 t already chosen
+  bool act = valid && Kpb > 0;
   uint8_t fl = 0;
   int k = 0, scored = 0;
-  __syncwarp();
-  while (k < Kpb) {
-    if (rsq <= kEpsR32 * ysq) break;
-    ++scored;
+  const int Kw = __reduce_max_sync(kFull, Kpb);
+  for (int it = 0; it < Kw; ++it) {
+    act = act && k < Kpb && !(rsq <= kEpsR32 * ysq);
+    if (!__any_sync(kFull, act)) break;
+    if (act) ++scored;
+    // proxy over the candidates, two per pass
     unsigned long long best = 0ull;
-    for (int c = lane, t = 0; c < nc; c += 32, ++t) {
-      if ((sel >> t) & 1u) continue;
-      const int a = cs[c];
-      const float inv = __ldg(inv_norm + a);
-      if (!(inv > 0.f)) continue;
-      const float *col = A + (int64_t)a * M;
-      float s = 0.f;
-      for (int m = 0; m < M; ++m) s = fmaf(__ldg(col + m), rs[m], s);
-      const unsigned long long key = pack_key(fabsf(s) * inv, a);
-      best = key > best ? key : best;
+    const int ncw = __reduce_max_sync(kFull, act ? nc : 0);
+    for (int c = 0; c < ncw; c += 2) {
+      const bool ok0 = act && c < nc && S.invn[c] > 0.f;
+      const bool ok1 = act && c + 1 < nc && S.invn[c + 1] > 0.f;
+      float4 a0[NCH], a1[NCH];
+      load_chunks<G, NCH>(a0, A + (int64_t)(ok0 ? S.cs[c] : 0) * M, nv, s, ok0);
+      load_chunks<G, NCH>(a1, A + (int64_t)(ok1 ? S.cs[c + 1] : 0) * M, nv, s, ok1);
+      const float p0 = gsum<G>(dotc<NCH>(a0, rv));
+      const float p1 = gsum<G>(dotc<NCH>(a1, rv));
+      if (ok0) {
+        const unsigned long long key = pack_key(fabsf(p0) * S.invn[c], S.cs[c]);
+        best = key > best ? key : best;
+      }
+      if (ok1) {
+        const unsigned long long key = pack_key(fabsf(p1) * S.invn[c + 1], S.cs[c + 1]);
+        best = key > best ? key : best;
+      }
     }
-    best = warp_max_u64(best);
-    if (!best) break;  // candidate set exhausted
-    const int q = key_idx(best);
-    for (int c = lane, t = 0; c < nc; c += 32, ++t)
-      if (cs[c] == q) sel |= 1u << t;
-    float aq[MPL];
-    load_vec<MPL>(aq, A + (int64_t)q * M, M, lane);
-    const int ok = omp_append<MPL>(lane, M, A, q, aq, yv, rv, k, oms, as, Ls, zs, fl, L64, rsq, stats);
-    if (!ok) break;
-    ++k;
-#pragma unroll
-    for (int t = 0; t < MPL; ++t) {
-      const int m = lane + 32 * t;
-      if (m < M) rs[m] = rv[t];
-    }
+    best = gmax<G>(best);
+    if (act && !best) act = false;  // candidate set exhausted
+    const int q = act ? key_idx(best) : 0;
+    if (act)
+      for (int c = s; c < nc; c += G)
+        if (S.cs[c] == q) S.invn[c] = -1.f;  // chosen: no longer eligible
     __syncwarp();
+    const bool ok = grp_append<G, NCH>(act, s, M, A, yrow, q, k, yv, rv, S, fl, rsq, stats);
+    if (act) {
+      if (ok) ++k;
+      else act = false;
+    }
   }
-  if (lane == 0) {
-    if (k < Kpb) atomicAdd((unsigned long long *)&stats[1], 1ull);
-    atomicAdd((unsigned long long *)&stats[2], (unsigned long long)nc * (unsigned long long)scored);
+  if (valid) {
+    if (s == 0) {
+      if (k < Kpb) atomicAdd((unsigned long long *)&stats[1], 1ull);
+      atomicAdd((unsigned long long *)&stats[2], (unsigned long long)nc * (unsigned long long)scored);
+      k_eff[b] = (int8_t)k;
+    }
+    for (int j = s; j < ldo; j += G) {
+      omega[b * ldo + j] = (j < k) ? S.om[j] : -1;
+      alpha[b * ldo + j] = (j < k) ? S.W[j] : 0.f;
+    }
   }
-  for (int j = lane; j < ldo; j += 32) {
-    omega[b * ldo + j] = (j < k) ? oms[j] : -1;
-    alpha[b * ldo + j] = (j < k) ? as[j] : 0.f;
-  }
-  if (lane == 0) k_eff[b] = (int8_t)k;
 }
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// (G, NCH) by problem dimension: M <= 16 G NCH, NCH <= 4.
 template <typename F>
-void dispatch_mpl(int M, F &&f) {
-  if (M <= 32) f(std::integral_constant<int, 1>{});
-  else if (M <= 64) f(std::integral_constant<int, 2>{});
-  else if (M <= 128) f(std::integral_constant<int, 4>{});
-  else f(std::integral_constant<int, 8>{});
+bool dispatch_group(int M, F &&f) {
+  if (M % 4) return false;
+  if (M <= 16) f(std::integral_constant<int, 4>{}, std::integral_constant<int, 1>{});
+  else if (M <= 32) f(std::integral_constant<int, 4>{}, std::integral_constant<int, 2>{});
+  else if (M <= 64) f(std::integral_constant<int, 4>{}, std::integral_constant<int, 4>{});
+  else if (M <= 128) f(std::integral_constant<int, 8>{}, std::integral_constant<int, 4>{});
+  else if (M <= 256) f(std::integral_constant<int, 16>{}, std::integral_constant<int, 4>{});
+  else return false;
+  return true;
 }
 
+int group_size(int M) { return M <= 64 ? 4 : (M <= 128 ? 8 : 16); }
+
 }  // namespace
+
+bool omp_dims_supported(int M) { return M > 0 && M % 4 == 0 && M <= 256; }
 
 void launch_omp_init(const float *Y, int64_t B, int M, int Mp, OmpState st, cudaStream_t s) {
   int64_t n = B * (int64_t)(M > Mp ? M : Mp);
@@ -608,11 +674,15 @@ void launch_omp_update(const float *Y, int M, const float *A, const float *inv_n
                        const int32_t *ids, int64_t n, int n_cand, const int8_t *Kp, int Kuni,
                        OmpState st, int64_t *stats, cudaStream_t s) {
   if (n == 0) return;
-  const size_t sm = sizeof(double) * 8 * ((st.Kb + 1) * (st.Kb + 2) / 2);
-  dispatch_mpl(M, [&](auto c) {
-    constexpr int MPL = decltype(c)::value;
-    omp_update_kernel<MPL><<<blocks(n, 8), 256, sm, s>>>(Y, M, A, inv_norm, ids, n, n_cand, Kp, Kuni,
-                                                          st, stats);
+  const int G = group_size(M);
+  const int per_cta = GRP_WARPS * (32 / G);
+  const size_t sm = (size_t)grp_smem_bytes(st.Kb, 0) * per_cta;
+  dispatch_group(M, [&](auto gc, auto nc) {
+    constexpr int GG = decltype(gc)::value, NCH = decltype(nc)::value;
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(omp_update_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    omp_update_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n,
+                                                                             n_cand, Kp, Kuni, st, stats);
   });
 }
 
@@ -623,15 +693,14 @@ void launch_omp_restricted(const float *Y, int M, const float *A, const float *i
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
                            cudaStream_t s) {
   if (n == 0) return;
-  const int n64 = (Kb + 1) * (Kb + 2) / 2;
-  const int nf = Kb * (Kb + 1) / 2 + 2 * Kb + M;
-  const size_t per_warp = ((size_t)(n64 * 8 + nf * 4 + (Kb + cap) * 4) + 15) / 16 * 16;
-  const size_t sm = per_warp * RS_WARPS;
-  dispatch_mpl(M, [&](auto c) {
-    constexpr int MPL = decltype(c)::value;
+  const int G = group_size(M);
+  const int per_cta = GRP_WARPS * (32 / G);
+  const size_t sm = (size_t)grp_smem_bytes(Kb, cap) * per_cta;
+  dispatch_group(M, [&](auto gc, auto nc) {
+    constexpr int GG = decltype(gc)::value, NCH = decltype(nc)::value;
     if (sm > 48 * 1024)
-      cudaFuncSetAttribute(omp_restricted_kernel<MPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    omp_restricted_kernel<MPL><<<blocks(n, RS_WARPS), RS_WARPS * 32, sm, s>>>(
+      cudaFuncSetAttribute(omp_restricted_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    omp_restricted_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(
         Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up, Kp, Kuni, Kb,
         omega, alpha, ldo, k_eff, stats);
   });
