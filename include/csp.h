@@ -117,6 +117,8 @@ typedef struct csp_solve_stats {
     int64_t overflow;          /* patches whose candidate set exceeded the kernel capacity  */
     int64_t restricted_scores; /* candidate inner products <a_i, r> computed by the restricted
                                   (finer-scale) steps, summed over patches and iterations   */
+    int64_t timeouts;          /* 1 when a bounded device wait expired (results invalid;
+                                  csp_solve_stats_get then returns CSP_ERR_TIMEOUT)         */
 } csp_solve_stats;
 
 /* Create a context on CUDA `device`.  mem_budget_bytes caps the device memory

@@ -55,7 +55,7 @@ class csp_solve_params(ctypes.Structure):
 class csp_solve_stats(ctypes.Structure):
     _fields_ = [("patches", ctypes.c_int64), ("fp64_fallbacks", ctypes.c_int64),
                 ("early_stops", ctypes.c_int64), ("overflow", ctypes.c_int64),
-                ("restricted_scores", ctypes.c_int64)]
+                ("restricted_scores", ctypes.c_int64), ("timeouts", ctypes.c_int64)]
 
 
 class csp_kernel_time(ctypes.Structure):

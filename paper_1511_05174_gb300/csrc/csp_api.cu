@@ -254,12 +254,12 @@ csp_status csp_create(csp_ctx **out, int device, size_t mem_budget_bytes) {
   ctx->budget = mem_budget_bytes;
   DeviceGuard g(device);
   if (!g.ok) { delete ctx; return fail(nullptr, CSP_ERR_CUDA, "cudaSetDevice failed"); }
-  if (dev_alloc_t(ctx, &ctx->stats_dev, 4) != CSP_OK) {
+  if (dev_alloc_t(ctx, &ctx->stats_dev, 8) != CSP_OK) {
     std::string m = ctx->err;
     delete ctx;
     return fail(nullptr, CSP_ERR_OOM, m);
   }
-  cudaMemset(ctx->stats_dev, 0, 4 * sizeof(int64_t));
+  cudaMemset(ctx->stats_dev, 0, 8 * sizeof(int64_t));
   *out = ctx;
   return CSP_OK;
 }
@@ -521,7 +521,7 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
     const int cap = ctx->lv[l - 1].max_children * Kb[l];
     if (cap > 1024) return fail(ctx, CSP_ERR_UNSUPPORTED, "candidate capacity above 1024 (max children x K)");
   }
-  CSP_CUDA(ctx, cudaMemsetAsync(ctx->stats_dev, 0, 4 * sizeof(int64_t), s));
+  CSP_CUDA(ctx, cudaMemsetAsync(ctx->stats_dev, 0, 8 * sizeof(int64_t), s));
   ctx->last_B = B;
   ctx->last_stream = s;
   if (B == 0) return CSP_OK;
@@ -577,12 +577,15 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
     st.omega = lv_om[top];
     st.alpha = lv_al[top];
     st.k_eff = lv_ke[top];
-    run(ctx, KK_INIT, s, B, [&] { launch_omp_init(Yl[top], B, L.M, bf16 ? L.Mp : 0, st, s); });
+    run(ctx, KK_INIT, s, B, [&] { launch_omp_init(Yl[top], B, L.M, bf16 ? L.Mp : 0, phased ? ctx->phase_ids : nullptr, st, s); });
+    bool maps_ok = true;
     for (int it = 0; it < Kb[top]; ++it) {
       for (int ph = 0; ph < nph; ++ph) {
         if (bf16)
           run(ctx, KK_PROXY_BF16, s, n_of(ph), [&] {
-            launch_proxy_bf16(st.Rbf, L.Mp, L.Abf[ph], L.T, ids_of(ph), n_of(ph), st.flags, st.cand, s);
+            maps_ok &= launch_proxy_bf16(st.Rbf, B, L.Mp, L.Abf[ph], L.T, phased ? ctx->phase_start[ph] : 0,
+                                         ids_of(ph), n_of(ph), st.flags, st.cand,
+                                         (unsigned long long *)(ctx->stats_dev + 4), s);
           });
         else
           run(ctx, KK_PROXY_FP32, s, n_of(ph), [&] {
@@ -592,9 +595,11 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
       }
       for (int ph = 0; ph < nph; ++ph)
         run(ctx, KK_UPDATE, s, n_of(ph), [&] {
-          launch_omp_update(Yl[top], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph), bf16 ? kTopP : 1,
-                            prm->K_patch[top], prm->K[top], st, ctx->stats_dev, s);
+          launch_omp_update(Yl[top], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph),
+                            phased ? ctx->phase_start[ph] : 0, bf16 ? kTopP : 1, prm->K_patch[top], prm->K[top], st,
+                            ctx->stats_dev, s);
         });
+      if (!maps_ok) return fail(ctx, CSP_ERR_CUDA, "tensor map encoding for the BF16 proxy failed");
     }
   }
   // restricted OMP down the scales (Algorithm 2 fine steps)
@@ -615,7 +620,7 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
 csp_status csp_solve_stats_get(csp_ctx *ctx, csp_solve_stats *out) {
   if (!ctx || !out) return fail(ctx, CSP_ERR_INVALID, "NULL argument");
   DeviceGuard dg(ctx->device);
-  int64_t h[4] = {0, 0, 0, 0};
+  int64_t h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   CSP_CUDA(ctx, cudaStreamSynchronize(ctx->last_stream));
   CSP_CUDA(ctx, cudaMemcpy(h, ctx->stats_dev, sizeof(h), cudaMemcpyDeviceToHost));
   out->patches = ctx->last_B;
@@ -623,6 +628,9 @@ csp_status csp_solve_stats_get(csp_ctx *ctx, csp_solve_stats *out) {
   out->early_stops = h[1];
   out->overflow = h[3];
   out->restricted_scores = h[2];
+  out->timeouts = h[4] != 0 ? 1 : 0;
+  if (h[4] != 0)
+    return fail(ctx, CSP_ERR_TIMEOUT, "a bounded device wait expired (code " + std::to_string(h[4]) + ")");
   return CSP_OK;
 }
 

@@ -134,17 +134,21 @@ struct OmpState {
   int ldo;           // row length of omega/alpha
 };
 
-void launch_omp_init(const float *Y, int64_t B, int M, int Mp, OmpState st, cudaStream_t s);
+// r = y, empty supports; the BF16 residual copy is written in sorted-position
+// order (row p holds patch perm[p]; perm == nullptr: identity).
+void launch_omp_init(const float *Y, int64_t B, int M, int Mp, const int32_t *perm, OmpState st, cudaStream_t s);
 void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_norm, int T,
                        const int32_t *ids, int64_t n, const int32_t *omega, int ldo,
                        const int8_t *k_eff, const uint8_t *flags, int32_t *cand, cudaStream_t s);
 bool proxy_bf16_supported(int M, int T);
 bool omp_dims_supported(int M);  // M % 4 == 0 and M <= 256
-void launch_proxy_bf16(const __nv_bfloat16 *Rbf, int Mp, const __nv_bfloat16 *Abf, int T,
-                       const int32_t *ids, int64_t n, const uint8_t *flags, int32_t *cand,
-                       cudaStream_t s);
+// Tensor-core proxy over the patches at sorted positions row0 .. row0 + n - 1
+// (list ids, may be null).  Returns false when a tensor map cannot be built.
+bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, const __nv_bfloat16 *Abf, int T,
+                       int64_t row0, const int32_t *ids, int64_t n, const uint8_t *flags, int32_t *cand,
+                       unsigned long long *err, cudaStream_t s);
 void launch_omp_update(const float *Y, int M, const float *A, const float *inv_norm,
-                       const int32_t *ids, int64_t n, int n_cand, const int8_t *Kp, int Kuni,
+                       const int32_t *ids, int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni,
                        OmpState st, int64_t *stats, cudaStream_t s);
 void launch_omp_restricted(const float *Y, int M, const float *A, const float *inv_norm,
                            const int32_t *ids, int64_t n, const int32_t *child_off,

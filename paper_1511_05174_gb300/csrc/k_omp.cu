@@ -281,12 +281,14 @@ __device__ bool grp_append(bool act, int s, int M, const float *__restrict__ A,
 // ---------------------------------------------------------------------------
 // State initialisation: r = y, empty supports.
 // ---------------------------------------------------------------------------
-__global__ void omp_init_kernel(const float *__restrict__ Y, int64_t B, int M, int Mp, OmpState st) {
+__global__ void omp_init_kernel(const float *__restrict__ Y, int64_t B, int M, int Mp,
+                                const int32_t *__restrict__ perm, OmpState st) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < B * M) st.R[e] = Y[e];
   if (st.Rbf && e < B * Mp) {
-    const int64_t b = e / Mp;
-    const int m = (int)(e - b * Mp);
+    const int64_t p = e / Mp;
+    const int m = (int)(e - p * Mp);
+    const int64_t b = perm ? perm[p] : p;
     st.Rbf[e] = __float2bfloat16_rn(m < M ? Y[b * M + m] : 0.f);
   }
   if (e < B * st.ldo) { st.omega[e] = -1; st.alpha[e] = 0.f; }
@@ -403,7 +405,8 @@ template <int G, int NCH>
 __global__ void __launch_bounds__(GRP_WARPS * 32)
 omp_update_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                   const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
-                  int n_cand, const int8_t *__restrict__ Kp, int Kuni, OmpState st, int64_t *stats) {
+                  int64_t rbf_row0, int n_cand, const int8_t *__restrict__ Kp, int Kuni, OmpState st,
+                  int64_t *stats) {
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
@@ -493,7 +496,7 @@ omp_update_kernel(const float *__restrict__ Y, int M, const float *__restrict__ 
   }
   if (st.Rbf) {
     const int Mp = (M + 63) / 64 * 64;
-    __nv_bfloat16 *rb = st.Rbf + b * Mp;
+    __nv_bfloat16 *rb = st.Rbf + (rbf_row0 + wi) * Mp;  // sorted-position order
 #pragma unroll
     for (int t = 0; t < NCH; ++t) {
       const int j = s + G * t;
@@ -648,11 +651,11 @@ int group_size(int M) { return M <= 64 ? 4 : (M <= 128 ? 8 : 16); }
 
 bool omp_dims_supported(int M) { return M > 0 && M % 4 == 0 && M <= 256; }
 
-void launch_omp_init(const float *Y, int64_t B, int M, int Mp, OmpState st, cudaStream_t s) {
+void launch_omp_init(const float *Y, int64_t B, int M, int Mp, const int32_t *perm, OmpState st, cudaStream_t s) {
   int64_t n = B * (int64_t)(M > Mp ? M : Mp);
   n = n > B * st.ldo ? n : B * st.ldo;
   if (n == 0) return;
-  omp_init_kernel<<<blocks(n, 256), 256, 0, s>>>(Y, B, M, Mp, st);
+  omp_init_kernel<<<blocks(n, 256), 256, 0, s>>>(Y, B, M, Mp, perm, st);
 }
 
 void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_norm, int T,
@@ -671,7 +674,7 @@ void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_n
 }
 
 void launch_omp_update(const float *Y, int M, const float *A, const float *inv_norm,
-                       const int32_t *ids, int64_t n, int n_cand, const int8_t *Kp, int Kuni,
+                       const int32_t *ids, int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni,
                        OmpState st, int64_t *stats, cudaStream_t s) {
   if (n == 0) return;
   const int G = group_size(M);
@@ -682,7 +685,7 @@ void launch_omp_update(const float *Y, int M, const float *A, const float *inv_n
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(omp_update_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     omp_update_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n,
-                                                                             n_cand, Kp, Kuni, st, stats);
+                                                                             rbf_row0, n_cand, Kp, Kuni, st, stats);
   });
 }
 
@@ -705,10 +708,5 @@ void launch_omp_restricted(const float *Y, int M, const float *A, const float *i
         omega, alpha, ldo, k_eff, stats);
   });
 }
-
-bool proxy_bf16_supported(int M, int T) { (void)M; (void)T; return false; }
-
-void launch_proxy_bf16(const __nv_bfloat16 *, int, const __nv_bfloat16 *, int, const int32_t *,
-                       int64_t, const uint8_t *, int32_t *, cudaStream_t) {}
 
 }  // namespace csp

@@ -1,0 +1,399 @@
+// Full-dictionary proxy on the 5th-generation tensor cores (sm_103a).
+//
+// The proxy step of OMP (Sec. II-B, Algorithm 1: k = argmax_i |<a_i, r>|)
+// over a tile of 128 patches is the dense contraction C = R A^T with R the
+// tile's residuals (128 x M) and A the effective dictionary (T x M), rows
+// scaled to unit norm so that |C| is the angle score.  Both operands are BF16
+// (zero-padded to Mp = 64 k), the accumulator FP32 in tensor memory.
+//
+// CTA layout (320 threads):
+//   warp 0  TMA producer: the residual tile once, then atom tiles of NT rows
+//           through a two-stage shared-memory ring (cp.async.bulk.tensor,
+//           128-byte swizzle, mbarrier transaction counts);
+//   warp 1  TMEM allocator and single-thread MMA issuer (tcgen05.mma
+//           kind::f16, M = 128, N = NT, K = 16 per instruction) into two
+//           TMEM accumulators of NT columns, released by tcgen05.commit;
+//   warps 2-9  epilogue: warps w and w + 4 share TMEM lane quadrant w % 4
+//           (thread <-> patch) and split each accumulator's columns in two
+//           halves; every thread keeps the four largest 32-bit packed keys
+//           (|score| bits above, T-complement of the atom index below, so ties
+//           go to the lowest index) with a branch-free min/max network in two
+//           independent chains; the halves merge through shared memory.
+// The kTopP candidates per patch are re-scored in FP32 by the update kernel,
+// which excludes atoms already chosen.
+//
+// Every mbarrier wait is bounded (kTimeoutCycles); on expiry the thread sets
+// the error word, the CTA drains its own outstanding copies and MMAs (again
+// with a bound), frees its tensor memory and exits.
+#include <cuda.h>
+
+#include "csp_internal.cuh"
+
+namespace csp {
+
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_EPI_WARPS = 8;                    // two per TMEM lane quadrant
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
+constexpr int TC_STAGES = 2;
+constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of parity `parity` to complete.  Gives up (and
+// records `code`) after kTimeoutCycles or when another thread recorded an error.
+__device__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsigned long long *err, int code) {
+  const long long t0 = clock64();
+  int spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if (++spins == 256) {
+      spins = 0;
+      if (*reinterpret_cast<volatile unsigned long long *>(err) != 0ull) return false;
+      if (clock64() - t0 > kTimeoutCycles) {
+        atomicExch(err, (unsigned long long)code);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)1 << 16;                         // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                         // descriptor version
+  d |= (uint64_t)2 << 61;                         // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: D FP32, A and B BF16, both
+// K-major, shape M x N.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+// Branch-free insertion of x into the sorted quadruple k0 >= k1 >= k2 >= k3.
+__device__ __forceinline__ void top4_insert(uint32_t x, uint32_t &k0, uint32_t &k1, uint32_t &k2, uint32_t &k3) {
+  const uint32_t l0 = min(k0, x);
+  k0 = max(k0, x);
+  const uint32_t l1 = min(k1, l0);
+  k1 = max(k1, l0);
+  const uint32_t l2 = min(k2, l1);
+  k2 = max(k2, l1);
+  k3 = max(k3, l2);
+}
+
+struct TcLayout {
+  int kb;       // 64-element K blocks
+  int nt;       // atoms per tile
+  int r_bytes;  // residual tile
+  int a_bytes;  // one atom-tile stage
+  int bar_off;  // barriers (after the 1024-aligned tiles)
+  int mrg_off;  // epilogue merge area: [TC_M][4] keys
+  int total;    // dynamic shared memory requested (includes alignment slack)
+};
+
+__host__ __device__ inline TcLayout tc_layout(int Mp, int nt) {
+  TcLayout L;
+  L.kb = Mp / 64;
+  L.nt = nt;
+  L.r_bytes = L.kb * TC_M * 128;
+  L.a_bytes = L.kb * nt * 128;
+  L.bar_off = L.r_bytes + TC_STAGES * L.a_bytes;
+  L.mrg_off = L.bar_off + 256;
+  L.total = L.mrg_off + TC_M * 4 * 4 + 1024;
+  return L;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 2)
+proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmA, int Mp, int T,
+                int nt, int idx_bits, int64_t row0, int64_t n, const int32_t *__restrict__ ids,
+                const uint8_t *__restrict__ flags, int32_t *__restrict__ cand, unsigned long long *err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const TcLayout lay = tc_layout(Mp, nt);
+  uint8_t *r_tile = smem;
+  uint8_t *a_stage = smem + lay.r_bytes;
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar_off);
+  uint64_t *full = bars;          // [2] TMA -> MMA
+  uint64_t *empty = bars + 2;     // [2] MMA -> TMA
+  uint64_t *tfull = bars + 4;     // [2] MMA -> epilogue
+  uint64_t *tempty = bars + 6;    // [2] epilogue -> MMA
+  uint64_t *rfull = bars + 8;     // residual tile landed
+  uint64_t *mdone = bars + 9;     // all MMAs retired
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 10);
+  uint32_t *merge = reinterpret_cast<uint32_t *>(smem + lay.mrg_off);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tile0 = (int64_t)blockIdx.x * TC_M;
+  const int n_at = (T + nt - 1) / nt;
+  const uint32_t ncols = 2u * (uint32_t)nt;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(full + i, 1);
+      mbar_init(empty + i, 1);
+      mbar_init(tfull + i, 1);
+      mbar_init(tempty + i, TC_EPI_WARPS);
+    }
+    mbar_init(rfull, 1);
+    mbar_init(mdone, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_holder;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer
+      int issued[2] = {0, 0};  // loads issued per stage
+      bool ok = true;
+      mbar_expect_tx(rfull, (uint32_t)lay.r_bytes);
+      for (int kb = 0; kb < lay.kb; ++kb)
+        tma_load_2d(r_tile + kb * TC_M * 128, &tmR, kb * 64, (int)(row0 + tile0), rfull);
+      for (int j = 0; j < n_at && ok; ++j) {
+        const int s = j & 1;
+        if (j >= 2) ok = mbar_wait(empty + s, (uint32_t)(((j >> 1) - 1) & 1), err, 1);
+        if (!ok) break;
+        mbar_expect_tx(full + s, (uint32_t)lay.a_bytes);
+        for (int kb = 0; kb < lay.kb; ++kb)
+          tma_load_2d(a_stage + s * lay.a_bytes + kb * nt * 128, &tmA, kb * 64, j * nt, full + s);
+        ++issued[s];
+      }
+      // drain: the last load of each stage and the residual tile have landed
+      mbar_wait(rfull, 0, err, 2);
+      for (int s = 0; s < 2; ++s)
+        if (issued[s]) mbar_wait(full + s, (uint32_t)((issued[s] - 1) & 1), err, 2);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      const uint32_t idesc = instr_desc(TC_M, nt);
+      bool ok = mbar_wait(rfull, 0, err, 3);
+      const uint32_t r_base = smem_u32(r_tile);
+      for (int j = 0; j < n_at && ok; ++j) {
+        const int s = j & 1, a = j & 1;
+        ok = mbar_wait(full + s, (uint32_t)((j >> 1) & 1), err, 4);
+        if (ok && j >= 2) ok = mbar_wait(tempty + a, (uint32_t)(((j >> 1) - 1) & 1), err, 5);
+        if (!ok) break;
+        tc_fence_after();
+        const uint32_t a_base = smem_u32(a_stage + s * lay.a_bytes);
+        const int ksteps = Mp / 16;
+        for (int ks = 0; ks < ksteps; ++ks) {
+          const int kb = ks >> 2, kin = ks & 3;
+          const uint64_t ad = smem_desc(r_base + kb * TC_M * 128 + kin * 32);
+          const uint64_t bd = smem_desc(a_base + kb * nt * 128 + kin * 32);
+          mma_bf16(tmem + (uint32_t)(a * nt), ad, bd, idesc, ks > 0 ? 1u : 0u);
+        }
+        mma_commit(empty + s);
+        mma_commit(tfull + a);
+      }
+      mma_commit(mdone);
+      mbar_wait(mdone, 0, err, 6);
+    }
+  } else {
+    // epilogue: warps 2..9; quadrant warp % 4, column half (warp - 2) / 4
+    const int quad = warp & 3, half = (warp - 2) >> 2;
+    const int row = quad * 32 + lane;
+    const uint32_t imask = (1u << idx_bits) - 1u;
+    const uint32_t smask = 0x7fffffffu & ~imask;
+    const int hcols = nt / 2;
+    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+    bool ok = true;
+    for (int j = 0; j < n_at && ok; ++j) {
+      const int a = j & 1;
+      ok = mbar_wait(tfull + a, (uint32_t)((j >> 1) & 1), err, 7);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) break;
+      tc_fence_after();
+      for (int c0 = 0; c0 < hcols; c0 += 64) {
+        uint32_t v[64];
+        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * nt + half * hcols + c0);
+        tmem_ld32_nowait(taddr, v);
+        tmem_ld32_nowait(taddr + 32, v + 32);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int base = j * nt + half * hcols + c0;
+        const uint32_t c = imask - (uint32_t)base;
+        if (base + 64 <= T) {
+#pragma unroll
+          for (int i = 0; i < 64; i += 2) {
+            top4_insert((v[i] & smask) | (c - (uint32_t)i), a0, a1, a2, a3);
+            top4_insert((v[i + 1] & smask) | (c - (uint32_t)(i + 1)), b0, b1, b2, b3);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 64; ++i)
+            if (base + i < T) top4_insert((v[i] & smask) | (c - (uint32_t)i), a0, a1, a2, a3);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty + a);
+    }
+    top4_insert(b0, a0, a1, a2, a3);
+    top4_insert(b1, a0, a1, a2, a3);
+    top4_insert(b2, a0, a1, a2, a3);
+    top4_insert(b3, a0, a1, a2, a3);
+    if (half == 1) {
+      merge[row * 4 + 0] = a0;
+      merge[row * 4 + 1] = a1;
+      merge[row * 4 + 2] = a2;
+      merge[row * 4 + 3] = a3;
+    }
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * TC_EPI_WARPS) : "memory");
+    const int64_t wi = tile0 + row;
+    if (half == 0 && ok && wi < n) {
+      for (int q = 0; q < 4; ++q) top4_insert(merge[row * 4 + q], a0, a1, a2, a3);
+      const int64_t b = ids ? ids[wi] : wi;
+      if (!(flags[b] & 1)) {
+        const uint32_t ks[4] = {a0, a1, a2, a3};
+#pragma unroll
+        for (int q = 0; q < kTopP; ++q)
+          cand[b * kTopP + q] = (q < 4 && ks[q]) ? (int)(imask - (ks[q] & imask)) : -1;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D BF16 tensor map over `rows` rows of `inner` elements, box 64 x box_rows,
+// 128-byte swizzle, zero fill outside the tensor.
+bool make_map(CUtensorMap *m, const void *base, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {inner, rows};
+  cuuint64_t strides[1] = {inner * 2};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int tile_atoms(int) { return 128; }  // 2 x 128 TMEM columns: two CTAs fit one SM's 512
+
+}  // namespace
+
+bool proxy_bf16_supported(int M, int T) {
+  const int Mp = (M + 63) / 64 * 64;
+  // packed 32-bit keys keep >= 16 score bits: T <= 2^15
+  return M > 0 && Mp <= 256 && T > 0 && T <= (1 << 15) && encode_fn() != nullptr;
+}
+
+bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, const __nv_bfloat16 *Abf, int T,
+                       int64_t row0, const int32_t *ids, int64_t n, const uint8_t *flags, int32_t *cand,
+                       unsigned long long *err, cudaStream_t s) {
+  if (n == 0) return true;
+  const int nt = tile_atoms(Mp);
+  CUtensorMap mR, mA;
+  if (!make_map(&mR, Rbf, (uint64_t)Mp, (uint64_t)rows_total, TC_M)) return false;
+  if (!make_map(&mA, Abf, (uint64_t)Mp, (uint64_t)T, (uint32_t)nt)) return false;
+  const TcLayout lay = tc_layout(Mp, nt);
+  // at least 80 KB per CTA keeps two CTAs (2 x 2 NT <= 512 TMEM columns) per SM at most
+  const int sm = lay.total < 80 * 1024 ? 80 * 1024 : lay.total;
+  static int configured = 0;
+  if (sm > configured) {
+    if (cudaFuncSetAttribute(proxy_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
+      return false;
+    configured = sm;
+  }
+  const unsigned grid = (unsigned)((n + TC_M - 1) / TC_M);
+  int idx_bits = 1;
+  while ((1 << idx_bits) < T) ++idx_bits;  // atom index field of the packed keys
+  proxy_tc_kernel<<<grid, TC_THREADS, sm, s>>>(mR, mA, Mp, T, nt, idx_bits, row0, n, ids, flags, cand, err);
+  return true;
+}
+
+}  // namespace csp

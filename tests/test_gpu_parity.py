@@ -46,21 +46,25 @@ def test_extract_is_exact(key):
     np.testing.assert_array_equal(g["Y"], oracle.extract_patches(w).astype(np.float32))
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("key", list(SMALL))
-def test_plain_parity(key):
+def test_plain_parity(key, prec):
+    """BF16: tensor-core proxy (tcgen05) with the top candidates re-scored in
+    FP32 -- held to the same support bar as the FP32 path."""
     w = _workload(key)
-    g = run_gpu(w, "plain")
+    g = run_gpu(w, "plain", prec)
     o, a, k, _ = oracle.plain_omp(w)
     rate, worst, bad = compare(w.dicts[0], g["sup"], g["coef"], g["keff"], o, a, k)
     assert rate >= MATCH, f"support mismatch on patches {bad[:10]}"
     assert worst <= REL_TOL
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("links", ["paper", "literal"])
 @pytest.mark.parametrize("key", list(SMALL))
-def test_cross_scale_parity(key, links):
+def test_cross_scale_parity(key, links, prec):
     w = _workload(key, links=links)
-    g = run_gpu(w, "cross_scale")
+    g = run_gpu(w, "cross_scale", prec)
     o, a, k, _ = oracle.cross_scale_omp(w)
     rate, worst, bad = compare(w.dicts[0], g["sup"], g["coef"], g["keff"], o, a, k)
     assert rate >= MATCH, f"support mismatch on patches {bad[:10]}"
@@ -79,10 +83,11 @@ def test_aggregate_matches_oracle(key):
     assert np.abs(g["img"] - ref).max() <= 1e-5 * scale
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("mode", ["plain", "cross_scale"])
-def test_psnr_matches_oracle(mode):
+def test_psnr_matches_oracle(mode, prec):
     w = _workload("bayer")
-    g = run_gpu(w, mode)
+    g = run_gpu(w, mode, prec)
     o, a, k, _ = oracle.plain_omp(w) if mode == "plain" else oracle.cross_scale_omp(w)
     img_o = oracle.aggregate(w, o, a, k)
     assert abs(oracle.psnr(w.truth, g["img"]) - oracle.psnr(w.truth, img_o)) <= 0.05
@@ -101,17 +106,21 @@ def test_bayer_all_four_phases():
         assert rate >= MATCH and worst <= REL_TOL, (mode, bad[:10])
 
 
-def test_independent_problems_nonunit_norms():
-    """Phi = I over 1000 independent problems with column norms in [0.5, 2]
-    (the angle proxy divides by ||a_i||), K = 6, noisy."""
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("B,M,T,K", [(1000, 64, 320, 6), (999, 64, 300, 8), (257, 256, 8192, 12),
+                                     (130, 128, 1000, 5), (64, 16, 64, 3)])
+def test_independent_problems_nonunit_norms(B, M, T, K, prec):
+    """Phi = I over independent problems with column norms in [0.5, 2] (the
+    angle proxy divides by ||a_i||), noisy; ragged patch counts (tile 64/128)
+    and atom counts (tile 128), M from 16 to 256."""
     from paper_1511_05174_gb300.context import Context
-    A, Y, _ = synthetic.make_independent_problems(1000, 64, 320, 6, seed=3, sigma=0.05)
+    A, Y, _ = synthetic.make_independent_problems(B, M, T, K, seed=3, sigma=0.05)
     ctx = Context(0)
-    ctx.set_geometry(8, 8, (1, 1), 8, 8, [(1, 1, 1, 1)])
+    ctx.set_geometry(8, 8, (1, M // 64 if M >= 64 else 1), 8 if M >= 64 else 4, 8, [(1, 1, 1, 1)])
     ctx.set_sensing("identity")
     ctx.load_dictionary(0, A)
-    sup, coef, keff = ctx.solve(torch.from_numpy(Y).cuda(), "plain", "fp32", K=[6], Kmax=8)
-    o, a, k, _ = oracle.omp_batch([A] * len(Y), Y, 6)
+    sup, coef, keff = ctx.solve(torch.from_numpy(Y).cuda(), "plain", prec, K=[K], Kmax=K + 2)
+    o, a, k, _ = oracle.omp_batch([A] * len(Y), Y, K)
     rate, worst, bad = compare(A, sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy().astype(int), o, a, k)
     assert rate >= MATCH and worst <= REL_TOL, bad[:10]
 
