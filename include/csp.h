@@ -194,6 +194,24 @@ csp_status csp_aggregate(csp_ctx *ctx, const int32_t *support, const float *coef
 csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *params,
                                 const float *meas_host, float *image_host, void *stream);
 
+/* ---- Autotuning (not part of the paper's method) --------------------------
+ * Kernel variants that compute the same result with different work
+ * decompositions (here: the restricted finer-scale solver, either re-reading
+ * candidate rows from L2 with cooperative lane groups, or staging them in
+ * shared memory).  csp_autotune runs csp_solve once per variant on the given
+ * batch (same arguments as csp_solve, outputs overwritten), times each with
+ * CUDA events, keeps the fastest for this context and reports the times.
+ * Synchronises `stream`. */
+#define CSP_TUNE_VARIANTS 2
+typedef struct csp_tune_result {
+    int restricted_variant;            /* chosen variant index                      */
+    double ms[CSP_TUNE_VARIANTS];      /* solve time per variant (ms)               */
+} csp_tune_result;
+
+csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const float *Y, int64_t B,
+                        int32_t *support_out, float *coef_out, int8_t *k_eff_out, void *stream,
+                        csp_tune_result *out);
+
 /* ---- Instrumentation (not part of the paper's method) ----------------------
  * Every kernel launch of a context is counted per kernel kind.  While
  * profiling is enabled, each launch is also bracketed by CUDA events on its

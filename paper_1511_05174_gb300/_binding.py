@@ -34,7 +34,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcsp.so")
 EXPORTS = ("csp_create", "csp_destroy", "csp_last_error", "csp_set_geometry", "csp_set_sensing",
            "csp_load_dictionary", "csp_load_scale_links", "csp_problem_size", "csp_extract_patches",
            "csp_solve", "csp_solve_stats_get", "csp_aggregate", "csp_reconstruct_host",
-           "csp_profile_enable", "csp_profile_read")
+           "csp_autotune", "csp_profile_enable", "csp_profile_read")
 
 
 class csp_geometry(ctypes.Structure):
@@ -60,6 +60,10 @@ class csp_solve_stats(ctypes.Structure):
 
 class csp_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+class csp_tune_result(ctypes.Structure):
+    _fields_ = [("restricted_variant", ctypes.c_int), ("ms", ctypes.c_double * 2)]
 
 
 class CspError(RuntimeError):
@@ -95,6 +99,8 @@ def load_library(path: str = LIB_PATH):
         "csp_solve_stats_get": (i, [vp, ctypes.POINTER(csp_solve_stats)]),
         "csp_aggregate": (i, [vp, vp, vp, vp, ctypes.c_int64, i, vp, vp]),
         "csp_reconstruct_host": (i, [vp, ctypes.POINTER(csp_solve_params), vp, vp, vp]),
+        "csp_autotune": (i, [vp, ctypes.POINTER(csp_solve_params), vp, ctypes.c_int64, vp, vp, vp, vp,
+                             ctypes.POINTER(csp_tune_result)]),
         "csp_profile_enable": (i, [vp, i]),
         "csp_profile_read": (i, [vp, ctypes.POINTER(csp_kernel_time), i, ctypes.POINTER(ctypes.c_int), i]),
     }
@@ -189,3 +195,11 @@ def csp_profile_read(ctx, reset: bool = False):
     n = ctypes.c_int()
     check(load_library().csp_profile_read(ctx, arr, cap, ctypes.byref(n), int(bool(reset))), ctx)
     return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, cap))}
+
+
+def csp_autotune(ctx, params: csp_solve_params, Y_ptr: int, B: int, sup_ptr: int, coef_ptr: int, keff_ptr: int,
+                 stream: int) -> csp_tune_result:
+    res = csp_tune_result()
+    check(load_library().csp_autotune(ctx, ctypes.byref(params), Y_ptr, B, sup_ptr, coef_ptr, keff_ptr, stream,
+                                      ctypes.byref(res)), ctx)
+    return res

@@ -146,6 +146,20 @@ class Context:
                     _stream_ptr(stream, self.device))
         return sup, coef, keff
 
+    def autotune(self, Y: torch.Tensor, mode: str = "cross_scale", precision: str = "fp32", K: Sequence[int] = (),
+                 K_patch=None, Kmax: Optional[int] = None, stream=None):
+        """Times each kernel variant on this batch and keeps the fastest.
+        Returns {"restricted_variant": v, "ms": [...]}."""
+        Y = Y.contiguous()
+        Bn = Y.shape[0]
+        p = self.params(mode, precision, K, K_patch, Kmax)
+        sup = torch.empty((Bn, p.Kmax), dtype=torch.int32, device=self.device)
+        coef = torch.empty((Bn, p.Kmax), dtype=torch.float32, device=self.device)
+        keff = torch.empty((Bn,), dtype=torch.int8, device=self.device)
+        r = b.csp_autotune(self._ctx, p, Y.data_ptr(), Bn, sup.data_ptr(), coef.data_ptr(), keff.data_ptr(),
+                           _stream_ptr(stream, self.device))
+        return {"restricted_variant": r.restricted_variant, "ms": list(r.ms)}
+
     def stats(self):
         st = b.csp_solve_stats_get(self._ctx)
         return {"patches": st.patches, "fp64_fallbacks": st.fp64_fallbacks, "early_stops": st.early_stops,

@@ -155,7 +155,8 @@ enum Slot {
   WS_R, WS_RBF, WS_L, WS_Z, WS_FLAGS, WS_CAND,
   WS_LV_OMEGA, WS_LV_ALPHA = WS_LV_OMEGA + CSP_MAX_LEVELS, WS_LV_KEFF = WS_LV_ALPHA + CSP_MAX_LEVELS,
   WS_LV_Y = WS_LV_KEFF + CSP_MAX_LEVELS,
-  WS_COUNT = WS_LV_Y + CSP_MAX_LEVELS
+  WS_XH = WS_LV_Y + CSP_MAX_LEVELS,
+  WS_COUNT
 };
 
 int level_dim(const csp_geometry &g, int l) {
@@ -608,7 +609,7 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
     const int cap = std::max(1, L.max_children * Kb[l + 1]);
     for (int ph = 0; ph < nph; ++ph)
       run(ctx, KK_RESTRICTED, s, n_of(ph), [&] {
-        launch_omp_restricted(Yl[l], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph), L.child_off,
+        launch_omp_restricted(ctx->restricted_variant, Yl[l], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph), L.child_off,
                               L.child_idx, cap, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1], prm->K_patch[l], prm->K[l],
                               Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], ctx->stats_dev, s);
       });
@@ -643,9 +644,11 @@ csp_status csp_aggregate(csp_ctx *ctx, const int32_t *support, const float *coef
   if (Kmax < 1 || Kmax > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "Kmax must be in 1..CSP_MAX_K");
   if (!support || !coef || !k_eff || !image_out) return fail(ctx, CSP_ERR_INVALID, "NULL buffer");
   DeviceGuard dg(ctx->device);
+  float *Xh = nullptr;
+  CSP_TRY(ws_get_t(ctx, WS_XH, (size_t)B * ctx->lv[0].N, &Xh));
   run(ctx, KK_AGGREGATE, (cudaStream_t)stream, B, [&] {
     launch_aggregate(ctx->gd, ctx->lv[0].D, ctx->lv[0].N, support, coef, k_eff, Kmax, ctx->cover_y, ctx->cover_x,
-                     image_out, (cudaStream_t)stream);
+                     Xh, image_out, (cudaStream_t)stream);
   });
   CSP_CUDA(ctx, cudaGetLastError());
   return CSP_OK;
@@ -694,6 +697,42 @@ csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *prm, const
   CSP_CUDA(ctx, cudaMemcpyAsync(image_host, ctx->h_img.p, img_n * 4, cudaMemcpyDeviceToHost, s));
   CSP_CUDA(ctx, cudaStreamSynchronize(s));
   return CSP_OK;
+}
+
+csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const float *Y, int64_t B,
+                        int32_t *support_out, float *coef_out, int8_t *k_eff_out, void *stream,
+                        csp_tune_result *out) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (!out) return fail(ctx, CSP_ERR_INVALID, "out is NULL");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CSP_CUDA(ctx, cudaEventCreate(&e0));
+  CSP_CUDA(ctx, cudaEventCreate(&e1));
+  const int saved = ctx->restricted_variant;
+  int best = saved;
+  double best_ms = 1e300;
+  csp_status st = CSP_OK;
+  for (int v = 0; v < CSP_TUNE_VARIANTS && st == CSP_OK; ++v) {
+    ctx->restricted_variant = v;
+    // one untimed run (workspace, caches), then a timed one
+    st = csp_solve(ctx, params, Y, B, support_out, coef_out, k_eff_out, stream);
+    if (st != CSP_OK) break;
+    cudaEventRecord(e0, s);
+    st = csp_solve(ctx, params, Y, B, support_out, coef_out, k_eff_out, stream);
+    cudaEventRecord(e1, s);
+    if (st != CSP_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(ctx, CSP_ERR_CUDA, "event synchronize failed"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    out->ms[v] = ms;
+    if (ms < best_ms) { best_ms = ms; best = v; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->restricted_variant = st == CSP_OK ? best : saved;
+  out->restricted_variant = ctx->restricted_variant;
+  return st;
 }
 
 csp_status csp_profile_enable(csp_ctx *ctx, int on) {

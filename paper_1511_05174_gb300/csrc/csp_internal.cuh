@@ -97,6 +97,7 @@ struct csp_ctx {
   int64_t launches[csp::KK_COUNT] = {};
   double prof_ms[csp::KK_COUNT] = {};
   bool prof = false;
+  int restricted_variant = 0;  // restricted-OMP kernel variant (see launch_omp_restricted)
   std::vector<csp::ProfRec> pending;
   std::vector<cudaEvent_t> ev_pool;
   // All device allocations (for the memory budget and destroy).
@@ -115,9 +116,10 @@ void launch_effective_dict(const GeomDev &g, int sense_kind, int shots, const ui
                            cudaStream_t s);
 void launch_norms(const float *A, int T, int M, int Mp, float *inv_norm, __nv_bfloat16 *Abf,
                   cudaStream_t s);
+// Synthesis into Xh ([B][N0] scratch) then per-pixel overlap-add average (2 launches).
 void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *support,
                       const float *coef, const int8_t *k_eff, int Kmax, const int32_t *cover_y,
-                      const int32_t *cover_x, float *img, cudaStream_t s);
+                      const int32_t *cover_x, float *Xh, float *img, cudaStream_t s);
 
 // OMP state of a full-dictionary level, in device memory.
 struct OmpState {
@@ -150,7 +152,8 @@ bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, con
 void launch_omp_update(const float *Y, int M, const float *A, const float *inv_norm,
                        const int32_t *ids, int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni,
                        OmpState st, int64_t *stats, cudaStream_t s);
-void launch_omp_restricted(const float *Y, int M, const float *A, const float *inv_norm,
+// variant 0: rows from L2 every pass (cooperative groups); 1: rows staged in shared memory.
+void launch_omp_restricted(int variant, const float *Y, int M, const float *A, const float *inv_norm,
                            const int32_t *ids, int64_t n, const int32_t *child_off,
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,

@@ -83,6 +83,33 @@ __device__ __forceinline__ void load_chunks(float4 (&v)[NCH], const float *__res
   }
 }
 
+// Same with plain (generic) loads: `row` may be in shared or global memory.
+template <int G, int NCH>
+__device__ __forceinline__ void load_chunks_gen(float4 (&v)[NCH], const float *row, int nv, int s, bool on) {
+  const float4 *r4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+  for (int t = 0; t < NCH; ++t) {
+    const int j = s + G * t;
+    v[t] = (on && j < nv) ? r4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+// Full dot product of two 16-byte aligned rows of nv float4 (generic loads),
+// four independent accumulators.
+__device__ __forceinline__ float row_dot(const float *a, const float *b, int nv) {
+  const float4 *a4 = reinterpret_cast<const float4 *>(a);
+  const float4 *b4 = reinterpret_cast<const float4 *>(b);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+  for (int j = 0; j < nv; ++j) {
+    const float4 x = a4[j], y = b4[j];
+    s0 = fmaf(x.x, y.x, s0);
+    s1 = fmaf(x.y, y.y, s1);
+    s2 = fmaf(x.z, y.z, s2);
+    s3 = fmaf(x.w, y.w, s3);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
 template <int NCH>
 __device__ __forceinline__ float dotc(const float4 (&a)[NCH], const float4 (&b)[NCH]) {
   float s0 = 0.f, s1 = 0.f;
@@ -105,6 +132,7 @@ struct GrpSmem {
   float *V;      // [Kb+1]      Gram column / back-substitution accumulator
   float *W;      // [Kb+1]      w = L^{-1} v, then alpha
   int *om;       // [Kb]        chosen atoms
+  const float **colp;  // [Kb+1] row of each chosen column (shared or global memory)
   int *cs;       // [cap]       candidate atoms (restricted kernel)
   float *invn;   // [cap]       their 1/||a|| (-1 once chosen or ineligible)
   int *misc;     // [4]
@@ -112,7 +140,7 @@ struct GrpSmem {
 
 __host__ __device__ inline int grp_smem_bytes(int Kb, int cap) {
   return up16(8 * tri(Kb + 1)) + up16(4 * tri(Kb)) + 2 * up16(4 * Kb) + 2 * up16(4 * (Kb + 1)) +
-         up16(4 * Kb) + 2 * up16(4 * cap) + 16;
+         up16(4 * Kb) + up16(8 * (Kb + 1)) + 2 * up16(4 * cap) + 16;
 }
 
 __device__ inline GrpSmem carve(char *p, int Kb, int cap) {
@@ -124,6 +152,7 @@ __device__ inline GrpSmem carve(char *p, int Kb, int cap) {
   S.V = reinterpret_cast<float *>(p); p += up16(4 * (Kb + 1));
   S.W = reinterpret_cast<float *>(p); p += up16(4 * (Kb + 1));
   S.om = reinterpret_cast<int *>(p); p += up16(4 * Kb);
+  S.colp = reinterpret_cast<const float **>(p); p += up16(8 * (Kb + 1));
   S.cs = reinterpret_cast<int *>(p); p += up16(4 * cap);
   S.invn = reinterpret_cast<float *>(p); p += up16(4 * cap);
   S.misc = reinterpret_cast<int *>(p);
@@ -131,16 +160,15 @@ __device__ inline GrpSmem carve(char *p, int Kb, int cap) {
 }
 
 // FP64 projection from scratch, run by one lane: Cholesky of A_S^T A_S for
-// S = om[0..k-1] + q with entries accumulated in FP64 from the FP32 columns,
-// then z = L^{-1} A_S^T y and alpha = L^{-T} z (into S.W).  Returns false when
-// q depends on the chosen columns.
-__device__ bool fp64_projection(const float *__restrict__ A, int M, const float *__restrict__ y,
-                                const GrpSmem &S, int k, int q) {
+// S = chosen + q (rows S.colp[0..k-1] and aq) with entries accumulated in FP64
+// from the FP32 columns, then z = L^{-1} A_S^T y and alpha = L^{-T} z (into
+// S.W).  Returns false when q depends on the chosen columns.
+__device__ bool fp64_projection(int M, const float *__restrict__ y, const GrpSmem &S, int k, const float *aq) {
   double *L64 = S.L64;
   for (int i = 0; i <= k; ++i) {
-    const float *ci = A + (int64_t)(i < k ? S.om[i] : q) * M;
+    const float *ci = i < k ? S.colp[i] : aq;
     for (int j = 0; j <= i; ++j) {
-      const float *cj = A + (int64_t)(j < k ? S.om[j] : q) * M;
+      const float *cj = j < k ? S.colp[j] : aq;
       double g = 0.0;
       for (int m = 0; m < M; ++m) g = fma((double)ci[m], (double)cj[m], g);
       double r = g;
@@ -155,7 +183,7 @@ __device__ bool fp64_projection(const float *__restrict__ A, int M, const float 
   }
   double zb[CSP_MAX_K + 1];
   for (int i = 0; i <= k; ++i) {
-    const float *ci = A + (int64_t)(i < k ? S.om[i] : q) * M;
+    const float *ci = i < k ? S.colp[i] : aq;
     double bi = 0.0;
     for (int m = 0; m < M; ++m) bi = fma((double)ci[m], (double)y[m], bi);
     for (int p = 0; p < i; ++p) bi -= L64[tri(i) + p] * zb[p];
@@ -171,33 +199,39 @@ __device__ bool fp64_projection(const float *__restrict__ A, int M, const float 
 }
 
 // ---------------------------------------------------------------------------
-// Group projection step.  `act`: this group appends atom q as its k-th column
-// (S.om[0..k-1] chosen; S.L/Linv/z valid unless fl has bit 1).  Lanes hold
-// their chunks of y and r.  On success alpha is in S.W[0..k], r and rsq are
-// updated, S.om[k] = q, and the FP32 factor gained row k.  Returns whether q
-// was appended (false: q depends on the chosen columns).  Warp-collective.
+// Group projection step.  `act`: this group appends atom q (row aqp, shared or
+// global memory) as its k-th column (S.om / S.colp [0..k-1] chosen; S.L/Linv/z
+// valid unless fl has bit 1).  Lanes hold their chunks of y and r.  On success
+// alpha is in S.W[0..k], r and rsq are updated, S.om[k] = q, S.colp[k] = aqp,
+// and the FP32 factor gained row k.  Returns whether q was appended (false: q
+// depends on the chosen columns).  Warp-collective.
 // ---------------------------------------------------------------------------
-template <int G, int NCH>
-__device__ bool grp_append(bool act, int s, int M, const float *__restrict__ A,
-                           const float *__restrict__ yrow, int q, int k, const float4 (&yv)[NCH],
-                           float4 (&rv)[NCH], const GrpSmem &S, uint8_t &fl, float &rsq,
+template <int G, int NCH, bool COOP>
+__device__ bool grp_append(bool act, int s, int M, const float *aqp, const float *__restrict__ yrow, int q, int k,
+                           const float4 (&yv)[NCH], float4 (&rv)[NCH], const GrpSmem &S, uint8_t &fl, float &rsq,
                            int64_t *stats) {
   const int nv = M >> 2;
   float4 aq[NCH];
-  load_chunks<G, NCH>(aq, A + (int64_t)q * M, nv, s, act);
+  load_chunks_gen<G, NCH>(aq, aqp, nv, s, act);
   const float aa = gsum<G>(dotc<NCH>(aq, aq));
   const float bq = gsum<G>(dotc<NCH>(aq, yv));
   const int kw = __reduce_max_sync(kFull, act ? k : 0);
-  // Gram column V[j] = <a_{om_j}, a_q>
-  for (int j = 0; j < kw; ++j) {
-    const bool o = act && j < k;
-    float4 c[NCH];
-    load_chunks<G, NCH>(c, A + (int64_t)(o ? S.om[j] : 0) * M, nv, s, o);
-    const float v = gsum<G>(dotc<NCH>(c, aq));
-    if (o && s == 0) S.V[j] = v;
+  const bool f32 = act && !(fl & 2);
+  // Gram column V[j] = <a_{om_j}, a_q>.  COOP: the group reads each chosen row
+  // as contiguous chunks and reduces with shuffles (columns in global memory);
+  // otherwise one full-row dot product per lane (columns in shared memory).
+  if (COOP) {
+    for (int j = 0; j < kw; ++j) {
+      const bool o = f32 && j < k;
+      float4 c[NCH];
+      load_chunks_gen<G, NCH>(c, o ? S.colp[j] : aqp, nv, s, o);
+      const float v = gsum<G>(dotc<NCH>(c, aq));
+      if (o && s == 0) S.V[j] = v;
+    }
+  } else if (f32) {
+    for (int j = s; j < k; j += G) S.V[j] = row_dot(S.colp[j], aqp, nv);
   }
   __syncwarp();
-  const bool f32 = act && !(fl & 2);
   // W = L^{-1} V, column-oriented: step i finalises W_i and updates V_j, j > i
   for (int i = 0; i < kw; ++i) {
     if (f32 && i < k) {
@@ -245,7 +279,7 @@ __device__ bool grp_append(bool act, int s, int M, const float *__restrict__ A,
   }
   // FP64 rebuild for the groups that need it (rare; one lane per group)
   const bool go64 = act && !ok32;
-  if (go64 && s == 0) S.misc[0] = fp64_projection(A, M, yrow, S, k, q) ? 1 : 0;
+  if (go64 && s == 0) S.misc[0] = fp64_projection(M, yrow, S, k, aqp) ? 1 : 0;
   __syncwarp();
   const bool appended = ok32 || (go64 && S.misc[0] != 0);
   // residue r = y - A_Omega alpha
@@ -258,7 +292,7 @@ __device__ bool grp_append(bool act, int s, int M, const float *__restrict__ A,
     if (o) {
       const float aj = S.W[j];
       float4 c[NCH];
-      if (j < k) load_chunks<G, NCH>(c, A + (int64_t)S.om[j] * M, nv, s, true);
+      if (j < k) load_chunks_gen<G, NCH>(c, S.colp[j], nv, s, true);
 #pragma unroll
       for (int t = 0; t < NCH; ++t) {
         const float4 col = (j < k) ? c[t] : aq[t];
@@ -272,7 +306,10 @@ __device__ bool grp_append(bool act, int s, int M, const float *__restrict__ A,
   const float r2 = gsum<G>(dotc<NCH>(rv, rv));
   if (appended) {
     rsq = r2;
-    if (s == 0) S.om[k] = q;
+    if (s == 0) {
+      S.om[k] = q;
+      S.colp[k] = aqp;
+    }
   }
   __syncwarp();
   return appended;
@@ -436,7 +473,11 @@ omp_update_kernel(const float *__restrict__ Y, int M, const float *__restrict__ 
   }
   // stage the chosen atoms
   if (act)
-    for (int j = s; j < k; j += G) S.om[j] = om_g[j];
+    for (int j = s; j < k; j += G) {
+      const int a = om_g[j];
+      S.om[j] = a;
+      S.colp[j] = A + (int64_t)a * M;
+    }
   __syncwarp();
   // candidate: the proxy's argmax, or the best of its re-scored top candidates
   const int32_t *cb = st.cand + b * kTopP;
@@ -478,7 +519,8 @@ omp_update_kernel(const float *__restrict__ Y, int M, const float *__restrict__ 
   }
   __syncwarp();
   float rsq = rsq0;
-  const bool ok = grp_append<G, NCH>(act, s, M, A, yrow, act ? q : 0, k, yv, rv, S, fl, rsq, stats);
+  const bool ok = grp_append<G, NCH, true>(act, s, M, A + (int64_t)(act ? q : 0) * M, yrow, act ? q : 0, k, yv, rv,
+                                           S, fl, rsq, stats);
   if (act && !ok) {
     if (s == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
     return;
@@ -523,12 +565,155 @@ omp_update_kernel(const float *__restrict__ Y, int M, const float *__restrict__ 
 // ---------------------------------------------------------------------------
 // Restricted OMP (fine step of Algorithm 2), all iterations, one group per
 // patch.  Candidates C = children of the coarser support (disjoint lists:
-// every finer atom has one parent); the proxy scores only C, two candidates
-// per group and pass, rows read from the L2-resident effective dictionary.
+// every finer atom has one parent).  The first capS candidate rows are copied
+// once into per-group shared memory (cp.async, rows padded to M + 4 floats so
+// that lanes reading different rows hit different banks); further candidates
+// are read from the L2-resident effective dictionary.  The proxy gives each
+// lane whole candidates (full-row dot products against r in shared memory,
+// no shuffles), then one group max; the projection uses the staged rows.
 // ---------------------------------------------------------------------------
+__host__ __device__ inline int rs_group_bytes(int M, int Kb, int cap, int capS) {
+  const int b = grp_smem_bytes(Kb, cap) + up16(4 * M) + 4 * capS * (M + 4);
+  return (b + 127) / 128 * 128 + 16;  // odd multiple of 16 bytes mod 128: group blocks start on different banks
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
 template <int G, int NCH>
 __global__ void __launch_bounds__(GRP_WARPS * 32)
-omp_restricted_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
+omp_restricted_staged_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
+                      const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
+                      const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx,
+                      int cap, int capS, const int32_t *__restrict__ omega_up, int ldo_up,
+                      const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
+                      int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
+                      int8_t *__restrict__ k_eff, int64_t *stats) {
+  constexpr int NG = 32 / G;
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
+  const int64_t wbase = ((int64_t)blockIdx.x * GRP_WARPS + wib) * NG;
+  if (wbase >= n) return;  // whole warp
+  const int64_t wi = wbase + g;
+  const bool valid = wi < n;
+  const int64_t b = valid ? (ids ? ids[wi] : wi) : 0;
+  char *gbase = smem_raw + (size_t)(wib * NG + g) * rs_group_bytes(M, Kb, cap, capS);
+  const GrpSmem S = carve(gbase, Kb, cap);
+  float *rs = reinterpret_cast<float *>(gbase + grp_smem_bytes(Kb, cap));
+  float *rows = rs + ((M + 3) & ~3);
+  const int ldr = M + 4;
+  const int nv = M >> 2;
+  int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
+  Kpb = Kpb < Kb ? Kpb : Kb;
+
+  // candidate set f(Omega_up)
+  int nc = 0;
+  if (valid) {
+    const int kup = keff_up[b];
+    for (int j = 0; j < kup; ++j) {
+      const int p = omega_up[b * ldo_up + j];
+      const int c0 = child_off[p], c1 = child_off[p + 1];
+      for (int i = s; i < c1 - c0; i += G)
+        if (nc + i < cap) {
+          const int a = child_idx[c0 + i];
+          S.cs[nc + i] = a;
+          S.invn[nc + i] = __ldg(inv_norm + a);
+        }
+      nc += c1 - c0;
+    }
+    if (nc > cap) {
+      if (s == 0) atomicAdd((unsigned long long *)&stats[3], 1ull);
+      nc = cap;
+    }
+  }
+  __syncwarp();
+  // stage the first capS candidate rows
+  const int nst = nc < capS ? nc : capS;
+  for (int c = 0; c < nst; ++c) {
+    const float *src = A + (int64_t)S.cs[c] * M;
+    float *dst = rows + c * ldr;
+    for (int j = s; j < nv; j += G) cp_async16(dst + 4 * j, src + 4 * j);
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  const float *yrow = Y + b * M;
+  float4 yv[NCH], rv[NCH];
+  load_chunks<G, NCH>(yv, yrow, nv, s, valid);
+#pragma unroll
+  for (int t = 0; t < NCH; ++t) {
+    rv[t] = yv[t];
+    const int j = s + G * t;
+    if (j < nv) reinterpret_cast<float4 *>(rs)[j] = yv[t];
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  __syncwarp();
+  const float ysq = gsum<G>(dotc<NCH>(yv, yv));
+  float rsq = ysq;
+  bool act = valid && Kpb > 0;
+  uint8_t fl = 0;
+  int k = 0, scored = 0;
+  const int Kw = __reduce_max_sync(kFull, Kpb);
+  for (int it = 0; it < Kw; ++it) {
+    act = act && k < Kpb && !(rsq <= kEpsR32 * ysq);
+    if (!__any_sync(kFull, act)) break;
+    if (act) ++scored;
+    // proxy: each lane scores whole candidates
+    unsigned long long best = 0ull;
+    if (act)
+      for (int c = s; c < nc; c += G) {
+        const float inv = S.invn[c];
+        if (!(inv > 0.f)) continue;
+        const float *row = c < capS ? rows + c * ldr : A + (int64_t)S.cs[c] * M;
+        const unsigned long long key = pack_key(fabsf(row_dot(row, rs, nv)) * inv, S.cs[c]);
+        best = key > best ? key : best;
+      }
+    best = gmax<G>(best);
+    if (act && !best) act = false;  // candidate set exhausted
+    const int q = act ? key_idx(best) : 0;
+    if (act)
+      for (int c = s; c < nc; c += G)
+        if (S.cs[c] == q) {
+          S.invn[c] = -1.f;  // chosen: no longer eligible
+          S.misc[1] = c;
+        }
+    __syncwarp();
+    const int qs = act ? S.misc[1] : 0;
+    const float *aqp = (act && qs < capS) ? rows + qs * ldr : A + (int64_t)q * M;
+    const bool ok = grp_append<G, NCH, false>(act, s, M, aqp, yrow, q, k, yv, rv, S, fl, rsq, stats);
+    if (act) {
+      if (ok) {
+        ++k;
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+          const int j = s + G * t;
+          if (j < nv) reinterpret_cast<float4 *>(rs)[j] = rv[t];
+        }
+      } else {
+        act = false;
+      }
+    }
+    __syncwarp();
+  }
+  if (valid) {
+    if (s == 0) {
+      if (k < Kpb) atomicAdd((unsigned long long *)&stats[1], 1ull);
+      atomicAdd((unsigned long long *)&stats[2], (unsigned long long)nc * (unsigned long long)scored);
+      k_eff[b] = (int8_t)k;
+    }
+    for (int j = s; j < ldo; j += G) {
+      omega[b * ldo + j] = (j < k) ? S.om[j] : -1;
+      alpha[b * ldo + j] = (j < k) ? S.W[j] : 0.f;
+    }
+  }
+}
+
+// Variant without staging: candidate rows are read from the L2-resident effective
+// dictionary on every pass, G = 4..16 lanes cooperate on each row (two rows per
+// pass), and the projection reads its columns from global memory.
+template <int G, int NCH>
+__global__ void __launch_bounds__(GRP_WARPS * 32)
+omp_restricted_coop_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                       const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
                       const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx,
                       int cap, const int32_t *__restrict__ omega_up, int ldo_up,
@@ -611,7 +796,7 @@ omp_restricted_kernel(const float *__restrict__ Y, int M, const float *__restric
       for (int c = s; c < nc; c += G)
         if (S.cs[c] == q) S.invn[c] = -1.f;  // chosen: no longer eligible
     __syncwarp();
-    const bool ok = grp_append<G, NCH>(act, s, M, A, yrow, q, k, yv, rv, S, fl, rsq, stats);
+    const bool ok = grp_append<G, NCH, true>(act, s, M, A + (int64_t)q * M, yrow, q, k, yv, rv, S, fl, rsq, stats);
     if (act) {
       if (ok) ++k;
       else act = false;
@@ -689,22 +874,50 @@ void launch_omp_update(const float *Y, int M, const float *A, const float *inv_n
   });
 }
 
-void launch_omp_restricted(const float *Y, int M, const float *A, const float *inv_norm,
+// (G, NCH) of the restricted kernel: wide groups (one candidate per lane).
+template <typename F>
+bool dispatch_group_wide(int M, F &&f) {
+  if (M % 4) return false;
+  if (M <= 64) f(std::integral_constant<int, 16>{}, std::integral_constant<int, 1>{});
+  else if (M <= 128) f(std::integral_constant<int, 32>{}, std::integral_constant<int, 1>{});
+  else if (M <= 256) f(std::integral_constant<int, 32>{}, std::integral_constant<int, 2>{});
+  else return false;
+  return true;
+}
+
+void launch_omp_restricted(int variant, const float *Y, int M, const float *A, const float *inv_norm,
                            const int32_t *ids, int64_t n, const int32_t *child_off,
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
                            cudaStream_t s) {
   if (n == 0) return;
-  const int G = group_size(M);
+  if (variant == 0) {
+    const int G = group_size(M);
+    const int per_cta = GRP_WARPS * (32 / G);
+    const size_t sm = (size_t)grp_smem_bytes(Kb, cap) * per_cta;
+    dispatch_group(M, [&](auto gc, auto nc) {
+      constexpr int GG = decltype(gc)::value, NCH = decltype(nc)::value;
+      if (sm > 48 * 1024)
+        cudaFuncSetAttribute(omp_restricted_coop_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      omp_restricted_coop_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(
+          Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega,
+          alpha, ldo, k_eff, stats);
+    });
+    return;
+  }
+  const int G = M <= 64 ? 16 : 32;
   const int per_cta = GRP_WARPS * (32 / G);
-  const size_t sm = (size_t)grp_smem_bytes(Kb, cap) * per_cta;
-  dispatch_group(M, [&](auto gc, auto nc) {
+  // staged rows per patch: about 6 KB of rows (at least 4, at most the capacity)
+  int capS = 6144 / (4 * (M + 4));
+  capS = capS < 4 ? 4 : (capS > cap ? cap : capS);
+  const size_t sm = (size_t)rs_group_bytes(M, Kb, cap, capS) * per_cta;
+  dispatch_group_wide(M, [&](auto gc, auto nc) {
     constexpr int GG = decltype(gc)::value, NCH = decltype(nc)::value;
     if (sm > 48 * 1024)
-      cudaFuncSetAttribute(omp_restricted_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    omp_restricted_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(
-        Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up, Kp, Kuni, Kb,
+      cudaFuncSetAttribute(omp_restricted_staged_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    omp_restricted_staged_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(
+        Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, capS, omega_up, ldo_up, keff_up, Kp, Kuni, Kb,
         omega, alpha, ldo, k_eff, stats);
   });
 }

@@ -132,13 +132,27 @@ __global__ void norms_kernel(const float *__restrict__ A, int T, int M, int Mp, 
   }
 }
 
-// One thread per image pixel (plane, y, x): mean over the covering patches of
-// x_hat_p at that pixel, summed in patch raster order (deterministic).
-__global__ void aggregate_kernel(GeomDev g, const float *__restrict__ D0, int N0,
-                                 const int32_t *__restrict__ support, const float *__restrict__ coef,
-                                 const int8_t *__restrict__ k_eff, int Kmax,
-                                 const int32_t *__restrict__ cover_y, const int32_t *__restrict__ cover_x,
-                                 float *__restrict__ img) {
+// Synthesis x_hat_p = D_|Omega alpha: one thread per element (b, n), reading
+// the chosen atoms' rows of the L2-resident fine dictionary (coalesced over n).
+__global__ void synth_kernel(const float *__restrict__ D0, int N0, const int32_t *__restrict__ support,
+                             const float *__restrict__ coef, const int8_t *__restrict__ k_eff, int Kmax,
+                             int64_t B, float *__restrict__ Xh) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * N0) return;
+  const int64_t b = e / N0;
+  const int n = (int)(e - b * N0);
+  const int k = k_eff[b];
+  float v = 0.f;
+  for (int j = 0; j < k; ++j)
+    v = fmaf(__ldg(coef + b * Kmax + j), __ldg(D0 + (int64_t)__ldg(support + b * Kmax + j) * N0 + n), v);
+  Xh[e] = v;
+}
+
+// Overlap-add: one thread per image pixel (plane, y, x), mean over the covering
+// patches of x_hat_p at that pixel, summed in patch raster order (deterministic).
+__global__ void gather_kernel(GeomDev g, const float *__restrict__ Xh, int N0,
+                              const int32_t *__restrict__ cover_y, const int32_t *__restrict__ cover_x,
+                              float *__restrict__ img) {
   const int planes = g.Ly * g.Lx;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (int64_t)planes * g.H * g.W) return;
@@ -154,12 +168,7 @@ __global__ void aggregate_kernel(GeomDev g, const float *__restrict__ D0, int N0
     for (int ix = x0; ix <= x1; ++ix) {
       const int px = x - origin(ix, g.stride, g.W, g.P);
       const int64_t b = (int64_t)iy * g.nx + ix;
-      const int k = k_eff[b];
-      const int n = (pl * g.P + py) * g.P + px;
-      float v = 0.f;
-      for (int j = 0; j < k; ++j)
-        v = fmaf(__ldg(coef + b * Kmax + j), __ldg(D0 + (int64_t)__ldg(support + b * Kmax + j) * N0 + n), v);
-      acc += v;
+      acc += __ldg(Xh + b * N0 + (pl * g.P + py) * g.P + px);
       ++cnt;
     }
   }
@@ -199,13 +208,14 @@ void launch_norms(const float *A, int T, int M, int Mp, float *inv_norm, __nv_bf
   norms_kernel<<<1, 1024, 0, s>>>(A, T, M, Mp, inv_norm, Abf);
 }
 
-void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *support,
-                      const float *coef, const int8_t *k_eff, int Kmax, const int32_t *cover_y,
-                      const int32_t *cover_x, float *img, cudaStream_t s) {
+void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *support, const float *coef,
+                      const int8_t *k_eff, int Kmax, const int32_t *cover_y, const int32_t *cover_x, float *Xh,
+                      float *img, cudaStream_t s) {
+  const int64_t B = (int64_t)g.nx * g.ny;
   const int64_t n = (int64_t)g.Ly * g.Lx * g.H * g.W;
   if (n == 0) return;
-  aggregate_kernel<<<blocks(n, 256), 256, 0, s>>>(g, D0, N0, support, coef, k_eff, Kmax, cover_y,
-                                                  cover_x, img);
+  if (B * N0) synth_kernel<<<blocks(B * N0, 256), 256, 0, s>>>(D0, N0, support, coef, k_eff, Kmax, B, Xh);
+  gather_kernel<<<blocks(n, 256), 256, 0, s>>>(g, Xh, N0, cover_y, cover_x, img);
 }
 
 }  // namespace csp
