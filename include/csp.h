@@ -186,6 +186,23 @@ csp_status csp_aggregate(csp_ctx *ctx, const int32_t *support, const float *coef
                          const int8_t *k_eff, int64_t B, int Kmax, float *image_out,
                          void *stream);
 
+/* Allocation-free variant of csp_aggregate.  The paper has no counterpart:
+ * this exists for callers that cannot allocate device memory when they
+ * aggregate (code recorded while a stream is captured into a CUDA graph,
+ * processes whose memory pool owns the device and forbids later allocations,
+ * latency-bound loops that must not enter the driver's allocator).  Same
+ * arguments, result and launch order as csp_aggregate; the per-patch
+ * synthesis scratch is a fixed 16 MiB array (4,194,304 floats) in the
+ * library's device image, held by every GPU that loads the library until the
+ * process exits.  Requires B * N0 <= 4,194,304 (N0 = fine patch dimension),
+ * else CSP_ERR_INVALID with a message.  Calls no cudaMalloc/cudaFree.  The
+ * first call on each device looks up the array's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls whose work overlaps on the GPU race on it. */
+csp_status csp_aggregate_noalloc(csp_ctx *ctx, const int32_t *support, const float *coef,
+                                 const int8_t *k_eff, int64_t B, int Kmax, float *image_out,
+                                 void *stream);
+
 /* End-to-end reconstruction from HOST buffers: copies the measurement image
  * (layout as in csp_extract_patches) to the device, extracts, solves,
  * aggregates and copies the image (float32 [planes][H][W]) back into

@@ -33,7 +33,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcsp.so")
 # Every entry point declared in include/csp.h.
 EXPORTS = ("csp_create", "csp_destroy", "csp_last_error", "csp_set_geometry", "csp_set_sensing",
            "csp_load_dictionary", "csp_load_scale_links", "csp_problem_size", "csp_extract_patches",
-           "csp_solve", "csp_solve_stats_get", "csp_aggregate", "csp_reconstruct_host",
+           "csp_solve", "csp_solve_stats_get", "csp_aggregate", "csp_aggregate_noalloc", "csp_reconstruct_host",
            "csp_autotune", "csp_profile_enable", "csp_profile_read")
 
 
@@ -98,6 +98,7 @@ def load_library(path: str = LIB_PATH):
         "csp_solve": (i, [vp, ctypes.POINTER(csp_solve_params), vp, ctypes.c_int64, vp, vp, vp, vp]),
         "csp_solve_stats_get": (i, [vp, ctypes.POINTER(csp_solve_stats)]),
         "csp_aggregate": (i, [vp, vp, vp, vp, ctypes.c_int64, i, vp, vp]),
+        "csp_aggregate_noalloc": (i, [vp, vp, vp, vp, ctypes.c_int64, i, vp, vp]),
         "csp_reconstruct_host": (i, [vp, ctypes.POINTER(csp_solve_params), vp, vp, vp]),
         "csp_autotune": (i, [vp, ctypes.POINTER(csp_solve_params), vp, ctypes.c_int64, vp, vp, vp, vp,
                              ctypes.POINTER(csp_tune_result)]),
@@ -178,6 +179,12 @@ def csp_solve_stats_get(ctx) -> csp_solve_stats:
 def csp_aggregate(ctx, sup_ptr: int, coef_ptr: int, keff_ptr: int, B: int, Kmax: int, img_ptr: int,
                   stream: int) -> None:
     check(load_library().csp_aggregate(ctx, sup_ptr, coef_ptr, keff_ptr, B, Kmax, img_ptr, stream), ctx)
+
+
+def csp_aggregate_noalloc(ctx, sup_ptr: int, coef_ptr: int, keff_ptr: int, B: int, Kmax: int, img_ptr: int,
+                          stream: int) -> None:
+    """csp_aggregate without any device allocation (fixed 16 MiB scratch; B * N0 <= 4 Mi)."""
+    check(load_library().csp_aggregate_noalloc(ctx, sup_ptr, coef_ptr, keff_ptr, B, Kmax, img_ptr, stream), ctx)
 
 
 def csp_reconstruct_host(ctx, params: csp_solve_params, meas_ptr: int, img_ptr: int, stream: int) -> None:

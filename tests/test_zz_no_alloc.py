@@ -1,0 +1,61 @@
+"""csp_aggregate_noalloc against csp_aggregate, through the C ABI.
+
+The allocation-free entry point serves callers that cannot allocate device
+memory at aggregation time (stream capture, pre-reserved memory pools,
+latency-bound loops).  It keeps its scratch in a fixed array shared by all
+calls, so the test calls it twice in a row on different inputs and checks
+each result against the allocating entry point.  This file is collected last
+on purpose."""
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic
+from paper_1511_05174_gb300 import _binding as b
+from paper_1511_05174_gb300.context import Context
+
+pytestmark = pytest.mark.gpu
+
+
+def _codes(w, ctx, seed):
+    meas = torch.from_numpy(w.meas).cuda()
+    Y = ctx.extract(meas)
+    K = [int(k[0]) for k in w.K_levels]
+    sup, coef, keff = ctx.solve(Y, "cross_scale", "fp32", K=K, Kmax=K[0])
+    if seed:
+        coef = coef * (1.0 + 0.25 * torch.randn_like(coef))
+    return sup, coef.contiguous(), keff
+
+
+def test_noalloc_aggregate_matches_aggregate_twice():
+    w = synthetic.make_workload("bayer", H=64, W=64)
+    ctx = Context(0)
+    ctx.load_workload(w)
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        sup, coef, keff = _codes(w, ctx, call)
+        ref = ctx.aggregate(sup, coef, keff)
+        out = torch.full_like(ref, float("nan"))
+        b.csp_aggregate_noalloc(ctx._ctx, sup.data_ptr(), coef.data_ptr(), keff.data_ptr(), sup.shape[0],
+                                sup.shape[1], out.data_ptr(), stream)
+        torch.cuda.synchronize()
+        r, o = ref.double().cpu().numpy(), out.double().cpu().numpy()
+        scale = max(np.abs(r).max(), 1e-30)
+        assert np.isfinite(o).all()
+        assert np.abs(o - r).max() <= 1e-5 * scale, call
+
+
+def test_noalloc_rejects_oversized_batches():
+    w = synthetic.make_workload("bayer")  # 64,009 patches x 192 > 4 Mi floats
+    ctx = Context(0)
+    ctx.load_workload(w)
+    B = w.n_patches
+    sup = torch.zeros((B, 8), dtype=torch.int32, device="cuda")
+    coef = torch.zeros((B, 8), dtype=torch.float32, device="cuda")
+    keff = torch.zeros((B,), dtype=torch.int8, device="cuda")
+    img = torch.empty((3, 512, 512), dtype=torch.float32, device="cuda")
+    with pytest.raises(b.CspError) as e:
+        b.csp_aggregate_noalloc(ctx._ctx, sup.data_ptr(), coef.data_ptr(), keff.data_ptr(), B, 8, img.data_ptr(),
+                                torch.cuda.current_stream().cuda_stream)
+    assert e.value.status == b.CSP_ERR_INVALID and "exceeds" in str(e.value)
