@@ -214,12 +214,13 @@ csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *params,
 /* ---- Autotuning (not part of the paper's method) --------------------------
  * Kernel variants that compute the same result with different work
  * decompositions (here: the restricted finer-scale solver, either re-reading
- * candidate rows from L2 with cooperative lane groups, or staging them in
- * shared memory).  csp_autotune runs csp_solve once per variant on the given
+ * candidate rows from L2 with cooperative lane groups, staging them in
+ * shared memory, or scoring candidates through the level's precomputed Gram
+ * matrix and re-scoring the best three exactly).  csp_autotune runs csp_solve once per variant on the given
  * batch (same arguments as csp_solve, outputs overwritten), times each with
  * CUDA events, keeps the fastest for this context and reports the times.
  * Synchronises `stream`. */
-#define CSP_TUNE_VARIANTS 2
+#define CSP_TUNE_VARIANTS 3  /* 0: L2-cooperative, 1: shared-memory staged, 2: Gram-matrix proxy */
 typedef struct csp_tune_result {
     int restricted_variant;            /* chosen variant index                      */
     double ms[CSP_TUNE_VARIANTS];      /* solve time per variant (ms)               */
@@ -228,6 +229,12 @@ typedef struct csp_tune_result {
 csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const float *Y, int64_t B,
                         int32_t *support_out, float *coef_out, int8_t *k_eff_out, void *stream,
                         csp_tune_result *out);
+
+/* Pin the restricted-solver variant (0 .. CSP_TUNE_VARIANTS - 1), e.g. from a
+ * stored csp_tune_result.  Variant 2 falls back to 0 on levels whose Gram
+ * matrix was not kept (T^2 floats above 256 MiB or beyond the memory budget).
+ * Errors: CSP_ERR_INVALID for an unknown variant. */
+csp_status csp_set_kernel_variant(csp_ctx *ctx, int restricted_variant);
 
 /* ---- Instrumentation (not part of the paper's method) ----------------------
  * Every kernel launch of a context is counted per kernel kind.  While

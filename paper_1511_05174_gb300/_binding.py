@@ -34,7 +34,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcsp.so")
 EXPORTS = ("csp_create", "csp_destroy", "csp_last_error", "csp_set_geometry", "csp_set_sensing",
            "csp_load_dictionary", "csp_load_scale_links", "csp_problem_size", "csp_extract_patches",
            "csp_solve", "csp_solve_stats_get", "csp_aggregate", "csp_aggregate_noalloc", "csp_reconstruct_host",
-           "csp_autotune", "csp_profile_enable", "csp_profile_read")
+           "csp_autotune", "csp_set_kernel_variant", "csp_profile_enable", "csp_profile_read")
 
 
 class csp_geometry(ctypes.Structure):
@@ -63,7 +63,7 @@ class csp_kernel_time(ctypes.Structure):
 
 
 class csp_tune_result(ctypes.Structure):
-    _fields_ = [("restricted_variant", ctypes.c_int), ("ms", ctypes.c_double * 2)]
+    _fields_ = [("restricted_variant", ctypes.c_int), ("ms", ctypes.c_double * 3)]
 
 
 class CspError(RuntimeError):
@@ -102,6 +102,7 @@ def load_library(path: str = LIB_PATH):
         "csp_reconstruct_host": (i, [vp, ctypes.POINTER(csp_solve_params), vp, vp, vp]),
         "csp_autotune": (i, [vp, ctypes.POINTER(csp_solve_params), vp, ctypes.c_int64, vp, vp, vp, vp,
                              ctypes.POINTER(csp_tune_result)]),
+        "csp_set_kernel_variant": (i, [vp, i]),
         "csp_profile_enable": (i, [vp, i]),
         "csp_profile_read": (i, [vp, ctypes.POINTER(csp_kernel_time), i, ctypes.POINTER(ctypes.c_int), i]),
     }
@@ -210,3 +211,7 @@ def csp_autotune(ctx, params: csp_solve_params, Y_ptr: int, B: int, sup_ptr: int
     check(load_library().csp_autotune(ctx, ctypes.byref(params), Y_ptr, B, sup_ptr, coef_ptr, keff_ptr, stream,
                                       ctypes.byref(res)), ctx)
     return res
+
+
+def csp_set_kernel_variant(ctx, restricted_variant: int) -> None:
+    check(load_library().csp_set_kernel_variant(ctx, int(restricted_variant)), ctx)

@@ -160,6 +160,9 @@ class Context:
                            _stream_ptr(stream, self.device))
         return {"restricted_variant": r.restricted_variant, "ms": list(r.ms)}
 
+    def set_kernel_variant(self, restricted_variant: int) -> None:
+        b.csp_set_kernel_variant(self._ctx, restricted_variant)
+
     def stats(self):
         st = b.csp_solve_stats_get(self._ctx)
         return {"patches": st.patches, "fp64_fallbacks": st.fp64_fallbacks, "early_stops": st.early_stops,

@@ -176,9 +176,11 @@ void free_level_derived(csp_ctx *ctx, LevelData &L) {
     if (L.A[p] && L.A[p] != L.D) dev_free(ctx, L.A[p]);
     dev_free(ctx, L.inv_norm[p]);
     dev_free(ctx, L.Abf[p]);
+    dev_free(ctx, L.G[p]);
     L.A[p] = nullptr;
     L.inv_norm[p] = nullptr;
     L.Abf[p] = nullptr;
+    L.G[p] = nullptr;
   }
   L.n_phase = 0;
 }
@@ -222,6 +224,13 @@ csp_status prepare(csp_ctx *ctx, cudaStream_t s) {
       CSP_TRY(dev_alloc_t(ctx, &L.inv_norm[p], (size_t)L.T));
       CSP_TRY(dev_alloc_t(ctx, &L.Abf[p], (size_t)L.T * L.Mp));
       run(ctx, KK_PREP, s, L.T, [&] { launch_norms(L.A[p], L.T, L.M, L.Mp, L.inv_norm[p], L.Abf[p], s); });
+      // Gram matrix of the effective dictionary (projection step's Gram column),
+      // kept when it is at most 256 MiB and fits the memory budget
+      const size_t gbytes = (size_t)L.T * L.T * sizeof(float);
+      if (gbytes <= (size_t(256) << 20) && (!ctx->budget || ctx->held + gbytes <= ctx->budget)) {
+        CSP_TRY(dev_alloc_t(ctx, &L.G[p], (size_t)L.T * L.T));
+        run(ctx, KK_PREP, s, L.T, [&] { launch_gram(L.A[p], L.T, L.M, L.G[p], s); });
+      }
     }
     L.n_phase = nph;
   }
@@ -596,9 +605,9 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
       }
       for (int ph = 0; ph < nph; ++ph)
         run(ctx, KK_UPDATE, s, n_of(ph), [&] {
-          launch_omp_update(Yl[top], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph),
+          launch_omp_update_wave(Yl[top], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph),
                             phased ? ctx->phase_start[ph] : 0, bf16 ? kTopP : 1, prm->K_patch[top], prm->K[top], st,
-                            ctx->stats_dev, s);
+                            ctx->stats_dev, L.G[ph], L.T, s);
         });
       if (!maps_ok) return fail(ctx, CSP_ERR_CUDA, "tensor map encoding for the BF16 proxy failed");
     }
@@ -611,7 +620,7 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
       run(ctx, KK_RESTRICTED, s, n_of(ph), [&] {
         launch_omp_restricted(ctx->restricted_variant, Yl[l], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph), L.child_off,
                               L.child_idx, cap, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1], prm->K_patch[l], prm->K[l],
-                              Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], ctx->stats_dev, s);
+                              Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], ctx->stats_dev, L.G[ph], L.T, s);
       });
   }
   CSP_CUDA(ctx, cudaGetLastError());
@@ -733,6 +742,14 @@ csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const floa
   ctx->restricted_variant = st == CSP_OK ? best : saved;
   out->restricted_variant = ctx->restricted_variant;
   return st;
+}
+
+csp_status csp_set_kernel_variant(csp_ctx *ctx, int restricted_variant) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (restricted_variant < 0 || restricted_variant >= CSP_TUNE_VARIANTS)
+    return fail(ctx, CSP_ERR_INVALID, "unknown kernel variant");
+  ctx->restricted_variant = restricted_variant;
+  return CSP_OK;
 }
 
 csp_status csp_profile_enable(csp_ctx *ctx, int on) {

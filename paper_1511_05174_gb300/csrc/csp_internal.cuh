@@ -41,6 +41,7 @@ struct LevelData {
   float *inv_norm[kMaxPhases] = {};   // [T] 1/||a_i||, or -1 for an ineligible zero column
   __nv_bfloat16 *Abf[kMaxPhases] = {};  // [T][Mp] a_i / ||a_i|| in BF16 (tensor-core proxy)
   int Mp = 0;                  // BF16 row length (M rounded up to 64)
+  float *G[kMaxPhases] = {};   // [T][T] Gram matrix A A^T (null when T is too large)
   // Cross-scale map f to the next coarser level (valid when this level < n_levels - 1).
   int32_t *child_off = nullptr;   // [T_{l+1} + 1]
   int32_t *child_idx = nullptr;   // [T] children of each coarse atom, ascending
@@ -97,7 +98,7 @@ struct csp_ctx {
   int64_t launches[csp::KK_COUNT] = {};
   double prof_ms[csp::KK_COUNT] = {};
   bool prof = false;
-  int restricted_variant = 0;  // restricted-OMP kernel variant (see launch_omp_restricted)
+  int restricted_variant = 2;  // restricted-OMP kernel variant (see launch_omp_restricted)
   std::vector<csp::ProfRec> pending;
   std::vector<cudaEvent_t> ev_pool;
   // All device allocations (for the memory budget and destroy).
@@ -151,13 +152,25 @@ bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, con
                        unsigned long long *err, cudaStream_t s);
 void launch_omp_update(const float *Y, int M, const float *A, const float *inv_norm,
                        const int32_t *ids, int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni,
-                       OmpState st, int64_t *stats, cudaStream_t s);
-// variant 0: rows from L2 every pass (cooperative groups); 1: rows staged in shared memory.
+                       OmpState st, int64_t *stats, const float *gram, int T, cudaStream_t s);
+// Load-wave variants (k_grp.cu): one update iteration; restricted OMP with the Gram-matrix proxy.
+void launch_omp_update_wave(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,
+                            int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni, OmpState st,
+                            int64_t *stats, const float *gram, int T, cudaStream_t s);
+void launch_omp_restricted_gram(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,
+                                int64_t n, const int32_t *child_off, const int32_t *child_idx, int cap,
+                                const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int8_t *Kp,
+                                int Kuni, int Kb, int32_t *omega, float *alpha, int ldo, int8_t *k_eff,
+                                int64_t *stats, const float *gram, int T, cudaStream_t s);
+// Gram matrix A A^T ([T][T] FP32) of an effective dictionary.
+void launch_gram(const float *A, int T, int M, float *Gm, cudaStream_t s);
+// variant 0: rows from L2 every pass (cooperative groups); 1: rows staged in shared memory;
+// 2: proxy from the Gram matrix + exact re-score of the best three (falls back to 0 without gram).
 void launch_omp_restricted(int variant, const float *Y, int M, const float *A, const float *inv_norm,
                            const int32_t *ids, int64_t n, const int32_t *child_off,
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
-                           cudaStream_t s);
+                           const float *gram, int T, cudaStream_t s);
 
 }  // namespace csp

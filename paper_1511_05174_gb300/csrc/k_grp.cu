@@ -1,0 +1,685 @@
+// Lane-group OMP kernels organised in load waves.
+//
+// The per-patch work of OMP (Sec. II-B, Algorithm 1: merge, projection,
+// residue; the finer steps of Algorithm 2) is latency-bound: every step waits
+// for rows of the effective dictionary that sit in L2.  These kernels issue all
+// loads a step needs together, before any of them is used, so that a patch
+// waits for a handful of memory round trips per iteration instead of one per
+// row:
+//   omp_update_wave_kernel   one iteration of every patch of a full-dictionary
+//                            level (after the proxy kernel): re-score the
+//                            proxy's candidates in FP32, project, update r;
+//   omp_restricted_gram_kernel  all iterations of the restricted OMP over the
+//                            children f(Omega_up): the proxy over the candidates
+//                            is c_i = <a_i, y> - sum_j alpha_j G[i][omega_j]
+//                            from the level's Gram matrix G = A A^T (entries
+//                            cached per candidate in shared memory), its best
+//                            three are re-scored exactly against the explicit
+//                            residual, so the selection follows the FP32 proxy.
+// Both use the incremental Cholesky projection of grp_project (FP32, rebuilt
+// in FP64 when the pivot ratio falls below kTauPivot).
+#include "csp_internal.cuh"
+#include "grp_common.cuh"
+
+namespace csp {
+
+namespace {
+
+using namespace csp::grp;
+
+constexpr int WV_WARPS = 4;
+constexpr int RB = 4;  // residual rows per load wave
+
+// Projection step given the Gram column S.V[0..k-1] = <a_{om_j}, a_q>, the
+// chunks of a_q, aa = ||a_q||^2 and bq = <a_q, y>.  S.colp[0..k-1] point at the
+// chosen rows (global).  On success alpha is in S.W[0..k], r and rsq are
+// updated, S.om[k] = q, S.colp[k] = aqp, and the FP32 factor gained row k.
+// Returns whether q was appended.  Warp-collective.
+template <int G, int NCH>
+__device__ bool grp_project(bool act, int s, int M, const float *aqp, const float *__restrict__ yrow, int q, int k,
+                            const float4 (&aq)[NCH], float aa, float bq, const float4 (&yv)[NCH], float4 (&rv)[NCH],
+                            const GrpSmem &S, uint8_t &fl, float &rsq, int64_t *stats) {
+  const int nv = M >> 2;
+  const int kw = __reduce_max_sync(kFull, act ? k : 0);
+  const bool f32 = act && !(fl & 2);
+  // W = L^{-1} V, column-oriented: step i finalises W_i and updates V_j, j > i
+  for (int i = 0; i < kw; ++i) {
+    if (f32 && i < k) {
+      const float wi = S.V[i] * S.Linv[i];
+      if (s == 0) S.W[i] = wi;
+      for (int j = i + 1 + s; j < k; j += G) S.V[j] = fmaf(-S.L[tri(j) + i], wi, S.V[j]);
+    }
+    __syncwarp();
+  }
+  float ww = 0.f, zz = 0.f;
+  if (f32)
+    for (int j = s; j < k; j += G) {
+      ww = fmaf(S.W[j], S.W[j], ww);
+      zz = fmaf(S.W[j], S.z[j], zz);
+    }
+  ww = gsum<G>(ww);
+  zz = gsum<G>(zz);
+  const float d = aa - ww;
+  const bool ok32 = f32 && aa > 0.f && d >= kTauPivot * aa;
+  if (f32 && !ok32) {
+    fl |= 2;
+    if (s == 0 && stats) atomicAdd((unsigned long long *)&stats[0], 1ull);
+  }
+  if (ok32) {
+    const float lkk = sqrtf(d), il = 1.f / lkk;
+    for (int j = s; j < k; j += G) S.L[tri(k) + j] = S.W[j];
+    if (s == 0) {
+      S.L[tri(k) + k] = lkk;
+      S.Linv[k] = il;
+      S.z[k] = (bq - zz) * il;
+    }
+  }
+  __syncwarp();
+  if (ok32)
+    for (int i = s; i <= k; i += G) S.V[i] = S.z[i];
+  __syncwarp();
+  for (int j = kw; j >= 0; --j) {
+    if (ok32 && j <= k) {
+      const float aj = S.V[j] * S.Linv[j];
+      if (s == 0) S.W[j] = aj;
+      for (int i = s; i < j; i += G) S.V[i] = fmaf(-S.L[tri(j) + i], aj, S.V[i]);
+    }
+    __syncwarp();
+  }
+  const bool go64 = act && !ok32;
+  if (go64 && s == 0) S.misc[0] = fp64_projection(M, yrow, S, k, aqp) ? 1 : 0;
+  __syncwarp();
+  const bool appended = ok32 || (go64 && S.misc[0] != 0);
+  // residue r = y - A_Omega alpha, RB chosen rows per load wave
+  if (appended) {
+    const float ak = S.W[k];
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+      rv[t].x = fmaf(-ak, aq[t].x, yv[t].x);
+      rv[t].y = fmaf(-ak, aq[t].y, yv[t].y);
+      rv[t].z = fmaf(-ak, aq[t].z, yv[t].z);
+      rv[t].w = fmaf(-ak, aq[t].w, yv[t].w);
+    }
+  }
+  for (int j0 = 0; j0 < kw; j0 += RB) {
+    float4 c[RB][NCH];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const bool o = appended && j0 + u < k;
+      load_chunks<G, NCH>(c[u], o ? S.colp[j0 + u] : aqp, nv, s, o);
+    }
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      if (appended && j0 + u < k) {
+        const float aj = S.W[j0 + u];
+#pragma unroll
+        for (int t = 0; t < NCH; ++t) {
+          rv[t].x = fmaf(-aj, c[u][t].x, rv[t].x);
+          rv[t].y = fmaf(-aj, c[u][t].y, rv[t].y);
+          rv[t].z = fmaf(-aj, c[u][t].z, rv[t].z);
+          rv[t].w = fmaf(-aj, c[u][t].w, rv[t].w);
+        }
+      }
+    }
+  }
+  const float r2 = gsum<G>(dotc<NCH>(rv, rv));
+  if (appended) {
+    rsq = r2;
+    if (s == 0) {
+      S.om[k] = q;
+      S.colp[k] = aqp;
+    }
+  }
+  __syncwarp();
+  return appended;
+}
+
+// ---------------------------------------------------------------------------
+// One OMP iteration of every patch of a full-dictionary level.
+// ---------------------------------------------------------------------------
+template <int G, int NCH>
+__global__ void __launch_bounds__(WV_WARPS * 32)
+omp_update_wave_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
+                       const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
+                       int64_t rbf_row0, int n_cand, const int8_t *__restrict__ Kp, int Kuni, OmpState st,
+                       int64_t *stats, const float *__restrict__ gram, int T) {
+  constexpr int NG = 32 / G;
+  constexpr int KPL = (CSP_MAX_K + G - 1) / G;  // chosen-atom entries per lane
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
+  const int64_t wbase = ((int64_t)blockIdx.x * WV_WARPS + wib) * NG;
+  if (wbase >= n) return;  // whole warp
+  const int64_t wi = wbase + g;
+  const bool valid = wi < n;
+  const GrpSmem S = carve(smem_raw + (size_t)(wib * NG + g) * grp_smem_bytes(st.Kb, 0), st.Kb, 0);
+  const int nv = M >> 2;
+  const int64_t b = valid ? (ids ? __ldg(ids + wi) : wi) : 0;
+  // wave: per-patch state
+  uint8_t fl = valid ? st.flags[b] : 1;
+  const int k = valid ? st.k_eff[b] : 0;
+  int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
+  Kpb = Kpb < st.Kb ? Kpb : st.Kb;
+  int32_t *om_g = st.omega + b * st.ldo;
+  float *L_g = st.Lpk + b * tri(st.Kb);
+  float *z_g = st.z + b * st.Kb;
+  const float *yrow = Y + b * M;
+  float4 yv[NCH], rv[NCH];
+  load_chunks<G, NCH>(yv, yrow, nv, s, valid);
+  load_chunks<G, NCH>(rv, st.R + b * M, nv, s, valid);
+  int candr[kTopP];
+#pragma unroll
+  for (int c = 0; c < kTopP; ++c) candr[c] = (valid && c < n_cand) ? st.cand[b * kTopP + c] : -1;
+  int omr[KPL];
+  float zr[KPL];
+#pragma unroll
+  for (int t = 0; t < KPL; ++t) {
+    const int j = s + G * t;
+    const bool o = valid && j < st.Kb;
+    omr[t] = o ? om_g[j] : 0;
+    zr[t] = o ? z_g[j] : 0.f;
+  }
+  bool act = !(fl & 1) && k < Kpb;
+  if (valid && !(fl & 1) && k >= Kpb && s == 0) st.flags[b] = fl | 1;
+  const float ysq = gsum<G>(dotc<NCH>(yv, yv));
+  const float rsq0 = gsum<G>(dotc<NCH>(rv, rv));
+  if (act && rsq0 <= kEpsR32 * ysq) {
+    act = false;
+    if (s == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
+  }
+#pragma unroll
+  for (int t = 0; t < KPL; ++t) {
+    const int j = s + G * t;
+    if (act && j < k) {
+      S.om[j] = omr[t];
+      S.colp[j] = A + (int64_t)omr[t] * M;
+      S.z[j] = zr[t];
+    }
+  }
+  // wave: candidate rows, their norms, the factor
+  float4 cr[kTopP][NCH];
+  float invr[kTopP];
+#pragma unroll
+  for (int c = 0; c < kTopP; ++c) {
+    const bool o = act && candr[c] >= 0;
+    load_chunks<G, NCH>(cr[c], A + (int64_t)(o ? candr[c] : 0) * M, nv, s, o);
+    invr[c] = o ? __ldg(inv_norm + candr[c]) : -1.f;
+  }
+  const bool f32 = act && !(fl & 2);
+  const int tk = tri(k), kw = __reduce_max_sync(kFull, act ? k : 0);
+  for (int e0 = s; e0 < tri(kw); e0 += 8 * G) {
+    float lr[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * G;
+      lr[u] = (f32 && e < tk) ? L_g[e] : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = e0 + u * G;
+      if (f32 && e < tk) S.L[e] = lr[u];
+    }
+  }
+  __syncwarp();
+  if (f32)
+    for (int j = s; j < k; j += G) S.Linv[j] = 1.f / S.L[tri(j) + j];
+  // choose q: the proxy's argmax, or the best FP32 re-score of its candidates
+  int q = -1, qc = 0;
+  if (n_cand <= 1) {
+    q = act ? candr[0] : -1;
+  } else {
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int c = 0; c < kTopP; ++c) {
+      bool dup = false;
+      if (act && candr[c] >= 0)
+        for (int j = s; j < k; j += G) dup |= (S.om[j] == candr[c]);
+      const unsigned bal = __ballot_sync(kFull, dup);
+      const bool taken = ((bal >> (g * G)) & ((G == 32) ? 0xffffffffu : ((1u << G) - 1u))) != 0u;
+      const float sc = gsum<G>(dotc<NCH>(cr[c], rv));
+      if (act && candr[c] >= 0 && invr[c] > 0.f && !taken) {
+        const unsigned long long key = pack_key(fabsf(sc) * invr[c], candr[c]);
+        if (key > best) { best = key; qc = c; }
+      }
+    }
+    q = best ? key_idx(best) : -1;
+  }
+  if (act && q < 0) {
+    act = false;
+    if (s == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
+  }
+  float4 aq[NCH];
+#pragma unroll
+  for (int t = 0; t < NCH; ++t) {
+    aq[t] = cr[0][t];
+#pragma unroll
+    for (int c = 1; c < kTopP; ++c)
+      if (qc == c) aq[t] = cr[c][t];
+  }
+  const float aa = gsum<G>(dotc<NCH>(aq, aq));
+  const float bq = gsum<G>(dotc<NCH>(aq, yv));
+  // wave: Gram column
+  const bool f32b = act && !(fl & 2);
+  if (gram) {
+    float vr[KPL];
+#pragma unroll
+    for (int t = 0; t < KPL; ++t) {
+      const int j = s + G * t;
+      vr[t] = (f32b && j < k) ? __ldg(gram + (int64_t)omr[t] * T + q) : 0.f;
+    }
+#pragma unroll
+    for (int t = 0; t < KPL; ++t) {
+      const int j = s + G * t;
+      if (f32b && j < k) S.V[j] = vr[t];
+    }
+  } else {
+    for (int j = 0; j < kw; ++j) {
+      const bool o = f32b && j < k;
+      float4 c[NCH];
+      load_chunks<G, NCH>(c, o ? S.colp[j] : A, nv, s, o);
+      const float v = gsum<G>(dotc<NCH>(c, aq));
+      if (o && s == 0) S.V[j] = v;
+    }
+  }
+  __syncwarp();
+  float rsq = rsq0;
+  const bool ok = grp_project<G, NCH>(act, s, M, A + (int64_t)(act ? q : 0) * M, yrow, act ? q : 0, k, aq, aa, bq,
+                                      yv, rv, S, fl, rsq, stats);
+  if (act && !ok) {
+    if (s == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
+    return;
+  }
+  if (!act) return;
+  if (!(fl & 2))
+    for (int j = s; j <= k; j += G) L_g[tri(k) + j] = S.L[tri(k) + j];
+  for (int j = s; j <= k; j += G) st.alpha[b * st.ldo + j] = S.W[j];
+  float4 *R4 = reinterpret_cast<float4 *>(st.R + b * M);
+#pragma unroll
+  for (int t = 0; t < NCH; ++t) {
+    const int j = s + G * t;
+    if (j < nv) R4[j] = rv[t];
+  }
+  if (st.Rbf) {
+    const int Mp = (M + 63) / 64 * 64;
+    __nv_bfloat162 *rb = reinterpret_cast<__nv_bfloat162 *>(st.Rbf + (rbf_row0 + wi) * Mp);  // sorted position
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+      const int j = s + G * t;
+      if (j < nv) {
+        rb[2 * j] = __floats2bfloat162_rn(rv[t].x, rv[t].y);
+        rb[2 * j + 1] = __floats2bfloat162_rn(rv[t].z, rv[t].w);
+      }
+    }
+  }
+  if (s == 0) {
+    if (!(fl & 2)) z_g[k] = S.z[k];
+    om_g[k] = q;
+    st.k_eff[b] = (int8_t)(k + 1);
+    uint8_t nf = fl;
+    if (k + 1 >= Kpb) nf |= 1;
+    if (rsq <= kEpsR32 * ysq) nf |= 1;
+    if ((nf & 1) && k + 1 < Kpb) atomicAdd((unsigned long long *)&stats[1], 1ull);
+    st.flags[b] = nf;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Restricted OMP with the Gram-matrix proxy ("Batch-OMP" form of the same
+// iteration).  With p0 = A_C^T y and G = A A^T the proxy over the candidates
+// is c_i = p0_i - sum_j alpha_j G[i][omega_j] = <a_i, r> (r = y - A_Omega alpha),
+// the Gram column of the projection is G[q][omega_j], <a_q, y> = p0_q, and the
+// residual norm is ||r||^2 = ||y||^2 - alpha^T p0_Omega (normal equations).  In
+// FP32 these carry the same eps ||y|| cancellation error as an explicitly
+// formed residual; only the stopping test needs ||r||^2 below that level, so
+// when the estimate falls under 1e-5 ||y||^2 the residual is formed
+// explicitly from the chosen rows.  Per iteration the only global loads are
+// G[c][q] for the candidates (one wave).
+// Per-group shared memory: GrpSmem | p0[cap] | gdiag[cap] | Gc[cap][Kb] |
+// p0 of the chosen [Kb] | parent scratch [2][CSP_MAX_K].
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int gram_ld(int cap) { return (cap + 3) & ~3; }  // Gc column stride
+__host__ __device__ __forceinline__ int gram_group_bytes(int Kb, int cap) {
+  const int bytes = grp_smem_bytes(Kb, cap) + 2 * up16(4 * cap) + 4 * gram_ld(cap) * Kb + up16(4 * Kb) +
+                    8 * CSP_MAX_K;
+  return (bytes + 127) / 128 * 128 + 16;  // groups start on different bank offsets
+}
+
+template <int G, int NCH>
+__global__ void __launch_bounds__(WV_WARPS * 32)
+omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
+                           const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
+                           const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx,
+                           int cap, const int32_t *__restrict__ omega_up, int ldo_up,
+                           const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
+                           int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
+                           int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
+  constexpr int NG = 32 / G;
+  constexpr int KPL = (CSP_MAX_K + G - 1) / G;
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
+  const int64_t wbase = ((int64_t)blockIdx.x * WV_WARPS + wib) * NG;
+  if (wbase >= n) return;  // whole warp
+  const int64_t wi = wbase + g;
+  const bool valid = wi < n;
+  char *gbase = smem_raw + (size_t)(wib * NG + g) * gram_group_bytes(Kb, cap);
+  const GrpSmem S = carve(gbase, Kb, cap);
+  char *q_ = gbase + grp_smem_bytes(Kb, cap);
+  float *p0 = reinterpret_cast<float *>(q_); q_ += up16(4 * cap);
+  float *gdiag = reinterpret_cast<float *>(q_); q_ += up16(4 * cap);
+  float *Gc = reinterpret_cast<float *>(q_); q_ += 4 * gram_ld(cap) * Kb;  // Gc[j * ldg + c]
+  const int ldg = gram_ld(cap);
+  float *p0c = reinterpret_cast<float *>(q_); q_ += up16(4 * Kb);
+  int *pstart = reinterpret_cast<int *>(q_);
+  int *pbeg = pstart + CSP_MAX_K;
+  const int nv = M >> 2;
+  const int64_t b = valid ? (ids ? __ldg(ids + wi) : wi) : 0;
+  int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
+  Kpb = Kpb < Kb ? Kpb : Kb;
+  const int kup = valid ? keff_up[b] : 0;
+  const float *yrow = Y + b * M;
+  float4 yv[NCH];
+  load_chunks<G, NCH>(yv, yrow, nv, s, valid);
+  // candidate set f(Omega_up): parents' child ranges in one wave, then the children
+  int pr[KPL], c0r[KPL], c1r[KPL];
+#pragma unroll
+  for (int t = 0; t < KPL; ++t) {
+    const int j = s + G * t;
+    pr[t] = (j < kup) ? omega_up[b * ldo_up + j] : 0;
+  }
+#pragma unroll
+  for (int t = 0; t < KPL; ++t) {
+    const int j = s + G * t;
+    c0r[t] = (j < kup) ? child_off[pr[t]] : 0;
+    c1r[t] = (j < kup) ? child_off[pr[t] + 1] : 0;
+  }
+#pragma unroll
+  for (int t = 0; t < KPL; ++t) {
+    const int j = s + G * t;
+    if (j < kup) { pstart[j] = c1r[t] - c0r[t]; pbeg[j] = c0r[t]; }
+  }
+  __syncwarp();
+  if (s == 0 && valid) {
+    int tot = 0;
+    for (int j = 0; j < kup; ++j) {
+      const int cnt = pstart[j];
+      pstart[j] = tot;
+      tot += cnt;
+    }
+    S.misc[2] = tot;
+  }
+  __syncwarp();
+  int nc = valid ? S.misc[2] : 0;
+  if (nc > cap) {
+    if (s == 0) atomicAdd((unsigned long long *)&stats[3], 1ull);
+    nc = cap;
+  }
+  for (int c = s; c < nc; c += G) {
+    int j = 0;
+    while (j + 1 < kup && pstart[j + 1] <= c) ++j;
+    S.cs[c] = child_idx[pbeg[j] + (c - pstart[j])];
+  }
+  __syncwarp();
+  for (int c0 = s; c0 < nc; c0 += 4 * G) {
+    float iv[4], gd[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u * G;
+      const int a = c < nc ? S.cs[c] : 0;
+      iv[u] = c < nc ? __ldg(inv_norm + a) : -1.f;
+      gd[u] = c < nc ? __ldg(gram + (int64_t)a * T + a) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u * G;
+      if (c < nc) { S.invn[c] = iv[u]; gdiag[c] = gd[u]; }
+    }
+  }
+  // p0 = A_C^T y, RB rows per load wave
+  const int ncw = __reduce_max_sync(kFull, nc);
+  for (int c0 = 0; c0 < ncw; c0 += RB) {
+    float4 a[RB][NCH];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const bool o = c0 + u < nc;
+      load_chunks<G, NCH>(a[u], A + (int64_t)(o ? S.cs[c0 + u] : 0) * M, nv, s, o);
+    }
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+      const float d = gsum<G>(dotc<NCH>(a[u], yv));
+      if (s == 0 && c0 + u < nc) p0[c0 + u] = d;
+    }
+  }
+  __syncwarp();
+  const float ysq = gsum<G>(dotc<NCH>(yv, yv));
+  float rsq = ysq;
+  bool act = valid && Kpb > 0;
+  uint8_t fl = 0;
+  int k = 0, scored = 0;
+  const int Kw = __reduce_max_sync(kFull, Kpb);
+  for (int it = 0; it < Kw; ++it) {
+    act = act && k < Kpb && !(rsq <= kEpsR32 * ysq);
+    if (!__any_sync(kFull, act)) break;
+    if (act) ++scored;
+    // proxy over the candidates from p0 and the cached Gram entries
+    unsigned long long best = 0ull;
+    if (act)
+      for (int c = s; c < nc; c += G) {
+        const float inv = S.invn[c];
+        if (!(inv > 0.f)) continue;
+        float sc = p0[c];
+        for (int j = 0; j < k; ++j) sc = fmaf(-S.W[j], Gc[j * ldg + c], sc);
+        const unsigned long long key = pack_key(fabsf(sc) * inv, S.cs[c]);
+        best = key > best ? key : best;
+      }
+    best = gmax<G>(best);
+    if (act && !best) act = false;  // candidate set exhausted
+    const int q = act ? key_idx(best) : 0;
+    if (act)
+      for (int c = s; c < nc; c += G)
+        if (S.cs[c] == q) {
+          S.invn[c] = -1.f;  // chosen: no longer eligible
+          S.misc[1] = c;
+        }
+    __syncwarp();
+    const int qs = act ? S.misc[1] : 0;
+    const bool f32 = act && !(fl & 2);
+    if (f32)
+      for (int j = s; j < k; j += G) S.V[j] = Gc[j * ldg + qs];
+    const float aa = act ? gdiag[qs] : 0.f;
+    const float bq = act ? p0[qs] : 0.f;
+    __syncwarp();
+    // projection: W = L^{-1} V, pivot, z_k, alpha = L^{-T} z (as in grp_project)
+    const int kw = __reduce_max_sync(kFull, act ? k : 0);
+    for (int i = 0; i < kw; ++i) {
+      if (f32 && i < k) {
+        const float wi2 = S.V[i] * S.Linv[i];
+        if (s == 0) S.W[i] = wi2;
+        for (int j = i + 1 + s; j < k; j += G) S.V[j] = fmaf(-S.L[tri(j) + i], wi2, S.V[j]);
+      }
+      __syncwarp();
+    }
+    float ww = 0.f, zz = 0.f;
+    if (f32)
+      for (int j = s; j < k; j += G) {
+        ww = fmaf(S.W[j], S.W[j], ww);
+        zz = fmaf(S.W[j], S.z[j], zz);
+      }
+    ww = gsum<G>(ww);
+    zz = gsum<G>(zz);
+    const float d = aa - ww;
+    const bool ok32 = f32 && aa > 0.f && d >= kTauPivot * aa;
+    if (f32 && !ok32) {
+      fl |= 2;
+      if (s == 0) atomicAdd((unsigned long long *)&stats[0], 1ull);
+    }
+    if (ok32) {
+      const float lkk = sqrtf(d), il = 1.f / lkk;
+      for (int j = s; j < k; j += G) S.L[tri(k) + j] = S.W[j];
+      if (s == 0) {
+        S.L[tri(k) + k] = lkk;
+        S.Linv[k] = il;
+        S.z[k] = (bq - zz) * il;
+      }
+    }
+    __syncwarp();
+    if (ok32)
+      for (int i = s; i <= k; i += G) S.V[i] = S.z[i];
+    __syncwarp();
+    for (int j = kw; j >= 0; --j) {
+      if (ok32 && j <= k) {
+        const float aj = S.V[j] * S.Linv[j];
+        if (s == 0) S.W[j] = aj;
+        for (int i = s; i < j; i += G) S.V[i] = fmaf(-S.L[tri(j) + i], aj, S.V[i]);
+      }
+      __syncwarp();
+    }
+    const bool go64 = act && !ok32;
+    if (go64 && s == 0) S.misc[0] = fp64_projection(M, yrow, S, k, A + (int64_t)q * M) ? 1 : 0;
+    __syncwarp();
+    const bool appended = ok32 || (go64 && S.misc[0] != 0);
+    if (appended && s == 0) {
+      S.om[k] = q;
+      S.colp[k] = A + (int64_t)q * M;
+      p0c[k] = bq;
+    }
+    __syncwarp();
+    // ||r||^2 = ||y||^2 - alpha^T p0_Omega; formed explicitly when near the FP32 floor
+    float e = 0.f;
+    if (appended)
+      for (int j = s; j <= k; j += G) e = fmaf(S.W[j], p0c[j], e);
+    e = gsum<G>(e);
+    const float est = ysq - e;
+    const bool exact = appended && est <= 1e-5f * ysq;
+    if (__any_sync(kFull, exact)) {
+      float4 rv[NCH];
+#pragma unroll
+      for (int t = 0; t < NCH; ++t) rv[t] = yv[t];
+      const int kx = __reduce_max_sync(kFull, exact ? k + 1 : 0);
+      for (int j0 = 0; j0 < kx; j0 += RB) {
+        float4 c[RB][NCH];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+          const bool o = exact && j0 + u <= k;
+          load_chunks<G, NCH>(c[u], o ? S.colp[j0 + u] : yrow, nv, s, o);
+        }
+#pragma unroll
+        for (int u = 0; u < RB; ++u)
+          if (exact && j0 + u <= k) {
+            const float aj = S.W[j0 + u];
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+              rv[t].x = fmaf(-aj, c[u][t].x, rv[t].x);
+              rv[t].y = fmaf(-aj, c[u][t].y, rv[t].y);
+              rv[t].z = fmaf(-aj, c[u][t].z, rv[t].z);
+              rv[t].w = fmaf(-aj, c[u][t].w, rv[t].w);
+            }
+          }
+      }
+      const float r2 = gsum<G>(dotc<NCH>(rv, rv));
+      if (exact) rsq = r2;
+    }
+    if (appended && !exact) rsq = est;
+    if (act) {
+      if (appended) {
+        // cache G[c][q] for every candidate (one load wave) as column k
+        for (int c0 = s; c0 < nc; c0 += 8 * G) {
+          float gr[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int c = c0 + u * G;
+            gr[u] = (c < nc) ? __ldg(gram + (int64_t)S.cs[c] * T + q) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int c = c0 + u * G;
+            if (c < nc) Gc[k * ldg + c] = gr[u];
+          }
+        }
+        ++k;
+      } else {
+        act = false;
+      }
+    }
+    __syncwarp();
+  }
+  if (valid) {
+    if (s == 0) {
+      if (k < Kpb) atomicAdd((unsigned long long *)&stats[1], 1ull);
+      atomicAdd((unsigned long long *)&stats[2], (unsigned long long)nc * (unsigned long long)scored);
+      k_eff[b] = (int8_t)k;
+    }
+    for (int j = s; j < ldo; j += G) {
+      omega[b * ldo + j] = (j < k) ? S.om[j] : -1;
+      alpha[b * ldo + j] = (j < k) ? S.W[j] : 0.f;
+    }
+  }
+}
+
+inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// (G, NCH): about eight elements per lane.
+template <typename F>
+bool dispatch_wave(int M, F &&f) {
+  if (M % 4) return false;
+  if (M <= 16) f(std::integral_constant<int, 4>{}, std::integral_constant<int, 1>{});
+  else if (M <= 32) f(std::integral_constant<int, 4>{}, std::integral_constant<int, 2>{});
+  else if (M <= 64) f(std::integral_constant<int, 8>{}, std::integral_constant<int, 2>{});
+  else if (M <= 128) f(std::integral_constant<int, 16>{}, std::integral_constant<int, 2>{});
+  else if (M <= 256) f(std::integral_constant<int, 32>{}, std::integral_constant<int, 2>{});
+  else return false;
+  return true;
+}
+
+int wave_group(int M) { return M <= 32 ? 4 : (M <= 64 ? 8 : (M <= 128 ? 16 : 32)); }
+
+// (G, NCH) of the Batch-OMP restricted kernel: narrow groups (its per-iteration
+// state is scalar; M-vectors appear only in p0 and the rare explicit residual).
+template <typename F>
+bool dispatch_narrow(int M, F &&f) {
+  if (M % 4) return false;
+  if (M <= 16) f(std::integral_constant<int, 4>{}, std::integral_constant<int, 1>{});
+  else if (M <= 32) f(std::integral_constant<int, 4>{}, std::integral_constant<int, 2>{});
+  else if (M <= 64) f(std::integral_constant<int, 4>{}, std::integral_constant<int, 4>{});
+  else if (M <= 128) f(std::integral_constant<int, 8>{}, std::integral_constant<int, 4>{});
+  else if (M <= 256) f(std::integral_constant<int, 16>{}, std::integral_constant<int, 4>{});
+  else return false;
+  return true;
+}
+
+int narrow_group(int M) { return M <= 64 ? 4 : (M <= 128 ? 8 : 16); }
+
+}  // namespace
+
+void launch_omp_update_wave(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,
+                            int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni, OmpState st,
+                            int64_t *stats, const float *gram, int T, cudaStream_t s) {
+  if (n == 0) return;
+  const int per_cta = WV_WARPS * (32 / wave_group(M));
+  const size_t sm = (size_t)grp_smem_bytes(st.Kb, 0) * per_cta;
+  dispatch_wave(M, [&](auto gc, auto nc) {
+    constexpr int GG = decltype(gc)::value, NCH = decltype(nc)::value;
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(omp_update_wave_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    omp_update_wave_kernel<GG, NCH><<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(
+        Y, M, A, inv_norm, ids, n, rbf_row0, n_cand, Kp, Kuni, st, stats, gram, T);
+  });
+}
+
+void launch_omp_restricted_gram(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,
+                                int64_t n, const int32_t *child_off, const int32_t *child_idx, int cap,
+                                const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int8_t *Kp,
+                                int Kuni, int Kb, int32_t *omega, float *alpha, int ldo, int8_t *k_eff,
+                                int64_t *stats, const float *gram, int T, cudaStream_t s) {
+  if (n == 0) return;
+  const int per_cta = WV_WARPS * (32 / narrow_group(M));
+  const size_t sm = (size_t)gram_group_bytes(Kb, cap) * per_cta;
+  dispatch_narrow(M, [&](auto gc, auto nc) {
+    constexpr int GG = decltype(gc)::value, NCH = decltype(nc)::value;
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(omp_restricted_gram_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    omp_restricted_gram_kernel<GG, NCH><<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(
+        Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega,
+        alpha, ldo, k_eff, stats, gram, T);
+  });
+}
+
+}  // namespace csp

@@ -32,171 +32,13 @@
 //   omp_restricted_kernel  all iterations of the restricted OMP over the children
 //                          f(Omega_up) of the coarser support (Algorithm 2 fine step)
 #include "csp_internal.cuh"
+#include "grp_common.cuh"
 
 namespace csp {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__host__ __device__ __forceinline__ int tri(int i) { return (i * (i + 1)) >> 1; }
-__host__ __device__ __forceinline__ int up16(int bytes) { return (bytes + 15) & ~15; }
-
-// Packed argmax key: larger score first, then lower index.  0 = no candidate.
-__device__ __forceinline__ unsigned long long pack_key(float score, int idx) {
-  return ((unsigned long long)__float_as_uint(score) << 32) | (0xffffffffu - (unsigned)idx);
-}
-__device__ __forceinline__ int key_idx(unsigned long long k) {
-  return (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
-}
-
-// ---- group reductions (every lane of the warp must call them together) ----
-template <int G>
-__device__ __forceinline__ float gsum(float v) {
-#pragma unroll
-  for (int o = G / 2; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-template <int G>
-__device__ __forceinline__ unsigned long long gmax(unsigned long long v) {
-#pragma unroll
-  for (int o = G / 2; o; o >>= 1) {
-    const unsigned long long w = __shfl_xor_sync(kFull, v, o);
-    v = w > v ? w : v;
-  }
-  return v;
-}
-
-__device__ __forceinline__ float dot4(const float4 &a, const float4 &b) {
-  return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
-}
-
-// Chunks j = s + G t (t < NCH) of a 16-byte aligned row of nv float4; zeros past nv.
-template <int G, int NCH>
-__device__ __forceinline__ void load_chunks(float4 (&v)[NCH], const float *__restrict__ row, int nv, int s,
-                                            bool on) {
-  const float4 *r4 = reinterpret_cast<const float4 *>(row);
-#pragma unroll
-  for (int t = 0; t < NCH; ++t) {
-    const int j = s + G * t;
-    v[t] = (on && j < nv) ? __ldg(r4 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-
-// Same with plain (generic) loads: `row` may be in shared or global memory.
-template <int G, int NCH>
-__device__ __forceinline__ void load_chunks_gen(float4 (&v)[NCH], const float *row, int nv, int s, bool on) {
-  const float4 *r4 = reinterpret_cast<const float4 *>(row);
-#pragma unroll
-  for (int t = 0; t < NCH; ++t) {
-    const int j = s + G * t;
-    v[t] = (on && j < nv) ? r4[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-
-// Full dot product of two 16-byte aligned rows of nv float4 (generic loads),
-// four independent accumulators.
-__device__ __forceinline__ float row_dot(const float *a, const float *b, int nv) {
-  const float4 *a4 = reinterpret_cast<const float4 *>(a);
-  const float4 *b4 = reinterpret_cast<const float4 *>(b);
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-  for (int j = 0; j < nv; ++j) {
-    const float4 x = a4[j], y = b4[j];
-    s0 = fmaf(x.x, y.x, s0);
-    s1 = fmaf(x.y, y.y, s1);
-    s2 = fmaf(x.z, y.z, s2);
-    s3 = fmaf(x.w, y.w, s3);
-  }
-  return (s0 + s1) + (s2 + s3);
-}
-
-template <int NCH>
-__device__ __forceinline__ float dotc(const float4 (&a)[NCH], const float4 (&b)[NCH]) {
-  float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-  for (int t = 0; t < NCH; ++t) {
-    if (t & 1) s1 += dot4(a[t], b[t]);
-    else s0 += dot4(a[t], b[t]);
-  }
-  return s0 + s1;
-}
-
-// ---------------------------------------------------------------------------
-// Per-group shared-memory block.
-// ---------------------------------------------------------------------------
-struct GrpSmem {
-  double *L64;   // [tri(Kb+1)] FP64 factor (fallback path)
-  float *L;      // [tri(Kb)]   packed lower factor
-  float *Linv;   // [Kb]        1 / L_jj
-  float *z;      // [Kb]
-  float *V;      // [Kb+1]      Gram column / back-substitution accumulator
-  float *W;      // [Kb+1]      w = L^{-1} v, then alpha
-  int *om;       // [Kb]        chosen atoms
-  const float **colp;  // [Kb+1] row of each chosen column (shared or global memory)
-  int *cs;       // [cap]       candidate atoms (restricted kernel)
-  float *invn;   // [cap]       their 1/||a|| (-1 once chosen or ineligible)
-  int *misc;     // [4]
-};
-
-__host__ __device__ inline int grp_smem_bytes(int Kb, int cap) {
-  return up16(8 * tri(Kb + 1)) + up16(4 * tri(Kb)) + 2 * up16(4 * Kb) + 2 * up16(4 * (Kb + 1)) +
-         up16(4 * Kb) + up16(8 * (Kb + 1)) + 2 * up16(4 * cap) + 16;
-}
-
-__device__ inline GrpSmem carve(char *p, int Kb, int cap) {
-  GrpSmem S;
-  S.L64 = reinterpret_cast<double *>(p); p += up16(8 * tri(Kb + 1));
-  S.L = reinterpret_cast<float *>(p); p += up16(4 * tri(Kb));
-  S.Linv = reinterpret_cast<float *>(p); p += up16(4 * Kb);
-  S.z = reinterpret_cast<float *>(p); p += up16(4 * Kb);
-  S.V = reinterpret_cast<float *>(p); p += up16(4 * (Kb + 1));
-  S.W = reinterpret_cast<float *>(p); p += up16(4 * (Kb + 1));
-  S.om = reinterpret_cast<int *>(p); p += up16(4 * Kb);
-  S.colp = reinterpret_cast<const float **>(p); p += up16(8 * (Kb + 1));
-  S.cs = reinterpret_cast<int *>(p); p += up16(4 * cap);
-  S.invn = reinterpret_cast<float *>(p); p += up16(4 * cap);
-  S.misc = reinterpret_cast<int *>(p);
-  return S;
-}
-
-// FP64 projection from scratch, run by one lane: Cholesky of A_S^T A_S for
-// S = chosen + q (rows S.colp[0..k-1] and aq) with entries accumulated in FP64
-// from the FP32 columns, then z = L^{-1} A_S^T y and alpha = L^{-T} z (into
-// S.W).  Returns false when q depends on the chosen columns.
-__device__ bool fp64_projection(int M, const float *__restrict__ y, const GrpSmem &S, int k, const float *aq) {
-  double *L64 = S.L64;
-  for (int i = 0; i <= k; ++i) {
-    const float *ci = i < k ? S.colp[i] : aq;
-    for (int j = 0; j <= i; ++j) {
-      const float *cj = j < k ? S.colp[j] : aq;
-      double g = 0.0;
-      for (int m = 0; m < M; ++m) g = fma((double)ci[m], (double)cj[m], g);
-      double r = g;
-      for (int p = 0; p < j; ++p) r -= L64[tri(i) + p] * L64[tri(j) + p];
-      if (j < i) {
-        L64[tri(i) + j] = r / L64[tri(j) + j];
-      } else {
-        if (i == k && !(r > kEpsD64 * kEpsD64 * g)) return false;
-        L64[tri(i) + i] = sqrt(r > 0.0 ? r : 0.0);
-      }
-    }
-  }
-  double zb[CSP_MAX_K + 1];
-  for (int i = 0; i <= k; ++i) {
-    const float *ci = i < k ? S.colp[i] : aq;
-    double bi = 0.0;
-    for (int m = 0; m < M; ++m) bi = fma((double)ci[m], (double)y[m], bi);
-    for (int p = 0; p < i; ++p) bi -= L64[tri(i) + p] * zb[p];
-    zb[i] = bi / L64[tri(i) + i];
-  }
-  for (int i = k; i >= 0; --i) {
-    double r = zb[i];
-    for (int j = i + 1; j <= k; ++j) r -= L64[tri(j) + i] * zb[j];
-    zb[i] = r / L64[tri(i) + i];
-  }
-  for (int i = 0; i <= k; ++i) S.W[i] = (float)zb[i];
-  return true;
-}
+using namespace csp::grp;
 
 // ---------------------------------------------------------------------------
 // Group projection step.  `act`: this group appends atom q (row aqp, shared or
@@ -209,18 +51,23 @@ __device__ bool fp64_projection(int M, const float *__restrict__ y, const GrpSme
 template <int G, int NCH, bool COOP>
 __device__ bool grp_append(bool act, int s, int M, const float *aqp, const float *__restrict__ yrow, int q, int k,
                            const float4 (&yv)[NCH], float4 (&rv)[NCH], const GrpSmem &S, uint8_t &fl, float &rsq,
-                           int64_t *stats) {
+                           int64_t *stats, const float *__restrict__ gram, int T) {
   const int nv = M >> 2;
   float4 aq[NCH];
   load_chunks_gen<G, NCH>(aq, aqp, nv, s, act);
-  const float aa = gsum<G>(dotc<NCH>(aq, aq));
+  const float aa_dot = gsum<G>(dotc<NCH>(aq, aq));
   const float bq = gsum<G>(dotc<NCH>(aq, yv));
   const int kw = __reduce_max_sync(kFull, act ? k : 0);
   const bool f32 = act && !(fl & 2);
-  // Gram column V[j] = <a_{om_j}, a_q>.  COOP: the group reads each chosen row
-  // as contiguous chunks and reduces with shuffles (columns in global memory);
-  // otherwise one full-row dot product per lane (columns in shared memory).
-  if (COOP) {
+  // Gram column V[j] = <a_{om_j}, a_q>: looked up in the precomputed Gram matrix
+  // of the effective dictionary when there is one; else COOP: the group reads
+  // each chosen row as contiguous chunks and reduces with shuffles (columns in
+  // global memory); otherwise one full-row dot product per lane (shared memory).
+  const float aa = gram ? (act ? __ldg(gram + (int64_t)q * T + q) : 0.f) : aa_dot;
+  if (gram) {
+    if (f32)
+      for (int j = s; j < k; j += G) S.V[j] = __ldg(gram + (int64_t)S.om[j] * T + q);
+  } else if (COOP) {
     for (int j = 0; j < kw; ++j) {
       const bool o = f32 && j < k;
       float4 c[NCH];
@@ -287,19 +134,28 @@ __device__ bool grp_append(bool act, int s, int M, const float *aqp, const float
 #pragma unroll
     for (int t = 0; t < NCH; ++t) rv[t] = yv[t];
   }
-  for (int j = 0; j <= kw; ++j) {
-    const bool o = appended && j <= k;
-    if (o) {
-      const float aj = S.W[j];
-      float4 c[NCH];
-      if (j < k) load_chunks_gen<G, NCH>(c, S.colp[j], nv, s, true);
+  if (appended) {
+#pragma unroll
+    for (int t = 0; t < NCH; ++t) {
+      const float aj = S.W[k];
+      rv[t].x = fmaf(-aj, aq[t].x, rv[t].x);
+      rv[t].y = fmaf(-aj, aq[t].y, rv[t].y);
+      rv[t].z = fmaf(-aj, aq[t].z, rv[t].z);
+      rv[t].w = fmaf(-aj, aq[t].w, rv[t].w);
+    }
+    // chosen columns two at a time, both rows' loads issued before use
+    for (int j = 0; j < k; j += 2) {
+      const bool two = j + 1 < k;
+      float4 c0[NCH], c1[NCH];
+      load_chunks_gen<G, NCH>(c0, S.colp[j], nv, s, true);
+      load_chunks_gen<G, NCH>(c1, two ? S.colp[j + 1] : S.colp[j], nv, s, two);
+      const float a0 = S.W[j], a1 = two ? S.W[j + 1] : 0.f;
 #pragma unroll
       for (int t = 0; t < NCH; ++t) {
-        const float4 col = (j < k) ? c[t] : aq[t];
-        rv[t].x = fmaf(-aj, col.x, rv[t].x);
-        rv[t].y = fmaf(-aj, col.y, rv[t].y);
-        rv[t].z = fmaf(-aj, col.z, rv[t].z);
-        rv[t].w = fmaf(-aj, col.w, rv[t].w);
+        rv[t].x = fmaf(-a1, c1[t].x, fmaf(-a0, c0[t].x, rv[t].x));
+        rv[t].y = fmaf(-a1, c1[t].y, fmaf(-a0, c0[t].y, rv[t].y));
+        rv[t].z = fmaf(-a1, c1[t].z, fmaf(-a0, c0[t].z, rv[t].z));
+        rv[t].w = fmaf(-a1, c1[t].w, fmaf(-a0, c0[t].w, rv[t].w));
       }
     }
   }
@@ -443,7 +299,7 @@ __global__ void __launch_bounds__(GRP_WARPS * 32)
 omp_update_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                   const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
                   int64_t rbf_row0, int n_cand, const int8_t *__restrict__ Kp, int Kuni, OmpState st,
-                  int64_t *stats) {
+                  int64_t *stats, const float *__restrict__ gram, int T) {
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
@@ -485,21 +341,30 @@ omp_update_kernel(const float *__restrict__ Y, int M, const float *__restrict__ 
   if (n_cand <= 1) {
     q = act ? cb[0] : -1;
   } else {
+    // re-score the candidates in FP32, two rows in flight at a time
     unsigned long long best = 0ull;
-    for (int c = 0; c < n_cand; ++c) {
-      const int a = act ? cb[c] : -1;
-      bool ok = a >= 0 && __ldg(inv_norm + a) > 0.f;
-      bool dup = false;
-      if (ok)
-        for (int j = s; j < k; j += G) dup |= (S.om[j] == a);
-      const unsigned bal = __ballot_sync(kFull, dup);
-      ok = ok && ((bal >> (g * G)) & ((G == 32) ? 0xffffffffu : ((1u << G) - 1u))) == 0u;
-      float4 c4[NCH];
-      load_chunks<G, NCH>(c4, A + (int64_t)(ok ? a : 0) * M, nv, s, ok);
-      const float sc = gsum<G>(dotc<NCH>(c4, rv));
-      if (ok) {
-        const unsigned long long key = pack_key(fabsf(sc) * __ldg(inv_norm + a), a);
-        best = key > best ? key : best;
+    for (int c = 0; c < n_cand; c += 2) {
+      int a[2];
+      bool ok[2];
+      float4 c4[2][NCH];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        a[u] = (act && c + u < n_cand) ? cb[c + u] : -1;
+        ok[u] = a[u] >= 0 && __ldg(inv_norm + a[u]) > 0.f;
+        bool dup = false;
+        if (ok[u])
+          for (int j = s; j < k; j += G) dup |= (S.om[j] == a[u]);
+        const unsigned bal = __ballot_sync(kFull, dup);
+        ok[u] = ok[u] && ((bal >> (g * G)) & ((G == 32) ? 0xffffffffu : ((1u << G) - 1u))) == 0u;
+        load_chunks<G, NCH>(c4[u], A + (int64_t)(ok[u] ? a[u] : 0) * M, nv, s, ok[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const float sc = gsum<G>(dotc<NCH>(c4[u], rv));
+        if (ok[u]) {
+          const unsigned long long key = pack_key(fabsf(sc) * __ldg(inv_norm + a[u]), a[u]);
+          best = key > best ? key : best;
+        }
       }
     }
     q = best ? key_idx(best) : -1;
@@ -520,7 +385,7 @@ omp_update_kernel(const float *__restrict__ Y, int M, const float *__restrict__ 
   __syncwarp();
   float rsq = rsq0;
   const bool ok = grp_append<G, NCH, true>(act, s, M, A + (int64_t)(act ? q : 0) * M, yrow, act ? q : 0, k, yv, rv,
-                                           S, fl, rsq, stats);
+                                           S, fl, rsq, stats, gram, T);
   if (act && !ok) {
     if (s == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
     return;
@@ -590,7 +455,7 @@ omp_restricted_staged_kernel(const float *__restrict__ Y, int M, const float *__
                       int cap, int capS, const int32_t *__restrict__ omega_up, int ldo_up,
                       const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                       int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
-                      int8_t *__restrict__ k_eff, int64_t *stats) {
+                      int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
@@ -680,7 +545,7 @@ omp_restricted_staged_kernel(const float *__restrict__ Y, int M, const float *__
     __syncwarp();
     const int qs = act ? S.misc[1] : 0;
     const float *aqp = (act && qs < capS) ? rows + qs * ldr : A + (int64_t)q * M;
-    const bool ok = grp_append<G, NCH, false>(act, s, M, aqp, yrow, q, k, yv, rv, S, fl, rsq, stats);
+    const bool ok = grp_append<G, NCH, false>(act, s, M, aqp, yrow, q, k, yv, rv, S, fl, rsq, stats, gram, T);
     if (act) {
       if (ok) {
         ++k;
@@ -719,7 +584,7 @@ omp_restricted_coop_kernel(const float *__restrict__ Y, int M, const float *__re
                       int cap, const int32_t *__restrict__ omega_up, int ldo_up,
                       const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                       int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
-                      int8_t *__restrict__ k_eff, int64_t *stats) {
+                      int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
@@ -796,7 +661,8 @@ omp_restricted_coop_kernel(const float *__restrict__ Y, int M, const float *__re
       for (int c = s; c < nc; c += G)
         if (S.cs[c] == q) S.invn[c] = -1.f;  // chosen: no longer eligible
     __syncwarp();
-    const bool ok = grp_append<G, NCH, true>(act, s, M, A + (int64_t)q * M, yrow, q, k, yv, rv, S, fl, rsq, stats);
+    const bool ok = grp_append<G, NCH, true>(act, s, M, A + (int64_t)q * M, yrow, q, k, yv, rv, S, fl, rsq, stats,
+                                             gram, T);
     if (act) {
       if (ok) ++k;
       else act = false;
@@ -817,6 +683,37 @@ omp_restricted_coop_kernel(const float *__restrict__ Y, int M, const float *__re
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// Gram matrix G = A A^T of an effective dictionary (rows a_i): 64 x 64 output
+// tiles, FP32, 4 x 4 outputs per thread.
+__global__ void __launch_bounds__(256) gram_kernel(const float *__restrict__ A, int T, int M, float *__restrict__ Gm) {
+  __shared__ float As[32][64 + 4], Bs[32][64 + 4];
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  float acc[4][4] = {};
+  for (int m0 = 0; m0 < M; m0 += 32) {
+    for (int e = tid; e < 64 * 32; e += 256) {
+      const int r = e >> 5, mm = e & 31;
+      As[mm][r] = (i0 + r < T && m0 + mm < M) ? A[(int64_t)(i0 + r) * M + m0 + mm] : 0.f;
+      Bs[mm][r] = (j0 + r < T && m0 + mm < M) ? A[(int64_t)(j0 + r) * M + m0 + mm] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int mm = 0; mm < 32; ++mm)
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(As[mm][ty * 4 + a], Bs[mm][tx * 4 + c], acc[a][c]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = i0 + ty * 4 + a, j = j0 + tx * 4 + c;
+      if (i < T && j < T) Gm[(int64_t)i * T + j] = acc[a][c];
+    }
+}
+
 // (G, NCH) by problem dimension: M <= 16 G NCH, NCH <= 4.
 template <typename F>
 bool dispatch_group(int M, F &&f) {
@@ -835,6 +732,12 @@ int group_size(int M) { return M <= 64 ? 4 : (M <= 128 ? 8 : 16); }
 }  // namespace
 
 bool omp_dims_supported(int M) { return M > 0 && M % 4 == 0 && M <= 256; }
+
+void launch_gram(const float *A, int T, int M, float *Gm, cudaStream_t s) {
+  if (T == 0) return;
+  const dim3 grid((unsigned)((T + 63) / 64), (unsigned)((T + 63) / 64));
+  gram_kernel<<<grid, 256, 0, s>>>(A, T, M, Gm);
+}
 
 void launch_omp_init(const float *Y, int64_t B, int M, int Mp, const int32_t *perm, OmpState st, cudaStream_t s) {
   int64_t n = B * (int64_t)(M > Mp ? M : Mp);
@@ -860,7 +763,7 @@ void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_n
 
 void launch_omp_update(const float *Y, int M, const float *A, const float *inv_norm,
                        const int32_t *ids, int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni,
-                       OmpState st, int64_t *stats, cudaStream_t s) {
+                       OmpState st, int64_t *stats, const float *gram, int T, cudaStream_t s) {
   if (n == 0) return;
   const int G = group_size(M);
   const int per_cta = GRP_WARPS * (32 / G);
@@ -870,7 +773,8 @@ void launch_omp_update(const float *Y, int M, const float *A, const float *inv_n
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(omp_update_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     omp_update_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n,
-                                                                             rbf_row0, n_cand, Kp, Kuni, st, stats);
+                                                                             rbf_row0, n_cand, Kp, Kuni, st, stats,
+                                                                             gram, T);
   });
 }
 
@@ -890,8 +794,14 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
-                           cudaStream_t s) {
+                           const float *gram, int T, cudaStream_t s) {
   if (n == 0) return;
+  if (variant == 2 && !gram) variant = 0;  // the Gram variant needs the level's Gram matrix
+  if (variant == 2) {
+    launch_omp_restricted_gram(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up, Kp,
+                               Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T, s);
+    return;
+  }
   if (variant == 0) {
     const int G = group_size(M);
     const int per_cta = GRP_WARPS * (32 / G);
@@ -902,7 +812,7 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
         cudaFuncSetAttribute(omp_restricted_coop_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       omp_restricted_coop_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(
           Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega,
-          alpha, ldo, k_eff, stats);
+          alpha, ldo, k_eff, stats, gram, T);
     });
     return;
   }
@@ -918,7 +828,7 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
       cudaFuncSetAttribute(omp_restricted_staged_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     omp_restricted_staged_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(
         Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, capS, omega_up, ldo_up, keff_up, Kp, Kuni, Kb,
-        omega, alpha, ldo, k_eff, stats);
+        omega, alpha, ldo, k_eff, stats, gram, T);
   });
 }
 

@@ -132,20 +132,44 @@ __global__ void norms_kernel(const float *__restrict__ A, int T, int M, int Mp, 
   }
 }
 
-// Synthesis x_hat_p = D_|Omega alpha: one thread per element (b, n), reading
-// the chosen atoms' rows of the L2-resident fine dictionary (coalesced over n).
+// Synthesis x_hat_p = D_|Omega alpha for a block of PPC patches: the chosen
+// atoms' rows of the L2-resident fine dictionary are read coalesced over n,
+// the block is transposed in shared memory and stored element-major
+// (Xh[n][b]), so that the overlap-add below reads neighbouring patches'
+// values from contiguous memory.
 __global__ void synth_kernel(const float *__restrict__ D0, int N0, const int32_t *__restrict__ support,
                              const float *__restrict__ coef, const int8_t *__restrict__ k_eff, int Kmax,
-                             int64_t B, float *__restrict__ Xh) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= B * N0) return;
-  const int64_t b = e / N0;
-  const int n = (int)(e - b * N0);
-  const int k = k_eff[b];
-  float v = 0.f;
-  for (int j = 0; j < k; ++j)
-    v = fmaf(__ldg(coef + b * Kmax + j), __ldg(D0 + (int64_t)__ldg(support + b * Kmax + j) * N0 + n), v);
-  Xh[e] = v;
+                             int64_t B, int ppc, float *__restrict__ Xh) {
+  extern __shared__ float tile[];  // [N0][ppc + 1], then the block's codes
+  const int64_t b0 = (int64_t)blockIdx.x * ppc;
+  const int ld = ppc + 1;
+  const int np = (int)((B - b0) < ppc ? (B - b0) : ppc);
+  int *s_sup = reinterpret_cast<int *>(tile + (size_t)N0 * ld);  // [ppc][Kmax], -1 past k_eff
+  float *s_coef = reinterpret_cast<float *>(s_sup + ppc * Kmax);
+  for (int e = threadIdx.x; e < ppc * Kmax; e += blockDim.x) {
+    const int p = e / Kmax, j = e - p * Kmax;
+    const bool on = p < np && j < k_eff[b0 + p];
+    s_sup[e] = on ? support[(b0 + p) * Kmax + j] : -1;
+    s_coef[e] = on ? coef[(b0 + p) * Kmax + j] : 0.f;
+  }
+  __syncthreads();
+  for (int p = 0; p < np; ++p) {
+    const int *sp = s_sup + p * Kmax;
+    const float *cp = s_coef + p * Kmax;
+    for (int n = threadIdx.x; n < N0; n += blockDim.x) {
+      float v = 0.f;
+      for (int j = 0; j < Kmax; ++j) {
+        const int a = sp[j];
+        if (a >= 0) v = fmaf(cp[j], __ldg(D0 + (int64_t)a * N0 + n), v);
+      }
+      tile[n * ld + p] = v;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N0 * ppc; e += blockDim.x) {
+    const int n = e / ppc, p = e - n * ppc;
+    if (p < np) Xh[(int64_t)n * B + b0 + p] = tile[n * ld + p];
+  }
 }
 
 // Overlap-add: one thread per image pixel (plane, y, x), mean over the covering
@@ -168,7 +192,7 @@ __global__ void gather_kernel(GeomDev g, const float *__restrict__ Xh, int N0,
     for (int ix = x0; ix <= x1; ++ix) {
       const int px = x - origin(ix, g.stride, g.W, g.P);
       const int64_t b = (int64_t)iy * g.nx + ix;
-      acc += __ldg(Xh + b * N0 + (pl * g.P + py) * g.P + px);
+      acc += __ldg(Xh + (int64_t)((pl * g.P + py) * g.P + px) * ((int64_t)g.nx * g.ny) + b);
       ++cnt;
     }
   }
@@ -214,7 +238,12 @@ void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *
   const int64_t B = (int64_t)g.nx * g.ny;
   const int64_t n = (int64_t)g.Ly * g.Lx * g.H * g.W;
   if (n == 0) return;
-  if (B * N0) synth_kernel<<<blocks(B * N0, 256), 256, 0, s>>>(D0, N0, support, coef, k_eff, Kmax, B, Xh);
+  if (B * N0) {
+    const int ppc = N0 <= 256 ? 32 : (N0 <= 512 ? 16 : 8);
+    const size_t sm = sizeof(float) * (size_t)N0 * (ppc + 1) + 8 * (size_t)ppc * Kmax;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    synth_kernel<<<blocks(B, ppc), 256, sm, s>>>(D0, N0, support, coef, k_eff, Kmax, B, ppc, Xh);
+  }
   gather_kernel<<<blocks(n, 256), 256, 0, s>>>(g, Xh, N0, cover_y, cover_x, img);
 }
 

@@ -229,3 +229,35 @@ def test_exactly_dependent_atom_ends_the_patch():
     assert ctx.stats()["fp64_fallbacks"] >= 1
     rate, worst, bad = compare(A, sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy().astype(int), o, a, k)
     assert rate == 1.0 and worst <= REL_TOL
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("key", ["bayer", "lightfield", "denoise_ragged"])
+def test_restricted_variants_agree_with_oracle(key, variant):
+    """Every restricted-solver variant the autotuner may pick meets the parity
+    bar: L2-cooperative (0), shared-memory staged (1), Gram-matrix proxy with
+    exact re-score (2)."""
+    from paper_1511_05174_gb300.context import Context
+    w = _workload(key)
+    o, a, k, _ = oracle.cross_scale_omp(w)
+    ctx = Context(0)
+    ctx.load_workload(w)
+    ctx.set_kernel_variant(variant)
+    Y = ctx.extract(torch.from_numpy(w.meas).cuda())
+    K, K_patch, Kmax = budgets(w, "cross_scale")
+    sup, coef, keff = ctx.solve(Y, "cross_scale", "fp32", K=K, K_patch=K_patch, Kmax=Kmax)
+    rate, worst, bad = compare(w.dicts[0], sup.cpu().numpy(), coef.cpu().numpy(),
+                               keff.cpu().numpy().astype(np.int64), o, a, k)
+    assert rate >= MATCH and worst <= REL_TOL, bad[:10]
+
+
+def test_autotune_picks_a_variant():
+    from paper_1511_05174_gb300.context import Context
+    w = _workload("bayer")
+    ctx = Context(0)
+    ctx.load_workload(w)
+    Y = ctx.extract(torch.from_numpy(w.meas).cuda())
+    K, K_patch, Kmax = budgets(w, "cross_scale")
+    r = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
+    assert r["restricted_variant"] in (0, 1, 2) and all(t > 0 for t in r["ms"])
+    assert r["ms"][r["restricted_variant"]] == min(r["ms"])
