@@ -106,7 +106,7 @@ csp_status ws_get_t(csp_ctx *ctx, int slot, size_t count, T **out) {
 }
 
 const char *const kKernelNames[KK_COUNT] = {"extract", "downsample", "prepare", "omp_init", "proxy_fp32",
-                                            "proxy_bf16", "omp_update", "restricted", "aggregate"};
+                                            "proxy_bf16", "omp_update", "restricted", "aggregate", "lift"};
 
 cudaEvent_t pool_event(csp_ctx *ctx) {
   if (!ctx->ev_pool.empty()) {
@@ -156,6 +156,7 @@ enum Slot {
   WS_LV_OMEGA, WS_LV_ALPHA = WS_LV_OMEGA + CSP_MAX_LEVELS, WS_LV_KEFF = WS_LV_ALPHA + CSP_MAX_LEVELS,
   WS_LV_Y = WS_LV_KEFF + CSP_MAX_LEVELS,
   WS_XH = WS_LV_Y + CSP_MAX_LEVELS,
+  WS_SCRATCH, WS_LIFT, WS_LIFTBF,
   WS_COUNT
 };
 
@@ -172,6 +173,9 @@ int count_1d(int E, int P, int s) {
 }
 
 void free_level_derived(csp_ctx *ctx, LevelData &L) {
+  dev_free(ctx, L.Dbf);
+  L.Dbf = nullptr;
+  L.per_patch = false;
   for (int p = 0; p < kMaxPhases; ++p) {
     if (L.A[p] && L.A[p] != L.D) dev_free(ctx, L.A[p]);
     dev_free(ctx, L.inv_norm[p]);
@@ -197,13 +201,34 @@ csp_status prepare(csp_ctx *ctx, cudaStream_t s) {
   if (ctx->prepared) return CSP_OK;
   if (!ctx->has_geom) return fail(ctx, CSP_ERR_NOT_READY, "geometry not set");
   if (!ctx->has_sensing) return fail(ctx, CSP_ERR_NOT_READY, "sensing operator not set");
-  if (ctx->sense_kind == CSP_SENSE_CODED_EXPOSURE)
-    return fail(ctx, CSP_ERR_UNSUPPORTED, "coded exposure (per-patch Phi) is not implemented in this build");
   const int nl = ctx->geom.n_levels;
   for (int l = 0; l < nl; ++l) {
     LevelData &L = ctx->lv[l];
     if (!L.D) return fail(ctx, CSP_ERR_NOT_READY, "dictionary of level " + std::to_string(l) + " not loaded");
     free_level_derived(ctx, L);
+    if (ctx->sense_kind == CSP_SENSE_CODED_EXPOSURE) {
+      // per-patch Phi: one effective dictionary per patch, per-patch column norms,
+      // and BF16 rows of D for the lifted tensor-core proxy
+      L.M = ctx->M;
+      L.Mp = (L.M + 63) / 64 * 64;
+      L.Np = (L.N + 63) / 64 * 64;
+      if (!omp_dims_supported(L.M))
+        return fail(ctx, CSP_ERR_UNSUPPORTED, "problem dimension must be a multiple of 4, <= 256");
+      const size_t rows = (size_t)ctx->B * L.T;
+      CSP_TRY(dev_alloc_t(ctx, &L.A[0], rows * L.M));
+      CSP_TRY(dev_alloc_t(ctx, &L.inv_norm[0], rows));
+      CSP_TRY(dev_alloc_t(ctx, &L.Dbf, (size_t)L.T * L.Np));
+      unsigned int *mx = nullptr;
+      CSP_TRY(ws_get_t(ctx, WS_SCRATCH, 4, &mx));
+      run(ctx, KK_PREP, s, (int64_t)rows, [&] {
+        launch_effective_dict_pp(ctx->gd, ctx->codes, l, L.D, L.T, L.N, L.A[0], ctx->B, s);
+      });
+      run(ctx, KK_PREP, s, (int64_t)rows, [&] { launch_inv_row_norms(L.A[0], (int64_t)rows, L.M, L.inv_norm[0], mx, s); });
+      run(ctx, KK_PREP, s, L.T, [&] { launch_bf16_rows(L.D, L.T, L.N, L.Np, L.Dbf, s); });
+      L.per_patch = true;
+      L.n_phase = 1;
+      continue;
+    }
     const bool ident = ctx->sense_kind == CSP_SENSE_IDENTITY;
     L.M = ident ? L.N : ctx->M;
     L.Mp = (L.M + 63) / 64 * 64;
@@ -368,6 +393,7 @@ csp_status csp_set_sensing(csp_ctx *ctx, const csp_sensing *sensing) {
       break;
     case CSP_SENSE_CODED_EXPOSURE:
       if (!sensing->codes) return fail(ctx, CSP_ERR_INVALID, "coded exposure needs codes");
+      if (g.plane_rows != 1) return fail(ctx, CSP_ERR_INVALID, "coded exposure needs a 1 x F (frames) plane grid");
       M = PP;
       code_bytes = (size_t)planes * g.H * g.W;
       break;
@@ -517,16 +543,16 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
   if (!prm->K_patch[0] && prm->K[0] > prm->Kmax) return fail(ctx, CSP_ERR_INVALID, "K[0] exceeds Kmax");
   for (int l = 0; l + 1 < nl; ++l)
     if (!ctx->lv[l].links) return fail(ctx, CSP_ERR_NOT_READY, "scale links of level " + std::to_string(l) + " not loaded");
-  if (ctx->sense_kind == CSP_SENSE_BAYER_RGGB && B != ctx->B)
-    return fail(ctx, CSP_ERR_INVALID, "Bayer sensing solves the geometry's patch grid: B must equal the patch count");
+  if ((ctx->sense_kind == CSP_SENSE_BAYER_RGGB || ctx->sense_kind == CSP_SENSE_CODED_EXPOSURE) && B != ctx->B)
+    return fail(ctx, CSP_ERR_INVALID, "Bayer / coded-exposure sensing solves the geometry's patch grid: B must equal the patch count");
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard dg(ctx->device);
   CSP_TRY(prepare(ctx, s));
   const bool bf16 = prm->precision == CSP_PREC_BF16;
   const int top = nl - 1;
   const LevelData &LT = ctx->lv[top];
-  if (bf16 && !proxy_bf16_supported(LT.M, LT.T))
-    return fail(ctx, CSP_ERR_UNSUPPORTED, "BF16 tensor-core proxy not available for this shape");
+  if (bf16 && !proxy_bf16_supported(LT.per_patch ? LT.N : LT.M, LT.T))
+    return fail(ctx, CSP_ERR_UNSUPPORTED, "BF16 tensor-core proxy not available for this shape (dimension <= 256)");
   for (int l = 1; l < nl; ++l) {
     const int cap = ctx->lv[l - 1].max_children * Kb[l];
     if (cap > 1024) return fail(ctx, CSP_ERR_UNSUPPORTED, "candidate capacity above 1024 (max children x K)");
@@ -574,10 +600,18 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
   // full-dictionary OMP at the top level (the only level in plain mode)
   {
     const LevelData &L = ctx->lv[top];
+    const bool pp = L.per_patch;
     OmpState st{};
     CSP_TRY(ws_get_t(ctx, WS_R, (size_t)B * L.M, &st.R));
     st.Rbf = nullptr;
-    if (bf16) CSP_TRY(ws_get_t(ctx, WS_RBF, (size_t)B * L.Mp, &st.Rbf));
+    if (bf16 && !pp) CSP_TRY(ws_get_t(ctx, WS_RBF, (size_t)B * L.Mp, &st.Rbf));
+    // per-patch Phi: the proxy runs on the lifted residual z = U^T Phi_p^T r against D
+    float *Zl = nullptr;
+    __nv_bfloat16 *Zbf = nullptr;
+    if (pp) {
+      if (!bf16) CSP_TRY(ws_get_t(ctx, WS_LIFT, (size_t)B * L.N, &Zl));
+      else CSP_TRY(ws_get_t(ctx, WS_LIFTBF, (size_t)B * L.Np, &Zbf));
+    }
     st.Kb = Kb[top];
     st.ldo = ldo[top];
     CSP_TRY(ws_get_t(ctx, WS_L, (size_t)B * (Kb[top] * (Kb[top] + 1) / 2), &st.Lpk));
@@ -587,27 +621,38 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
     st.omega = lv_om[top];
     st.alpha = lv_al[top];
     st.k_eff = lv_ke[top];
-    run(ctx, KK_INIT, s, B, [&] { launch_omp_init(Yl[top], B, L.M, bf16 ? L.Mp : 0, phased ? ctx->phase_ids : nullptr, st, s); });
+    const int64_t a_ps = pp ? (int64_t)L.T * L.M : 0, inv_ps = pp ? (int64_t)L.T : 0;
+    run(ctx, KK_INIT, s, B, [&] {
+      launch_omp_init(Yl[top], B, L.M, (bf16 && !pp) ? L.Mp : 0, phased ? ctx->phase_ids : nullptr, st, s);
+    });
     bool maps_ok = true;
     for (int it = 0; it < Kb[top]; ++it) {
+      if (pp)
+        run(ctx, KK_LIFT, s, B, [&] { launch_lift(ctx->gd, ctx->codes, top, st.R, B, Zl, Zbf, bf16 ? L.Np : L.N, s); });
       for (int ph = 0; ph < nph; ++ph) {
         if (bf16)
           run(ctx, KK_PROXY_BF16, s, n_of(ph), [&] {
-            maps_ok &= launch_proxy_bf16(st.Rbf, B, L.Mp, L.Abf[ph], L.T, phased ? ctx->phase_start[ph] : 0,
-                                         ids_of(ph), n_of(ph), st.flags, st.cand,
-                                         (unsigned long long *)(ctx->stats_dev + 4), s);
+            maps_ok &= pp ? launch_proxy_bf16(Zbf, B, L.Np, L.Dbf, L.T, 0, ids_of(ph), n_of(ph), st.flags, st.cand,
+                                              (unsigned long long *)(ctx->stats_dev + 4), L.inv_norm[0], s)
+                          : launch_proxy_bf16(st.Rbf, B, L.Mp, L.Abf[ph], L.T, phased ? ctx->phase_start[ph] : 0,
+                                              ids_of(ph), n_of(ph), st.flags, st.cand,
+                                              (unsigned long long *)(ctx->stats_dev + 4), nullptr, s);
           });
         else
           run(ctx, KK_PROXY_FP32, s, n_of(ph), [&] {
-            launch_proxy_fp32(st.R, L.M, L.A[ph], L.inv_norm[ph], L.T, ids_of(ph), n_of(ph), st.omega, st.ldo,
-                              st.k_eff, st.flags, st.cand, s);
+            if (pp)
+              launch_proxy_fp32(Zl, L.N, L.D, nullptr, L.T, ids_of(ph), n_of(ph), st.omega, st.ldo, st.k_eff, st.flags,
+                                st.cand, L.inv_norm[0], s);
+            else
+              launch_proxy_fp32(st.R, L.M, L.A[ph], L.inv_norm[ph], L.T, ids_of(ph), n_of(ph), st.omega, st.ldo,
+                                st.k_eff, st.flags, st.cand, nullptr, s);
           });
       }
       for (int ph = 0; ph < nph; ++ph)
         run(ctx, KK_UPDATE, s, n_of(ph), [&] {
           launch_omp_update_wave(Yl[top], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph),
-                            phased ? ctx->phase_start[ph] : 0, bf16 ? kTopP : 1, prm->K_patch[top], prm->K[top], st,
-                            ctx->stats_dev, L.G[ph], L.T, s);
+                                 phased ? ctx->phase_start[ph] : 0, bf16 ? kTopP : 1, prm->K_patch[top], prm->K[top],
+                                 st, ctx->stats_dev, L.G[ph], L.T, a_ps, inv_ps, s);
         });
       if (!maps_ok) return fail(ctx, CSP_ERR_CUDA, "tensor map encoding for the BF16 proxy failed");
     }
@@ -618,9 +663,10 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
     const int cap = std::max(1, L.max_children * Kb[l + 1]);
     for (int ph = 0; ph < nph; ++ph)
       run(ctx, KK_RESTRICTED, s, n_of(ph), [&] {
-        launch_omp_restricted(ctx->restricted_variant, Yl[l], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph), L.child_off,
-                              L.child_idx, cap, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1], prm->K_patch[l], prm->K[l],
-                              Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], ctx->stats_dev, L.G[ph], L.T, s);
+        launch_omp_restricted(ctx->restricted_variant, Yl[l], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph),
+                              L.child_off, L.child_idx, cap, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1], prm->K_patch[l],
+                              prm->K[l], Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], ctx->stats_dev, L.G[ph], L.T,
+                              L.per_patch ? (int64_t)L.T * L.M : 0, L.per_patch ? (int64_t)L.T : 0, s);
       });
   }
   CSP_CUDA(ctx, cudaGetLastError());

@@ -42,6 +42,9 @@ struct LevelData {
   __nv_bfloat16 *Abf[kMaxPhases] = {};  // [T][Mp] a_i / ||a_i|| in BF16 (tensor-core proxy)
   int Mp = 0;                  // BF16 row length (M rounded up to 64)
   float *G[kMaxPhases] = {};   // [T][T] Gram matrix A A^T (null when T is too large)
+  bool per_patch = false;      // A[0] holds one effective dictionary per patch ([B][T][M])
+  __nv_bfloat16 *Dbf = nullptr;  // per-patch mode: BF16 rows of D (unnormalised, padded to Np)
+  int Np = 0;                  // per-patch mode: lifted dimension N rounded up to 64
   // Cross-scale map f to the next coarser level (valid when this level < n_levels - 1).
   int32_t *child_off = nullptr;   // [T_{l+1} + 1]
   int32_t *child_idx = nullptr;   // [T] children of each coarse atom, ascending
@@ -60,7 +63,7 @@ struct Buf {
 namespace csp {
 enum KernelKind {
   KK_EXTRACT, KK_DOWNSAMPLE, KK_PREP, KK_INIT, KK_PROXY_FP32, KK_PROXY_BF16, KK_UPDATE, KK_RESTRICTED,
-  KK_AGGREGATE, KK_COUNT
+  KK_AGGREGATE, KK_LIFT, KK_COUNT
 };
 struct ProfRec {
   int kind;
@@ -117,6 +120,15 @@ void launch_effective_dict(const GeomDev &g, int sense_kind, int shots, const ui
                            cudaStream_t s);
 void launch_norms(const float *A, int T, int M, int Mp, float *inv_norm, __nv_bfloat16 *Abf,
                   cudaStream_t s);
+// Per-patch sensing (per-pixel coded exposure): A_p = Phi_p U_l D for every patch
+// ([B][T][P*P]), inverse row norms over `rows` rows (scratch: one device uint),
+// BF16 rows of D (unnormalised, padded to Np), lifted residual z = U_l^T Phi_p^T r.
+void launch_effective_dict_pp(const GeomDev &g, const uint8_t *codes, int level, const float *D, int T, int N,
+                              float *A, int64_t B, cudaStream_t s);
+void launch_inv_row_norms(const float *A, int64_t rows, int M, float *inv, unsigned int *scratch, cudaStream_t s);
+void launch_bf16_rows(const float *D, int T, int N, int Np, __nv_bfloat16 *out, cudaStream_t s);
+void launch_lift(const GeomDev &g, const uint8_t *codes, int level, const float *R, int64_t B, float *Z,
+                 __nv_bfloat16 *Zbf, int Np, cudaStream_t s);
 // Synthesis into Xh ([B][N0] scratch) then per-pixel overlap-add average (2 launches).
 void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *support,
                       const float *coef, const int8_t *k_eff, int Kmax, const int32_t *cover_y,
@@ -140,23 +152,24 @@ struct OmpState {
 // r = y, empty supports; the BF16 residual copy is written in sorted-position
 // order (row p holds patch perm[p]; perm == nullptr: identity).
 void launch_omp_init(const float *Y, int64_t B, int M, int Mp, const int32_t *perm, OmpState st, cudaStream_t s);
+// pinv: optional per-patch inverse norms [B][T] (per-patch Phi), else inv_norm[T].
 void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_norm, int T,
                        const int32_t *ids, int64_t n, const int32_t *omega, int ldo,
-                       const int8_t *k_eff, const uint8_t *flags, int32_t *cand, cudaStream_t s);
+                       const int8_t *k_eff, const uint8_t *flags, int32_t *cand, const float *pinv,
+                       cudaStream_t s);
 bool proxy_bf16_supported(int M, int T);
 bool omp_dims_supported(int M);  // M % 4 == 0 and M <= 256
 // Tensor-core proxy over the patches at sorted positions row0 .. row0 + n - 1
 // (list ids, may be null).  Returns false when a tensor map cannot be built.
 bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, const __nv_bfloat16 *Abf, int T,
                        int64_t row0, const int32_t *ids, int64_t n, const uint8_t *flags, int32_t *cand,
-                       unsigned long long *err, cudaStream_t s);
-void launch_omp_update(const float *Y, int M, const float *A, const float *inv_norm,
-                       const int32_t *ids, int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni,
-                       OmpState st, int64_t *stats, const float *gram, int T, cudaStream_t s);
+                       unsigned long long *err, const float *pinv, cudaStream_t s);
 // Load-wave variants (k_grp.cu): one update iteration; restricted OMP with the Gram-matrix proxy.
+// a_pstride / inv_pstride: per-patch strides of A and inv_norm (0: shared by all patches).
 void launch_omp_update_wave(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,
                             int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni, OmpState st,
-                            int64_t *stats, const float *gram, int T, cudaStream_t s);
+                            int64_t *stats, const float *gram, int T, int64_t a_pstride, int64_t inv_pstride,
+                            cudaStream_t s);
 void launch_omp_restricted_gram(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,
                                 int64_t n, const int32_t *child_off, const int32_t *child_idx, int cap,
                                 const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int8_t *Kp,
@@ -171,6 +184,6 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
-                           const float *gram, int T, cudaStream_t s);
+                           const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, cudaStream_t s);
 
 }  // namespace csp

@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(WV_WARPS * 32)
 omp_update_wave_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                        const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
                        int64_t rbf_row0, int n_cand, const int8_t *__restrict__ Kp, int Kuni, OmpState st,
-                       int64_t *stats, const float *__restrict__ gram, int T) {
+                       int64_t *stats, const float *__restrict__ gram, int T, int64_t a_pstride,
+                       int64_t inv_pstride) {
   constexpr int NG = 32 / G;
   constexpr int KPL = (CSP_MAX_K + G - 1) / G;  // chosen-atom entries per lane
   extern __shared__ __align__(16) char smem_raw[];
@@ -154,6 +155,8 @@ omp_update_wave_kernel(const float *__restrict__ Y, int M, const float *__restri
   const GrpSmem S = carve(smem_raw + (size_t)(wib * NG + g) * grp_smem_bytes(st.Kb, 0), st.Kb, 0);
   const int nv = M >> 2;
   const int64_t b = valid ? (ids ? __ldg(ids + wi) : wi) : 0;
+  A += b * a_pstride;            // per-patch effective dictionary (stride 0: shared)
+  inv_norm += b * inv_pstride;
   // wave: per-patch state
   uint8_t fl = valid ? st.flags[b] : 1;
   const int k = valid ? st.k_eff[b] : 0;
@@ -651,7 +654,8 @@ int narrow_group(int M) { return M <= 64 ? 4 : (M <= 128 ? 8 : 16); }
 
 void launch_omp_update_wave(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,
                             int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni, OmpState st,
-                            int64_t *stats, const float *gram, int T, cudaStream_t s) {
+                            int64_t *stats, const float *gram, int T, int64_t a_pstride, int64_t inv_pstride,
+                            cudaStream_t s) {
   if (n == 0) return;
   const int per_cta = WV_WARPS * (32 / wave_group(M));
   const size_t sm = (size_t)grp_smem_bytes(st.Kb, 0) * per_cta;
@@ -660,7 +664,7 @@ void launch_omp_update_wave(const float *Y, int M, const float *A, const float *
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(omp_update_wave_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     omp_update_wave_kernel<GG, NCH><<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(
-        Y, M, A, inv_norm, ids, n, rbf_row0, n_cand, Kp, Kuni, st, stats, gram, T);
+        Y, M, A, inv_norm, ids, n, rbf_row0, n_cand, Kp, Kuni, st, stats, gram, T, a_pstride, inv_pstride);
   });
 }
 

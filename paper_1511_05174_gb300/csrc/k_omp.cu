@@ -199,13 +199,14 @@ proxy_fp32_kernel(const float *__restrict__ R, int M, const float *__restrict__ 
                   const float *__restrict__ inv_norm, int T, const int32_t *__restrict__ ids,
                   int64_t n, const int32_t *__restrict__ omega, int ldo,
                   const int8_t *__restrict__ k_eff, const uint8_t *__restrict__ flags,
-                  int32_t *__restrict__ cand) {
+                  int32_t *__restrict__ cand, const float *__restrict__ pinv) {
   extern __shared__ __align__(16) float smem[];
   const int Mr = (M + PX_KC - 1) / PX_KC * PX_KC;
   float *Rs = smem;                      // [Mr][PX_TP]  residuals, measurement-major
   float *As = Rs + (size_t)Mr * PX_TP;   // [PX_KC][PX_AS] atom chunk, measurement-major
   int *Om = (int *)(As + PX_KC * PX_AS); // [PX_TP][ldo]
   int *Kc = Om + PX_TP * ldo;            // [PX_TP]
+  int64_t *Pb = reinterpret_cast<int64_t *>(Kc + PX_TP + (PX_TP & 1));  // [PX_TP] patch ids
   const int tid = threadIdx.x;
   const int64_t p0 = (int64_t)blockIdx.x * PX_TP;
 
@@ -226,7 +227,9 @@ proxy_fp32_kernel(const float *__restrict__ R, int M, const float *__restrict__ 
   }
   for (int p = tid; p < PX_TP; p += 256) {
     const int64_t pi = p0 + p;
-    Kc[p] = (pi < n) ? k_eff[ids ? ids[pi] : pi] : 0;
+    const int64_t bb = (pi < n) ? (ids ? ids[pi] : pi) : 0;
+    Kc[p] = (pi < n) ? k_eff[bb] : 0;
+    Pb[p] = bb;
   }
 
   const int ty = tid >> 4, tx = tid & 15;
@@ -257,10 +260,13 @@ proxy_fp32_kernel(const float *__restrict__ R, int M, const float *__restrict__ 
     for (int j = 0; j < 4; ++j) {
       const int ai = a0 + tx * 4 + j;
       if (ai >= T) continue;
-      const float inv = __ldg(inv_norm + ai);
-      if (!(inv > 0.f)) continue;
+      const float invs = pinv ? 1.f : __ldg(inv_norm + ai);
+      if (!(invs > 0.f)) continue;
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
+        // per-patch norms (per-patch Phi): 1/||Phi_p U d_i|| from the patch's row of the table
+        const float inv = pinv ? __ldg(pinv + Pb[ty * 4 + i] * (int64_t)T + ai) : invs;
+        if (!(inv > 0.f)) continue;
         const unsigned long long key = pack_key(fabsf(acc[i][j]) * inv, ai);
         if (key > best[i]) {
           const int p = ty * 4 + i;
@@ -289,143 +295,7 @@ proxy_fp32_kernel(const float *__restrict__ R, int M, const float *__restrict__ 
   }
 }
 
-// ---------------------------------------------------------------------------
-// Update: one iteration of every patch of the id list (one group per patch).
-// ---------------------------------------------------------------------------
 constexpr int GRP_WARPS = 4;
-
-template <int G, int NCH>
-__global__ void __launch_bounds__(GRP_WARPS * 32)
-omp_update_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
-                  const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
-                  int64_t rbf_row0, int n_cand, const int8_t *__restrict__ Kp, int Kuni, OmpState st,
-                  int64_t *stats, const float *__restrict__ gram, int T) {
-  constexpr int NG = 32 / G;
-  extern __shared__ __align__(16) char smem_raw[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
-  const int64_t wbase = ((int64_t)blockIdx.x * GRP_WARPS + wib) * NG;
-  if (wbase >= n) return;  // whole warp
-  const int64_t wi = wbase + g;
-  const bool valid = wi < n;
-  const int64_t b = valid ? (ids ? ids[wi] : wi) : 0;
-  const GrpSmem S = carve(smem_raw + (size_t)(wib * NG + g) * grp_smem_bytes(st.Kb, 0), st.Kb, 0);
-  const int nv = M >> 2;
-  uint8_t fl = valid ? st.flags[b] : 1;
-  const int k = valid ? st.k_eff[b] : 0;
-  int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
-  Kpb = Kpb < st.Kb ? Kpb : st.Kb;
-  bool act = !(fl & 1) && k < Kpb;
-  if (valid && !(fl & 1) && k >= Kpb && s == 0) st.flags[b] = fl | 1;
-  int32_t *om_g = st.omega + b * st.ldo;
-  const float *yrow = Y + b * M;
-  float4 yv[NCH], rv[NCH];
-  load_chunks<G, NCH>(yv, yrow, nv, s, act);
-  load_chunks<G, NCH>(rv, st.R + b * M, nv, s, act);
-  const float ysq = gsum<G>(dotc<NCH>(yv, yv));
-  const float rsq0 = gsum<G>(dotc<NCH>(rv, rv));
-  if (act && rsq0 <= kEpsR32 * ysq) {
-    act = false;
-    if (s == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
-  }
-  // stage the chosen atoms
-  if (act)
-    for (int j = s; j < k; j += G) {
-      const int a = om_g[j];
-      S.om[j] = a;
-      S.colp[j] = A + (int64_t)a * M;
-    }
-  __syncwarp();
-  // candidate: the proxy's argmax, or the best of its re-scored top candidates
-  const int32_t *cb = st.cand + b * kTopP;
-  int q = -1;
-  if (n_cand <= 1) {
-    q = act ? cb[0] : -1;
-  } else {
-    // re-score the candidates in FP32, two rows in flight at a time
-    unsigned long long best = 0ull;
-    for (int c = 0; c < n_cand; c += 2) {
-      int a[2];
-      bool ok[2];
-      float4 c4[2][NCH];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        a[u] = (act && c + u < n_cand) ? cb[c + u] : -1;
-        ok[u] = a[u] >= 0 && __ldg(inv_norm + a[u]) > 0.f;
-        bool dup = false;
-        if (ok[u])
-          for (int j = s; j < k; j += G) dup |= (S.om[j] == a[u]);
-        const unsigned bal = __ballot_sync(kFull, dup);
-        ok[u] = ok[u] && ((bal >> (g * G)) & ((G == 32) ? 0xffffffffu : ((1u << G) - 1u))) == 0u;
-        load_chunks<G, NCH>(c4[u], A + (int64_t)(ok[u] ? a[u] : 0) * M, nv, s, ok[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const float sc = gsum<G>(dotc<NCH>(c4[u], rv));
-        if (ok[u]) {
-          const unsigned long long key = pack_key(fabsf(sc) * __ldg(inv_norm + a[u]), a[u]);
-          best = key > best ? key : best;
-        }
-      }
-    }
-    q = best ? key_idx(best) : -1;
-  }
-  if (act && q < 0) {
-    act = false;
-    if (s == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
-  }
-  float *L_g = st.Lpk + b * tri(st.Kb);
-  float *z_g = st.z + b * st.Kb;
-  if (act && !(fl & 2)) {
-    for (int e = s; e < tri(k); e += G) S.L[e] = L_g[e];
-    for (int j = s; j < k; j += G) {
-      S.z[j] = z_g[j];
-      S.Linv[j] = 1.f / L_g[tri(j) + j];
-    }
-  }
-  __syncwarp();
-  float rsq = rsq0;
-  const bool ok = grp_append<G, NCH, true>(act, s, M, A + (int64_t)(act ? q : 0) * M, yrow, act ? q : 0, k, yv, rv,
-                                           S, fl, rsq, stats, gram, T);
-  if (act && !ok) {
-    if (s == 0) { st.flags[b] = fl | 1; atomicAdd((unsigned long long *)&stats[1], 1ull); }
-    return;
-  }
-  if (!act) return;
-  // write back
-  if (!(fl & 2))
-    for (int j = s; j <= k; j += G) L_g[tri(k) + j] = S.L[tri(k) + j];
-  for (int j = s; j <= k; j += G) st.alpha[b * st.ldo + j] = S.W[j];
-  float4 *R4 = reinterpret_cast<float4 *>(st.R + b * M);
-#pragma unroll
-  for (int t = 0; t < NCH; ++t) {
-    const int j = s + G * t;
-    if (j < nv) R4[j] = rv[t];
-  }
-  if (st.Rbf) {
-    const int Mp = (M + 63) / 64 * 64;
-    __nv_bfloat16 *rb = st.Rbf + (rbf_row0 + wi) * Mp;  // sorted-position order
-#pragma unroll
-    for (int t = 0; t < NCH; ++t) {
-      const int j = s + G * t;
-      if (j < nv) {
-        rb[4 * j + 0] = __float2bfloat16_rn(rv[t].x);
-        rb[4 * j + 1] = __float2bfloat16_rn(rv[t].y);
-        rb[4 * j + 2] = __float2bfloat16_rn(rv[t].z);
-        rb[4 * j + 3] = __float2bfloat16_rn(rv[t].w);
-      }
-    }
-  }
-  if (s == 0) {
-    if (!(fl & 2)) z_g[k] = S.z[k];
-    om_g[k] = q;
-    st.k_eff[b] = (int8_t)(k + 1);
-    uint8_t nf = fl;
-    if (k + 1 >= Kpb) nf |= 1;
-    if (rsq <= kEpsR32 * ysq) nf |= 1;
-    if ((nf & 1) && k + 1 < Kpb) atomicAdd((unsigned long long *)&stats[1], 1ull);
-    st.flags[b] = nf;
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Restricted OMP (fine step of Algorithm 2), all iterations, one group per
@@ -455,7 +325,8 @@ omp_restricted_staged_kernel(const float *__restrict__ Y, int M, const float *__
                       int cap, int capS, const int32_t *__restrict__ omega_up, int ldo_up,
                       const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                       int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
-                      int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
+                      int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T,
+                      int64_t a_pstride, int64_t inv_pstride) {
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
@@ -464,6 +335,8 @@ omp_restricted_staged_kernel(const float *__restrict__ Y, int M, const float *__
   const int64_t wi = wbase + g;
   const bool valid = wi < n;
   const int64_t b = valid ? (ids ? ids[wi] : wi) : 0;
+  A += b * a_pstride;            // per-patch effective dictionary (stride 0: shared)
+  inv_norm += b * inv_pstride;
   char *gbase = smem_raw + (size_t)(wib * NG + g) * rs_group_bytes(M, Kb, cap, capS);
   const GrpSmem S = carve(gbase, Kb, cap);
   float *rs = reinterpret_cast<float *>(gbase + grp_smem_bytes(Kb, cap));
@@ -584,7 +457,8 @@ omp_restricted_coop_kernel(const float *__restrict__ Y, int M, const float *__re
                       int cap, const int32_t *__restrict__ omega_up, int ldo_up,
                       const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                       int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
-                      int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
+                      int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T,
+                      int64_t a_pstride, int64_t inv_pstride) {
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
@@ -593,6 +467,8 @@ omp_restricted_coop_kernel(const float *__restrict__ Y, int M, const float *__re
   const int64_t wi = wbase + g;
   const bool valid = wi < n;
   const int64_t b = valid ? (ids ? ids[wi] : wi) : 0;
+  A += b * a_pstride;            // per-patch effective dictionary (stride 0: shared)
+  inv_norm += b * inv_pstride;
   const GrpSmem S = carve(smem_raw + (size_t)(wib * NG + g) * grp_smem_bytes(Kb, cap), Kb, cap);
   const int nv = M >> 2;
   int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
@@ -748,34 +624,19 @@ void launch_omp_init(const float *Y, int64_t B, int M, int Mp, const int32_t *pe
 
 void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_norm, int T,
                        const int32_t *ids, int64_t n, const int32_t *omega, int ldo,
-                       const int8_t *k_eff, const uint8_t *flags, int32_t *cand, cudaStream_t s) {
+                       const int8_t *k_eff, const uint8_t *flags, int32_t *cand, const float *pinv,
+                       cudaStream_t s) {
   if (n == 0) return;
   const int Mr = (M + PX_KC - 1) / PX_KC * PX_KC;
-  const size_t sm = sizeof(float) * ((size_t)Mr * PX_TP + PX_KC * PX_AS) + sizeof(int) * (PX_TP * ldo + PX_TP);
+  const size_t sm = sizeof(float) * ((size_t)Mr * PX_TP + PX_KC * PX_AS) + sizeof(int) * (PX_TP * ldo + PX_TP + 2) +
+                    sizeof(int64_t) * PX_TP;
   static size_t configured = 0;
   if (sm > 48 * 1024 && sm > configured) {
     cudaFuncSetAttribute(proxy_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     configured = sm;
   }
   proxy_fp32_kernel<<<blocks(n, PX_TP), 256, sm, s>>>(R, M, A, inv_norm, T, ids, n, omega, ldo, k_eff,
-                                                      flags, cand);
-}
-
-void launch_omp_update(const float *Y, int M, const float *A, const float *inv_norm,
-                       const int32_t *ids, int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni,
-                       OmpState st, int64_t *stats, const float *gram, int T, cudaStream_t s) {
-  if (n == 0) return;
-  const int G = group_size(M);
-  const int per_cta = GRP_WARPS * (32 / G);
-  const size_t sm = (size_t)grp_smem_bytes(st.Kb, 0) * per_cta;
-  dispatch_group(M, [&](auto gc, auto nc) {
-    constexpr int GG = decltype(gc)::value, NCH = decltype(nc)::value;
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(omp_update_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    omp_update_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n,
-                                                                             rbf_row0, n_cand, Kp, Kuni, st, stats,
-                                                                             gram, T);
-  });
+                                                      flags, cand, pinv);
 }
 
 // (G, NCH) of the restricted kernel: wide groups (one candidate per lane).
@@ -794,9 +655,9 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
-                           const float *gram, int T, cudaStream_t s) {
+                           const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, cudaStream_t s) {
   if (n == 0) return;
-  if (variant == 2 && !gram) variant = 0;  // the Gram variant needs the level's Gram matrix
+  if (variant == 2 && (!gram || a_pstride)) variant = 0;  // the Gram variant needs a shared Gram matrix  // the Gram variant needs the level's Gram matrix
   if (variant == 2) {
     launch_omp_restricted_gram(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up, Kp,
                                Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T, s);
@@ -812,7 +673,7 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
         cudaFuncSetAttribute(omp_restricted_coop_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       omp_restricted_coop_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(
           Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega,
-          alpha, ldo, k_eff, stats, gram, T);
+          alpha, ldo, k_eff, stats, gram, T, a_pstride, inv_pstride);
     });
     return;
   }
@@ -828,7 +689,7 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
       cudaFuncSetAttribute(omp_restricted_staged_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     omp_restricted_staged_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(
         Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, capS, omega_up, ldo_up, keff_up, Kp, Kuni, Kb,
-        omega, alpha, ldo, k_eff, stats, gram, T);
+        omega, alpha, ldo, k_eff, stats, gram, T, a_pstride, inv_pstride);
   });
 }
 

@@ -95,6 +95,94 @@ __global__ void effective_dict_kernel(GeomDev g, int kind, int shots, const uint
   A[e] = v;
 }
 
+// Per-patch effective dictionaries for per-pixel coded exposure (plane grid
+// 1 x F frames): A_p[i][m] = (Phi_p U_l d_i)[m] = sum_t code[t][oy+py][ox+px]
+// d_i[level index of (t, py, px)], one thread per (patch, atom, pixel).
+__global__ void effective_dict_pp_kernel(GeomDev g, const uint8_t *__restrict__ codes, int l,
+                                         const float *__restrict__ D, int T, int N, float *__restrict__ A,
+                                         int64_t B) {
+  const int M = g.P * g.P;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * T * M) return;
+  const int m = (int)(e % M);
+  const int64_t bi = e / M;
+  const int i = (int)(bi % T);
+  const int64_t b = bi / T;
+  const int iy = (int)(b / g.nx), ix = (int)(b - (int64_t)iy * g.nx);
+  const int oy = origin(iy, g.stride, g.H, g.P), ox = origin(ix, g.stride, g.W, g.P);
+  const int py = m / g.P, px = m - py * g.P;
+  const float *d = D + (int64_t)i * N;
+  const int F = g.Lx;
+  float v = 0.f;
+  for (int t = 0; t < F; ++t)
+    if (codes[((int64_t)t * g.H + oy + py) * g.W + ox + px]) v += d[level_index(g, l, 0, t, py, px)];
+  A[e] = v;
+}
+
+// Row norms of a [rows][M] matrix: out = ||row|| (first pass), running max
+// of the norms in *mx (float bits, non-negative, compared as integers).
+__global__ void row_norms_kernel(const float *__restrict__ A, int64_t rows, int M, float *__restrict__ out,
+                                 unsigned int *mx) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= rows) return;
+  float s = 0.f;
+  for (int m = lane; m < M; m += 32) { const float a = A[r * M + m]; s = fmaf(a, a, s); }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    const float nrm = sqrtf(s);
+    out[r] = nrm;
+    atomicMax(mx, __float_as_uint(nrm));
+  }
+}
+
+// Second pass: 1/norm, or -1 for rows with norm <= 1e-12 of the largest.
+__global__ void inv_norms_kernel(float *__restrict__ v, int64_t rows, const unsigned int *mx) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  const float thr = 1e-12f * __uint_as_float(*mx);
+  const float nrm = v[r];
+  v[r] = (nrm > thr && nrm > 0.f) ? 1.f / nrm : -1.f;
+}
+
+// BF16 copy of dictionary rows (not normalised), zero padded to Np.
+__global__ void bf16_rows_kernel(const float *__restrict__ D, int T, int N, int Np, __nv_bfloat16 *__restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)T * Np) return;
+  const int i = (int)(e / Np), n = (int)(e - (int64_t)i * Np);
+  out[e] = __float2bfloat16_rn(n < N ? D[(int64_t)i * N + n] : 0.f);
+}
+
+// Lifted residual of per-pixel coded exposure at level l: z = U_l^T Phi_p^T r,
+// z[(t_l, py_l, px_l)] = sum over the factor block of code[t][oy+py][ox+px]
+// r[py][px].  One thread per (patch, level element); FP32 and a BF16 copy
+// padded to Np.
+__global__ void lift_kernel(GeomDev g, const uint8_t *__restrict__ codes, int l, const float *__restrict__ R,
+                            int64_t B, float *__restrict__ Z, __nv_bfloat16 *__restrict__ Zbf, int Np) {
+  const int fx = g.f[l][1], sy = g.f[l][2], sx = g.f[l][3];
+  const int Lxl = g.Lx / fx, Pyl = g.P / sy, Pxl = g.P / sx;
+  const int Nl = Lxl * Pyl * Pxl;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * Np) return;
+  const int64_t b = e / Np;
+  const int n = (int)(e - b * Np);
+  float acc = 0.f;
+  if (n < Nl) {
+    const int pxl = n % Pxl, pyl = (n / Pxl) % Pyl, tl = n / (Pxl * Pyl);
+    const int iy = (int)(b / g.nx), ix = (int)(b - (int64_t)iy * g.nx);
+    const int oy = origin(iy, g.stride, g.H, g.P), ox = origin(ix, g.stride, g.W, g.P);
+    const float *r = R + b * (g.P * g.P);
+    for (int dt = 0; dt < fx; ++dt)
+      for (int dy = 0; dy < sy; ++dy)
+        for (int dx = 0; dx < sx; ++dx) {
+          const int t = tl * fx + dt, py = pyl * sy + dy, px = pxl * sx + dx;
+          if (codes[((int64_t)t * g.H + oy + py) * g.W + ox + px]) acc += r[py * g.P + px];
+        }
+    if (Z) Z[b * Nl + n] = acc;
+  }
+  if (Zbf) Zbf[e] = __float2bfloat16_rn(acc);
+}
+
 // Column norms of A; 1/||a_i|| (or -1 for columns with ||a_i|| <= 1e-12 max_j ||a_j||,
 // which are never chosen) and the BF16 copy of a_i/||a_i|| padded to Mp.
 // One CTA, run once per dictionary.
@@ -245,6 +333,31 @@ void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *
     synth_kernel<<<blocks(B, ppc), 256, sm, s>>>(D0, N0, support, coef, k_eff, Kmax, B, ppc, Xh);
   }
   gather_kernel<<<blocks(n, 256), 256, 0, s>>>(g, Xh, N0, cover_y, cover_x, img);
+}
+
+void launch_effective_dict_pp(const GeomDev &g, const uint8_t *codes, int level, const float *D, int T, int N,
+                              float *A, int64_t B, cudaStream_t s) {
+  const int64_t n = B * T * (int64_t)(g.P * g.P);
+  if (n == 0) return;
+  effective_dict_pp_kernel<<<blocks(n, 256), 256, 0, s>>>(g, codes, level, D, T, N, A, B);
+}
+
+void launch_inv_row_norms(const float *A, int64_t rows, int M, float *inv, unsigned int *scratch, cudaStream_t s) {
+  if (rows == 0) return;
+  cudaMemsetAsync(scratch, 0, sizeof(unsigned int), s);
+  row_norms_kernel<<<blocks(rows * 32, 256), 256, 0, s>>>(A, rows, M, inv, scratch);
+  inv_norms_kernel<<<blocks(rows, 256), 256, 0, s>>>(inv, rows, scratch);
+}
+
+void launch_bf16_rows(const float *D, int T, int N, int Np, __nv_bfloat16 *out, cudaStream_t s) {
+  if ((int64_t)T * Np == 0) return;
+  bf16_rows_kernel<<<blocks((int64_t)T * Np, 256), 256, 0, s>>>(D, T, N, Np, out);
+}
+
+void launch_lift(const GeomDev &g, const uint8_t *codes, int level, const float *R, int64_t B, float *Z,
+                 __nv_bfloat16 *Zbf, int Np, cudaStream_t s) {
+  if (B * Np == 0) return;
+  lift_kernel<<<blocks(B * Np, 256), 256, 0, s>>>(g, codes, level, R, B, Z, Zbf, Np);
 }
 
 }  // namespace csp

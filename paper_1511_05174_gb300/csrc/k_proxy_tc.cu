@@ -168,7 +168,8 @@ __host__ __device__ inline TcLayout tc_layout(int Mp, int nt) {
 __global__ void __launch_bounds__(TC_THREADS, 2)
 proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmA, int Mp, int T,
                 int nt, int idx_bits, int64_t row0, int64_t n, const int32_t *__restrict__ ids,
-                const uint8_t *__restrict__ flags, int32_t *__restrict__ cand, unsigned long long *err) {
+                const uint8_t *__restrict__ flags, int32_t *__restrict__ cand, unsigned long long *err,
+                const float *__restrict__ pinv) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const TcLayout lay = tc_layout(Mp, nt);
@@ -266,6 +267,9 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
     const uint32_t imask = (1u << idx_bits) - 1u;
     const uint32_t smask = 0x7fffffffu & ~imask;
     const int hcols = nt / 2;
+    // per-patch norms (per-patch Phi): scores scaled by 1/||Phi_p U d_i|| of this thread's patch
+    const int64_t wi_row = tile0 + row;
+    const float *prow = (pinv && wi_row < n) ? pinv + (ids ? (int64_t)ids[wi_row] : wi_row) * (int64_t)T : nullptr;
     uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
     bool ok = true;
     for (int j = 0; j < n_at && ok; ++j) {
@@ -282,6 +286,13 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int base = j * nt + half * hcols + c0;
         const uint32_t c = imask - (uint32_t)base;
+        if (pinv) {
+#pragma unroll
+          for (int i = 0; i < 64; ++i) {
+            const float pv = (prow && base + i < T) ? __ldg(prow + base + i) : 0.f;
+            v[i] = __float_as_uint(fabsf(__uint_as_float(v[i])) * pv);
+          }
+        }
         if (base + 64 <= T) {
 #pragma unroll
           for (int i = 0; i < 64; i += 2) {
@@ -374,7 +385,7 @@ bool proxy_bf16_supported(int M, int T) {
 
 bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, const __nv_bfloat16 *Abf, int T,
                        int64_t row0, const int32_t *ids, int64_t n, const uint8_t *flags, int32_t *cand,
-                       unsigned long long *err, cudaStream_t s) {
+                       unsigned long long *err, const float *pinv, cudaStream_t s) {
   if (n == 0) return true;
   const int nt = tile_atoms(Mp);
   CUtensorMap mR, mA;
@@ -392,7 +403,7 @@ bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, con
   const unsigned grid = (unsigned)((n + TC_M - 1) / TC_M);
   int idx_bits = 1;
   while ((1 << idx_bits) < T) ++idx_bits;  // atom index field of the packed keys
-  proxy_tc_kernel<<<grid, TC_THREADS, sm, s>>>(mR, mA, Mp, T, nt, idx_bits, row0, n, ids, flags, cand, err);
+  proxy_tc_kernel<<<grid, TC_THREADS, sm, s>>>(mR, mA, Mp, T, nt, idx_bits, row0, n, ids, flags, cand, err, pinv);
   return true;
 }
 
