@@ -123,6 +123,32 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
+# multi-rank bookkeeping (one replica per GPU; no collective on the data path)
+# ----------------------------------------------------------------------------
+def dist_env():
+    """(world, rank, local_rank) from the torchrun environment (1, 0, 0 without it)."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """The slowest rank's time: an all-reduce MAX (any backend; CPU tensors with gloo)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, patches_per_rank: int, steps: int, total_seconds: float) -> float:
+    """Whole-job patches/s: every rank processes its own image per step (weak scaling),
+    timed by the slowest rank."""
+    return world * patches_per_rank * steps / total_seconds
+
+
+# ----------------------------------------------------------------------------
 # roofline bookkeeping
 # ----------------------------------------------------------------------------
 def kernel_source_sha():
@@ -183,9 +209,9 @@ def run_reference(args):
     import oracle
     import synthetic
 
-    rank = int(os.environ.get("RANK", "0"))
+    world, rank, _ = dist_env()
     if rank != 0:
-        return
+        return  # the CPU oracle runs once, on rank 0
     w = synthetic.make_workload(args.workload, links=args.links)
     Y = oracle.extract_patches(w)
     cores = oracle.num_threads()
@@ -256,9 +282,7 @@ def main():
     import synthetic
     from paper_1511_05174_gb300.context import Context
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
@@ -318,18 +342,15 @@ def main():
         prof = ctx.profile_read(reset=True)
         ctx.profile(False)
         st = ctx.stats()
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item()), prof, st, clocks
+        return max_over_ranks(ms, world, dev), prof, st, clocks
 
     cs_ms, cs_prof, cs_stats, clocks = timed("cross_scale", ClockSampler(local))
     cs_img = img.double().cpu().numpy()
     pl_ms, pl_prof, pl_stats, _ = timed("plain")
     pl_img = img.double().cpu().numpy()
 
-    value = world * B * args.steps / (cs_ms / 1e3)
-    plain_value = world * B * args.steps / (pl_ms / 1e3)
+    value = job_throughput(world, B, args.steps, cs_ms / 1e3)
+    plain_value = job_throughput(world, B, args.steps, pl_ms / 1e3)
 
     # dominant kernel of the headline (cross-scale) step
     launches = {k: v for k, v in cs_prof.items()}
@@ -376,10 +397,7 @@ def main():
             t0 = time.perf_counter()
             ctx.reconstruct_host(meas_h, img_h, "cross_scale", args.precision, K=K, Kmax=Kmax)
             tot += time.perf_counter() - t0
-        t = torch.tensor([tot], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * B * args.steps / float(t.item()), "unit": UNIT,
+        e2e = {"value": job_throughput(world, B, args.steps, max_over_ranks(tot, world, dev)), "unit": UNIT,
                "h2d_bytes_per_step": int(w.meas.nbytes), "d2h_bytes_per_step": int(img.numel() * 4)}
 
     def psnr(est):
