@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-jobs", type=int, default=96)
     return ap.parse_args()
 
 
@@ -270,6 +272,62 @@ def cpu_baseline(w, seconds=12.0):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+def serving_bench(w, args, K, Kmax, device, jobs):
+    """The serving engine on this GPU: saturation throughput of a burst of
+    whole-image jobs, then latency under Poisson arrivals at 70% of it.
+    Per GPU; host buffers; every job copies its measurements in and its image
+    out.  Returns a dict for the JSON line."""
+    from paper_1511_05174_gb300.server import Server
+
+    g = w.geometry
+    srv = Server(device, n_streams=2)
+    try:
+        mid = srv.add_workload_model(w, "cross_scale", args.precision, K=K, Kmax=Kmax)
+        outs = [np.empty((g.planes, g.H, g.W), np.float32) for _ in range(8)]
+        meas = np.ascontiguousarray(w.meas, dtype=np.float32)
+
+        def run(n, gaps=None):
+            ids = []
+            t0 = time.perf_counter()
+            t_next = t0
+            for i in range(n):
+                if gaps is not None:
+                    t_next += gaps[i]
+                    while time.perf_counter() < t_next:
+                        pass
+                ids.append(srv.submit(mid, meas, g.H, g.W, out=outs[i % len(outs)]))
+            for j in ids:
+                st = srv.wait(j, 120)
+                if st != 0:
+                    raise RuntimeError(f"serving job failed with status {st}")
+            infos = [srv.info(j) for j in ids]
+            for j in ids:
+                srv.release(j)
+            return infos
+
+        run(8)  # warm-up: workspaces, pools, staging
+        burst = run(jobs)
+        span = max(i["t_done"] for i in burst) - min(i["t_submit"] for i in burst)
+        sat_jobs = jobs / span
+        rate = 0.7 * sat_jobs
+        gaps = np.random.default_rng(0).exponential(1.0 / rate, size=jobs)
+        pois = run(jobs, gaps)
+        lat = np.array([i["t_done"] - i["t_submit"] for i in pois]) * 1e3
+        wait = np.array([i["t_admit"] - i["t_submit"] for i in pois]) * 1e3
+        return {
+            "model": f"{w.name} {g.H}x{g.W} cross_scale {args.precision}", "n_streams": 2, "per_gpu": True,
+            "saturation": {"jobs": jobs, "jobs_per_s": sat_jobs, "value": sat_jobs * w.n_patches, "unit": UNIT,
+                           "mean_batch_jobs": float(np.mean([i["batch_jobs"] for i in burst]))},
+            "poisson": {"rate_jobs_per_s": rate, "jobs": jobs, "latency_ms_p50": float(np.percentile(lat, 50)),
+                        "latency_ms_p99": float(np.percentile(lat, 99)),
+                        "queue_ms_p50": float(np.percentile(wait, 50)),
+                        "mean_batch_jobs": float(np.mean([i["batch_jobs"] for i in pois]))},
+            "h2d_bytes_per_job": int(meas.nbytes), "d2h_bytes_per_job": int(outs[0].nbytes),
+        }
+    finally:
+        srv.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -405,6 +463,10 @@ def main():
         peak = float(w.truth.max() - w.truth.min())
         return 10 * np.log10(peak * peak / mse)
 
+    serving = None
+    if not args.no_serving:
+        serving = serving_bench(w, args, K, Kmax, local, args.serving_jobs)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(w)
@@ -428,6 +490,7 @@ def main():
             "gpu_launches": gpu_launches,
             "clocks": clocks,
             "e2e": e2e,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

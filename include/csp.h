@@ -211,6 +211,79 @@ csp_status csp_aggregate_noalloc(csp_ctx *ctx, const int32_t *support, const flo
 csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *params,
                                 const float *meas_host, float *image_host, void *stream);
 
+/* ---- Serving: continuous batching of reconstruction jobs -----------------
+ * Not part of the paper's method: a request loop around csp_solve.  A server
+ * owns one CUDA device, a device-memory budget for in-flight jobs and a
+ * scheduler thread.  Models (dictionaries, links, patch geometry without the
+ * image extent, sensing kind and solve parameters) stay resident.  Jobs
+ * (an image of a model: extent, measurements, per-job codes) are queued by
+ * csp_submit and admitted in arrival order while their device memory fits the
+ * budget and a batch slot is free; admitted jobs of the same model are
+ * coalesced into one batched solve (one set of launches over all their
+ * patches, up to max_batch_patches), and batches run concurrently on
+ * n_streams CUDA streams, so jobs that arrive while others are on the GPU
+ * start as soon as memory and a slot free up.  Every patch is solved
+ * independently, so a job's result does not depend on the jobs it shares a
+ * batch with.  Supported sensing kinds: IDENTITY, BAYER_RGGB, CODED_EXPOSURE.
+ * Admission counts each job's batch memory and its share of the solver
+ * workspace; each stream keeps its workspace at the largest batch it ran. */
+typedef struct csp_server csp_server;
+
+typedef struct csp_server_config {
+    int device;                 /* CUDA device                                             */
+    size_t mem_budget_bytes;    /* device memory for in-flight jobs (0: 16 GiB)             */
+    int64_t max_batch_patches;  /* patches coalesced into one solve at most (0: 262144)    */
+    int n_streams;              /* batches in flight at once, 1..8 (0: 2)                  */
+} csp_server_config;
+
+typedef struct csp_model_desc {
+    csp_geometry geom;          /* H and W are ignored (they are per job)                  */
+    int sense_kind;             /* CSP_SENSE_IDENTITY, _BAYER_RGGB or _CODED_EXPOSURE      */
+    const float *D[CSP_MAX_LEVELS];        /* HOST, atom-major [T_l][N_l] (copied)        */
+    int T[CSP_MAX_LEVELS];
+    const int32_t *parent[CSP_MAX_LEVELS]; /* HOST links of levels 0 .. n_levels-2        */
+    csp_solve_params params;    /* mode, precision, K, Kmax (K_patch must be NULL)         */
+} csp_model_desc;
+
+typedef struct csp_job_desc {
+    int model_id;
+    int H, W;                   /* image extent                                           */
+    const float *meas_host;     /* measurement image (layout as csp_extract_patches); read
+                                   when the job starts, keep it alive until the job is done */
+    const uint8_t *codes_host;  /* CODED_EXPOSURE: [planes][H][W] 0/1 codes (copied at submit) */
+    float *image_host;          /* output image [planes][H][W], written before "done"      */
+} csp_job_desc;
+
+typedef struct csp_job_info {
+    int64_t patches;
+    double t_submit, t_admit, t_done;  /* seconds on the server's steady clock             */
+    int batch_jobs;             /* jobs coalesced into this job's batch                    */
+    int64_t batch_patches;
+    csp_status status;          /* CSP_OK, CSP_ERR_NOT_READY while queued/running, or error */
+} csp_job_info;
+
+csp_status csp_server_create(csp_server **out, const csp_server_config *cfg);
+/* Waits for every job, stops the scheduler, frees everything. NULL is ignored. */
+void csp_server_destroy(csp_server *srv);
+const char *csp_server_last_error(const csp_server *srv);
+/* Register a model; prepares its effective dictionaries.  model_id out. */
+csp_status csp_server_add_model(csp_server *srv, const csp_model_desc *desc, int *model_id);
+/* paused != 0: admit no further job until resumed (batches already in flight
+ * complete; queued jobs stay queued).  Used to drain the server or to queue a
+ * burst of jobs that should start together. */
+csp_status csp_server_pause(csp_server *srv, int paused);
+/* Queue a job.  CSP_ERR_OOM if its device memory exceeds the whole budget
+ * (it could never be admitted), CSP_ERR_INVALID on bad arguments. */
+csp_status csp_submit(csp_server *srv, const csp_job_desc *job, uint64_t *job_id);
+/* Non-blocking: *done = 1 once the image is in image_host (or the job failed). */
+csp_status csp_poll(csp_server *srv, uint64_t job_id, int *done);
+/* Blocks until done or timeout_us (< 0: no limit); CSP_ERR_TIMEOUT if not done. */
+csp_status csp_wait(csp_server *srv, uint64_t job_id, int64_t timeout_us);
+csp_status csp_job_info_get(csp_server *srv, uint64_t job_id, csp_job_info *out);
+/* Forget a finished job (its info is no longer available).  CSP_ERR_NOT_READY
+ * while it is queued or running. */
+csp_status csp_job_release(csp_server *srv, uint64_t job_id);
+
 /* ---- Autotuning (not part of the paper's method) --------------------------
  * Kernel variants that compute the same result with different work
  * decompositions (here: the restricted finer-scale solver, either re-reading

@@ -34,7 +34,10 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcsp.so")
 EXPORTS = ("csp_create", "csp_destroy", "csp_last_error", "csp_set_geometry", "csp_set_sensing",
            "csp_load_dictionary", "csp_load_scale_links", "csp_problem_size", "csp_extract_patches",
            "csp_solve", "csp_solve_stats_get", "csp_aggregate", "csp_aggregate_noalloc", "csp_reconstruct_host",
-           "csp_autotune", "csp_set_kernel_variant", "csp_profile_enable", "csp_profile_read")
+           "csp_autotune", "csp_set_kernel_variant", "csp_profile_enable", "csp_profile_read",
+           "csp_server_create", "csp_server_destroy", "csp_server_last_error", "csp_server_add_model",
+           "csp_submit", "csp_poll", "csp_wait", "csp_job_info_get", "csp_job_release",
+           "csp_server_pause")
 
 
 class csp_geometry(ctypes.Structure):
@@ -64,6 +67,28 @@ class csp_kernel_time(ctypes.Structure):
 
 class csp_tune_result(ctypes.Structure):
     _fields_ = [("restricted_variant", ctypes.c_int), ("ms", ctypes.c_double * 3)]
+
+
+class csp_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int), ("mem_budget_bytes", ctypes.c_size_t),
+                ("max_batch_patches", ctypes.c_int64), ("n_streams", ctypes.c_int)]
+
+
+class csp_model_desc(ctypes.Structure):
+    _fields_ = [("geom", csp_geometry), ("sense_kind", ctypes.c_int), ("D", ctypes.c_void_p * MAX_LEVELS),
+                ("T", ctypes.c_int * MAX_LEVELS), ("parent", ctypes.c_void_p * MAX_LEVELS),
+                ("params", csp_solve_params)]
+
+
+class csp_job_desc(ctypes.Structure):
+    _fields_ = [("model_id", ctypes.c_int), ("H", ctypes.c_int), ("W", ctypes.c_int),
+                ("meas_host", ctypes.c_void_p), ("codes_host", ctypes.c_void_p), ("image_host", ctypes.c_void_p)]
+
+
+class csp_job_info(ctypes.Structure):
+    _fields_ = [("patches", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("batch_jobs", ctypes.c_int), ("batch_patches", ctypes.c_int64),
+                ("status", ctypes.c_int)]
 
 
 class CspError(RuntimeError):
@@ -105,6 +130,16 @@ def load_library(path: str = LIB_PATH):
         "csp_set_kernel_variant": (i, [vp, i]),
         "csp_profile_enable": (i, [vp, i]),
         "csp_profile_read": (i, [vp, ctypes.POINTER(csp_kernel_time), i, ctypes.POINTER(ctypes.c_int), i]),
+        "csp_server_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(csp_server_config)]),
+        "csp_server_destroy": (None, [vp]),
+        "csp_server_last_error": (ctypes.c_char_p, [vp]),
+        "csp_server_add_model": (i, [vp, ctypes.POINTER(csp_model_desc), ctypes.POINTER(ctypes.c_int)]),
+        "csp_submit": (i, [vp, ctypes.POINTER(csp_job_desc), ctypes.POINTER(ctypes.c_uint64)]),
+        "csp_poll": (i, [vp, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int)]),
+        "csp_wait": (i, [vp, ctypes.c_uint64, ctypes.c_int64]),
+        "csp_job_info_get": (i, [vp, ctypes.c_uint64, ctypes.POINTER(csp_job_info)]),
+        "csp_job_release": (i, [vp, ctypes.c_uint64]),
+        "csp_server_pause": (i, [vp, i]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -215,3 +250,66 @@ def csp_autotune(ctx, params: csp_solve_params, Y_ptr: int, B: int, sup_ptr: int
 
 def csp_set_kernel_variant(ctx, restricted_variant: int) -> None:
     check(load_library().csp_set_kernel_variant(ctx, int(restricted_variant)), ctx)
+
+
+# Serving (continuous batching of reconstruction jobs).
+
+def check_server(status: int, srv) -> None:
+    if status != CSP_OK:
+        raise CspError(status, load_library().csp_server_last_error(srv).decode(errors="replace"))
+
+
+def csp_server_create(device: int = 0, mem_budget_bytes: int = 0, max_batch_patches: int = 0, n_streams: int = 0):
+    lib = load_library()
+    srv = ctypes.c_void_p()
+    cfg = csp_server_config(device, mem_budget_bytes, max_batch_patches, n_streams)
+    st = lib.csp_server_create(ctypes.byref(srv), ctypes.byref(cfg))
+    if st != CSP_OK:
+        raise CspError(st, lib.csp_last_error(None).decode(errors="replace"))
+    return srv
+
+
+def csp_server_destroy(srv) -> None:
+    load_library().csp_server_destroy(srv)
+
+
+def csp_server_last_error(srv) -> str:
+    return load_library().csp_server_last_error(srv).decode(errors="replace")
+
+
+def csp_server_add_model(srv, desc: csp_model_desc) -> int:
+    mid = ctypes.c_int()
+    check_server(load_library().csp_server_add_model(srv, ctypes.byref(desc), ctypes.byref(mid)), srv)
+    return mid.value
+
+
+def csp_submit(srv, job: csp_job_desc) -> int:
+    jid = ctypes.c_uint64()
+    check_server(load_library().csp_submit(srv, ctypes.byref(job), ctypes.byref(jid)), srv)
+    return jid.value
+
+
+def csp_poll(srv, job_id: int) -> bool:
+    done = ctypes.c_int()
+    check_server(load_library().csp_poll(srv, job_id, ctypes.byref(done)), srv)
+    return bool(done.value)
+
+
+def csp_wait(srv, job_id: int, timeout_us: int = -1) -> int:
+    """Status of the job (raises CspError only for an unknown job; a timeout
+    returns CSP_ERR_TIMEOUT)."""
+    return int(load_library().csp_wait(srv, job_id, timeout_us))
+
+
+def csp_job_info_get(srv, job_id: int) -> csp_job_info:
+    info = csp_job_info()
+    check_server(load_library().csp_job_info_get(srv, job_id, ctypes.byref(info)), srv)
+    return info
+
+
+def csp_job_release(srv, job_id: int) -> None:
+    check_server(load_library().csp_job_release(srv, job_id), srv)
+
+
+def csp_server_pause(srv, paused: bool) -> None:
+    check_server(load_library().csp_server_pause(srv, int(bool(paused))), srv)

@@ -83,10 +83,11 @@ csp_status dev_alloc_t(csp_ctx *ctx, T **p, size_t count) {
   return s;
 }
 
-// Grow-only workspace slot.
-csp_status ws_get(csp_ctx *ctx, int slot, size_t bytes, void **out) {
-  if ((int)ctx->ws.size() <= slot) ctx->ws.resize(slot + 1);
-  Buf &b = ctx->ws[slot];
+// Grow-only workspace slot (allocations count against ctx's budget).
+csp_status ws_get(csp_ctx *ctx, Workspace &W, int slot, size_t bytes, void **out) {
+  if (W.owner) ctx = W.owner;
+  if ((int)W.ws.size() <= slot) W.ws.resize(slot + 1);
+  Buf &b = W.ws[slot];
   if (b.bytes < bytes) {
     dev_free(ctx, b.p);
     b.p = nullptr;
@@ -98,9 +99,9 @@ csp_status ws_get(csp_ctx *ctx, int slot, size_t bytes, void **out) {
   return CSP_OK;
 }
 template <typename T>
-csp_status ws_get_t(csp_ctx *ctx, int slot, size_t count, T **out) {
+csp_status ws_get_t(csp_ctx *ctx, Workspace &W, int slot, size_t count, T **out) {
   void *v = nullptr;
-  csp_status s = ws_get(ctx, slot, count * sizeof(T) + 16, &v);
+  csp_status s = ws_get(ctx, W, slot, count * sizeof(T) + 16, &v);
   *out = static_cast<T *>(v);
   return s;
 }
@@ -189,6 +190,16 @@ void free_level_derived(csp_ctx *ctx, LevelData &L) {
   L.n_phase = 0;
 }
 
+// Per-patch data of the context's own grid (coded exposure).
+void free_own_patches(csp_ctx *ctx) {
+  for (int l = 0; l < CSP_MAX_LEVELS; ++l) {
+    dev_free(ctx, ctx->pp_A[l]);
+    dev_free(ctx, ctx->pp_inv[l]);
+    ctx->pp_A[l] = ctx->pp_inv[l] = nullptr;
+  }
+  ctx->pp_ready = false;
+}
+
 void free_links(csp_ctx *ctx, LevelData &L) {
   dev_free(ctx, L.child_off);
   dev_free(ctx, L.child_idx);
@@ -214,16 +225,7 @@ csp_status prepare(csp_ctx *ctx, cudaStream_t s) {
       L.Np = (L.N + 63) / 64 * 64;
       if (!omp_dims_supported(L.M))
         return fail(ctx, CSP_ERR_UNSUPPORTED, "problem dimension must be a multiple of 4, <= 256");
-      const size_t rows = (size_t)ctx->B * L.T;
-      CSP_TRY(dev_alloc_t(ctx, &L.A[0], rows * L.M));
-      CSP_TRY(dev_alloc_t(ctx, &L.inv_norm[0], rows));
       CSP_TRY(dev_alloc_t(ctx, &L.Dbf, (size_t)L.T * L.Np));
-      unsigned int *mx = nullptr;
-      CSP_TRY(ws_get_t(ctx, WS_SCRATCH, 4, &mx));
-      run(ctx, KK_PREP, s, (int64_t)rows, [&] {
-        launch_effective_dict_pp(ctx->gd, ctx->codes, l, L.D, L.T, L.N, L.A[0], ctx->B, s);
-      });
-      run(ctx, KK_PREP, s, (int64_t)rows, [&] { launch_inv_row_norms(L.A[0], (int64_t)rows, L.M, L.inv_norm[0], mx, s); });
       run(ctx, KK_PREP, s, L.T, [&] { launch_bf16_rows(L.D, L.T, L.N, L.Np, L.Dbf, s); });
       L.per_patch = true;
       L.n_phase = 1;
@@ -269,7 +271,235 @@ csp_status prepare(csp_ctx *ctx, cudaStream_t s) {
 
 bool valid_ptr_or_empty(const void *p, int64_t n) { return p != nullptr || n == 0; }
 
+// Shape limits of a solve on this context (after prepare).
+csp_status check_solve_shape(csp_ctx *ctx, const csp_solve_params *prm) {
+  const int nl = prm->mode == CSP_MODE_PLAIN ? 1 : ctx->geom.n_levels;
+  const int top = nl - 1;
+  const LevelData &LT = ctx->lv[top];
+  if (prm->precision == CSP_PREC_BF16 && !proxy_bf16_supported(LT.per_patch ? LT.N : LT.M, LT.T))
+    return fail(ctx, CSP_ERR_UNSUPPORTED, "BF16 tensor-core proxy not available for this shape (dimension <= 256)");
+  for (int l = 1; l < nl; ++l) {
+    const int Kl = prm->K_patch[l] ? prm->Kmax : prm->K[l];
+    const int cap = ctx->lv[l - 1].max_children * Kl;
+    if (cap > 1024) return fail(ctx, CSP_ERR_UNSUPPORTED, "candidate capacity above 1024 (max children x K)");
+  }
+  return CSP_OK;
+}
+
+// Per-patch effective dictionaries and norms for B patches with code blocks
+// pc, into A_pp/inv_pp (allocated by the caller, [B][T_l][M] and [B][T_l]).
+csp_status build_patch_dicts(csp_ctx *ctx, const uint8_t *pc, int64_t B, float *const *A_pp, float *const *inv_pp,
+                             unsigned int *scratch, cudaStream_t s) {
+  for (int l = 0; l < ctx->geom.n_levels; ++l) {
+    LevelData &L = ctx->lv[l];
+    const int64_t rows = B * L.T;
+    run(ctx, KK_PREP, s, rows, [&] { launch_effective_dict_pp(ctx->gd, pc, l, L.D, L.T, L.N, A_pp[l], B, s); });
+    run(ctx, KK_PREP, s, rows, [&] { launch_inv_row_norms(A_pp[l], rows, L.M, inv_pp[l], scratch, s); });
+  }
+  CSP_CUDA(ctx, cudaGetLastError());
+  return CSP_OK;
+}
+
+// Coded exposure: this context's own patch grid gets its per-patch data once.
+csp_status prepare_own_patches(csp_ctx *ctx, cudaStream_t s) {
+  if (ctx->sense_kind != CSP_SENSE_CODED_EXPOSURE || ctx->pp_ready) return CSP_OK;
+  for (int l = 0; l < ctx->geom.n_levels; ++l) {
+    const LevelData &L = ctx->lv[l];
+    CSP_TRY(dev_alloc_t(ctx, &ctx->pp_A[l], (size_t)ctx->B * L.T * L.M));
+    CSP_TRY(dev_alloc_t(ctx, &ctx->pp_inv[l], (size_t)ctx->B * L.T));
+  }
+  unsigned int *scratch = nullptr;
+  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_SCRATCH, 4, &scratch));
+  CSP_TRY(build_patch_dicts(ctx, ctx->pcodes, ctx->B, ctx->pp_A, ctx->pp_inv, scratch, s));
+  ctx->pp_ready = true;
+  return CSP_OK;
+}
+
+// Solve the patch set `ps` with the context's dictionaries (prepared), using
+// workspace W.  Arguments validated by the caller.
+csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_solve_params *prm, const float *Y,
+                      int32_t *support_out, float *coef_out, int8_t *k_eff_out, cudaStream_t s) {
+  const int64_t B = ps.B;
+  const int nl = prm->mode == CSP_MODE_PLAIN ? 1 : ctx->geom.n_levels;
+  int Kb[CSP_MAX_LEVELS];
+  for (int l = 0; l < nl; ++l) Kb[l] = prm->K_patch[l] ? prm->Kmax : prm->K[l];
+  const bool bf16 = prm->precision == CSP_PREC_BF16;
+  const int top = nl - 1;
+  CSP_CUDA(ctx, cudaMemsetAsync(W.stats_dev, 0, 8 * sizeof(int64_t), s));
+  if (B == 0) return CSP_OK;
+
+  // phase groups
+  const bool phased = ps.phase_ids != nullptr;
+  const int nph = phased ? 4 : 1;
+  auto ids_of = [&](int ph) -> const int32_t * { return phased ? ps.phase_ids + ps.phase_start[ph] : nullptr; };
+  auto n_of = [&](int ph) -> int64_t { return phased ? ps.phase_start[ph + 1] - ps.phase_start[ph] : B; };
+
+  // per-level measurement vectors (Phi = I: y_l = W_l y)
+  const float *Yl[CSP_MAX_LEVELS];
+  for (int l = 0; l < nl; ++l) {
+    if (l > 0 && ctx->sense_kind == CSP_SENSE_IDENTITY) {
+      float *buf = nullptr;
+      CSP_TRY(ws_get_t(ctx, W, WS_LV_Y + l, (size_t)B * ctx->lv[l].M, &buf));
+      run(ctx, KK_DOWNSAMPLE, s, B, [&] { launch_downsample(ctx->gd, l, Y, buf, B, s); });
+      Yl[l] = buf;
+    } else {
+      Yl[l] = Y;
+    }
+  }
+
+  // per-level outputs (level 0 writes straight into the caller's buffers)
+  int32_t *lv_om[CSP_MAX_LEVELS];
+  float *lv_al[CSP_MAX_LEVELS];
+  int8_t *lv_ke[CSP_MAX_LEVELS];
+  int ldo[CSP_MAX_LEVELS];
+  for (int l = 0; l < nl; ++l) {
+    if (l == 0) {
+      lv_om[0] = support_out; lv_al[0] = coef_out; lv_ke[0] = k_eff_out; ldo[0] = prm->Kmax;
+    } else {
+      ldo[l] = Kb[l];
+      CSP_TRY(ws_get_t(ctx, W, WS_LV_OMEGA + l, (size_t)B * Kb[l], &lv_om[l]));
+      CSP_TRY(ws_get_t(ctx, W, WS_LV_ALPHA + l, (size_t)B * Kb[l], &lv_al[l]));
+      CSP_TRY(ws_get_t(ctx, W, WS_LV_KEFF + l, (size_t)B, &lv_ke[l]));
+    }
+  }
+
+  // full-dictionary OMP at the top level (the only level in plain mode)
+  {
+    const LevelData &L = ctx->lv[top];
+    const bool pp = L.per_patch;
+    OmpState st{};
+    CSP_TRY(ws_get_t(ctx, W, WS_R, (size_t)B * L.M, &st.R));
+    st.Rbf = nullptr;
+    if (bf16 && !pp) CSP_TRY(ws_get_t(ctx, W, WS_RBF, (size_t)B * L.Mp, &st.Rbf));
+    // per-patch Phi: the proxy runs on the lifted residual z = U^T Phi_p^T r against D
+    float *Zl = nullptr;
+    __nv_bfloat16 *Zbf = nullptr;
+    if (pp) {
+      if (!bf16) CSP_TRY(ws_get_t(ctx, W, WS_LIFT, (size_t)B * L.N, &Zl));
+      else CSP_TRY(ws_get_t(ctx, W, WS_LIFTBF, (size_t)B * L.Np, &Zbf));
+    }
+    st.Kb = Kb[top];
+    st.ldo = ldo[top];
+    CSP_TRY(ws_get_t(ctx, W, WS_L, (size_t)B * (Kb[top] * (Kb[top] + 1) / 2), &st.Lpk));
+    CSP_TRY(ws_get_t(ctx, W, WS_Z, (size_t)B * Kb[top], &st.z));
+    CSP_TRY(ws_get_t(ctx, W, WS_FLAGS, (size_t)B, &st.flags));
+    CSP_TRY(ws_get_t(ctx, W, WS_CAND, (size_t)B * kTopP, &st.cand));
+    st.omega = lv_om[top];
+    st.alpha = lv_al[top];
+    st.k_eff = lv_ke[top];
+    const int64_t a_ps = pp ? (int64_t)L.T * L.M : 0, inv_ps = pp ? (int64_t)L.T : 0;
+    run(ctx, KK_INIT, s, B, [&] {
+      launch_omp_init(Yl[top], B, L.M, (bf16 && !pp) ? L.Mp : 0, phased ? ps.phase_ids : nullptr, st, s);
+    });
+    bool maps_ok = true;
+    for (int it = 0; it < Kb[top]; ++it) {
+      if (pp)
+        run(ctx, KK_LIFT, s, B, [&] { launch_lift(ctx->gd, ps.pcodes, top, st.R, B, Zl, Zbf, bf16 ? L.Np : L.N, s); });
+      for (int ph = 0; ph < nph; ++ph) {
+        if (bf16)
+          run(ctx, KK_PROXY_BF16, s, n_of(ph), [&] {
+            maps_ok &= pp ? launch_proxy_bf16(Zbf, B, L.Np, L.Dbf, L.T, 0, ids_of(ph), n_of(ph), st.flags, st.cand,
+                                              (unsigned long long *)(W.stats_dev + 4), ps.inv_pp[top], s)
+                          : launch_proxy_bf16(st.Rbf, B, L.Mp, L.Abf[ph], L.T, phased ? ps.phase_start[ph] : 0,
+                                              ids_of(ph), n_of(ph), st.flags, st.cand,
+                                              (unsigned long long *)(W.stats_dev + 4), nullptr, s);
+          });
+        else
+          run(ctx, KK_PROXY_FP32, s, n_of(ph), [&] {
+            if (pp)
+              launch_proxy_fp32(Zl, L.N, L.D, nullptr, L.T, ids_of(ph), n_of(ph), st.omega, st.ldo, st.k_eff, st.flags,
+                                st.cand, ps.inv_pp[top], s);
+            else
+              launch_proxy_fp32(st.R, L.M, L.A[ph], L.inv_norm[ph], L.T, ids_of(ph), n_of(ph), st.omega, st.ldo,
+                                st.k_eff, st.flags, st.cand, nullptr, s);
+          });
+      }
+      for (int ph = 0; ph < nph; ++ph)
+        run(ctx, KK_UPDATE, s, n_of(ph), [&] {
+          launch_omp_update_wave(Yl[top], L.M, pp ? ps.A_pp[top] : L.A[ph], pp ? ps.inv_pp[top] : L.inv_norm[ph],
+                                 ids_of(ph), n_of(ph),
+                                 phased ? ps.phase_start[ph] : 0, bf16 ? kTopP : 1, prm->K_patch[top], prm->K[top],
+                                 st, W.stats_dev, L.G[ph], L.T, a_ps, inv_ps, s);
+        });
+      if (!maps_ok) return fail(ctx, CSP_ERR_CUDA, "tensor map encoding for the BF16 proxy failed");
+    }
+  }
+  // restricted OMP down the scales (Algorithm 2 fine steps)
+  for (int l = top - 1; l >= 0; --l) {
+    const LevelData &L = ctx->lv[l];
+    const int cap = std::max(1, L.max_children * Kb[l + 1]);
+    for (int ph = 0; ph < nph; ++ph)
+      run(ctx, KK_RESTRICTED, s, n_of(ph), [&] {
+        launch_omp_restricted(ctx->restricted_variant, Yl[l], L.M, L.per_patch ? ps.A_pp[l] : L.A[ph],
+                              L.per_patch ? ps.inv_pp[l] : L.inv_norm[ph], ids_of(ph), n_of(ph),
+                              L.child_off, L.child_idx, cap, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1], prm->K_patch[l],
+                              prm->K[l], Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], W.stats_dev, L.G[ph], L.T,
+                              L.per_patch ? (int64_t)L.T * L.M : 0, L.per_patch ? (int64_t)L.T : 0, s);
+      });
+  }
+  CSP_CUDA(ctx, cudaGetLastError());
+  return CSP_OK;
+}
+
 }  // namespace
+
+namespace csp {
+
+csp_status prepare_model(csp_ctx *ctx, cudaStream_t s) { return prepare(ctx, s); }
+
+csp_status check_solve_params(csp_ctx *ctx, const csp_solve_params *prm) {
+  if (!prm) return fail(ctx, CSP_ERR_INVALID, "params is NULL");
+  if (prm->mode != CSP_MODE_PLAIN && prm->mode != CSP_MODE_CROSS_SCALE) return fail(ctx, CSP_ERR_INVALID, "unknown mode");
+  if (prm->precision != CSP_PREC_FP32 && prm->precision != CSP_PREC_BF16)
+    return fail(ctx, CSP_ERR_INVALID, "unknown precision");
+  if (prm->Kmax < 1 || prm->Kmax > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "Kmax must be in 1..CSP_MAX_K");
+  const int nl = prm->mode == CSP_MODE_PLAIN ? 1 : ctx->geom.n_levels;
+  for (int l = 0; l < nl; ++l)
+    if (!prm->K_patch[l] && (prm->K[l] < 1 || prm->K[l] > CSP_MAX_K))
+      return fail(ctx, CSP_ERR_INVALID, "K[l] must be in 1..CSP_MAX_K");
+  if (!prm->K_patch[0] && prm->K[0] > prm->Kmax) return fail(ctx, CSP_ERR_INVALID, "K[0] exceeds Kmax");
+  for (int l = 0; l + 1 < nl; ++l)
+    if (!ctx->lv[l].links) return fail(ctx, CSP_ERR_NOT_READY, "scale links of level " + std::to_string(l) + " not loaded");
+  return check_solve_shape(ctx, prm);
+}
+
+csp_status solve_patchset(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_solve_params *prm,
+                          const float *Y, int32_t *support_out, float *coef_out, int8_t *k_eff_out, cudaStream_t s) {
+  return solve_core(ctx, ps, W, prm, Y, support_out, coef_out, k_eff_out, s);
+}
+
+csp_status build_patch_dicts_for(csp_ctx *ctx, const uint8_t *pc, int64_t B, float *const *A_pp,
+                                 float *const *inv_pp, unsigned int *scratch, cudaStream_t s) {
+  return build_patch_dicts(ctx, pc, B, A_pp, inv_pp, scratch, s);
+}
+
+int64_t patch_count_1d(int E, int P, int stride) { return count_1d(E, P, stride); }
+
+void cover_ranges(int E, int P, int stride, int n, std::vector<int32_t> &c) {
+  c.assign(2 * (size_t)E, 0);
+  for (int y = 0; y < E; ++y) {
+    int lo = -1, hi = -2;
+    for (int i = 0; i < n; ++i) {
+      const int o = std::min(i * stride, E - P);
+      if (o <= y && y < o + P) { if (lo < 0) lo = i; hi = i; }
+    }
+    c[2 * y] = lo < 0 ? 0 : lo;
+    c[2 * y + 1] = hi;
+  }
+}
+
+GeomDev make_geom_dev(const csp_geometry &g, int H, int W) {
+  GeomDev d{};
+  d.H = H; d.W = W; d.Ly = g.plane_rows; d.Lx = g.plane_cols; d.P = g.P; d.stride = g.stride;
+  d.nx = (int)count_1d(W, g.P, g.stride);
+  d.ny = (int)count_1d(H, g.P, g.stride);
+  d.n_levels = g.n_levels;
+  for (int l = 0; l < CSP_MAX_LEVELS; ++l)
+    for (int c = 0; c < 4; ++c) d.f[l][c] = l < g.n_levels ? g.factors[l][c] : 1;
+  return d;
+}
+
+}  // namespace csp
 
 extern "C" {
 
@@ -289,12 +519,12 @@ csp_status csp_create(csp_ctx **out, int device, size_t mem_budget_bytes) {
   ctx->budget = mem_budget_bytes;
   DeviceGuard g(device);
   if (!g.ok) { delete ctx; return fail(nullptr, CSP_ERR_CUDA, "cudaSetDevice failed"); }
-  if (dev_alloc_t(ctx, &ctx->stats_dev, 8) != CSP_OK) {
+  if (dev_alloc_t(ctx, &ctx->wsp.stats_dev, 8) != CSP_OK) {
     std::string m = ctx->err;
     delete ctx;
     return fail(nullptr, CSP_ERR_OOM, m);
   }
-  cudaMemset(ctx->stats_dev, 0, 8 * sizeof(int64_t));
+  cudaMemset(ctx->wsp.stats_dev, 0, 8 * sizeof(int64_t));
   *out = ctx;
   return CSP_OK;
 }
@@ -361,6 +591,8 @@ csp_status csp_set_geometry(csp_ctx *ctx, const csp_geometry *geom) {
   }
   dev_free(ctx, ctx->codes);
   ctx->codes = nullptr;
+  dev_free(ctx, ctx->pcodes);
+  ctx->pcodes = nullptr;
   dev_free(ctx, ctx->phase_ids);
   ctx->phase_ids = nullptr;
   ctx->has_sensing = false;
@@ -373,6 +605,7 @@ csp_status csp_set_geometry(csp_ctx *ctx, const csp_geometry *geom) {
   ctx->B = nx * ny;
   ctx->has_geom = true;
   ctx->prepared = false;
+  free_own_patches(ctx);
   return CSP_OK;
 }
 
@@ -431,11 +664,20 @@ csp_status csp_set_sensing(csp_ctx *ctx, const csp_sensing *sensing) {
     CSP_TRY(dev_alloc_t(ctx, &ctx->phase_ids, ids.size()));
     CSP_CUDA(ctx, cudaMemcpy(ctx->phase_ids, ids.data(), ids.size() * 4, cudaMemcpyHostToDevice));
   }
+  dev_free(ctx, ctx->pcodes);
+  ctx->pcodes = nullptr;
+  if (sensing->kind == CSP_SENSE_CODED_EXPOSURE) {
+    // per-patch code blocks of this grid: the per-patch operators read only these
+    CSP_TRY(dev_alloc_t(ctx, &ctx->pcodes, (size_t)ctx->B * planes * PP));
+    launch_patch_codes(ctx->gd, ctx->codes, ctx->B, ctx->pcodes, nullptr);
+    CSP_CUDA(ctx, cudaDeviceSynchronize());
+  }
   ctx->sense_kind = sensing->kind;
   ctx->shots = sensing->kind == CSP_SENSE_CODED_APERTURE ? sensing->shots : 0;
   ctx->M = M;
   ctx->has_sensing = true;
   ctx->prepared = false;
+  free_own_patches(ctx);
   return CSP_OK;
 }
 
@@ -460,6 +702,7 @@ csp_status csp_load_dictionary(csp_ctx *ctx, int level, const float *D, int N_l,
   L.N = N_l;
   L.T = T_l;
   ctx->prepared = false;
+  free_own_patches(ctx);
   return CSP_OK;
 }
 
@@ -518,6 +761,7 @@ csp_status csp_extract_patches(csp_ctx *ctx, const float *meas, float *Y_out, in
   return CSP_OK;
 }
 
+
 csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, int64_t B,
                      int32_t *support_out, float *coef_out, int8_t *k_eff_out, void *stream) {
   if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
@@ -532,14 +776,9 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
   if (prm->Kmax < 1 || prm->Kmax > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "Kmax must be in 1..CSP_MAX_K");
   if (!ctx->has_geom || !ctx->has_sensing) return fail(ctx, CSP_ERR_NOT_READY, "geometry and sensing must be set");
   const int nl = prm->mode == CSP_MODE_PLAIN ? 1 : ctx->geom.n_levels;
-  int Kb[CSP_MAX_LEVELS];
-  for (int l = 0; l < nl; ++l) {
-    if (prm->K_patch[l]) Kb[l] = prm->Kmax;
-    else {
-      if (prm->K[l] < 1 || prm->K[l] > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "K[l] must be in 1..CSP_MAX_K");
-      Kb[l] = prm->K[l];
-    }
-  }
+  for (int l = 0; l < nl; ++l)
+    if (!prm->K_patch[l] && (prm->K[l] < 1 || prm->K[l] > CSP_MAX_K))
+      return fail(ctx, CSP_ERR_INVALID, "K[l] must be in 1..CSP_MAX_K");
   if (!prm->K_patch[0] && prm->K[0] > prm->Kmax) return fail(ctx, CSP_ERR_INVALID, "K[0] exceeds Kmax");
   for (int l = 0; l + 1 < nl; ++l)
     if (!ctx->lv[l].links) return fail(ctx, CSP_ERR_NOT_READY, "scale links of level " + std::to_string(l) + " not loaded");
@@ -548,129 +787,19 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard dg(ctx->device);
   CSP_TRY(prepare(ctx, s));
-  const bool bf16 = prm->precision == CSP_PREC_BF16;
-  const int top = nl - 1;
-  const LevelData &LT = ctx->lv[top];
-  if (bf16 && !proxy_bf16_supported(LT.per_patch ? LT.N : LT.M, LT.T))
-    return fail(ctx, CSP_ERR_UNSUPPORTED, "BF16 tensor-core proxy not available for this shape (dimension <= 256)");
-  for (int l = 1; l < nl; ++l) {
-    const int cap = ctx->lv[l - 1].max_children * Kb[l];
-    if (cap > 1024) return fail(ctx, CSP_ERR_UNSUPPORTED, "candidate capacity above 1024 (max children x K)");
+  CSP_TRY(check_solve_shape(ctx, prm));
+  CSP_TRY(prepare_own_patches(ctx, s));
+  PatchSet ps;
+  ps.B = B;
+  if (ctx->sense_kind == CSP_SENSE_BAYER_RGGB) {
+    ps.phase_ids = ctx->phase_ids;
+    for (int p = 0; p <= kMaxPhases; ++p) ps.phase_start[p] = ctx->phase_start[p];
   }
-  CSP_CUDA(ctx, cudaMemsetAsync(ctx->stats_dev, 0, 8 * sizeof(int64_t), s));
+  ps.pcodes = ctx->pcodes;
+  for (int l = 0; l < CSP_MAX_LEVELS; ++l) { ps.A_pp[l] = ctx->pp_A[l]; ps.inv_pp[l] = ctx->pp_inv[l]; }
   ctx->last_B = B;
   ctx->last_stream = s;
-  if (B == 0) return CSP_OK;
-
-  // phase groups
-  const bool phased = ctx->sense_kind == CSP_SENSE_BAYER_RGGB;
-  const int nph = phased ? 4 : 1;
-  auto ids_of = [&](int ph) -> const int32_t * { return phased ? ctx->phase_ids + ctx->phase_start[ph] : nullptr; };
-  auto n_of = [&](int ph) -> int64_t { return phased ? ctx->phase_start[ph + 1] - ctx->phase_start[ph] : B; };
-
-  // per-level measurement vectors (Phi = I: y_l = W_l y)
-  const float *Yl[CSP_MAX_LEVELS];
-  for (int l = 0; l < nl; ++l) {
-    if (l > 0 && ctx->sense_kind == CSP_SENSE_IDENTITY) {
-      float *buf = nullptr;
-      CSP_TRY(ws_get_t(ctx, WS_LV_Y + l, (size_t)B * ctx->lv[l].M, &buf));
-      run(ctx, KK_DOWNSAMPLE, s, B, [&] { launch_downsample(ctx->gd, l, Y, buf, B, s); });
-      Yl[l] = buf;
-    } else {
-      Yl[l] = Y;
-    }
-  }
-
-  // per-level outputs (level 0 writes straight into the caller's buffers)
-  int32_t *lv_om[CSP_MAX_LEVELS];
-  float *lv_al[CSP_MAX_LEVELS];
-  int8_t *lv_ke[CSP_MAX_LEVELS];
-  int ldo[CSP_MAX_LEVELS];
-  for (int l = 0; l < nl; ++l) {
-    if (l == 0) {
-      lv_om[0] = support_out; lv_al[0] = coef_out; lv_ke[0] = k_eff_out; ldo[0] = prm->Kmax;
-    } else {
-      ldo[l] = Kb[l];
-      CSP_TRY(ws_get_t(ctx, WS_LV_OMEGA + l, (size_t)B * Kb[l], &lv_om[l]));
-      CSP_TRY(ws_get_t(ctx, WS_LV_ALPHA + l, (size_t)B * Kb[l], &lv_al[l]));
-      CSP_TRY(ws_get_t(ctx, WS_LV_KEFF + l, (size_t)B, &lv_ke[l]));
-    }
-  }
-
-  // full-dictionary OMP at the top level (the only level in plain mode)
-  {
-    const LevelData &L = ctx->lv[top];
-    const bool pp = L.per_patch;
-    OmpState st{};
-    CSP_TRY(ws_get_t(ctx, WS_R, (size_t)B * L.M, &st.R));
-    st.Rbf = nullptr;
-    if (bf16 && !pp) CSP_TRY(ws_get_t(ctx, WS_RBF, (size_t)B * L.Mp, &st.Rbf));
-    // per-patch Phi: the proxy runs on the lifted residual z = U^T Phi_p^T r against D
-    float *Zl = nullptr;
-    __nv_bfloat16 *Zbf = nullptr;
-    if (pp) {
-      if (!bf16) CSP_TRY(ws_get_t(ctx, WS_LIFT, (size_t)B * L.N, &Zl));
-      else CSP_TRY(ws_get_t(ctx, WS_LIFTBF, (size_t)B * L.Np, &Zbf));
-    }
-    st.Kb = Kb[top];
-    st.ldo = ldo[top];
-    CSP_TRY(ws_get_t(ctx, WS_L, (size_t)B * (Kb[top] * (Kb[top] + 1) / 2), &st.Lpk));
-    CSP_TRY(ws_get_t(ctx, WS_Z, (size_t)B * Kb[top], &st.z));
-    CSP_TRY(ws_get_t(ctx, WS_FLAGS, (size_t)B, &st.flags));
-    CSP_TRY(ws_get_t(ctx, WS_CAND, (size_t)B * kTopP, &st.cand));
-    st.omega = lv_om[top];
-    st.alpha = lv_al[top];
-    st.k_eff = lv_ke[top];
-    const int64_t a_ps = pp ? (int64_t)L.T * L.M : 0, inv_ps = pp ? (int64_t)L.T : 0;
-    run(ctx, KK_INIT, s, B, [&] {
-      launch_omp_init(Yl[top], B, L.M, (bf16 && !pp) ? L.Mp : 0, phased ? ctx->phase_ids : nullptr, st, s);
-    });
-    bool maps_ok = true;
-    for (int it = 0; it < Kb[top]; ++it) {
-      if (pp)
-        run(ctx, KK_LIFT, s, B, [&] { launch_lift(ctx->gd, ctx->codes, top, st.R, B, Zl, Zbf, bf16 ? L.Np : L.N, s); });
-      for (int ph = 0; ph < nph; ++ph) {
-        if (bf16)
-          run(ctx, KK_PROXY_BF16, s, n_of(ph), [&] {
-            maps_ok &= pp ? launch_proxy_bf16(Zbf, B, L.Np, L.Dbf, L.T, 0, ids_of(ph), n_of(ph), st.flags, st.cand,
-                                              (unsigned long long *)(ctx->stats_dev + 4), L.inv_norm[0], s)
-                          : launch_proxy_bf16(st.Rbf, B, L.Mp, L.Abf[ph], L.T, phased ? ctx->phase_start[ph] : 0,
-                                              ids_of(ph), n_of(ph), st.flags, st.cand,
-                                              (unsigned long long *)(ctx->stats_dev + 4), nullptr, s);
-          });
-        else
-          run(ctx, KK_PROXY_FP32, s, n_of(ph), [&] {
-            if (pp)
-              launch_proxy_fp32(Zl, L.N, L.D, nullptr, L.T, ids_of(ph), n_of(ph), st.omega, st.ldo, st.k_eff, st.flags,
-                                st.cand, L.inv_norm[0], s);
-            else
-              launch_proxy_fp32(st.R, L.M, L.A[ph], L.inv_norm[ph], L.T, ids_of(ph), n_of(ph), st.omega, st.ldo,
-                                st.k_eff, st.flags, st.cand, nullptr, s);
-          });
-      }
-      for (int ph = 0; ph < nph; ++ph)
-        run(ctx, KK_UPDATE, s, n_of(ph), [&] {
-          launch_omp_update_wave(Yl[top], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph),
-                                 phased ? ctx->phase_start[ph] : 0, bf16 ? kTopP : 1, prm->K_patch[top], prm->K[top],
-                                 st, ctx->stats_dev, L.G[ph], L.T, a_ps, inv_ps, s);
-        });
-      if (!maps_ok) return fail(ctx, CSP_ERR_CUDA, "tensor map encoding for the BF16 proxy failed");
-    }
-  }
-  // restricted OMP down the scales (Algorithm 2 fine steps)
-  for (int l = top - 1; l >= 0; --l) {
-    const LevelData &L = ctx->lv[l];
-    const int cap = std::max(1, L.max_children * Kb[l + 1]);
-    for (int ph = 0; ph < nph; ++ph)
-      run(ctx, KK_RESTRICTED, s, n_of(ph), [&] {
-        launch_omp_restricted(ctx->restricted_variant, Yl[l], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph),
-                              L.child_off, L.child_idx, cap, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1], prm->K_patch[l],
-                              prm->K[l], Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], ctx->stats_dev, L.G[ph], L.T,
-                              L.per_patch ? (int64_t)L.T * L.M : 0, L.per_patch ? (int64_t)L.T : 0, s);
-      });
-  }
-  CSP_CUDA(ctx, cudaGetLastError());
-  return CSP_OK;
+  return solve_core(ctx, ps, ctx->wsp, prm, Y, support_out, coef_out, k_eff_out, s);
 }
 
 csp_status csp_solve_stats_get(csp_ctx *ctx, csp_solve_stats *out) {
@@ -678,7 +807,7 @@ csp_status csp_solve_stats_get(csp_ctx *ctx, csp_solve_stats *out) {
   DeviceGuard dg(ctx->device);
   int64_t h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   CSP_CUDA(ctx, cudaStreamSynchronize(ctx->last_stream));
-  CSP_CUDA(ctx, cudaMemcpy(h, ctx->stats_dev, sizeof(h), cudaMemcpyDeviceToHost));
+  CSP_CUDA(ctx, cudaMemcpy(h, ctx->wsp.stats_dev, sizeof(h), cudaMemcpyDeviceToHost));
   out->patches = ctx->last_B;
   out->fp64_fallbacks = h[0];
   out->early_stops = h[1];
@@ -700,7 +829,7 @@ csp_status csp_aggregate(csp_ctx *ctx, const int32_t *support, const float *coef
   if (!support || !coef || !k_eff || !image_out) return fail(ctx, CSP_ERR_INVALID, "NULL buffer");
   DeviceGuard dg(ctx->device);
   float *Xh = nullptr;
-  CSP_TRY(ws_get_t(ctx, WS_XH, (size_t)B * ctx->lv[0].N, &Xh));
+  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_XH, (size_t)B * ctx->lv[0].N, &Xh));
   run(ctx, KK_AGGREGATE, (cudaStream_t)stream, B, [&] {
     launch_aggregate(ctx->gd, ctx->lv[0].D, ctx->lv[0].N, support, coef, k_eff, Kmax, ctx->cover_y, ctx->cover_x,
                      Xh, image_out, (cudaStream_t)stream);

@@ -60,7 +60,26 @@ struct Buf {
 
 }  // namespace csp
 
+struct csp_ctx;
 namespace csp {
+// The patches of one solve.  A context solves its own patch grid; the serving
+// engine solves batches that concatenate the patches of several images.
+struct PatchSet {
+  int64_t B = 0;
+  const int32_t *phase_ids = nullptr;       // Bayer: patch ids sorted by mosaic phase (null: one group)
+  int64_t phase_start[kMaxPhases + 1] = {};
+  const uint8_t *pcodes = nullptr;          // coded exposure: [B][F*P*P] per-patch code blocks
+  float *A_pp[CSP_MAX_LEVELS] = {};         // coded exposure: per-patch effective dictionaries [B][T_l][M]
+  float *inv_pp[CSP_MAX_LEVELS] = {};       // ... and their inverse column norms [B][T_l]
+};
+
+// Grow-only workspace slots and solve counters of one solver instance.
+struct Workspace {
+  std::vector<Buf> ws;
+  int64_t *stats_dev = nullptr;  // 8 counters (see csp_solve_stats)
+  csp_ctx *owner = nullptr;      // context whose allocator owns the slots (null: the solving context)
+};
+
 enum KernelKind {
   KK_EXTRACT, KK_DOWNSAMPLE, KK_PREP, KK_INIT, KK_PROXY_FP32, KK_PROXY_BF16, KK_UPDATE, KK_RESTRICTED,
   KK_AGGREGATE, KK_LIFT, KK_COUNT
@@ -90,9 +109,13 @@ struct csp_ctx {
   int64_t phase_start[csp::kMaxPhases + 1] = {};
   // Aggregation: covering patch-index range of every row / column.
   int32_t *cover_y = nullptr, *cover_x = nullptr;
-  // Workspace (grown on demand).
-  std::vector<csp::Buf> ws;
-  int64_t *stats_dev = nullptr;          // 4 counters (see csp_solve_stats)
+  // Workspace (grown on demand) and counters of csp_solve.
+  csp::Workspace wsp;
+  // Coded exposure: per-patch code blocks and per-patch effective dictionaries of this grid.
+  uint8_t *pcodes = nullptr;
+  float *pp_A[CSP_MAX_LEVELS] = {};
+  float *pp_inv[CSP_MAX_LEVELS] = {};
+  bool pp_ready = false;
   int64_t last_B = 0;
   cudaStream_t last_stream = nullptr;
   // Host-path buffers of csp_reconstruct_host.
@@ -123,11 +146,12 @@ void launch_norms(const float *A, int T, int M, int Mp, float *inv_norm, __nv_bf
 // Per-patch sensing (per-pixel coded exposure): A_p = Phi_p U_l D for every patch
 // ([B][T][P*P]), inverse row norms over `rows` rows (scratch: one device uint),
 // BF16 rows of D (unnormalised, padded to Np), lifted residual z = U_l^T Phi_p^T r.
-void launch_effective_dict_pp(const GeomDev &g, const uint8_t *codes, int level, const float *D, int T, int N,
+void launch_patch_codes(const GeomDev &g, const uint8_t *codes, int64_t B, uint8_t *pc, cudaStream_t s);
+void launch_effective_dict_pp(const GeomDev &g, const uint8_t *pc, int level, const float *D, int T, int N,
                               float *A, int64_t B, cudaStream_t s);
 void launch_inv_row_norms(const float *A, int64_t rows, int M, float *inv, unsigned int *scratch, cudaStream_t s);
 void launch_bf16_rows(const float *D, int T, int N, int Np, __nv_bfloat16 *out, cudaStream_t s);
-void launch_lift(const GeomDev &g, const uint8_t *codes, int level, const float *R, int64_t B, float *Z,
+void launch_lift(const GeomDev &g, const uint8_t *pc, int level, const float *R, int64_t B, float *Z,
                  __nv_bfloat16 *Zbf, int Np, cudaStream_t s);
 // Synthesis into Xh ([B][N0] scratch) then per-pixel overlap-add average (2 launches).
 void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *support,
@@ -185,5 +209,17 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
                            const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, cudaStream_t s);
+
+// ---- solve entry points shared by csp_solve and the serving engine (csp_api.cu) ----
+csp_status prepare_model(csp_ctx *ctx, cudaStream_t s);                       // effective dictionaries etc.
+csp_status check_solve_params(csp_ctx *ctx, const csp_solve_params *prm);   // argument and shape checks
+csp_status solve_patchset(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_solve_params *prm,
+                          const float *Y, int32_t *support_out, float *coef_out, int8_t *k_eff_out, cudaStream_t s);
+csp_status build_patch_dicts_for(csp_ctx *ctx, const uint8_t *pc, int64_t B, float *const *A_pp, float *const *inv_pp,
+                                 unsigned int *scratch, cudaStream_t s);
+// Patch origins helper (host): covering-patch ranges of every row/column for aggregation.
+void cover_ranges(int E, int P, int stride, int n, std::vector<int32_t> &out);
+int64_t patch_count_1d(int E, int P, int stride);
+GeomDev make_geom_dev(const csp_geometry &g, int H, int W);
 
 }  // namespace csp

@@ -95,27 +95,42 @@ __global__ void effective_dict_kernel(GeomDev g, int kind, int shots, const uint
   A[e] = v;
 }
 
+// Per-patch code blocks of per-pixel coded exposure: pc[b][(t * P + py) * P + px]
+// = code[t][oy + py][ox + px] for the patch at (oy, ox) (plane grid 1 x F).
+__global__ void patch_codes_kernel(GeomDev g, const uint8_t *__restrict__ codes, int64_t B,
+                                   uint8_t *__restrict__ pc) {
+  const int F = g.Lx, PP = g.P * g.P;
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= B * F * PP) return;
+  const int64_t b = e / (F * PP);
+  const int r = (int)(e - b * F * PP);
+  const int t = r / PP, m = r - t * PP, py = m / g.P, px = m - py * g.P;
+  const int iy = (int)(b / g.nx), ix = (int)(b - (int64_t)iy * g.nx);
+  const int oy = origin(iy, g.stride, g.H, g.P), ox = origin(ix, g.stride, g.W, g.P);
+  pc[e] = codes[((int64_t)t * g.H + oy + py) * g.W + ox + px];
+}
+
 // Per-patch effective dictionaries for per-pixel coded exposure (plane grid
-// 1 x F frames): A_p[i][m] = (Phi_p U_l d_i)[m] = sum_t code[t][oy+py][ox+px]
-// d_i[level index of (t, py, px)], one thread per (patch, atom, pixel).
-__global__ void effective_dict_pp_kernel(GeomDev g, const uint8_t *__restrict__ codes, int l,
+// 1 x F frames): A_p[i][m] = (Phi_p U_l d_i)[m] = sum_t pc_p[t][py][px]
+// d_i[level index of (t, py, px)], one thread per (patch, atom, pixel).  Only
+// the patch-local code blocks are read, so patches of different images can
+// share one launch.
+__global__ void effective_dict_pp_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l,
                                          const float *__restrict__ D, int T, int N, float *__restrict__ A,
                                          int64_t B) {
-  const int M = g.P * g.P;
+  const int M = g.P * g.P, F = g.Lx;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= B * T * M) return;
   const int m = (int)(e % M);
   const int64_t bi = e / M;
   const int i = (int)(bi % T);
   const int64_t b = bi / T;
-  const int iy = (int)(b / g.nx), ix = (int)(b - (int64_t)iy * g.nx);
-  const int oy = origin(iy, g.stride, g.H, g.P), ox = origin(ix, g.stride, g.W, g.P);
   const int py = m / g.P, px = m - py * g.P;
   const float *d = D + (int64_t)i * N;
-  const int F = g.Lx;
+  const uint8_t *c = pc + b * (int64_t)F * M;
   float v = 0.f;
   for (int t = 0; t < F; ++t)
-    if (codes[((int64_t)t * g.H + oy + py) * g.W + ox + px]) v += d[level_index(g, l, 0, t, py, px)];
+    if (c[t * M + m]) v += d[level_index(g, l, 0, t, py, px)];
   A[e] = v;
 }
 
@@ -154,14 +169,14 @@ __global__ void bf16_rows_kernel(const float *__restrict__ D, int T, int N, int 
 }
 
 // Lifted residual of per-pixel coded exposure at level l: z = U_l^T Phi_p^T r,
-// z[(t_l, py_l, px_l)] = sum over the factor block of code[t][oy+py][ox+px]
-// r[py][px].  One thread per (patch, level element); FP32 and a BF16 copy
-// padded to Np.
-__global__ void lift_kernel(GeomDev g, const uint8_t *__restrict__ codes, int l, const float *__restrict__ R,
+// z[(t_l, py_l, px_l)] = sum over the factor block of pc_p[t][py][px] r[py][px].
+// One thread per (patch, level element); FP32 (optional) and a BF16 copy
+// (optional) padded to Np.
+__global__ void lift_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const float *__restrict__ R,
                             int64_t B, float *__restrict__ Z, __nv_bfloat16 *__restrict__ Zbf, int Np) {
   const int fx = g.f[l][1], sy = g.f[l][2], sx = g.f[l][3];
   const int Lxl = g.Lx / fx, Pyl = g.P / sy, Pxl = g.P / sx;
-  const int Nl = Lxl * Pyl * Pxl;
+  const int Nl = Lxl * Pyl * Pxl, PP = g.P * g.P;
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= B * Np) return;
   const int64_t b = e / Np;
@@ -169,14 +184,13 @@ __global__ void lift_kernel(GeomDev g, const uint8_t *__restrict__ codes, int l,
   float acc = 0.f;
   if (n < Nl) {
     const int pxl = n % Pxl, pyl = (n / Pxl) % Pyl, tl = n / (Pxl * Pyl);
-    const int iy = (int)(b / g.nx), ix = (int)(b - (int64_t)iy * g.nx);
-    const int oy = origin(iy, g.stride, g.H, g.P), ox = origin(ix, g.stride, g.W, g.P);
-    const float *r = R + b * (g.P * g.P);
+    const float *r = R + b * PP;
+    const uint8_t *c = pc + b * (int64_t)g.Lx * PP;
     for (int dt = 0; dt < fx; ++dt)
       for (int dy = 0; dy < sy; ++dy)
         for (int dx = 0; dx < sx; ++dx) {
           const int t = tl * fx + dt, py = pyl * sy + dy, px = pxl * sx + dx;
-          if (codes[((int64_t)t * g.H + oy + py) * g.W + ox + px]) acc += r[py * g.P + px];
+          if (c[t * PP + py * g.P + px]) acc += r[py * g.P + px];
         }
     if (Z) Z[b * Nl + n] = acc;
   }
@@ -335,11 +349,17 @@ void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *
   gather_kernel<<<blocks(n, 256), 256, 0, s>>>(g, Xh, N0, cover_y, cover_x, img);
 }
 
-void launch_effective_dict_pp(const GeomDev &g, const uint8_t *codes, int level, const float *D, int T, int N,
+void launch_patch_codes(const GeomDev &g, const uint8_t *codes, int64_t B, uint8_t *pc, cudaStream_t s) {
+  const int64_t n = B * g.Lx * (int64_t)(g.P * g.P);
+  if (n == 0) return;
+  patch_codes_kernel<<<blocks(n, 256), 256, 0, s>>>(g, codes, B, pc);
+}
+
+void launch_effective_dict_pp(const GeomDev &g, const uint8_t *pc, int level, const float *D, int T, int N,
                               float *A, int64_t B, cudaStream_t s) {
   const int64_t n = B * T * (int64_t)(g.P * g.P);
   if (n == 0) return;
-  effective_dict_pp_kernel<<<blocks(n, 256), 256, 0, s>>>(g, codes, level, D, T, N, A, B);
+  effective_dict_pp_kernel<<<blocks(n, 256), 256, 0, s>>>(g, pc, level, D, T, N, A, B);
 }
 
 void launch_inv_row_norms(const float *A, int64_t rows, int M, float *inv, unsigned int *scratch, cudaStream_t s) {
@@ -354,10 +374,10 @@ void launch_bf16_rows(const float *D, int T, int N, int Np, __nv_bfloat16 *out, 
   bf16_rows_kernel<<<blocks((int64_t)T * Np, 256), 256, 0, s>>>(D, T, N, Np, out);
 }
 
-void launch_lift(const GeomDev &g, const uint8_t *codes, int level, const float *R, int64_t B, float *Z,
+void launch_lift(const GeomDev &g, const uint8_t *pc, int level, const float *R, int64_t B, float *Z,
                  __nv_bfloat16 *Zbf, int Np, cudaStream_t s) {
   if (B * Np == 0) return;
-  lift_kernel<<<blocks(B * Np, 256), 256, 0, s>>>(g, codes, level, R, B, Z, Zbf, Np);
+  lift_kernel<<<blocks(B * Np, 256), 256, 0, s>>>(g, pc, level, R, B, Z, Zbf, Np);
 }
 
 }  // namespace csp

@@ -265,10 +265,13 @@ def _presets(name: str, links: str):
 
 def make_workload(name: str, seed: int = 0, links: str = "paper", H: Optional[int] = None,
                   W: Optional[int] = None, T0: Optional[int] = None, sigma: Optional[float] = None,
-                  Q: int = 4, K_range: Tuple[int, int] = (8, 20), shots: int = 4) -> Workload:
+                  Q: int = 4, K_range: Tuple[int, int] = (8, 20), shots: int = 4,
+                  dict_seed: Optional[int] = None) -> Workload:
     """Build one seeded workload.  ``H``/``W``/``T0``/``sigma`` override the
     full-size preset (tests use small images); everything else keeps the
-    preset's structure."""
+    preset's structure.  ``dict_seed`` (default: ``seed``) seeds the
+    dictionaries and scale links alone, so that several images (jobs) can
+    share one model."""
     geo_kw, T0_def, K_lv, sigma_def, skind = _presets(name, links)
     if H is not None:
         geo_kw["H"] = H
@@ -279,6 +282,9 @@ def make_workload(name: str, seed: int = 0, links: str = "paper", H: Optional[in
     sigma = sigma_def if sigma is None else sigma
     ss = np.random.SeedSequence(seed).spawn(_N_STREAMS)
     rng = [np.random.default_rng(s) for s in ss]
+    if dict_seed is not None and dict_seed != seed:
+        dss = np.random.SeedSequence(dict_seed).spawn(_N_STREAMS)
+        rng[_S_DICT], rng[_S_SUBSET] = np.random.default_rng(dss[_S_DICT]), np.random.default_rng(dss[_S_SUBSET])
 
     dicts, parents = _build_dictionaries(g, T0, Q, links, rng[_S_DICT], rng[_S_SUBSET])
     L = g.n_levels
