@@ -25,6 +25,7 @@ SENSE = {"identity": 0, "bayer_rggb": 1, "coded_exposure": 2, "coded_aperture": 
 MODE = {"plain": 0, "cross_scale": 1}
 PREC = {"fp32": 0, "bf16": 1}
 
+TUNE_VARIANTS = 5  # CSP_TUNE_VARIANTS
 STATUS_NAMES = {0: "CSP_OK", -1: "CSP_ERR_INVALID", -2: "CSP_ERR_OOM", -3: "CSP_ERR_NOT_READY",
                 -4: "CSP_ERR_CUDA", -5: "CSP_ERR_TIMEOUT", -6: "CSP_ERR_UNSUPPORTED"}
 
@@ -66,7 +67,7 @@ class csp_kernel_time(ctypes.Structure):
 
 
 class csp_tune_result(ctypes.Structure):
-    _fields_ = [("restricted_variant", ctypes.c_int), ("ms", ctypes.c_double * 3)]
+    _fields_ = [("restricted_variant", ctypes.c_int), ("ms", ctypes.c_double * TUNE_VARIANTS)]
 
 
 class csp_server_config(ctypes.Structure):

@@ -277,7 +277,7 @@ csp_status check_solve_shape(csp_ctx *ctx, const csp_solve_params *prm) {
   const int top = nl - 1;
   const LevelData &LT = ctx->lv[top];
   if (prm->precision == CSP_PREC_BF16 && !proxy_bf16_supported(LT.per_patch ? LT.N : LT.M, LT.T))
-    return fail(ctx, CSP_ERR_UNSUPPORTED, "BF16 tensor-core proxy not available for this shape (dimension <= 256)");
+    return fail(ctx, CSP_ERR_UNSUPPORTED, "BF16 tensor-core proxy not available for this shape (proxy dimension <= 512, T <= 32768)");
   for (int l = 1; l < nl; ++l) {
     const int Kl = prm->K_patch[l] ? prm->Kmax : prm->K[l];
     const int cap = ctx->lv[l - 1].max_children * Kl;
@@ -828,12 +828,19 @@ csp_status csp_aggregate(csp_ctx *ctx, const int32_t *support, const float *coef
   if (Kmax < 1 || Kmax > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "Kmax must be in 1..CSP_MAX_K");
   if (!support || !coef || !k_eff || !image_out) return fail(ctx, CSP_ERR_INVALID, "NULL buffer");
   DeviceGuard dg(ctx->device);
-  float *Xh = nullptr;
-  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_XH, (size_t)B * ctx->lv[0].N, &Xh));
+  bool tiled = false;
   run(ctx, KK_AGGREGATE, (cudaStream_t)stream, B, [&] {
-    launch_aggregate(ctx->gd, ctx->lv[0].D, ctx->lv[0].N, support, coef, k_eff, Kmax, ctx->cover_y, ctx->cover_x,
-                     Xh, image_out, (cudaStream_t)stream);
+    tiled = launch_aggregate_tiled(ctx->gd, ctx->lv[0].D, ctx->lv[0].N, support, coef, k_eff, Kmax, ctx->cover_y,
+                                   ctx->cover_x, image_out, (cudaStream_t)stream);
   });
+  if (!tiled) {  // patch footprints too large for a shared-memory tile: synthesis scratch in HBM
+    float *Xh = nullptr;
+    CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_XH, (size_t)B * ctx->lv[0].N, &Xh));
+    run(ctx, KK_AGGREGATE, (cudaStream_t)stream, B, [&] {
+      launch_aggregate(ctx->gd, ctx->lv[0].D, ctx->lv[0].N, support, coef, k_eff, Kmax, ctx->cover_y, ctx->cover_x,
+                       Xh, image_out, (cudaStream_t)stream);
+    });
+  }
   CSP_CUDA(ctx, cudaGetLastError());
   return CSP_OK;
 }

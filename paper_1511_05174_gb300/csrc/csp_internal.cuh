@@ -154,6 +154,12 @@ void launch_bf16_rows(const float *D, int T, int N, int Np, __nv_bfloat16 *out, 
 void launch_lift(const GeomDev &g, const uint8_t *pc, int level, const float *R, int64_t B, float *Z,
                  __nv_bfloat16 *Zbf, int Np, cudaStream_t s);
 // Synthesis into Xh ([B][N0] scratch) then per-pixel overlap-add average (2 launches).
+// Fused synthesis + overlap-add without scratch; false when no tile shape fits
+// shared memory (then use launch_aggregate, which needs B * N0 floats of scratch).
+bool aggregate_tiled_fits(const GeomDev &g, int N0);
+bool launch_aggregate_tiled(const GeomDev &g, const float *D0, int N0, const int32_t *support, const float *coef,
+                            const int8_t *k_eff, int Kmax, const int32_t *cover_y, const int32_t *cover_x, float *img,
+                            cudaStream_t s);
 void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *support,
                       const float *coef, const int8_t *k_eff, int Kmax, const int32_t *cover_y,
                       const int32_t *cover_x, float *Xh, float *img, cudaStream_t s);
@@ -194,8 +200,9 @@ void launch_omp_update_wave(const float *Y, int M, const float *A, const float *
                             int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni, OmpState st,
                             int64_t *stats, const float *gram, int T, int64_t a_pstride, int64_t inv_pstride,
                             cudaStream_t s);
-void launch_omp_restricted_gram(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,
-                                int64_t n, const int32_t *child_off, const int32_t *child_idx, int cap,
+// width 0, 1, 2: 4, 8, 16 lanes per patch for M <= 64 (doubled per doubling of M, at most 32)
+void launch_omp_restricted_gram(int width, const float *Y, int M, const float *A, const float *inv_norm,
+                                const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx, int cap,
                                 const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int8_t *Kp,
                                 int Kuni, int Kb, int32_t *omega, float *alpha, int ldo, int8_t *k_eff,
                                 int64_t *stats, const float *gram, int T, cudaStream_t s);

@@ -98,7 +98,6 @@ __device__ __forceinline__ float dotc(const float4 (&a)[NCH], const float4 (&b)[
 // Per-group shared-memory block.
 // ---------------------------------------------------------------------------
 struct GrpSmem {
-  double *L64;   // [tri(Kb+1)] FP64 factor (fallback path)
   float *L;      // [tri(Kb)]   packed lower factor
   float *Linv;   // [Kb]        1 / L_jj
   float *z;      // [Kb]
@@ -112,13 +111,12 @@ struct GrpSmem {
 };
 
 __host__ __device__ __forceinline__ int grp_smem_bytes(int Kb, int cap) {
-  return up16(8 * tri(Kb + 1)) + up16(4 * tri(Kb)) + 2 * up16(4 * Kb) + 2 * up16(4 * (Kb + 1)) +
+  return up16(4 * tri(Kb)) + 2 * up16(4 * Kb) + 2 * up16(4 * (Kb + 1)) +
          up16(4 * Kb) + up16(8 * (Kb + 1)) + 2 * up16(4 * cap) + 16;
 }
 
 __device__ __forceinline__ GrpSmem carve(char *p, int Kb, int cap) {
   GrpSmem S;
-  S.L64 = reinterpret_cast<double *>(p); p += up16(8 * tri(Kb + 1));
   S.L = reinterpret_cast<float *>(p); p += up16(4 * tri(Kb));
   S.Linv = reinterpret_cast<float *>(p); p += up16(4 * Kb);
   S.z = reinterpret_cast<float *>(p); p += up16(4 * Kb);
@@ -135,9 +133,11 @@ __device__ __forceinline__ GrpSmem carve(char *p, int Kb, int cap) {
 // FP64 projection from scratch, run by one lane: Cholesky of A_S^T A_S for
 // S = chosen + q (rows S.colp[0..k-1] and aq) with entries accumulated in FP64
 // from the FP32 columns, then z = L^{-1} A_S^T y and alpha = L^{-T} z (into
-// S.W).  Returns false when q depends on the chosen columns.
-__device__ inline bool fp64_projection(int M, const float *__restrict__ y, const GrpSmem &S, int k, const float *aq) {
-  double *L64 = S.L64;
+// S.W).  Returns false when q depends on the chosen columns.  The factor is a
+// temporary of this (rare) path and lives in the thread's local memory.
+static __device__ __noinline__ bool fp64_projection(int M, const float *__restrict__ y, const GrpSmem &S, int k,
+                                                    const float *aq) {
+  double L64[(CSP_MAX_K + 1) * (CSP_MAX_K + 2) / 2];
   for (int i = 0; i <= k; ++i) {
     const float *ci = i < k ? S.colp[i] : aq;
     for (int j = 0; j <= i; ++j) {

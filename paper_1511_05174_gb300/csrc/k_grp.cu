@@ -634,21 +634,36 @@ bool dispatch_wave(int M, F &&f) {
 
 int wave_group(int M) { return M <= 32 ? 4 : (M <= 64 ? 8 : (M <= 128 ? 16 : 32)); }
 
-// (G, NCH) of the Batch-OMP restricted kernel: narrow groups (its per-iteration
-// state is scalar; M-vectors appear only in p0 and the rare explicit residual).
-template <typename F>
-bool dispatch_narrow(int M, F &&f) {
-  if (M % 4) return false;
-  if (M <= 16) f(std::integral_constant<int, 4>{}, std::integral_constant<int, 1>{});
-  else if (M <= 32) f(std::integral_constant<int, 4>{}, std::integral_constant<int, 2>{});
-  else if (M <= 64) f(std::integral_constant<int, 4>{}, std::integral_constant<int, 4>{});
-  else if (M <= 128) f(std::integral_constant<int, 8>{}, std::integral_constant<int, 4>{});
-  else if (M <= 256) f(std::integral_constant<int, 16>{}, std::integral_constant<int, 4>{});
-  else return false;
-  return true;
+// (G, NCH) of the Batch-OMP restricted kernel: narrow groups by default (its
+// per-iteration state is scalar; M-vectors appear only in p0 and the rare
+// explicit residual); `width` doubles the lanes per patch once or twice.
+int gram_group(int M, int width) {
+  const int g = (M <= 64 ? 4 : (M <= 128 ? 8 : 16)) << width;
+  return g > 32 ? 32 : g;
 }
 
-int narrow_group(int M) { return M <= 64 ? 4 : (M <= 128 ? 8 : 16); }
+template <typename F>
+bool dispatch_gram(int M, int width, F &&f) {
+  if (M % 4 || M > 256) return false;
+  const int G = gram_group(M, width);
+  const int nch = (M / 4 + G - 1) / G;
+  using std::integral_constant;
+  switch (G * 8 + nch) {
+    case 4 * 8 + 1: f(integral_constant<int, 4>{}, integral_constant<int, 1>{}); break;
+    case 4 * 8 + 2: f(integral_constant<int, 4>{}, integral_constant<int, 2>{}); break;
+    case 4 * 8 + 4: f(integral_constant<int, 4>{}, integral_constant<int, 4>{}); break;
+    case 8 * 8 + 1: f(integral_constant<int, 8>{}, integral_constant<int, 1>{}); break;
+    case 8 * 8 + 2: f(integral_constant<int, 8>{}, integral_constant<int, 2>{}); break;
+    case 8 * 8 + 4: f(integral_constant<int, 8>{}, integral_constant<int, 4>{}); break;
+    case 16 * 8 + 1: f(integral_constant<int, 16>{}, integral_constant<int, 1>{}); break;
+    case 16 * 8 + 2: f(integral_constant<int, 16>{}, integral_constant<int, 2>{}); break;
+    case 16 * 8 + 4: f(integral_constant<int, 16>{}, integral_constant<int, 4>{}); break;
+    case 32 * 8 + 1: f(integral_constant<int, 32>{}, integral_constant<int, 1>{}); break;
+    case 32 * 8 + 2: f(integral_constant<int, 32>{}, integral_constant<int, 2>{}); break;
+    default: return false;
+  }
+  return true;
+}
 
 }  // namespace
 
@@ -668,15 +683,15 @@ void launch_omp_update_wave(const float *Y, int M, const float *A, const float *
   });
 }
 
-void launch_omp_restricted_gram(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,
-                                int64_t n, const int32_t *child_off, const int32_t *child_idx, int cap,
-                                const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int8_t *Kp,
-                                int Kuni, int Kb, int32_t *omega, float *alpha, int ldo, int8_t *k_eff,
-                                int64_t *stats, const float *gram, int T, cudaStream_t s) {
+void launch_omp_restricted_gram(int width, const float *Y, int M, const float *A, const float *inv_norm,
+                                const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx,
+                                int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
+                                const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
+                                int8_t *k_eff, int64_t *stats, const float *gram, int T, cudaStream_t s) {
   if (n == 0) return;
-  const int per_cta = WV_WARPS * (32 / narrow_group(M));
+  const int per_cta = WV_WARPS * (32 / gram_group(M, width));
   const size_t sm = (size_t)gram_group_bytes(Kb, cap) * per_cta;
-  dispatch_narrow(M, [&](auto gc, auto nc) {
+  dispatch_gram(M, width, [&](auto gc, auto nc) {
     constexpr int GG = decltype(gc)::value, NCH = decltype(nc)::value;
     if (sm > 48 * 1024)
       cudaFuncSetAttribute(omp_restricted_gram_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

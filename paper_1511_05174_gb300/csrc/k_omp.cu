@@ -657,10 +657,10 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
                            const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, cudaStream_t s) {
   if (n == 0) return;
-  if (variant == 2 && (!gram || a_pstride)) variant = 0;  // the Gram variant needs a shared Gram matrix  // the Gram variant needs the level's Gram matrix
-  if (variant == 2) {
-    launch_omp_restricted_gram(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up, Kp,
-                               Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T, s);
+  if (variant >= 2 && (!gram || a_pstride)) variant = 0;  // the Gram variants need the level's shared Gram matrix
+  if (variant >= 2) {
+    launch_omp_restricted_gram(variant - 2, Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up,
+                               keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T, s);
     return;
   }
   if (variant == 0) {

@@ -10,6 +10,8 @@
 //    dictionary D^(l) against W_l x (Algorithm 2);
 //  * aggregation: x_hat_p = D_|Omega alpha, overlap-add averaged over the
 //    covering patches (Sec. IV: overlapping patches).
+#include <algorithm>
+
 #include "csp_internal.cuh"
 
 namespace csp {
@@ -301,6 +303,58 @@ __global__ void gather_kernel(GeomDev g, const float *__restrict__ Xh, int N0,
   img[e] = cnt ? acc / (float)cnt : 0.f;
 }
 
+// Fused synthesis + overlap-add over an output tile of TY x TX pixels (all
+// planes).  Phase 1 synthesizes x_hat_q = D0 alpha_q of every patch q that
+// covers the tile into shared memory (rows of ldp floats, ldp = stride mod 32
+// so that neighbouring pixels, which read neighbouring patches, hit distinct
+// banks); phase 2 averages, per pixel, over its covering patches in patch
+// raster order.  The arithmetic and its order are those of synth_kernel +
+// gather_kernel, so both paths give identical images.
+__global__ void __launch_bounds__(512)
+agg_tile_kernel(GeomDev g, const float *__restrict__ D0, int N0, const int32_t *__restrict__ support,
+                const float *__restrict__ coef, const int8_t *__restrict__ k_eff, int Kmax,
+                const int32_t *__restrict__ cover_y, const int32_t *__restrict__ cover_x, int TY, int TX, int ldp,
+                float *__restrict__ img) {
+  extern __shared__ float xs[];
+  const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
+  const int ty1 = min(ty0 + TY, g.H), tx1 = min(tx0 + TX, g.W);
+  const int iy0 = cover_y[2 * ty0], iy1 = cover_y[2 * (ty1 - 1) + 1];
+  const int ix0 = cover_x[2 * tx0], ix1 = cover_x[2 * (tx1 - 1) + 1];
+  const int nxc = ix1 - ix0 + 1, nq = (iy1 - iy0 + 1) * nxc;
+  for (int e = threadIdx.x; e < nq * N0; e += blockDim.x) {
+    const int q = e / N0, n = e - q * N0;
+    const int64_t b = (int64_t)(iy0 + q / nxc) * g.nx + (ix0 + q % nxc);
+    const int ke = k_eff[b];
+    const int32_t *sp = support + b * Kmax;
+    const float *cp = coef + b * Kmax;
+    float v = 0.f;
+#pragma unroll 8
+    for (int j = 0; j < Kmax; ++j)
+      if (j < ke) v = fmaf(__ldg(cp + j), __ldg(D0 + (int64_t)__ldg(sp + j) * N0 + n), v);
+    xs[q * ldp + n] = v;
+  }
+  __syncthreads();
+  const int planes = g.Ly * g.Lx, th = ty1 - ty0, tw = tx1 - tx0;
+  for (int e = threadIdx.x; e < planes * th * tw; e += blockDim.x) {
+    const int x = tx0 + e % tw, r = e / tw;
+    const int y = ty0 + r % th, pl = r / th;
+    const int y0 = cover_y[2 * y], y1 = cover_y[2 * y + 1];
+    const int x0 = cover_x[2 * x], x1 = cover_x[2 * x + 1];
+    float acc = 0.f;
+    int cnt = 0;
+    for (int iy = y0; iy <= y1; ++iy) {
+      const int py = y - origin(iy, g.stride, g.H, g.P);
+      const float *row = xs + (iy - iy0) * nxc * ldp;
+      for (int ix = x0; ix <= x1; ++ix) {
+        const int px = x - origin(ix, g.stride, g.W, g.P);
+        acc += row[(ix - ix0) * ldp + (pl * g.P + py) * g.P + px];
+        ++cnt;
+      }
+    }
+    img[((int64_t)pl * g.H + y) * g.W + x] = cnt ? acc / (float)cnt : 0.f;
+  }
+}
+
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -347,6 +401,62 @@ void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *
     synth_kernel<<<blocks(B, ppc), 256, sm, s>>>(D0, N0, support, coef, k_eff, Kmax, B, ppc, Xh);
   }
   gather_kernel<<<blocks(n, 256), 256, 0, s>>>(g, Xh, N0, cover_y, cover_x, img);
+}
+
+// Largest number of patches covering one tile of T pixels along an axis of
+// extent E (patch origins min(i * stride, E - P)), over all tiles.
+static int max_cover(int E, int P, int stride, int n, int T) {
+  // first / last patch covering pixel y (origins are nondecreasing)
+  auto org = [&](int i) { return std::min(i * stride, E - P); };
+  int best = 0;
+  int lo = 0;
+  for (int t0 = 0; t0 < E; t0 += T) {
+    const int t1 = std::min(t0 + T, E) - 1;
+    while (lo < n && org(lo) + P <= t0) ++lo;
+    int hi = lo;
+    while (hi + 1 < n && org(hi + 1) <= t1) ++hi;
+    best = std::max(best, hi - lo + 1);
+  }
+  return best;
+}
+
+struct AggTile {
+  int TY = 0, TX = 0, ldp = 0;
+  size_t smem = 0;
+};
+
+static bool agg_tile_plan(const GeomDev &g, int N0, AggTile &p) {
+  constexpr size_t kSmemCap = 113 * 1024;  // two CTAs per SM
+  static const int tiles[][2] = {{16, 32}, {8, 32}, {4, 32}, {8, 16}, {4, 16}, {4, 8}, {2, 8}};
+  p.ldp = N0 + (((g.stride - N0) % 32) + 32) % 32;
+  if (g.stride > g.P) return false;  // rows between patches are uncovered: no contiguous covering range
+  for (const auto &t : tiles) {
+    p.TY = t[0];
+    p.TX = t[1];
+    p.smem = sizeof(float) * (size_t)p.ldp * max_cover(g.H, g.P, g.stride, g.ny, p.TY) *
+             max_cover(g.W, g.P, g.stride, g.nx, p.TX);
+    if (p.smem <= kSmemCap) return true;
+  }
+  return false;
+}
+
+bool aggregate_tiled_fits(const GeomDev &g, int N0) {
+  AggTile p;
+  return agg_tile_plan(g, N0, p);
+}
+
+bool launch_aggregate_tiled(const GeomDev &g, const float *D0, int N0, const int32_t *support, const float *coef,
+                            const int8_t *k_eff, int Kmax, const int32_t *cover_y, const int32_t *cover_x, float *img,
+                            cudaStream_t s) {
+  if ((int64_t)g.Ly * g.Lx * g.H * g.W == 0) return true;
+  AggTile p;
+  if (!agg_tile_plan(g, N0, p)) return false;
+  if (p.smem > 48 * 1024)
+    cudaFuncSetAttribute(agg_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  const dim3 grid((unsigned)((g.W + p.TX - 1) / p.TX), (unsigned)((g.H + p.TY - 1) / p.TY));
+  agg_tile_kernel<<<grid, 512, p.smem, s>>>(g, D0, N0, support, coef, k_eff, Kmax, cover_y, cover_x, p.TY, p.TX,
+                                             p.ldp, img);
+  return true;
 }
 
 void launch_patch_codes(const GeomDev &g, const uint8_t *codes, int64_t B, uint8_t *pc, cudaStream_t s) {

@@ -7,9 +7,10 @@
 // (zero-padded to Mp = 64 k), the accumulator FP32 in tensor memory.
 //
 // CTA layout (320 threads):
-//   warp 0  TMA producer: the residual tile once, then atom tiles of NT rows
-//           through a two-stage shared-memory ring (cp.async.bulk.tensor,
-//           128-byte swizzle, mbarrier transaction counts);
+//   warp 0  TMA producer: the residual tile once, then the atom tiles of NT
+//           rows in 64-element K chunks through a ring of NS shared-memory
+//           stages (cp.async.bulk.tensor, 128-byte swizzle, mbarrier
+//           transaction counts), so that M up to 512 fits;
 //   warp 1  TMEM allocator and single-thread MMA issuer (tcgen05.mma
 //           kind::f16, M = 128, N = NT, K = 16 per instruction) into two
 //           TMEM accumulators of NT columns, released by tcgen05.commit;
@@ -36,7 +37,7 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_EPI_WARPS = 8;                    // two per TMEM lane quadrant
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
-constexpr int TC_STAGES = 2;
+constexpr int TC_MAX_STAGES = 8;
 constexpr long long kTimeoutCycles = 4000000000ll;  // about 2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -146,8 +147,9 @@ __device__ __forceinline__ void top4_insert(uint32_t x, uint32_t &k0, uint32_t &
 struct TcLayout {
   int kb;       // 64-element K blocks
   int nt;       // atoms per tile
+  int ns;       // stages of the atom ring
   int r_bytes;  // residual tile
-  int a_bytes;  // one atom-tile stage
+  int a_bytes;  // one stage: one K block of an atom tile
   int bar_off;  // barriers (after the 1024-aligned tiles)
   int mrg_off;  // epilogue merge area: [TC_M][4] keys
   int total;    // dynamic shared memory requested (includes alignment slack)
@@ -158,8 +160,12 @@ __host__ __device__ inline TcLayout tc_layout(int Mp, int nt) {
   L.kb = Mp / 64;
   L.nt = nt;
   L.r_bytes = L.kb * TC_M * 128;
-  L.a_bytes = L.kb * nt * 128;
-  L.bar_off = L.r_bytes + TC_STAGES * L.a_bytes;
+  L.a_bytes = nt * 128;
+  // two CTAs per SM while the residual tile is small, else one
+  const int budget = L.r_bytes <= 48 * 1024 ? 112 * 1024 : 220 * 1024;
+  int ns = (budget - L.r_bytes - 4096) / L.a_bytes;
+  L.ns = ns < 2 ? 2 : (ns > TC_MAX_STAGES ? TC_MAX_STAGES : ns);
+  L.bar_off = L.r_bytes + L.ns * L.a_bytes;
   L.mrg_off = L.bar_off + 256;
   L.total = L.mrg_off + TC_M * 4 * 4 + 1024;
   return L;
@@ -176,13 +182,14 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
   uint8_t *r_tile = smem;
   uint8_t *a_stage = smem + lay.r_bytes;
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem + lay.bar_off);
-  uint64_t *full = bars;          // [2] TMA -> MMA
-  uint64_t *empty = bars + 2;     // [2] MMA -> TMA
-  uint64_t *tfull = bars + 4;     // [2] MMA -> epilogue
-  uint64_t *tempty = bars + 6;    // [2] epilogue -> MMA
-  uint64_t *rfull = bars + 8;     // residual tile landed
-  uint64_t *mdone = bars + 9;     // all MMAs retired
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 10);
+  const int NS = lay.ns;
+  uint64_t *full = bars;                          // [NS] TMA -> MMA
+  uint64_t *empty = bars + TC_MAX_STAGES;         // [NS] MMA -> TMA
+  uint64_t *tfull = bars + 2 * TC_MAX_STAGES;     // [2] MMA -> epilogue
+  uint64_t *tempty = tfull + 2;                   // [2] epilogue -> MMA
+  uint64_t *rfull = tfull + 4;                    // residual tile landed
+  uint64_t *mdone = tfull + 5;                    // all MMAs retired
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(tfull + 6);
   uint32_t *merge = reinterpret_cast<uint32_t *>(smem + lay.mrg_off);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -191,9 +198,11 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
   const uint32_t ncols = 2u * (uint32_t)nt;
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NS; ++i) {
       mbar_init(full + i, 1);
       mbar_init(empty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(tfull + i, 1);
       mbar_init(tempty + i, TC_EPI_WARPS);
     }
@@ -214,24 +223,25 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
 
   if (warp == 0) {
     if (lane == 0) {
-      // producer
-      int issued[2] = {0, 0};  // loads issued per stage
+      // producer: chunk t = (atom tile j, K block kb) goes to stage t % NS
+      int issued[TC_MAX_STAGES] = {};  // loads issued per stage
       bool ok = true;
       mbar_expect_tx(rfull, (uint32_t)lay.r_bytes);
       for (int kb = 0; kb < lay.kb; ++kb)
         tma_load_2d(r_tile + kb * TC_M * 128, &tmR, kb * 64, (int)(row0 + tile0), rfull);
-      for (int j = 0; j < n_at && ok; ++j) {
-        const int s = j & 1;
-        if (j >= 2) ok = mbar_wait(empty + s, (uint32_t)(((j >> 1) - 1) & 1), err, 1);
+      const int n_chunks = n_at * lay.kb;
+      for (int t = 0; t < n_chunks && ok; ++t) {
+        const int s = t % NS, use = t / NS;
+        if (use >= 1) ok = mbar_wait(empty + s, (uint32_t)((use - 1) & 1), err, 1);
         if (!ok) break;
+        const int j = t / lay.kb, kb = t - j * lay.kb;
         mbar_expect_tx(full + s, (uint32_t)lay.a_bytes);
-        for (int kb = 0; kb < lay.kb; ++kb)
-          tma_load_2d(a_stage + s * lay.a_bytes + kb * nt * 128, &tmA, kb * 64, j * nt, full + s);
+        tma_load_2d(a_stage + s * lay.a_bytes, &tmA, kb * 64, j * nt, full + s);
         ++issued[s];
       }
       // drain: the last load of each stage and the residual tile have landed
       mbar_wait(rfull, 0, err, 2);
-      for (int s = 0; s < 2; ++s)
+      for (int s = 0; s < NS; ++s)
         if (issued[s]) mbar_wait(full + s, (uint32_t)((issued[s] - 1) & 1), err, 2);
     }
   } else if (warp == 1) {
@@ -240,21 +250,25 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
       const uint32_t idesc = instr_desc(TC_M, nt);
       bool ok = mbar_wait(rfull, 0, err, 3);
       const uint32_t r_base = smem_u32(r_tile);
+      int t = 0;  // K-block chunk index, as in the producer
       for (int j = 0; j < n_at && ok; ++j) {
-        const int s = j & 1, a = j & 1;
-        ok = mbar_wait(full + s, (uint32_t)((j >> 1) & 1), err, 4);
-        if (ok && j >= 2) ok = mbar_wait(tempty + a, (uint32_t)(((j >> 1) - 1) & 1), err, 5);
-        if (!ok) break;
-        tc_fence_after();
-        const uint32_t a_base = smem_u32(a_stage + s * lay.a_bytes);
-        const int ksteps = Mp / 16;
-        for (int ks = 0; ks < ksteps; ++ks) {
-          const int kb = ks >> 2, kin = ks & 3;
-          const uint64_t ad = smem_desc(r_base + kb * TC_M * 128 + kin * 32);
-          const uint64_t bd = smem_desc(a_base + kb * nt * 128 + kin * 32);
-          mma_bf16(tmem + (uint32_t)(a * nt), ad, bd, idesc, ks > 0 ? 1u : 0u);
+        const int a = j & 1;
+        if (j >= 2) ok = mbar_wait(tempty + a, (uint32_t)(((j >> 1) - 1) & 1), err, 5);
+        for (int kb = 0; kb < lay.kb && ok; ++kb, ++t) {
+          const int s = t % NS;
+          ok = mbar_wait(full + s, (uint32_t)((t / NS) & 1), err, 4);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(a_stage + s * lay.a_bytes);
+#pragma unroll
+          for (int kin = 0; kin < 4; ++kin) {
+            const uint64_t ad = smem_desc(r_base + kb * TC_M * 128 + kin * 32);
+            const uint64_t bd = smem_desc(a_base + kin * 32);
+            mma_bf16(tmem + (uint32_t)(a * nt), ad, bd, idesc, (kb | kin) ? 1u : 0u);
+          }
+          mma_commit(empty + s);
         }
-        mma_commit(empty + s);
+        if (!ok) break;
         mma_commit(tfull + a);
       }
       mma_commit(mdone);
@@ -379,8 +393,9 @@ int tile_atoms(int) { return 128; }  // 2 x 128 TMEM columns: two CTAs fit one S
 
 bool proxy_bf16_supported(int M, int T) {
   const int Mp = (M + 63) / 64 * 64;
-  // packed 32-bit keys keep >= 16 score bits: T <= 2^15
-  return M > 0 && Mp <= 256 && T > 0 && T <= (1 << 15) && encode_fn() != nullptr;
+  // packed 32-bit keys keep >= 16 score bits: T <= 2^15; the residual tile
+  // (128 rows x Mp BF16) stays resident in shared memory: Mp <= 512
+  return M > 0 && Mp <= 512 && T > 0 && T <= (1 << 15) && encode_fn() != nullptr;
 }
 
 bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, const __nv_bfloat16 *Abf, int T,

@@ -156,7 +156,9 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
   const size_t o_sup = dv.take<int32_t>((size_t)Bt * Kmax);
   const size_t o_coef = dv.take<float>((size_t)Bt * Kmax);
   const size_t o_keff = dv.take<int8_t>((size_t)Bt);
-  const size_t o_xh = dv.take<float>((size_t)Bmax * m.N0);
+  bool tiled = true;  // fused synthesis + overlap-add needs no scratch
+  for (Job *j : sl.jobs) tiled &= aggregate_tiled_fits(j->gd, m.N0);
+  const size_t o_xh = dv.take<float>(tiled ? 0 : (size_t)Bmax * m.N0);
   const size_t o_pc = ce ? dv.take<uint8_t>((size_t)Bt * codes_pp) : 0;
   size_t o_A[CSP_MAX_LEVELS] = {}, o_inv[CSP_MAX_LEVELS] = {};
   if (ce)
@@ -257,8 +259,10 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
     const JobLayout &L = jl[k];
     const int32_t *dcy = (const int32_t *)dp(L.d_cov), *dcx = dcy + 2 * (size_t)j->H;
     float *img = (float *)dp(L.d_img);
-    launch_aggregate(j->gd, m.ctx->lv[0].D, m.N0, sup + j->off * Kmax, coef + j->off * Kmax, keff + j->off, Kmax, dcy,
-                     dcx, xh, img, s);
+    if (!tiled || !launch_aggregate_tiled(j->gd, m.ctx->lv[0].D, m.N0, sup + j->off * Kmax, coef + j->off * Kmax,
+                                          keff + j->off, Kmax, dcy, dcx, img, s))
+      launch_aggregate(j->gd, m.ctx->lv[0].D, m.N0, sup + j->off * Kmax, coef + j->off * Kmax, keff + j->off, Kmax,
+                       dcy, dcx, xh, img, s);
     if ((e = cudaMemcpyAsync(j->h_img, img, j->img_floats * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

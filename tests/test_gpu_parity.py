@@ -53,13 +53,7 @@ def test_plain_parity(key, prec):
     """BF16: tensor-core proxy (tcgen05) with the top candidates re-scored in
     FP32 -- held to the same support bar as the FP32 path."""
     w = _workload(key)
-    if key == "video" and prec == "bf16":
-        # per-patch Phi: the lifted proxy has dimension 512 > 256 at the finest scale
-        from paper_1511_05174_gb300 import _binding as b
-        with pytest.raises(b.CspError) as e:
-            run_gpu(w, "plain", prec)
-        assert e.value.status == b.CSP_ERR_UNSUPPORTED
-        return
+    # video: per-patch Phi, the lifted proxy runs at dimension 512 (eight K blocks)
     g = run_gpu(w, "plain", prec)
     o, a, k, _ = oracle.plain_omp(w)
     rate, worst, bad = compare(w.dicts[0], g["sup"], g["coef"], g["keff"], o, a, k)
@@ -239,12 +233,12 @@ def test_exactly_dependent_atom_ends_the_patch():
     assert rate == 1.0 and worst <= REL_TOL
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("key", ["bayer", "lightfield", "denoise_ragged", "video"])
 def test_restricted_variants_agree_with_oracle(key, variant):
     """Every restricted-solver variant the autotuner may pick meets the parity
     bar: L2-cooperative (0), shared-memory staged (1), Gram-matrix proxy with
-    exact re-score (2)."""
+    narrow, middle and wide lane groups (2, 3, 4)."""
     from paper_1511_05174_gb300.context import Context
     w = _workload(key)
     o, a, k, _ = oracle.cross_scale_omp(w)
@@ -267,5 +261,5 @@ def test_autotune_picks_a_variant():
     Y = ctx.extract(torch.from_numpy(w.meas).cuda())
     K, K_patch, Kmax = budgets(w, "cross_scale")
     r = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
-    assert r["restricted_variant"] in (0, 1, 2) and all(t > 0 for t in r["ms"])
+    assert r["restricted_variant"] in range(5) and all(t > 0 for t in r["ms"])
     assert r["ms"][r["restricted_variant"]] == min(r["ms"])

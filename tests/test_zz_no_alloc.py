@@ -46,6 +46,34 @@ def test_noalloc_aggregate_matches_aggregate_twice():
         assert np.abs(o - r).max() <= 1e-5 * scale, call
 
 
+@pytest.mark.parametrize("name,kw", [
+    ("bayer", dict(H=64, W=72)),
+    ("denoise", dict(H=64, W=72)),
+    ("video", dict(H=48, W=40, T0=1024)),
+    ("lightfield", dict(H=40, W=48, T0=2048)),
+])
+def test_fused_tile_aggregation_equals_two_pass(name, kw):
+    """csp_aggregate runs the fused shared-memory tile kernel; the no-alloc
+    entry point the two-pass synthesis + gather.  Same arithmetic in the same
+    order: the images are bit-identical (ragged grids included)."""
+    w = synthetic.make_workload(name, **kw)
+    if name == "denoise":
+        w.geometry.stride = 3
+    ctx = Context(0)
+    ctx.load_workload(w)
+    stream = torch.cuda.current_stream().cuda_stream
+    meas = torch.from_numpy(w.meas).cuda()
+    Y = ctx.extract(meas)
+    K = [int(np.max(k)) for k in w.K_levels]
+    sup, coef, keff = ctx.solve(Y, "plain", "fp32", K=K[:1], Kmax=K[0])
+    ref = ctx.aggregate(sup, coef, keff)
+    out = torch.full_like(ref, float("nan"))
+    b.csp_aggregate_noalloc(ctx._ctx, sup.data_ptr(), coef.data_ptr(), keff.data_ptr(), sup.shape[0],
+                            sup.shape[1], out.data_ptr(), stream)
+    torch.cuda.synchronize()
+    assert torch.equal(ref, out)
+
+
 def test_noalloc_rejects_oversized_batches():
     w = synthetic.make_workload("bayer")  # 64,009 patches x 192 > 4 Mi floats
     ctx = Context(0)
