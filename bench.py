@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-jobs", type=int, default=96)
+    ap.add_argument("--serving-jobs", type=int, default=24, help="jobs per offered rate")
     return ap.parse_args()
 
 
@@ -272,58 +272,74 @@ def cpu_baseline(w, seconds=12.0):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
-def serving_bench(w, args, K, Kmax, device, jobs):
-    """The serving engine on this GPU: saturation throughput of a burst of
-    whole-image jobs, then latency under Poisson arrivals at 70% of it.
-    Per GPU; host buffers; every job copies its measurements in and its image
-    out.  Returns a dict for the JSON line."""
+SERVING_RATES = (10, 20, 50, 100, 200)  # offered jobs/s
+
+
+def serving_pool(kinds=("denoise", "bayer", "video"), per_kind=4, seed=0, lo=128, hi=2048):
+    """Distinct jobs of each kind (own seed, own coded-exposure mask), sides
+    uniform in [lo, hi] (multiples of 8); one model (dictionaries and links)
+    per kind.  Returns [(kind, workload)]."""
+    import synthetic
+    rng = np.random.default_rng(seed)
+    pool = []
+    for kind in kinds:
+        for i in range(per_kind):
+            side = int(rng.integers(lo // 8, hi // 8 + 1)) * 8
+            pool.append((kind, synthetic.make_workload(kind, seed=1000 + 10 * i + len(pool), H=side, W=side,
+                                                       dict_seed=0)))
+    return pool
+
+
+def serving_bench(args, device, pool, mode, jobs_per_rate):
+    """Serving engine on this GPU: continuous batching of a Poisson stream of
+    jobs drawn uniformly from `pool`, at each offered rate in SERVING_RATES.
+    Host buffers in and out; per job the latency is done - submitted.
+    Returns a dict for the JSON line."""
     from paper_1511_05174_gb300.server import Server
 
-    g = w.geometry
-    srv = Server(device, n_streams=2)
+    srv = Server(device, mem_budget_bytes=64 << 30, n_streams=2)
     try:
-        mid = srv.add_workload_model(w, "cross_scale", args.precision, K=K, Kmax=Kmax)
-        outs = [np.empty((g.planes, g.H, g.W), np.float32) for _ in range(8)]
-        meas = np.ascontiguousarray(w.meas, dtype=np.float32)
+        models = {}
+        for kind, w in pool:
+            if kind not in models:
+                models[kind] = srv.add_workload_model(w, mode, args.precision)
+        outs = [np.empty((w.geometry.planes, w.geometry.H, w.geometry.W), np.float32) for _, w in pool]
+        meas = [np.ascontiguousarray(w.meas, dtype=np.float32) for _, w in pool]
 
-        def run(n, gaps=None):
+        def run(order, gaps=None):
             ids = []
-            t0 = time.perf_counter()
-            t_next = t0
-            for i in range(n):
+            t_next = time.perf_counter()
+            for n, i in enumerate(order):
                 if gaps is not None:
-                    t_next += gaps[i]
+                    t_next += gaps[n]
                     while time.perf_counter() < t_next:
                         pass
-                ids.append(srv.submit(mid, meas, g.H, g.W, out=outs[i % len(outs)]))
+                kind, w = pool[i]
+                codes = w.sensing.codes if w.sensing.kind == "coded_exposure" else None
+                ids.append(srv.submit(models[kind], meas[i], w.geometry.H, w.geometry.W, codes=codes, out=outs[i]))
+            infos = []
             for j in ids:
-                st = srv.wait(j, 120)
+                st = srv.wait(j, 600)
                 if st != 0:
                     raise RuntimeError(f"serving job failed with status {st}")
-            infos = [srv.info(j) for j in ids]
-            for j in ids:
+                infos.append(srv.info(j))
                 srv.release(j)
             return infos
 
-        run(8)  # warm-up: workspaces, pools, staging
-        burst = run(jobs)
-        span = max(i["t_done"] for i in burst) - min(i["t_submit"] for i in burst)
-        sat_jobs = jobs / span
-        rate = 0.7 * sat_jobs
-        gaps = np.random.default_rng(0).exponential(1.0 / rate, size=jobs)
-        pois = run(jobs, gaps)
-        lat = np.array([i["t_done"] - i["t_submit"] for i in pois]) * 1e3
-        wait = np.array([i["t_admit"] - i["t_submit"] for i in pois]) * 1e3
-        return {
-            "model": f"{w.name} {g.H}x{g.W} cross_scale {args.precision}", "n_streams": 2, "per_gpu": True,
-            "saturation": {"jobs": jobs, "jobs_per_s": sat_jobs, "value": sat_jobs * w.n_patches, "unit": UNIT,
-                           "mean_batch_jobs": float(np.mean([i["batch_jobs"] for i in burst]))},
-            "poisson": {"rate_jobs_per_s": rate, "jobs": jobs, "latency_ms_p50": float(np.percentile(lat, 50)),
-                        "latency_ms_p99": float(np.percentile(lat, 99)),
-                        "queue_ms_p50": float(np.percentile(wait, 50)),
-                        "mean_batch_jobs": float(np.mean([i["batch_jobs"] for i in pois]))},
-            "h2d_bytes_per_job": int(meas.nbytes), "d2h_bytes_per_job": int(outs[0].nbytes),
-        }
+        run(range(len(pool)))  # warm-up: every job once (workspaces, pools, staging)
+        rng = np.random.default_rng(1)
+        rates = []
+        for rate in SERVING_RATES:
+            order = rng.integers(0, len(pool), size=jobs_per_rate)
+            infos = run(order, rng.exponential(1.0 / rate, size=jobs_per_rate))
+            lat = np.array([i["t_done"] - i["t_submit"] for i in infos]) * 1e3
+            span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+            patches = sum(i["patches"] for i in infos)
+            rates.append({"offered_jobs_per_s": rate, "jobs": len(infos), "value": patches / span, "unit": UNIT,
+                          "jobs_per_s": len(infos) / span, "latency_ms_p50": float(np.percentile(lat, 50)),
+                          "latency_ms_p99": float(np.percentile(lat, 99)),
+                          "mean_batch_jobs": float(np.mean([i["batch_jobs"] for i in infos]))})
+        return rates
     finally:
         srv.close()
 
@@ -465,7 +481,12 @@ def main():
 
     serving = None
     if not args.no_serving:
-        serving = serving_bench(w, args, K, Kmax, local, args.serving_jobs)
+        pool = serving_pool()
+        serving = {"pool": [{"kind": k, "side": int(w.geometry.H), "patches": int(w.n_patches)} for k, w in pool],
+                   "precision": args.precision, "n_streams": 2, "per_gpu": True,
+                   "note": "Poisson arrivals; each job drawn uniformly from the pool; host buffers in and out"}
+        for mode in ("cross_scale", "plain"):
+            serving[mode] = serving_bench(args, local, pool, mode, args.serving_jobs)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -479,7 +500,8 @@ def main():
             "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
             "data": "synthetic (seeded; Gaussian unit-norm atoms, K-sparse N(0,1) codes)",
             "config": {**workload_config(w, args), "form": "cross_scale", "precision": args.precision,
-                       "restricted_variant": tune["restricted_variant"]},
+                       "restricted_variant": tune["restricted_variant"],
+                       "autotune_ms": [round(t, 4) for t in tune["ms"]]},
             "plain_omp": {"value": plain_value, "unit": UNIT, "ms_per_step": pl_ms / args.steps,
                           "kernels": kernels_plain},
             "speedup_cross_scale_vs_plain": value / plain_value,

@@ -157,7 +157,7 @@ enum Slot {
   WS_LV_OMEGA, WS_LV_ALPHA = WS_LV_OMEGA + CSP_MAX_LEVELS, WS_LV_KEFF = WS_LV_ALPHA + CSP_MAX_LEVELS,
   WS_LV_Y = WS_LV_KEFF + CSP_MAX_LEVELS,
   WS_XH = WS_LV_Y + CSP_MAX_LEVELS,
-  WS_SCRATCH, WS_LIFT, WS_LIFTBF,
+  WS_SCRATCH, WS_LIFT, WS_LIFTBF, WS_PPC_A, WS_PPC_INV, WS_PART,
   WS_COUNT
 };
 
@@ -197,7 +197,6 @@ void free_own_patches(csp_ctx *ctx) {
     dev_free(ctx, ctx->pp_inv[l]);
     ctx->pp_A[l] = ctx->pp_inv[l] = nullptr;
   }
-  ctx->pp_ready = false;
 }
 
 void free_links(csp_ctx *ctx, LevelData &L) {
@@ -288,31 +287,26 @@ csp_status check_solve_shape(csp_ctx *ctx, const csp_solve_params *prm) {
 
 // Per-patch effective dictionaries and norms for B patches with code blocks
 // pc, into A_pp/inv_pp (allocated by the caller, [B][T_l][M] and [B][T_l]).
-csp_status build_patch_dicts(csp_ctx *ctx, const uint8_t *pc, int64_t B, float *const *A_pp, float *const *inv_pp,
+csp_status build_patch_dicts(csp_ctx *ctx, int l, const uint8_t *pc, int64_t B, float *A_pp, float *inv_pp,
                              unsigned int *scratch, cudaStream_t s) {
-  for (int l = 0; l < ctx->geom.n_levels; ++l) {
-    LevelData &L = ctx->lv[l];
-    const int64_t rows = B * L.T;
-    run(ctx, KK_PREP, s, rows, [&] { launch_effective_dict_pp(ctx->gd, pc, l, L.D, L.T, L.N, A_pp[l], B, s); });
-    run(ctx, KK_PREP, s, rows, [&] { launch_inv_row_norms(A_pp[l], rows, L.M, inv_pp[l], scratch, s); });
-  }
+  LevelData &L = ctx->lv[l];
+  const int64_t rows = B * L.T;
+  run(ctx, KK_PREP, s, rows, [&] { launch_effective_dict_pp(ctx->gd, pc, l, L.D, L.T, L.N, A_pp, B, s); });
+  run(ctx, KK_PREP, s, rows, [&] { launch_inv_row_norms(A_pp, rows, L.M, inv_pp, scratch, s); });
   CSP_CUDA(ctx, cudaGetLastError());
   return CSP_OK;
 }
 
-// Coded exposure: this context's own patch grid gets its per-patch data once.
-csp_status prepare_own_patches(csp_ctx *ctx, cudaStream_t s) {
-  if (ctx->sense_kind != CSP_SENSE_CODED_EXPOSURE || ctx->pp_ready) return CSP_OK;
-  for (int l = 0; l < ctx->geom.n_levels; ++l) {
-    const LevelData &L = ctx->lv[l];
-    CSP_TRY(dev_alloc_t(ctx, &ctx->pp_A[l], (size_t)ctx->B * L.T * L.M));
-    CSP_TRY(dev_alloc_t(ctx, &ctx->pp_inv[l], (size_t)ctx->B * L.T));
-  }
+// Coded exposure: this context's own patch grid gets the full per-patch
+// effective dictionary of level l (the full-dictionary level of a solve) once.
+csp_status prepare_own_patches(csp_ctx *ctx, int l, cudaStream_t s) {
+  if (ctx->sense_kind != CSP_SENSE_CODED_EXPOSURE || ctx->pp_A[l]) return CSP_OK;
+  const LevelData &L = ctx->lv[l];
+  CSP_TRY(dev_alloc_t(ctx, &ctx->pp_A[l], (size_t)ctx->B * L.T * L.M));
+  CSP_TRY(dev_alloc_t(ctx, &ctx->pp_inv[l], (size_t)ctx->B * L.T));
   unsigned int *scratch = nullptr;
   CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_SCRATCH, 4, &scratch));
-  CSP_TRY(build_patch_dicts(ctx, ctx->pcodes, ctx->B, ctx->pp_A, ctx->pp_inv, scratch, s));
-  ctx->pp_ready = true;
-  return CSP_OK;
+  return build_patch_dicts(ctx, l, ctx->pcodes, ctx->B, ctx->pp_A[l], ctx->pp_inv[l], scratch, s);
 }
 
 // Solve the patch set `ps` with the context's dictionaries (prepared), using
@@ -378,6 +372,13 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
       if (!bf16) CSP_TRY(ws_get_t(ctx, W, WS_LIFT, (size_t)B * L.N, &Zl));
       else CSP_TRY(ws_get_t(ctx, W, WS_LIFTBF, (size_t)B * L.Np, &Zbf));
     }
+    // partial top-4 keys when the tensor-core proxy splits the atoms over CTAs
+    uint32_t *part = nullptr;
+    if (bf16) {
+      int S = 1;
+      for (int ph = 0; ph < nph; ++ph) S = std::max(S, proxy_bf16_splits(n_of(ph), L.T));
+      if (S > 1) CSP_TRY(ws_get_t(ctx, W, WS_PART, (size_t)B * S * 4, &part));
+    }
     st.Kb = Kb[top];
     st.ldo = ldo[top];
     CSP_TRY(ws_get_t(ctx, W, WS_L, (size_t)B * (Kb[top] * (Kb[top] + 1) / 2), &st.Lpk));
@@ -399,10 +400,10 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
         if (bf16)
           run(ctx, KK_PROXY_BF16, s, n_of(ph), [&] {
             maps_ok &= pp ? launch_proxy_bf16(Zbf, B, L.Np, L.Dbf, L.T, 0, ids_of(ph), n_of(ph), st.flags, st.cand,
-                                              (unsigned long long *)(W.stats_dev + 4), ps.inv_pp[top], s)
+                                              (unsigned long long *)(W.stats_dev + 4), ps.inv_pp[top], part, s)
                           : launch_proxy_bf16(st.Rbf, B, L.Mp, L.Abf[ph], L.T, phased ? ps.phase_start[ph] : 0,
                                               ids_of(ph), n_of(ph), st.flags, st.cand,
-                                              (unsigned long long *)(W.stats_dev + 4), nullptr, s);
+                                              (unsigned long long *)(W.stats_dev + 4), nullptr, part, s);
           });
         else
           run(ctx, KK_PROXY_FP32, s, n_of(ph), [&] {
@@ -428,13 +429,23 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
   for (int l = top - 1; l >= 0; --l) {
     const LevelData &L = ctx->lv[l];
     const int cap = std::max(1, L.max_children * Kb[l + 1]);
+    float *Ac = nullptr, *invc = nullptr;
+    if (L.per_patch) {
+      // per-patch Phi: rows of this level's effective dictionary for each patch's candidates only
+      CSP_TRY(ws_get_t(ctx, W, WS_PPC_A, (size_t)B * cap * L.M, &Ac));
+      CSP_TRY(ws_get_t(ctx, W, WS_PPC_INV, (size_t)B * cap, &invc));
+      run(ctx, KK_PREP, s, B, [&] {
+        launch_pp_candidates(ctx->gd, ps.pcodes, l, L.D, L.N, L.M, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1],
+                             L.child_off, L.child_idx, cap, B, Ac, invc, s);
+      });
+    }
     for (int ph = 0; ph < nph; ++ph)
       run(ctx, KK_RESTRICTED, s, n_of(ph), [&] {
-        launch_omp_restricted(ctx->restricted_variant, Yl[l], L.M, L.per_patch ? ps.A_pp[l] : L.A[ph],
-                              L.per_patch ? ps.inv_pp[l] : L.inv_norm[ph], ids_of(ph), n_of(ph),
+        launch_omp_restricted(ctx->restricted_variant, Yl[l], L.M, L.per_patch ? Ac : L.A[ph],
+                              L.per_patch ? invc : L.inv_norm[ph], ids_of(ph), n_of(ph),
                               L.child_off, L.child_idx, cap, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1], prm->K_patch[l],
                               prm->K[l], Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], W.stats_dev, L.G[ph], L.T,
-                              L.per_patch ? (int64_t)L.T * L.M : 0, L.per_patch ? (int64_t)L.T : 0, s);
+                              L.per_patch ? (int64_t)cap * L.M : 0, L.per_patch ? (int64_t)cap : 0, L.per_patch, s);
       });
   }
   CSP_CUDA(ctx, cudaGetLastError());
@@ -468,9 +479,9 @@ csp_status solve_patchset(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const 
   return solve_core(ctx, ps, W, prm, Y, support_out, coef_out, k_eff_out, s);
 }
 
-csp_status build_patch_dicts_for(csp_ctx *ctx, const uint8_t *pc, int64_t B, float *const *A_pp,
-                                 float *const *inv_pp, unsigned int *scratch, cudaStream_t s) {
-  return build_patch_dicts(ctx, pc, B, A_pp, inv_pp, scratch, s);
+csp_status build_patch_dicts_for(csp_ctx *ctx, int level, const uint8_t *pc, int64_t B, float *A_pp, float *inv_pp,
+                                 unsigned int *scratch, cudaStream_t s) {
+  return build_patch_dicts(ctx, level, pc, B, A_pp, inv_pp, scratch, s);
 }
 
 int64_t patch_count_1d(int E, int P, int stride) { return count_1d(E, P, stride); }
@@ -788,7 +799,7 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
   DeviceGuard dg(ctx->device);
   CSP_TRY(prepare(ctx, s));
   CSP_TRY(check_solve_shape(ctx, prm));
-  CSP_TRY(prepare_own_patches(ctx, s));
+  CSP_TRY(prepare_own_patches(ctx, nl - 1, s));  // the full-dictionary level of this solve
   PatchSet ps;
   ps.B = B;
   if (ctx->sense_kind == CSP_SENSE_BAYER_RGGB) {

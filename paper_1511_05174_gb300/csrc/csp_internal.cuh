@@ -71,6 +71,8 @@ struct PatchSet {
   const uint8_t *pcodes = nullptr;          // coded exposure: [B][F*P*P] per-patch code blocks
   float *A_pp[CSP_MAX_LEVELS] = {};         // coded exposure: per-patch effective dictionaries [B][T_l][M]
   float *inv_pp[CSP_MAX_LEVELS] = {};       // ... and their inverse column norms [B][T_l]
+                                            // (needed for the full-dictionary level only; the
+                                            // restricted levels build their candidates' rows)
 };
 
 // Grow-only workspace slots and solve counters of one solver instance.
@@ -115,7 +117,6 @@ struct csp_ctx {
   uint8_t *pcodes = nullptr;
   float *pp_A[CSP_MAX_LEVELS] = {};
   float *pp_inv[CSP_MAX_LEVELS] = {};
-  bool pp_ready = false;
   int64_t last_B = 0;
   cudaStream_t last_stream = nullptr;
   // Host-path buffers of csp_reconstruct_host.
@@ -156,7 +157,7 @@ void launch_lift(const GeomDev &g, const uint8_t *pc, int level, const float *R,
 // Synthesis into Xh ([B][N0] scratch) then per-pixel overlap-add average (2 launches).
 // Fused synthesis + overlap-add without scratch; false when no tile shape fits
 // shared memory (then use launch_aggregate, which needs B * N0 floats of scratch).
-bool aggregate_tiled_fits(const GeomDev &g, int N0);
+bool aggregate_tiled_fits(const GeomDev &g, int N0, int Kmax);
 bool launch_aggregate_tiled(const GeomDev &g, const float *D0, int N0, const int32_t *support, const float *coef,
                             const int8_t *k_eff, int Kmax, const int32_t *cover_y, const int32_t *cover_x, float *img,
                             cudaStream_t s);
@@ -191,9 +192,13 @@ bool proxy_bf16_supported(int M, int T);
 bool omp_dims_supported(int M);  // M % 4 == 0 and M <= 256
 // Tensor-core proxy over the patches at sorted positions row0 .. row0 + n - 1
 // (list ids, may be null).  Returns false when a tensor map cannot be built.
+// With few patch tiles the atom tiles are split over proxy_bf16_splits(n, T)
+// CTAs per patch tile; `part` ([n][splits][4] uint32 scratch) then holds their
+// partial top-4 keys until a merge kernel writes cand.  part == null: no split.
+int proxy_bf16_splits(int64_t n, int T);
 bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, const __nv_bfloat16 *Abf, int T,
                        int64_t row0, const int32_t *ids, int64_t n, const uint8_t *flags, int32_t *cand,
-                       unsigned long long *err, const float *pinv, cudaStream_t s);
+                       unsigned long long *err, const float *pinv, uint32_t *part, cudaStream_t s);
 // Load-wave variants (k_grp.cu): one update iteration; restricted OMP with the Gram-matrix proxy.
 // a_pstride / inv_pstride: per-patch strides of A and inv_norm (0: shared by all patches).
 void launch_omp_update_wave(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,
@@ -215,14 +220,22 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
-                           const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, cudaStream_t s);
+                           const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, bool cpos,
+                           cudaStream_t s);
+// Per-pixel coded exposure, restricted level l: rows of the effective
+// dictionary for the candidates f(Omega_up) of every patch only, in candidate
+// order ([B][cap][M], row c of patch b = a_{cs_c} for that patch's codes) and
+// their inverse norms ([B][cap]); read by launch_omp_restricted(cpos = true).
+void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
+                          const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int32_t *child_off,
+                          const int32_t *child_idx, int cap, int64_t B, float *Ac, float *invc, cudaStream_t s);
 
 // ---- solve entry points shared by csp_solve and the serving engine (csp_api.cu) ----
 csp_status prepare_model(csp_ctx *ctx, cudaStream_t s);                       // effective dictionaries etc.
 csp_status check_solve_params(csp_ctx *ctx, const csp_solve_params *prm);   // argument and shape checks
 csp_status solve_patchset(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_solve_params *prm,
                           const float *Y, int32_t *support_out, float *coef_out, int8_t *k_eff_out, cudaStream_t s);
-csp_status build_patch_dicts_for(csp_ctx *ctx, const uint8_t *pc, int64_t B, float *const *A_pp, float *const *inv_pp,
+csp_status build_patch_dicts_for(csp_ctx *ctx, int level, const uint8_t *pc, int64_t B, float *A_pp, float *inv_pp,
                                  unsigned int *scratch, cudaStream_t s);
 // Patch origins helper (host): covering-patch ranges of every row/column for aggregation.
 void cover_ranges(int E, int P, int stride, int n, std::vector<int32_t> &out);

@@ -326,7 +326,7 @@ omp_restricted_staged_kernel(const float *__restrict__ Y, int M, const float *__
                       const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                       int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
                       int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T,
-                      int64_t a_pstride, int64_t inv_pstride) {
+                      int64_t a_pstride, int64_t inv_pstride, bool cpos) {
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
@@ -357,7 +357,7 @@ omp_restricted_staged_kernel(const float *__restrict__ Y, int M, const float *__
         if (nc + i < cap) {
           const int a = child_idx[c0 + i];
           S.cs[nc + i] = a;
-          S.invn[nc + i] = __ldg(inv_norm + a);
+          S.invn[nc + i] = __ldg(inv_norm + (cpos ? nc + i : a));
         }
       nc += c1 - c0;
     }
@@ -370,7 +370,7 @@ omp_restricted_staged_kernel(const float *__restrict__ Y, int M, const float *__
   // stage the first capS candidate rows
   const int nst = nc < capS ? nc : capS;
   for (int c = 0; c < nst; ++c) {
-    const float *src = A + (int64_t)S.cs[c] * M;
+    const float *src = A + (int64_t)(cpos ? c : S.cs[c]) * M;
     float *dst = rows + c * ldr;
     for (int j = s; j < nv; j += G) cp_async16(dst + 4 * j, src + 4 * j);
   }
@@ -402,7 +402,7 @@ omp_restricted_staged_kernel(const float *__restrict__ Y, int M, const float *__
       for (int c = s; c < nc; c += G) {
         const float inv = S.invn[c];
         if (!(inv > 0.f)) continue;
-        const float *row = c < capS ? rows + c * ldr : A + (int64_t)S.cs[c] * M;
+        const float *row = c < capS ? rows + c * ldr : A + (int64_t)(cpos ? c : S.cs[c]) * M;
         const unsigned long long key = pack_key(fabsf(row_dot(row, rs, nv)) * inv, S.cs[c]);
         best = key > best ? key : best;
       }
@@ -417,7 +417,7 @@ omp_restricted_staged_kernel(const float *__restrict__ Y, int M, const float *__
         }
     __syncwarp();
     const int qs = act ? S.misc[1] : 0;
-    const float *aqp = (act && qs < capS) ? rows + qs * ldr : A + (int64_t)q * M;
+    const float *aqp = (act && qs < capS) ? rows + qs * ldr : A + (int64_t)(cpos ? qs : q) * M;
     const bool ok = grp_append<G, NCH, false>(act, s, M, aqp, yrow, q, k, yv, rv, S, fl, rsq, stats, gram, T);
     if (act) {
       if (ok) {
@@ -458,7 +458,7 @@ omp_restricted_coop_kernel(const float *__restrict__ Y, int M, const float *__re
                       const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                       int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
                       int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T,
-                      int64_t a_pstride, int64_t inv_pstride) {
+                      int64_t a_pstride, int64_t inv_pstride, bool cpos) {
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
@@ -485,7 +485,7 @@ omp_restricted_coop_kernel(const float *__restrict__ Y, int M, const float *__re
         if (nc + i < cap) {
           const int a = child_idx[c0 + i];
           S.cs[nc + i] = a;
-          S.invn[nc + i] = __ldg(inv_norm + a);
+          S.invn[nc + i] = __ldg(inv_norm + (cpos ? nc + i : a));
         }
       nc += c1 - c0;
     }
@@ -517,8 +517,8 @@ omp_restricted_coop_kernel(const float *__restrict__ Y, int M, const float *__re
       const bool ok0 = act && c < nc && S.invn[c] > 0.f;
       const bool ok1 = act && c + 1 < nc && S.invn[c + 1] > 0.f;
       float4 a0[NCH], a1[NCH];
-      load_chunks<G, NCH>(a0, A + (int64_t)(ok0 ? S.cs[c] : 0) * M, nv, s, ok0);
-      load_chunks<G, NCH>(a1, A + (int64_t)(ok1 ? S.cs[c + 1] : 0) * M, nv, s, ok1);
+      load_chunks<G, NCH>(a0, A + (int64_t)(ok0 ? (cpos ? c : S.cs[c]) : 0) * M, nv, s, ok0);
+      load_chunks<G, NCH>(a1, A + (int64_t)(ok1 ? (cpos ? c + 1 : S.cs[c + 1]) : 0) * M, nv, s, ok1);
       const float p0 = gsum<G>(dotc<NCH>(a0, rv));
       const float p1 = gsum<G>(dotc<NCH>(a1, rv));
       if (ok0) {
@@ -535,10 +535,14 @@ omp_restricted_coop_kernel(const float *__restrict__ Y, int M, const float *__re
     const int q = act ? key_idx(best) : 0;
     if (act)
       for (int c = s; c < nc; c += G)
-        if (S.cs[c] == q) S.invn[c] = -1.f;  // chosen: no longer eligible
+        if (S.cs[c] == q) {
+          S.invn[c] = -1.f;  // chosen: no longer eligible
+          S.misc[1] = c;
+        }
     __syncwarp();
-    const bool ok = grp_append<G, NCH, true>(act, s, M, A + (int64_t)q * M, yrow, q, k, yv, rv, S, fl, rsq, stats,
-                                             gram, T);
+    const int qs = act ? S.misc[1] : 0;
+    const bool ok = grp_append<G, NCH, true>(act, s, M, A + (int64_t)(cpos ? qs : q) * M, yrow, q, k, yv, rv, S, fl,
+                                             rsq, stats, gram, T);
     if (act) {
       if (ok) ++k;
       else act = false;
@@ -655,9 +659,10 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
-                           const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, cudaStream_t s) {
+                           const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, bool cpos,
+                           cudaStream_t s) {
   if (n == 0) return;
-  if (variant >= 2 && (!gram || a_pstride)) variant = 0;  // the Gram variants need the level's shared Gram matrix
+  if (variant >= 2 && (!gram || a_pstride || cpos)) variant = 0;  // the Gram variants need the level's shared Gram matrix
   if (variant >= 2) {
     launch_omp_restricted_gram(variant - 2, Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up,
                                keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T, s);
@@ -673,7 +678,7 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
         cudaFuncSetAttribute(omp_restricted_coop_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
       omp_restricted_coop_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(
           Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega,
-          alpha, ldo, k_eff, stats, gram, T, a_pstride, inv_pstride);
+          alpha, ldo, k_eff, stats, gram, T, a_pstride, inv_pstride, cpos);
     });
     return;
   }
@@ -689,7 +694,7 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
       cudaFuncSetAttribute(omp_restricted_staged_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     omp_restricted_staged_kernel<GG, NCH><<<blocks(n, per_cta), GRP_WARPS * 32, sm, s>>>(
         Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, capS, omega_up, ldo_up, keff_up, Kp, Kuni, Kb,
-        omega, alpha, ldo, k_eff, stats, gram, T, a_pstride, inv_pstride);
+        omega, alpha, ldo, k_eff, stats, gram, T, a_pstride, inv_pstride, cpos);
   });
 }
 

@@ -136,6 +136,48 @@ __global__ void effective_dict_pp_kernel(GeomDev g, const uint8_t *__restrict__ 
   A[e] = v;
 }
 
+// Candidate rows of per-pixel coded exposure at a restricted level: one warp
+// per patch enumerates f(Omega_up) in the order of the restricted kernels
+// (parents in support order, each parent's children in link order, at most
+// cap) and writes a_c[m] = sum_t pc_p[t][m] d_c[level index of (t, m)] --
+// the arithmetic of effective_dict_pp_kernel -- and 1/||a_c|| (-1 for a zero
+// row), the norm reduced as in row_norms_kernel.
+__global__ void pp_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const float *__restrict__ D,
+                                     int N, int M, const int32_t *__restrict__ omega_up, int ldo_up,
+                                     const int8_t *__restrict__ keff_up, const int32_t *__restrict__ child_off,
+                                     const int32_t *__restrict__ child_idx, int cap, int64_t B,
+                                     float *__restrict__ Ac, float *__restrict__ invc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (b >= B) return;
+  const int F = g.Lx;
+  const uint8_t *c = pc + b * (int64_t)F * M;
+  float *Ab = Ac + b * (int64_t)cap * M;
+  const int kup = keff_up[b];
+  int nc = 0;
+  for (int j = 0; j < kup && nc < cap; ++j) {
+    const int p = omega_up[b * ldo_up + j];
+    const int c0 = child_off[p], c1 = child_off[p + 1];
+    for (int i = 0; i < c1 - c0 && nc < cap; ++i, ++nc) {
+      const float *d = D + (int64_t)child_idx[c0 + i] * N;
+      float sq = 0.f;
+      for (int m = lane; m < M; m += 32) {
+        const int py = m / g.P, px = m - py * g.P;
+        float v = 0.f;
+        for (int t = 0; t < F; ++t)
+          if (c[t * M + m]) v += __ldg(d + level_index(g, l, 0, t, py, px));
+        Ab[(int64_t)nc * M + m] = v;
+        sq = fmaf(v, v, sq);
+      }
+      for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      if (lane == 0) {
+        const float nrm = sqrtf(sq);
+        invc[b * cap + nc] = nrm > 0.f ? 1.f / nrm : -1.f;
+      }
+    }
+  }
+}
+
 // Row norms of a [rows][M] matrix: out = ||row|| (first pass), running max
 // of the norms in *mx (float bits, non-negative, compared as integers).
 __global__ void row_norms_kernel(const float *__restrict__ A, int64_t rows, int M, float *__restrict__ out,
@@ -304,33 +346,49 @@ __global__ void gather_kernel(GeomDev g, const float *__restrict__ Xh, int N0,
 }
 
 // Fused synthesis + overlap-add over an output tile of TY x TX pixels (all
-// planes).  Phase 1 synthesizes x_hat_q = D0 alpha_q of every patch q that
-// covers the tile into shared memory (rows of ldp floats, ldp = stride mod 32
-// so that neighbouring pixels, which read neighbouring patches, hit distinct
-// banks); phase 2 averages, per pixel, over its covering patches in patch
-// raster order.  The arithmetic and its order are those of synth_kernel +
-// gather_kernel, so both paths give identical images.
+// planes).  Phase 0 stages the codes (support, coefficients) of every patch q
+// covering the tile; phase 1 synthesizes x_hat_q = D0 alpha_q into shared
+// memory (rows of ldp floats, ldp = stride mod 32 so that neighbouring pixels,
+// which read neighbouring patches, hit distinct banks), only at the elements
+// that fall inside the tile; phase 2 averages, per pixel, over its covering
+// patches in patch raster order.  The arithmetic and its order are those of
+// synth_kernel + gather_kernel, so both paths give identical images.
 __global__ void __launch_bounds__(512)
 agg_tile_kernel(GeomDev g, const float *__restrict__ D0, int N0, const int32_t *__restrict__ support,
                 const float *__restrict__ coef, const int8_t *__restrict__ k_eff, int Kmax,
                 const int32_t *__restrict__ cover_y, const int32_t *__restrict__ cover_x, int TY, int TX, int ldp,
-                float *__restrict__ img) {
-  extern __shared__ float xs[];
+                int nq_max, float *__restrict__ img) {
+  extern __shared__ float xs[];  // [nq_max][ldp] patches, then [nq_max][Kmax] supports and coefficients
+  int *s_sup = reinterpret_cast<int *>(xs + (size_t)nq_max * ldp);
+  float *s_coef = reinterpret_cast<float *>(s_sup + nq_max * Kmax);
   const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
   const int ty1 = min(ty0 + TY, g.H), tx1 = min(tx0 + TX, g.W);
   const int iy0 = cover_y[2 * ty0], iy1 = cover_y[2 * (ty1 - 1) + 1];
   const int ix0 = cover_x[2 * tx0], ix1 = cover_x[2 * (tx1 - 1) + 1];
   const int nxc = ix1 - ix0 + 1, nq = (iy1 - iy0 + 1) * nxc;
+  const int PP = g.P * g.P;
+  for (int e = threadIdx.x; e < nq * Kmax; e += blockDim.x) {
+    const int q = e / Kmax, j = e - q * Kmax;
+    const int64_t b = (int64_t)(iy0 + q / nxc) * g.nx + (ix0 + q % nxc);
+    const bool on = j < k_eff[b];
+    s_sup[e] = on ? support[b * Kmax + j] : -1;
+    s_coef[e] = on ? coef[b * Kmax + j] : 0.f;
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < nq * N0; e += blockDim.x) {
     const int q = e / N0, n = e - q * N0;
-    const int64_t b = (int64_t)(iy0 + q / nxc) * g.nx + (ix0 + q % nxc);
-    const int ke = k_eff[b];
-    const int32_t *sp = support + b * Kmax;
-    const float *cp = coef + b * Kmax;
+    const int r = n % PP, py = r / g.P, px = r - py * g.P;
+    const int y = origin(iy0 + q / nxc, g.stride, g.H, g.P) + py;
+    const int x = origin(ix0 + q % nxc, g.stride, g.W, g.P) + px;
+    if (y < ty0 || y >= ty1 || x < tx0 || x >= tx1) continue;  // outside the tile: never read
+    const int *sp = s_sup + q * Kmax;
+    const float *cp = s_coef + q * Kmax;
     float v = 0.f;
 #pragma unroll 8
-    for (int j = 0; j < Kmax; ++j)
-      if (j < ke) v = fmaf(__ldg(cp + j), __ldg(D0 + (int64_t)__ldg(sp + j) * N0 + n), v);
+    for (int j = 0; j < Kmax; ++j) {
+      const int a = sp[j];
+      if (a >= 0) v = fmaf(cp[j], __ldg(D0 + (int64_t)a * N0 + n), v);
+    }
     xs[q * ldp + n] = v;
   }
   __syncthreads();
@@ -421,11 +479,11 @@ static int max_cover(int E, int P, int stride, int n, int T) {
 }
 
 struct AggTile {
-  int TY = 0, TX = 0, ldp = 0;
+  int TY = 0, TX = 0, ldp = 0, nq = 0;
   size_t smem = 0;
 };
 
-static bool agg_tile_plan(const GeomDev &g, int N0, AggTile &p) {
+static bool agg_tile_plan(const GeomDev &g, int N0, int Kmax, AggTile &p) {
   constexpr size_t kSmemCap = 113 * 1024;  // two CTAs per SM
   static const int tiles[][2] = {{16, 32}, {8, 32}, {4, 32}, {8, 16}, {4, 16}, {4, 8}, {2, 8}};
   p.ldp = N0 + (((g.stride - N0) % 32) + 32) % 32;
@@ -433,16 +491,16 @@ static bool agg_tile_plan(const GeomDev &g, int N0, AggTile &p) {
   for (const auto &t : tiles) {
     p.TY = t[0];
     p.TX = t[1];
-    p.smem = sizeof(float) * (size_t)p.ldp * max_cover(g.H, g.P, g.stride, g.ny, p.TY) *
-             max_cover(g.W, g.P, g.stride, g.nx, p.TX);
+    p.nq = max_cover(g.H, g.P, g.stride, g.ny, p.TY) * max_cover(g.W, g.P, g.stride, g.nx, p.TX);
+    p.smem = sizeof(float) * (size_t)p.nq * (p.ldp + 2 * Kmax);
     if (p.smem <= kSmemCap) return true;
   }
   return false;
 }
 
-bool aggregate_tiled_fits(const GeomDev &g, int N0) {
+bool aggregate_tiled_fits(const GeomDev &g, int N0, int Kmax) {
   AggTile p;
-  return agg_tile_plan(g, N0, p);
+  return agg_tile_plan(g, N0, Kmax, p);
 }
 
 bool launch_aggregate_tiled(const GeomDev &g, const float *D0, int N0, const int32_t *support, const float *coef,
@@ -450,12 +508,12 @@ bool launch_aggregate_tiled(const GeomDev &g, const float *D0, int N0, const int
                             cudaStream_t s) {
   if ((int64_t)g.Ly * g.Lx * g.H * g.W == 0) return true;
   AggTile p;
-  if (!agg_tile_plan(g, N0, p)) return false;
+  if (!agg_tile_plan(g, N0, Kmax, p)) return false;
   if (p.smem > 48 * 1024)
     cudaFuncSetAttribute(agg_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
   const dim3 grid((unsigned)((g.W + p.TX - 1) / p.TX), (unsigned)((g.H + p.TY - 1) / p.TY));
   agg_tile_kernel<<<grid, 512, p.smem, s>>>(g, D0, N0, support, coef, k_eff, Kmax, cover_y, cover_x, p.TY, p.TX,
-                                             p.ldp, img);
+                                             p.ldp, p.nq, img);
   return true;
 }
 
@@ -470,6 +528,14 @@ void launch_effective_dict_pp(const GeomDev &g, const uint8_t *pc, int level, co
   const int64_t n = B * T * (int64_t)(g.P * g.P);
   if (n == 0) return;
   effective_dict_pp_kernel<<<blocks(n, 256), 256, 0, s>>>(g, pc, level, D, T, N, A, B);
+}
+
+void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
+                          const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int32_t *child_off,
+                          const int32_t *child_idx, int cap, int64_t B, float *Ac, float *invc, cudaStream_t s) {
+  if (B == 0) return;
+  pp_candidates_kernel<<<blocks(B * 32, 256), 256, 0, s>>>(g, pc, level, D, N, M, omega_up, ldo_up, keff_up,
+                                                          child_off, child_idx, cap, B, Ac, invc);
 }
 
 void launch_inv_row_norms(const float *A, int64_t rows, int M, float *inv, unsigned int *scratch, cudaStream_t s) {

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmA, int Mp, int T,
                 int nt, int idx_bits, int64_t row0, int64_t n, const int32_t *__restrict__ ids,
                 const uint8_t *__restrict__ flags, int32_t *__restrict__ cand, unsigned long long *err,
-                const float *__restrict__ pinv) {
+                const float *__restrict__ pinv, int tiles_per_split, uint32_t *__restrict__ part) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const TcLayout lay = tc_layout(Mp, nt);
@@ -194,7 +194,10 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tile0 = (int64_t)blockIdx.x * TC_M;
-  const int n_at = (T + nt - 1) / nt;
+  // this CTA's atom tiles: [j0, j0 + n_at) of the dictionary's ceil(T / nt)
+  const int j0 = blockIdx.y * tiles_per_split;
+  const int n_all = (T + nt - 1) / nt;
+  const int n_at = min(tiles_per_split, n_all - j0);
   const uint32_t ncols = 2u * (uint32_t)nt;
 
   if (threadIdx.x == 0) {
@@ -236,7 +239,7 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
         if (!ok) break;
         const int j = t / lay.kb, kb = t - j * lay.kb;
         mbar_expect_tx(full + s, (uint32_t)lay.a_bytes);
-        tma_load_2d(a_stage + s * lay.a_bytes, &tmA, kb * 64, j * nt, full + s);
+        tma_load_2d(a_stage + s * lay.a_bytes, &tmA, kb * 64, (j0 + j) * nt, full + s);
         ++issued[s];
       }
       // drain: the last load of each stage and the residual tile have landed
@@ -298,7 +301,7 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
         tmem_ld32_nowait(taddr, v);
         tmem_ld32_nowait(taddr + 32, v + 32);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int base = j * nt + half * hcols + c0;
+        const int base = (j0 + j) * nt + half * hcols + c0;
         const uint32_t c = imask - (uint32_t)base;
         if (pinv) {
 #pragma unroll
@@ -338,7 +341,13 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
     if (half == 0 && ok && wi < n) {
       for (int q = 0; q < 4; ++q) top4_insert(merge[row * 4 + q], a0, a1, a2, a3);
       const int64_t b = ids ? ids[wi] : wi;
-      if (!(flags[b] & 1)) {
+      if (part) {  // atom range split across CTAs: partial top 4, merged by proxy_merge_kernel
+        uint32_t *pp = part + (wi * gridDim.y + blockIdx.y) * 4;
+        pp[0] = a0;
+        pp[1] = a1;
+        pp[2] = a2;
+        pp[3] = a3;
+      } else if (!(flags[b] & 1)) {
         const uint32_t ks[4] = {a0, a1, a2, a3};
 #pragma unroll
         for (int q = 0; q < kTopP; ++q)
@@ -351,6 +360,23 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
   tc_fence_after();
   if (warp == 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+}
+
+// Top 4 of the S partial top-4 lists of every patch (atom range split).
+__global__ void proxy_merge_kernel(const uint32_t *__restrict__ part, int S, int idx_bits, int64_t n,
+                                   const int32_t *__restrict__ ids, const uint8_t *__restrict__ flags,
+                                   int32_t *__restrict__ cand) {
+  const int64_t wi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (wi >= n) return;
+  const int64_t b = ids ? ids[wi] : wi;
+  if (flags[b] & 1) return;
+  uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+  const uint32_t *pp = part + wi * S * 4;
+  for (int i = 0; i < 4 * S; ++i) top4_insert(pp[i], a0, a1, a2, a3);
+  const uint32_t imask = (1u << idx_bits) - 1u;
+  const uint32_t ks[4] = {a0, a1, a2, a3};
+#pragma unroll
+  for (int q = 0; q < kTopP; ++q) cand[b * kTopP + q] = (q < 4 && ks[q]) ? (int)(imask - (ks[q] & imask)) : -1;
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -398,9 +424,24 @@ bool proxy_bf16_supported(int M, int T) {
   return M > 0 && Mp <= 512 && T > 0 && T <= (1 << 15) && encode_fn() != nullptr;
 }
 
+int proxy_bf16_splits(int64_t n, int T) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  }
+  const int64_t tiles = (n + TC_M - 1) / TC_M;
+  const int n_at = (T + tile_atoms(0) - 1) / tile_atoms(0);
+  if (tiles >= 2 * sms || n_at < 2) return 1;
+  // about two CTAs per SM: split the atom tiles over S CTAs per patch tile
+  const int S = (int)((2 * sms + tiles - 1) / tiles);
+  return S < n_at ? S : n_at;
+}
+
 bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, const __nv_bfloat16 *Abf, int T,
                        int64_t row0, const int32_t *ids, int64_t n, const uint8_t *flags, int32_t *cand,
-                       unsigned long long *err, const float *pinv, cudaStream_t s) {
+                       unsigned long long *err, const float *pinv, uint32_t *part, cudaStream_t s) {
   if (n == 0) return true;
   const int nt = tile_atoms(Mp);
   CUtensorMap mR, mA;
@@ -415,10 +456,16 @@ bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, con
       return false;
     configured = sm;
   }
-  const unsigned grid = (unsigned)((n + TC_M - 1) / TC_M);
   int idx_bits = 1;
   while ((1 << idx_bits) < T) ++idx_bits;  // atom index field of the packed keys
-  proxy_tc_kernel<<<grid, TC_THREADS, sm, s>>>(mR, mA, Mp, T, nt, idx_bits, row0, n, ids, flags, cand, err, pinv);
+  const int n_all = (T + nt - 1) / nt;
+  const int S = part ? proxy_bf16_splits(n, T) : 1;
+  const int tps = (n_all + S - 1) / S;
+  const dim3 grid((unsigned)((n + TC_M - 1) / TC_M), (unsigned)((n_all + tps - 1) / tps));
+  proxy_tc_kernel<<<grid, TC_THREADS, sm, s>>>(mR, mA, Mp, T, nt, idx_bits, row0, n, ids, flags, cand, err, pinv,
+                                               tps, grid.y > 1 ? part : nullptr);
+  if (grid.y > 1)
+    proxy_merge_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, (int)grid.y, idx_bits, n, ids, flags, cand);
   return true;
 }
 

@@ -34,6 +34,8 @@ struct Model {
   csp_solve_params params{};
   int M = 0, N0 = 0, planes = 0, PP = 0;
   size_t bytes_per_patch = 0;
+  size_t pp_bytes = 0;       // coded exposure: per-patch effective dictionaries and norms, all levels
+  int64_t pp_slice = 0;      // ... built for at most this many patches at a time
 };
 
 struct Job {
@@ -128,9 +130,21 @@ size_t model_patch_bytes(const Model &m) {
     b += (size_t)(tri(K) + K) * 4 + (size_t)K * 9 + 1;
     b += (size_t)c->lv[l].N * 4;            // downsampled y (Phi = I) or lifted residual
   }
-  if (m.sense_kind == CSP_SENSE_CODED_EXPOSURE) {
-    b += (size_t)m.planes * m.PP;           // code block
-    for (int l = 0; l < m.geom.n_levels; ++l) b += (size_t)c->lv[l].T * ((size_t)m.M + 1) * 4;
+  if (m.sense_kind == CSP_SENSE_CODED_EXPOSURE) b += (size_t)m.planes * m.PP;  // code block
+  return b;
+}
+
+// Coded exposure: bytes of one patch's effective dictionary (and norms) of the
+// full-dictionary level, plus the candidate rows of the restricted levels.
+size_t model_pp_bytes(const Model &m) {
+  if (m.sense_kind != CSP_SENSE_CODED_EXPOSURE) return 0;
+  const csp_solve_params &p = m.params;
+  const int nl = p.mode == CSP_MODE_PLAIN ? 1 : m.geom.n_levels;
+  const LevelData &LT = m.ctx->lv[nl - 1];
+  size_t b = ((size_t)LT.T * m.M + LT.T) * 4 + 512;
+  for (int l = 0; l + 1 < nl; ++l) {
+    const int cap = std::max(1, m.ctx->lv[l].max_children * (p.K[l + 1] > 0 ? p.K[l + 1] : p.Kmax));
+    b += ((size_t)cap * m.M + cap) * 4 + 32;
   }
   return b;
 }
@@ -157,15 +171,15 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
   const size_t o_coef = dv.take<float>((size_t)Bt * Kmax);
   const size_t o_keff = dv.take<int8_t>((size_t)Bt);
   bool tiled = true;  // fused synthesis + overlap-add needs no scratch
-  for (Job *j : sl.jobs) tiled &= aggregate_tiled_fits(j->gd, m.N0);
+  for (Job *j : sl.jobs) tiled &= aggregate_tiled_fits(j->gd, m.N0, Kmax);
   const size_t o_xh = dv.take<float>(tiled ? 0 : (size_t)Bmax * m.N0);
   const size_t o_pc = ce ? dv.take<uint8_t>((size_t)Bt * codes_pp) : 0;
-  size_t o_A[CSP_MAX_LEVELS] = {}, o_inv[CSP_MAX_LEVELS] = {};
-  if (ce)
-    for (int l = 0; l < m.geom.n_levels; ++l) {
-      o_A[l] = dv.take<float>((size_t)Bt * m.ctx->lv[l].T * m.ctx->lv[l].M);
-      o_inv[l] = dv.take<float>((size_t)Bt * m.ctx->lv[l].T);
-    }
+  // coded exposure: the per-patch effective dictionaries of the full-dictionary
+  // level exist for one slice of at most m.pp_slice patches at a time
+  const int top = m.params.mode == CSP_MODE_PLAIN ? 0 : m.geom.n_levels - 1;
+  const int64_t slice = ce ? std::min<int64_t>(Bt, m.pp_slice) : 0;
+  const size_t o_A = ce ? dv.take<float>((size_t)slice * m.ctx->lv[top].T * m.ctx->lv[top].M) : 0;
+  const size_t o_inv = ce ? dv.take<float>((size_t)slice * m.ctx->lv[top].T) : 0;
   const size_t o_scr = dv.take<unsigned int>(4);
   const size_t o_ids = dv.take<int32_t>((size_t)Bt), h_ids = hs.take<int32_t>((size_t)Bt);
   struct JobLayout { size_t d_meas, d_codes, d_img, d_cov, h_meas, h_codes, h_img, h_cov; };
@@ -243,16 +257,24 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
     ps.phase_ids = (const int32_t *)dp(o_ids);
   }
   if (ce) {
-    ps.pcodes = dp(o_pc);
-    for (int l = 0; l < m.geom.n_levels; ++l) {
-      ps.A_pp[l] = (float *)dp(o_A[l]);
-      ps.inv_pp[l] = (float *)dp(o_inv[l]);
+    // slice by slice: per-patch operators, then the solve of those patches
+    for (int64_t off = 0; off < Bt; off += slice) {
+      PatchSet pss;
+      pss.B = std::min(slice, Bt - off);
+      pss.pcodes = dp(o_pc) + off * codes_pp;
+      pss.A_pp[top] = (float *)dp(o_A);
+      pss.inv_pp[top] = (float *)dp(o_inv);
+      if (build_patch_dicts_for(m.ctx, top, pss.pcodes, pss.B, pss.A_pp[top], pss.inv_pp[top],
+                                (unsigned int *)dp(o_scr), s) != CSP_OK)
+        return cudaErrorUnknown;
+      if (solve_patchset(m.ctx, pss, sl.W, &m.params, Y + off * m.M, sup + off * Kmax, coef + off * Kmax,
+                         keff + off, s) != CSP_OK)
+        return cudaErrorUnknown;
     }
-    if (build_patch_dicts_for(m.ctx, ps.pcodes, Bt, ps.A_pp, ps.inv_pp, (unsigned int *)dp(o_scr), s) != CSP_OK)
-      return cudaErrorUnknown;
+  } else if (solve_patchset(m.ctx, ps, sl.W, &m.params, Y, sup, coef, keff, s) != CSP_OK) {
+    // one solve over every patch of the batch
+    return cudaErrorUnknown;
   }
-  // one solve over every patch of the batch
-  if (solve_patchset(m.ctx, ps, sl.W, &m.params, Y, sup, coef, keff, s) != CSP_OK) return cudaErrorUnknown;
   // outputs: overlap-add and copy-out job by job
   for (size_t k = 0; k < sl.jobs.size(); ++k) {
     Job *j = sl.jobs[k];
@@ -270,13 +292,12 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
 }
 
 // Called with the server lock held, after the batch's work has completed
-// (or failed and its stream was synchronized).
+// (or failed and its stream was synchronized) and its images were copied out.
 void release_batch(csp_server *srv, Slot &sl, csp_status st) {
   if (sl.dev) cudaFreeAsync(sl.dev, sl.stream);
   sl.dev = nullptr;
   const double t = now_s();
   for (Job *j : sl.jobs) {
-    if (st == CSP_OK && j->image_host && j->h_img) std::memcpy(j->image_host, j->h_img, j->img_floats * 4);
     j->h_img = nullptr;
     j->codes.clear();
     j->codes.shrink_to_fit();
@@ -300,6 +321,14 @@ void scheduler(csp_server *srv) {
       if (!sl.busy) continue;
       const cudaError_t q = cudaEventQuery(sl.ev);
       if (q == cudaErrorNotReady) continue;
+      if (q == cudaSuccess) {
+        // images from the pinned staging area to the callers' buffers, without
+        // the lock (the slot stays busy and its jobs not done meanwhile)
+        lk.unlock();
+        for (Job *j : sl.jobs)
+          if (j->image_host && j->h_img) std::memcpy(j->image_host, j->h_img, j->img_floats * 4);
+        lk.lock();
+      }
       release_batch(srv, sl, q == cudaSuccess ? CSP_OK : CSP_ERR_CUDA);
       if (q != cudaSuccess) srv->err = std::string("batch failed: ") + cudaGetErrorString(q);
       progressed = true;
@@ -469,6 +498,11 @@ csp_status csp_server_add_model(csp_server *srv, const csp_model_desc *d, int *m
   m.planes = planes;
   m.PP = g.P * g.P;
   m.bytes_per_patch = model_patch_bytes(m);
+  m.pp_bytes = model_pp_bytes(m);
+  if (m.pp_bytes) {
+    const size_t slice_bytes = std::max<size_t>(size_t(512) << 20, srv->budget / 4);
+    m.pp_slice = std::max<int64_t>(1, (int64_t)(slice_bytes / m.pp_bytes));
+  }
   std::lock_guard<std::mutex> lk(srv->mu);
   srv->models.push_back(m);
   *model_id = (int)srv->models.size() - 1;
@@ -506,7 +540,8 @@ csp_status csp_submit(csp_server *srv, const csp_job_desc *jd, uint64_t *job_id)
   j->meas_floats = m.sense_kind == CSP_SENSE_IDENTITY ? (size_t)m.planes * HW : HW;
   j->img_floats = (size_t)m.planes * HW;
   if (m.sense_kind == CSP_SENSE_CODED_EXPOSURE) j->codes.assign(jd->codes_host, jd->codes_host + (size_t)m.planes * HW);
-  j->bytes = (size_t)j->B * m.bytes_per_patch + (j->meas_floats + j->img_floats) * 4 + j->codes.size() +
+  j->bytes = (size_t)j->B * m.bytes_per_patch + (size_t)std::min<int64_t>(j->B, m.pp_slice) * m.pp_bytes +
+             (j->meas_floats + j->img_floats) * 4 + j->codes.size() +
              (size_t)(jd->H + jd->W) * 8 + 4096;
   if (j->bytes > srv->budget) {
     delete j;

@@ -52,6 +52,16 @@ def test_mixed_batch_equals_alone(name, kw, prec):
         assert info["t_submit"] <= info["t_admit"] <= info["t_done"]
 
 
+def test_video_job_in_slices_equals_alone():
+    # 3,969 patches with ~350 KB of per-patch operators each: the server builds
+    # them for one 512 MiB slice (~1,500 patches) at a time
+    w = _w("video", 256, 256, seed=3, T0=1024)
+    with Server(0, mem_budget_bytes=1 << 30) as srv:
+        mid = srv.add_workload_model(w, "cross_scale", "fp32")
+        img = srv.result(srv.submit(mid, w.meas, 256, 256, codes=w.sensing.codes), 120).copy()
+    assert np.array_equal(img, _alone(w, "cross_scale", "fp32"))
+
+
 def test_two_models_interleaved():
     wd = [_w("denoise", 64, 64, seed=s) for s in (1, 2, 3)]
     wb = [_w("bayer", 64, 64, seed=s) for s in (4, 5, 6)]
