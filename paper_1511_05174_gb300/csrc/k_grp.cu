@@ -267,7 +267,7 @@ omp_update_wave_kernel(const float *__restrict__ Y, int M, const float *__restri
 #pragma unroll
     for (int t = 0; t < KPL; ++t) {
       const int j = s + G * t;
-      vr[t] = (f32b && j < k) ? __ldg(gram + (int64_t)omr[t] * T + q) : 0.f;
+      vr[t] = (f32b && j < k) ? __ldg(gram + (int64_t)q * T + omr[t]) : 0.f;  // row q (G symmetric)
     }
 #pragma unroll
     for (int t = 0; t < KPL; ++t) {
@@ -484,6 +484,14 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
         }
     __syncwarp();
     const int qs = act ? S.misc[1] : 0;
+    // G[q][c] for the first 8G candidates (row q: G is symmetric), issued now so
+    // that the L2 round trip overlaps the projection; cached as column k below
+    float gpre[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = s + u * G;
+      gpre[u] = (act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
+    }
     const bool f32 = act && !(fl & 2);
     if (f32)
       for (int j = s; j < k; j += G) S.V[j] = Gc[j * ldg + qs];
@@ -583,13 +591,18 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
     if (appended && !exact) rsq = est;
     if (act) {
       if (appended) {
-        // cache G[c][q] for every candidate (one load wave) as column k
-        for (int c0 = s; c0 < nc; c0 += 8 * G) {
+        // cache G[c][q] for every candidate as column k (the first 8G prefetched)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = s + u * G;
+          if (c < nc) Gc[k * ldg + c] = gpre[u];
+        }
+        for (int c0 = s + 8 * G; c0 < nc; c0 += 8 * G) {
           float gr[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int c = c0 + u * G;
-            gr[u] = (c < nc) ? __ldg(gram + (int64_t)S.cs[c] * T + q) : 0.f;
+            gr[u] = (c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u) {

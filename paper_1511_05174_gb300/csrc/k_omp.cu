@@ -66,7 +66,7 @@ __device__ bool grp_append(bool act, int s, int M, const float *aqp, const float
   const float aa = gram ? (act ? __ldg(gram + (int64_t)q * T + q) : 0.f) : aa_dot;
   if (gram) {
     if (f32)
-      for (int j = s; j < k; j += G) S.V[j] = __ldg(gram + (int64_t)S.om[j] * T + q);
+      for (int j = s; j < k; j += G) S.V[j] = __ldg(gram + (int64_t)q * T + S.om[j]);  // row q (G symmetric)
   } else if (COOP) {
     for (int j = 0; j < kw; ++j) {
       const bool o = f32 && j < k;

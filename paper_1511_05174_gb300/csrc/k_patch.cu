@@ -137,44 +137,57 @@ __global__ void effective_dict_pp_kernel(GeomDev g, const uint8_t *__restrict__ 
 }
 
 // Candidate rows of per-pixel coded exposure at a restricted level: one warp
-// per patch enumerates f(Omega_up) in the order of the restricted kernels
-// (parents in support order, each parent's children in link order, at most
-// cap) and writes a_c[m] = sum_t pc_p[t][m] d_c[level index of (t, m)] --
-// the arithmetic of effective_dict_pp_kernel -- and 1/||a_c|| (-1 for a zero
-// row), the norm reduced as in row_norms_kernel.
+// per (patch, candidate position c).  The warp locates position c in f(Omega_up)
+// in the order of the restricted kernels (parents in support order, each
+// parent's children in link order, at most cap), then writes
+// a_c[m] = sum_t pc_p[t][m] d_c[level index of (t, m)] -- the arithmetic of
+// effective_dict_pp_kernel -- and 1/||a_c|| (-1 for a zero row), the norm
+// reduced as in row_norms_kernel.
 __global__ void pp_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const float *__restrict__ D,
                                      int N, int M, const int32_t *__restrict__ omega_up, int ldo_up,
                                      const int8_t *__restrict__ keff_up, const int32_t *__restrict__ child_off,
                                      const int32_t *__restrict__ child_idx, int cap, int64_t B,
                                      float *__restrict__ Ac, float *__restrict__ invc) {
   const int lane = threadIdx.x & 31;
-  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (b >= B) return;
-  const int F = g.Lx;
-  const uint8_t *c = pc + b * (int64_t)F * M;
-  float *Ab = Ac + b * (int64_t)cap * M;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= B * cap) return;
+  const int64_t b = w / cap;
+  const int c = (int)(w - b * cap);
+  // child counts of the parents (lane j: parent j), inclusive prefix sum
   const int kup = keff_up[b];
-  int nc = 0;
-  for (int j = 0; j < kup && nc < cap; ++j) {
-    const int p = omega_up[b * ldo_up + j];
-    const int c0 = child_off[p], c1 = child_off[p + 1];
-    for (int i = 0; i < c1 - c0 && nc < cap; ++i, ++nc) {
-      const float *d = D + (int64_t)child_idx[c0 + i] * N;
-      float sq = 0.f;
-      for (int m = lane; m < M; m += 32) {
-        const int py = m / g.P, px = m - py * g.P;
-        float v = 0.f;
-        for (int t = 0; t < F; ++t)
-          if (c[t * M + m]) v += __ldg(d + level_index(g, l, 0, t, py, px));
-        Ab[(int64_t)nc * M + m] = v;
-        sq = fmaf(v, v, sq);
-      }
-      for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-      if (lane == 0) {
-        const float nrm = sqrtf(sq);
-        invc[b * cap + nc] = nrm > 0.f ? 1.f / nrm : -1.f;
-      }
-    }
+  int c0 = 0, cnt = 0;
+  if (lane < kup) {
+    const int p = omega_up[b * ldo_up + lane];
+    c0 = child_off[p];
+    cnt = child_off[p + 1] - c0;
+  }
+  int incl = cnt;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  // the parent holding position c: first lane with incl > c
+  const unsigned hit = __ballot_sync(0xffffffffu, lane < kup && incl > c);
+  if (!hit) return;  // c >= |f(Omega_up)|: no such candidate
+  const int j = __ffs(hit) - 1;
+  const int base = __shfl_sync(0xffffffffu, c0, j), before = __shfl_sync(0xffffffffu, incl - cnt, j);
+  const float *d = D + (int64_t)child_idx[base + (c - before)] * N;
+  const uint8_t *cb = pc + b * (int64_t)g.Lx * M;
+  float *row = Ac + w * M;
+  const int F = g.Lx;
+  float sq = 0.f;
+  for (int m = lane; m < M; m += 32) {
+    const int py = m / g.P, px = m - py * g.P;
+    float v = 0.f;
+    for (int t = 0; t < F; ++t)
+      if (cb[t * M + m]) v += __ldg(d + level_index(g, l, 0, t, py, px));
+    row[m] = v;
+    sq = fmaf(v, v, sq);
+  }
+  for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+  if (lane == 0) {
+    const float nrm = sqrtf(sq);
+    invc[w] = nrm > 0.f ? 1.f / nrm : -1.f;
   }
 }
 
@@ -353,7 +366,7 @@ __global__ void gather_kernel(GeomDev g, const float *__restrict__ Xh, int N0,
 // that fall inside the tile; phase 2 averages, per pixel, over its covering
 // patches in patch raster order.  The arithmetic and its order are those of
 // synth_kernel + gather_kernel, so both paths give identical images.
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(512, 2)
 agg_tile_kernel(GeomDev g, const float *__restrict__ D0, int N0, const int32_t *__restrict__ support,
                 const float *__restrict__ coef, const int8_t *__restrict__ k_eff, int Kmax,
                 const int32_t *__restrict__ cover_y, const int32_t *__restrict__ cover_x, int TY, int TX, int ldp,
@@ -375,21 +388,47 @@ agg_tile_kernel(GeomDev g, const float *__restrict__ D0, int N0, const int32_t *
     s_coef[e] = on ? coef[b * Kmax + j] : 0.f;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < nq * N0; e += blockDim.x) {
-    const int q = e / N0, n = e - q * N0;
-    const int r = n % PP, py = r / g.P, px = r - py * g.P;
-    const int y = origin(iy0 + q / nxc, g.stride, g.H, g.P) + py;
-    const int x = origin(ix0 + q % nxc, g.stride, g.W, g.P) + px;
-    if (y < ty0 || y >= ty1 || x < tx0 || x >= tx1) continue;  // outside the tile: never read
-    const int *sp = s_sup + q * Kmax;
-    const float *cp = s_coef + q * Kmax;
-    float v = 0.f;
-#pragma unroll 8
-    for (int j = 0; j < Kmax; ++j) {
-      const int a = sp[j];
-      if (a >= 0) v = fmaf(cp[j], __ldg(D0 + (int64_t)a * N0 + n), v);
+  // U elements per thread and JB atoms at a time: U * JB independent loads in flight
+  constexpr int U = 2, JB = 4;
+  const int total = nq * N0;
+  for (int e0 = threadIdx.x; e0 < total; e0 += U * blockDim.x) {
+    int qo[U], no[U];
+    bool on[U];
+    float v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + u * blockDim.x;
+      const int q = e / N0, n = e - q * N0;
+      const int r = n % PP, py = r / g.P, px = r - py * g.P;
+      const int y = origin(iy0 + q / nxc, g.stride, g.H, g.P) + py;
+      const int x = origin(ix0 + q % nxc, g.stride, g.W, g.P) + px;
+      on[u] = e < total && y >= ty0 && y < ty1 && x >= tx0 && x < tx1;  // outside the tile: never read
+      qo[u] = on[u] ? q : 0;
+      no[u] = n;
+      v[u] = 0.f;
     }
-    xs[q * ldp + n] = v;
+    for (int j0 = 0; j0 < Kmax; j0 += JB) {
+      float dv[U][JB], cv[U][JB];
+      unsigned used = 0u;  // bit u * JB + jj: atom j0 + jj exists for element u
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+          const int j = j0 + jj;
+          const int a = (on[u] && j < Kmax) ? s_sup[qo[u] * Kmax + j] : -1;
+          cv[u][jj] = a >= 0 ? s_coef[qo[u] * Kmax + j] : 0.f;
+          dv[u][jj] = a >= 0 ? __ldg(D0 + (int64_t)a * N0 + no[u]) : 0.f;
+          if (a >= 0) used |= 1u << (u * JB + jj);
+        }
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj)
+          if (used & (1u << (u * JB + jj))) v[u] = fmaf(cv[u][jj], dv[u][jj], v[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (on[u]) xs[qo[u] * ldp + no[u]] = v[u];
   }
   __syncthreads();
   const int planes = g.Ly * g.Lx, th = ty1 - ty0, tw = tx1 - tx0;
@@ -534,8 +573,8 @@ void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const 
                           const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int32_t *child_off,
                           const int32_t *child_idx, int cap, int64_t B, float *Ac, float *invc, cudaStream_t s) {
   if (B == 0) return;
-  pp_candidates_kernel<<<blocks(B * 32, 256), 256, 0, s>>>(g, pc, level, D, N, M, omega_up, ldo_up, keff_up,
-                                                          child_off, child_idx, cap, B, Ac, invc);
+  pp_candidates_kernel<<<blocks(B * cap * 32, 256), 256, 0, s>>>(g, pc, level, D, N, M, omega_up, ldo_up, keff_up,
+                                                                child_off, child_idx, cap, B, Ac, invc);
 }
 
 void launch_inv_row_norms(const float *A, int64_t rows, int M, float *inv, unsigned int *scratch, cudaStream_t s) {

@@ -40,7 +40,7 @@ from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
-WORKLOAD_NAMES = ("denoise", "bayer", "video", "lightfield")
+WORKLOAD_NAMES = ("denoise", "bayer", "video", "lightfield", "inpaint")
 
 # Stream indices of the seed sequence; one independent stream per ingredient.
 _S_DICT, _S_SUBSET, _S_SUPPORT, _S_VALUES, _S_NOISE, _S_CODES, _S_KPATCH, _N_STREAMS = range(8)
@@ -260,6 +260,12 @@ def _presets(name: str, links: str):
         geo = dict(kind="lightfield", H=256, W=256, plane_grid=(4, 4), P=8, stride=4,
                    level_factors=[(1, 1, 1, 1), (2, 2, 1, 1), (2, 2, 2, 2)])
         return geo, 8192, None, 0.005, "coded_aperture"
+    if name == "inpaint":
+        # grayscale image with a random half of the pixels kept (N/M = 2): the
+        # per-pixel retention mask is a one-frame coded exposure y = c * x
+        geo = dict(kind="image", H=512, W=512, plane_grid=(1, 1), P=8, stride=4,
+                   level_factors=[(1, 1, 1, 1), (1, 1, 2, 2)])
+        return geo, 1024, [8, 4] if links == "paper" else [8, 8], 0.005, "coded_exposure"
     raise ValueError(f"unknown workload {name!r}; expected one of {WORKLOAD_NAMES}")
 
 

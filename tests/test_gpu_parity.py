@@ -25,6 +25,7 @@ SMALL = {
     "bayer": dict(name="bayer", H=64, W=64),
     "lightfield": dict(name="lightfield", H=48, W=48, T0=2048),
     "video": dict(name="video", H=48, W=48, T0=1024),
+    "inpaint": dict(name="inpaint", H=64, W=56, T0=512),
 }
 
 
@@ -74,7 +75,7 @@ def test_cross_scale_parity(key, links, prec):
     assert g["stats"]["overflow"] == 0
 
 
-@pytest.mark.parametrize("key", ["denoise", "bayer", "lightfield", "video"])
+@pytest.mark.parametrize("key", ["denoise", "bayer", "lightfield", "video", "inpaint"])
 def test_aggregate_matches_oracle(key):
     """Overlap-add of the GPU's own codes against the oracle's aggregation of
     the same codes."""

@@ -223,7 +223,7 @@ def test_patch_origins_ragged_tail():
     assert synthetic.patch_count_1d(10, 4, 4) == 3
 
 
-@pytest.mark.parametrize("name", ["denoise", "bayer", "video", "lightfield"])
+@pytest.mark.parametrize("name", ["denoise", "bayer", "video", "lightfield", "inpaint"])
 def test_WU_identity_and_nearest_neighbour(name):
     """W U = I on R^{N_low} (Sec. III-C), U replicates each coarse entry."""
     w = synthetic.make_workload(name, H=16, W=16, T0=64)
@@ -238,7 +238,7 @@ def test_WU_identity_and_nearest_neighbour(name):
         assert np.count_nonzero(u) == g.level_dim(0) // Nl and set(np.unique(u)) == {0.0, 1.0}
 
 
-@pytest.mark.parametrize("name", ["denoise", "bayer", "video", "lightfield"])
+@pytest.mark.parametrize("name", ["denoise", "bayer", "video", "lightfield", "inpaint"])
 def test_extraction_matches_camera_model(name):
     """Noiseless: the extracted patch equals Phi_p applied to the ground-truth
     patch (y = Phi x, Sec. III-C).  The camera simulation lives in the input
@@ -251,6 +251,21 @@ def test_extraction_matches_camera_model(name):
         x = w.truth[:, oy[b]:oy[b] + g.P, ox[b]:ox[b] + g.P].reshape(1, -1)
         np.testing.assert_allclose(oracle.phi_apply(w.sensing, g, int(oy[b]), int(ox[b]), x)[0], Y[b],
                                    rtol=1e-6, atol=1e-6)
+
+
+def test_inpainting_operator_keeps_the_retained_pixels():
+    """Random pixel retention (the paper's inpainting task, Sec. IV): the
+    operator of a patch is the diagonal 0/1 mask of its retained pixels, so
+    every effective atom is the atom with the removed pixels set to zero and
+    OMP's angle score uses the norm over the retained pixels only."""
+    w = synthetic.make_workload("inpaint", H=16, W=16, T0=64)
+    g = w.geometry
+    oy, ox = oracle.patch_grid(g)
+    for b in range(0, len(oy), 5):
+        Phi = oracle.sensing_matrix(w.sensing, g, int(oy[b]), int(ox[b]))
+        mask = w.sensing.codes[0, oy[b]:oy[b] + g.P, ox[b]:ox[b] + g.P].reshape(-1).astype(float)
+        np.testing.assert_array_equal(Phi, np.diag(mask))
+    assert 0.4 < w.sensing.codes.mean() < 0.6  # N/M = 2
 
 
 def test_bayer_matrix_rows_are_rggb_selectors():
