@@ -336,18 +336,22 @@ omp_update_wave_kernel(const float *__restrict__ Y, int M, const float *__restri
 // when the estimate falls under 1e-5 ||y||^2 the residual is formed
 // explicitly from the chosen rows.  Per iteration the only global loads are
 // G[c][q] for the candidates (one wave).
-// Per-group shared memory: GrpSmem | p0[cap] | gdiag[cap] | Gc[cap][Kb] |
-// p0 of the chosen [Kb] | parent scratch [2][CSP_MAX_K].
+// Per-group shared memory: GrpSmem | p0[cap] | Gc[cap][Kb] (its first 64 words
+// hold the parents' child ranges while the candidate list is built) | p0 of
+// the chosen [Kb].
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ int gram_ld(int cap) { return (cap + 3) & ~3; }  // Gc column stride
+__host__ __device__ __forceinline__ int gram_gc_floats(int Kb, int cap) {
+  const int f = gram_ld(cap) * Kb;
+  return f > 2 * CSP_MAX_K ? f : 2 * CSP_MAX_K;
+}
 __host__ __device__ __forceinline__ int gram_group_bytes(int Kb, int cap) {
-  const int bytes = grp_smem_bytes(Kb, cap) + 2 * up16(4 * cap) + 4 * gram_ld(cap) * Kb + up16(4 * Kb) +
-                    8 * CSP_MAX_K;
+  const int bytes = grp_smem_bytes(Kb, cap) + up16(4 * cap) + 4 * gram_gc_floats(Kb, cap) + up16(4 * Kb);
   return (bytes + 127) / 128 * 128 + 16;  // groups start on different bank offsets
 }
 
 template <int G, int NCH>
-__global__ void __launch_bounds__(WV_WARPS * 32)
+__global__ void __launch_bounds__(WV_WARPS * 32, 5)
 omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                            const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
                            const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx,
@@ -367,11 +371,10 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
   const GrpSmem S = carve(gbase, Kb, cap);
   char *q_ = gbase + grp_smem_bytes(Kb, cap);
   float *p0 = reinterpret_cast<float *>(q_); q_ += up16(4 * cap);
-  float *gdiag = reinterpret_cast<float *>(q_); q_ += up16(4 * cap);
-  float *Gc = reinterpret_cast<float *>(q_); q_ += 4 * gram_ld(cap) * Kb;  // Gc[j * ldg + c]
+  float *Gc = reinterpret_cast<float *>(q_); q_ += 4 * gram_gc_floats(Kb, cap);  // Gc[j * ldg + c]
   const int ldg = gram_ld(cap);
-  float *p0c = reinterpret_cast<float *>(q_); q_ += up16(4 * Kb);
-  int *pstart = reinterpret_cast<int *>(q_);
+  float *p0c = reinterpret_cast<float *>(q_);
+  int *pstart = reinterpret_cast<int *>(Gc);  // parents' child ranges, before Gc is used
   int *pbeg = pstart + CSP_MAX_K;
   const int nv = M >> 2;
   const int64_t b = valid ? (ids ? __ldg(ids + wi) : wi) : 0;
@@ -422,20 +425,19 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
   }
   __syncwarp();
   for (int c0 = s; c0 < nc; c0 += 4 * G) {
-    float iv[4], gd[4];
+    float iv[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int c = c0 + u * G;
-      const int a = c < nc ? S.cs[c] : 0;
-      iv[u] = c < nc ? __ldg(inv_norm + a) : -1.f;
-      gd[u] = c < nc ? __ldg(gram + (int64_t)a * T + a) : 0.f;
+      iv[u] = c < nc ? __ldg(inv_norm + S.cs[c]) : -1.f;
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int c = c0 + u * G;
-      if (c < nc) { S.invn[c] = iv[u]; gdiag[c] = gd[u]; }
+      if (c < nc) S.invn[c] = iv[u];
     }
   }
+  __syncwarp();  // the parents' child ranges (aliasing Gc) are no longer read
   // p0 = A_C^T y, RB rows per load wave
   const int ncw = __reduce_max_sync(kFull, nc);
   for (int c0 = 0; c0 < ncw; c0 += RB) {
@@ -492,10 +494,10 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
       const int c = s + u * G;
       gpre[u] = (act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
     }
+    const float aa = act ? __ldg(gram + (int64_t)q * T + q) : 0.f;  // ||a_q||^2
     const bool f32 = act && !(fl & 2);
     if (f32)
       for (int j = s; j < k; j += G) S.V[j] = Gc[j * ldg + qs];
-    const float aa = act ? gdiag[qs] : 0.f;
     const float bq = act ? p0[qs] : 0.f;
     __syncwarp();
     // projection: W = L^{-1} V, pivot, z_k, alpha = L^{-T} z (as in grp_project)

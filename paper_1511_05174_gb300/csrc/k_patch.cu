@@ -360,20 +360,22 @@ __global__ void gather_kernel(GeomDev g, const float *__restrict__ Xh, int N0,
 
 // Fused synthesis + overlap-add over an output tile of TY x TX pixels (all
 // planes).  Phase 0 stages the codes (support, coefficients) of every patch q
-// covering the tile; phase 1 synthesizes x_hat_q = D0 alpha_q into shared
-// memory (rows of ldp floats, ldp = stride mod 32 so that neighbouring pixels,
-// which read neighbouring patches, hit distinct banks), only at the elements
-// that fall inside the tile; phase 2 averages, per pixel, over its covering
-// patches in patch raster order.  The arithmetic and its order are those of
-// synth_kernel + gather_kernel, so both paths give identical images.
+// covering the tile and the (py, px) of every patch element n; phase 1 (a warp
+// per covering patch) synthesizes x_hat_q = D0 alpha_q into shared memory
+// (rows of ldp floats, ldp = stride mod 32 so that neighbouring pixels, which
+// read neighbouring patches, hit distinct banks), only at the elements inside
+// the tile; phase 2 averages, per pixel, over its covering patches in patch
+// raster order.  The arithmetic and its order are those of synth_kernel +
+// gather_kernel, so both paths give identical images.
 __global__ void __launch_bounds__(512, 2)
 agg_tile_kernel(GeomDev g, const float *__restrict__ D0, int N0, const int32_t *__restrict__ support,
                 const float *__restrict__ coef, const int8_t *__restrict__ k_eff, int Kmax,
                 const int32_t *__restrict__ cover_y, const int32_t *__restrict__ cover_x, int TY, int TX, int ldp,
                 int nq_max, float *__restrict__ img) {
-  extern __shared__ float xs[];  // [nq_max][ldp] patches, then [nq_max][Kmax] supports and coefficients
+  extern __shared__ float xs[];  // [nq_max][ldp] patches | [nq_max][Kmax] atoms | [nq_max][Kmax] coefs | [N0] (py, px)
   int *s_sup = reinterpret_cast<int *>(xs + (size_t)nq_max * ldp);
   float *s_coef = reinterpret_cast<float *>(s_sup + nq_max * Kmax);
+  int *s_yx = reinterpret_cast<int *>(s_coef + nq_max * Kmax);
   const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
   const int ty1 = min(ty0 + TY, g.H), tx1 = min(tx0 + TX, g.W);
   const int iy0 = cover_y[2 * ty0], iy1 = cover_y[2 * (ty1 - 1) + 1];
@@ -387,48 +389,39 @@ agg_tile_kernel(GeomDev g, const float *__restrict__ D0, int N0, const int32_t *
     s_sup[e] = on ? support[b * Kmax + j] : -1;
     s_coef[e] = on ? coef[b * Kmax + j] : 0.f;
   }
+  for (int n = threadIdx.x; n < N0; n += blockDim.x) {
+    const int r = n % PP;
+    s_yx[n] = ((r / g.P) << 16) | (r % g.P);
+  }
   __syncthreads();
-  // U elements per thread and JB atoms at a time: U * JB independent loads in flight
-  constexpr int U = 2, JB = 4;
-  const int total = nq * N0;
-  for (int e0 = threadIdx.x; e0 < total; e0 += U * blockDim.x) {
-    int qo[U], no[U];
-    bool on[U];
-    float v[U];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int q = warp; q < nq; q += nwarps) {
+    // the part of patch q inside the tile, in patch coordinates
+    const int oy = origin(iy0 + q / nxc, g.stride, g.H, g.P), ox = origin(ix0 + q % nxc, g.stride, g.W, g.P);
+    const int py0 = ty0 - oy, py1 = ty1 - oy, px0 = tx0 - ox, px1 = tx1 - ox;
+    const int *sp = s_sup + q * Kmax;
+    const float *cp = s_coef + q * Kmax;
+    float *xq = xs + q * ldp;
+    for (int n = lane; n < N0; n += 32) {
+      const int yx = s_yx[n], py = yx >> 16, px = yx & 0xffff;
+      if (py < py0 || py >= py1 || px < px0 || px >= px1) continue;  // outside the tile: never read
+      float v = 0.f;
+      for (int j0 = 0; j0 < Kmax; j0 += 8) {
+        float dv[8];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int e = e0 + u * blockDim.x;
-      const int q = e / N0, n = e - q * N0;
-      const int r = n % PP, py = r / g.P, px = r - py * g.P;
-      const int y = origin(iy0 + q / nxc, g.stride, g.H, g.P) + py;
-      const int x = origin(ix0 + q % nxc, g.stride, g.W, g.P) + px;
-      on[u] = e < total && y >= ty0 && y < ty1 && x >= tx0 && x < tx1;  // outside the tile: never read
-      qo[u] = on[u] ? q : 0;
-      no[u] = n;
-      v[u] = 0.f;
-    }
-    for (int j0 = 0; j0 < Kmax; j0 += JB) {
-      float dv[U][JB], cv[U][JB];
-      unsigned used = 0u;  // bit u * JB + jj: atom j0 + jj exists for element u
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int jj = 0; jj < JB; ++jj) {
+        for (int jj = 0; jj < 8; ++jj) {
           const int j = j0 + jj;
-          const int a = (on[u] && j < Kmax) ? s_sup[qo[u] * Kmax + j] : -1;
-          cv[u][jj] = a >= 0 ? s_coef[qo[u] * Kmax + j] : 0.f;
-          dv[u][jj] = a >= 0 ? __ldg(D0 + (int64_t)a * N0 + no[u]) : 0.f;
-          if (a >= 0) used |= 1u << (u * JB + jj);
+          const int a = j < Kmax ? sp[j] : -1;
+          dv[jj] = a >= 0 ? __ldg(D0 + (int64_t)a * N0 + n) : 0.f;
         }
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-#pragma unroll
-        for (int jj = 0; jj < JB; ++jj)
-          if (used & (1u << (u * JB + jj))) v[u] = fmaf(cv[u][jj], dv[u][jj], v[u]);
+        for (int jj = 0; jj < 8; ++jj) {
+          const int j = j0 + jj;
+          if (j < Kmax && sp[j] >= 0) v = fmaf(cp[j], dv[jj], v);
+        }
+      }
+      xq[n] = v;
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (on[u]) xs[qo[u] * ldp + no[u]] = v[u];
   }
   __syncthreads();
   const int planes = g.Ly * g.Lx, th = ty1 - ty0, tw = tx1 - tx0;
@@ -531,7 +524,7 @@ static bool agg_tile_plan(const GeomDev &g, int N0, int Kmax, AggTile &p) {
     p.TY = t[0];
     p.TX = t[1];
     p.nq = max_cover(g.H, g.P, g.stride, g.ny, p.TY) * max_cover(g.W, g.P, g.stride, g.nx, p.TX);
-    p.smem = sizeof(float) * (size_t)p.nq * (p.ldp + 2 * Kmax);
+    p.smem = sizeof(float) * ((size_t)p.nq * (p.ldp + 2 * Kmax) + N0);
     if (p.smem <= kSmemCap) return true;
   }
   return false;
