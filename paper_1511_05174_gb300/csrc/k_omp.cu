@@ -176,16 +176,24 @@ __device__ bool grp_append(bool act, int s, int M, const float *aqp, const float
 // ---------------------------------------------------------------------------
 __global__ void omp_init_kernel(const float *__restrict__ Y, int64_t B, int M, int Mp,
                                 const int32_t *__restrict__ perm, OmpState st) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < B * M) st.R[e] = Y[e];
-  if (st.Rbf && e < B * Mp) {
-    const int64_t p = e / Mp;
-    const int m = (int)(e - p * Mp);
+  // four consecutive elements per thread (M and Mp are multiples of 4)
+  const int64_t e4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e4 < B * M / 4) reinterpret_cast<float4 *>(st.R)[e4] = __ldg(reinterpret_cast<const float4 *>(Y) + e4);
+  if (st.Rbf && e4 < B * Mp / 4) {
+    const int64_t p = e4 / (Mp / 4);
+    const int m = 4 * (int)(e4 - p * (Mp / 4));
     const int64_t b = perm ? perm[p] : p;
-    st.Rbf[e] = __float2bfloat16_rn(m < M ? Y[b * M + m] : 0.f);
+    const float4 v = m < M ? __ldg(reinterpret_cast<const float4 *>(Y + b * M + m)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    __nv_bfloat162 *o = reinterpret_cast<__nv_bfloat162 *>(st.Rbf + 4 * e4);
+    o[0] = __floats2bfloat162_rn(v.x, v.y);
+    o[1] = __floats2bfloat162_rn(v.z, v.w);
   }
-  if (e < B * st.ldo) { st.omega[e] = -1; st.alpha[e] = 0.f; }
-  if (e < B) { st.k_eff[e] = 0; st.flags[e] = 0; }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t e = 4 * e4 + u;
+    if (e < B * st.ldo) { st.omega[e] = -1; st.alpha[e] = 0.f; }
+    if (e < B) { st.k_eff[e] = 0; st.flags[e] = 0; }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -623,7 +631,7 @@ void launch_omp_init(const float *Y, int64_t B, int M, int Mp, const int32_t *pe
   int64_t n = B * (int64_t)(M > Mp ? M : Mp);
   n = n > B * st.ldo ? n : B * st.ldo;
   if (n == 0) return;
-  omp_init_kernel<<<blocks(n, 256), 256, 0, s>>>(Y, B, M, Mp, perm, st);
+  omp_init_kernel<<<blocks((n + 3) / 4, 256), 256, 0, s>>>(Y, B, M, Mp, perm, st);
 }
 
 void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_norm, int T,

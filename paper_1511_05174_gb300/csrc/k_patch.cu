@@ -35,6 +35,24 @@ __device__ __forceinline__ int level_index(const GeomDev &g, int l, int ly, int 
 // Phi = I, shot for coded aperture, 0 otherwise).
 __global__ void extract_kernel(GeomDev g, const float *__restrict__ meas, float *__restrict__ Y,
                                int64_t B, int M) {
+  // four consecutive rows m of one patch per thread (M and P are multiples of 4,
+  // so the four lie in one row of the patch)
+  const int64_t e4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int M4 = M >> 2;
+  if (e4 >= B * M4) return;
+  const int64_t b = e4 / M4;
+  const int m = 4 * (int)(e4 - b * M4);
+  const int iy = (int)(b / g.nx), ix = (int)(b - (int64_t)iy * g.nx);
+  const int oy = origin(iy, g.stride, g.H, g.P), ox = origin(ix, g.stride, g.W, g.P);
+  const int PP = g.P * g.P;
+  const int q = m / PP, r = m - q * PP, py = r / g.P, px = r - py * g.P;
+  const float *src = meas + ((int64_t)q * g.H + oy + py) * g.W + ox + px;
+  reinterpret_cast<float4 *>(Y)[e4] = make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), __ldg(src + 3));
+}
+
+// Scalar variant for patch sides that are not a multiple of 4.
+__global__ void extract1_kernel(GeomDev g, const float *__restrict__ meas, float *__restrict__ Y,
+                                int64_t B, int M) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= B * M) return;
   const int64_t b = e / M;
@@ -372,10 +390,12 @@ agg_tile_kernel(GeomDev g, const float *__restrict__ D0, int N0, const int32_t *
                 const float *__restrict__ coef, const int8_t *__restrict__ k_eff, int Kmax,
                 const int32_t *__restrict__ cover_y, const int32_t *__restrict__ cover_x, int TY, int TX, int ldp,
                 int nq_max, float *__restrict__ img) {
-  extern __shared__ float xs[];  // [nq_max][ldp] patches | [nq_max][Kmax] atoms | [nq_max][Kmax] coefs | [N0] (py, px)
+  extern __shared__ float xs[];  // [nq_max][ldp] patches | [nq_max][Kmax] atoms | [nq_max][Kmax] coefs |
+                                 // [nq_max] k_eff | [N0] (py, px)
   int *s_sup = reinterpret_cast<int *>(xs + (size_t)nq_max * ldp);
   float *s_coef = reinterpret_cast<float *>(s_sup + nq_max * Kmax);
-  int *s_yx = reinterpret_cast<int *>(s_coef + nq_max * Kmax);
+  int *s_keff = reinterpret_cast<int *>(s_coef + nq_max * Kmax);
+  int *s_yx = s_keff + nq_max;
   const int ty0 = blockIdx.y * TY, tx0 = blockIdx.x * TX;
   const int ty1 = min(ty0 + TY, g.H), tx1 = min(tx0 + TX, g.W);
   const int iy0 = cover_y[2 * ty0], iy1 = cover_y[2 * (ty1 - 1) + 1];
@@ -385,9 +405,10 @@ agg_tile_kernel(GeomDev g, const float *__restrict__ D0, int N0, const int32_t *
   for (int e = threadIdx.x; e < nq * Kmax; e += blockDim.x) {
     const int q = e / Kmax, j = e - q * Kmax;
     const int64_t b = (int64_t)(iy0 + q / nxc) * g.nx + (ix0 + q % nxc);
-    const bool on = j < k_eff[b];
-    s_sup[e] = on ? support[b * Kmax + j] : -1;
-    s_coef[e] = on ? coef[b * Kmax + j] : 0.f;
+    const int ke = k_eff[b];
+    if (j == 0) s_keff[q] = ke < Kmax ? ke : Kmax;
+    s_sup[e] = j < ke ? support[b * Kmax + j] : -1;
+    s_coef[e] = j < ke ? coef[b * Kmax + j] : 0.f;
   }
   for (int n = threadIdx.x; n < N0; n += blockDim.x) {
     const int r = n % PP;
@@ -399,28 +420,32 @@ agg_tile_kernel(GeomDev g, const float *__restrict__ D0, int N0, const int32_t *
     // the part of patch q inside the tile, in patch coordinates
     const int oy = origin(iy0 + q / nxc, g.stride, g.H, g.P), ox = origin(ix0 + q % nxc, g.stride, g.W, g.P);
     const int py0 = ty0 - oy, py1 = ty1 - oy, px0 = tx0 - ox, px1 = tx1 - ox;
-    const int *sp = s_sup + q * Kmax;
-    const float *cp = s_coef + q * Kmax;
+    const int ke = s_keff[q];
     float *xq = xs + q * ldp;
-    for (int n = lane; n < N0; n += 32) {
-      const int yx = s_yx[n], py = yx >> 16, px = yx & 0xffff;
-      if (py < py0 || py >= py1 || px < px0 || px >= px1) continue;  // outside the tile: never read
-      float v = 0.f;
-      for (int j0 = 0; j0 < Kmax; j0 += 8) {
+    // atoms j0 .. j0 + 7 at a time: their rows and coefficients in registers,
+    // x_hat accumulated in place in j order (the order of synth_kernel)
+    for (int j0 = 0; j0 == 0 || j0 < ke; j0 += 8) {
+      const int cnt = ke - j0 < 8 ? ke - j0 : 8;
+      const float *rp[8];
+      float cj[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) {
+        const int j = jj < cnt ? j0 + jj : j0;
+        rp[jj] = D0 + (int64_t)(jj < cnt ? s_sup[q * Kmax + j] : 0) * N0;
+        cj[jj] = jj < cnt ? s_coef[q * Kmax + j] : 0.f;
+      }
+      for (int n = lane; n < N0; n += 32) {
+        const int yx = s_yx[n], py = yx >> 16, px = yx & 0xffff;
+        if (py < py0 || py >= py1 || px < px0 || px >= px1) continue;  // outside the tile: never read
         float dv[8];
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int j = j0 + jj;
-          const int a = j < Kmax ? sp[j] : -1;
-          dv[jj] = a >= 0 ? __ldg(D0 + (int64_t)a * N0 + n) : 0.f;
-        }
+        for (int jj = 0; jj < 8; ++jj) dv[jj] = jj < cnt ? __ldg(rp[jj] + n) : 0.f;
+        float v = j0 ? xq[n] : 0.f;
 #pragma unroll
-        for (int jj = 0; jj < 8; ++jj) {
-          const int j = j0 + jj;
-          if (j < Kmax && sp[j] >= 0) v = fmaf(cp[j], dv[jj], v);
-        }
+        for (int jj = 0; jj < 8; ++jj)
+          if (jj < cnt) v = fmaf(cj[jj], dv[jj], v);
+        xq[n] = v;
       }
-      xq[n] = v;
     }
   }
   __syncthreads();
@@ -453,7 +478,10 @@ void launch_extract(const GeomDev &g, int sense_kind, int shots, const float *me
                     int64_t B, int M, cudaStream_t s) {
   (void)sense_kind; (void)shots;
   if (B * M == 0) return;
-  extract_kernel<<<blocks(B * M, 256), 256, 0, s>>>(g, meas, Y, B, M);
+  if (g.P % 4 == 0 && M % 4 == 0)
+    extract_kernel<<<blocks(B * M / 4, 256), 256, 0, s>>>(g, meas, Y, B, M);
+  else
+    extract1_kernel<<<blocks(B * M, 256), 256, 0, s>>>(g, meas, Y, B, M);
 }
 
 void launch_downsample(const GeomDev &g, int level, const float *Y0, float *Yl, int64_t B,
@@ -524,7 +552,7 @@ static bool agg_tile_plan(const GeomDev &g, int N0, int Kmax, AggTile &p) {
     p.TY = t[0];
     p.TX = t[1];
     p.nq = max_cover(g.H, g.P, g.stride, g.ny, p.TY) * max_cover(g.W, g.P, g.stride, g.nx, p.TX);
-    p.smem = sizeof(float) * ((size_t)p.nq * (p.ldp + 2 * Kmax) + N0);
+    p.smem = sizeof(float) * ((size_t)p.nq * (p.ldp + 2 * Kmax + 1) + N0);
     if (p.smem <= kSmemCap) return true;
   }
   return false;
