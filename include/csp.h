@@ -289,12 +289,15 @@ csp_status csp_job_release(csp_server *srv, uint64_t job_id);
  * decompositions (here: the restricted finer-scale solver, either re-reading
  * candidate rows from L2 with cooperative lane groups, staging them in
  * shared memory, or scoring candidates through the level's precomputed Gram
- * matrix -- the "Batch-OMP" form of the same iteration -- with 4, 8 or 16
- * lanes per patch for M <= 64, twice that for larger M).  csp_autotune runs
+ * matrix -- the "Batch-OMP" form of the same iteration, scoring p0 - G alpha,
+ * or its Gram-Schmidt form, which updates the correlations per appended atom
+ * and solves for alpha once -- each with 4, 8 or 16 lanes per patch for
+ * M <= 64, twice that for larger M).  csp_autotune runs
  * csp_solve once per variant on the given batch (same arguments as
  * csp_solve, outputs overwritten), times each with CUDA events, keeps the
  * fastest for this context and reports the times.  Synchronises `stream`. */
-#define CSP_TUNE_VARIANTS 5  /* 0: L2-cooperative, 1: shared-memory staged, 2-4: Gram-matrix proxy, narrow to wide */
+#define CSP_TUNE_VARIANTS 8  /* 0: L2-cooperative, 1: shared-memory staged, 2-4: Gram-matrix proxy, 5-7: Gram-Schmidt
+                                form, each narrow to wide */
 typedef struct csp_tune_result {
     int restricted_variant;            /* chosen variant index                      */
     double ms[CSP_TUNE_VARIANTS];      /* solve time per variant (ms)               */
@@ -305,7 +308,7 @@ csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const floa
                         csp_tune_result *out);
 
 /* Pin the restricted-solver variant (0 .. CSP_TUNE_VARIANTS - 1), e.g. from a
- * stored csp_tune_result.  Variants 2-4 fall back to 0 on levels whose Gram
+ * stored csp_tune_result.  Variants 2-7 fall back to 0 on levels whose Gram
  * matrix was not kept (T^2 floats above 256 MiB or beyond the memory budget).
  * Errors: CSP_ERR_INVALID for an unknown variant. */
 csp_status csp_set_kernel_variant(csp_ctx *ctx, int restricted_variant);

@@ -205,8 +205,9 @@ void launch_omp_update_wave(const float *Y, int M, const float *A, const float *
                             int64_t n, int64_t rbf_row0, int n_cand, const int8_t *Kp, int Kuni, OmpState st,
                             int64_t *stats, const float *gram, int T, int64_t a_pstride, int64_t inv_pstride,
                             cudaStream_t s);
-// width 0, 1, 2: 4, 8, 16 lanes per patch for M <= 64 (doubled per doubling of M, at most 32)
-void launch_omp_restricted_gram(int width, const float *Y, int M, const float *A, const float *inv_norm,
+// width 0, 1, 2: 4, 8, 16 lanes per patch for M <= 64 (doubled per doubling of M, at most 32);
+// qr: Gram-Schmidt form (correlations updated per appended atom) instead of p0 - G alpha
+void launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const float *A, const float *inv_norm,
                                 const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx, int cap,
                                 const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int8_t *Kp,
                                 int Kuni, int Kb, int32_t *omega, float *alpha, int ldo, int8_t *k_eff,

@@ -350,40 +350,17 @@ __host__ __device__ __forceinline__ int gram_group_bytes(int Kb, int cap) {
   return (bytes + 127) / 128 * 128 + 16;  // groups start on different bank offsets
 }
 
+// Candidate list f(Omega_up) of one patch (parents in support order, each
+// parent's children in link order, at most cap; overflow counted in stats[3]),
+// the candidates' inverse norms, and p0 = A_C^T y (RB rows per load wave).
+// pstart / pbeg: 2 x CSP_MAX_K ints of scratch.  Returns |C|.  Warp-collective.
 template <int G, int NCH>
-__global__ void __launch_bounds__(WV_WARPS * 32, 5)
-omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
-                           const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
-                           const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx,
-                           int cap, const int32_t *__restrict__ omega_up, int ldo_up,
-                           const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
-                           int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
-                           int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
-  constexpr int NG = 32 / G;
+__device__ int gram_setup(bool valid, int s, int64_t b, int kup, const int32_t *__restrict__ omega_up, int ldo_up,
+                          const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx, int cap,
+                          const GrpSmem &S, int *pstart, int *pbeg, const float *__restrict__ inv_norm,
+                          int64_t *stats, int M, const float *__restrict__ A, const float4 (&yv)[NCH], float *p0) {
   constexpr int KPL = (CSP_MAX_K + G - 1) / G;
-  extern __shared__ __align__(16) char smem_raw[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
-  const int64_t wbase = ((int64_t)blockIdx.x * WV_WARPS + wib) * NG;
-  if (wbase >= n) return;  // whole warp
-  const int64_t wi = wbase + g;
-  const bool valid = wi < n;
-  char *gbase = smem_raw + (size_t)(wib * NG + g) * gram_group_bytes(Kb, cap);
-  const GrpSmem S = carve(gbase, Kb, cap);
-  char *q_ = gbase + grp_smem_bytes(Kb, cap);
-  float *p0 = reinterpret_cast<float *>(q_); q_ += up16(4 * cap);
-  float *Gc = reinterpret_cast<float *>(q_); q_ += 4 * gram_gc_floats(Kb, cap);  // Gc[j * ldg + c]
-  const int ldg = gram_ld(cap);
-  float *p0c = reinterpret_cast<float *>(q_);
-  int *pstart = reinterpret_cast<int *>(Gc);  // parents' child ranges, before Gc is used
-  int *pbeg = pstart + CSP_MAX_K;
   const int nv = M >> 2;
-  const int64_t b = valid ? (ids ? __ldg(ids + wi) : wi) : 0;
-  int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
-  Kpb = Kpb < Kb ? Kpb : Kb;
-  const int kup = valid ? keff_up[b] : 0;
-  const float *yrow = Y + b * M;
-  float4 yv[NCH];
-  load_chunks<G, NCH>(yv, yrow, nv, s, valid);
   // candidate set f(Omega_up): parents' child ranges in one wave, then the children
   int pr[KPL], c0r[KPL], c1r[KPL];
 #pragma unroll
@@ -454,6 +431,44 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
     }
   }
   __syncwarp();
+  return nc;
+}
+
+template <int G, int NCH>
+__global__ void __launch_bounds__(WV_WARPS * 32, 5)
+omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
+                           const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
+                           const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx,
+                           int cap, const int32_t *__restrict__ omega_up, int ldo_up,
+                           const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
+                           int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
+                           int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
+  constexpr int NG = 32 / G;
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
+  const int64_t wbase = ((int64_t)blockIdx.x * WV_WARPS + wib) * NG;
+  if (wbase >= n) return;  // whole warp
+  const int64_t wi = wbase + g;
+  const bool valid = wi < n;
+  char *gbase = smem_raw + (size_t)(wib * NG + g) * gram_group_bytes(Kb, cap);
+  const GrpSmem S = carve(gbase, Kb, cap);
+  char *q_ = gbase + grp_smem_bytes(Kb, cap);
+  float *p0 = reinterpret_cast<float *>(q_); q_ += up16(4 * cap);
+  float *Gc = reinterpret_cast<float *>(q_); q_ += 4 * gram_gc_floats(Kb, cap);  // Gc[j * ldg + c]
+  const int ldg = gram_ld(cap);
+  float *p0c = reinterpret_cast<float *>(q_);
+  int *pstart = reinterpret_cast<int *>(Gc);  // parents' child ranges, before Gc is used
+  int *pbeg = pstart + CSP_MAX_K;
+  const int nv = M >> 2;
+  const int64_t b = valid ? (ids ? __ldg(ids + wi) : wi) : 0;
+  int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
+  Kpb = Kpb < Kb ? Kpb : Kb;
+  const int kup = valid ? keff_up[b] : 0;
+  const float *yrow = Y + b * M;
+  float4 yv[NCH];
+  load_chunks<G, NCH>(yv, yrow, nv, s, valid);
+  const int nc = gram_setup<G, NCH>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
+                                   inv_norm, stats, M, A, yv, p0);
   const float ysq = gsum<G>(dotc<NCH>(yv, yv));
   float rsq = ysq;
   bool act = valid && Kpb > 0;
@@ -632,6 +647,247 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
   }
 }
 
+// ---------------------------------------------------------------------------
+// Restricted OMP in Gram-Schmidt form (same iteration, same Gram matrix).
+// With u_j the orthonormal directions of the chosen atoms (A_Omega = U L^T, L
+// the Cholesky factor of A_Omega^T A_Omega), the group keeps Q_C = A_C^T U
+// (column j = <a_c, u_j> for every candidate c) and the correlations
+// c_c = <a_c, r>.  Appending atom q needs no triangular solve: the new row of L
+// is w = Q_C[q] (the row of q), L_kk = sqrt(||a_q||^2 - ||w||^2),
+// z_k = <u_k, y> = (p0_q - w.z) / L_kk, the new column of Q_C is
+// (G[q][C] - Q_C w) / L_kk, then c -= z_k Q_C[:, k] and ||r||^2 -= z_k^2.
+// alpha = L^{-T} z is solved once at the end (and near the FP32 floor of
+// ||r||^2, where the residual is formed explicitly).  A patch whose FP32 pivot
+// fails continues in FP64 from scratch each iteration, with the correlations
+// recomputed from the Gram rows of its chosen atoms.
+// Per-group shared memory: GrpSmem | p0[cap] | c[cap] | Q_C[Kb][ldg] (its
+// first 64 words hold the parents' child ranges while the candidates are
+// listed) | p0 of the chosen [Kb].
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int qr_group_bytes(int Kb, int cap) {
+  const int bytes = grp_smem_bytes(Kb, cap) + 2 * up16(4 * cap) + 4 * gram_gc_floats(Kb, cap) + up16(4 * Kb);
+  return (bytes + 127) / 128 * 128 + 16;  // groups start on different bank offsets
+}
+
+// alpha = L^{-T} z over rows 0 .. kl of the packed factor (into S.W), for the
+// groups with `on`; kw >= kl for every group of the warp.  Warp-collective.
+template <int G>
+__device__ __forceinline__ void grp_backsub(bool on, int s, int kl, int kw, const GrpSmem &S) {
+  if (on)
+    for (int i = s; i <= kl; i += G) S.V[i] = S.z[i];
+  __syncwarp();
+  for (int j = kw; j >= 0; --j) {
+    if (on && j <= kl) {
+      const float aj = S.V[j] * S.Linv[j];
+      if (s == 0) S.W[j] = aj;
+      for (int i = s; i < j; i += G) S.V[i] = fmaf(-S.L[tri(j) + i], aj, S.V[i]);
+    }
+    __syncwarp();
+  }
+}
+
+template <int G, int NCH>
+__global__ void __launch_bounds__(WV_WARPS * 32, 5)
+omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
+                         const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
+                         const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx,
+                         int cap, const int32_t *__restrict__ omega_up, int ldo_up,
+                         const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
+                         int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
+                         int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
+  constexpr int NG = 32 / G;
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
+  const int64_t wbase = ((int64_t)blockIdx.x * WV_WARPS + wib) * NG;
+  if (wbase >= n) return;  // whole warp
+  const int64_t wi = wbase + g;
+  const bool valid = wi < n;
+  char *gbase = smem_raw + (size_t)(wib * NG + g) * qr_group_bytes(Kb, cap);
+  const GrpSmem S = carve(gbase, Kb, cap);
+  char *q_ = gbase + grp_smem_bytes(Kb, cap);
+  float *p0 = reinterpret_cast<float *>(q_); q_ += up16(4 * cap);
+  float *cc = reinterpret_cast<float *>(q_); q_ += up16(4 * cap);
+  float *Qc = reinterpret_cast<float *>(q_); q_ += 4 * gram_gc_floats(Kb, cap);  // Qc[j * ldg + c]
+  const int ldg = gram_ld(cap);
+  float *p0c = reinterpret_cast<float *>(q_);
+  int *pstart = reinterpret_cast<int *>(Qc);  // parents' child ranges, before Qc is used
+  int *pbeg = pstart + CSP_MAX_K;
+  const int nv = M >> 2;
+  const int64_t b = valid ? (ids ? __ldg(ids + wi) : wi) : 0;
+  int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
+  Kpb = Kpb < Kb ? Kpb : Kb;
+  const int kup = valid ? keff_up[b] : 0;
+  const float *yrow = Y + b * M;
+  float4 yv[NCH];
+  load_chunks<G, NCH>(yv, yrow, nv, s, valid);
+  const int nc = gram_setup<G, NCH>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
+                                   inv_norm, stats, M, A, yv, p0);
+  for (int c = s; c < nc; c += G) cc[c] = p0[c];
+  __syncwarp();
+  const float ysq = gsum<G>(dotc<NCH>(yv, yv));
+  float rsq = ysq;
+  bool act = valid && Kpb > 0;
+  uint8_t fl = 0;  // bit 1: FP64 from here on
+  int k = 0, scored = 0;
+  const int Kw = __reduce_max_sync(kFull, Kpb);
+  for (int it = 0; it < Kw; ++it) {
+    act = act && k < Kpb && !(rsq <= kEpsR32 * ysq);
+    if (!__any_sync(kFull, act)) break;
+    if (act) ++scored;
+    // proxy from the current correlations
+    unsigned long long best = 0ull;
+    if (act)
+      for (int c = s; c < nc; c += G) {
+        const float inv = S.invn[c];
+        if (!(inv > 0.f)) continue;
+        const unsigned long long key = pack_key(fabsf(cc[c]) * inv, S.cs[c]);
+        best = key > best ? key : best;
+      }
+    best = gmax<G>(best);
+    if (act && !best) act = false;  // candidate set exhausted
+    const int q = act ? key_idx(best) : 0;
+    if (act)
+      for (int c = s; c < nc; c += G)
+        if (S.cs[c] == q) {
+          S.invn[c] = -1.f;  // chosen: no longer eligible
+          S.misc[1] = c;
+        }
+    __syncwarp();
+    const int qs = act ? S.misc[1] : 0;
+    // G[q][C] (row q: G is symmetric) and G[q][q], issued before their use
+    float gpre[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = s + u * G;
+      gpre[u] = (act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
+    }
+    const float aa = act ? __ldg(gram + (int64_t)q * T + q) : 0.f;
+    const bool f32 = act && !(fl & 2);
+    // new row of L: w_j = <u_j, a_q> = Q_C[q][j]
+    float ww = 0.f, wz = 0.f;
+    if (f32)
+      for (int j = s; j < k; j += G) {
+        const float w = Qc[j * ldg + qs];
+        S.W[j] = w;
+        ww = fmaf(w, w, ww);
+        wz = fmaf(w, S.z[j], wz);
+      }
+    ww = gsum<G>(ww);
+    wz = gsum<G>(wz);
+    const float d = aa - ww;
+    const bool ok32 = f32 && aa > 0.f && d >= kTauPivot * aa;
+    if (f32 && !ok32) {
+      fl |= 2;
+      if (s == 0) atomicAdd((unsigned long long *)&stats[0], 1ull);
+    }
+    float il = 0.f, zk = 0.f;
+    if (ok32) {
+      const float lkk = sqrtf(d);
+      il = 1.f / lkk;
+      zk = (p0[qs] - wz) * il;
+      for (int j = s; j < k; j += G) S.L[tri(k) + j] = S.W[j];
+      if (s == 0) {
+        S.L[tri(k) + k] = lkk;
+        S.Linv[k] = il;
+        S.z[k] = zk;
+        S.om[k] = q;
+        S.colp[k] = A + (int64_t)q * M;
+        p0c[k] = p0[qs];
+      }
+    }
+    __syncwarp();
+    if (ok32) {
+      // column k of Q_C and the correlations
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = s + u * G;
+        if (c < nc) {
+          float v = gpre[u];
+          for (int j = 0; j < k; ++j) v = fmaf(-S.W[j], Qc[j * ldg + c], v);
+          v *= il;
+          Qc[k * ldg + c] = v;
+          cc[c] = fmaf(-zk, v, cc[c]);
+        }
+      }
+      for (int c = s + 8 * G; c < nc; c += G) {
+        float v = __ldg(gram + (int64_t)q * T + S.cs[c]);
+        for (int j = 0; j < k; ++j) v = fmaf(-S.W[j], Qc[j * ldg + c], v);
+        v *= il;
+        Qc[k * ldg + c] = v;
+        cc[c] = fmaf(-zk, v, cc[c]);
+      }
+      rsq = rsq - zk * zk;
+    }
+    // FP64 from scratch for the patches whose FP32 pivot failed (now or before)
+    const bool go64 = act && !ok32;
+    if (go64 && s == 0) S.misc[0] = fp64_projection(M, yrow, S, k, A + (int64_t)q * M) ? 1 : 0;
+    __syncwarp();
+    const bool app64 = go64 && S.misc[0] != 0;
+    if (app64 && s == 0) {
+      S.om[k] = q;
+      S.colp[k] = A + (int64_t)q * M;
+    }
+    __syncwarp();
+    if (app64)  // correlations c = p0 - G[C][Omega] alpha from the Gram rows of the chosen atoms
+      for (int c = s; c < nc; c += G) {
+        float v = p0[c];
+        for (int j = 0; j <= k; ++j) v = fmaf(-S.W[j], __ldg(gram + (int64_t)S.om[j] * T + S.cs[c]), v);
+        cc[c] = v;
+      }
+    // ||r||^2 formed explicitly in FP64 mode and near the FP32 floor
+    const bool exact = app64 || (ok32 && rsq <= 1e-5f * ysq);
+    if (__any_sync(kFull, exact)) {
+      const bool need = exact && !app64;  // FP32: alpha over rows 0..k first
+      grp_backsub<G>(need, s, k, __reduce_max_sync(kFull, need ? k : 0), S);
+      float4 rv[NCH];
+#pragma unroll
+      for (int t = 0; t < NCH; ++t) rv[t] = yv[t];
+      const int kx = __reduce_max_sync(kFull, exact ? k + 1 : 0);
+      for (int j0 = 0; j0 < kx; j0 += RB) {
+        float4 cr[RB][NCH];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+          const bool o = exact && j0 + u <= k;
+          load_chunks<G, NCH>(cr[u], o ? S.colp[j0 + u] : yrow, nv, s, o);
+        }
+#pragma unroll
+        for (int u = 0; u < RB; ++u)
+          if (exact && j0 + u <= k) {
+            const float aj = S.W[j0 + u];
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+              rv[t].x = fmaf(-aj, cr[u][t].x, rv[t].x);
+              rv[t].y = fmaf(-aj, cr[u][t].y, rv[t].y);
+              rv[t].z = fmaf(-aj, cr[u][t].z, rv[t].z);
+              rv[t].w = fmaf(-aj, cr[u][t].w, rv[t].w);
+            }
+          }
+      }
+      const float r2 = gsum<G>(dotc<NCH>(rv, rv));
+      if (exact) rsq = r2;
+    }
+    if (act) {
+      if (ok32 || app64) ++k;
+      else act = false;
+    }
+    __syncwarp();
+  }
+  // alpha = L^{-T} z for the patches that stayed in FP32 (FP64 ones hold it in S.W)
+  const bool fin = valid && !(fl & 2) && k > 0;
+  grp_backsub<G>(fin, s, k - 1, __reduce_max_sync(kFull, fin ? k - 1 : 0), S);
+  if (valid) {
+    if (s == 0) {
+      if (k < Kpb) atomicAdd((unsigned long long *)&stats[1], 1ull);
+      atomicAdd((unsigned long long *)&stats[2], (unsigned long long)nc * (unsigned long long)scored);
+      k_eff[b] = (int8_t)k;
+    }
+    for (int j = s; j < ldo; j += G) {
+      omega[b * ldo + j] = (j < k) ? S.om[j] : -1;
+      alpha[b * ldo + j] = (j < k) ? S.W[j] : 0.f;
+    }
+  }
+}
+
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // (G, NCH): about eight elements per lane.
@@ -698,21 +954,21 @@ void launch_omp_update_wave(const float *Y, int M, const float *A, const float *
   });
 }
 
-void launch_omp_restricted_gram(int width, const float *Y, int M, const float *A, const float *inv_norm,
+void launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const float *A, const float *inv_norm,
                                 const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx,
                                 int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
                                 const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
                                 int8_t *k_eff, int64_t *stats, const float *gram, int T, cudaStream_t s) {
   if (n == 0) return;
   const int per_cta = WV_WARPS * (32 / gram_group(M, width));
-  const size_t sm = (size_t)gram_group_bytes(Kb, cap) * per_cta;
+  const size_t sm = (size_t)(qr ? qr_group_bytes(Kb, cap) : gram_group_bytes(Kb, cap)) * per_cta;
   dispatch_gram(M, width, [&](auto gc, auto nc) {
     constexpr int GG = decltype(gc)::value, NCH = decltype(nc)::value;
-    if (sm > 48 * 1024)
-      cudaFuncSetAttribute(omp_restricted_gram_kernel<GG, NCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    omp_restricted_gram_kernel<GG, NCH><<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(
-        Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega,
-        alpha, ldo, k_eff, stats, gram, T);
+    auto kern = qr ? omp_restricted_qr_kernel<GG, NCH> : omp_restricted_gram_kernel<GG, NCH>;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kern<<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up,
+                                                      ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats,
+                                                      gram, T);
   });
 }
 

@@ -234,12 +234,42 @@ def test_exactly_dependent_atom_ends_the_patch():
     assert rate == 1.0 and worst <= REL_TOL
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", list(range(8)))
+def test_restricted_dependent_candidate_falls_back_to_fp64(variant):
+    """Fine step of Algorithm 2 whose candidate set holds an exactly dependent
+    atom (a_2 = a_0 + a_1, integer atoms): every restricted variant rejects it
+    through the FP64 pivot test, k_eff = 2, and the coefficients are the least
+    squares ones, as in the oracle (one coarse atom whose children are all
+    fine atoms: cross-scale OMP equals plain OMP here)."""
+    from paper_1511_05174_gb300.context import Context
+    rng = np.random.default_rng(13)
+    A = rng.integers(-3, 4, size=(3, 64)).astype(np.float32)
+    A[2] = A[0] + A[1]
+    Y = np.stack([A[0] + 0.5 * A[1] + 0.01 * rng.standard_normal(64) for _ in range(40)]).astype(np.float32)
+    coarse = A[:1].reshape(1, 8, 8)
+    coarse = coarse.reshape(1, 4, 2, 4, 2).mean(axis=(2, 4)).reshape(1, 16).astype(np.float32)
+    ctx = Context(0)
+    ctx.set_geometry(8, 8, (1, 1), 8, 8, [(1, 1, 1, 1), (1, 1, 2, 2)])
+    ctx.set_sensing("identity")
+    ctx.load_dictionary(0, A)
+    ctx.load_dictionary(1, coarse)
+    ctx.load_links(0, np.zeros(3, np.int32))
+    ctx.set_kernel_variant(variant)
+    sup, coef, keff = ctx.solve(torch.from_numpy(Y).cuda(), "cross_scale", "fp32", K=[3, 1], Kmax=3)
+    o, a, k, _ = oracle.omp_batch([A] * len(Y), Y, 3)
+    assert np.all(k == 2)
+    assert np.all(keff.cpu().numpy() == 2)
+    assert ctx.stats()["fp64_fallbacks"] >= 1
+    rate, worst, bad = compare(A, sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy().astype(int), o, a, k)
+    assert rate == 1.0 and worst <= REL_TOL
+
+
+@pytest.mark.parametrize("variant", list(range(8)))
 @pytest.mark.parametrize("key", ["bayer", "lightfield", "denoise_ragged", "video"])
 def test_restricted_variants_agree_with_oracle(key, variant):
     """Every restricted-solver variant the autotuner may pick meets the parity
     bar: L2-cooperative (0), shared-memory staged (1), Gram-matrix proxy with
-    narrow, middle and wide lane groups (2, 3, 4)."""
+    narrow, middle and wide lane groups (2, 3, 4), its Gram-Schmidt form (5, 6, 7)."""
     from paper_1511_05174_gb300.context import Context
     w = _workload(key)
     o, a, k, _ = oracle.cross_scale_omp(w)
@@ -262,5 +292,5 @@ def test_autotune_picks_a_variant():
     Y = ctx.extract(torch.from_numpy(w.meas).cuda())
     K, K_patch, Kmax = budgets(w, "cross_scale")
     r = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
-    assert r["restricted_variant"] in range(5) and all(t > 0 for t in r["ms"])
+    assert r["restricted_variant"] in range(8) and all(t > 0 for t in r["ms"])
     assert r["ms"][r["restricted_variant"]] == min(r["ms"])
