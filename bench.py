@@ -181,15 +181,24 @@ def read_traffic(kernel: str, workload: str):
         return None
 
 
-def algorithmic(kind, w, prof_launches, stats, B, steps):
+def algorithmic(kind, w, prof_launches, stats, B, steps, M):
     """Algorithmic work of one launch of `kind` on this workload: (amount, unit, bound).
-    `stats` are the solve statistics of one step."""
+    `stats` are the solve statistics of one step; M the measurements per patch."""
     g = w.geometry
-    M = 64 if w.sensing.kind != "identity" else g.planes * g.P * g.P
     top = w.dicts[-1].shape[0]
-    if kind == "proxy_fp32":
-        T = top if prof_launches.get("restricted") else w.dicts[0].shape[0]
-        return 2.0 * M * T * B, "TFLOP/s", "alu"
+    per_patch_phi = w.sensing.kind == "coded_exposure"
+    if kind in ("proxy_fp32", "proxy_bf16"):
+        cross = bool(prof_launches.get("restricted"))
+        D = w.dicts[-1] if cross else w.dicts[0]
+        T = D.shape[0]
+        dim = D.shape[1] if per_patch_phi else M  # per-pixel Phi: the lifted proxy runs at the atom dimension
+        if kind == "proxy_bf16":
+            dim = (dim + 63) // 64 * 64
+        # one launch per iteration and Bayer phase group: the step's proxy work
+        # (every patch, every iteration) over the step's launches
+        iters = int(np.max(w.K_levels[-1 if cross else 0]))
+        launches = max(prof_launches[kind][0] / steps, 1.0)
+        return 2.0 * dim * T * B * iters / launches, "TFLOP/s", ("tensor" if kind == "proxy_bf16" else "alu")
     if kind == "restricted":
         per_step = max(prof_launches.get("restricted", (1,))[0] / steps, 1.0)
         return 2.0 * M * stats.get("restricted_scores", 0) / per_step, "TFLOP/s", "alu"
@@ -197,7 +206,7 @@ def algorithmic(kind, w, prof_launches, stats, B, steps):
         # y, r read and r written, 4 B each, per patch
         return 3.0 * 4 * M * B, "GB/s", "hbm"
     if kind == "aggregate":
-        K = int(w.K_levels[0][0])
+        K = int(np.max(w.K_levels[0]))
         return 4.0 * g.planes * g.H * g.W + B * (K * 8 + 1), "GB/s", "hbm"
     if kind == "extract":
         return 4.0 * B * M + 4.0 * w.meas.size, "GB/s", "hbm"
@@ -430,7 +439,7 @@ def main():
     launches = {k: v for k, v in cs_prof.items()}
     dom = max(cs_prof.items(), key=lambda kv: kv[1][1])[0]
     n_launch, tot_ms = cs_prof[dom]
-    amount, unit, bound = algorithmic(dom, w, launches, cs_stats, B, args.steps)
+    amount, unit, bound = algorithmic(dom, w, launches, cs_stats, B, args.steps, M)
     roofline = None
     if amount is not None and n_launch:
         per_s = amount / (tot_ms / n_launch / 1e3)
@@ -442,6 +451,10 @@ def main():
         if bound == "hbm":
             peak, src = (peaks.get("hbm_gbs"), "measured") if peaks.get("hbm_gbs") else (6800.0, "fallback")
             achieved = per_s / 1e9
+        elif bound == "tensor":
+            peak, src = ((peaks.get("bf16_tflops"), "measured (BF16 dense, burst)") if peaks.get("bf16_tflops")
+                         else (1900.0, "fallback"))
+            achieved = per_s / 1e12
         else:
             peak, src = FP32_PEAK_TFLOPS, "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"
             achieved = per_s / 1e12

@@ -313,6 +313,14 @@ csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const floa
  * Errors: CSP_ERR_INVALID for an unknown variant. */
 csp_status csp_set_kernel_variant(csp_ctx *ctx, int restricted_variant);
 
+/* Aggregation path of csp_aggregate (same arithmetic in the same order, so the
+ * same image): 0 automatic (two-pass unless its scratch of B * N0 floats
+ * exceeds 1 GiB), 1 two-pass (synthesis into device scratch, then the
+ * per-pixel average), 2 fused shared-memory tiles (no scratch; falls back to
+ * two-pass when a patch footprint does not fit a tile).  CSP_ERR_INVALID for
+ * another value. */
+csp_status csp_set_aggregate_path(csp_ctx *ctx, int path);
+
 /* ---- Instrumentation (not part of the paper's method) ----------------------
  * Every kernel launch of a context is counted per kernel kind.  While
  * profiling is enabled, each launch is also bracketed by CUDA events on its

@@ -160,6 +160,10 @@ class Context:
                            _stream_ptr(stream, self.device))
         return {"restricted_variant": r.restricted_variant, "ms": list(r.ms)}
 
+    def set_aggregate_path(self, path: int) -> None:
+        """0 automatic, 1 two-pass, 2 fused shared-memory tiles (same image)."""
+        b.csp_set_aggregate_path(self._ctx, path)
+
     def set_kernel_variant(self, restricted_variant: int) -> None:
         b.csp_set_kernel_variant(self._ctx, restricted_variant)
 

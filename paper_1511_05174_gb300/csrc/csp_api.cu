@@ -839,12 +839,13 @@ csp_status csp_aggregate(csp_ctx *ctx, const int32_t *support, const float *coef
   if (Kmax < 1 || Kmax > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "Kmax must be in 1..CSP_MAX_K");
   if (!support || !coef || !k_eff || !image_out) return fail(ctx, CSP_ERR_INVALID, "NULL buffer");
   DeviceGuard dg(ctx->device);
-  bool tiled = false;
-  run(ctx, KK_AGGREGATE, (cudaStream_t)stream, B, [&] {
-    tiled = launch_aggregate_tiled(ctx->gd, ctx->lv[0].D, ctx->lv[0].N, support, coef, k_eff, Kmax, ctx->cover_y,
-                                   ctx->cover_x, image_out, (cudaStream_t)stream);
-  });
-  if (!tiled) {  // patch footprints too large for a shared-memory tile: synthesis scratch in HBM
+  bool tiled = aggregate_use_tiled(ctx->aggregate_path, ctx->gd, ctx->lv[0].N, Kmax);
+  if (tiled)
+    run(ctx, KK_AGGREGATE, (cudaStream_t)stream, B, [&] {
+      tiled = launch_aggregate_tiled(ctx->gd, ctx->lv[0].D, ctx->lv[0].N, support, coef, k_eff, Kmax, ctx->cover_y,
+                                     ctx->cover_x, image_out, (cudaStream_t)stream);
+    });
+  if (!tiled) {  // two-pass: synthesis scratch in HBM (L2-resident at these sizes)
     float *Xh = nullptr;
     CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_XH, (size_t)B * ctx->lv[0].N, &Xh));
     run(ctx, KK_AGGREGATE, (cudaStream_t)stream, B, [&] {
@@ -935,6 +936,13 @@ csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const floa
   ctx->restricted_variant = st == CSP_OK ? best : saved;
   out->restricted_variant = ctx->restricted_variant;
   return st;
+}
+
+csp_status csp_set_aggregate_path(csp_ctx *ctx, int path) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (path < 0 || path > 2) return fail(ctx, CSP_ERR_INVALID, "unknown aggregation path");
+  ctx->aggregate_path = path;
+  return CSP_OK;
 }
 
 csp_status csp_set_kernel_variant(csp_ctx *ctx, int restricted_variant) {

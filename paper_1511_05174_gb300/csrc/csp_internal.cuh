@@ -126,6 +126,7 @@ struct csp_ctx {
   double prof_ms[csp::KK_COUNT] = {};
   bool prof = false;
   int restricted_variant = 2;  // restricted-OMP kernel variant (see launch_omp_restricted)
+  int aggregate_path = 0;      // 0 automatic, 1 two-pass (synthesis scratch), 2 fused shared-memory tiles
   std::vector<csp::ProfRec> pending;
   std::vector<cudaEvent_t> ev_pool;
   // All device allocations (for the memory budget and destroy).
@@ -158,6 +159,12 @@ void launch_lift(const GeomDev &g, const uint8_t *pc, int level, const float *R,
 // Fused synthesis + overlap-add without scratch; false when no tile shape fits
 // shared memory (then use launch_aggregate, which needs B * N0 floats of scratch).
 bool aggregate_tiled_fits(const GeomDev &g, int N0, int Kmax);
+// Automatic choice: the two-pass path unless its B * N0 scratch exceeds 1 GiB.
+inline bool aggregate_use_tiled(int path, const GeomDev &g, int N0, int Kmax) {
+  if (path == 1) return false;
+  if (path == 2) return aggregate_tiled_fits(g, N0, Kmax);
+  return (int64_t)g.nx * g.ny * N0 * 4 > (int64_t(1) << 30) && aggregate_tiled_fits(g, N0, Kmax);
+}
 bool launch_aggregate_tiled(const GeomDev &g, const float *D0, int N0, const int32_t *support, const float *coef,
                             const int8_t *k_eff, int Kmax, const int32_t *cover_y, const int32_t *cover_x, float *img,
                             cudaStream_t s);

@@ -130,6 +130,23 @@ __device__ __forceinline__ GrpSmem carve(char *p, int Kb, int cap) {
   return S;
 }
 
+// alpha = L^{-T} z over rows 0 .. kl of the packed factor (into S.W), for the
+// groups with `on`; kw >= kl for every group of the warp.  Warp-collective.
+template <int G>
+__device__ __forceinline__ void grp_backsub(bool on, int s, int kl, int kw, const GrpSmem &S) {
+  if (on)
+    for (int i = s; i <= kl; i += G) S.V[i] = S.z[i];
+  __syncwarp();
+  for (int j = kw; j >= 0; --j) {
+    if (on && j <= kl) {
+      const float aj = S.V[j] * S.Linv[j];
+      if (s == 0) S.W[j] = aj;
+      for (int i = s; i < j; i += G) S.V[i] = fmaf(-S.L[tri(j) + i], aj, S.V[i]);
+    }
+    __syncwarp();
+  }
+}
+
 // FP64 projection from scratch, run by one lane: Cholesky of A_S^T A_S for
 // S = chosen + q (rows S.colp[0..k-1] and aq) with entries accumulated in FP64
 // from the FP32 columns, then z = L^{-1} A_S^T y and alpha = L^{-T} z (into

@@ -564,6 +564,10 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
     if (go64 && s == 0) S.misc[0] = fp64_projection(M, yrow, S, k, A + (int64_t)q * M) ? 1 : 0;
     __syncwarp();
     const bool appended = ok32 || (go64 && S.misc[0] != 0);
+    // q depends on the chosen columns: its FP32 attempt overwrote S.W; alpha of
+    // the chosen ones again from the (unchanged) factor
+    const bool restore = f32 && !appended;
+    grp_backsub<G>(restore, s, k - 1, __reduce_max_sync(kFull, restore ? k - 1 : 0), S);
     if (appended && s == 0) {
       S.om[k] = q;
       S.colp[k] = A + (int64_t)q * M;
@@ -667,23 +671,6 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
 __host__ __device__ __forceinline__ int qr_group_bytes(int Kb, int cap) {
   const int bytes = grp_smem_bytes(Kb, cap) + 2 * up16(4 * cap) + 4 * gram_gc_floats(Kb, cap) + up16(4 * Kb);
   return (bytes + 127) / 128 * 128 + 16;  // groups start on different bank offsets
-}
-
-// alpha = L^{-T} z over rows 0 .. kl of the packed factor (into S.W), for the
-// groups with `on`; kw >= kl for every group of the warp.  Warp-collective.
-template <int G>
-__device__ __forceinline__ void grp_backsub(bool on, int s, int kl, int kw, const GrpSmem &S) {
-  if (on)
-    for (int i = s; i <= kl; i += G) S.V[i] = S.z[i];
-  __syncwarp();
-  for (int j = kw; j >= 0; --j) {
-    if (on && j <= kl) {
-      const float aj = S.V[j] * S.Linv[j];
-      if (s == 0) S.W[j] = aj;
-      for (int i = s; i < j; i += G) S.V[i] = fmaf(-S.L[tri(j) + i], aj, S.V[i]);
-    }
-    __syncwarp();
-  }
 }
 
 template <int G, int NCH>
@@ -823,6 +810,10 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
     if (go64 && s == 0) S.misc[0] = fp64_projection(M, yrow, S, k, A + (int64_t)q * M) ? 1 : 0;
     __syncwarp();
     const bool app64 = go64 && S.misc[0] != 0;
+    // q depends on the chosen columns: alpha of the chosen ones from the FP32
+    // factor (S.W held w); FP64-mode patches still hold their last alpha
+    const bool restore = f32 && !ok32 && !app64;
+    grp_backsub<G>(restore, s, k - 1, __reduce_max_sync(kFull, restore ? k - 1 : 0), S);
     if (app64 && s == 0) {
       S.om[k] = q;
       S.colp[k] = A + (int64_t)q * M;

@@ -309,43 +309,38 @@ __global__ void norms_kernel(const float *__restrict__ A, int T, int M, int Mp, 
   }
 }
 
-// Synthesis x_hat_p = D_|Omega alpha for a block of PPC patches: the chosen
-// atoms' rows of the L2-resident fine dictionary are read coalesced over n,
-// the block is transposed in shared memory and stored element-major
-// (Xh[n][b]), so that the overlap-add below reads neighbouring patches'
-// values from contiguous memory.
+// Synthesis x_hat_p = D0 alpha_p (Sec. IV), patch-major Xh[b][n]: a warp per
+// patch, lanes over the elements n (coalesced rows of D0 and of Xh), the
+// patch's atoms eight at a time with their row pointers and coefficients in
+// registers; v = fma(alpha_j, D0[a_j][n], v) in j order.
 __global__ void synth_kernel(const float *__restrict__ D0, int N0, const int32_t *__restrict__ support,
                              const float *__restrict__ coef, const int8_t *__restrict__ k_eff, int Kmax,
-                             int64_t B, int ppc, float *__restrict__ Xh) {
-  extern __shared__ float tile[];  // [N0][ppc + 1], then the block's codes
-  const int64_t b0 = (int64_t)blockIdx.x * ppc;
-  const int ld = ppc + 1;
-  const int np = (int)((B - b0) < ppc ? (B - b0) : ppc);
-  int *s_sup = reinterpret_cast<int *>(tile + (size_t)N0 * ld);  // [ppc][Kmax], -1 past k_eff
-  float *s_coef = reinterpret_cast<float *>(s_sup + ppc * Kmax);
-  for (int e = threadIdx.x; e < ppc * Kmax; e += blockDim.x) {
-    const int p = e / Kmax, j = e - p * Kmax;
-    const bool on = p < np && j < k_eff[b0 + p];
-    s_sup[e] = on ? support[(b0 + p) * Kmax + j] : -1;
-    s_coef[e] = on ? coef[(b0 + p) * Kmax + j] : 0.f;
-  }
-  __syncthreads();
-  for (int p = 0; p < np; ++p) {
-    const int *sp = s_sup + p * Kmax;
-    const float *cp = s_coef + p * Kmax;
-    for (int n = threadIdx.x; n < N0; n += blockDim.x) {
-      float v = 0.f;
-      for (int j = 0; j < Kmax; ++j) {
-        const int a = sp[j];
-        if (a >= 0) v = fmaf(cp[j], __ldg(D0 + (int64_t)a * N0 + n), v);
-      }
-      tile[n * ld + p] = v;
+                             int64_t B, float *__restrict__ Xh) {
+  const int lane = threadIdx.x & 31;
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (b >= B) return;
+  int ke = k_eff[b];
+  ke = ke < Kmax ? ke : Kmax;
+  float *xb = Xh + b * N0;
+  for (int j0 = 0; j0 == 0 || j0 < ke; j0 += 8) {
+    const int cnt = ke - j0 < 8 ? ke - j0 : 8;
+    const float *rp[8];
+    float cj[8];
+#pragma unroll
+    for (int jj = 0; jj < 8; ++jj) {
+      rp[jj] = D0 + (int64_t)(jj < cnt ? __ldg(support + b * Kmax + j0 + jj) : 0) * N0;
+      cj[jj] = jj < cnt ? __ldg(coef + b * Kmax + j0 + jj) : 0.f;
     }
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < N0 * ppc; e += blockDim.x) {
-    const int n = e / ppc, p = e - n * ppc;
-    if (p < np) Xh[(int64_t)n * B + b0 + p] = tile[n * ld + p];
+    for (int n = lane; n < N0; n += 32) {
+      float dv[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) dv[jj] = jj < cnt ? __ldg(rp[jj] + n) : 0.f;
+      float v = j0 ? xb[n] : 0.f;
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj)
+        if (jj < cnt) v = fmaf(cj[jj], dv[jj], v);
+      xb[n] = v;
+    }
   }
 }
 
@@ -366,10 +361,10 @@ __global__ void gather_kernel(GeomDev g, const float *__restrict__ Xh, int N0,
   int cnt = 0;
   for (int iy = y0; iy <= y1; ++iy) {
     const int py = y - origin(iy, g.stride, g.H, g.P);
+    const float *row = Xh + ((int64_t)iy * g.nx) * N0 + (pl * g.P + py) * g.P;
     for (int ix = x0; ix <= x1; ++ix) {
       const int px = x - origin(ix, g.stride, g.W, g.P);
-      const int64_t b = (int64_t)iy * g.nx + ix;
-      acc += __ldg(Xh + (int64_t)((pl * g.P + py) * g.P + px) * ((int64_t)g.nx * g.ny) + b);
+      acc += __ldg(row + (int64_t)ix * N0 + px);
       ++cnt;
     }
   }
@@ -512,12 +507,7 @@ void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *
   const int64_t B = (int64_t)g.nx * g.ny;
   const int64_t n = (int64_t)g.Ly * g.Lx * g.H * g.W;
   if (n == 0) return;
-  if (B * N0) {
-    const int ppc = N0 <= 256 ? 32 : (N0 <= 512 ? 16 : 8);
-    const size_t sm = sizeof(float) * (size_t)N0 * (ppc + 1) + 8 * (size_t)ppc * Kmax;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(synth_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    synth_kernel<<<blocks(B, ppc), 256, sm, s>>>(D0, N0, support, coef, k_eff, Kmax, B, ppc, Xh);
-  }
+  if (B * N0) synth_kernel<<<blocks(B * 32, 256), 256, 0, s>>>(D0, N0, support, coef, k_eff, Kmax, B, Xh);
   gather_kernel<<<blocks(n, 256), 256, 0, s>>>(g, Xh, N0, cover_y, cover_x, img);
 }
 

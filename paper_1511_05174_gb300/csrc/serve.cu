@@ -170,8 +170,8 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
   const size_t o_sup = dv.take<int32_t>((size_t)Bt * Kmax);
   const size_t o_coef = dv.take<float>((size_t)Bt * Kmax);
   const size_t o_keff = dv.take<int8_t>((size_t)Bt);
-  bool tiled = true;  // fused synthesis + overlap-add needs no scratch
-  for (Job *j : sl.jobs) tiled &= aggregate_tiled_fits(j->gd, m.N0, Kmax);
+  bool tiled = true;  // fused synthesis + overlap-add (no scratch) for very large jobs only
+  for (Job *j : sl.jobs) tiled &= aggregate_use_tiled(0, j->gd, m.N0, Kmax);
   const size_t o_xh = dv.take<float>(tiled ? 0 : (size_t)Bmax * m.N0);
   const size_t o_pc = ce ? dv.take<uint8_t>((size_t)Bt * codes_pp) : 0;
   // coded exposure: the per-patch effective dictionaries of the full-dictionary

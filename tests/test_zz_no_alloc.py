@@ -53,9 +53,9 @@ def test_noalloc_aggregate_matches_aggregate_twice():
     ("lightfield", dict(H=40, W=48, T0=2048)),
 ])
 def test_fused_tile_aggregation_equals_two_pass(name, kw):
-    """csp_aggregate runs the fused shared-memory tile kernel; the no-alloc
-    entry point the two-pass synthesis + gather.  Same arithmetic in the same
-    order: the images are bit-identical (ragged grids included)."""
+    """The fused shared-memory tile path, the two-pass path and the no-alloc
+    entry point (two-pass on a fixed scratch): same arithmetic in the same
+    order, so the images are bit-identical (ragged grids included)."""
     w = synthetic.make_workload(name, **kw)
     if name == "denoise":
         w.geometry.stride = 3
@@ -66,12 +66,17 @@ def test_fused_tile_aggregation_equals_two_pass(name, kw):
     Y = ctx.extract(meas)
     K = [int(np.max(k)) for k in w.K_levels]
     sup, coef, keff = ctx.solve(Y, "plain", "fp32", K=K[:1], Kmax=K[0])
+    ctx.set_aggregate_path(2)
     ref = ctx.aggregate(sup, coef, keff)
+    ctx.set_aggregate_path(1)
+    two = ctx.aggregate(sup, coef, keff)
     out = torch.full_like(ref, float("nan"))
     b.csp_aggregate_noalloc(ctx._ctx, sup.data_ptr(), coef.data_ptr(), keff.data_ptr(), sup.shape[0],
                             sup.shape[1], out.data_ptr(), stream)
     torch.cuda.synchronize()
-    assert torch.equal(ref, out)
+    assert torch.equal(ref, out) and torch.equal(two, out)
+    with pytest.raises(b.CspError):
+        ctx.set_aggregate_path(3)
 
 
 def test_noalloc_rejects_oversized_batches():
