@@ -331,15 +331,24 @@ __global__ void synth_kernel(const float *__restrict__ D0, int N0, const int32_t
       rp[jj] = D0 + (int64_t)(jj < cnt ? __ldg(support + b * Kmax + j0 + jj) : 0) * N0;
       cj[jj] = jj < cnt ? __ldg(coef + b * Kmax + j0 + jj) : 0.f;
     }
-    for (int n = lane; n < N0; n += 32) {
-      float dv[8];
+    // two elements per pass: 16 loads in flight per lane
+    for (int n = lane; n < N0; n += 64) {
+      const bool two = n + 32 < N0;
+      float dv[8], dw[8];
 #pragma unroll
-      for (int jj = 0; jj < 8; ++jj) dv[jj] = jj < cnt ? __ldg(rp[jj] + n) : 0.f;
-      float v = j0 ? xb[n] : 0.f;
+      for (int jj = 0; jj < 8; ++jj) {
+        dv[jj] = jj < cnt ? __ldg(rp[jj] + n) : 0.f;
+        dw[jj] = (two && jj < cnt) ? __ldg(rp[jj] + n + 32) : 0.f;
+      }
+      float v = j0 ? xb[n] : 0.f, u = (two && j0) ? xb[n + 32] : 0.f;
 #pragma unroll
       for (int jj = 0; jj < 8; ++jj)
-        if (jj < cnt) v = fmaf(cj[jj], dv[jj], v);
+        if (jj < cnt) {
+          v = fmaf(cj[jj], dv[jj], v);
+          u = fmaf(cj[jj], dw[jj], u);
+        }
       xb[n] = v;
+      if (two) xb[n + 32] = u;
     }
   }
 }
@@ -357,18 +366,26 @@ __global__ void gather_kernel(GeomDev g, const float *__restrict__ Xh, int N0,
   const int pl = (int)(e / ((int64_t)g.W * g.H));
   const int y0 = cover_y[2 * y], y1 = cover_y[2 * y + 1];
   const int x0 = cover_x[2 * x], x1 = cover_x[2 * x + 1];
+  const int np = (y1 - y0 + 1) * (x1 - x0 + 1);
+  // covering patches in raster order, eight loads in flight, summed in order
   float acc = 0.f;
-  int cnt = 0;
-  for (int iy = y0; iy <= y1; ++iy) {
-    const int py = y - origin(iy, g.stride, g.H, g.P);
-    const float *row = Xh + ((int64_t)iy * g.nx) * N0 + (pl * g.P + py) * g.P;
-    for (int ix = x0; ix <= x1; ++ix) {
-      const int px = x - origin(ix, g.stride, g.W, g.P);
-      acc += __ldg(row + (int64_t)ix * N0 + px);
-      ++cnt;
+  int iy = y0, ix = x0;
+  for (int p0 = 0; p0 < np; p0 += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      v[u] = 0.f;
+      if (p0 + u < np) {
+        const int py = y - origin(iy, g.stride, g.H, g.P), px = x - origin(ix, g.stride, g.W, g.P);
+        v[u] = __ldg(Xh + ((int64_t)iy * g.nx + ix) * N0 + (pl * g.P + py) * g.P + px);
+        if (++ix > x1) { ix = x0; ++iy; }
+      }
     }
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (p0 + u < np) acc += v[u];
   }
-  img[e] = cnt ? acc / (float)cnt : 0.f;
+  img[e] = np ? acc / (float)np : 0.f;
 }
 
 // Fused synthesis + overlap-add over an output tile of TY x TX pixels (all
