@@ -138,7 +138,7 @@ __device__ bool grp_project(bool act, int s, int M, const float *aqp, const floa
 // One OMP iteration of every patch of a full-dictionary level.
 // ---------------------------------------------------------------------------
 template <int G, int NCH>
-__global__ void __launch_bounds__(WV_WARPS * 32, 5)
+__global__ void __launch_bounds__(WV_WARPS * 32)
 omp_update_wave_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                        const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
                        int64_t rbf_row0, int n_cand, const int8_t *__restrict__ Kp, int Kuni, OmpState st,

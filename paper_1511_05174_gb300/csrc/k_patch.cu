@@ -154,58 +154,68 @@ __global__ void effective_dict_pp_kernel(GeomDev g, const uint8_t *__restrict__ 
   A[e] = v;
 }
 
-// Candidate rows of per-pixel coded exposure at a restricted level: one warp
-// per (patch, candidate position c).  The warp locates position c in f(Omega_up)
-// in the order of the restricted kernels (parents in support order, each
-// parent's children in link order, at most cap), then writes
-// a_c[m] = sum_t pc_p[t][m] d_c[level index of (t, m)] -- the arithmetic of
-// effective_dict_pp_kernel -- and 1/||a_c|| (-1 for a zero row), the norm
-// reduced as in row_norms_kernel.
-__global__ void pp_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const float *__restrict__ D,
-                                     int N, int M, const int32_t *__restrict__ omega_up, int ldo_up,
-                                     const int8_t *__restrict__ keff_up, const int32_t *__restrict__ child_off,
-                                     const int32_t *__restrict__ child_idx, int cap, int64_t B,
-                                     float *__restrict__ Ac, float *__restrict__ invc) {
-  const int lane = threadIdx.x & 31;
-  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (w >= B * cap) return;
-  const int64_t b = w / cap;
-  const int c = (int)(w - b * cap);
-  // child counts of the parents (lane j: parent j), inclusive prefix sum
-  const int kup = keff_up[b];
-  int c0 = 0, cnt = 0;
-  if (lane < kup) {
-    const int p = omega_up[b * ldo_up + lane];
-    c0 = child_off[p];
-    cnt = child_off[p + 1] - c0;
-  }
-  int incl = cnt;
-  for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  // the parent holding position c: first lane with incl > c
-  const unsigned hit = __ballot_sync(0xffffffffu, lane < kup && incl > c);
-  if (!hit) return;  // c >= |f(Omega_up)|: no such candidate
-  const int j = __ffs(hit) - 1;
-  const int base = __shfl_sync(0xffffffffu, c0, j), before = __shfl_sync(0xffffffffu, incl - cnt, j);
-  const float *d = D + (int64_t)child_idx[base + (c - before)] * N;
-  const uint8_t *cb = pc + b * (int64_t)g.Lx * M;
-  float *row = Ac + w * M;
+// Candidate rows of per-pixel coded exposure at a restricted level: one CTA
+// per patch.  The CTA lists f(Omega_up) in the order of the restricted kernels
+// (parents in support order, each parent's children in link order, at most
+// cap) and tabulates, per (frame t, pixel m), the offset of the level element
+// d[level index of (t, m)] when the patch's code there is 1 (-1 otherwise);
+// then a warp per candidate c writes a_c[m] = sum_t pc_p[t][m] d_c[...] -- the
+// arithmetic and order of effective_dict_pp_kernel -- and 1/||a_c|| (-1 for a
+// zero row), the norm reduced as in row_norms_kernel.
+__global__ void __launch_bounds__(256)
+pp_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const float *__restrict__ D, int N, int M,
+                     const int32_t *__restrict__ omega_up, int ldo_up, const int8_t *__restrict__ keff_up,
+                     const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx, int cap,
+                     int64_t B, float *__restrict__ Ac, float *__restrict__ invc) {
+  extern __shared__ int sm_pp[];  // [F * M] element offsets (-1: code 0) | [cap] candidate atoms
+  const int64_t b = blockIdx.x;
+  if (b >= B) return;
   const int F = g.Lx;
-  float sq = 0.f;
-  for (int m = lane; m < M; m += 32) {
-    const int py = m / g.P, px = m - py * g.P;
-    float v = 0.f;
-    for (int t = 0; t < F; ++t)
-      if (cb[t * M + m]) v += __ldg(d + level_index(g, l, 0, t, py, px));
-    row[m] = v;
-    sq = fmaf(v, v, sq);
+  int *off = sm_pp;
+  int *cs = sm_pp + F * M;
+  __shared__ int s_nc;
+  const uint8_t *cb = pc + b * (int64_t)F * M;
+  for (int e = threadIdx.x; e < F * M; e += blockDim.x) {
+    const int t = e / M, m = e - t * M, py = m / g.P, px = m - py * g.P;
+    off[e] = cb[e] ? level_index(g, l, 0, t, py, px) : -1;
   }
-  for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-  if (lane == 0) {
-    const float nrm = sqrtf(sq);
-    invc[w] = nrm > 0.f ? 1.f / nrm : -1.f;
+  if (threadIdx.x == 0) {
+    const int kup = keff_up[b];
+    int nc = 0;
+    for (int j = 0; j < kup && nc < cap; ++j) {
+      const int p = omega_up[b * ldo_up + j];
+      for (int i = child_off[p]; i < child_off[p + 1] && nc < cap; ++i) cs[nc++] = child_idx[i];
+    }
+    s_nc = nc;
+  }
+  __syncthreads();
+  const int nc = s_nc;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < nc; c += nw) {
+    const float *d = D + (int64_t)cs[c] * N;
+    float *row = Ac + (b * cap + c) * (int64_t)M;
+    float sq = 0.f;
+    for (int m = lane; m < M; m += 32) {
+      float dv[8];
+      float v = 0.f;
+      for (int t0 = 0; t0 < F; t0 += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int o = t0 + u < F ? off[(t0 + u) * M + m] : -1;
+          dv[u] = o >= 0 ? __ldg(d + o) : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (t0 + u < F && off[(t0 + u) * M + m] >= 0) v += dv[u];
+      }
+      row[m] = v;
+      sq = fmaf(v, v, sq);
+    }
+    for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) {
+      const float nrm = sqrtf(sq);
+      invc[b * cap + c] = nrm > 0.f ? 1.f / nrm : -1.f;
+    }
   }
 }
 
@@ -601,8 +611,10 @@ void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const 
                           const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int32_t *child_off,
                           const int32_t *child_idx, int cap, int64_t B, float *Ac, float *invc, cudaStream_t s) {
   if (B == 0) return;
-  pp_candidates_kernel<<<blocks(B * cap * 32, 256), 256, 0, s>>>(g, pc, level, D, N, M, omega_up, ldo_up, keff_up,
-                                                                child_off, child_idx, cap, B, Ac, invc);
+  const size_t sm = sizeof(int) * ((size_t)g.Lx * M + cap);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(pp_candidates_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  pp_candidates_kernel<<<(unsigned)B, 256, sm, s>>>(g, pc, level, D, N, M, omega_up, ldo_up, keff_up, child_off,
+                                                    child_idx, cap, B, Ac, invc);
 }
 
 void launch_inv_row_norms(const float *A, int64_t rows, int M, float *inv, unsigned int *scratch, cudaStream_t s) {
