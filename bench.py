@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--variant", type=int, default=None,
+                    help="pin the restricted-solver variant (0-7) instead of autotuning (profiling runs)")
     ap.add_argument("--serving-jobs", type=int, default=24, help="jobs per offered rate")
     return ap.parse_args()
 
@@ -396,13 +398,18 @@ def main():
         if world > 1:
             dist.barrier()
 
+    if args.variant is not None:
+        ctx.set_kernel_variant(args.variant)
     for _ in range(max(args.warmup, 3)):
         step("cross_scale")
         step("plain")
     # the library's autotuner picks the restricted-solver variant for this shape (untimed)
-    ctx.extract(meas_d, Y)
-    tune = ctx.autotune(Y, "cross_scale", args.precision, K=K, Kmax=Kmax)
-    step("cross_scale")
+    if args.variant is None:
+        ctx.extract(meas_d, Y)
+        tune = ctx.autotune(Y, "cross_scale", args.precision, K=K, Kmax=Kmax)
+        step("cross_scale")
+    else:
+        tune = {"restricted_variant": args.variant, "ms": []}
     torch.cuda.synchronize()
 
     def timed(mode, sampler=None):
