@@ -321,6 +321,16 @@ csp_status csp_set_kernel_variant(csp_ctx *ctx, int restricted_variant);
  * another value. */
 csp_status csp_set_aggregate_path(csp_ctx *ctx, int path);
 
+/* Form of the full-dictionary OMP (plain OMP; the coarsest level of
+ * cross-scale OMP): 0 automatic (fused for the BF16 proxy when supported),
+ * 1 one launch per iteration for the proxy and one for the update, 2 fused:
+ * all iterations of 128 patches in one CTA with residuals and factors on
+ * chip (shared effective dictionary with T <= 256, a multiple of 64, M <= 64,
+ * K <= 8, BF16 precision; other shapes use form 1).  The two forms select the
+ * same atoms (same tensor-core proxy, FP32 re-score of its four best) and
+ * differ in FP32 rounding only.  CSP_ERR_INVALID for another value. */
+csp_status csp_set_top_level_form(csp_ctx *ctx, int form);
+
 /* ---- Instrumentation (not part of the paper's method) ----------------------
  * Every kernel launch of a context is counted per kernel kind.  While
  * profiling is enabled, each launch is also bracketed by CUDA events on its

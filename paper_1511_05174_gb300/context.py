@@ -160,6 +160,10 @@ class Context:
                            _stream_ptr(stream, self.device))
         return {"restricted_variant": r.restricted_variant, "ms": list(r.ms)}
 
+    def set_top_level_form(self, form: int) -> None:
+        """0 automatic, 1 per-iteration kernels, 2 fused full-dictionary kernel."""
+        b.csp_set_top_level_form(self._ctx, form)
+
     def set_aggregate_path(self, path: int) -> None:
         """0 automatic, 1 two-pass, 2 fused shared-memory tiles (same image)."""
         b.csp_set_aggregate_path(self._ctx, path)

@@ -107,7 +107,8 @@ csp_status ws_get_t(csp_ctx *ctx, Workspace &W, int slot, size_t count, T **out)
 }
 
 const char *const kKernelNames[KK_COUNT] = {"extract", "downsample", "prepare", "omp_init", "proxy_fp32",
-                                            "proxy_bf16", "omp_update", "restricted", "aggregate", "lift"};
+                                            "proxy_bf16", "omp_update", "restricted", "aggregate", "lift",
+                                            "omp_fused"};
 
 cudaEvent_t pool_event(csp_ctx *ctx) {
   if (!ctx->ev_pool.empty()) {
@@ -357,8 +358,25 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
     }
   }
 
-  // full-dictionary OMP at the top level (the only level in plain mode)
+  // full-dictionary OMP at the top level (the only level in plain mode): all
+  // iterations in one fused kernel when the dictionary is small and shared
+  bool fused_done = false;
   {
+    const LevelData &L = ctx->lv[top];
+    const bool want = ctx->top_form == 2 || (ctx->top_form == 0 && bf16);
+    if (want && bf16 && !L.per_patch && L.Mp == 64 && fused_top_supported(L.M, L.T, Kb[top])) {
+      fused_done = true;
+      for (int ph = 0; ph < nph && fused_done; ++ph)
+        run(ctx, KK_FUSED, s, n_of(ph), [&] {
+          fused_done &= launch_omp_fused_tc(Yl[top], L.M, L.A[ph], L.inv_norm[ph], L.Abf[ph], L.Mp, L.T, ids_of(ph),
+                                            n_of(ph), prm->K_patch[top], prm->K[top], Kb[top], lv_om[top],
+                                            lv_al[top], ldo[top], lv_ke[top], W.stats_dev,
+                                            (unsigned long long *)(W.stats_dev + 4), s);
+        });
+      if (!fused_done) return fail(ctx, CSP_ERR_CUDA, "fused full-dictionary kernel could not be launched");
+    }
+  }
+  if (!fused_done) {
     const LevelData &L = ctx->lv[top];
     const bool pp = L.per_patch;
     OmpState st{};
@@ -936,6 +954,13 @@ csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const floa
   ctx->restricted_variant = st == CSP_OK ? best : saved;
   out->restricted_variant = ctx->restricted_variant;
   return st;
+}
+
+csp_status csp_set_top_level_form(csp_ctx *ctx, int form) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (form < 0 || form > 2) return fail(ctx, CSP_ERR_INVALID, "unknown full-dictionary form");
+  ctx->top_form = form;
+  return CSP_OK;
 }
 
 csp_status csp_set_aggregate_path(csp_ctx *ctx, int path) {

@@ -84,7 +84,7 @@ struct Workspace {
 
 enum KernelKind {
   KK_EXTRACT, KK_DOWNSAMPLE, KK_PREP, KK_INIT, KK_PROXY_FP32, KK_PROXY_BF16, KK_UPDATE, KK_RESTRICTED,
-  KK_AGGREGATE, KK_LIFT, KK_COUNT
+  KK_AGGREGATE, KK_LIFT, KK_FUSED, KK_COUNT
 };
 struct ProfRec {
   int kind;
@@ -127,6 +127,7 @@ struct csp_ctx {
   bool prof = false;
   int restricted_variant = 2;  // restricted-OMP kernel variant (see launch_omp_restricted)
   int aggregate_path = 0;      // 0 automatic, 1 two-pass (synthesis scratch), 2 fused shared-memory tiles
+  int top_form = 0;            // full-dictionary level: 0 automatic, 1 per-iteration kernels, 2 fused kernel
   std::vector<csp::ProfRec> pending;
   std::vector<cudaEvent_t> ev_pool;
   // All device allocations (for the memory budget and destroy).
@@ -206,6 +207,15 @@ int proxy_bf16_splits(int64_t n, int T);
 bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, const __nv_bfloat16 *Abf, int T,
                        int64_t row0, const int32_t *ids, int64_t n, const uint8_t *flags, int32_t *cand,
                        unsigned long long *err, const float *pinv, uint32_t *part, cudaStream_t s);
+// Fused full-dictionary OMP (k_fused.cu): all Kb iterations of a shared
+// dictionary with T <= 256 (multiple of 64) atoms, M <= 64, Kb <= 8, BF16
+// tensor-core proxy with FP32 re-score; writes omega/alpha/k_eff directly.
+// Returns false when the shape is not supported or a tensor map fails.
+bool fused_top_supported(int M, int T, int Kb);
+bool launch_omp_fused_tc(const float *Y, int M, const float *A, const float *inv_norm, const __nv_bfloat16 *Abf,
+                         int Mp, int T, const int32_t *ids, int64_t n, const int8_t *Kp, int Kuni, int Kb,
+                         int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
+                         unsigned long long *err, cudaStream_t s);
 // Load-wave variants (k_grp.cu): one update iteration; restricted OMP with the Gram-matrix proxy.
 // a_pstride / inv_pstride: per-patch strides of A and inv_norm (0: shared by all patches).
 void launch_omp_update_wave(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,

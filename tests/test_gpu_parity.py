@@ -128,6 +128,53 @@ def test_independent_problems_nonunit_norms(B, M, T, K, prec):
     assert rate >= MATCH and worst <= REL_TOL, bad[:10]
 
 
+@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("B,M,T,K", [(1000, 64, 256, 6), (777, 64, 192, 5), (300, 16, 64, 3), (129, 32, 128, 8)])
+def test_full_dictionary_forms_agree_with_oracle(B, M, T, K, form):
+    """The fused full-dictionary kernel (form 2: every iteration of 128 patches
+    in one CTA) and the per-iteration kernels (form 1), BF16 proxy with FP32
+    re-score, against the oracle; ragged tiles, per-patch budgets."""
+    from paper_1511_05174_gb300.context import Context
+    A, Y, _ = synthetic.make_independent_problems(B, M, T, K, seed=5, sigma=0.05)
+    Kp = np.random.default_rng(6).integers(0, K + 1, size=B).astype(np.int8)
+    ctx = Context(0)
+    ctx.set_geometry(8, 8, (1, M // 64 if M >= 64 else M // 16), 8 if M >= 64 else 4, 8, [(1, 1, 1, 1)])
+    ctx.set_sensing("identity")
+    ctx.load_dictionary(0, A)
+    ctx.set_top_level_form(form)
+    ctx.profile(True)
+    sup, coef, keff = ctx.solve(torch.from_numpy(Y).cuda(), "plain", "bf16", K=[K],
+                                K_patch=[torch.from_numpy(Kp).cuda()], Kmax=K)
+    prof = ctx.profile_read()
+    assert ("omp_fused" in prof) == (form == 2)
+    o, a, k, _ = oracle.omp_batch([A] * len(Y), Y, [int(x) for x in Kp])
+    rate, worst, bad = compare(A, sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy().astype(int), o, a, k)
+    assert rate >= MATCH and worst <= REL_TOL, bad[:10]
+
+
+def test_fused_form_rejects_dependent_atom():
+    """Fused form: a_2 = a_0 + a_1 exactly (integer atoms, the other 61 atoms
+    zero and never eligible); the FP64 pivot test rejects a_2, k_eff = 2 and
+    the coefficients are the least squares ones, as in the oracle."""
+    from paper_1511_05174_gb300.context import Context
+    rng = np.random.default_rng(14)
+    A = np.zeros((64, 64), np.float32)
+    A[:2] = rng.integers(-3, 4, size=(2, 64))
+    A[2] = A[0] + A[1]
+    Y = np.stack([A[0] + 0.5 * A[1] + 0.01 * rng.standard_normal(64) for _ in range(40)]).astype(np.float32)
+    ctx = Context(0)
+    ctx.set_geometry(8, 8, (1, 1), 8, 8, [(1, 1, 1, 1)])
+    ctx.set_sensing("identity")
+    ctx.load_dictionary(0, A)
+    ctx.set_top_level_form(2)
+    sup, coef, keff = ctx.solve(torch.from_numpy(Y).cuda(), "plain", "bf16", K=[3], Kmax=3)
+    o, a, k, _ = oracle.omp_batch([A[:3]] * len(Y), Y, 3)
+    assert np.all(k == 2) and np.all(keff.cpu().numpy() == 2)
+    assert ctx.stats()["fp64_fallbacks"] >= 1
+    rate, worst, bad = compare(A[:3], sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy().astype(int), o, a, k)
+    assert rate == 1.0 and worst <= REL_TOL
+
+
 def test_degenerate_inputs():
     """Zero measurements (k_eff = 0), duplicate atoms (dependence), a zero
     atom (never chosen) and K = 1."""
