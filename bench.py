@@ -409,7 +409,7 @@ def main():
         tune = ctx.autotune(Y, "cross_scale", args.precision, K=K, Kmax=Kmax)
         step("cross_scale")
     else:
-        tune = {"restricted_variant": args.variant, "ms": []}
+        tune = {"restricted_variant": args.variant, "ms": [], "top_level_form": 0, "ms_top": []}
     torch.cuda.synchronize()
 
     def timed(mode, sampler=None):
@@ -521,7 +521,9 @@ def main():
             "data": "synthetic (seeded; Gaussian unit-norm atoms, K-sparse N(0,1) codes)",
             "config": {**workload_config(w, args), "form": "cross_scale", "precision": args.precision,
                        "restricted_variant": tune["restricted_variant"],
-                       "autotune_ms": [round(t, 4) for t in tune["ms"]]},
+                       "autotune_ms": [round(t, 4) for t in tune["ms"]],
+                       "top_level_form": tune.get("top_level_form"),
+                       "top_level_ms": [round(t, 4) for t in tune.get("ms_top", [])]},
             "plain_omp": {"value": plain_value, "unit": UNIT, "ms_per_step": pl_ms / args.steps,
                           "kernels": kernels_plain},
             "speedup_cross_scale_vs_plain": value / plain_value,

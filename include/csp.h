@@ -295,12 +295,18 @@ csp_status csp_job_release(csp_server *srv, uint64_t job_id);
  * M <= 64, twice that for larger M).  csp_autotune runs
  * csp_solve once per variant on the given batch (same arguments as
  * csp_solve, outputs overwritten), times each with CUDA events, keeps the
- * fastest for this context and reports the times.  Synchronises `stream`. */
+ * fastest for this context and reports the times; then, with that variant,
+ * times the two forms of the full-dictionary level (csp_set_top_level_form)
+ * where the fused form applies and keeps the faster.  Synchronises `stream`. */
 #define CSP_TUNE_VARIANTS 8  /* 0: L2-cooperative, 1: shared-memory staged, 2-4: Gram-matrix proxy, 5-7: Gram-Schmidt
                                 form, each narrow to wide */
 typedef struct csp_tune_result {
     int restricted_variant;            /* chosen variant index                      */
     double ms[CSP_TUNE_VARIANTS];      /* solve time per variant (ms)               */
+    int top_level_form;                /* chosen full-dictionary form (1 or 2), see
+                                          csp_set_top_level_form                     */
+    double ms_top[2];                  /* solve time with form 1 and form 2 (0 when
+                                          form 2 does not apply)                     */
 } csp_tune_result;
 
 csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const float *Y, int64_t B,

@@ -158,7 +158,8 @@ class Context:
         keff = torch.empty((Bn,), dtype=torch.int8, device=self.device)
         r = b.csp_autotune(self._ctx, p, Y.data_ptr(), Bn, sup.data_ptr(), coef.data_ptr(), keff.data_ptr(),
                            _stream_ptr(stream, self.device))
-        return {"restricted_variant": r.restricted_variant, "ms": list(r.ms)}
+        return {"restricted_variant": r.restricted_variant, "ms": list(r.ms), "top_level_form": r.top_level_form,
+                "ms_top": list(r.ms_top)}
 
     def set_top_level_form(self, form: int) -> None:
         """0 automatic, 1 per-iteration kernels, 2 fused full-dictionary kernel."""

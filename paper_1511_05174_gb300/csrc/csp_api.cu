@@ -949,10 +949,34 @@ csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const floa
     out->ms[v] = ms;
     if (ms < best_ms) { best_ms = ms; best = v; }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   ctx->restricted_variant = st == CSP_OK ? best : saved;
   out->restricted_variant = ctx->restricted_variant;
+  // full-dictionary form: per-iteration kernels (1) against the fused kernel (2)
+  const int saved_form = ctx->top_form;
+  out->top_level_form = 1;
+  out->ms_top[0] = out->ms_top[1] = 0.0;
+  const int nl = params->mode == CSP_MODE_PLAIN ? 1 : ctx->geom.n_levels;
+  const LevelData &LT = ctx->lv[nl - 1];
+  const int Ktop = params->K_patch[nl - 1] ? params->Kmax : params->K[nl - 1];
+  const bool fusable = params->precision == CSP_PREC_BF16 && !LT.per_patch && LT.Mp == 64 &&
+                       fused_top_supported(LT.M, LT.T, Ktop);
+  for (int form = 1; form <= (fusable ? 2 : 1) && st == CSP_OK; ++form) {
+    ctx->top_form = form;
+    st = csp_solve(ctx, params, Y, B, support_out, coef_out, k_eff_out, stream);
+    if (st != CSP_OK) break;
+    cudaEventRecord(e0, s);
+    st = csp_solve(ctx, params, Y, B, support_out, coef_out, k_eff_out, stream);
+    cudaEventRecord(e1, s);
+    if (st != CSP_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) { st = fail(ctx, CSP_ERR_CUDA, "event synchronize failed"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    out->ms_top[form - 1] = ms;
+  }
+  if (st == CSP_OK && fusable) out->top_level_form = out->ms_top[1] < out->ms_top[0] ? 2 : 1;
+  ctx->top_form = st == CSP_OK ? out->top_level_form : saved_form;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   return st;
 }
 

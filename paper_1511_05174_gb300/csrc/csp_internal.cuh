@@ -16,10 +16,16 @@ namespace csp {
 //  - kTauPivot: the FP32 Cholesky pivot d = ||a||^2 - ||w||^2 is trusted when
 //    d / ||a||^2 >= kTauPivot; below it the projection is redone in FP64.
 //  - kEpsD64: in FP64, an atom with L_kk <= kEpsD64 * ||a_k|| depends on the
-//    chosen atoms and ends the patch (same test as a QR pivot |R_kk|).
+//    chosen atoms and ends the patch.  The FP64 factor comes from the normal
+//    equations A_S^T A_S, whose rounding leaves L_kk of an exactly dependent
+//    atom near sqrt(eps_64) ||a_k|| (about 1e-8), not near eps ||a_k|| as a QR
+//    pivot would; the threshold sits above that floor.  It classifies atoms
+//    like the oracle's QR test (|R_kk| <= 1e-10 ||a_k||) except those whose
+//    distance from the chosen atoms' span lies between 1e-10 and 3e-7 of
+//    their norm.
 //  - kEpsR32: the patch ends when ||r||^2 <= kEpsR32 * ||y||^2 (FP32 noise floor).
 constexpr float kTauPivot = 1e-3f;
-constexpr double kEpsD64 = 1e-10;
+constexpr double kEpsD64 = 3e-7;
 constexpr float kEpsR32 = 1e-12f;
 
 constexpr int kMaxPhases = 4;      // Bayer: 4 mosaic phases; other operators: 1

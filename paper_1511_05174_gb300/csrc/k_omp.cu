@@ -11,7 +11,8 @@
 //   residue     r = y - A_Omega alpha
 // When the pivot ratio (||a_k||^2 - ||w||^2) / ||a_k||^2 falls below
 // kTauPivot the factor is rebuilt from scratch in FP64 for that patch, which
-// also decides linear dependence (L_kk <= kEpsD64 ||a_k||) like a QR pivot.
+// also decides linear dependence (L_kk <= kEpsD64 ||a_k||, the FP64 analogue of
+// a QR pivot test above the rounding floor of the normal equations).
 //
 // Work decomposition: a GROUP of G lanes (G = 4, 8 or 16) solves one patch;
 // a warp holds 32 / G patches.  Lane s of a group owns the float4 chunks

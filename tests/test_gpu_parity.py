@@ -341,3 +341,7 @@ def test_autotune_picks_a_variant():
     r = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
     assert r["restricted_variant"] in range(8) and all(t > 0 for t in r["ms"])
     assert r["ms"][r["restricted_variant"]] == min(r["ms"])
+    # the BF16 Bayer coarse level (T = 256, M = 64, K = 4) has both full-dictionary forms
+    r2 = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
+    assert r2["top_level_form"] in (1, 2) and r2["ms_top"][0] > 0 and r2["ms_top"][1] > 0
+    assert r2["ms_top"][r2["top_level_form"] - 1] == min(r2["ms_top"])
