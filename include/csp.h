@@ -328,7 +328,7 @@ csp_status csp_set_kernel_variant(csp_ctx *ctx, int restricted_variant);
 csp_status csp_set_aggregate_path(csp_ctx *ctx, int path);
 
 /* Form of the full-dictionary OMP (plain OMP; the coarsest level of
- * cross-scale OMP): 0 automatic (fused for the BF16 proxy when supported),
+ * cross-scale OMP): 0 automatic (form 1 unless csp_autotune chose form 2),
  * 1 one launch per iteration for the proxy and one for the update, 2 fused:
  * all iterations of 128 patches in one CTA with residuals and factors on
  * chip (shared effective dictionary with T <= 256, a multiple of 64, M <= 64,

@@ -363,7 +363,7 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
   bool fused_done = false;
   {
     const LevelData &L = ctx->lv[top];
-    const bool want = ctx->top_form == 2 || (ctx->top_form == 0 && bf16);
+    const bool want = ctx->top_form == 2;  // 0: per-iteration kernels unless csp_autotune chose the fused form
     if (want && bf16 && !L.per_patch && L.Mp == 64 && fused_top_supported(L.M, L.T, Kb[top])) {
       fused_done = true;
       for (int ph = 0; ph < nph && fused_done; ++ph)

@@ -86,13 +86,16 @@ __device__ __forceinline__ float pair_sum(float v) { return v + __shfl_xor_sync(
 // with its register chunks.
 __device__ __forceinline__ float half_dot(const float *row, int h, const float4 (&v)[FZ_NCH]) {
   const float4 *r4 = reinterpret_cast<const float4 *>(row + h * FZ_HALF);
-  float s = 0.f;
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;  // four independent chains
 #pragma unroll
   for (int t = 0; t < FZ_NCH; ++t) {
     const float4 a = r4[t];
-    s = fmaf(a.x, v[t].x, fmaf(a.y, v[t].y, fmaf(a.z, v[t].z, fmaf(a.w, v[t].w, s))));
+    s0 = fmaf(a.x, v[t].x, s0);
+    s1 = fmaf(a.y, v[t].y, s1);
+    s2 = fmaf(a.z, v[t].z, s2);
+    s3 = fmaf(a.w, v[t].w, s3);
   }
-  return s;
+  return (s0 + s1) + (s2 + s3);
 }
 
 // BF16 copy of this thread's half of the residual into row `row` of the
@@ -248,17 +251,23 @@ omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__rest
       asm volatile("bar.sync 1, 256;" ::: "memory");
       if (*s_flag) break;
       tc_fence_after();
-      uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;  // two independent chains
       for (int c0 = 0; c0 < hcols; c0 += 32) {
         uint32_t v[32];
         tmem_ld32_nowait(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ehalf * hcols + c0), v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int base = ehalf * hcols + c0;
+        const int base = ehalf * hcols + c0;  // T is a multiple of 64: every column is an atom
         const uint32_t cb = imask - (uint32_t)base;
 #pragma unroll
-        for (int i = 0; i < 32; ++i)
-          if (base + i < T) top4_insert((v[i] & smask) | (cb - (uint32_t)i), a0, a1, a2, a3);
+        for (int i = 0; i < 32; i += 2) {
+          top4_insert((v[i] & smask) | (cb - (uint32_t)i), a0, a1, a2, a3);
+          top4_insert((v[i + 1] & smask) | (cb - (uint32_t)(i + 1)), b0, b1, b2, b3);
+        }
       }
+      top4_insert(b0, a0, a1, a2, a3);
+      top4_insert(b1, a0, a1, a2, a3);
+      top4_insert(b2, a0, a1, a2, a3);
+      top4_insert(b3, a0, a1, a2, a3);
       tc_fence_before();
       if (ehalf == 1) {
         cand[erow * 4 + 0] = a0;
@@ -278,17 +287,24 @@ omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__rest
       // ---- update: a thread pair per patch ----
       act = act && k < Kpb && !(rsq <= kEpsR32 * ysq);
       unsigned long long best = 0ull;
+      int ci[4];
+      float sc[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const uint32_t key = cand[p * 4 + c];
-        const int ci = key ? (int)(imask - (key & imask)) : -1;
+        ci[c] = key ? (int)(imask - (key & imask)) : -1;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) sc[c] = half_dot(a_fp + (ci[c] >= 0 ? ci[c] : 0) * FZ_MP, h, rv);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        sc[c] = pair_sum(sc[c]);
         bool taken = false;
-        if (act && ci >= 0)
-          for (int j = 0; j < k; ++j) taken |= (omp[j] == ci);
-        const float sc = pair_sum(half_dot(a_fp + (ci >= 0 ? ci : 0) * FZ_MP, h, rv));
-        const float inv = ci >= 0 ? s_inv[ci] : -1.f;
-        if (act && ci >= 0 && inv > 0.f && !taken) {
-          const unsigned long long kk = pack_key(fabsf(sc) * inv, ci);
+        if (act && ci[c] >= 0)
+          for (int j = 0; j < k; ++j) taken |= (omp[j] == ci[c]);
+        const float inv = ci[c] >= 0 ? s_inv[ci[c]] : -1.f;
+        if (act && ci[c] >= 0 && inv > 0.f && !taken) {
+          const unsigned long long kk = pack_key(fabsf(sc[c]) * inv, ci[c]);
           best = kk > best ? kk : best;
         }
       }
