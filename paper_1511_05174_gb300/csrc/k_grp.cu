@@ -469,6 +469,8 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
   load_chunks<G, NCH>(yv, yrow, nv, s, valid);
   const int nc = gram_setup<G, NCH>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
                                    inv_norm, stats, M, A, yv, p0);
+  // lane steps over the candidates (c = s + u G) any group of this warp needs, at most 8
+  const int ucnt = min(8, __reduce_max_sync(kFull, (nc + G - 1) / G));
   const float ysq = gsum<G>(dotc<NCH>(yv, yv));
   float rsq = ysq;
   bool act = valid && Kpb > 0;
@@ -507,7 +509,7 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int c = s + u * G;
-      gpre[u] = (act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
+      gpre[u] = (u < ucnt && act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
     }
     const float aa = act ? __ldg(gram + (int64_t)q * T + q) : 0.f;  // ||a_q||^2
     const bool f32 = act && !(fl & 2);
@@ -567,7 +569,8 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
     // q depends on the chosen columns: its FP32 attempt overwrote S.W; alpha of
     // the chosen ones again from the (unchanged) factor
     const bool restore = f32 && !appended;
-    grp_backsub<G>(restore, s, k - 1, __reduce_max_sync(kFull, restore ? k - 1 : 0), S);
+    if (__any_sync(kFull, restore))
+      grp_backsub<G>(restore, s, k - 1, __reduce_max_sync(kFull, restore ? k - 1 : 0), S);
     if (appended && s == 0) {
       S.om[k] = q;
       S.colp[k] = A + (int64_t)q * M;
@@ -616,7 +619,7 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int c = s + u * G;
-          if (c < nc) Gc[k * ldg + c] = gpre[u];
+          if (u < ucnt && c < nc) Gc[k * ldg + c] = gpre[u];
         }
         for (int c0 = s + 8 * G; c0 < nc; c0 += 8 * G) {
           float gr[8];
@@ -709,6 +712,8 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
   load_chunks<G, NCH>(yv, yrow, nv, s, valid);
   const int nc = gram_setup<G, NCH>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
                                    inv_norm, stats, M, A, yv, p0);
+  // lane steps over the candidates (c = s + u G) any group of this warp needs, at most 8
+  const int ucnt = min(8, __reduce_max_sync(kFull, (nc + G - 1) / G));
   for (int c = s; c < nc; c += G) cc[c] = p0[c];
   __syncwarp();
   const float ysq = gsum<G>(dotc<NCH>(yv, yv));
@@ -746,7 +751,7 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const int c = s + u * G;
-      gpre[u] = (act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
+      gpre[u] = (u < ucnt && act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
     }
     const float aa = act ? __ldg(gram + (int64_t)q * T + q) : 0.f;
     const bool f32 = act && !(fl & 2);
@@ -788,7 +793,7 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int c = s + u * G;
-        if (c < nc) {
+        if (u < ucnt && c < nc) {
           float v = gpre[u];
           for (int j = 0; j < k; ++j) v = fmaf(-S.W[j], Qc[j * ldg + c], v);
           v *= il;
@@ -813,7 +818,8 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
     // q depends on the chosen columns: alpha of the chosen ones from the FP32
     // factor (S.W held w); FP64-mode patches still hold their last alpha
     const bool restore = f32 && !ok32 && !app64;
-    grp_backsub<G>(restore, s, k - 1, __reduce_max_sync(kFull, restore ? k - 1 : 0), S);
+    if (__any_sync(kFull, restore))
+      grp_backsub<G>(restore, s, k - 1, __reduce_max_sync(kFull, restore ? k - 1 : 0), S);
     if (app64 && s == 0) {
       S.om[k] = q;
       S.colp[k] = A + (int64_t)q * M;

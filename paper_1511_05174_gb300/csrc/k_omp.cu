@@ -133,7 +133,8 @@ __device__ bool grp_append(bool act, int s, int M, const float *aqp, const float
   // q depends on the chosen columns: its FP32 attempt overwrote S.W; alpha of
   // the chosen ones again from the (unchanged) factor
   const bool restore = f32 && !appended;
-  grp_backsub<G>(restore, s, k - 1, __reduce_max_sync(kFull, restore ? k - 1 : 0), S);
+  if (__any_sync(kFull, restore))
+    grp_backsub<G>(restore, s, k - 1, __reduce_max_sync(kFull, restore ? k - 1 : 0), S);
   // residue r = y - A_Omega alpha
   if (appended) {
 #pragma unroll
