@@ -158,7 +158,7 @@ enum Slot {
   WS_LV_OMEGA, WS_LV_ALPHA = WS_LV_OMEGA + CSP_MAX_LEVELS, WS_LV_KEFF = WS_LV_ALPHA + CSP_MAX_LEVELS,
   WS_LV_Y = WS_LV_KEFF + CSP_MAX_LEVELS,
   WS_XH = WS_LV_Y + CSP_MAX_LEVELS,
-  WS_SCRATCH, WS_LIFT, WS_LIFTBF, WS_PPC_A, WS_PPC_INV, WS_PART,
+  WS_SCRATCH, WS_LIFT, WS_LIFTBF, WS_PPC_A, WS_PPC_INV, WS_PART, WS_KEYS,
   WS_COUNT
 };
 
@@ -390,12 +390,21 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
       if (!bf16) CSP_TRY(ws_get_t(ctx, W, WS_LIFT, (size_t)B * L.N, &Zl));
       else CSP_TRY(ws_get_t(ctx, W, WS_LIFTBF, (size_t)B * L.Np, &Zbf));
     }
-    // partial top-4 keys when the tensor-core proxy splits the atoms over CTAs
+    // partial top-4 keys when the tensor-core proxy splits the atoms over CTAs;
+    // best keys of the split FP32 proxy (zeroed here, left zeroed by each use)
     uint32_t *part = nullptr;
+    unsigned long long *keys = nullptr;
     if (bf16) {
       int S = 1;
       for (int ph = 0; ph < nph; ++ph) S = std::max(S, proxy_bf16_splits(n_of(ph), L.T));
       if (S > 1) CSP_TRY(ws_get_t(ctx, W, WS_PART, (size_t)B * S * 4, &part));
+    } else {
+      int S = 1;
+      for (int ph = 0; ph < nph; ++ph) S = std::max(S, proxy_fp32_splits(n_of(ph), L.T));
+      if (S > 1) {
+        CSP_TRY(ws_get_t(ctx, W, WS_KEYS, (size_t)B, &keys));
+        CSP_CUDA(ctx, cudaMemsetAsync(keys, 0, (size_t)B * sizeof(unsigned long long), s));
+      }
     }
     st.Kb = Kb[top];
     st.ldo = ldo[top];
@@ -427,10 +436,10 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
           run(ctx, KK_PROXY_FP32, s, n_of(ph), [&] {
             if (pp)
               launch_proxy_fp32(Zl, L.N, L.D, nullptr, L.T, ids_of(ph), n_of(ph), st.omega, st.ldo, st.k_eff, st.flags,
-                                st.cand, ps.inv_pp[top], s);
+                                st.cand, ps.inv_pp[top], keys, s);
             else
               launch_proxy_fp32(st.R, L.M, L.A[ph], L.inv_norm[ph], L.T, ids_of(ph), n_of(ph), st.omega, st.ldo,
-                                st.k_eff, st.flags, st.cand, nullptr, s);
+                                st.k_eff, st.flags, st.cand, nullptr, keys, s);
           });
       }
       for (int ph = 0; ph < nph; ++ph)

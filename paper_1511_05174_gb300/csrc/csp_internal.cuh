@@ -198,10 +198,13 @@ struct OmpState {
 // order (row p holds patch perm[p]; perm == nullptr: identity).
 void launch_omp_init(const float *Y, int64_t B, int M, int Mp, const int32_t *perm, OmpState st, cudaStream_t s);
 // pinv: optional per-patch inverse norms [B][T] (per-patch Phi), else inv_norm[T].
+// keys: optional [B] zeroed scratch; with few patch tiles the atoms are then
+// split over several CTAs per tile whose best keys meet there (keys are left zeroed).
+int proxy_fp32_splits(int64_t n, int T);
 void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_norm, int T,
                        const int32_t *ids, int64_t n, const int32_t *omega, int ldo,
                        const int8_t *k_eff, const uint8_t *flags, int32_t *cand, const float *pinv,
-                       cudaStream_t s);
+                       unsigned long long *keys, cudaStream_t s);
 bool proxy_bf16_supported(int M, int T);
 bool omp_dims_supported(int M);  // M % 4 == 0 and M <= 256
 // Tensor-core proxy over the patches at sorted positions row0 .. row0 + n - 1

@@ -203,110 +203,170 @@ __global__ void omp_init_kernel(const float *__restrict__ Y, int64_t B, int M, i
 }
 
 // ---------------------------------------------------------------------------
-// FP32 proxy: tile of 64 patches x all atoms.  256 threads as 16 x 16, each
-// owning 4 patches x 4 atoms of every 64-atom tile.
+// FP32 proxy (FP32 CUDA cores): a tile of 128 patches x 128 atoms per step,
+// 256 threads as 16 x 16, each owning 8 patches x 8 atoms; the contraction
+// over M runs in chunks of 16 through double-buffered shared memory (the next
+// chunk is loaded into registers while the current one is used).  Fused
+// epilogue: |score| / ||a_i|| (shared or per-patch norms), chosen atoms masked
+// through a per-tile bit set, running argmax as packed keys (ties to the lowest
+// index).  With few patch tiles the atoms are split over grid.y CTAs whose
+// best keys meet in `keys` by atomicMax; proxy_keys_kernel then writes cand.
 // ---------------------------------------------------------------------------
-constexpr int PX_TP = 64, PX_TA = 64, PX_KC = 32, PX_AS = PX_TA + 4;
+constexpr int PF_TP = 128, PF_TA = 128, PF_KC = 16, PF_LD = PF_TP + 4;
 
-__global__ void __launch_bounds__(256)
+__host__ __device__ inline size_t proxy_fp32_smem(int ldo) {
+  return sizeof(float) * 4 * PF_KC * PF_LD + sizeof(uint32_t) * PF_TP * 4 + sizeof(int) * (PF_TP * ldo + PF_TP) +
+         sizeof(int64_t) * PF_TP + 16;
+}
+
+__global__ void __launch_bounds__(256, 1)
 proxy_fp32_kernel(const float *__restrict__ R, int M, const float *__restrict__ A,
                   const float *__restrict__ inv_norm, int T, const int32_t *__restrict__ ids,
                   int64_t n, const int32_t *__restrict__ omega, int ldo,
                   const int8_t *__restrict__ k_eff, const uint8_t *__restrict__ flags,
-                  int32_t *__restrict__ cand, const float *__restrict__ pinv) {
+                  int32_t *__restrict__ cand, const float *__restrict__ pinv, int tiles_per_split,
+                  unsigned long long *__restrict__ keys) {
   extern __shared__ __align__(16) float smem[];
-  const int Mr = (M + PX_KC - 1) / PX_KC * PX_KC;
-  float *Rs = smem;                      // [Mr][PX_TP]  residuals, measurement-major
-  float *As = Rs + (size_t)Mr * PX_TP;   // [PX_KC][PX_AS] atom chunk, measurement-major
-  int *Om = (int *)(As + PX_KC * PX_AS); // [PX_TP][ldo]
-  int *Kc = Om + PX_TP * ldo;            // [PX_TP]
-  int64_t *Pb = reinterpret_cast<int64_t *>(Kc + PX_TP + (PX_TP & 1));  // [PX_TP] patch ids
-  const int tid = threadIdx.x;
-  const int64_t p0 = (int64_t)blockIdx.x * PX_TP;
-
-  for (int e = tid; e < PX_TP * Mr; e += 256) {
-    const int p = e / Mr, m = e - p * Mr;
+  float *Rs = smem;                             // [2][PF_KC][PF_LD]  residual chunk, k-major
+  float *As = Rs + 2 * PF_KC * PF_LD;           // [2][PF_KC][PF_LD]  atom chunk, k-major
+  uint32_t *msk = reinterpret_cast<uint32_t *>(As + 2 * PF_KC * PF_LD);  // [PF_TP][4] chosen atoms of the tile
+  int *Om = reinterpret_cast<int *>(msk + PF_TP * 4);                    // [PF_TP][ldo]
+  int *Kc = Om + PF_TP * ldo;                                            // [PF_TP]
+  int64_t *Pb = reinterpret_cast<int64_t *>(reinterpret_cast<uintptr_t>(Kc + PF_TP + 3) & ~uintptr_t(7));
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int64_t p0 = (int64_t)blockIdx.x * PF_TP;
+  for (int p = tid; p < PF_TP; p += 256) {
     const int64_t pi = p0 + p;
-    float v = 0.f;
-    if (pi < n && m < M) {
-      const int64_t b = ids ? ids[pi] : pi;
-      v = R[b * M + m];
-    }
-    Rs[m * PX_TP + p] = v;
-  }
-  for (int e = tid; e < PX_TP * ldo; e += 256) {
-    const int p = e / ldo, j = e - p * ldo;
-    const int64_t pi = p0 + p;
-    Om[e] = (pi < n) ? omega[(ids ? ids[pi] : pi) * ldo + j] : -1;
-  }
-  for (int p = tid; p < PX_TP; p += 256) {
-    const int64_t pi = p0 + p;
-    const int64_t bb = (pi < n) ? (ids ? ids[pi] : pi) : 0;
-    Kc[p] = (pi < n) ? k_eff[bb] : 0;
+    const int64_t bb = pi < n ? (ids ? ids[pi] : pi) : 0;
+    Kc[p] = pi < n ? k_eff[bb] : 0;
     Pb[p] = bb;
   }
-
-  const int ty = tid >> 4, tx = tid & 15;
-  unsigned long long best[4] = {0ull, 0ull, 0ull, 0ull};
-  for (int a0 = 0; a0 < T; a0 += PX_TA) {
-    float acc[4][4] = {};
-    for (int m0 = 0; m0 < Mr; m0 += PX_KC) {
-      __syncthreads();
-      for (int e = tid; e < PX_TA * PX_KC; e += 256) {
-        const int a = e / PX_KC, mm = e - a * PX_KC;
-        const int ai = a0 + a, m = m0 + mm;
-        As[mm * PX_AS + a] = (ai < T && m < M) ? __ldg(A + (int64_t)ai * M + m) : 0.f;
-      }
-      __syncthreads();
-#pragma unroll 8
-      for (int mm = 0; mm < PX_KC; ++mm) {
-        const float4 rv = *reinterpret_cast<const float4 *>(Rs + (m0 + mm) * PX_TP + ty * 4);
-        const float4 av = *reinterpret_cast<const float4 *>(As + mm * PX_AS + tx * 4);
-        const float r4[4] = {rv.x, rv.y, rv.z, rv.w};
-        const float a4[4] = {av.x, av.y, av.z, av.w};
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(r4[i], a4[j], acc[i][j]);
-      }
+  __syncthreads();
+  for (int e = tid; e < PF_TP * ldo; e += 256) {
+    const int p = e / ldo;
+    Om[e] = (p0 + p < n) ? omega[Pb[p] * ldo + (e - p * ldo)] : -1;
+  }
+  // global -> register chunk loader: thread t covers row t / 2, k offsets (t & 1) * 8 .. + 7
+  const int lrow = tid >> 1, lk = (tid & 1) * 8;
+  const bool rrow_ok = p0 + lrow < n;
+  const float *rrow = R + (rrow_ok ? Pb[lrow] : 0) * (int64_t)M;
+  const int a_lo = blockIdx.y * tiles_per_split * PF_TA;
+  const int a_hi = min(T, a_lo + tiles_per_split * PF_TA);
+  unsigned long long best[8] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
+  for (int a0 = a_lo; a0 < a_hi; a0 += PF_TA) {
+    const bool arow_ok = a0 + lrow < T;
+    const float *arow = A + (arow_ok ? a0 + lrow : 0) * (int64_t)M;
+    __syncthreads();  // the previous tile's epilogue no longer reads msk
+    for (int e = tid; e < PF_TP * 4; e += 256) msk[e] = 0u;
+    __syncthreads();
+    for (int e = tid; e < PF_TP * ldo; e += 256) {
+      const int p = e / ldo, j = e - p * ldo, a = Om[e] - a0;
+      if (j < Kc[p] && a >= 0 && a < PF_TA) atomicOr(&msk[p * 4 + (a >> 5)], 1u << (a & 31));
     }
+    float acc[8][8];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int ai = a0 + tx * 4 + j;
-      if (ai >= T) continue;
-      const float invs = pinv ? 1.f : __ldg(inv_norm + ai);
-      if (!(invs > 0.f)) continue;
+    for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        // per-patch norms (per-patch Phi): 1/||Phi_p U d_i|| from the patch's row of the table
-        const float inv = pinv ? __ldg(pinv + Pb[ty * 4 + i] * (int64_t)T + ai) : invs;
-        if (!(inv > 0.f)) continue;
+      for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    float4 gr[2], ga[2];
+    auto load = [&](int k0) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = k0 + lk + 4 * h;
+        gr[h] = (rrow_ok && k < M) ? __ldg(reinterpret_cast<const float4 *>(rrow + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        ga[h] = (arow_ok && k < M) ? __ldg(reinterpret_cast<const float4 *>(arow + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    };
+    auto stash = [&](int buf) {
+      float *rs = Rs + buf * PF_KC * PF_LD, *as = As + buf * PF_KC * PF_LD;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = lk + 4 * h;
+        rs[(k + 0) * PF_LD + lrow] = gr[h].x;
+        rs[(k + 1) * PF_LD + lrow] = gr[h].y;
+        rs[(k + 2) * PF_LD + lrow] = gr[h].z;
+        rs[(k + 3) * PF_LD + lrow] = gr[h].w;
+        as[(k + 0) * PF_LD + lrow] = ga[h].x;
+        as[(k + 1) * PF_LD + lrow] = ga[h].y;
+        as[(k + 2) * PF_LD + lrow] = ga[h].z;
+        as[(k + 3) * PF_LD + lrow] = ga[h].w;
+      }
+    };
+    load(0);
+    stash(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < M; k0 += PF_KC) {
+      const bool more = k0 + PF_KC < M;
+      if (more) load(k0 + PF_KC);
+      const float *rs = Rs + buf * PF_KC * PF_LD, *as = As + buf * PF_KC * PF_LD;
+#pragma unroll 4
+      for (int kk = 0; kk < PF_KC; ++kk) {
+        const float4 r0 = *reinterpret_cast<const float4 *>(rs + kk * PF_LD + ty * 8);
+        const float4 r1 = *reinterpret_cast<const float4 *>(rs + kk * PF_LD + ty * 8 + 4);
+        const float4 x0 = *reinterpret_cast<const float4 *>(as + kk * PF_LD + tx * 8);
+        const float4 x1 = *reinterpret_cast<const float4 *>(as + kk * PF_LD + tx * 8 + 4);
+        const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+        const float av[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(rv[i], av[j], acc[i][j]);
+      }
+      if (more) stash(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+    // epilogue: masked angle scores, running argmax per patch
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int p = ty * 8 + i;
+      const uint32_t m32 = msk[p * 4 + (tx >> 2)];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int ai = a0 + tx * 8 + j;
+        if (ai >= a_hi) continue;
+        const float inv = pinv ? __ldg(pinv + Pb[p] * (int64_t)T + ai) : __ldg(inv_norm + ai);
+        if (!(inv > 0.f) || ((m32 >> ((tx & 3) * 8 + j)) & 1u)) continue;
         const unsigned long long key = pack_key(fabsf(acc[i][j]) * inv, ai);
-        if (key > best[i]) {
-          const int p = ty * 4 + i;
-          bool chosen = false;
-          for (int q = 0; q < Kc[p]; ++q) chosen |= (Om[p * ldo + q] == ai);
-          if (!chosen) best[i] = key;
-        }
+        best[i] = key > best[i] ? key : best[i];
       }
     }
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < 8; ++i) {
     unsigned long long v = best[i];
 #pragma unroll
     for (int o = 8; o; o >>= 1) {
       const unsigned long long w = __shfl_xor_sync(kFull, v, o);
       v = w > v ? w : v;
     }
-    const int64_t pi = p0 + ty * 4 + i;
+    const int64_t pi = p0 + ty * 8 + i;
     if (tx == 0 && pi < n) {
-      const int64_t b = ids ? ids[pi] : pi;
-      cand[b * kTopP] = v ? key_idx(v) : -1;
+      const int64_t b = Pb[ty * 8 + i];
+      if (keys) {
+        if (v) atomicMax(keys + b, v);
+      } else {
+        cand[b * kTopP] = v ? key_idx(v) : -1;
 #pragma unroll
-      for (int c = 1; c < kTopP; ++c) cand[b * kTopP + c] = -1;
+        for (int c = 1; c < kTopP; ++c) cand[b * kTopP + c] = -1;
+      }
     }
   }
+}
+
+// Split atom range: cand from the merged best keys (and the keys reset for the
+// next iteration).
+__global__ void proxy_keys_kernel(unsigned long long *__restrict__ keys, const int32_t *__restrict__ ids, int64_t n,
+                                  int32_t *__restrict__ cand) {
+  const int64_t wi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (wi >= n) return;
+  const int64_t b = ids ? ids[wi] : wi;
+  const unsigned long long v = keys[b];
+  keys[b] = 0ull;
+  cand[b * kTopP] = v ? key_idx(v) : -1;
+#pragma unroll
+  for (int c = 1; c < kTopP; ++c) cand[b * kTopP + c] = -1;
 }
 
 constexpr int GRP_WARPS = 4;
@@ -640,21 +700,39 @@ void launch_omp_init(const float *Y, int64_t B, int M, int Mp, const int32_t *pe
   omp_init_kernel<<<blocks((n + 3) / 4, 256), 256, 0, s>>>(Y, B, M, Mp, perm, st);
 }
 
+int proxy_fp32_splits(int64_t n, int T) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  }
+  const int64_t tiles = (n + PF_TP - 1) / PF_TP;
+  const int n_at = (T + PF_TA - 1) / PF_TA;
+  if (tiles >= 2 * sms || n_at < 2) return 1;
+  const int S = (int)((2 * sms + tiles - 1) / tiles);  // about two CTAs per SM
+  return S < n_at ? S : n_at;
+}
+
 void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_norm, int T,
                        const int32_t *ids, int64_t n, const int32_t *omega, int ldo,
                        const int8_t *k_eff, const uint8_t *flags, int32_t *cand, const float *pinv,
-                       cudaStream_t s) {
+                       unsigned long long *keys, cudaStream_t s) {
   if (n == 0) return;
-  const int Mr = (M + PX_KC - 1) / PX_KC * PX_KC;
-  const size_t sm = sizeof(float) * ((size_t)Mr * PX_TP + PX_KC * PX_AS) + sizeof(int) * (PX_TP * ldo + PX_TP + 2) +
-                    sizeof(int64_t) * PX_TP;
+  const size_t sm = proxy_fp32_smem(ldo);
   static size_t configured = 0;
   if (sm > 48 * 1024 && sm > configured) {
     cudaFuncSetAttribute(proxy_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     configured = sm;
   }
-  proxy_fp32_kernel<<<blocks(n, PX_TP), 256, sm, s>>>(R, M, A, inv_norm, T, ids, n, omega, ldo, k_eff,
-                                                      flags, cand, pinv);
+  const int n_all = (T + PF_TA - 1) / PF_TA;
+  const int S = keys ? proxy_fp32_splits(n, T) : 1;
+  const int tps = (n_all + S - 1) / S;
+  const dim3 grid((unsigned)((n + PF_TP - 1) / PF_TP), (unsigned)((n_all + tps - 1) / tps));
+  unsigned long long *kk = grid.y > 1 ? keys : nullptr;
+  proxy_fp32_kernel<<<grid, 256, sm, s>>>(R, M, A, inv_norm, T, ids, n, omega, ldo, k_eff, flags, cand, pinv, tps,
+                                          kk);
+  if (kk) proxy_keys_kernel<<<blocks(n, 256), 256, 0, s>>>(kk, ids, n, cand);
 }
 
 // (G, NCH) of the restricted kernel: wide groups (one candidate per lane).
