@@ -337,6 +337,15 @@ csp_status csp_set_aggregate_path(csp_ctx *ctx, int path);
  * differ in FP32 rounding only.  CSP_ERR_INVALID for another value. */
 csp_status csp_set_top_level_form(csp_ctx *ctx, int form);
 
+/* Test hook for failure detection (not part of the method).  on != 0: the
+ * tensor-core proxy's TMA producer issues no atom-tile loads, so the MMA
+ * thread's bounded mbarrier wait expires (after about 2 s), the kernel records
+ * an error code, every CTA leaves its pipeline and frees its tensor memory,
+ * and csp_solve_stats_get returns CSP_ERR_TIMEOUT.  Nothing faults; with the
+ * hook off again the context solves normally.  Applies to BF16 solves that use
+ * the per-iteration form. */
+csp_status csp_set_wait_test(csp_ctx *ctx, int on);
+
 /* ---- Instrumentation (not part of the paper's method) ----------------------
  * Every kernel launch of a context is counted per kernel kind.  While
  * profiling is enabled, each launch is also bracketed by CUDA events on its

@@ -161,6 +161,10 @@ class Context:
         return {"restricted_variant": r.restricted_variant, "ms": list(r.ms), "top_level_form": r.top_level_form,
                 "ms_top": list(r.ms_top)}
 
+    def set_wait_test(self, on: bool) -> None:
+        """Failure-detection test hook (see csp_set_wait_test)."""
+        b.csp_set_wait_test(self._ctx, on)
+
     def set_top_level_form(self, form: int) -> None:
         """0 automatic, 1 per-iteration kernels, 2 fused full-dictionary kernel."""
         b.csp_set_top_level_form(self._ctx, form)

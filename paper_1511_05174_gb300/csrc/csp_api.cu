@@ -427,10 +427,10 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
         if (bf16)
           run(ctx, KK_PROXY_BF16, s, n_of(ph), [&] {
             maps_ok &= pp ? launch_proxy_bf16(Zbf, B, L.Np, L.Dbf, L.T, 0, ids_of(ph), n_of(ph), st.flags, st.cand,
-                                              (unsigned long long *)(W.stats_dev + 4), ps.inv_pp[top], part, s)
+                                              (unsigned long long *)(W.stats_dev + 4), ps.inv_pp[top], part, ctx->wait_test, s)
                           : launch_proxy_bf16(st.Rbf, B, L.Mp, L.Abf[ph], L.T, phased ? ps.phase_start[ph] : 0,
                                               ids_of(ph), n_of(ph), st.flags, st.cand,
-                                              (unsigned long long *)(W.stats_dev + 4), nullptr, part, s);
+                                              (unsigned long long *)(W.stats_dev + 4), nullptr, part, ctx->wait_test, s);
           });
         else
           run(ctx, KK_PROXY_FP32, s, n_of(ph), [&] {
@@ -987,6 +987,12 @@ csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const floa
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return st;
+}
+
+csp_status csp_set_wait_test(csp_ctx *ctx, int on) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  ctx->wait_test = on != 0;
+  return CSP_OK;
 }
 
 csp_status csp_set_top_level_form(csp_ctx *ctx, int form) {

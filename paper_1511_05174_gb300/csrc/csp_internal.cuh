@@ -134,6 +134,7 @@ struct csp_ctx {
   int restricted_variant = 2;  // restricted-OMP kernel variant (see launch_omp_restricted)
   int aggregate_path = 0;      // 0 automatic, 1 two-pass (synthesis scratch), 2 fused shared-memory tiles
   int top_form = 0;            // full-dictionary level: 0 automatic, 1 per-iteration kernels, 2 fused kernel
+  bool wait_test = false;      // test hook: the tensor-core proxy loads no atom tiles (its waits expire)
   std::vector<csp::ProfRec> pending;
   std::vector<cudaEvent_t> ev_pool;
   // All device allocations (for the memory budget and destroy).
@@ -215,7 +216,8 @@ bool omp_dims_supported(int M);  // M % 4 == 0 and M <= 256
 int proxy_bf16_splits(int64_t n, int T);
 bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, const __nv_bfloat16 *Abf, int T,
                        int64_t row0, const int32_t *ids, int64_t n, const uint8_t *flags, int32_t *cand,
-                       unsigned long long *err, const float *pinv, uint32_t *part, cudaStream_t s);
+                       unsigned long long *err, const float *pinv, uint32_t *part, bool wait_test,
+                       cudaStream_t s);
 // Fused full-dictionary OMP (k_fused.cu): all Kb iterations of a shared
 // dictionary with T <= 256 (multiple of 64) atoms, M <= 64, Kb <= 8, BF16
 // tensor-core proxy with FP32 re-score; writes omega/alpha/k_eff directly.

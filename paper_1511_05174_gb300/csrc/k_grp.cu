@@ -171,7 +171,11 @@ omp_update_wave_kernel(const float *__restrict__ Y, int M, const float *__restri
   load_chunks<G, NCH>(rv, st.R + b * M, nv, s, valid);
   int candr[kTopP];
 #pragma unroll
-  for (int c = 0; c < kTopP; ++c) candr[c] = (valid && c < n_cand) ? st.cand[b * kTopP + c] : -1;
+  for (int c = 0; c < kTopP; ++c) {
+    // a candidate outside [0, T) (never written by an aborted proxy) is no candidate
+    const int cv = (valid && c < n_cand) ? st.cand[b * kTopP + c] : -1;
+    candr[c] = (cv >= 0 && cv < T) ? cv : -1;
+  }
   int omr[KPL];
   float zr[KPL];
 #pragma unroll

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
 proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__ CUtensorMap tmA, int Mp, int T,
                 int nt, int idx_bits, int64_t row0, int64_t n, const int32_t *__restrict__ ids,
                 const uint8_t *__restrict__ flags, int32_t *__restrict__ cand, unsigned long long *err,
-                const float *__restrict__ pinv, int tiles_per_split, uint32_t *__restrict__ part) {
+                const float *__restrict__ pinv, int tiles_per_split, uint32_t *__restrict__ part, int wait_test) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const TcLayout lay = tc_layout(Mp, nt);
@@ -130,7 +130,8 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
       mbar_expect_tx(rfull, (uint32_t)lay.r_bytes);
       for (int kb = 0; kb < lay.kb; ++kb)
         tma_load_2d(r_tile + kb * TC_M * 128, &tmR, kb * 64, (int)(row0 + tile0), rfull);
-      const int n_chunks = n_at * lay.kb;
+      // wait test: no atom tiles are loaded, so the MMA thread's bounded wait expires
+      const int n_chunks = wait_test ? 0 : n_at * lay.kb;
       for (int t = 0; t < n_chunks && ok; ++t) {
         const int s = t % NS, use = t / NS;
         if (use >= 1) ok = mbar_wait(empty + s, (uint32_t)((use - 1) & 1), err, 1);
@@ -343,7 +344,8 @@ int proxy_bf16_splits(int64_t n, int T) {
 
 bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, const __nv_bfloat16 *Abf, int T,
                        int64_t row0, const int32_t *ids, int64_t n, const uint8_t *flags, int32_t *cand,
-                       unsigned long long *err, const float *pinv, uint32_t *part, cudaStream_t s) {
+                       unsigned long long *err, const float *pinv, uint32_t *part, bool wait_test,
+                       cudaStream_t s) {
   if (n == 0) return true;
   const int nt = tile_atoms(Mp);
   CUtensorMap mR, mA;
@@ -365,7 +367,7 @@ bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, con
   const int tps = (n_all + S - 1) / S;
   const dim3 grid((unsigned)((n + TC_M - 1) / TC_M), (unsigned)((n_all + tps - 1) / tps));
   proxy_tc_kernel<<<grid, TC_THREADS, sm, s>>>(mR, mA, Mp, T, nt, idx_bits, row0, n, ids, flags, cand, err, pinv,
-                                               tps, grid.y > 1 ? part : nullptr);
+                                               tps, grid.y > 1 ? part : nullptr, wait_test ? 1 : 0);
   if (grid.y > 1)
     proxy_merge_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(part, (int)grid.y, idx_bits, n, ids, flags, cand);
   return true;

@@ -331,6 +331,35 @@ def test_restricted_variants_agree_with_oracle(key, variant):
     assert rate >= MATCH and worst <= REL_TOL, bad[:10]
 
 
+def test_expired_device_wait_is_reported_and_context_recovers():
+    """Failure detection without a fault: with the test hook the tensor-core
+    proxy loads no atom tiles, its bounded wait expires, the solve reports
+    CSP_ERR_TIMEOUT through the statistics; afterwards the same context solves
+    correctly."""
+    from paper_1511_05174_gb300 import _binding as b
+    from paper_1511_05174_gb300.context import Context
+    w = _workload("bayer")
+    ctx = Context(0)
+    ctx.load_workload(w)
+    ctx.set_top_level_form(1)
+    Y = ctx.extract(torch.from_numpy(w.meas).cuda())
+    K, K_patch, Kmax = budgets(w, "cross_scale")
+    ctx.set_wait_test(True)
+    ctx.solve(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
+    torch.cuda.synchronize()
+    with pytest.raises(b.CspError) as e:
+        ctx.stats()
+    assert e.value.status == b.CSP_ERR_TIMEOUT
+    ctx.set_wait_test(False)
+    sup, coef, keff = ctx.solve(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
+    st = ctx.stats()
+    assert st["patches"] == w.n_patches
+    o, a, k, _ = oracle.cross_scale_omp(w)
+    rate, worst, bad = compare(w.dicts[0], sup.cpu().numpy(), coef.cpu().numpy(),
+                               keff.cpu().numpy().astype(np.int64), o, a, k)
+    assert rate >= MATCH and worst <= REL_TOL
+
+
 def test_autotune_picks_a_variant():
     from paper_1511_05174_gb300.context import Context
     w = _workload("bayer")
