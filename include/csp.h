@@ -61,6 +61,9 @@ typedef int csp_status;
 #define CSP_SENSE_CODED_EXPOSURE 2  /* video CS: per-pixel binary code per frame, M = P * P   */
 #define CSP_SENSE_CODED_APERTURE 3  /* light-field CS: per-shot binary code per view,
                                        M = shots * P * P                                     */
+#define CSP_SENSE_DENSE          4  /* patch CS: one dense Phi (M x N) for every patch,
+                                       M = shots; measurements are per patch (pass Y to
+                                       csp_solve directly: no extraction)                   */
 
 #define CSP_MODE_PLAIN        0     /* Algorithm 1 on the fine dictionary                    */
 #define CSP_MODE_CROSS_SCALE  1     /* Algorithm 2 over all loaded levels                    */
@@ -85,14 +88,17 @@ typedef struct csp_geometry {
                                   next.  W = box average, U = nearest replicate, W U = I. */
 } csp_geometry;
 
-/* Sensing operator.  `codes` is a HOST pointer, copied by the library:
- *   CODED_EXPOSURE: uint8 [planes][H][W] (frame-major), values 0/1;
- *   CODED_APERTURE: uint8 [shots][planes], values 0/1;
+/* Sensing operator.  `codes` and `phi` are HOST pointers, copied by the library:
+ *   CODED_EXPOSURE: codes uint8 [planes][H][W] (frame-major), values 0/1;
+ *   CODED_APERTURE: codes uint8 [shots][planes], values 0/1;
+ *   DENSE: phi float32 [shots][planes * P * P] row-major (shots = M, a multiple
+ *          of 4, at most 256), the same Phi for every patch;
  *   otherwise ignored (may be NULL). */
 typedef struct csp_sensing {
     int kind;
     int shots;
     const uint8_t *codes;
+    const float *phi;
 } csp_sensing;
 
 /* Solve parameters.

@@ -169,6 +169,8 @@ def meas_dim(g, sensing) -> int:
         return g.P * g.P
     if sensing.kind == "coded_aperture":
         return sensing.codes.shape[0] * g.P * g.P
+    if sensing.kind == "dense":
+        return sensing.codes.shape[0]
     raise ValueError(sensing.kind)
 
 
@@ -191,6 +193,8 @@ def phi_apply(sensing, g, oy: int, ox: int, V: np.ndarray) -> np.ndarray:
     if sensing.kind == "coded_aperture":
         c = sensing.codes.astype(np.float64)                             # [S, V]
         return np.einsum("sv,nvyx->nsyx", c, X).reshape(n, -1)
+    if sensing.kind == "dense":                                          # one Phi [M, N] for every patch
+        return V @ sensing.codes.astype(np.float64).T
     raise ValueError(sensing.kind)
 
 
@@ -202,7 +206,7 @@ def sensing_matrix(sensing, g, oy: int, ox: int) -> np.ndarray:
 
 def phi_key(sensing, oy: int, ox: int, b: int):
     """Patches with the same key share Phi_p."""
-    if sensing.kind in ("identity", "coded_aperture"):
+    if sensing.kind in ("identity", "coded_aperture", "dense"):
         return 0
     if sensing.kind == "bayer_rggb":
         return (int(oy) % 2, int(ox) % 2)
@@ -220,6 +224,8 @@ def extract_patches(w) -> np.ndarray:
     P = g.P
     m = w.meas.astype(np.float64)
     B = len(oy)
+    if s.kind == "dense":  # the measurements are per patch already
+        return m.reshape(B, -1).copy()
     out = np.zeros((B, meas_dim(g, s)))
     for b in range(B):
         if s.kind == "identity":

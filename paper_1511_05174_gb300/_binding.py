@@ -21,7 +21,7 @@ CSP_ERR_CUDA = -4
 CSP_ERR_TIMEOUT = -5
 CSP_ERR_UNSUPPORTED = -6
 
-SENSE = {"identity": 0, "bayer_rggb": 1, "coded_exposure": 2, "coded_aperture": 3}
+SENSE = {"identity": 0, "bayer_rggb": 1, "coded_exposure": 2, "coded_aperture": 3, "dense": 4}
 MODE = {"plain": 0, "cross_scale": 1}
 PREC = {"fp32": 0, "bf16": 1}
 
@@ -49,7 +49,7 @@ class csp_geometry(ctypes.Structure):
 
 
 class csp_sensing(ctypes.Structure):
-    _fields_ = [("kind", ctypes.c_int), ("shots", ctypes.c_int), ("codes", ctypes.c_void_p)]
+    _fields_ = [("kind", ctypes.c_int), ("shots", ctypes.c_int), ("codes", ctypes.c_void_p), ("phi", ctypes.c_void_p)]
 
 
 class csp_solve_params(ctypes.Structure):

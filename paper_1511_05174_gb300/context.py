@@ -61,11 +61,19 @@ class Context:
         self._planes = int(plane_grid[0]) * int(plane_grid[1])
 
     def set_sensing(self, kind: str, codes: Optional[np.ndarray] = None, shots: int = 0) -> None:
+        """codes: uint8 codes (coded exposure / aperture) or, for "dense", Phi
+        float32 [M, N] (shots = M is then taken from its shape)."""
         s = b.csp_sensing()
         s.kind = b.SENSE[kind]
+        self._codes = None
+        if kind == "dense":
+            self._codes = np.ascontiguousarray(codes, dtype=np.float32)
+            s.phi = self._codes.ctypes.data
+            shots = self._codes.shape[0]
+        elif codes is not None:
+            self._codes = np.ascontiguousarray(codes, dtype=np.uint8)
+            s.codes = self._codes.ctypes.data
         s.shots = int(shots)
-        self._codes = None if codes is None else np.ascontiguousarray(codes, dtype=np.uint8)
-        s.codes = self._codes.ctypes.data if self._codes is not None else None
         b.csp_set_sensing(self._ctx, s)
         self.B, self.M = b.csp_problem_size(self._ctx)
         self.sense_kind = kind

@@ -244,8 +244,11 @@ csp_status prepare(csp_ctx *ctx, cudaStream_t s) {
       } else {
         CSP_TRY(dev_alloc_t(ctx, &L.A[p], (size_t)L.T * L.M));
         run(ctx, KK_PREP, s, (int64_t)L.T * L.M, [&] {
-          launch_effective_dict(ctx->gd, ctx->sense_kind, ctx->shots, ctx->codes, l, p, L.D, L.T, L.N, L.A[p],
-                                L.M, s);
+          if (ctx->sense_kind == CSP_SENSE_DENSE)
+            launch_effective_dict_dense(ctx->gd, ctx->phi, l, L.D, L.T, L.N, L.A[p], L.M, s);
+          else
+            launch_effective_dict(ctx->gd, ctx->sense_kind, ctx->shots, ctx->codes, l, p, L.D, L.T, L.N, L.A[p],
+                                  L.M, s);
         });
       }
       CSP_TRY(dev_alloc_t(ctx, &L.inv_norm[p], (size_t)L.T));
@@ -631,6 +634,8 @@ csp_status csp_set_geometry(csp_ctx *ctx, const csp_geometry *geom) {
   ctx->codes = nullptr;
   dev_free(ctx, ctx->pcodes);
   ctx->pcodes = nullptr;
+  dev_free(ctx, ctx->phi);
+  ctx->phi = nullptr;
   dev_free(ctx, ctx->phase_ids);
   ctx->phase_ids = nullptr;
   ctx->has_sensing = false;
@@ -673,6 +678,11 @@ csp_status csp_set_sensing(csp_ctx *ctx, const csp_sensing *sensing) {
       M = sensing->shots * PP;
       code_bytes = (size_t)sensing->shots * planes;
       break;
+    case CSP_SENSE_DENSE:
+      if (!sensing->phi || sensing->shots < 4 || sensing->shots % 4)
+        return fail(ctx, CSP_ERR_INVALID, "dense sensing needs phi and M = shots, a positive multiple of 4");
+      M = sensing->shots;
+      break;
     default: return fail(ctx, CSP_ERR_INVALID, "unknown sensing kind");
   }
   if (M > 256) return fail(ctx, CSP_ERR_UNSUPPORTED, "measurement dimension above 256 is not supported");
@@ -682,6 +692,13 @@ csp_status csp_set_sensing(csp_ctx *ctx, const csp_sensing *sensing) {
   if (code_bytes) {
     CSP_TRY(dev_alloc_t(ctx, &ctx->codes, code_bytes));
     CSP_CUDA(ctx, cudaMemcpy(ctx->codes, sensing->codes, code_bytes, cudaMemcpyHostToDevice));
+  }
+  dev_free(ctx, ctx->phi);
+  ctx->phi = nullptr;
+  if (sensing->kind == CSP_SENSE_DENSE) {
+    const size_t n = (size_t)M * planes * PP;
+    CSP_TRY(dev_alloc_t(ctx, &ctx->phi, n));
+    CSP_CUDA(ctx, cudaMemcpy(ctx->phi, sensing->phi, n * sizeof(float), cudaMemcpyHostToDevice));
   }
   // patches grouped by Bayer phase (a single group for every other operator)
   dev_free(ctx, ctx->phase_ids);
@@ -790,6 +807,8 @@ csp_status csp_extract_patches(csp_ctx *ctx, const float *meas, float *Y_out, in
   if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
   if (!ctx->has_geom || !ctx->has_sensing) return fail(ctx, CSP_ERR_NOT_READY, "geometry and sensing must be set");
   if (!meas || !Y_out) return fail(ctx, CSP_ERR_INVALID, "NULL buffer");
+  if (ctx->sense_kind == CSP_SENSE_DENSE)
+    return fail(ctx, CSP_ERR_UNSUPPORTED, "dense sensing measures each patch: pass the measurements to csp_solve");
   DeviceGuard dg(ctx->device);
   run(ctx, KK_EXTRACT, (cudaStream_t)stream, ctx->B * ctx->M, [&] {
     launch_extract(ctx->gd, ctx->sense_kind, ctx->shots, meas, Y_out, ctx->B, ctx->M, (cudaStream_t)stream);

@@ -108,6 +108,7 @@ struct csp_ctx {
   csp::GeomDev gd{};
   int sense_kind = -1, shots = 0;
   uint8_t *codes = nullptr;     // device copy of the codes
+  float *phi = nullptr;         // dense sensing: device copy of Phi [M][planes * P * P]
   size_t codes_bytes = 0;
   int64_t B = 0;
   int M = 0;
@@ -156,6 +157,9 @@ void launch_norms(const float *A, int T, int M, int Mp, float *inv_norm, __nv_bf
 // Per-patch sensing (per-pixel coded exposure): A_p = Phi_p U_l D for every patch
 // ([B][T][P*P]), inverse row norms over `rows` rows (scratch: one device uint),
 // BF16 rows of D (unnormalised, padded to Np), lifted residual z = U_l^T Phi_p^T r.
+// Dense Phi: A[i][m] = sum_n Phi[m][n] (U_l d_i)[n] (level-0 patch index n).
+void launch_effective_dict_dense(const GeomDev &g, const float *phi, int level, const float *D, int T, int N,
+                                 float *A, int M, cudaStream_t s);
 void launch_patch_codes(const GeomDev &g, const uint8_t *codes, int64_t B, uint8_t *pc, cudaStream_t s);
 void launch_effective_dict_pp(const GeomDev &g, const uint8_t *pc, int level, const float *D, int T, int N,
                               float *A, int64_t B, cudaStream_t s);

@@ -219,6 +219,26 @@ pp_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const flo
   }
 }
 
+// Dense Phi (the same for every patch): a_i = Phi U_l d_i, one thread per
+// (atom i, measurement m), the level-0 patch index n = (plane, py, px) mapped
+// to its level-l element by U_l (nearest replication).
+__global__ void effective_dict_dense_kernel(GeomDev g, const float *__restrict__ phi, int l,
+                                            const float *__restrict__ D, int T, int N, float *__restrict__ A,
+                                            int M) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)T * M) return;
+  const int i = (int)(e / M), m = (int)(e - (int64_t)i * M);
+  const int PP = g.P * g.P, N0 = g.Ly * g.Lx * PP;
+  const float *d = D + (int64_t)i * N;
+  const float *row = phi + (int64_t)m * N0;
+  float v = 0.f;
+  for (int n = 0; n < N0; ++n) {
+    const int pl = n / PP, r = n - pl * PP, py = r / g.P, px = r - py * g.P;
+    v = fmaf(__ldg(row + n), __ldg(d + level_index(g, l, pl / g.Lx, pl % g.Lx, py, px)), v);
+  }
+  A[e] = v;
+}
+
 // Row norms of a [rows][M] matrix: out = ||row|| (first pass), running max
 // of the norms in *mx (float bits, non-negative, compared as integers).
 __global__ void row_norms_kernel(const float *__restrict__ A, int64_t rows, int M, float *__restrict__ out,
@@ -592,6 +612,12 @@ bool launch_aggregate_tiled(const GeomDev &g, const float *D0, int N0, const int
   agg_tile_kernel<<<grid, 512, p.smem, s>>>(g, D0, N0, support, coef, k_eff, Kmax, cover_y, cover_x, p.TY, p.TX,
                                              p.ldp, p.nq, img);
   return true;
+}
+
+void launch_effective_dict_dense(const GeomDev &g, const float *phi, int level, const float *D, int T, int N,
+                                 float *A, int M, cudaStream_t s) {
+  if ((int64_t)T * M == 0) return;
+  effective_dict_dense_kernel<<<blocks((int64_t)T * M, 256), 256, 0, s>>>(g, phi, level, D, T, N, A, M);
 }
 
 void launch_patch_codes(const GeomDev &g, const uint8_t *codes, int64_t B, uint8_t *pc, cudaStream_t s) {

@@ -40,7 +40,7 @@ from typing import List, Optional, Sequence, Tuple
 
 import numpy as np
 
-WORKLOAD_NAMES = ("denoise", "bayer", "video", "lightfield", "inpaint")
+WORKLOAD_NAMES = ("denoise", "bayer", "video", "lightfield", "inpaint", "cs_dense")
 
 # Stream indices of the seed sequence; one independent stream per ingredient.
 _S_DICT, _S_SUBSET, _S_SUPPORT, _S_VALUES, _S_NOISE, _S_CODES, _S_KPATCH, _N_STREAMS = range(8)
@@ -89,7 +89,7 @@ class Sensing:
     """Camera model.  ``codes`` is uint8: coded exposure [F, H, W]; coded
     aperture [S, V] (shot x view); None for identity and Bayer."""
 
-    kind: str  # "identity" | "bayer_rggb" | "coded_exposure" | "coded_aperture"
+    kind: str  # "identity" | "bayer_rggb" | "coded_exposure" | "coded_aperture" | "dense"
     codes: Optional[np.ndarray] = None
 
 
@@ -266,7 +266,34 @@ def _presets(name: str, links: str):
         geo = dict(kind="image", H=512, W=512, plane_grid=(1, 1), P=8, stride=4,
                    level_factors=[(1, 1, 1, 1), (1, 1, 2, 2)])
         return geo, 1024, [8, 4] if links == "paper" else [8, 8], 0.005, "coded_exposure"
+    if name == "cs_dense":
+        # compressive sensing of each patch with one dense Gaussian Phi (32 x 64)
+        geo = dict(kind="image", H=128, W=128, plane_grid=(1, 1), P=8, stride=4,
+                   level_factors=[(1, 1, 1, 1), (1, 1, 2, 2)])
+        return geo, 512, [6, 3] if links == "paper" else [6, 6], 0.005, "dense"
     raise ValueError(f"unknown workload {name!r}; expected one of {WORKLOAD_NAMES}")
+
+
+DENSE_M = 32  # measurements per patch of the dense-Phi workload
+
+
+def _patch_origins(extent: int, P: int, stride: int) -> np.ndarray:
+    """Origins 0, s, 2s, ... <= extent - P, plus extent - P if the stride misses it."""
+    o = list(range(0, extent - P + 1, stride))
+    if o[-1] != extent - P:
+        o.append(extent - P)
+    return np.asarray(o, np.int64)
+
+
+def _simulate_patches(phi: np.ndarray, truth: np.ndarray, g: Geometry, sigma: float, rng_noise) -> np.ndarray:
+    """Per-patch measurements y_p = Phi x_p + e (Sec. III-C) of every patch of
+    the grid, raster order: [B, M]."""
+    P = g.P
+    oy, ox = _patch_origins(g.H, P, g.stride), _patch_origins(g.W, P, g.stride)
+    X = np.stack([truth[:, y:y + P, x:x + P].ravel() for y in oy for x in ox])
+    m = X @ phi.astype(np.float64).T
+    m = m + sigma * rng_noise.standard_normal(m.shape)
+    return m.astype(np.float32)
 
 
 def make_workload(name: str, seed: int = 0, links: str = "paper", H: Optional[int] = None,
@@ -313,12 +340,18 @@ def make_workload(name: str, seed: int = 0, links: str = "paper", H: Optional[in
         codes = (rng[_S_CODES].random((g.planes, g.H, g.W)) < 0.5).astype(np.uint8)
     elif skind == "coded_aperture":
         codes = (rng[_S_CODES].random((shots, g.planes)) < 0.5).astype(np.uint8)
+    elif skind == "dense":
+        N = g.planes * g.P * g.P
+        codes = (rng[_S_CODES].standard_normal((DENSE_M, N)) / np.sqrt(DENSE_M)).astype(np.float32)
     else:
         codes = None
     sensing = Sensing(skind, codes)
 
     truth = _truth_image(g, dicts[0], children, dicts[-1].shape[0], K_tile, rng[_S_SUPPORT], rng[_S_VALUES])
-    meas = _simulate_camera(sensing, truth, sigma, rng[_S_NOISE])
+    if skind == "dense":  # per-patch measurements [B, M]
+        meas = _simulate_patches(codes, truth, g, sigma, rng[_S_NOISE])
+    else:
+        meas = _simulate_camera(sensing, truth, sigma, rng[_S_NOISE])
     return Workload(name, g, sensing, dicts, parents, K_levels, truth, meas, sigma, seed, links)
 
 

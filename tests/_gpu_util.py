@@ -22,7 +22,8 @@ def run_gpu(w, mode="cross_scale", precision="fp32", ctx=None):
     ctx = ctx or Context(0)
     ctx.load_workload(w)
     meas = torch.from_numpy(np.ascontiguousarray(w.meas)).cuda()
-    Y = ctx.extract(meas)
+    # dense Phi: the measurements are per patch already ([B, M])
+    Y = meas.contiguous() if w.sensing.kind == "dense" else ctx.extract(meas)
     K, K_patch, Kmax = budgets(w, mode)
     sup, coef, keff = ctx.solve(Y, mode, precision, K=K, K_patch=K_patch, Kmax=Kmax)
     img = ctx.aggregate(sup, coef, keff)

@@ -26,6 +26,7 @@ SMALL = {
     "lightfield": dict(name="lightfield", H=48, W=48, T0=2048),
     "video": dict(name="video", H=48, W=48, T0=1024),
     "inpaint": dict(name="inpaint", H=64, W=56, T0=512),
+    "cs_dense": dict(name="cs_dense", H=64, W=72, T0=512),
 }
 
 
@@ -41,7 +42,7 @@ def _workload(key, links="paper", **kw):
     return w
 
 
-@pytest.mark.parametrize("key", list(SMALL))
+@pytest.mark.parametrize("key", [k for k in SMALL if k != "cs_dense"])
 def test_extract_is_exact(key):
     w = _workload(key)
     g = run_gpu(w, "plain")
@@ -75,7 +76,19 @@ def test_cross_scale_parity(key, links, prec):
     assert g["stats"]["overflow"] == 0
 
 
-@pytest.mark.parametrize("key", ["denoise", "bayer", "lightfield", "video", "inpaint"])
+def test_dense_sensing_has_no_extraction():
+    from paper_1511_05174_gb300 import _binding as b
+    from paper_1511_05174_gb300.context import Context
+    w = _workload("cs_dense")
+    ctx = Context(0)
+    ctx.load_workload(w)
+    assert ctx.M == w.sensing.codes.shape[0]
+    with pytest.raises(b.CspError) as e:
+        ctx.extract(torch.zeros(64, 72, device="cuda"))
+    assert e.value.status == b.CSP_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("key", ["denoise", "bayer", "lightfield", "video", "inpaint", "cs_dense"])
 def test_aggregate_matches_oracle(key):
     """Overlap-add of the GPU's own codes against the oracle's aggregation of
     the same codes."""

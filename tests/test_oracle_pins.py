@@ -223,7 +223,7 @@ def test_patch_origins_ragged_tail():
     assert synthetic.patch_count_1d(10, 4, 4) == 3
 
 
-@pytest.mark.parametrize("name", ["denoise", "bayer", "video", "lightfield", "inpaint"])
+@pytest.mark.parametrize("name", ["denoise", "bayer", "video", "lightfield", "inpaint", "cs_dense"])
 def test_WU_identity_and_nearest_neighbour(name):
     """W U = I on R^{N_low} (Sec. III-C), U replicates each coarse entry."""
     w = synthetic.make_workload(name, H=16, W=16, T0=64)
@@ -238,7 +238,7 @@ def test_WU_identity_and_nearest_neighbour(name):
         assert np.count_nonzero(u) == g.level_dim(0) // Nl and set(np.unique(u)) == {0.0, 1.0}
 
 
-@pytest.mark.parametrize("name", ["denoise", "bayer", "video", "lightfield", "inpaint"])
+@pytest.mark.parametrize("name", ["denoise", "bayer", "video", "lightfield", "inpaint", "cs_dense"])
 def test_extraction_matches_camera_model(name):
     """Noiseless: the extracted patch equals Phi_p applied to the ground-truth
     patch (y = Phi x, Sec. III-C).  The camera simulation lives in the input
