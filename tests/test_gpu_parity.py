@@ -216,6 +216,37 @@ def test_degenerate_inputs():
         assert rate >= MATCH and worst <= REL_TOL, (K, bad[:10])
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_maximum_sparsity_budget(prec):
+    """K = CSP_MAX_K = 32 on noiseless 32-sparse problems (M = 128, T = 256):
+    the largest factor, the longest chains, ragged patch tile (200)."""
+    from paper_1511_05174_gb300.context import Context
+    A, Y, _ = synthetic.make_independent_problems(200, 128, 256, 32, seed=9, sigma=0.0, unit_norm=True)
+    ctx = Context(0)
+    ctx.set_geometry(8, 8, (1, 2), 8, 8, [(1, 1, 1, 1)])
+    ctx.set_sensing("identity")
+    ctx.load_dictionary(0, A)
+    sup, coef, keff = ctx.solve(torch.from_numpy(Y).cuda(), "plain", prec, K=[32], Kmax=32)
+    o, a, k, _ = oracle.omp_batch([A] * len(Y), Y, 32)
+    rate, worst, bad = compare(A, sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy().astype(int), o, a, k)
+    assert rate >= MATCH and worst <= REL_TOL, bad[:10]
+
+
+def test_empty_batch():
+    """B = 0: nothing to solve, nothing written, no error."""
+    from paper_1511_05174_gb300.context import Context
+    A, _, _ = synthetic.make_independent_problems(1, 64, 128, 4, seed=1)
+    ctx = Context(0)
+    ctx.set_geometry(8, 8, (1, 1), 8, 8, [(1, 1, 1, 1)])
+    ctx.set_sensing("identity")
+    ctx.load_dictionary(0, A)
+    for prec in ("fp32", "bf16"):
+        sup, coef, keff = ctx.solve(torch.zeros((0, 64), device="cuda"), "plain", prec, K=[4], Kmax=4)
+        torch.cuda.synchronize()
+        assert sup.shape == (0, 4) and keff.shape == (0,)
+        assert ctx.stats()["patches"] == 0
+
+
 def test_per_patch_budgets_lightfield():
     """K drawn per patch in [8, 20] (and ceil(K/2), ceil(K/4) at coarser scales)."""
     w = _workload("lightfield")
@@ -236,17 +267,30 @@ def test_deterministic():
         np.testing.assert_array_equal(g1[key], g2[key])
 
 
-def test_full_size_bayer_sampled():
-    """Full 512x512 Bayer workload (64,009 patches) in the benchmark's launch
-    configuration; the oracle solves a seeded sample of 300 patches."""
-    w = synthetic.make_workload("bayer")
+@pytest.mark.parametrize("name,prec,n_sample", [
+    ("bayer", "fp32", 300), ("bayer", "bf16", 300), ("video", "bf16", 120), ("lightfield", "bf16", 60),
+    ("inpaint", "bf16", 300),
+])
+def test_full_size_sampled(name, prec, n_sample):
+    """Full-size workload in the benchmark's launch configuration (the
+    autotuner picks the restricted variant and the full-dictionary form first);
+    the oracle solves a seeded sample of patches, plain and cross-scale."""
+    from paper_1511_05174_gb300.context import Context
+    w = synthetic.make_workload(name)
     rng = np.random.default_rng(0)
-    sample = np.sort(rng.choice(w.n_patches, 300, replace=False))
+    sample = np.sort(rng.choice(w.n_patches, n_sample, replace=False))
     Y = oracle.extract_patches(w)
+    ctx = Context(0)
+    ctx.load_workload(w)
+    Yd = ctx.extract(torch.from_numpy(w.meas).cuda())
+    Kc, K_patch, Kmax = budgets(w, "cross_scale")
+    ctx.autotune(Yd, "cross_scale", prec, K=Kc, K_patch=K_patch, Kmax=Kmax)
     for mode, fn in (("plain", oracle.plain_omp), ("cross_scale", oracle.cross_scale_omp)):
-        g = run_gpu(w, mode)
+        K, K_patch, Kmax = budgets(w, mode)
+        sup, coef, keff = ctx.solve(Yd, mode, prec, K=K, K_patch=K_patch, Kmax=Kmax)
         o, a, k, _ = fn(w, Y=Y, patches=sample)
-        rate, worst, bad = compare(w.dicts[0], g["sup"][sample], g["coef"][sample], g["keff"][sample], o, a, k)
+        rate, worst, bad = compare(w.dicts[0], sup.cpu().numpy()[sample], coef.cpu().numpy()[sample],
+                                   keff.cpu().numpy().astype(np.int64)[sample], o, a, k)
         assert rate >= MATCH and worst <= REL_TOL, (mode, sample[bad[:10]])
 
 
