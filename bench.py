@@ -413,9 +413,11 @@ def main():
     torch.cuda.synchronize()
 
     def timed(mode, sampler=None):
-        ctx.profile_read(reset=True)
-        ctx.profile(True)
+        """Headline timing (CUDA events around each step, solves replayed from
+        the library's CUDA graph), then a second pass with per-kernel profiling
+        (launch-by-launch events, graph replay off) for the breakdown."""
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        step(mode)  # records the graph of this mode's solve
         barrier()
         torch.cuda.synchronize()
         if sampler:
@@ -429,11 +431,18 @@ def main():
         clocks = sampler.stop() if sampler else None
         barrier()
         ms = sum(a.elapsed_time(b) for a, b in ev)
+        st = ctx.stats()
+        ctx.profile_read(reset=True)
+        ctx.profile(True)
+        for i in range(args.steps):
+            flush.zero_()
+            step(mode)
+        torch.cuda.synchronize()
         prof = ctx.profile_read(reset=True)
         ctx.profile(False)
-        st = ctx.stats()
         return max_over_ranks(ms, world, dev), prof, st, clocks
 
+    ctx.set_graph_mode(True)
     cs_ms, cs_prof, cs_stats, clocks = timed("cross_scale", ClockSampler(local))
     cs_img = img.double().cpu().numpy()
     pl_ms, pl_prof, pl_stats, _ = timed("plain")
@@ -520,6 +529,7 @@ def main():
             "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
             "data": "synthetic (seeded; Gaussian unit-norm atoms, K-sparse N(0,1) codes)",
             "config": {**workload_config(w, args), "form": "cross_scale", "precision": args.precision,
+                       "cuda_graph": "solve replayed from a CUDA graph (csp_set_graph_mode)",
                        "restricted_variant": tune["restricted_variant"],
                        "autotune_ms": [round(t, 4) for t in tune["ms"]],
                        "top_level_form": tune.get("top_level_form"),

@@ -352,6 +352,16 @@ csp_status csp_set_top_level_form(csp_ctx *ctx, int form);
  * the per-iteration form. */
 csp_status csp_set_wait_test(csp_ctx *ctx, int on);
 
+/* Graph mode (not part of the method).  on != 0: csp_solve records the launches
+ * of a call in a CUDA graph (after running the call once normally) and replays
+ * the graph for the following calls with the same parameters, buffers and
+ * batch size, as long as the context's set-up, kernel variant and form are
+ * unchanged; any other call is run normally and recorded in place of the old
+ * graph.  Results are identical.  Profiling (csp_profile_enable) turns replay
+ * off.  The caller must keep the buffers of a recorded call alive while graph
+ * mode is on (or turn it off, which frees the graph). */
+csp_status csp_set_graph_mode(csp_ctx *ctx, int on);
+
 /* ---- Instrumentation (not part of the paper's method) ----------------------
  * Every kernel launch of a context is counted per kernel kind.  While
  * profiling is enabled, each launch is also bracketed by CUDA events on its

@@ -169,6 +169,10 @@ class Context:
         return {"restricted_variant": r.restricted_variant, "ms": list(r.ms), "top_level_form": r.top_level_form,
                 "ms_top": list(r.ms_top)}
 
+    def set_graph_mode(self, on: bool = True) -> None:
+        """Replay identical solves from a CUDA graph (see csp_set_graph_mode)."""
+        b.csp_set_graph_mode(self._ctx, on)
+
     def set_wait_test(self, on: bool) -> None:
         """Failure-detection test hook (see csp_set_wait_test)."""
         b.csp_set_wait_test(self._ctx, on)

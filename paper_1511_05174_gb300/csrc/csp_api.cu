@@ -577,6 +577,8 @@ void csp_destroy(csp_ctx *ctx) {
   for (auto &a : ctx->allocs) cudaFree(a.first);
   for (auto &r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   delete ctx;
 }
 
@@ -648,6 +650,7 @@ csp_status csp_set_geometry(csp_ctx *ctx, const csp_geometry *geom) {
   ctx->B = nx * ny;
   ctx->has_geom = true;
   ctx->prepared = false;
+  ++ctx->state_version;
   free_own_patches(ctx);
   return CSP_OK;
 }
@@ -732,6 +735,7 @@ csp_status csp_set_sensing(csp_ctx *ctx, const csp_sensing *sensing) {
   ctx->M = M;
   ctx->has_sensing = true;
   ctx->prepared = false;
+  ++ctx->state_version;
   free_own_patches(ctx);
   return CSP_OK;
 }
@@ -757,6 +761,7 @@ csp_status csp_load_dictionary(csp_ctx *ctx, int level, const float *D, int N_l,
   L.N = N_l;
   L.T = T_l;
   ctx->prepared = false;
+  ++ctx->state_version;
   free_own_patches(ctx);
   return CSP_OK;
 }
@@ -792,6 +797,7 @@ csp_status csp_load_scale_links(csp_ctx *ctx, int level, const int32_t *parent, 
   CSP_CUDA(ctx, cudaMemcpy(F.child_idx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice));
   F.max_children = mx;
   F.links = true;
+  ++ctx->state_version;
   return CSP_OK;
 }
 
@@ -856,7 +862,67 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
   for (int l = 0; l < CSP_MAX_LEVELS; ++l) { ps.A_pp[l] = ctx->pp_A[l]; ps.inv_pp[l] = ctx->pp_inv[l]; }
   ctx->last_B = B;
   ctx->last_stream = s;
-  return solve_core(ctx, ps, ctx->wsp, prm, Y, support_out, coef_out, k_eff_out, s);
+  if (!ctx->graph_mode || ctx->prof)
+    return solve_core(ctx, ps, ctx->wsp, prm, Y, support_out, coef_out, k_eff_out, s);
+  // graph mode: replay the captured launches of an identical call
+  csp_ctx::GraphKey key;
+  std::memset(&key, 0, sizeof(key));  // padding included: compared byte by byte
+  key.prm.mode = prm->mode;
+  key.prm.precision = prm->precision;
+  for (int l = 0; l < CSP_MAX_LEVELS; ++l) {
+    key.prm.K[l] = prm->K[l];
+    key.prm.K_patch[l] = prm->K_patch[l];
+  }
+  key.prm.Kmax = prm->Kmax;
+  key.Y = Y;
+  key.B = B;
+  key.sup = support_out;
+  key.coef = coef_out;
+  key.keff = k_eff_out;
+  key.version = ctx->state_version;
+  key.restricted_variant = ctx->restricted_variant;
+  key.top_form = ctx->top_form;
+  key.wait_test = ctx->wait_test;
+  if (ctx->gexec && std::memcmp(&key, &ctx->gkey, sizeof(key)) == 0) {
+    CSP_CUDA(ctx, cudaGraphLaunch(ctx->gexec, s));
+    return CSP_OK;
+  }
+  // a new call: run it (this allocates whatever it needs and gives the result),
+  // then capture the same launches on a private stream for the next calls
+  if (ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  CSP_TRY(solve_core(ctx, ps, ctx->wsp, prm, Y, support_out, coef_out, k_eff_out, s));
+  if (!ctx->gstream) CSP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+  CSP_CUDA(ctx, cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed));
+  const csp_status st = solve_core(ctx, ps, ctx->wsp, prm, Y, support_out, coef_out, k_eff_out, ctx->gstream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(ctx->gstream, &graph);
+  if (st != CSP_OK || ec != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return st != CSP_OK ? st : fail(ctx, CSP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    ctx->gexec = nullptr;
+    cudaGetLastError();
+    return fail(ctx, CSP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+  }
+  std::memcpy(&ctx->gkey, &key, sizeof(key));
+  return CSP_OK;
+}
+
+csp_status csp_set_graph_mode(csp_ctx *ctx, int on) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  ctx->graph_mode = on != 0;
+  if (!ctx->graph_mode && ctx->gexec) {
+    cudaGraphExecDestroy(ctx->gexec);
+    ctx->gexec = nullptr;
+  }
+  return CSP_OK;
 }
 
 csp_status csp_solve_stats_get(csp_ctx *ctx, csp_solve_stats *out) {

@@ -136,6 +136,22 @@ struct csp_ctx {
   int aggregate_path = 0;      // 0 automatic, 1 two-pass (synthesis scratch), 2 fused shared-memory tiles
   int top_form = 0;            // full-dictionary level: 0 automatic, 1 per-iteration kernels, 2 fused kernel
   bool wait_test = false;      // test hook: the tensor-core proxy loads no atom tiles (its waits expire)
+  // CUDA graph of the last solve (csp_set_graph_mode): replayed while the call
+  // and the context's buffers are unchanged (state_version counts the changes)
+  bool graph_mode = false;
+  uint64_t state_version = 0;
+  struct GraphKey {
+    csp_solve_params prm;
+    const float *Y;
+    int64_t B;
+    int32_t *sup;
+    float *coef;
+    int8_t *keff;
+    uint64_t version;
+    int restricted_variant, top_form, wait_test;
+  } gkey{};
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t gstream = nullptr;
   std::vector<csp::ProfRec> pending;
   std::vector<cudaEvent_t> ev_pool;
   // All device allocations (for the memory budget and destroy).

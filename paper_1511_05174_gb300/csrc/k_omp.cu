@@ -720,11 +720,8 @@ void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_n
                        unsigned long long *keys, cudaStream_t s) {
   if (n == 0) return;
   const size_t sm = proxy_fp32_smem(ldo);
-  static size_t configured = 0;
-  if (sm > 48 * 1024 && sm > configured) {
-    cudaFuncSetAttribute(proxy_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    configured = sm;
-  }
+  // the attribute is per device and function: set it on every launch (a host-side call)
+  if (sm > 48 * 1024) cudaFuncSetAttribute(proxy_fp32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const int n_all = (T + PF_TA - 1) / PF_TA;
   const int S = keys ? proxy_fp32_splits(n, T) : 1;
   const int tps = (n_all + S - 1) / S;

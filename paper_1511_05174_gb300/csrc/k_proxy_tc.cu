@@ -354,12 +354,10 @@ bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, con
   const TcLayout lay = tc_layout(Mp, nt);
   // at least 80 KB per CTA keeps two CTAs (2 x 2 NT <= 512 TMEM columns) per SM at most
   const int sm = lay.total < 80 * 1024 ? 80 * 1024 : lay.total;
-  static int configured = 0;
-  if (sm > configured) {
-    if (cudaFuncSetAttribute(proxy_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
-      return false;
-    configured = sm;
-  }
+  // the attribute is per device and function: set it on every launch (a host-side call)
+  if (cudaFuncSetAttribute(proxy_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
+    return false;
+
   int idx_bits = 1;
   while ((1 << idx_bits) < T) ++idx_bits;  // atom index field of the packed keys
   const int n_all = (T + nt - 1) / nt;

@@ -417,6 +417,47 @@ def test_expired_device_wait_is_reported_and_context_recovers():
     assert rate >= MATCH and worst <= REL_TOL
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_graph_mode_replays_identical_results(prec):
+    """Graph mode: the first solve runs and records, the next identical calls
+    replay the CUDA graph; new measurement values in the same buffer, another
+    kernel variant or another batch are handled; results equal graph-off ones."""
+    from paper_1511_05174_gb300.context import Context
+    w = _workload("bayer")
+    w2 = synthetic.make_workload("bayer", H=64, W=64, seed=7, dict_seed=0)
+    ref = Context(0)
+    ref.load_workload(w)
+    ctx = Context(0)
+    ctx.load_workload(w)
+    ctx.set_graph_mode(True)
+    K, K_patch, Kmax = budgets(w, "cross_scale")
+    Y = ctx.extract(torch.from_numpy(w.meas).cuda())
+    Yr = ref.extract(torch.from_numpy(w.meas).cuda())
+    outs = (torch.empty((w.n_patches, Kmax), dtype=torch.int32, device="cuda"),
+            torch.empty((w.n_patches, Kmax), dtype=torch.float32, device="cuda"),
+            torch.empty((w.n_patches,), dtype=torch.int8, device="cuda"))
+
+    def same(meas, variant):
+        ctx.set_kernel_variant(variant)
+        ref.set_kernel_variant(variant)
+        ctx.extract(torch.from_numpy(meas).cuda(), Y)
+        ref.extract(torch.from_numpy(meas).cuda(), Yr)
+        for _ in range(3):  # record, then replay twice
+            for t in outs:
+                t.fill_(0)
+            ctx.solve(Y, "cross_scale", prec, K=K, K_patch=K_patch, Kmax=Kmax, out=outs)
+            r = ref.solve(Yr, "cross_scale", prec, K=K, K_patch=K_patch, Kmax=Kmax)
+            torch.cuda.synchronize()
+            assert all(torch.equal(a, b) for a, b in zip(outs, r))
+        assert ctx.stats()["patches"] == w.n_patches
+
+    same(w.meas, 2)
+    same(w2.meas, 2)  # same buffers, new contents: replayed
+    same(w2.meas, 6)  # another variant: recorded again
+    ctx.set_graph_mode(False)
+    same(w.meas, 0)
+
+
 def test_autotune_picks_a_variant():
     from paper_1511_05174_gb300.context import Context
     w = _workload("bayer")
