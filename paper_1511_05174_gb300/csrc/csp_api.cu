@@ -368,14 +368,19 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
     const LevelData &L = ctx->lv[top];
     const bool want = ctx->top_form == 2;  // 0: per-iteration kernels unless csp_autotune chose the fused form
     if (want && bf16 && !L.per_patch && L.Mp == 64 && fused_top_supported(L.M, L.T, Kb[top])) {
-      fused_done = true;
-      for (int ph = 0; ph < nph && fused_done; ++ph)
-        run(ctx, KK_FUSED, s, n_of(ph), [&] {
-          fused_done &= launch_omp_fused_tc(Yl[top], L.M, L.A[ph], L.inv_norm[ph], L.Abf[ph], L.Mp, L.T, ids_of(ph),
-                                            n_of(ph), prm->K_patch[top], prm->K[top], Kb[top], lv_om[top],
-                                            lv_al[top], ldo[top], lv_ke[top], W.stats_dev,
-                                            (unsigned long long *)(W.stats_dev + 4), s);
-        });
+      const float *Aph[kMaxPhases] = {}, *Iph[kMaxPhases] = {};
+      const __nv_bfloat16 *Bph[kMaxPhases] = {};
+      for (int ph = 0; ph < nph; ++ph) {
+        Aph[ph] = L.A[ph];
+        Iph[ph] = L.inv_norm[ph];
+        Bph[ph] = L.Abf[ph];
+      }
+      run(ctx, KK_FUSED, s, B, [&] {
+        fused_done = launch_omp_fused_tc(Yl[top], L.M, Aph, Iph, Bph, nph, phased ? ps.phase_start : nullptr, L.Mp,
+                                         L.T, phased ? ps.phase_ids : nullptr, B, prm->K_patch[top], prm->K[top],
+                                         Kb[top], lv_om[top], lv_al[top], ldo[top], lv_ke[top], W.stats_dev,
+                                         (unsigned long long *)(W.stats_dev + 4), s);
+      });
       if (!fused_done) return fail(ctx, CSP_ERR_CUDA, "fused full-dictionary kernel could not be launched");
     }
   }

@@ -241,12 +241,16 @@ bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, con
 // Fused full-dictionary OMP (k_fused.cu): all Kb iterations of a shared
 // dictionary with T <= 256 (multiple of 64) atoms, M <= 64, Kb <= 8, BF16
 // tensor-core proxy with FP32 re-score; writes omega/alpha/k_eff directly.
-// Returns false when the shape is not supported or a tensor map fails.
+// One launch covers the nph phase groups (host phase_start[nph + 1] gives the
+// positions of each group in `ids`; null: one group of n patches, ids may be
+// null); A / inv_norm / Abf hold one pointer per phase.  Returns false when the
+// shape is not supported or a tensor map fails.
 bool fused_top_supported(int M, int T, int Kb);
-bool launch_omp_fused_tc(const float *Y, int M, const float *A, const float *inv_norm, const __nv_bfloat16 *Abf,
-                         int Mp, int T, const int32_t *ids, int64_t n, const int8_t *Kp, int Kuni, int Kb,
-                         int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
-                         unsigned long long *err, cudaStream_t s);
+bool launch_omp_fused_tc(const float *Y, int M, const float *const *A, const float *const *inv_norm,
+                         const __nv_bfloat16 *const *Abf, int nph, const int64_t *phase_start, int Mp, int T,
+                         const int32_t *ids, int64_t n, const int8_t *Kp, int Kuni, int Kb, int32_t *omega,
+                         float *alpha, int ldo, int8_t *k_eff, int64_t *stats, unsigned long long *err,
+                         cudaStream_t s);
 // Load-wave variants (k_grp.cu): one update iteration; restricted OMP with the Gram-matrix proxy.
 // a_pstride / inv_pstride: per-patch strides of A and inv_norm (0: shared by all patches).
 void launch_omp_update_wave(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,

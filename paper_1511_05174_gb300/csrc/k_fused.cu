@@ -1,5 +1,5 @@
 // Fused full-dictionary OMP for a small shared dictionary: every iteration of
-// Algorithm 1 (proxy, merge, projection, residue) for a tile of 128 patches in
+// Algorithm 1 (proxy, merge, projection, residue) for tiles of 128 patches in
 // one CTA, with the residuals and the per-patch state kept on chip.  This is
 // the coarse step of Algorithm 2 on shared-Phi workloads (T <= 256 atoms,
 // M <= 64 measurements, K <= 8), where the separate per-iteration launches
@@ -18,14 +18,27 @@
 //           falls below kTauPivot, which also rejects dependent atoms), solve for
 //           alpha, form r = y - A_Omega alpha, and write r back as the next
 //           BF16 tile (128-byte swizzle, the layout the MMA reads).
-// The FP32 rows of A (zero padded to 64) stay in shared memory, so the
-// re-score, the Gram column and the residue read no global memory.
+// The FP32 rows of A (zero padded to 64, rows 68 words apart so that the rows
+// of different patches fall on different banks) stay in shared memory, so the
+// re-score, the Gram column and the residue read no global memory.  The two
+// threads of a patch own interleaved float4 chunks (2t and 2t + 1) of every
+// 64-vector.
 //
-// Roles: warp 0 loads the BF16 atoms by TMA, warp 1 owns the tensor memory and
-// issues the MMAs, warps 2-9 run the epilogue (TMEM lane quadrant = warp % 4,
-// half of the columns each) and then the update (thread pair per patch).
-// Every mbarrier wait is bounded; on expiry the error word is set, all threads
-// leave the iteration loop together, and the tensor memory is freed.
+// A CTA runs NGRP groups of 256 threads, each with its own tile of 128 patches,
+// its own half of the tensor memory and its own barriers, over one copy of
+// the atoms: while one group is in its scalar update the tensor cores and the
+// other group's epilogue proceed.  One launch covers every mosaic phase (each
+// CTA's tiles belong to one phase, whose atoms it loads).
+//
+// Roles: thread 0 loads the BF16 atoms by TMA; warp 0 owns the tensor memory;
+// in each group, thread 0 issues the group's MMAs once the group barrier shows
+// its residual tile complete, warps 8g .. 8g+7 run the epilogue (TMEM lane
+// quadrant = warp % 4, half of the columns each) and then the update (thread
+// pair per patch).  Every mbarrier wait is bounded; on expiry the error word is
+// set, the group's threads leave the iteration loop together, and the tensor
+// memory is freed.
+#include <cstring>
+
 #include "csp_internal.cuh"
 #include "grp_common.cuh"
 #include "tc_common.cuh"
@@ -39,57 +52,75 @@ using csp::grp::GrpSmem;
 using csp::grp::key_idx;
 using csp::grp::pack_key;
 
-constexpr int FZ_M = 128;        // patches per CTA (MMA M)
+constexpr int FZ_M = 128;        // patches per group tile (MMA M)
 constexpr int FZ_MP = 64;        // padded measurement dimension (one 128-byte K block)
+constexpr int FZ_AS = 68;        // words between FP32 atom rows in shared memory
 constexpr int FZ_KMAX = 8;       // largest K of the fused form
-constexpr int FZ_THREADS = 320;  // warps 0-1 + eight epilogue/update warps
-constexpr int FZ_HALF = FZ_MP / 2;  // elements per thread of a pair
-constexpr int FZ_NCH = FZ_HALF / 4;  // float4 per thread of a pair
+constexpr int FZ_GT = 256;       // threads of a group: a pair per patch
+constexpr int FZ_NCH = 8;        // float4 chunks per thread of a pair
+constexpr int FZ_MAXPH = kMaxPhases;
 
 __host__ __device__ constexpr int ftri(int i) { return i * (i + 1) / 2; }
 
+// Shared memory: the atoms (shared by the groups), then one block per group.
 struct FzLayout {
-  int a_bf;    // BF16 atoms [T][64], 128-byte swizzle (offset 0, 1024-aligned)
-  int r_bf;    // BF16 residual tile [128][64]
-  int a_fp;    // FP32 atoms [T][64]
-  int inv;     // [T] 1/||a_i||
-  int L, Linv, z, V, W;  // per patch, FP32
-  int om, colp, cand;    // per patch
+  int a_bf;   // BF16 atoms [T][64], 128-byte swizzle (offset 0, 1024-aligned)
+  int a_fp;   // FP32 atoms [T][FZ_AS]
+  int inv;    // [T] 1/||a_i||
+  int grp, gstride;                 // first group block, bytes per block (1024-aligned)
+  int r_bf, cand, L, Linv, z, om, V, W;  // offsets within a group block
+  int ls, ks, vs;                   // per-patch strides (words, odd): L, Linv/z/om, V/W
   int bars;
   int total;
 };
 
-__host__ __device__ inline FzLayout fz_layout(int T) {
+__host__ __device__ inline FzLayout fz_layout(int T, int Kb, int ngrp) {
   FzLayout L;
+  L.ls = ftri(Kb) | 1;
+  L.ks = Kb | 1;
+  L.vs = (Kb + 1) | 1;
   int o = 0;
   L.a_bf = o; o += T * FZ_MP * 2;
-  L.r_bf = o; o += FZ_M * FZ_MP * 2;
-  L.a_fp = o; o += T * FZ_MP * 4;
+  L.a_fp = o; o += T * FZ_AS * 4;
   L.inv = o; o += T * 4;
-  L.L = o; o += FZ_M * ftri(FZ_KMAX) * 4;
-  L.Linv = o; o += FZ_M * FZ_KMAX * 4;
-  L.z = o; o += FZ_M * FZ_KMAX * 4;
-  L.V = o; o += FZ_M * (FZ_KMAX + 1) * 4;
-  L.W = o; o += FZ_M * (FZ_KMAX + 1) * 4;
-  L.om = o; o += FZ_M * FZ_KMAX * 4;
-  o = (o + 15) & ~15;
-  L.colp = o; o += FZ_M * (FZ_KMAX + 1) * 8;
-  L.cand = o; o += FZ_M * 4 * 4;
-  L.bars = o; o += 64;
+  o = (o + 1023) & ~1023;
+  L.grp = o;
+  int g = 0;
+  L.r_bf = g; g += FZ_M * FZ_MP * 2;  // BF16 residual tile [128][64], 128-byte swizzle
+  L.cand = g; g += FZ_M * 16;         // [128] top-4 keys
+  L.L = g; g += FZ_M * L.ls * 4;
+  L.Linv = g; g += FZ_M * L.ks * 4;
+  L.z = g; g += FZ_M * L.ks * 4;
+  L.om = g; g += FZ_M * L.ks * 4;
+  L.V = g; g += FZ_M * L.vs * 4;
+  L.W = g; g += FZ_M * L.vs * 4;
+  L.gstride = (g + 1023) & ~1023;
+  o += ngrp * L.gstride;
+  L.bars = o; o += 128;
   L.total = o + 1024;  // alignment slack
   return L;
 }
 
+// Per-phase operands of one launch.
+struct FzArgs {
+  CUtensorMap map[FZ_MAXPH];            // BF16 atoms of each phase
+  const float *A[FZ_MAXPH];             // FP32 effective dictionary [T][M]
+  const float *inv[FZ_MAXPH];           // [T] 1/||a_i||
+  int64_t row0[FZ_MAXPH + 1];           // first position of each phase in the patch list
+  int cta0[FZ_MAXPH + 1];               // first CTA of each phase
+  int nph;
+};
+
 __device__ __forceinline__ float pair_sum(float v) { return v + __shfl_xor_sync(0xffffffffu, v, 1); }
 
-// Partial dot of this thread's half of a 64-wide row (shared or global memory)
-// with its register chunks.
+// Partial dot of this thread's chunks (2t + h) of a 64-wide shared row with its
+// register chunks; four independent chains, summed in a fixed order.
 __device__ __forceinline__ float half_dot(const float *row, int h, const float4 (&v)[FZ_NCH]) {
-  const float4 *r4 = reinterpret_cast<const float4 *>(row + h * FZ_HALF);
-  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;  // four independent chains
+  const float4 *r4 = reinterpret_cast<const float4 *>(row);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll
   for (int t = 0; t < FZ_NCH; ++t) {
-    const float4 a = r4[t];
+    const float4 a = r4[2 * t + h];
     s0 = fmaf(a.x, v[t].x, s0);
     s1 = fmaf(a.y, v[t].y, s1);
     s2 = fmaf(a.z, v[t].z, s2);
@@ -98,133 +129,146 @@ __device__ __forceinline__ float half_dot(const float *row, int h, const float4 
   return (s0 + s1) + (s2 + s3);
 }
 
-// BF16 copy of this thread's half of the residual into row `row` of the
-// 128-byte-swizzled tile (16-byte chunk c of a row sits at chunk c ^ (row % 8)).
+// Same for two shared rows.
+__device__ __forceinline__ float half_dot2(const float *ra, const float *rb, int h) {
+  const float4 *a4 = reinterpret_cast<const float4 *>(ra);
+  const float4 *b4 = reinterpret_cast<const float4 *>(rb);
+  float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll
+  for (int t = 0; t < FZ_NCH; ++t) {
+    const float4 a = a4[2 * t + h], b = b4[2 * t + h];
+    s0 = fmaf(a.x, b.x, s0);
+    s1 = fmaf(a.y, b.y, s1);
+    s2 = fmaf(a.z, b.z, s2);
+    s3 = fmaf(a.w, b.w, s3);
+  }
+  return (s0 + s1) + (s2 + s3);
+}
+
+// BF16 copy of this thread's chunks into row `row` of the 128-byte-swizzled
+// tile: 16-byte chunk j of a row (elements 8j .. 8j+7: float4 chunks 2j of
+// thread 0 and 2j+1 of thread 1) sits at chunk j ^ (row % 8).
 __device__ __forceinline__ void store_rbf(uint8_t *tile, int row, int h, const float4 (&r)[FZ_NCH]) {
 #pragma unroll
-  for (int q = 0; q < FZ_NCH / 2; ++q) {  // 8 elements per 16-byte chunk
-    const int c = h * (FZ_NCH / 2) + q;
-    const float4 a = r[2 * q], b = r[2 * q + 1];
-    __nv_bfloat162 w0 = __floats2bfloat162_rn(a.x, a.y), w1 = __floats2bfloat162_rn(a.z, a.w);
-    __nv_bfloat162 w2 = __floats2bfloat162_rn(b.x, b.y), w3 = __floats2bfloat162_rn(b.z, b.w);
-    uint4 u;
-    u.x = *reinterpret_cast<uint32_t *>(&w0);
-    u.y = *reinterpret_cast<uint32_t *>(&w1);
-    u.z = *reinterpret_cast<uint32_t *>(&w2);
-    u.w = *reinterpret_cast<uint32_t *>(&w3);
-    *reinterpret_cast<uint4 *>(tile + row * 128 + ((c ^ (row & 7)) << 4)) = u;
+  for (int j = 0; j < FZ_NCH; ++j) {
+    __nv_bfloat162 w0 = __floats2bfloat162_rn(r[j].x, r[j].y), w1 = __floats2bfloat162_rn(r[j].z, r[j].w);
+    uint2 v;
+    v.x = *reinterpret_cast<uint32_t *>(&w0);
+    v.y = *reinterpret_cast<uint32_t *>(&w1);
+    *reinterpret_cast<uint2 *>(tile + row * 128 + ((j ^ (row & 7)) << 4) + 8 * h) = v;
   }
 }
 
-__global__ void __launch_bounds__(FZ_THREADS, 1)
-omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__restrict__ Y, int M,
-                    const float *__restrict__ A, const float *__restrict__ inv_norm, int T, int idx_bits,
-                    const int32_t *__restrict__ ids, int64_t n, const int8_t *__restrict__ Kp, int Kuni, int Kb,
+__device__ __forceinline__ void group_bar(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(FZ_GT) : "memory");
+}
+
+template <int NGRP>
+__global__ void __launch_bounds__(NGRP * FZ_GT, 1)
+omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict__ Y, int M, int T, int idx_bits,
+                    const int32_t *__restrict__ ids, const int8_t *__restrict__ Kp, int Kuni, int Kb,
                     int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo, int8_t *__restrict__ k_eff,
                     int64_t *stats, unsigned long long *err) {
   extern __shared__ uint8_t fz_raw[];
   uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(fz_raw) + 1023) & ~uintptr_t(1023));
-  const FzLayout lay = fz_layout(T);
+  const FzLayout lay = fz_layout(T, Kb, NGRP);
   uint8_t *a_bf = sm + lay.a_bf;
-  uint8_t *r_bf = sm + lay.r_bf;
   float *a_fp = reinterpret_cast<float *>(sm + lay.a_fp);
   float *s_inv = reinterpret_cast<float *>(sm + lay.inv);
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + lay.bars);
-  uint64_t *afull = bars, *rready = bars + 1, *accfull = bars + 2;
-  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 4);
-  int *s_flag = reinterpret_cast<int *>(bars + 5);
-  uint32_t *cand = reinterpret_cast<uint32_t *>(sm + lay.cand);  // [128][4] keys (half 1 merges in)
+  uint64_t *afull = bars, *accfull = bars + 1;  // accfull[NGRP]
+  uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 1 + NGRP);
+  int *s_flag = reinterpret_cast<int *>(bars + 2 + NGRP);  // [NGRP]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t tile0 = (int64_t)blockIdx.x * FZ_M;
+  // this CTA's phase and tiles
+  int ph = 0;
+  while (ph + 1 < args.nph && (int)blockIdx.x >= args.cta0[ph + 1]) ++ph;
+  const float *A = args.A[ph];
+  const float *inv_norm = args.inv[ph];
+  const int64_t prow0 = args.row0[ph], pn = args.row0[ph + 1] - prow0;
+  const int64_t tile_first = (int64_t)(blockIdx.x - args.cta0[ph]) * NGRP;
+  const int64_t ntiles = (pn + FZ_M - 1) / FZ_M;
+  const int nact = (int)(ntiles - tile_first < NGRP ? ntiles - tile_first : NGRP);  // groups with a tile
   uint32_t ncols = 32;
   while ((int)ncols < T) ncols <<= 1;
 
   if (threadIdx.x == 0) {
     mbar_init(afull, 1);
-    mbar_init(rready, 1);
-    mbar_init(accfull, 1);
-    *s_flag = 0;
+    for (int g = 0; g < NGRP; ++g) {
+      mbar_init(accfull + g, 1);
+      s_flag[g] = 0;
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
+  if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_holder)),
-                 "r"(ncols)
+                 "r"(ncols * NGRP)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // FP32 atoms (zero padded to 64) and inverse norms, cooperatively
-  for (int e = threadIdx.x; e < T * FZ_MP; e += blockDim.x) {
-    const int i = e / FZ_MP, m = e - i * FZ_MP;
-    a_fp[e] = m < M ? __ldg(A + (int64_t)i * M + m) : 0.f;
+  // FP32 atoms (zero padded to 64) and inverse norms, cooperatively, four
+  // 16-byte loads in flight per thread
+  {
+    const int nv = M >> 2, total4 = T * (FZ_MP / 4), nt = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < total4; e0 += 4 * nt) {
+      float4 v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + q * nt, i = e >> 4, c = e & 15;
+        v[q] = (e < total4 && c < nv) ? __ldg(reinterpret_cast<const float4 *>(A + (int64_t)i * M) + c)
+                                      : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + q * nt;
+        if (e < total4) reinterpret_cast<float4 *>(a_fp + (e >> 4) * FZ_AS)[e & 15] = v[q];
+      }
+    }
+    for (int i = threadIdx.x; i < T; i += nt) s_inv[i] = __ldg(inv_norm + i);
   }
-  for (int i = threadIdx.x; i < T; i += blockDim.x) s_inv[i] = __ldg(inv_norm + i);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_holder;
 
-  if (warp == 0) {
-    if (lane == 0) {
-      mbar_expect_tx(afull, (uint32_t)(T * 128));
-      tma_load_2d(a_bf, &tmA, 0, 0, afull);
-      mbar_wait(afull, 0, err, 11);  // drain before exit
-    }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t idesc = instr_desc(FZ_M, T);
-      bool ok = mbar_wait(afull, 0, err, 12);
-      for (int it = 0; it < Kb && ok; ++it) {
-        ok = mbar_wait(rready, (uint32_t)(it & 1), err, 13);
-        if (!ok) break;
-        tc_fence_after();
-#pragma unroll
-        for (int kin = 0; kin < 4; ++kin) {
-          const uint64_t ad = smem_desc(smem_u32(r_bf) + kin * 32);
-          const uint64_t bd = smem_desc(smem_u32(a_bf) + kin * 32);
-          mma_bf16(tmem, ad, bd, idesc, kin ? 1u : 0u);
-        }
-        mma_commit(accfull);
-      }
-    }
-  } else {
-    // ---- epilogue / update threads (256) ----
-    const int u = threadIdx.x - 64;
-    const int p = u >> 1, h = u & 1;  // update: patch p, half h
-    const int quad = warp & 3, ehalf = (warp - 2) >> 2, erow = quad * 32 + lane;  // epilogue row
-    const int64_t wi = tile0 + p;
-    const bool valid = wi < n;
-    const int64_t b = valid ? (ids ? (int64_t)ids[wi] : wi) : 0;
+  if (threadIdx.x == 0) {
+    mbar_expect_tx(afull, (uint32_t)(T * 128));
+    tma_load_2d(a_bf, &args.map[ph], 0, 0, afull);
+  }
+  if (warp / 8 < nact) {
+    // ---- a group: epilogue and update of one tile ----
+    const int g = warp / 8;
+    uint8_t *gb = sm + lay.grp + g * lay.gstride;
+    uint8_t *r_bf = gb + lay.r_bf;
+    uint4 *cand4 = reinterpret_cast<uint4 *>(gb + lay.cand);
+    uint64_t *af = accfull + g;
+    volatile int *flag = s_flag + g;
+    const uint32_t tm = tmem + (uint32_t)g * ncols;
+    const int bar_id = 1 + g;
+    const int u = threadIdx.x - g * FZ_GT;
+    const int p = u >> 1, h = u & 1;  // update: patch p, chunks 2t + h
+    const int quad = warp & 3, ehalf = (warp & 7) >> 2, erow = quad * 32 + lane;  // epilogue row
+    const int64_t wl = (tile_first + g) * FZ_M + p;  // position within the phase
+    const bool valid = wl < pn;
+    const int64_t b = valid ? (ids ? (int64_t)ids[prow0 + wl] : prow0 + wl) : 0;
     int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
     Kpb = Kpb < Kb ? Kpb : Kb;
-    float *Lp = reinterpret_cast<float *>(sm + lay.L) + p * ftri(FZ_KMAX);
-    float *Linv = reinterpret_cast<float *>(sm + lay.Linv) + p * FZ_KMAX;
-    float *zp = reinterpret_cast<float *>(sm + lay.z) + p * FZ_KMAX;
-    float *Vp = reinterpret_cast<float *>(sm + lay.V) + p * (FZ_KMAX + 1);
-    float *Wp = reinterpret_cast<float *>(sm + lay.W) + p * (FZ_KMAX + 1);
-    int *omp = reinterpret_cast<int *>(sm + lay.om) + p * FZ_KMAX;
-    const float **colp = reinterpret_cast<const float **>(sm + lay.colp) + p * (FZ_KMAX + 1);
-    GrpSmem S{};  // view for the FP64 rebuild
-    S.L = Lp;
-    S.Linv = Linv;
-    S.z = zp;
-    S.V = Vp;
-    S.W = Wp;
-    S.om = omp;
-    S.colp = colp;
+    float *Lp = reinterpret_cast<float *>(gb + lay.L) + p * lay.ls;
+    float *Linv = reinterpret_cast<float *>(gb + lay.Linv) + p * lay.ks;
+    float *zp = reinterpret_cast<float *>(gb + lay.z) + p * lay.ks;
+    int *omp = reinterpret_cast<int *>(gb + lay.om) + p * lay.ks;
+    float *Vp = reinterpret_cast<float *>(gb + lay.V) + p * lay.vs;
+    float *Wp = reinterpret_cast<float *>(gb + lay.W) + p * lay.vs;
+    auto arow = [&](int i) -> const float * { return a_fp + i * FZ_AS; };
     int fb_misc = 0;
-    // y and r: this thread's half, zero padded
+    // y and r: this thread's chunks, zero padded
     const float *yrow = Y + b * M;
     float4 yv[FZ_NCH], rv[FZ_NCH];
 #pragma unroll
     for (int t = 0; t < FZ_NCH; ++t) {
-      float e4[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int m = h * FZ_HALF + 4 * t + c;
-        e4[c] = (valid && m < M) ? __ldg(yrow + m) : 0.f;
-      }
-      yv[t] = make_float4(e4[0], e4[1], e4[2], e4[3]);
+      const int m0 = 4 * (2 * t + h);
+      yv[t] = (valid && m0 < M) ? __ldg(reinterpret_cast<const float4 *>(yrow + m0)) : make_float4(0.f, 0.f, 0.f, 0.f);
       rv[t] = yv[t];
     }
     float ysq = 0.f;
@@ -241,20 +285,30 @@ omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__rest
     const uint32_t smask = 0x7fffffffu & ~imask;
     const int hcols = T / 2;
     for (int it = 0; it < Kb; ++it) {
-      // the residual tile is complete: hand it to the MMA
+      // the residual tile is complete: C = R A^T into this group's columns
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (u == 0) mbar_arrive(rready);
+      group_bar(bar_id);
+      if (u == 0 && (it > 0 || mbar_wait(afull, 0, err, 12))) {
+        tc_fence_after();
+        const uint32_t idesc = instr_desc(FZ_M, T);
+#pragma unroll
+        for (int kin = 0; kin < 4; ++kin) {
+          const uint64_t ad = smem_desc(smem_u32(r_bf) + kin * 32);
+          const uint64_t bd = smem_desc(smem_u32(a_bf) + kin * 32);
+          mma_bf16(tm, ad, bd, idesc, kin ? 1u : 0u);
+        }
+        mma_commit(af);
+      }
       // ---- epilogue: top 4 keys of this row's half of the columns ----
-      bool ok = mbar_wait(accfull, (uint32_t)(it & 1), err, 14);
-      if (!ok) *s_flag = 1;
-      asm volatile("bar.sync 1, 256;" ::: "memory");
-      if (*s_flag) break;
+      const bool okw = mbar_wait(af, (uint32_t)(it & 1), err, 14);
+      if (!okw) *flag = 1;
+      group_bar(bar_id);
+      if (*flag) break;
       tc_fence_after();
       uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;  // two independent chains
       for (int c0 = 0; c0 < hcols; c0 += 32) {
         uint32_t v[32];
-        tmem_ld32_nowait(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ehalf * hcols + c0), v);
+        tmem_ld32_nowait(tm + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ehalf * hcols + c0), v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int base = ehalf * hcols + c0;  // T is a multiple of 64: every column is an atom
         const uint32_t cb = imask - (uint32_t)base;
@@ -269,33 +323,28 @@ omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__rest
       top4_insert(b2, a0, a1, a2, a3);
       top4_insert(b3, a0, a1, a2, a3);
       tc_fence_before();
-      if (ehalf == 1) {
-        cand[erow * 4 + 0] = a0;
-        cand[erow * 4 + 1] = a1;
-        cand[erow * 4 + 2] = a2;
-        cand[erow * 4 + 3] = a3;
-      }
-      asm volatile("bar.sync 1, 256;" ::: "memory");
+      if (ehalf == 1) cand4[erow] = make_uint4(a0, a1, a2, a3);
+      group_bar(bar_id);
       if (ehalf == 0) {
-        for (int q = 0; q < 4; ++q) top4_insert(cand[erow * 4 + q], a0, a1, a2, a3);
-        cand[erow * 4 + 0] = a0;
-        cand[erow * 4 + 1] = a1;
-        cand[erow * 4 + 2] = a2;
-        cand[erow * 4 + 3] = a3;
+        const uint4 o = cand4[erow];
+        top4_insert(o.x, a0, a1, a2, a3);
+        top4_insert(o.y, a0, a1, a2, a3);
+        top4_insert(o.z, a0, a1, a2, a3);
+        top4_insert(o.w, a0, a1, a2, a3);
+        cand4[erow] = make_uint4(a0, a1, a2, a3);
       }
-      asm volatile("bar.sync 1, 256;" ::: "memory");
+      group_bar(bar_id);
       // ---- update: a thread pair per patch ----
       act = act && k < Kpb && !(rsq <= kEpsR32 * ysq);
       unsigned long long best = 0ull;
+      const uint4 ck = cand4[p];
+      const uint32_t keys[4] = {ck.x, ck.y, ck.z, ck.w};
       int ci[4];
       float sc[4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const uint32_t key = cand[p * 4 + c];
-        ci[c] = key ? (int)(imask - (key & imask)) : -1;
-      }
+      for (int c = 0; c < 4; ++c) ci[c] = keys[c] ? (int)(imask - (keys[c] & imask)) : -1;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) sc[c] = half_dot(a_fp + (ci[c] >= 0 ? ci[c] : 0) * FZ_MP, h, rv);
+      for (int c = 0; c < 4; ++c) sc[c] = half_dot(arow(ci[c] >= 0 ? ci[c] : 0), h, rv);
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         sc[c] = pair_sum(sc[c]);
@@ -313,18 +362,15 @@ omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__rest
         if (h == 0) atomicAdd((unsigned long long *)&stats[1], 1ull);
       }
       const int q = act ? (int)key_idx(best) : 0;
-      const float *aq = a_fp + q * FZ_MP;
-      float4 av[FZ_NCH];
-#pragma unroll
-      for (int t = 0; t < FZ_NCH; ++t) av[t] = reinterpret_cast<const float4 *>(aq + h * FZ_HALF)[t];
-      const float aa = pair_sum(half_dot(aq, h, av));
+      const float *aq = arow(q);
+      const float aa = pair_sum(half_dot2(aq, aq, h));
       const float bq = pair_sum(half_dot(aq, h, yv));
       const bool f32 = act && !(fl & 2);
       // Gram column V_j = <a_om_j, a_q>
       const int kw = __reduce_max_sync(0xffffffffu, act ? k : 0);
       for (int j = 0; j < kw; ++j) {
         const bool o = f32 && j < k;
-        const float vj = pair_sum(half_dot(o ? colp[j] : aq, h, av));
+        const float vj = pair_sum(half_dot2(o ? arow(omp[j]) : aq, aq, h));
         if (o && h == 0) Vp[j] = vj;
       }
       __syncwarp();
@@ -333,9 +379,9 @@ omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__rest
       if (f32 && h == 0) {
         float ww = 0.f, wz = 0.f;
         for (int i = 0; i < k; ++i) {
-          float s = Vp[i];
-          for (int j = 0; j < i; ++j) s = fmaf(-Lp[ftri(i) + j], Wp[j], s);
-          const float w = s * Linv[i];
+          float sacc = Vp[i];
+          for (int j = 0; j < i; ++j) sacc = fmaf(-Lp[ftri(i) + j], Wp[j], sacc);
+          const float w = sacc * Linv[i];
           Wp[i] = w;
           ww = fmaf(w, w, ww);
           wz = fmaf(w, zp[i], wz);
@@ -349,9 +395,9 @@ omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__rest
           Linv[k] = il;
           zp[k] = (bq - wz) * il;
           for (int i = k; i >= 0; --i) {
-            float s = zp[i];
-            for (int j = i + 1; j <= k; ++j) s = fmaf(-Lp[ftri(j) + i], Wp[j], s);
-            Wp[i] = s * Linv[i];
+            float sacc = zp[i];
+            for (int j = i + 1; j <= k; ++j) sacc = fmaf(-Lp[ftri(j) + i], Wp[j], sacc);
+            Wp[i] = sacc * Linv[i];
           }
         } else {
           atomicAdd((unsigned long long *)&stats[0], 1ull);
@@ -361,15 +407,22 @@ omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__rest
       if (f32 && !ok32) fl |= 2;
       // FP64 from scratch (rare; one thread of the pair)
       const bool go64 = act && !ok32;
-      if (go64 && h == 0) fb_misc = csp::grp::fp64_projection(M, yrow, S, k, aq) ? 1 : 0;
+      if (go64 && h == 0) {
+        const float *cp[FZ_KMAX + 1];
+        for (int j = 0; j < k; ++j) cp[j] = arow(omp[j]);
+        GrpSmem S{};
+        S.W = Wp;
+        S.colp = cp;
+        fb_misc = csp::grp::fp64_projection(M, yrow, S, k, aq) ? 1 : 0;
+      }
       const bool app64 = __shfl_sync(0xffffffffu, fb_misc, lane & ~1) != 0 && go64;
       const bool appended = ok32 || app64;
       if (act && f32 && !appended && h == 0) {
         // q depends on the chosen columns: alpha of the chosen ones from the factor
         for (int i = k - 1; i >= 0; --i) {
-          float s = zp[i];
-          for (int j = i + 1; j < k; ++j) s = fmaf(-Lp[ftri(j) + i], Wp[j], s);
-          Wp[i] = s * Linv[i];
+          float sacc = zp[i];
+          for (int j = i + 1; j < k; ++j) sacc = fmaf(-Lp[ftri(j) + i], Wp[j], sacc);
+          Wp[i] = sacc * Linv[i];
         }
       }
       if (act && !appended) {
@@ -378,10 +431,7 @@ omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__rest
       }
       __syncwarp();
       // residue r = y - A_Omega alpha
-      if (appended && h == 0) {
-        omp[k] = q;
-        colp[k] = aq;
-      }
+      if (appended && h == 0) omp[k] = q;
       __syncwarp();
       const int kr = __reduce_max_sync(0xffffffffu, appended ? k + 1 : 0);
       if (appended) {
@@ -391,10 +441,10 @@ omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__rest
       for (int j = 0; j < kr; ++j) {
         if (appended && j <= k) {
           const float aj = Wp[j];
-          const float4 *c4 = reinterpret_cast<const float4 *>(colp[j] + h * FZ_HALF);
+          const float4 *c4 = reinterpret_cast<const float4 *>(arow(omp[j]));
 #pragma unroll
           for (int t = 0; t < FZ_NCH; ++t) {
-            const float4 cc = c4[t];
+            const float4 cc = c4[2 * t + h];
             rv[t].x = fmaf(-aj, cc.x, rv[t].x);
             rv[t].y = fmaf(-aj, cc.y, rv[t].y);
             rv[t].z = fmaf(-aj, cc.z, rv[t].z);
@@ -426,11 +476,22 @@ omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__rest
       }
     }
   }
+  if (threadIdx.x == 0) mbar_drain(afull, 0);  // no TMA write outlives the CTA
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols * NGRP) : "memory");
+}
+
+int device_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  }
+  return sms;
 }
 
 }  // namespace
@@ -438,25 +499,50 @@ omp_fused_tc_kernel(const __grid_constant__ CUtensorMap tmA, const float *__rest
 bool fused_top_supported(int M, int T, int Kb) {
   // T a multiple of 64: each epilogue half reads whole 32-column TMEM blocks
   return M > 0 && M <= FZ_MP && M % 4 == 0 && T >= 64 && T <= 256 && T % 64 == 0 && Kb >= 1 && Kb <= FZ_KMAX &&
-         fz_layout(T).total <= 227 * 1024;
+         fz_layout(T, Kb, 1).total <= 227 * 1024;
 }
 
-bool launch_omp_fused_tc(const float *Y, int M, const float *A, const float *inv_norm, const __nv_bfloat16 *Abf,
-                         int Mp, int T, const int32_t *ids, int64_t n, const int8_t *Kp, int Kuni, int Kb,
-                         int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
-                         unsigned long long *err, cudaStream_t s) {
+bool launch_omp_fused_tc(const float *Y, int M, const float *const *A, const float *const *inv_norm,
+                         const __nv_bfloat16 *const *Abf, int nph, const int64_t *phase_start, int Mp, int T,
+                         const int32_t *ids, int64_t n, const int8_t *Kp, int Kuni, int Kb, int32_t *omega,
+                         float *alpha, int ldo, int8_t *k_eff, int64_t *stats, unsigned long long *err,
+                         cudaStream_t s) {
   if (n == 0) return true;
-  if (Mp != FZ_MP || !fused_top_supported(M, T, Kb)) return false;
-  CUtensorMap mA;
-  if (!tc_make_map_bf16(&mA, Abf, (uint64_t)Mp, (uint64_t)T, (uint32_t)T)) return false;
-  const int sm = fz_layout(T).total;
-  if (cudaFuncSetAttribute(omp_fused_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
-    return false;
+  if (Mp != FZ_MP || nph < 1 || nph > FZ_MAXPH || !fused_top_supported(M, T, Kb)) return false;
+  FzArgs args;
+  memset(&args, 0, sizeof(args));
+  args.nph = nph;
+  int64_t tiles = 0;
+  for (int ph = 0; ph <= nph; ++ph) args.row0[ph] = phase_start ? phase_start[ph] : (ph ? n : 0);
+  for (int ph = 0; ph < nph; ++ph) tiles += (args.row0[ph + 1] - args.row0[ph] + FZ_M - 1) / FZ_M;
+  // two tiles per CTA (sharing the atoms) once there are more tiles than SMs
+  const int ngrp = (tiles > device_sms() && fz_layout(T, Kb, 2).total <= 227 * 1024) ? 2 : 1;
+  int64_t ctas = 0;
+  for (int ph = 0; ph < nph; ++ph) {
+    if (!tc_make_map_bf16(&args.map[ph], Abf[ph], (uint64_t)Mp, (uint64_t)T, (uint32_t)T)) return false;
+    args.A[ph] = A[ph];
+    args.inv[ph] = inv_norm[ph];
+    args.cta0[ph] = (int)ctas;
+    const int64_t t = (args.row0[ph + 1] - args.row0[ph] + FZ_M - 1) / FZ_M;
+    ctas += (t + ngrp - 1) / ngrp;
+  }
+  args.cta0[nph] = (int)ctas;
+  if (ctas == 0) return true;
+  if (ctas > INT32_MAX) return false;
   int idx_bits = 1;
   while ((1 << idx_bits) < T) ++idx_bits;
-  const unsigned grid = (unsigned)((n + FZ_M - 1) / FZ_M);
-  omp_fused_tc_kernel<<<grid, FZ_THREADS, sm, s>>>(mA, Y, M, A, inv_norm, T, idx_bits, ids, n, Kp, Kuni, Kb, omega,
-                                                   alpha, ldo, k_eff, stats, err);
+  const int sm = fz_layout(T, Kb, ngrp).total;
+  if (ngrp == 2) {
+    if (cudaFuncSetAttribute(omp_fused_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
+      return false;
+    omp_fused_tc_kernel<2><<<(unsigned)ctas, 2 * FZ_GT, sm, s>>>(args, Y, M, T, idx_bits, ids, Kp, Kuni, Kb,
+                                                                      omega, alpha, ldo, k_eff, stats, err);
+  } else {
+    if (cudaFuncSetAttribute(omp_fused_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
+      return false;
+    omp_fused_tc_kernel<1><<<(unsigned)ctas, FZ_GT, sm, s>>>(args, Y, M, T, idx_bits, ids, Kp, Kuni, Kb,
+                                                                  omega, alpha, ldo, k_eff, stats, err);
+  }
   return true;
 }
 

@@ -165,6 +165,33 @@ def test_full_dictionary_forms_agree_with_oracle(B, M, T, K, form):
     assert rate >= MATCH and worst <= REL_TOL, bad[:10]
 
 
+@pytest.mark.parametrize("H,stride,n_sample", [(512, 2, 300), (168, 1, 300)])
+def test_fused_form_at_size(H, stride, n_sample):
+    """Fused full-dictionary form forced on the Bayer coarse level (T 256, M 64,
+    K 4), cross-scale: the 512x512 image (64,009 patches, one mosaic phase,
+    two 128-patch tiles per CTA) and a stride-1 168x168 image (25,921 patches
+    over the four phases in one launch); the oracle solves a seeded sample."""
+    from paper_1511_05174_gb300.context import Context
+    w = synthetic.make_workload("bayer", H=H, W=H)
+    w.geometry.stride = stride
+    B = w.n_patches
+    w.K_levels = [np.full(B, int(k[0]), np.int32) for k in w.K_levels]
+    sample = np.sort(np.random.default_rng(1).choice(B, n_sample, replace=False))
+    ctx = Context(0)
+    ctx.load_workload(w)
+    Yd = ctx.extract(torch.from_numpy(w.meas).cuda())
+    K, K_patch, Kmax = budgets(w, "cross_scale")
+    ctx.set_top_level_form(2)
+    ctx.profile(True)
+    sup, coef, keff = ctx.solve(Yd, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
+    prof = ctx.profile_read()
+    assert prof["omp_fused"][0] == 1  # one launch for every phase
+    o, a, k, _ = oracle.cross_scale_omp(w, Y=oracle.extract_patches(w), patches=sample)
+    rate, worst, bad = compare(w.dicts[0], sup.cpu().numpy()[sample], coef.cpu().numpy()[sample],
+                               keff.cpu().numpy().astype(np.int64)[sample], o, a, k)
+    assert rate >= MATCH and worst <= REL_TOL, sample[bad[:10]]
+
+
 def test_fused_form_rejects_dependent_atom():
     """Fused form: a_2 = a_0 + a_1 exactly (integer atoms, the other 61 atoms
     zero and never eligible); the FP64 pivot test rejects a_2, k_eff = 2 and
