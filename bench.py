@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--variant", type=int, default=None,
-                    help="pin the restricted-solver variant (0-7) instead of autotuning (profiling runs)")
+                    help="pin the restricted-solver variant (0-9) instead of autotuning (profiling runs)")
     ap.add_argument("--serving-jobs", type=int, default=24, help="jobs per offered rate")
     return ap.parse_args()
 

@@ -298,14 +298,16 @@ csp_status csp_job_release(csp_server *srv, uint64_t job_id);
  * matrix -- the "Batch-OMP" form of the same iteration, scoring p0 - G alpha,
  * or its Gram-Schmidt form, which updates the correlations per appended atom
  * and solves for alpha once -- each with 4, 8 or 16 lanes per patch for
- * M <= 64, twice that for larger M).  csp_autotune runs
+ * M <= 64, twice that for larger M; the Gram-Schmidt form also with each
+ * lane's candidates held in registers, 8 or 16 lanes per patch).  csp_autotune runs
  * csp_solve once per variant on the given batch (same arguments as
  * csp_solve, outputs overwritten), times each with CUDA events, keeps the
  * fastest for this context and reports the times; then, with that variant,
  * times the two forms of the full-dictionary level (csp_set_top_level_form)
  * where the fused form applies and keeps the faster.  Synchronises `stream`. */
-#define CSP_TUNE_VARIANTS 8  /* 0: L2-cooperative, 1: shared-memory staged, 2-4: Gram-matrix proxy, 5-7: Gram-Schmidt
-                                form, each narrow to wide */
+#define CSP_TUNE_VARIANTS 10 /* 0: L2-cooperative, 1: shared-memory staged, 2-4: Gram-matrix proxy, 5-7: Gram-Schmidt
+                                form, each narrow to wide; 8-9: Gram-Schmidt form with the candidates' state in
+                                registers, 8 and 16 lanes per patch */
 typedef struct csp_tune_result {
     int restricted_variant;            /* chosen variant index                      */
     double ms[CSP_TUNE_VARIANTS];      /* solve time per variant (ms)               */
@@ -320,7 +322,8 @@ csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const floa
                         csp_tune_result *out);
 
 /* Pin the restricted-solver variant (0 .. CSP_TUNE_VARIANTS - 1), e.g. from a
- * stored csp_tune_result.  Variants 2-7 fall back to 0 on levels whose Gram
+ * stored csp_tune_result.  Variants 8-9 run as variant 6 where M > 8 x lanes,
+ * Kb > 8 or more than 8 candidates per lane.  Variants 2-9 fall back to 0 on levels whose Gram
  * matrix was not kept (T^2 floats above 256 MiB or beyond the memory budget).
  * Errors: CSP_ERR_INVALID for an unknown variant. */
 csp_status csp_set_kernel_variant(csp_ctx *ctx, int restricted_variant);

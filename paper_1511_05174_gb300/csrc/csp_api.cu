@@ -370,13 +370,15 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
     if (want && bf16 && !L.per_patch && L.Mp == 64 && fused_top_supported(L.M, L.T, Kb[top])) {
       const float *Aph[kMaxPhases] = {}, *Iph[kMaxPhases] = {};
       const __nv_bfloat16 *Bph[kMaxPhases] = {};
+      const float *Gph[kMaxPhases] = {};
       for (int ph = 0; ph < nph; ++ph) {
         Aph[ph] = L.A[ph];
         Iph[ph] = L.inv_norm[ph];
         Bph[ph] = L.Abf[ph];
+        Gph[ph] = L.G[ph];
       }
       run(ctx, KK_FUSED, s, B, [&] {
-        fused_done = launch_omp_fused_tc(Yl[top], L.M, Aph, Iph, Bph, nph, phased ? ps.phase_start : nullptr, L.Mp,
+        fused_done = launch_omp_fused_tc(Yl[top], L.M, Aph, Iph, Bph, Gph, nph, phased ? ps.phase_start : nullptr, L.Mp,
                                          L.T, phased ? ps.phase_ids : nullptr, B, prm->K_patch[top], prm->K[top],
                                          Kb[top], lv_om[top], lv_al[top], ldo[top], lv_ke[top], W.stats_dev,
                                          (unsigned long long *)(W.stats_dev + 4), s);

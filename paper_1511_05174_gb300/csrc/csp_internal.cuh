@@ -243,11 +243,13 @@ bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, con
 // tensor-core proxy with FP32 re-score; writes omega/alpha/k_eff directly.
 // One launch covers the nph phase groups (host phase_start[nph + 1] gives the
 // positions of each group in `ids`; null: one group of n patches, ids may be
-// null); A / inv_norm / Abf hold one pointer per phase.  Returns false when the
-// shape is not supported or a tensor map fails.
+// null); A / inv_norm / Abf / gram hold one pointer per phase (a null Gram
+// matrix: the Gram columns from the rows).  Returns false when the shape is
+// not supported or a tensor map fails.
 bool fused_top_supported(int M, int T, int Kb);
 bool launch_omp_fused_tc(const float *Y, int M, const float *const *A, const float *const *inv_norm,
-                         const __nv_bfloat16 *const *Abf, int nph, const int64_t *phase_start, int Mp, int T,
+                         const __nv_bfloat16 *const *Abf, const float *const *gram, int nph,
+                         const int64_t *phase_start, int Mp, int T,
                          const int32_t *ids, int64_t n, const int8_t *Kp, int Kuni, int Kb, int32_t *omega,
                          float *alpha, int ldo, int8_t *k_eff, int64_t *stats, unsigned long long *err,
                          cudaStream_t s);
@@ -264,6 +266,13 @@ void launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const
                                 const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int8_t *Kp,
                                 int Kuni, int Kb, int32_t *omega, float *alpha, int ldo, int8_t *k_eff,
                                 int64_t *stats, const float *gram, int T, cudaStream_t s);
+// Gram-Schmidt form with the candidates' state in registers (G = 8 or 16 lanes
+// per patch); false (nothing launched) when M > 8 G, Kb > 8 or cap > 8 G.
+bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, const float *inv_norm,
+                               const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx,
+                               int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
+                               const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
+                               int8_t *k_eff, int64_t *stats, const float *gram, int T, cudaStream_t s);
 // Gram matrix A A^T ([T][T] FP32) of an effective dictionary.
 void launch_gram(const float *A, int T, int M, float *Gm, cudaStream_t s);
 // variant 0: rows from L2 every pass (cooperative groups); 1: rows staged in shared memory;

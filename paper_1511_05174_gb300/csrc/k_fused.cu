@@ -67,6 +67,7 @@ struct FzLayout {
   int a_bf;   // BF16 atoms [T][64], 128-byte swizzle (offset 0, 1024-aligned)
   int a_fp;   // FP32 atoms [T][FZ_AS]
   int inv;    // [T] 1/||a_i||
+  int nrm;    // [T] ||a_i||^2 (FP32, the update's own dot product)
   int grp, gstride;                 // first group block, bytes per block (1024-aligned)
   int r_bf, cand, L, Linv, z, om, V, W;  // offsets within a group block
   int ls, ks, vs;                   // per-patch strides (words, odd): L, Linv/z/om, V/W
@@ -83,6 +84,7 @@ __host__ __device__ inline FzLayout fz_layout(int T, int Kb, int ngrp) {
   L.a_bf = o; o += T * FZ_MP * 2;
   L.a_fp = o; o += T * FZ_AS * 4;
   L.inv = o; o += T * 4;
+  L.nrm = o; o += T * 4;
   o = (o + 1023) & ~1023;
   L.grp = o;
   int g = 0;
@@ -106,6 +108,7 @@ struct FzArgs {
   CUtensorMap map[FZ_MAXPH];            // BF16 atoms of each phase
   const float *A[FZ_MAXPH];             // FP32 effective dictionary [T][M]
   const float *inv[FZ_MAXPH];           // [T] 1/||a_i||
+  const float *G[FZ_MAXPH];             // [T][T] Gram matrix A A^T (null: Gram column from the rows)
   int64_t row0[FZ_MAXPH + 1];           // first position of each phase in the patch list
   int cta0[FZ_MAXPH + 1];               // first CTA of each phase
   int nph;
@@ -175,6 +178,7 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
   uint8_t *a_bf = sm + lay.a_bf;
   float *a_fp = reinterpret_cast<float *>(sm + lay.a_fp);
   float *s_inv = reinterpret_cast<float *>(sm + lay.inv);
+  float *s_nrm = reinterpret_cast<float *>(sm + lay.nrm);
   uint64_t *bars = reinterpret_cast<uint64_t *>(sm + lay.bars);
   uint64_t *afull = bars, *accfull = bars + 1;  // accfull[NGRP]
   uint32_t *tmem_holder = reinterpret_cast<uint32_t *>(bars + 1 + NGRP);
@@ -186,6 +190,7 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
   while (ph + 1 < args.nph && (int)blockIdx.x >= args.cta0[ph + 1]) ++ph;
   const float *A = args.A[ph];
   const float *inv_norm = args.inv[ph];
+  const float *Gm = args.G[ph];
   const int64_t prow0 = args.row0[ph], pn = args.row0[ph + 1] - prow0;
   const int64_t tile_first = (int64_t)(blockIdx.x - args.cta0[ph]) * NGRP;
   const int64_t ntiles = (pn + FZ_M - 1) / FZ_M;
@@ -226,6 +231,14 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
       }
     }
     for (int i = threadIdx.x; i < T; i += nt) s_inv[i] = __ldg(inv_norm + i);
+  }
+  __syncthreads();
+  // ||a_i||^2 with the pair arithmetic of the update (half_dot2 + pair sum)
+  for (int e = threadIdx.x; e < 2 * T; e += blockDim.x) {
+    const int i = e >> 1, h = e & 1;
+    const float *ai = a_fp + i * FZ_AS;
+    const float v = pair_sum(half_dot2(ai, ai, h));
+    if (h == 0) s_nrm[i] = v;
   }
   tc_fence_before();
   __syncthreads();
@@ -284,6 +297,12 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
     const uint32_t imask = (1u << idx_bits) - 1u;
     const uint32_t smask = 0x7fffffffu & ~imask;
     const int hcols = T / 2;
+    // with two groups, group 1 starts once group 0 has finished its first
+    // epilogue, so that one group's epilogue (integer-pipe bound) runs beside
+    // the other's update (shared-memory bound) instead of in step with it
+    const bool stagger = NGRP == 2 && nact == 2;
+    bool staged = false;
+    if (stagger && g == 1) asm volatile("bar.sync 3, %0;" ::"n"(2 * FZ_GT) : "memory");
     for (int it = 0; it < Kb; ++it) {
       // the residual tile is complete: C = R A^T into this group's columns
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -306,14 +325,14 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
       if (*flag) break;
       tc_fence_after();
       uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;  // two independent chains
-      for (int c0 = 0; c0 < hcols; c0 += 32) {
-        uint32_t v[32];
-        tmem_ld32_nowait(tm + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ehalf * hcols + c0), v);
+      for (int c0 = 0; c0 < hcols; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16_nowait(tm + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ehalf * hcols + c0), v);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int base = ehalf * hcols + c0;  // T is a multiple of 64: every column is an atom
         const uint32_t cb = imask - (uint32_t)base;
 #pragma unroll
-        for (int i = 0; i < 32; i += 2) {
+        for (int i = 0; i < 16; i += 2) {
           top4_insert((v[i] & smask) | (cb - (uint32_t)i), a0, a1, a2, a3);
           top4_insert((v[i + 1] & smask) | (cb - (uint32_t)(i + 1)), b0, b1, b2, b3);
         }
@@ -334,6 +353,10 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
         cand4[erow] = make_uint4(a0, a1, a2, a3);
       }
       group_bar(bar_id);
+      if (stagger && g == 0 && !staged) {
+        asm volatile("bar.arrive 3, %0;" ::"n"(2 * FZ_GT) : "memory");
+        staged = true;
+      }
       // ---- update: a thread pair per patch ----
       act = act && k < Kpb && !(rsq <= kEpsR32 * ysq);
       unsigned long long best = 0ull;
@@ -363,15 +386,26 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
       }
       const int q = act ? (int)key_idx(best) : 0;
       const float *aq = arow(q);
-      const float aa = pair_sum(half_dot2(aq, aq, h));
-      const float bq = pair_sum(half_dot(aq, h, yv));
       const bool f32 = act && !(fl & 2);
-      // Gram column V_j = <a_om_j, a_q>
-      const int kw = __reduce_max_sync(0xffffffffu, act ? k : 0);
-      for (int j = 0; j < kw; ++j) {
-        const bool o = f32 && j < k;
-        const float vj = pair_sum(half_dot2(o ? arow(omp[j]) : aq, aq, h));
-        if (o && h == 0) Vp[j] = vj;
+      // Gram column V_j = <a_om_j, a_q> = G[q][om_j] (G symmetric), issued first
+      float vr[FZ_KMAX];
+      if (Gm) {
+#pragma unroll
+        for (int j = 0; j < FZ_KMAX; ++j) vr[j] = (f32 && h == 0 && j < k) ? __ldg(Gm + (int64_t)q * T + omp[j]) : 0.f;
+      }
+      const float aa = s_nrm[q];
+      const float bq = pair_sum(half_dot(aq, h, yv));
+      if (Gm) {
+#pragma unroll
+        for (int j = 0; j < FZ_KMAX; ++j)
+          if (f32 && h == 0 && j < k) Vp[j] = vr[j];
+      } else {
+        const int kw = __reduce_max_sync(0xffffffffu, act ? k : 0);
+        for (int j = 0; j < kw; ++j) {
+          const bool o = f32 && j < k;
+          const float vj = pair_sum(half_dot2(o ? arow(omp[j]) : aq, aq, h));
+          if (o && h == 0) Vp[j] = vj;
+        }
       }
       __syncwarp();
       // projection (scalar work on h == 0): w = L^{-1} V, pivot, z_k, alpha = L^{-T} z
@@ -468,6 +502,7 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
       // next proxy input (the MMA of this iteration has retired: accfull fired)
       store_rbf(r_bf, p, h, rv);
     }
+    if (stagger && g == 0 && !staged) asm volatile("bar.arrive 3, %0;" ::"n"(2 * FZ_GT) : "memory");
     if (valid) {
       if (h == 0) k_eff[b] = (int8_t)k;
       for (int j = h; j < ldo; j += 2) {
@@ -503,7 +538,7 @@ bool fused_top_supported(int M, int T, int Kb) {
 }
 
 bool launch_omp_fused_tc(const float *Y, int M, const float *const *A, const float *const *inv_norm,
-                         const __nv_bfloat16 *const *Abf, int nph, const int64_t *phase_start, int Mp, int T,
+                         const __nv_bfloat16 *const *Abf, const float *const *gram, int nph, const int64_t *phase_start, int Mp, int T,
                          const int32_t *ids, int64_t n, const int8_t *Kp, int Kuni, int Kb, int32_t *omega,
                          float *alpha, int ldo, int8_t *k_eff, int64_t *stats, unsigned long long *err,
                          cudaStream_t s) {
@@ -522,6 +557,7 @@ bool launch_omp_fused_tc(const float *Y, int M, const float *const *A, const flo
     if (!tc_make_map_bf16(&args.map[ph], Abf[ph], (uint64_t)Mp, (uint64_t)T, (uint32_t)T)) return false;
     args.A[ph] = A[ph];
     args.inv[ph] = inv_norm[ph];
+    args.G[ph] = gram ? gram[ph] : nullptr;
     args.cta0[ph] = (int)ctas;
     const int64_t t = (args.row0[ph + 1] - args.row0[ph] + FZ_M - 1) / FZ_M;
     ctas += (t + ngrp - 1) / ngrp;

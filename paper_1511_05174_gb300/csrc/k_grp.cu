@@ -354,18 +354,17 @@ __host__ __device__ __forceinline__ int gram_group_bytes(int Kb, int cap) {
   return (bytes + 127) / 128 * 128 + 16;  // groups start on different bank offsets
 }
 
-// Candidate list f(Omega_up) of one patch (parents in support order, each
-// parent's children in link order, at most cap; overflow counted in stats[3]),
-// the candidates' inverse norms, and p0 = A_C^T y (RB rows per load wave).
-// pstart / pbeg: 2 x CSP_MAX_K ints of scratch.  Returns |C|.  Warp-collective.
-template <int G, int NCH>
-__device__ int gram_setup(bool valid, int s, int64_t b, int kup, const int32_t *__restrict__ omega_up, int ldo_up,
-                          const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx, int cap,
-                          const GrpSmem &S, int *pstart, int *pbeg, const float *__restrict__ inv_norm,
-                          int64_t *stats, int M, const float *__restrict__ A, const float4 (&yv)[NCH], float *p0) {
+// Candidate list f(Omega_up) of one patch into S.cs (parents in support order,
+// each parent's children in link order, at most cap; overflow counted in
+// stats[3]).  pstart / pbeg: 2 x CSP_MAX_K ints of scratch.  Returns |C|.
+// Warp-collective.
+template <int G>
+__device__ int list_candidates(bool valid, int s, int64_t b, int kup, const int32_t *__restrict__ omega_up,
+                               int ldo_up, const int32_t *__restrict__ child_off,
+                               const int32_t *__restrict__ child_idx, int cap, const GrpSmem &S, int *pstart,
+                               int *pbeg, int64_t *stats) {
   constexpr int KPL = (CSP_MAX_K + G - 1) / G;
-  const int nv = M >> 2;
-  // candidate set f(Omega_up): parents' child ranges in one wave, then the children
+  // parents' child ranges in one wave, then the children
   int pr[KPL], c0r[KPL], c1r[KPL];
 #pragma unroll
   for (int t = 0; t < KPL; ++t) {
@@ -405,6 +404,19 @@ __device__ int gram_setup(bool valid, int s, int64_t b, int kup, const int32_t *
     S.cs[c] = child_idx[pbeg[j] + (c - pstart[j])];
   }
   __syncwarp();
+  return nc;
+}
+
+// The candidate list (list_candidates), the candidates' inverse norms, and
+// p0 = A_C^T y (RB rows per load wave).  Returns |C|.  Warp-collective.
+template <int G, int NCH>
+__device__ int gram_setup(bool valid, int s, int64_t b, int kup, const int32_t *__restrict__ omega_up, int ldo_up,
+                          const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx, int cap,
+                          const GrpSmem &S, int *pstart, int *pbeg, const float *__restrict__ inv_norm,
+                          int64_t *stats, int M, const float *__restrict__ A, const float4 (&yv)[NCH], float *p0) {
+  const int nv = M >> 2;
+  const int nc = list_candidates<G>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
+                                    stats);
   for (int c0 = s; c0 < nc; c0 += 4 * G) {
     float iv[4];
 #pragma unroll
@@ -889,6 +901,221 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
   }
 }
 
+// ---------------------------------------------------------------------------
+// Restricted OMP in Gram-Schmidt form with the candidate state in registers.
+// Same iteration as omp_restricted_qr_kernel, but lane s of a group owns the
+// candidates c = s + G u (u < CPL) and keeps, per candidate, its atom index,
+// 1/||a_c||, the correlation c_c = <a_c, r> and its row of Q_C = A_C^T U
+// (KM >= Kb entries, zero beyond the chosen count) in registers.  Per
+// iteration: the argmax over the group, the owner of q publishes its row of
+// Q_C (w, the new row of L) through shared memory, every lane updates its own
+// candidates from G[q][c] (one load wave), so the only shared-memory traffic
+// is the k-vector w.  FP64 fallback, the explicit residual near the FP32
+// floor and the outputs are those of the shared-memory form.
+// M <= 8 G (two float4 chunks of y per lane for p0 = A_C^T y).
+// Per-group shared memory: GrpSmem | p0[cap] | parents' child ranges [2 x CSP_MAX_K].
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int reg_group_bytes(int Kb, int cap) {
+  const int bytes = grp_smem_bytes(Kb, cap) + up16(4 * cap) + 8 * CSP_MAX_K;
+  return (bytes + 127) / 128 * 128 + 16;
+}
+
+template <int G, int CPL, int KM>
+__global__ void __launch_bounds__(WV_WARPS * 32, 4)
+omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
+                          const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
+                          const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx,
+                          int cap, const int32_t *__restrict__ omega_up, int ldo_up,
+                          const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
+                          int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
+                          int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
+  constexpr int NG = 32 / G;
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
+  const int64_t wbase = ((int64_t)blockIdx.x * WV_WARPS + wib) * NG;
+  if (wbase >= n) return;  // whole warp
+  const int64_t wi = wbase + g;
+  const bool valid = wi < n;
+  char *gbase = smem_raw + (size_t)(wib * NG + g) * reg_group_bytes(Kb, cap);
+  const GrpSmem S = carve(gbase, Kb, cap);
+  float *p0 = reinterpret_cast<float *>(gbase + grp_smem_bytes(Kb, cap));
+  int *pstart = reinterpret_cast<int *>(gbase + grp_smem_bytes(Kb, cap) + up16(4 * cap));
+  int *pbeg = pstart + CSP_MAX_K;
+  const int nv = M >> 2;
+  const int64_t b = valid ? (ids ? __ldg(ids + wi) : wi) : 0;
+  int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
+  Kpb = Kpb < Kb ? Kpb : Kb;
+  const int kup = valid ? keff_up[b] : 0;
+  const float *yrow = Y + b * M;
+  const float4 *y4 = reinterpret_cast<const float4 *>(yrow);
+  // candidates, their inverse norms and p0 = A_C^T y (group-cooperative, in shared memory)
+  float4 yv[2];
+  load_chunks<G, 2>(yv, yrow, nv, s, valid);
+  const int nc = gram_setup<G, 2>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
+                                  inv_norm, stats, M, A, yv, p0);
+  const float ysq = gsum<G>(dotc<2>(yv, yv));
+  // this lane's candidates into registers (u < ucnt: a bound uniform over the warp, <= CPL)
+  const int ucnt = __reduce_max_sync(kFull, (nc + G - 1) / G);
+  int cs[CPL];
+  float inv[CPL], cc[CPL], Q[CPL][KM];
+#pragma unroll
+  for (int u = 0; u < CPL; ++u) {
+    const int c = s + G * u;
+    const bool o = u < ucnt && c < nc;
+    cs[u] = o ? S.cs[c] : -1;
+    inv[u] = o ? S.invn[c] : -1.f;
+    cc[u] = o ? p0[c] : 0.f;
+#pragma unroll
+    for (int j = 0; j < KM; ++j) Q[u][j] = 0.f;
+  }
+  float rsq = ysq;
+  bool act = valid && Kpb > 0;
+  uint8_t fl = 0;  // bit 1: FP64 from here on
+  int k = 0, scored = 0;
+  const int Kw = __reduce_max_sync(kFull, Kpb);
+  for (int it = 0; it < Kw; ++it) {
+    act = act && k < Kpb && !(rsq <= kEpsR32 * ysq);
+    if (!__any_sync(kFull, act)) break;
+    if (act) ++scored;
+    // proxy from the current correlations
+    unsigned long long best = 0ull;
+#pragma unroll
+    for (int u = 0; u < CPL; ++u)
+      if (u < ucnt && act && inv[u] > 0.f) {
+        const unsigned long long key = pack_key(fabsf(cc[u]) * inv[u], cs[u]);
+        best = key > best ? key : best;
+      }
+    best = gmax<G>(best);
+    if (act && !best) act = false;  // candidate set exhausted
+    const int q = act ? key_idx(best) : 0;
+    // G[q][C] (row q: G is symmetric) and G[q][q], issued first
+    float gpre[CPL];
+#pragma unroll
+    for (int u = 0; u < CPL; ++u) gpre[u] = (u < ucnt && act && cs[u] >= 0) ? __ldg(gram + (int64_t)q * T + cs[u]) : 0.f;
+    const float aa = act ? __ldg(gram + (int64_t)q * T + q) : 0.f;
+    // the owner of q: no longer eligible; publishes its row of Q_C and p0_q
+#pragma unroll
+    for (int u = 0; u < CPL; ++u)
+      if (u < ucnt && act && cs[u] == q) {
+        inv[u] = -1.f;
+#pragma unroll
+        for (int j = 0; j < KM; ++j)
+          if (j < k) S.V[j] = Q[u][j];
+        S.misc[1] = s + G * u;
+      }
+    __syncwarp();
+    const bool f32 = act && !(fl & 2);
+    // new row of L: w_j = <u_j, a_q>
+    float w[KM];
+    float ww = 0.f, wz = 0.f;
+#pragma unroll
+    for (int j = 0; j < KM; ++j) {
+      const bool o = f32 && j < k;
+      w[j] = o ? S.V[j] : 0.f;
+      ww = fmaf(w[j], w[j], ww);
+      wz = fmaf(w[j], o ? S.z[j] : 0.f, wz);
+    }
+    const float d = aa - ww;
+    const bool ok32 = f32 && aa > 0.f && d >= kTauPivot * aa;
+    if (f32 && !ok32) {
+      fl |= 2;
+      if (s == 0) atomicAdd((unsigned long long *)&stats[0], 1ull);
+    }
+    if (ok32) {
+      const float lkk = sqrtf(d);
+      const float il = 1.f / lkk;
+      const float zk = (p0[S.misc[1]] - wz) * il;
+      if (s == 0) {
+#pragma unroll
+        for (int j = 0; j < KM; ++j)
+          if (j < k) S.L[tri(k) + j] = w[j];
+        S.L[tri(k) + k] = lkk;
+        S.Linv[k] = il;
+        S.z[k] = zk;
+        S.om[k] = q;
+        S.colp[k] = A + (int64_t)q * M;
+      }
+      // column k of Q_C and the correlations
+#pragma unroll
+      for (int u = 0; u < CPL; ++u)
+        if (u < ucnt && cs[u] >= 0) {
+          float v = gpre[u];
+#pragma unroll
+          for (int j = 0; j < KM; ++j) v = fmaf(-w[j], Q[u][j], v);
+          v *= il;
+#pragma unroll
+          for (int j = 0; j < KM; ++j)
+            if (j == k) Q[u][j] = v;
+          cc[u] = fmaf(-zk, v, cc[u]);
+        }
+      rsq = rsq - zk * zk;
+    }
+    // FP64 from scratch for the patches whose FP32 pivot failed (now or before)
+    const bool go64 = act && !ok32;
+    if (go64 && s == 0) S.misc[0] = fp64_projection(M, yrow, S, k, A + (int64_t)q * M) ? 1 : 0;
+    __syncwarp();
+    const bool app64 = go64 && S.misc[0] != 0;
+    // q depends on the chosen columns: alpha of the chosen ones from the FP32 factor
+    const bool restore = f32 && !ok32 && !app64;
+    if (__any_sync(kFull, restore))
+      grp_backsub<G>(restore, s, k - 1, __reduce_max_sync(kFull, restore ? k - 1 : 0), S);
+    if (app64 && s == 0) {
+      S.om[k] = q;
+      S.colp[k] = A + (int64_t)q * M;
+    }
+    __syncwarp();
+    if (app64)  // correlations c = p0 - G[C][Omega] alpha from the Gram rows of the chosen atoms
+#pragma unroll
+      for (int u = 0; u < CPL; ++u)
+        if (u < ucnt && cs[u] >= 0) {
+          float v = p0[s + G * u];
+          for (int j = 0; j <= k; ++j) v = fmaf(-S.W[j], __ldg(gram + (int64_t)S.om[j] * T + cs[u]), v);
+          cc[u] = v;
+        }
+    // ||r||^2 formed explicitly in FP64 mode and near the FP32 floor
+    const bool exact = app64 || (ok32 && rsq <= 1e-5f * ysq);
+    if (__any_sync(kFull, exact)) {
+      const bool need = exact && !app64;  // FP32: alpha over rows 0..k first
+      grp_backsub<G>(need, s, k, __reduce_max_sync(kFull, need ? k : 0), S);
+      float r2 = 0.f;
+      if (exact)
+        for (int j = s; j < nv; j += G) {
+          float4 r = __ldg(y4 + j);
+          for (int i = 0; i <= k; ++i) {
+            const float ai = S.W[i];
+            const float4 a = __ldg(reinterpret_cast<const float4 *>(S.colp[i]) + j);
+            r.x = fmaf(-ai, a.x, r.x);
+            r.y = fmaf(-ai, a.y, r.y);
+            r.z = fmaf(-ai, a.z, r.z);
+            r.w = fmaf(-ai, a.w, r.w);
+          }
+          r2 += dot4(r, r);
+        }
+      r2 = gsum<G>(r2);
+      if (exact) rsq = r2;
+    }
+    if (act) {
+      if (ok32 || app64) ++k;
+      else act = false;
+    }
+    __syncwarp();
+  }
+  // alpha = L^{-T} z for the patches that stayed in FP32 (FP64 ones hold it in S.W)
+  const bool fin = valid && !(fl & 2) && k > 0;
+  grp_backsub<G>(fin, s, k - 1, __reduce_max_sync(kFull, fin ? k - 1 : 0), S);
+  if (valid) {
+    if (s == 0) {
+      if (k < Kpb) atomicAdd((unsigned long long *)&stats[1], 1ull);
+      atomicAdd((unsigned long long *)&stats[2], (unsigned long long)nc * (unsigned long long)scored);
+      k_eff[b] = (int8_t)k;
+    }
+    for (int j = s; j < ldo; j += G) {
+      omega[b * ldo + j] = (j < k) ? S.om[j] : -1;
+      alpha[b * ldo + j] = (j < k) ? S.W[j] : 0.f;
+    }
+  }
+}
+
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // (G, NCH): about eight elements per lane.
@@ -971,6 +1198,36 @@ void launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const
                                                       ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats,
                                                       gram, T);
   });
+}
+
+bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, const float *inv_norm,
+                               const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx,
+                               int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
+                               const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
+                               int8_t *k_eff, int64_t *stats, const float *gram, int T, cudaStream_t s) {
+  if (M % 4 || M > 8 * G || Kb > 8 || (G != 8 && G != 16)) return false;
+  const int per_g = (cap + G - 1) / G;
+  if (per_g > 8) return false;
+  if (n == 0) return true;
+  const int CPL = per_g <= 2 ? 2 : (per_g <= 4 ? 4 : 8);
+  const int per_cta = WV_WARPS * (32 / G);
+  const size_t sm = (size_t)reg_group_bytes(Kb, cap) * per_cta;
+  auto go = [&](auto kern) {
+    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kern<<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up,
+                                                      ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats,
+                                                      gram, T);
+  };
+  switch ((G == 8 ? 0 : 100) + CPL) {
+    case 2: go(omp_restricted_reg_kernel<8, 2, 8>); break;
+    case 4: go(omp_restricted_reg_kernel<8, 4, 8>); break;
+    case 8: go(omp_restricted_reg_kernel<8, 8, 8>); break;
+    case 102: go(omp_restricted_reg_kernel<16, 2, 8>); break;
+    case 104: go(omp_restricted_reg_kernel<16, 4, 8>); break;
+    case 108: go(omp_restricted_reg_kernel<16, 8, 8>); break;
+    default: return false;
+  }
+  return true;
 }
 
 }  // namespace csp

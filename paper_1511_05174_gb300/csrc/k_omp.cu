@@ -752,6 +752,13 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            cudaStream_t s) {
   if (n == 0) return;
   if (variant >= 2 && (!gram || a_pstride || cpos)) variant = 0;  // the Gram variants need the level's shared Gram matrix
+  if (variant >= 8) {  // 8, 9: Gram-Schmidt form with register-resident candidates, 8 / 16 lanes per patch
+    if (launch_omp_restricted_reg(variant == 8 ? 8 : 16, Y, M, A, inv_norm, ids, n, child_off, child_idx, cap,
+                                  omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T,
+                                  s))
+      return;
+    variant = 6;  // shape outside the register form: the shared-memory Gram-Schmidt form
+  }
   if (variant >= 2) {  // 2-4: Gram proxy p0 - G alpha; 5-7: Gram-Schmidt form; narrow to wide lane groups
     launch_omp_restricted_gram((variant - 2) % 3, variant >= 5, Y, M, A, inv_norm, ids, n, child_off, child_idx, cap,
                                omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T, s);

@@ -365,7 +365,7 @@ def test_exactly_dependent_atom_ends_the_patch():
     assert rate == 1.0 and worst <= REL_TOL
 
 
-@pytest.mark.parametrize("variant", list(range(8)))
+@pytest.mark.parametrize("variant", list(range(10)))
 def test_restricted_dependent_candidate_falls_back_to_fp64(variant):
     """Fine step of Algorithm 2 whose candidate set holds an exactly dependent
     atom (a_2 = a_0 + a_1, integer atoms): every restricted variant rejects it
@@ -395,7 +395,7 @@ def test_restricted_dependent_candidate_falls_back_to_fp64(variant):
     assert rate == 1.0 and worst <= REL_TOL
 
 
-@pytest.mark.parametrize("variant", list(range(8)))
+@pytest.mark.parametrize("variant", list(range(10)))
 @pytest.mark.parametrize("key", ["bayer", "lightfield", "denoise_ragged", "video"])
 def test_restricted_variants_agree_with_oracle(key, variant):
     """Every restricted-solver variant the autotuner may pick meets the parity
@@ -493,7 +493,7 @@ def test_autotune_picks_a_variant():
     Y = ctx.extract(torch.from_numpy(w.meas).cuda())
     K, K_patch, Kmax = budgets(w, "cross_scale")
     r = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
-    assert r["restricted_variant"] in range(8) and all(t > 0 for t in r["ms"])
+    assert r["restricted_variant"] in range(10) and all(t > 0 for t in r["ms"])
     assert r["ms"][r["restricted_variant"]] == min(r["ms"])
     # the BF16 Bayer coarse level (T = 256, M = 64, K = 4) has both full-dictionary forms
     r2 = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
