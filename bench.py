@@ -414,8 +414,9 @@ def main():
 
     def timed(mode, sampler=None):
         """Headline timing (CUDA events around each step, solves replayed from
-        the library's CUDA graph), then a second pass with per-kernel profiling
-        (launch-by-launch events, graph replay off) for the breakdown."""
+        the library's CUDA graph, pipelined on two streams where it applies),
+        then a second pass with per-kernel profiling (launch-by-launch events
+        on one stream: graph replay and the pipeline off) for the breakdown."""
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         step(mode)  # records the graph of this mode's solve
         barrier()
@@ -434,12 +435,14 @@ def main():
         st = ctx.stats()
         ctx.profile_read(reset=True)
         ctx.profile(True)
+        ctx.set_pipeline(False)
         for i in range(args.steps):
             flush.zero_()
             step(mode)
         torch.cuda.synchronize()
         prof = ctx.profile_read(reset=True)
         ctx.profile(False)
+        ctx.set_pipeline(True)
         return max_over_ranks(ms, world, dev), prof, st, clocks
 
     ctx.set_graph_mode(True)
@@ -530,6 +533,9 @@ def main():
             "data": "synthetic (seeded; Gaussian unit-norm atoms, K-sparse N(0,1) codes)",
             "config": {**workload_config(w, args), "form": "cross_scale", "precision": args.precision,
                        "cuda_graph": "solve replayed from a CUDA graph (csp_set_graph_mode)",
+                       "pipeline": "fused coarse level of the second chunk beside the restricted level of the "
+                                   "first on a second stream (csp_set_pipeline); per-kernel times from a "
+                                   "one-stream pass",
                        "restricted_variant": tune["restricted_variant"],
                        "autotune_ms": [round(t, 4) for t in tune["ms"]],
                        "top_level_form": tune.get("top_level_form"),

@@ -365,6 +365,15 @@ csp_status csp_set_wait_test(csp_ctx *ctx, int on);
  * mode is on (or turn it off, which frees the graph). */
 csp_status csp_set_graph_mode(csp_ctx *ctx, int on);
 
+/* Pipelined cross-scale solve (not part of the method).  on != 0 (the
+ * default): when the full-dictionary level runs in the fused form, all
+ * patches fall in one mosaic phase group (always so without a mosaic) and
+ * there are more of them than one wave of that kernel holds, that wave's patches go down the finer levels on a second
+ * stream of the context while the fused kernel runs the rest, and the call's
+ * stream waits for both.  Results are identical either way; off: everything
+ * on the call's stream.  Errors: CSP_ERR_INVALID for a NULL ctx. */
+csp_status csp_set_pipeline(csp_ctx *ctx, int on);
+
 /* ---- Instrumentation (not part of the paper's method) ----------------------
  * Every kernel launch of a context is counted per kernel kind.  While
  * profiling is enabled, each launch is also bracketed by CUDA events on its

@@ -173,6 +173,10 @@ class Context:
         """Replay identical solves from a CUDA graph (see csp_set_graph_mode)."""
         b.csp_set_graph_mode(self._ctx, on)
 
+    def set_pipeline(self, on: bool = True) -> None:
+        """Pipelined cross-scale solve on two streams (see csp_set_pipeline)."""
+        b.csp_set_pipeline(self._ctx, on)
+
     def set_wait_test(self, on: bool) -> None:
         """Failure-detection test hook (see csp_set_wait_test)."""
         b.csp_set_wait_test(self._ctx, on)

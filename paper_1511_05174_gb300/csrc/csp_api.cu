@@ -313,6 +313,14 @@ csp_status prepare_own_patches(csp_ctx *ctx, int l, cudaStream_t s) {
   return build_patch_dicts(ctx, l, ctx->pcodes, ctx->B, ctx->pp_A[l], ctx->pp_inv[l], scratch, s);
 }
 
+// The second stream and the fork/join events of the pipelined solve.
+csp_status ensure_aux(csp_ctx *ctx) {
+  if (!ctx->aux) CSP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+  if (!ctx->ev_fork) CSP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+  if (!ctx->ev_join) CSP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  return CSP_OK;
+}
+
 // Solve the patch set `ps` with the context's dictionaries (prepared), using
 // workspace W.  Arguments validated by the caller.
 csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_solve_params *prm, const float *Y,
@@ -376,6 +384,60 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
         Iph[ph] = L.inv_norm[ph];
         Bph[ph] = L.Abf[ph];
         Gph[ph] = L.G[ph];
+      }
+      // pipelined cross-scale solve: the first chunk (one full wave of the fused
+      // kernel) goes down the scales on a second stream while the fused kernel
+      // runs the rest, so the restricted solver fills the SMs the fused
+      // kernel's last wave leaves idle.  Patches are independent: same results.
+      // Applies to one non-empty phase group (positions map to patch ids
+      // through its ids when there are ids, else they are the patch ids).
+      bool finer_shared = top > 0;
+      for (int l = 0; l < top; ++l) finer_shared = finer_shared && !ctx->lv[l].per_patch;
+      int ph0 = 0, nonempty = 0;
+      for (int ph = 0; ph < nph; ++ph)
+        if (n_of(ph) > 0) { ph0 = ph; ++nonempty; }
+      const int64_t wave = fused_wave_patches(L.T, Kb[top]);
+      if (ctx->pipeline && nonempty == 1 && finer_shared && B > wave) {
+        CSP_TRY(ensure_aux(ctx));
+        const int32_t *ids0 = ids_of(ph0);
+        auto fused_range = [&](int64_t off, int64_t n, cudaStream_t st) {
+          const int64_t d = ids0 ? 0 : off;  // data offset
+          bool ok = false;
+          run(ctx, KK_FUSED, st, n, [&] {
+            ok = launch_omp_fused_tc(Yl[top] + d * L.M, L.M, Aph + ph0, Iph + ph0, Bph + ph0, Gph + ph0, 1, nullptr,
+                                     L.Mp, L.T, ids0 ? ids0 + off : nullptr, n,
+                                     prm->K_patch[top] ? prm->K_patch[top] + d : nullptr, prm->K[top], Kb[top],
+                                     lv_om[top] + d * ldo[top], lv_al[top] + d * ldo[top], ldo[top], lv_ke[top] + d,
+                                     W.stats_dev, (unsigned long long *)(W.stats_dev + 4), st);
+          });
+          return ok;
+        };
+        auto restrict_range = [&](int64_t off, int64_t n, cudaStream_t st) {
+          const int64_t d = ids0 ? 0 : off;
+          for (int l = top - 1; l >= 0; --l) {
+            const LevelData &Lr = ctx->lv[l];
+            const int cap = std::max(1, Lr.max_children * Kb[l + 1]);
+            run(ctx, KK_RESTRICTED, st, n, [&] {
+              launch_omp_restricted(ctx->restricted_variant, Yl[l] + d * Lr.M, Lr.M, Lr.A[ph0], Lr.inv_norm[ph0],
+                                    ids0 ? ids0 + off : nullptr, n, Lr.child_off, Lr.child_idx, cap,
+                                    lv_om[l + 1] + d * ldo[l + 1], ldo[l + 1], lv_ke[l + 1] + d,
+                                    prm->K_patch[l] ? prm->K_patch[l] + d : nullptr, prm->K[l], Kb[l],
+                                    lv_om[l] + d * ldo[l], lv_al[l] + d * ldo[l], ldo[l], lv_ke[l] + d, W.stats_dev,
+                                    Lr.G[ph0], Lr.T, 0, 0, false, st);
+            });
+          }
+        };
+        if (!fused_range(0, wave, s)) return fail(ctx, CSP_ERR_CUDA, "fused full-dictionary kernel could not be launched");
+        CSP_CUDA(ctx, cudaEventRecord(ctx->ev_fork, s));
+        if (!fused_range(wave, B - wave, s))
+          return fail(ctx, CSP_ERR_CUDA, "fused full-dictionary kernel could not be launched");
+        CSP_CUDA(ctx, cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+        restrict_range(0, wave, ctx->aux);
+        restrict_range(wave, B - wave, s);
+        CSP_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->aux));
+        CSP_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
+        CSP_CUDA(ctx, cudaGetLastError());
+        return CSP_OK;
       }
       run(ctx, KK_FUSED, s, B, [&] {
         fused_done = launch_omp_fused_tc(Yl[top], L.M, Aph, Iph, Bph, Gph, nph, phased ? ps.phase_start : nullptr, L.Mp,
@@ -586,6 +648,9 @@ void csp_destroy(csp_ctx *ctx) {
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
+  if (ctx->aux) cudaStreamDestroy(ctx->aux);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   delete ctx;
 }
 
@@ -890,6 +955,7 @@ csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, 
   key.restricted_variant = ctx->restricted_variant;
   key.top_form = ctx->top_form;
   key.wait_test = ctx->wait_test;
+  key.pipeline = ctx->pipeline;
   if (ctx->gexec && std::memcmp(&key, &ctx->gkey, sizeof(key)) == 0) {
     CSP_CUDA(ctx, cudaGraphLaunch(ctx->gexec, s));
     return CSP_OK;
@@ -929,6 +995,12 @@ csp_status csp_set_graph_mode(csp_ctx *ctx, int on) {
     cudaGraphExecDestroy(ctx->gexec);
     ctx->gexec = nullptr;
   }
+  return CSP_OK;
+}
+
+csp_status csp_set_pipeline(csp_ctx *ctx, int on) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  ctx->pipeline = on != 0;
   return CSP_OK;
 }
 

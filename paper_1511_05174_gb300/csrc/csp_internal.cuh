@@ -148,10 +148,15 @@ struct csp_ctx {
     float *coef;
     int8_t *keff;
     uint64_t version;
-    int restricted_variant, top_form, wait_test;
+    int restricted_variant, top_form, wait_test, pipeline;
   } gkey{};
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t gstream = nullptr;
+  // second stream of the pipelined cross-scale solve (restricted level of the
+  // first chunk beside the fused full-dictionary level of the second)
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool pipeline = true;        // csp_set_pipeline
   std::vector<csp::ProfRec> pending;
   std::vector<cudaEvent_t> ev_pool;
   // All device allocations (for the memory budget and destroy).
@@ -247,6 +252,8 @@ bool launch_proxy_bf16(const __nv_bfloat16 *Rbf, int64_t rows_total, int Mp, con
 // matrix: the Gram columns from the rows).  Returns false when the shape is
 // not supported or a tensor map fails.
 bool fused_top_supported(int M, int T, int Kb);
+// Patches one wave of the fused kernel holds (every SM busy), for this shape.
+int64_t fused_wave_patches(int T, int Kb);
 bool launch_omp_fused_tc(const float *Y, int M, const float *const *A, const float *const *inv_norm,
                          const __nv_bfloat16 *const *Abf, const float *const *gram, int nph,
                          const int64_t *phase_start, int Mp, int T,

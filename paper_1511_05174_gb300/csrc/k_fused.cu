@@ -537,6 +537,11 @@ bool fused_top_supported(int M, int T, int Kb) {
          fz_layout(T, Kb, 1).total <= 227 * 1024;
 }
 
+int64_t fused_wave_patches(int T, int Kb) {
+  const int ngrp = fz_layout(T, Kb, 2).total <= 227 * 1024 ? 2 : 1;
+  return (int64_t)device_sms() * ngrp * FZ_M;
+}
+
 bool launch_omp_fused_tc(const float *Y, int M, const float *const *A, const float *const *inv_norm,
                          const __nv_bfloat16 *const *Abf, const float *const *gram, int nph, const int64_t *phase_start, int Mp, int T,
                          const int32_t *ids, int64_t n, const int8_t *Kp, int Kuni, int Kb, int32_t *omega,
@@ -568,18 +573,24 @@ bool launch_omp_fused_tc(const float *Y, int M, const float *const *A, const flo
   int idx_bits = 1;
   while ((1 << idx_bits) < T) ++idx_bits;
   const int sm = fz_layout(T, Kb, ngrp).total;
-  if (ngrp == 2) {
-    if (cudaFuncSetAttribute(omp_fused_tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
-      return false;
-    omp_fused_tc_kernel<2><<<(unsigned)ctas, 2 * FZ_GT, sm, s>>>(args, Y, M, T, idx_bits, ids, Kp, Kuni, Kb,
-                                                                      omega, alpha, ldo, k_eff, stats, err);
-  } else {
-    if (cudaFuncSetAttribute(omp_fused_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess)
-      return false;
-    omp_fused_tc_kernel<1><<<(unsigned)ctas, FZ_GT, sm, s>>>(args, Y, M, T, idx_bits, ids, Kp, Kuni, Kb,
-                                                                  omega, alpha, ldo, k_eff, stats, err);
-  }
-  return true;
+  auto kern = ngrp == 2 ? omp_fused_tc_kernel<2> : omp_fused_tc_kernel<1>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) != cudaSuccess) return false;
+  // highest stream priority: when a restricted level runs beside it (pipelined
+  // solve), whole SMs go to this kernel's CTAs first
+  int lo = 0, hi = 0;
+  cudaDeviceGetStreamPriorityRange(&lo, &hi);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3(ngrp * FZ_GT);
+  cfg.dynamicSmemBytes = (size_t)sm;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = hi;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args, Y, M, T, idx_bits, ids, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats,
+                            err) == cudaSuccess;
 }
 
 }  // namespace csp

@@ -524,8 +524,9 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
     float gpre[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
+      if (u >= ucnt) break;  // ucnt is uniform over the warp
       const int c = s + u * G;
-      gpre[u] = (u < ucnt && act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
+      gpre[u] = (act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
     }
     const float aa = act ? __ldg(gram + (int64_t)q * T + q) : 0.f;  // ||a_q||^2
     const bool f32 = act && !(fl & 2);
@@ -766,8 +767,9 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
     float gpre[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
+      if (u >= ucnt) break;  // ucnt is uniform over the warp
       const int c = s + u * G;
-      gpre[u] = (u < ucnt && act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
+      gpre[u] = (act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
     }
     const float aa = act ? __ldg(gram + (int64_t)q * T + q) : 0.f;
     const bool f32 = act && !(fl & 2);
@@ -808,8 +810,9 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
       // column k of Q_C and the correlations
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
+        if (u >= ucnt) break;
         const int c = s + u * G;
-        if (u < ucnt && c < nc) {
+        if (c < nc) {
           float v = gpre[u];
           for (int j = 0; j < k; ++j) v = fmaf(-S.W[j], Qc[j * ldg + c], v);
           v *= il;
