@@ -905,6 +905,267 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
 }
 
 // ---------------------------------------------------------------------------
+// The Gram-Schmidt form for Kb <= 8 with Q_C stored by candidate: row c of
+// Q_C (its 8 entries <a_c, u_j>, zero beyond the chosen count) is 32 bytes,
+// its two 16-byte halves swapped when bit 2 of c is set so that the 8 lanes of
+// a group read 8 rows without bank conflicts.  A candidate's column update is
+// then two 16-byte loads and 8 FMAs against w held in registers; the new row
+// of L (w = Q_C[q]) is two broadcast loads; the argmax keeps the winner's slot
+// and finds its lane by ballot; ||w||^2 and <w, z> are formed by every lane
+// (z in registers), with no group reduction.  Same iteration, outputs and
+// FP64 / explicit-residual paths as omp_restricted_qr_kernel.
+// Per-group shared memory: GrpSmem | p0[cap] | c[cap] | Q_C[cap][8] (its first
+// 64 words hold the parents' child ranges while the candidates are listed).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int qr8_q_floats(int cap) {
+  return 8 * cap > 2 * CSP_MAX_K ? 8 * cap : 2 * CSP_MAX_K;
+}
+__host__ __device__ __forceinline__ int qr8_group_bytes(int Kb, int cap) {
+  const int bytes = grp_smem_bytes(Kb, cap) + 2 * up16(4 * cap) + 4 * qr8_q_floats(cap);
+  return (bytes + 127) / 128 * 128 + 16;  // groups start on different bank offsets
+}
+
+template <int G, int NCH>
+__global__ void __launch_bounds__(WV_WARPS * 32, 5)
+omp_restricted_qr8_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
+                          const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
+                          const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx,
+                          int cap, const int32_t *__restrict__ omega_up, int ldo_up,
+                          const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
+                          int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
+                          int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
+  constexpr int NG = 32 / G;
+  constexpr unsigned GMASK = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+  extern __shared__ __align__(16) char smem_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
+  const int64_t wbase = ((int64_t)blockIdx.x * WV_WARPS + wib) * NG;
+  if (wbase >= n) return;  // whole warp
+  const int64_t wi = wbase + g;
+  const bool valid = wi < n;
+  char *gbase = smem_raw + (size_t)(wib * NG + g) * qr8_group_bytes(Kb, cap);
+  const GrpSmem S = carve(gbase, Kb, cap);
+  char *q_ = gbase + grp_smem_bytes(Kb, cap);
+  float *p0 = reinterpret_cast<float *>(q_); q_ += up16(4 * cap);
+  float *cc = reinterpret_cast<float *>(q_); q_ += up16(4 * cap);
+  float *Q = reinterpret_cast<float *>(q_);  // Q_C rows, [cap][8], halves swapped for bit 2 of c
+  float4 *Q4 = reinterpret_cast<float4 *>(Q);
+  int *pstart = reinterpret_cast<int *>(Q);  // parents' child ranges, before Q_C is used
+  int *pbeg = pstart + CSP_MAX_K;
+  const int nv = M >> 2;
+  const int64_t b = valid ? (ids ? __ldg(ids + wi) : wi) : 0;
+  int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
+  Kpb = Kpb < Kb ? Kpb : Kb;
+  const int kup = valid ? keff_up[b] : 0;
+  const float *yrow = Y + b * M;
+  float4 yv[NCH];
+  load_chunks<G, NCH>(yv, yrow, nv, s, valid);
+  const int nc = gram_setup<G, NCH>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
+                                   inv_norm, stats, M, A, yv, p0);
+  const int ucnt = min(8, __reduce_max_sync(kFull, (nc + G - 1) / G));
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int c = s; c < nc; c += G) {
+    cc[c] = p0[c];
+    Q4[2 * c] = zero4;
+    Q4[2 * c + 1] = zero4;
+  }
+  __syncwarp();
+  const float ysq = gsum<G>(dotc<NCH>(yv, yv));
+  float rsq = ysq;
+  bool act = valid && Kpb > 0;
+  uint8_t fl = 0;  // bit 1: FP64 from here on
+  int k = 0, scored = 0;
+  float zr[8];  // z_j of the chosen (zero beyond k)
+#pragma unroll
+  for (int j = 0; j < 8; ++j) zr[j] = 0.f;
+  const int Kw = __reduce_max_sync(kFull, Kpb);
+  for (int it = 0; it < Kw; ++it) {
+    act = act && k < Kpb && !(rsq <= kEpsR32 * ysq);
+    if (!__any_sync(kFull, act)) break;
+    if (act) ++scored;
+    // proxy from the current correlations; the lane's best key and its slot
+    unsigned long long best = 0ull;
+    int bslot = 0;
+    if (act)
+      for (int c = s; c < nc; c += G) {
+        const float inv = S.invn[c];
+        if (!(inv > 0.f)) continue;
+        const unsigned long long key = pack_key(fabsf(cc[c]) * inv, S.cs[c]);
+        if (key > best) {
+          best = key;
+          bslot = c;
+        }
+      }
+    const unsigned long long gbest = gmax<G>(best);
+    if (act && !gbest) act = false;  // candidate set exhausted
+    const int q = act ? key_idx(gbest) : 0;
+    // the winner's lane (keys are distinct): its slot qs, no longer eligible
+    const bool mine = act && best == gbest;
+    const unsigned gm = (__ballot_sync(kFull, mine) >> (g * G)) & GMASK;
+    const int qs = __shfl_sync(kFull, bslot, g * G + (gm ? __ffs(gm) - 1 : 0));
+    if (mine) S.invn[bslot] = -1.f;
+    // G[q][C] (row q: G is symmetric) and G[q][q], issued before their use
+    float gpre[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (u >= ucnt) break;  // ucnt is uniform over the warp
+      const int c = s + u * G;
+      gpre[u] = (act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
+    }
+    const float aa = act ? __ldg(gram + (int64_t)q * T + q) : 0.f;
+    const bool f32 = act && !(fl & 2);
+    // new row of L: w = Q_C[q] (broadcast loads of row qs)
+    float w[8];
+    {
+      const int sq = (qs >> 2) & 1;
+      const float4 h0 = f32 ? Q4[2 * qs + sq] : zero4, h1 = f32 ? Q4[2 * qs + 1 - sq] : zero4;
+      w[0] = h0.x; w[1] = h0.y; w[2] = h0.z; w[3] = h0.w;
+      w[4] = h1.x; w[5] = h1.y; w[6] = h1.z; w[7] = h1.w;
+    }
+    float ww = 0.f, wz = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      ww = fmaf(w[j], w[j], ww);
+      wz = fmaf(w[j], zr[j], wz);
+    }
+    const float d = aa - ww;
+    const bool ok32 = f32 && aa > 0.f && d >= kTauPivot * aa;
+    if (f32 && !ok32) {
+      fl |= 2;
+      if (s == 0) atomicAdd((unsigned long long *)&stats[0], 1ull);
+    }
+    if (ok32) {
+      const float lkk = sqrtf(d);
+      const float il = 1.f / lkk;
+      const float zk = (p0[qs] - wz) * il;
+      if (s == 0) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (j < k) S.L[tri(k) + j] = w[j];
+        S.L[tri(k) + k] = lkk;
+        S.Linv[k] = il;
+        S.z[k] = zk;
+        S.om[k] = q;
+        S.colp[k] = A + (int64_t)q * M;
+      }
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (j == k) zr[j] = zk;
+      // column k of Q_C and the correlations
+      const int kofs = (k & 3);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (u >= ucnt) break;
+        const int c = s + u * G;
+        if (c < nc) {
+          const int sc = (c >> 2) & 1;
+          const float4 qa = Q4[2 * c + sc], qb = Q4[2 * c + 1 - sc];
+          float v = gpre[u];
+          v = fmaf(-w[0], qa.x, v);
+          v = fmaf(-w[1], qa.y, v);
+          v = fmaf(-w[2], qa.z, v);
+          v = fmaf(-w[3], qa.w, v);
+          v = fmaf(-w[4], qb.x, v);
+          v = fmaf(-w[5], qb.y, v);
+          v = fmaf(-w[6], qb.z, v);
+          v = fmaf(-w[7], qb.w, v);
+          v *= il;
+          Q[8 * c + ((((k >> 2) ^ sc)) << 2) + kofs] = v;
+          cc[c] = fmaf(-zk, v, cc[c]);
+        }
+      }
+      for (int c = s + 8 * G; c < nc; c += G) {
+        const int sc = (c >> 2) & 1;
+        const float4 qa = Q4[2 * c + sc], qb = Q4[2 * c + 1 - sc];
+        float v = __ldg(gram + (int64_t)q * T + S.cs[c]);
+        v = fmaf(-w[0], qa.x, v);
+        v = fmaf(-w[1], qa.y, v);
+        v = fmaf(-w[2], qa.z, v);
+        v = fmaf(-w[3], qa.w, v);
+        v = fmaf(-w[4], qb.x, v);
+        v = fmaf(-w[5], qb.y, v);
+        v = fmaf(-w[6], qb.z, v);
+        v = fmaf(-w[7], qb.w, v);
+        v *= il;
+        Q[8 * c + ((((k >> 2) ^ sc)) << 2) + kofs] = v;
+        cc[c] = fmaf(-zk, v, cc[c]);
+      }
+      rsq = rsq - zk * zk;
+    }
+    // FP64 from scratch for the patches whose FP32 pivot failed (now or before)
+    const bool go64 = act && !ok32;
+    if (go64 && s == 0) S.misc[0] = fp64_projection(M, yrow, S, k, A + (int64_t)q * M) ? 1 : 0;
+    __syncwarp();
+    const bool app64 = go64 && S.misc[0] != 0;
+    // q depends on the chosen columns: alpha of the chosen ones from the FP32 factor
+    const bool restore = f32 && !ok32 && !app64;
+    if (__any_sync(kFull, restore))
+      grp_backsub<G>(restore, s, k - 1, __reduce_max_sync(kFull, restore ? k - 1 : 0), S);
+    if (app64 && s == 0) {
+      S.om[k] = q;
+      S.colp[k] = A + (int64_t)q * M;
+    }
+    __syncwarp();
+    if (app64)  // correlations c = p0 - G[C][Omega] alpha from the Gram rows of the chosen atoms
+      for (int c = s; c < nc; c += G) {
+        float v = p0[c];
+        for (int j = 0; j <= k; ++j) v = fmaf(-S.W[j], __ldg(gram + (int64_t)S.om[j] * T + S.cs[c]), v);
+        cc[c] = v;
+      }
+    // ||r||^2 formed explicitly in FP64 mode and near the FP32 floor
+    const bool exact = app64 || (ok32 && rsq <= 1e-5f * ysq);
+    if (__any_sync(kFull, exact)) {
+      const bool need = exact && !app64;  // FP32: alpha over rows 0..k first
+      grp_backsub<G>(need, s, k, __reduce_max_sync(kFull, need ? k : 0), S);
+      float4 rv[NCH];
+#pragma unroll
+      for (int t = 0; t < NCH; ++t) rv[t] = yv[t];
+      const int kx = __reduce_max_sync(kFull, exact ? k + 1 : 0);
+      for (int j0 = 0; j0 < kx; j0 += RB) {
+        float4 cr[RB][NCH];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+          const bool o = exact && j0 + u <= k;
+          load_chunks<G, NCH>(cr[u], o ? S.colp[j0 + u] : yrow, nv, s, o);
+        }
+#pragma unroll
+        for (int u = 0; u < RB; ++u)
+          if (exact && j0 + u <= k) {
+            const float aj = S.W[j0 + u];
+#pragma unroll
+            for (int t = 0; t < NCH; ++t) {
+              rv[t].x = fmaf(-aj, cr[u][t].x, rv[t].x);
+              rv[t].y = fmaf(-aj, cr[u][t].y, rv[t].y);
+              rv[t].z = fmaf(-aj, cr[u][t].z, rv[t].z);
+              rv[t].w = fmaf(-aj, cr[u][t].w, rv[t].w);
+            }
+          }
+      }
+      const float r2 = gsum<G>(dotc<NCH>(rv, rv));
+      if (exact) rsq = r2;
+    }
+    if (act) {
+      if (ok32 || app64) ++k;
+      else act = false;
+    }
+    __syncwarp();
+  }
+  // alpha = L^{-T} z for the patches that stayed in FP32 (FP64 ones hold it in S.W)
+  const bool fin = valid && !(fl & 2) && k > 0;
+  grp_backsub<G>(fin, s, k - 1, __reduce_max_sync(kFull, fin ? k - 1 : 0), S);
+  if (valid) {
+    if (s == 0) {
+      if (k < Kpb) atomicAdd((unsigned long long *)&stats[1], 1ull);
+      atomicAdd((unsigned long long *)&stats[2], (unsigned long long)nc * (unsigned long long)scored);
+      k_eff[b] = (int8_t)k;
+    }
+    for (int j = s; j < ldo; j += G) {
+      omega[b * ldo + j] = (j < k) ? S.om[j] : -1;
+      alpha[b * ldo + j] = (j < k) ? S.W[j] : 0.f;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Restricted OMP in Gram-Schmidt form with the candidate state in registers.
 // Same iteration as omp_restricted_qr_kernel, but lane s of a group owns the
 // candidates c = s + G u (u < CPL) and keeps, per candidate, its atom index,
@@ -1192,10 +1453,14 @@ void launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const
                                 int8_t *k_eff, int64_t *stats, const float *gram, int T, cudaStream_t s) {
   if (n == 0) return;
   const int per_cta = WV_WARPS * (32 / gram_group(M, width));
-  const size_t sm = (size_t)(qr ? qr_group_bytes(Kb, cap) : gram_group_bytes(Kb, cap)) * per_cta;
+  const bool qr8 = qr && Kb <= 8;  // Q_C stored by candidate
+  const size_t sm =
+      (size_t)(qr8 ? qr8_group_bytes(Kb, cap) : (qr ? qr_group_bytes(Kb, cap) : gram_group_bytes(Kb, cap))) *
+      per_cta;
   dispatch_gram(M, width, [&](auto gc, auto nc) {
     constexpr int GG = decltype(gc)::value, NCH = decltype(nc)::value;
-    auto kern = qr ? omp_restricted_qr_kernel<GG, NCH> : omp_restricted_gram_kernel<GG, NCH>;
+    auto kern = qr8 ? omp_restricted_qr8_kernel<GG, NCH>
+                    : (qr ? omp_restricted_qr_kernel<GG, NCH> : omp_restricted_gram_kernel<GG, NCH>);
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kern<<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up,
                                                       ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats,
