@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the restricted-solver variant (0-9) instead of autotuning (profiling runs)")
     ap.add_argument("--serving-jobs", type=int, default=24, help="jobs per offered rate")
+    ap.add_argument("--no-pipeline", action="store_true",
+                    help="one stream throughout (csp_set_pipeline off; profiling runs)")
+    ap.add_argument("--top-form", type=int, default=None, choices=[1, 2],
+                    help="pin the full-dictionary form (1 per-iteration, 2 fused) with --variant (profiling runs)")
     return ap.parse_args()
 
 
@@ -400,6 +404,10 @@ def main():
 
     if args.variant is not None:
         ctx.set_kernel_variant(args.variant)
+    if args.top_form is not None:
+        ctx.set_top_level_form(args.top_form)
+    if args.no_pipeline:
+        ctx.set_pipeline(False)
     for _ in range(max(args.warmup, 3)):
         step("cross_scale")
         step("plain")
@@ -409,7 +417,7 @@ def main():
         tune = ctx.autotune(Y, "cross_scale", args.precision, K=K, Kmax=Kmax)
         step("cross_scale")
     else:
-        tune = {"restricted_variant": args.variant, "ms": [], "top_level_form": 0, "ms_top": []}
+        tune = {"restricted_variant": args.variant, "ms": [], "top_level_form": args.top_form or 0, "ms_top": []}
     torch.cuda.synchronize()
 
     def timed(mode, sampler=None):
@@ -442,7 +450,7 @@ def main():
         torch.cuda.synchronize()
         prof = ctx.profile_read(reset=True)
         ctx.profile(False)
-        ctx.set_pipeline(True)
+        ctx.set_pipeline(not args.no_pipeline)
         return max_over_ranks(ms, world, dev), prof, st, clocks
 
     ctx.set_graph_mode(True)
@@ -533,9 +541,10 @@ def main():
             "data": "synthetic (seeded; Gaussian unit-norm atoms, K-sparse N(0,1) codes)",
             "config": {**workload_config(w, args), "form": "cross_scale", "precision": args.precision,
                        "cuda_graph": "solve replayed from a CUDA graph (csp_set_graph_mode)",
-                       "pipeline": "fused coarse level of the second chunk beside the restricted level of the "
-                                   "first on a second stream (csp_set_pipeline); per-kernel times from a "
-                                   "one-stream pass",
+                       "pipeline": ("off (one stream)" if args.no_pipeline else
+                                    "fused coarse level of the second chunk beside the restricted level of the "
+                                    "first on a second stream (csp_set_pipeline); per-kernel times from a "
+                                    "one-stream pass"),
                        "restricted_variant": tune["restricted_variant"],
                        "autotune_ms": [round(t, 4) for t in tune["ms"]],
                        "top_level_form": tune.get("top_level_form"),
