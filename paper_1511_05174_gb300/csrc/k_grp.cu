@@ -408,7 +408,8 @@ __device__ int list_candidates(bool valid, int s, int64_t b, int kup, const int3
 }
 
 // The candidate list (list_candidates), the candidates' inverse norms, and
-// p0 = A_C^T y (RB rows per load wave).  Returns |C|.  Warp-collective.
+// p0 = A_C^T y (8 rows per load wave where registers allow, else 4).  Returns
+// |C|.  Warp-collective.
 template <int G, int NCH>
 __device__ int gram_setup(bool valid, int s, int64_t b, int kup, const int32_t *__restrict__ omega_up, int ldo_up,
                           const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx, int cap,
@@ -417,31 +418,24 @@ __device__ int gram_setup(bool valid, int s, int64_t b, int kup, const int32_t *
   const int nv = M >> 2;
   const int nc = list_candidates<G>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
                                     stats);
-  for (int c0 = s; c0 < nc; c0 += 4 * G) {
-    float iv[4];
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = c0 + u * G;
-      iv[u] = c < nc ? __ldg(inv_norm + S.cs[c]) : -1.f;
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int c = c0 + u * G;
-      if (c < nc) S.invn[c] = iv[u];
-    }
-  }
   __syncwarp();  // the parents' child ranges (aliasing Gc) are no longer read
-  // p0 = A_C^T y, RB rows per load wave
+  // p0 = A_C^T y and the candidates' inverse norms, RBP rows per load wave (lane s
+  // fetches the norm of row s of the wave)
+  constexpr int RBP = NCH > 2 ? 2 : (G >= 8 ? 8 : 4);  // RBP <= G
   const int ncw = __reduce_max_sync(kFull, nc);
-  for (int c0 = 0; c0 < ncw; c0 += RB) {
-    float4 a[RB][NCH];
+  for (int c0 = 0; c0 < ncw; c0 += RBP) {
+    const int ci = c0 + s;
+    const bool oi = s < RBP && ci < nc;
+    const float iv = oi ? __ldg(inv_norm + S.cs[ci]) : -1.f;
+    float4 a[RBP][NCH];
 #pragma unroll
-    for (int u = 0; u < RB; ++u) {
+    for (int u = 0; u < RBP; ++u) {
       const bool o = c0 + u < nc;
       load_chunks<G, NCH>(a[u], A + (int64_t)(o ? S.cs[c0 + u] : 0) * M, nv, s, o);
     }
+    if (oi) S.invn[ci] = iv;
 #pragma unroll
-    for (int u = 0; u < RB; ++u) {
+    for (int u = 0; u < RBP; ++u) {
       const float d = gsum<G>(dotc<NCH>(a[u], yv));
       if (s == 0 && c0 + u < nc) p0[c0 + u] = d;
     }
@@ -1120,15 +1114,16 @@ omp_restricted_qr8_kernel(const float *__restrict__ Y, int M, const float *__res
 #pragma unroll
       for (int t = 0; t < NCH; ++t) rv[t] = yv[t];
       const int kx = __reduce_max_sync(kFull, exact ? k + 1 : 0);
-      for (int j0 = 0; j0 < kx; j0 += RB) {
-        float4 cr[RB][NCH];
+      constexpr int RBX = NCH > 2 ? 1 : RB;  // rows per load wave of this rare path
+      for (int j0 = 0; j0 < kx; j0 += RBX) {
+        float4 cr[RBX][NCH];
 #pragma unroll
-        for (int u = 0; u < RB; ++u) {
+        for (int u = 0; u < RBX; ++u) {
           const bool o = exact && j0 + u <= k;
           load_chunks<G, NCH>(cr[u], o ? S.colp[j0 + u] : yrow, nv, s, o);
         }
 #pragma unroll
-        for (int u = 0; u < RB; ++u)
+        for (int u = 0; u < RBX; ++u)
           if (exact && j0 + u <= k) {
             const float aj = S.W[j0 + u];
 #pragma unroll
