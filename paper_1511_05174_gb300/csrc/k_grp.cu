@@ -989,13 +989,29 @@ omp_restricted_qr8_kernel(const float *__restrict__ Y, int M, const float *__res
           bslot = c;
         }
       }
-    const unsigned long long gbest = gmax<G>(best);
-    if (act && !gbest) act = false;  // candidate set exhausted
-    const int q = act ? key_idx(gbest) : 0;
-    // the winner's lane (keys are distinct): its slot qs, no longer eligible
-    const bool mine = act && best == gbest;
-    const unsigned gm = (__ballot_sync(kFull, mine) >> (g * G)) & GMASK;
-    const int qs = __shfl_sync(kFull, bslot, g * G + (gm ? __ffs(gm) - 1 : 0));
+    // group argmax of the packed keys: the largest score bits first, then (only
+    // where two lanes tie on the score) the largest complemented index
+    const unsigned bs = (unsigned)(best >> 32);
+    unsigned ms = bs;
+#pragma unroll
+    for (int o = G / 2; o; o >>= 1) ms = max(ms, __shfl_xor_sync(kFull, ms, o));
+    const bool top = best != 0ull && bs == ms;
+    unsigned tb = (__ballot_sync(kFull, top) >> (g * G)) & GMASK;
+    if (__any_sync(kFull, __popc(tb) > 1)) {
+      const unsigned lw = top ? (unsigned)best : 0u;
+      unsigned ml = lw;
+#pragma unroll
+      for (int o = G / 2; o; o >>= 1) ml = max(ml, __shfl_xor_sync(kFull, ml, o));
+      tb = (__ballot_sync(kFull, top && lw == ml) >> (g * G)) & GMASK;
+    }
+    if (act && !tb) act = false;  // candidate set exhausted
+    const int wl = g * G + (tb ? __ffs(tb) - 1 : 0);
+    // every lane takes part in both shuffles (inactive groups read their lane 0)
+    const unsigned qlw = __shfl_sync(kFull, (unsigned)best, wl);
+    const int qs = __shfl_sync(kFull, bslot, wl);
+    const int q = act ? (int)(0xffffffffu - qlw) : 0;
+    // the winner's slot qs is no longer eligible
+    const bool mine = act && lane == wl;
     if (mine) S.invn[bslot] = -1.f;
     // G[q][C] (row q: G is symmetric) and G[q][q], issued before their use
     float gpre[8];
@@ -1028,8 +1044,8 @@ omp_restricted_qr8_kernel(const float *__restrict__ Y, int M, const float *__res
       if (s == 0) atomicAdd((unsigned long long *)&stats[0], 1ull);
     }
     if (ok32) {
-      const float lkk = sqrtf(d);
-      const float il = 1.f / lkk;
+      const float il = rsqrtf(d);  // d >= kTauPivot aa > 0
+      const float lkk = d * il;
       const float zk = (p0[qs] - wz) * il;
       if (s == 0) {
 #pragma unroll
