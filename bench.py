@@ -207,7 +207,10 @@ def algorithmic(kind, w, prof_launches, stats, B, steps, M):
         return 2.0 * dim * T * B * iters / launches, "TFLOP/s", ("tensor" if kind == "proxy_bf16" else "alu")
     if kind == "restricted":
         per_step = max(prof_launches.get("restricted", (1,))[0] / steps, 1.0)
-        return 2.0 * M * stats.get("restricted_scores", 0) / per_step, "TFLOP/s", "alu"
+        flops = 2.0 * M * stats.get("restricted_scores", 0)
+        if stats.get("synthesized"):  # x_hat_p = D0 alpha_p written by the finest level: 2 N0 K per patch
+            flops += 2.0 * w.dicts[0].shape[1] * float(np.sum(w.K_levels[0]))
+        return flops / per_step, "TFLOP/s", "alu"
     if kind == "omp_update":
         # y, r read and r written, 4 B each, per patch
         return 3.0 * 4 * M * B, "GB/s", "hbm"
@@ -393,10 +396,8 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step(mode):
-        ctx.extract(meas_d, Y)
-        ctx.solve(Y, mode, args.precision, K=K if mode == "cross_scale" else K[:1], Kmax=Kmax,
-                  out=(sup, coef, keff))
-        ctx.aggregate(sup, coef, keff, img)
+        # the whole path in one library call: extraction, solve, synthesis + overlap-add
+        ctx.reconstruct(meas_d, img, mode, args.precision, K=K if mode == "cross_scale" else K[:1], Kmax=Kmax)
 
     def barrier():
         if world > 1:
@@ -540,7 +541,10 @@ def main():
             "dtype": "f32" if args.precision == "fp32" else "bf16+f32",
             "data": "synthetic (seeded; Gaussian unit-norm atoms, K-sparse N(0,1) codes)",
             "config": {**workload_config(w, args), "form": "cross_scale", "precision": args.precision,
-                       "cuda_graph": "solve replayed from a CUDA graph (csp_set_graph_mode)",
+                       "cuda_graph": "extraction, solve and aggregation of a step replayed from one CUDA graph "
+                                     "(csp_reconstruct in graph mode)",
+                       "synthesis": ("written by the finest restricted level" if cs_stats.get("synthesized")
+                                     else "separate pass"),
                        "pipeline": ("off (one stream)" if args.no_pipeline else
                                     "fused coarse level of the second chunk beside the restricted level of the "
                                     "first on a second stream (csp_set_pipeline); per-kernel times from a "

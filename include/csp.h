@@ -125,6 +125,8 @@ typedef struct csp_solve_stats {
                                   (finer-scale) steps, summed over patches and iterations   */
     int64_t timeouts;          /* 1 when a bounded device wait expired (results invalid;
                                   csp_solve_stats_get then returns CSP_ERR_TIMEOUT)         */
+    int64_t synthesized;       /* 1 when the last call was csp_reconstruct and its finest
+                                  restricted level wrote x_hat_p itself (no synthesis pass) */
 } csp_solve_stats;
 
 /* Create a context on CUDA `device`.  mem_budget_bytes caps the device memory
@@ -209,11 +211,26 @@ csp_status csp_aggregate_noalloc(csp_ctx *ctx, const int32_t *support, const flo
                                  const int8_t *k_eff, int64_t B, int Kmax, float *image_out,
                                  void *stream);
 
+/* The whole path on DEVICE buffers (Sec. IV; Algorithms 1 and 2): the patch
+ * vectors of the geometry's patch grid from the measurement image `meas`
+ * (layout as in csp_extract_patches), the solve with `params` (as csp_solve;
+ * per-patch budgets are not accepted, K_patch must be NULL), and the synthesis
+ * x_hat_p = D0 alpha_p with the overlap-add into image_out (float32
+ * [planes][H][W], as csp_aggregate).  The patch vectors, supports and
+ * coefficients live in buffers of the context.  Same image as the three calls;
+ * with the Gram-Schmidt restricted solver (variants 5-7, Kb <= 8) the finest
+ * level writes x_hat_p itself, which saves the synthesis pass.  In graph mode
+ * (csp_set_graph_mode) identical calls are replayed from one CUDA graph.
+ * Errors: those of the three calls; CSP_ERR_UNSUPPORTED for dense sensing (no
+ * measurement image).  Stream-ordered; returns before the work completes. */
+csp_status csp_reconstruct(csp_ctx *ctx, const csp_solve_params *params, const float *meas, float *image_out,
+                           void *stream);
+
 /* End-to-end reconstruction from HOST buffers: copies the measurement image
- * (layout as in csp_extract_patches) to the device, extracts, solves,
- * aggregates and copies the image (float32 [planes][H][W]) back into
- * image_host.  Per-patch budgets are not accepted here (K_patch must be NULL).
- * Returns when the image is in host memory. */
+ * (layout as in csp_extract_patches) to the device, runs csp_reconstruct and
+ * copies the image (float32 [planes][H][W]) back into image_host.  Per-patch
+ * budgets are not accepted here (K_patch must be NULL).  Returns when the
+ * image is in host memory. */
 csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *params,
                                 const float *meas_host, float *image_host, void *stream);
 

@@ -39,7 +39,7 @@ EXPORTS = ("csp_create", "csp_destroy", "csp_last_error", "csp_set_geometry", "c
            "csp_server_create", "csp_server_destroy", "csp_server_last_error", "csp_server_add_model",
            "csp_submit", "csp_poll", "csp_wait", "csp_job_info_get", "csp_job_release",
            "csp_server_pause", "csp_set_aggregate_path", "csp_set_top_level_form",
-           "csp_set_wait_test", "csp_set_graph_mode", "csp_set_pipeline")
+           "csp_set_wait_test", "csp_set_graph_mode", "csp_set_pipeline", "csp_reconstruct")
 
 
 class csp_geometry(ctypes.Structure):
@@ -60,7 +60,8 @@ class csp_solve_params(ctypes.Structure):
 class csp_solve_stats(ctypes.Structure):
     _fields_ = [("patches", ctypes.c_int64), ("fp64_fallbacks", ctypes.c_int64),
                 ("early_stops", ctypes.c_int64), ("overflow", ctypes.c_int64),
-                ("restricted_scores", ctypes.c_int64), ("timeouts", ctypes.c_int64)]
+                ("restricted_scores", ctypes.c_int64), ("timeouts", ctypes.c_int64),
+                ("synthesized", ctypes.c_int64)]
 
 
 class csp_kernel_time(ctypes.Structure):
@@ -128,6 +129,7 @@ def load_library(path: str = LIB_PATH):
         "csp_aggregate": (i, [vp, vp, vp, vp, ctypes.c_int64, i, vp, vp]),
         "csp_aggregate_noalloc": (i, [vp, vp, vp, vp, ctypes.c_int64, i, vp, vp]),
         "csp_reconstruct_host": (i, [vp, ctypes.POINTER(csp_solve_params), vp, vp, vp]),
+        "csp_reconstruct": (i, [vp, ctypes.POINTER(csp_solve_params), vp, vp, vp]),
         "csp_autotune": (i, [vp, ctypes.POINTER(csp_solve_params), vp, ctypes.c_int64, vp, vp, vp, vp,
                              ctypes.POINTER(csp_tune_result)]),
         "csp_set_kernel_variant": (i, [vp, i]),
@@ -229,6 +231,10 @@ def csp_aggregate_noalloc(ctx, sup_ptr: int, coef_ptr: int, keff_ptr: int, B: in
                           stream: int) -> None:
     """csp_aggregate without any device allocation (fixed 16 MiB scratch; B * N0 <= 4 Mi)."""
     check(load_library().csp_aggregate_noalloc(ctx, sup_ptr, coef_ptr, keff_ptr, B, Kmax, img_ptr, stream), ctx)
+
+
+def csp_reconstruct(ctx, params: csp_solve_params, meas_ptr: int, image_ptr: int, stream: int) -> None:
+    check(load_library().csp_reconstruct(ctx, ctypes.byref(params), meas_ptr, image_ptr, stream), ctx)
 
 
 def csp_reconstruct_host(ctx, params: csp_solve_params, meas_ptr: int, img_ptr: int, stream: int) -> None:

@@ -195,7 +195,8 @@ class Context:
     def stats(self):
         st = b.csp_solve_stats_get(self._ctx)
         return {"patches": st.patches, "fp64_fallbacks": st.fp64_fallbacks, "early_stops": st.early_stops,
-                "overflow": st.overflow, "restricted_scores": st.restricted_scores}
+                "overflow": st.overflow, "restricted_scores": st.restricted_scores,
+                "synthesized": bool(st.synthesized)}
 
     def profile(self, on: bool = True) -> None:
         b.csp_profile_enable(self._ctx, on)
@@ -210,6 +211,20 @@ class Context:
             img = torch.empty((self._planes, H, W), dtype=torch.float32, device=self.device)
         b.csp_aggregate(self._ctx, sup.data_ptr(), coef.data_ptr(), keff.data_ptr(), sup.shape[0], sup.shape[1],
                         img.data_ptr(), _stream_ptr(stream, self.device))
+        return img
+
+    def reconstruct(self, meas: torch.Tensor, img: Optional[torch.Tensor] = None, mode: str = "cross_scale",
+                    precision: str = "fp32", K: Sequence[int] = (), Kmax: Optional[int] = None,
+                    stream=None) -> torch.Tensor:
+        """Extraction, solve and aggregation on device tensors in one call
+        (csp_reconstruct); returns the image [planes, H, W]."""
+        meas = meas.contiguous()
+        assert meas.dtype == torch.float32 and meas.is_cuda
+        H, W = self.geometry[0], self.geometry[1]
+        if img is None:
+            img = torch.empty((self._planes, H, W), dtype=torch.float32, device=self.device)
+        p = self.params(mode, precision, K, None, Kmax)
+        b.csp_reconstruct(self._ctx, p, meas.data_ptr(), img.data_ptr(), _stream_ptr(stream, self.device))
         return img
 
     def reconstruct_host(self, meas: np.ndarray, img: np.ndarray, mode: str = "cross_scale",

@@ -94,6 +94,7 @@ csp_status ws_get(csp_ctx *ctx, Workspace &W, int slot, size_t bytes, void **out
     b.bytes = 0;
     CSP_TRY(dev_alloc(ctx, &b.p, bytes));
     b.bytes = bytes;
+    ++ctx->state_version;  // recorded graphs hold the old buffer
   }
   *out = b.p;
   return CSP_OK;
@@ -322,11 +323,15 @@ csp_status ensure_aux(csp_ctx *ctx) {
 }
 
 // Solve the patch set `ps` with the context's dictionaries (prepared), using
-// workspace W.  Arguments validated by the caller.
+// workspace W.  With Xh (B x N0 floats), the finest restricted level may also
+// synthesize x_hat_b = D0 alpha_b into Xh (*synthesized tells whether it did).  Arguments validated by the caller.
 csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_solve_params *prm, const float *Y,
-                      int32_t *support_out, float *coef_out, int8_t *k_eff_out, cudaStream_t s) {
+                      int32_t *support_out, float *coef_out, int8_t *k_eff_out, cudaStream_t s, float *Xh = nullptr,
+                      bool *synthesized = nullptr) {
   const int64_t B = ps.B;
   const int nl = prm->mode == CSP_MODE_PLAIN ? 1 : ctx->geom.n_levels;
+  if (synthesized) *synthesized = false;
+  bool synth_all = Xh != nullptr && nl > 1;  // the finest level is restricted only in cross-scale mode
   int Kb[CSP_MAX_LEVELS];
   for (int l = 0; l < nl; ++l) Kb[l] = prm->K_patch[l] ? prm->Kmax : prm->K[l];
   const bool bf16 = prm->precision == CSP_PREC_BF16;
@@ -418,12 +423,14 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
             const LevelData &Lr = ctx->lv[l];
             const int cap = std::max(1, Lr.max_children * Kb[l + 1]);
             run(ctx, KK_RESTRICTED, st, n, [&] {
-              launch_omp_restricted(ctx->restricted_variant, Yl[l] + d * Lr.M, Lr.M, Lr.A[ph0], Lr.inv_norm[ph0],
-                                    ids0 ? ids0 + off : nullptr, n, Lr.child_off, Lr.child_idx, cap,
-                                    lv_om[l + 1] + d * ldo[l + 1], ldo[l + 1], lv_ke[l + 1] + d,
-                                    prm->K_patch[l] ? prm->K_patch[l] + d : nullptr, prm->K[l], Kb[l],
-                                    lv_om[l] + d * ldo[l], lv_al[l] + d * ldo[l], ldo[l], lv_ke[l] + d, W.stats_dev,
-                                    Lr.G[ph0], Lr.T, 0, 0, false, st);
+              const bool sy = launch_omp_restricted(
+                  ctx->restricted_variant, Yl[l] + d * Lr.M, Lr.M, Lr.A[ph0], Lr.inv_norm[ph0],
+                  ids0 ? ids0 + off : nullptr, n, Lr.child_off, Lr.child_idx, cap, lv_om[l + 1] + d * ldo[l + 1],
+                  ldo[l + 1], lv_ke[l + 1] + d, prm->K_patch[l] ? prm->K_patch[l] + d : nullptr, prm->K[l], Kb[l],
+                  lv_om[l] + d * ldo[l], lv_al[l] + d * ldo[l], ldo[l], lv_ke[l] + d, W.stats_dev, Lr.G[ph0], Lr.T, 0,
+                  0, false, st, l == 0 ? ctx->lv[0].D : nullptr, ctx->lv[0].N,
+                  (l == 0 && Xh) ? Xh + d * ctx->lv[0].N : nullptr);
+              if (l == 0) synth_all = synth_all && sy;
             });
           }
         };
@@ -437,6 +444,7 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
         CSP_CUDA(ctx, cudaEventRecord(ctx->ev_join, ctx->aux));
         CSP_CUDA(ctx, cudaStreamWaitEvent(s, ctx->ev_join, 0));
         CSP_CUDA(ctx, cudaGetLastError());
+        if (synthesized) *synthesized = synth_all;
         return CSP_OK;
       }
       run(ctx, KK_FUSED, s, B, [&] {
@@ -540,14 +548,17 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
     }
     for (int ph = 0; ph < nph; ++ph)
       run(ctx, KK_RESTRICTED, s, n_of(ph), [&] {
-        launch_omp_restricted(ctx->restricted_variant, Yl[l], L.M, L.per_patch ? Ac : L.A[ph],
-                              L.per_patch ? invc : L.inv_norm[ph], ids_of(ph), n_of(ph),
-                              L.child_off, L.child_idx, cap, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1], prm->K_patch[l],
-                              prm->K[l], Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], W.stats_dev, L.G[ph], L.T,
-                              L.per_patch ? (int64_t)cap * L.M : 0, L.per_patch ? (int64_t)cap : 0, L.per_patch, s);
+        const bool sy = launch_omp_restricted(
+            ctx->restricted_variant, Yl[l], L.M, L.per_patch ? Ac : L.A[ph], L.per_patch ? invc : L.inv_norm[ph],
+            ids_of(ph), n_of(ph), L.child_off, L.child_idx, cap, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1],
+            prm->K_patch[l], prm->K[l], Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], W.stats_dev, L.G[ph], L.T,
+            L.per_patch ? (int64_t)cap * L.M : 0, L.per_patch ? (int64_t)cap : 0, L.per_patch, s,
+            l == 0 ? ctx->lv[0].D : nullptr, ctx->lv[0].N, l == 0 ? Xh : nullptr);
+        if (l == 0) synth_all = synth_all && sy;
       });
   }
   CSP_CUDA(ctx, cudaGetLastError());
+  if (synthesized) *synthesized = synth_all;
   return CSP_OK;
 }
 
@@ -611,6 +622,168 @@ GeomDev make_geom_dev(const csp_geometry &g, int H, int W) {
 
 }  // namespace csp
 
+namespace csp {
+
+// Checks of csp_solve's arguments (buffers checked by the caller).
+csp_status check_solve_args(csp_ctx *ctx, const csp_solve_params *prm, int64_t B) {
+  if (!prm) return fail(ctx, CSP_ERR_INVALID, "params is NULL");
+  if (B < 0) return fail(ctx, CSP_ERR_INVALID, "B < 0");
+  if (prm->mode != CSP_MODE_PLAIN && prm->mode != CSP_MODE_CROSS_SCALE) return fail(ctx, CSP_ERR_INVALID, "unknown mode");
+  if (prm->precision != CSP_PREC_FP32 && prm->precision != CSP_PREC_BF16)
+    return fail(ctx, CSP_ERR_INVALID, "unknown precision");
+  if (prm->Kmax < 1 || prm->Kmax > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "Kmax must be in 1..CSP_MAX_K");
+  if (!ctx->has_geom || !ctx->has_sensing) return fail(ctx, CSP_ERR_NOT_READY, "geometry and sensing must be set");
+  const int nl = prm->mode == CSP_MODE_PLAIN ? 1 : ctx->geom.n_levels;
+  for (int l = 0; l < nl; ++l)
+    if (!prm->K_patch[l] && (prm->K[l] < 1 || prm->K[l] > CSP_MAX_K))
+      return fail(ctx, CSP_ERR_INVALID, "K[l] must be in 1..CSP_MAX_K");
+  if (!prm->K_patch[0] && prm->K[0] > prm->Kmax) return fail(ctx, CSP_ERR_INVALID, "K[0] exceeds Kmax");
+  for (int l = 0; l + 1 < nl; ++l)
+    if (!ctx->lv[l].links) return fail(ctx, CSP_ERR_NOT_READY, "scale links of level " + std::to_string(l) + " not loaded");
+  if ((ctx->sense_kind == CSP_SENSE_BAYER_RGGB || ctx->sense_kind == CSP_SENSE_CODED_EXPOSURE) && B != ctx->B)
+    return fail(ctx, CSP_ERR_INVALID, "Bayer / coded-exposure sensing solves the geometry's patch grid: B must equal the patch count");
+  return CSP_OK;
+}
+
+// Prepared dictionaries and the patch set of a solve of B patches.
+csp_status solve_setup(csp_ctx *ctx, const csp_solve_params *prm, int64_t B, cudaStream_t s, PatchSet &ps) {
+  const int nl = prm->mode == CSP_MODE_PLAIN ? 1 : ctx->geom.n_levels;
+  CSP_TRY(prepare(ctx, s));
+  CSP_TRY(check_solve_shape(ctx, prm));
+  CSP_TRY(prepare_own_patches(ctx, nl - 1, s));  // the full-dictionary level of this solve
+  ps.B = B;
+  if (ctx->sense_kind == CSP_SENSE_BAYER_RGGB) {
+    ps.phase_ids = ctx->phase_ids;
+    for (int p = 0; p <= kMaxPhases; ++p) ps.phase_start[p] = ctx->phase_start[p];
+  }
+  ps.pcodes = ctx->pcodes;
+  for (int l = 0; l < CSP_MAX_LEVELS; ++l) { ps.A_pp[l] = ctx->pp_A[l]; ps.inv_pp[l] = ctx->pp_inv[l]; }
+  ctx->last_B = B;
+  ctx->last_stream = s;
+  return CSP_OK;
+}
+
+// Graph mode: replay the graph in `slot` when `key` matches the call it was
+// recorded from; otherwise run `body` on s (which allocates whatever it
+// needs and gives the result), then record the same launches on a private
+// stream into the slot for the next calls.
+template <typename F>
+csp_status run_graphed(csp_ctx *ctx, csp_ctx::GraphSlot &slot, const csp_ctx::GraphKey &key, cudaStream_t s,
+                       F &&body) {
+  if (slot.exec && std::memcmp(&key, &slot.key, sizeof(key)) == 0) {
+    CSP_CUDA(ctx, cudaGraphLaunch(slot.exec, s));
+    return CSP_OK;
+  }
+  if (slot.exec) {
+    cudaGraphExecDestroy(slot.exec);
+    slot.exec = nullptr;
+  }
+  CSP_TRY(body(s));
+  if (!ctx->gstream) CSP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
+  CSP_CUDA(ctx, cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed));
+  const csp_status st = body(ctx->gstream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(ctx->gstream, &graph);
+  if (st != CSP_OK || ec != cudaSuccess || !graph) {
+    if (graph) cudaGraphDestroy(graph);
+    cudaGetLastError();
+    return st != CSP_OK ? st : fail(ctx, CSP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&slot.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    slot.exec = nullptr;
+    cudaGetLastError();
+    return fail(ctx, CSP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
+  }
+  std::memcpy(&slot.key, &key, sizeof(key));
+  return CSP_OK;
+}
+
+// The context state and call arguments a recorded graph depends on.
+csp_ctx::GraphKey graph_key(const csp_ctx *ctx, const csp_solve_params *prm) {
+  csp_ctx::GraphKey key;
+  std::memset(&key, 0, sizeof(key));  // padding included: compared byte by byte
+  key.prm.mode = prm->mode;
+  key.prm.precision = prm->precision;
+  for (int l = 0; l < CSP_MAX_LEVELS; ++l) {
+    key.prm.K[l] = prm->K[l];
+    key.prm.K_patch[l] = prm->K_patch[l];
+  }
+  key.prm.Kmax = prm->Kmax;
+  key.version = ctx->state_version;
+  key.restricted_variant = ctx->restricted_variant;
+  key.top_form = ctx->top_form;
+  key.wait_test = ctx->wait_test;
+  key.pipeline = ctx->pipeline;
+  key.aggregate_path = ctx->aggregate_path;
+  return key;
+}
+
+// Extraction, solve and aggregation of the context's patch grid from the
+// device measurement image `meas` into the device image `img`, with the
+// context's own buffers for the patches and codes.
+csp_status reconstruct_core(csp_ctx *ctx, const csp_solve_params *prm, const float *meas, float *img, cudaStream_t s) {
+  const int64_t B = ctx->B;
+  const int N0 = ctx->lv[0].N;
+  float *Y = (float *)ctx->h_Y.p;
+  int32_t *sup = (int32_t *)ctx->h_sup.p;
+  float *coef = (float *)ctx->h_coef.p;
+  int8_t *keff = (int8_t *)ctx->h_keff.p;
+  CSP_TRY(csp_extract_patches(ctx, meas, Y, nullptr, s));
+  PatchSet ps;
+  CSP_TRY(solve_setup(ctx, prm, B, s, ps));
+  bool tiled = aggregate_use_tiled(ctx->aggregate_path, ctx->gd, N0, prm->Kmax);
+  float *Xh = nullptr;
+  if (!tiled) CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_XH, (size_t)B * N0, &Xh));
+  bool synthesized = false;
+  CSP_TRY(solve_core(ctx, ps, ctx->wsp, prm, Y, sup, coef, keff, s, Xh, &synthesized));
+  ctx->recon_synth = synthesized;
+  if (tiled)
+    run(ctx, KK_AGGREGATE, s, B, [&] {
+      tiled = launch_aggregate_tiled(ctx->gd, ctx->lv[0].D, N0, sup, coef, keff, prm->Kmax, ctx->cover_y,
+                                     ctx->cover_x, img, s);
+    });
+  if (!tiled) {
+    if (!Xh) CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_XH, (size_t)B * N0, &Xh));
+    run(ctx, KK_AGGREGATE, s, B, [&] {
+      if (!synthesized) launch_synth(ctx->gd, ctx->lv[0].D, N0, sup, coef, keff, prm->Kmax, Xh, s);
+      launch_gather(ctx->gd, Xh, N0, ctx->cover_y, ctx->cover_x, img, s);
+    });
+  }
+  CSP_CUDA(ctx, cudaGetLastError());
+  return CSP_OK;
+}
+
+// Device buffers of the context's own patch grid for a reconstruction.
+csp_status reconstruct_buffers(csp_ctx *ctx, const csp_solve_params *prm) {
+  auto grow = [&](Buf &b, size_t bytes) -> csp_status {
+    if (b.bytes >= bytes) return CSP_OK;
+    dev_free(ctx, b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    CSP_TRY(dev_alloc(ctx, &b.p, bytes));
+    b.bytes = bytes;
+    ++ctx->state_version;  // recorded graphs hold the old buffers
+    return CSP_OK;
+  };
+  const int64_t B = ctx->B;
+  CSP_TRY(grow(ctx->h_Y, (size_t)B * ctx->M * 4 + 16));
+  CSP_TRY(grow(ctx->h_sup, (size_t)B * prm->Kmax * 4 + 16));
+  CSP_TRY(grow(ctx->h_coef, (size_t)B * prm->Kmax * 4 + 16));
+  CSP_TRY(grow(ctx->h_keff, (size_t)B + 16));
+  return CSP_OK;
+}
+
+}  // namespace csp
+
+using csp::check_solve_args;
+using csp::solve_setup;
+using csp::run_graphed;
+using csp::graph_key;
+using csp::reconstruct_core;
+using csp::reconstruct_buffers;
+
 extern "C" {
 
 csp_status csp_create(csp_ctx **out, int device, size_t mem_budget_bytes) {
@@ -646,7 +819,8 @@ void csp_destroy(csp_ctx *ctx) {
   for (auto &a : ctx->allocs) cudaFree(a.first);
   for (auto &r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
-  if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+  if (ctx->g_solve.exec) cudaGraphExecDestroy(ctx->g_solve.exec);
+  if (ctx->g_recon.exec) cudaGraphExecDestroy(ctx->g_recon.exec);
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -900,101 +1074,65 @@ csp_status csp_extract_patches(csp_ctx *ctx, const float *meas, float *Y_out, in
 csp_status csp_solve(csp_ctx *ctx, const csp_solve_params *prm, const float *Y, int64_t B,
                      int32_t *support_out, float *coef_out, int8_t *k_eff_out, void *stream) {
   if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
-  if (!prm) return fail(ctx, CSP_ERR_INVALID, "params is NULL");
-  if (B < 0) return fail(ctx, CSP_ERR_INVALID, "B < 0");
+  CSP_TRY(check_solve_args(ctx, prm, B));
   if (!valid_ptr_or_empty(Y, B) || !valid_ptr_or_empty(support_out, B) || !valid_ptr_or_empty(coef_out, B) ||
       !valid_ptr_or_empty(k_eff_out, B))
     return fail(ctx, CSP_ERR_INVALID, "NULL buffer");
-  if (prm->mode != CSP_MODE_PLAIN && prm->mode != CSP_MODE_CROSS_SCALE) return fail(ctx, CSP_ERR_INVALID, "unknown mode");
-  if (prm->precision != CSP_PREC_FP32 && prm->precision != CSP_PREC_BF16)
-    return fail(ctx, CSP_ERR_INVALID, "unknown precision");
-  if (prm->Kmax < 1 || prm->Kmax > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "Kmax must be in 1..CSP_MAX_K");
-  if (!ctx->has_geom || !ctx->has_sensing) return fail(ctx, CSP_ERR_NOT_READY, "geometry and sensing must be set");
-  const int nl = prm->mode == CSP_MODE_PLAIN ? 1 : ctx->geom.n_levels;
-  for (int l = 0; l < nl; ++l)
-    if (!prm->K_patch[l] && (prm->K[l] < 1 || prm->K[l] > CSP_MAX_K))
-      return fail(ctx, CSP_ERR_INVALID, "K[l] must be in 1..CSP_MAX_K");
-  if (!prm->K_patch[0] && prm->K[0] > prm->Kmax) return fail(ctx, CSP_ERR_INVALID, "K[0] exceeds Kmax");
-  for (int l = 0; l + 1 < nl; ++l)
-    if (!ctx->lv[l].links) return fail(ctx, CSP_ERR_NOT_READY, "scale links of level " + std::to_string(l) + " not loaded");
-  if ((ctx->sense_kind == CSP_SENSE_BAYER_RGGB || ctx->sense_kind == CSP_SENSE_CODED_EXPOSURE) && B != ctx->B)
-    return fail(ctx, CSP_ERR_INVALID, "Bayer / coded-exposure sensing solves the geometry's patch grid: B must equal the patch count");
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard dg(ctx->device);
-  CSP_TRY(prepare(ctx, s));
-  CSP_TRY(check_solve_shape(ctx, prm));
-  CSP_TRY(prepare_own_patches(ctx, nl - 1, s));  // the full-dictionary level of this solve
   PatchSet ps;
-  ps.B = B;
-  if (ctx->sense_kind == CSP_SENSE_BAYER_RGGB) {
-    ps.phase_ids = ctx->phase_ids;
-    for (int p = 0; p <= kMaxPhases; ++p) ps.phase_start[p] = ctx->phase_start[p];
-  }
-  ps.pcodes = ctx->pcodes;
-  for (int l = 0; l < CSP_MAX_LEVELS; ++l) { ps.A_pp[l] = ctx->pp_A[l]; ps.inv_pp[l] = ctx->pp_inv[l]; }
-  ctx->last_B = B;
-  ctx->last_stream = s;
-  if (!ctx->graph_mode || ctx->prof)
-    return solve_core(ctx, ps, ctx->wsp, prm, Y, support_out, coef_out, k_eff_out, s);
-  // graph mode: replay the captured launches of an identical call
-  csp_ctx::GraphKey key;
-  std::memset(&key, 0, sizeof(key));  // padding included: compared byte by byte
-  key.prm.mode = prm->mode;
-  key.prm.precision = prm->precision;
-  for (int l = 0; l < CSP_MAX_LEVELS; ++l) {
-    key.prm.K[l] = prm->K[l];
-    key.prm.K_patch[l] = prm->K_patch[l];
-  }
-  key.prm.Kmax = prm->Kmax;
+  CSP_TRY(solve_setup(ctx, prm, B, s, ps));
+  ctx->last_synth = false;
+  auto body = [&](cudaStream_t st) {
+    return solve_core(ctx, ps, ctx->wsp, prm, Y, support_out, coef_out, k_eff_out, st);
+  };
+  if (!ctx->graph_mode || ctx->prof) return body(s);
+  csp_ctx::GraphKey key = graph_key(ctx, prm);
   key.Y = Y;
   key.B = B;
   key.sup = support_out;
   key.coef = coef_out;
   key.keff = k_eff_out;
-  key.version = ctx->state_version;
-  key.restricted_variant = ctx->restricted_variant;
-  key.top_form = ctx->top_form;
-  key.wait_test = ctx->wait_test;
-  key.pipeline = ctx->pipeline;
-  if (ctx->gexec && std::memcmp(&key, &ctx->gkey, sizeof(key)) == 0) {
-    CSP_CUDA(ctx, cudaGraphLaunch(ctx->gexec, s));
-    return CSP_OK;
+  return run_graphed(ctx, ctx->g_solve, key, s, body);
+}
+
+csp_status csp_reconstruct(csp_ctx *ctx, const csp_solve_params *prm, const float *meas, float *image_out,
+                           void *stream) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (!prm || !meas || !image_out) return fail(ctx, CSP_ERR_INVALID, "NULL argument");
+  for (int l = 0; l < CSP_MAX_LEVELS; ++l)
+    if (prm->K_patch[l]) return fail(ctx, CSP_ERR_INVALID, "per-patch budgets are not accepted by csp_reconstruct");
+  if (ctx->sense_kind == CSP_SENSE_DENSE)
+    return fail(ctx, CSP_ERR_UNSUPPORTED, "dense sensing has no measurement image to extract patches from");
+  CSP_TRY(check_solve_args(ctx, prm, ctx->B));
+  if (!ctx->lv[0].D) return fail(ctx, CSP_ERR_NOT_READY, "fine dictionary not loaded");
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceGuard dg(ctx->device);
+  CSP_TRY(reconstruct_buffers(ctx, prm));
+  auto body = [&](cudaStream_t st) { return reconstruct_core(ctx, prm, meas, image_out, st); };
+  csp_status st = CSP_OK;
+  if (!ctx->graph_mode || ctx->prof) {
+    st = body(s);
+  } else {
+    csp_ctx::GraphKey key = graph_key(ctx, prm);
+    key.Y = meas;
+    key.B = ctx->B;
+    key.coef = image_out;
+    st = run_graphed(ctx, ctx->g_recon, key, s, body);
   }
-  // a new call: run it (this allocates whatever it needs and gives the result),
-  // then capture the same launches on a private stream for the next calls
-  if (ctx->gexec) {
-    cudaGraphExecDestroy(ctx->gexec);
-    ctx->gexec = nullptr;
-  }
-  CSP_TRY(solve_core(ctx, ps, ctx->wsp, prm, Y, support_out, coef_out, k_eff_out, s));
-  if (!ctx->gstream) CSP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->gstream, cudaStreamNonBlocking));
-  CSP_CUDA(ctx, cudaStreamBeginCapture(ctx->gstream, cudaStreamCaptureModeRelaxed));
-  const csp_status st = solve_core(ctx, ps, ctx->wsp, prm, Y, support_out, coef_out, k_eff_out, ctx->gstream);
-  cudaGraph_t graph = nullptr;
-  const cudaError_t ec = cudaStreamEndCapture(ctx->gstream, &graph);
-  if (st != CSP_OK || ec != cudaSuccess || !graph) {
-    if (graph) cudaGraphDestroy(graph);
-    cudaGetLastError();
-    return st != CSP_OK ? st : fail(ctx, CSP_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ec));
-  }
-  const cudaError_t ei = cudaGraphInstantiate(&ctx->gexec, graph, 0);
-  cudaGraphDestroy(graph);
-  if (ei != cudaSuccess) {
-    ctx->gexec = nullptr;
-    cudaGetLastError();
-    return fail(ctx, CSP_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ei));
-  }
-  std::memcpy(&ctx->gkey, &key, sizeof(key));
-  return CSP_OK;
+  ctx->last_synth = st == CSP_OK && ctx->recon_synth;
+  return st;
 }
 
 csp_status csp_set_graph_mode(csp_ctx *ctx, int on) {
   if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
   ctx->graph_mode = on != 0;
-  if (!ctx->graph_mode && ctx->gexec) {
-    cudaGraphExecDestroy(ctx->gexec);
-    ctx->gexec = nullptr;
-  }
+  if (!ctx->graph_mode)
+    for (csp_ctx::GraphSlot *g : {&ctx->g_solve, &ctx->g_recon})
+      if (g->exec) {
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+      }
   return CSP_OK;
 }
 
@@ -1016,6 +1154,7 @@ csp_status csp_solve_stats_get(csp_ctx *ctx, csp_solve_stats *out) {
   out->overflow = h[3];
   out->restricted_scores = h[2];
   out->timeouts = h[4] != 0 ? 1 : 0;
+  out->synthesized = ctx->last_synth ? 1 : 0;
   if (h[4] != 0)
     return fail(ctx, CSP_ERR_TIMEOUT, "a bounded device wait expired (code " + std::to_string(h[4]) + ")");
   return CSP_OK;
@@ -1064,7 +1203,6 @@ csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *prm, const
     default: meas_n = (size_t)g.H * g.W;
   }
   const size_t img_n = (size_t)planes * g.H * g.W;
-  const int64_t B = ctx->B;
   cudaStream_t s = (cudaStream_t)stream;
   DeviceGuard dg(ctx->device);
   auto grow = [&](Buf &b, size_t bytes) -> csp_status {
@@ -1074,20 +1212,13 @@ csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *prm, const
     b.bytes = 0;
     CSP_TRY(dev_alloc(ctx, &b.p, bytes));
     b.bytes = bytes;
+    ++ctx->state_version;  // recorded graphs hold the old buffers
     return CSP_OK;
   };
   CSP_TRY(grow(ctx->h_meas, meas_n * 4));
-  CSP_TRY(grow(ctx->h_Y, (size_t)B * ctx->M * 4 + 16));
-  CSP_TRY(grow(ctx->h_sup, (size_t)B * prm->Kmax * 4 + 16));
-  CSP_TRY(grow(ctx->h_coef, (size_t)B * prm->Kmax * 4 + 16));
-  CSP_TRY(grow(ctx->h_keff, (size_t)B + 16));
   CSP_TRY(grow(ctx->h_img, img_n * 4));
   CSP_CUDA(ctx, cudaMemcpyAsync(ctx->h_meas.p, meas_host, meas_n * 4, cudaMemcpyHostToDevice, s));
-  CSP_TRY(csp_extract_patches(ctx, (const float *)ctx->h_meas.p, (float *)ctx->h_Y.p, nullptr, stream));
-  CSP_TRY(csp_solve(ctx, prm, (const float *)ctx->h_Y.p, B, (int32_t *)ctx->h_sup.p, (float *)ctx->h_coef.p,
-                    (int8_t *)ctx->h_keff.p, stream));
-  CSP_TRY(csp_aggregate(ctx, (const int32_t *)ctx->h_sup.p, (const float *)ctx->h_coef.p,
-                        (const int8_t *)ctx->h_keff.p, B, prm->Kmax, (float *)ctx->h_img.p, stream));
+  CSP_TRY(csp_reconstruct(ctx, prm, (const float *)ctx->h_meas.p, (float *)ctx->h_img.p, stream));
   CSP_CUDA(ctx, cudaMemcpyAsync(image_host, ctx->h_img.p, img_n * 4, cudaMemcpyDeviceToHost, s));
   CSP_CUDA(ctx, cudaStreamSynchronize(s));
   return CSP_OK;

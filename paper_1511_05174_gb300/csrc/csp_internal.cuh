@@ -136,27 +136,34 @@ struct csp_ctx {
   int aggregate_path = 0;      // 0 automatic, 1 two-pass (synthesis scratch), 2 fused shared-memory tiles
   int top_form = 0;            // full-dictionary level: 0 automatic, 1 per-iteration kernels, 2 fused kernel
   bool wait_test = false;      // test hook: the tensor-core proxy loads no atom tiles (its waits expire)
-  // CUDA graph of the last solve (csp_set_graph_mode): replayed while the call
-  // and the context's buffers are unchanged (state_version counts the changes)
+  // CUDA graphs of the last csp_solve and csp_reconstruct (csp_set_graph_mode):
+  // replayed while the call and the context's buffers are unchanged
+  // (state_version counts the changes)
   bool graph_mode = false;
   uint64_t state_version = 0;
   struct GraphKey {
     csp_solve_params prm;
-    const float *Y;
+    const float *Y;  // csp_solve: the patch vectors; csp_reconstruct: the measurement image
     int64_t B;
     int32_t *sup;
-    float *coef;
+    float *coef;     // csp_reconstruct: the output image
     int8_t *keff;
     uint64_t version;
-    int restricted_variant, top_form, wait_test, pipeline;
-  } gkey{};
-  cudaGraphExec_t gexec = nullptr;
+    int restricted_variant, top_form, wait_test, pipeline, aggregate_path;
+  };
+  struct GraphSlot {
+    GraphKey key{};
+    cudaGraphExec_t exec = nullptr;
+  };
+  GraphSlot g_solve, g_recon;  // csp_solve and csp_reconstruct
   cudaStream_t gstream = nullptr;
   // second stream of the pipelined cross-scale solve (restricted level of the
   // first chunk beside the fused full-dictionary level of the second)
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool pipeline = true;        // csp_set_pipeline
+  bool recon_synth = false;    // the recorded / last csp_reconstruct fused the synthesis
+  bool last_synth = false;     // reported by csp_solve_stats_get
   std::vector<csp::ProfRec> pending;
   std::vector<cudaEvent_t> ev_pool;
   // All device allocations (for the memory budget and destroy).
@@ -204,6 +211,12 @@ bool launch_aggregate_tiled(const GeomDev &g, const float *D0, int N0, const int
 void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *support,
                       const float *coef, const int8_t *k_eff, int Kmax, const int32_t *cover_y,
                       const int32_t *cover_x, float *Xh, float *img, cudaStream_t s);
+// The two passes of launch_aggregate: x_hat_p = D0 alpha_p into Xh [B][N0], then
+// the overlap-add of Xh into the image.
+void launch_synth(const GeomDev &g, const float *D0, int N0, const int32_t *support, const float *coef,
+                  const int8_t *k_eff, int Kmax, float *Xh, cudaStream_t s);
+void launch_gather(const GeomDev &g, const float *Xh, int N0, const int32_t *cover_y, const int32_t *cover_x,
+                   float *img, cudaStream_t s);
 
 // OMP state of a full-dictionary level, in device memory.
 struct OmpState {
@@ -268,11 +281,12 @@ void launch_omp_update_wave(const float *Y, int M, const float *A, const float *
                             cudaStream_t s);
 // width 0, 1, 2: 4, 8, 16 lanes per patch for M <= 64 (doubled per doubling of M, at most 32);
 // qr: Gram-Schmidt form (correlations updated per appended atom) instead of p0 - G alpha
-void launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const float *A, const float *inv_norm,
-                                const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx, int cap,
-                                const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int8_t *Kp,
-                                int Kuni, int Kb, int32_t *omega, float *alpha, int ldo, int8_t *k_eff,
-                                int64_t *stats, const float *gram, int T, cudaStream_t s);
+bool launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const float *A, const float *inv_norm,
+                                const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx,
+                                int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
+                                const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
+                                int8_t *k_eff, int64_t *stats, const float *gram, int T, const float *D0, int N0,
+                                float *Xh, cudaStream_t s);
 // Gram-Schmidt form with the candidates' state in registers (G = 8 or 16 lanes
 // per patch); false (nothing launched) when M > 8 G, Kb > 8 or cap > 8 G.
 bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, const float *inv_norm,
@@ -284,13 +298,13 @@ bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, con
 void launch_gram(const float *A, int T, int M, float *Gm, cudaStream_t s);
 // variant 0: rows from L2 every pass (cooperative groups); 1: rows staged in shared memory;
 // 2: proxy from the Gram matrix + exact re-score of the best three (falls back to 0 without gram).
-void launch_omp_restricted(int variant, const float *Y, int M, const float *A, const float *inv_norm,
+bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, const float *inv_norm,
                            const int32_t *ids, int64_t n, const int32_t *child_off,
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
                            const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, bool cpos,
-                           cudaStream_t s);
+                           cudaStream_t s, const float *D0 = nullptr, int N0 = 0, float *Xh = nullptr);
 // Per-pixel coded exposure, restricted level l: rows of the effective
 // dictionary for the candidates f(Omega_up) of every patch only, in candidate
 // order ([B][cap][M], row c of patch b = a_{cs_c} for that patch's codes) and

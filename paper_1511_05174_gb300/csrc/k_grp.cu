@@ -927,7 +927,8 @@ omp_restricted_qr8_kernel(const float *__restrict__ Y, int M, const float *__res
                           int cap, const int32_t *__restrict__ omega_up, int ldo_up,
                           const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                           int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
-                          int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
+                          int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T,
+                          const float *__restrict__ D0, int N0, float *__restrict__ Xh) {
   constexpr int NG = 32 / G;
   constexpr unsigned GMASK = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
   extern __shared__ __align__(16) char smem_raw[];
@@ -1172,6 +1173,41 @@ omp_restricted_qr8_kernel(const float *__restrict__ Y, int M, const float *__res
     for (int j = s; j < ldo; j += G) {
       omega[b * ldo + j] = (j < k) ? S.om[j] : -1;
       alpha[b * ldo + j] = (j < k) ? S.W[j] : 0.f;
+    }
+  }
+  // synthesis x_hat_b = D0_Omega alpha (Sec. IV) into Xh[b] when asked for: the
+  // chosen rows in support order, one FMA each from zero, as synth_kernel does
+  if (Xh && valid) {
+    constexpr int XS = 6;  // float4 chunks per lane per pass
+    const int n4 = N0 >> 2;
+    float4 *xb = reinterpret_cast<float4 *>(Xh + b * N0);
+    for (int c0 = s; c0 < n4; c0 += G * XS) {
+      float4 acc[XS];
+#pragma unroll
+      for (int t = 0; t < XS; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+      for (int j = 0; j < k; ++j) {
+        const float aj = S.W[j];
+        const float4 *dr = reinterpret_cast<const float4 *>(D0 + (int64_t)S.om[j] * N0);
+        float4 d[XS];
+#pragma unroll
+        for (int t = 0; t < XS; ++t) {
+          const int ch = c0 + G * t;
+          d[t] = ch < n4 ? __ldg(dr + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < XS; ++t) {
+          acc[t].x = fmaf(aj, d[t].x, acc[t].x);
+          acc[t].y = fmaf(aj, d[t].y, acc[t].y);
+          acc[t].z = fmaf(aj, d[t].z, acc[t].z);
+          acc[t].w = fmaf(aj, d[t].w, acc[t].w);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < XS; ++t) {
+        const int ch = c0 + G * t;
+        if (ch < n4) xb[ch] = acc[t];
+      }
     }
   }
 }
@@ -1457,26 +1493,36 @@ void launch_omp_update_wave(const float *Y, int M, const float *A, const float *
   });
 }
 
-void launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const float *A, const float *inv_norm,
+bool launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const float *A, const float *inv_norm,
                                 const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx,
                                 int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
                                 const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
-                                int8_t *k_eff, int64_t *stats, const float *gram, int T, cudaStream_t s) {
-  if (n == 0) return;
-  const int per_cta = WV_WARPS * (32 / gram_group(M, width));
+                                int8_t *k_eff, int64_t *stats, const float *gram, int T, const float *D0, int N0,
+                                float *Xh, cudaStream_t s) {
   const bool qr8 = qr && Kb <= 8;  // Q_C stored by candidate
+  const bool synth = qr8 && Xh && D0 && N0 > 0 && N0 % 4 == 0;
+  if (n == 0) return synth;
+  const int per_cta = WV_WARPS * (32 / gram_group(M, width));
   const size_t sm =
       (size_t)(qr8 ? qr8_group_bytes(Kb, cap) : (qr ? qr_group_bytes(Kb, cap) : gram_group_bytes(Kb, cap))) *
       per_cta;
   dispatch_gram(M, width, [&](auto gc, auto nc) {
     constexpr int GG = decltype(gc)::value, NCH = decltype(nc)::value;
-    auto kern = qr8 ? omp_restricted_qr8_kernel<GG, NCH>
-                    : (qr ? omp_restricted_qr_kernel<GG, NCH> : omp_restricted_gram_kernel<GG, NCH>);
+    if (qr8) {
+      auto kern = omp_restricted_qr8_kernel<GG, NCH>;
+      if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      kern<<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap,
+                                                        omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo,
+                                                        k_eff, stats, gram, T, D0, N0, synth ? Xh : nullptr);
+      return;
+    }
+    auto kern = qr ? omp_restricted_qr_kernel<GG, NCH> : omp_restricted_gram_kernel<GG, NCH>;
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kern<<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up,
                                                       ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats,
                                                       gram, T);
   });
+  return synth;
 }
 
 bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, const float *inv_norm,

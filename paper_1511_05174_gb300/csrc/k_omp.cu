@@ -743,27 +743,26 @@ bool dispatch_group_wide(int M, F &&f) {
   return true;
 }
 
-void launch_omp_restricted(int variant, const float *Y, int M, const float *A, const float *inv_norm,
+bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, const float *inv_norm,
                            const int32_t *ids, int64_t n, const int32_t *child_off,
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
                            const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, bool cpos,
-                           cudaStream_t s) {
-  if (n == 0) return;
+                           cudaStream_t s, const float *D0, int N0, float *Xh) {
+  if (n == 0) return false;
   if (variant >= 2 && (!gram || a_pstride || cpos)) variant = 0;  // the Gram variants need the level's shared Gram matrix
   if (variant >= 8) {  // 8, 9: Gram-Schmidt form with register-resident candidates, 8 / 16 lanes per patch
     if (launch_omp_restricted_reg(variant == 8 ? 8 : 16, Y, M, A, inv_norm, ids, n, child_off, child_idx, cap,
                                   omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T,
                                   s))
-      return;
+      return false;
     variant = 6;  // shape outside the register form: the shared-memory Gram-Schmidt form
   }
-  if (variant >= 2) {  // 2-4: Gram proxy p0 - G alpha; 5-7: Gram-Schmidt form; narrow to wide lane groups
-    launch_omp_restricted_gram((variant - 2) % 3, variant >= 5, Y, M, A, inv_norm, ids, n, child_off, child_idx, cap,
-                               omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T, s);
-    return;
-  }
+  if (variant >= 2)  // 2-4: Gram proxy p0 - G alpha; 5-7: Gram-Schmidt form; narrow to wide lane groups
+    return launch_omp_restricted_gram((variant - 2) % 3, variant >= 5, Y, M, A, inv_norm, ids, n, child_off,
+                                      child_idx, cap, omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo,
+                                      k_eff, stats, gram, T, D0, N0, Xh, s);
   if (variant == 0) {
     const int G = group_size(M);
     const int per_cta = GRP_WARPS * (32 / G);
@@ -776,7 +775,7 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
           Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega,
           alpha, ldo, k_eff, stats, gram, T, a_pstride, inv_pstride, cpos);
     });
-    return;
+    return false;
   }
   const int G = M <= 64 ? 16 : 32;
   const int per_cta = GRP_WARPS * (32 / G);
@@ -792,6 +791,7 @@ void launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
         Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, capS, omega_up, ldo_up, keff_up, Kp, Kuni, Kb,
         omega, alpha, ldo, k_eff, stats, gram, T, a_pstride, inv_pstride, cpos);
   });
+  return false;
 }
 
 }  // namespace csp

@@ -548,14 +548,24 @@ void launch_norms(const float *A, int T, int M, int Mp, float *inv_norm, __nv_bf
   norms_kernel<<<1, 1024, 0, s>>>(A, T, M, Mp, inv_norm, Abf);
 }
 
+void launch_synth(const GeomDev &g, const float *D0, int N0, const int32_t *support, const float *coef,
+                  const int8_t *k_eff, int Kmax, float *Xh, cudaStream_t s) {
+  const int64_t B = (int64_t)g.nx * g.ny;
+  if (B * N0) synth_kernel<<<blocks(B * 32, 256), 256, 0, s>>>(D0, N0, support, coef, k_eff, Kmax, B, Xh);
+}
+
+void launch_gather(const GeomDev &g, const float *Xh, int N0, const int32_t *cover_y, const int32_t *cover_x,
+                   float *img, cudaStream_t s) {
+  const int64_t n = (int64_t)g.Ly * g.Lx * g.H * g.W;
+  if (n) gather_kernel<<<blocks(n, 256), 256, 0, s>>>(g, Xh, N0, cover_y, cover_x, img);
+}
+
 void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *support, const float *coef,
                       const int8_t *k_eff, int Kmax, const int32_t *cover_y, const int32_t *cover_x, float *Xh,
                       float *img, cudaStream_t s) {
-  const int64_t B = (int64_t)g.nx * g.ny;
-  const int64_t n = (int64_t)g.Ly * g.Lx * g.H * g.W;
-  if (n == 0) return;
-  if (B * N0) synth_kernel<<<blocks(B * 32, 256), 256, 0, s>>>(D0, N0, support, coef, k_eff, Kmax, B, Xh);
-  gather_kernel<<<blocks(n, 256), 256, 0, s>>>(g, Xh, N0, cover_y, cover_x, img);
+  if ((int64_t)g.Ly * g.Lx * g.H * g.W == 0) return;
+  launch_synth(g, D0, N0, support, coef, k_eff, Kmax, Xh, s);
+  launch_gather(g, Xh, N0, cover_y, cover_x, img, s);
 }
 
 // Largest number of patches covering one tile of T pixels along an axis of

@@ -535,3 +535,68 @@ def test_pipelined_solve_equals_one_stream():
         for a, t in zip(ref, out):
             assert np.array_equal(a, t.cpu().numpy())
     ctx.set_graph_mode(False)
+
+
+@pytest.mark.parametrize("key,mode,prec,variant,form", [
+    ("bayer", "cross_scale", "bf16", 6, 2),   # finest level synthesizes x_hat itself
+    ("bayer", "cross_scale", "bf16", 0, 1),   # separate synthesis pass
+    ("bayer", "plain", "fp32", 6, 1),
+    ("denoise_ragged", "cross_scale", "fp32", 5, 1),
+    ("inpaint", "cross_scale", "bf16", 6, 1),  # per-pixel Phi: no Gram variants
+])
+def test_reconstruct_equals_three_calls(key, mode, prec, variant, form):
+    """csp_reconstruct (device buffers, one call) gives the image of
+    extract + solve + aggregate exactly, also replayed from its CUDA graph."""
+    from paper_1511_05174_gb300.context import Context
+    w = _workload(key)
+    ctx = Context(0)
+    ctx.load_workload(w)
+    ctx.set_kernel_variant(variant)
+    ctx.set_top_level_form(form)
+    meas = torch.from_numpy(np.ascontiguousarray(w.meas)).cuda()
+    K, K_patch, Kmax = budgets(w, mode)
+    assert K_patch is None
+    Y = ctx.extract(meas)
+    sup, coef, keff = ctx.solve(Y, mode, prec, K=K, Kmax=Kmax)
+    ref = ctx.aggregate(sup, coef, keff).cpu().numpy()
+    img = torch.full_like(torch.from_numpy(ref).cuda(), -3.0)
+    ctx.reconstruct(meas, img, mode, prec, K=K, Kmax=Kmax)
+    torch.cuda.synchronize()
+    assert np.array_equal(img.cpu().numpy(), ref)
+    ctx.set_graph_mode(True)
+    for _ in range(3):  # record, then replay
+        img.fill_(-3.0)
+        ctx.reconstruct(meas, img, mode, prec, K=K, Kmax=Kmax)
+        torch.cuda.synchronize()
+        assert np.array_equal(img.cpu().numpy(), ref)
+    host = np.zeros_like(ref)
+    ctx.reconstruct_host(np.ascontiguousarray(w.meas), host, mode, prec, K=K, Kmax=Kmax)
+    assert np.array_equal(host, ref)
+    ctx.set_graph_mode(False)
+
+
+def test_reconstruct_at_size_pipelined():
+    """The 512x512 Bayer image through csp_reconstruct with the fused coarse
+    level, the two-stream pipeline and the fused synthesis, graph-replayed:
+    the image of the separate calls on one stream."""
+    from paper_1511_05174_gb300.context import Context
+    w = synthetic.make_workload("bayer")
+    ctx = Context(0)
+    ctx.load_workload(w)
+    ctx.set_kernel_variant(6)
+    ctx.set_top_level_form(2)
+    meas = torch.from_numpy(np.ascontiguousarray(w.meas)).cuda()
+    K, _, Kmax = budgets(w, "cross_scale")
+    ctx.set_pipeline(False)
+    Y = ctx.extract(meas)
+    sup, coef, keff = ctx.solve(Y, "cross_scale", "bf16", K=K, Kmax=Kmax)
+    ref = ctx.aggregate(sup, coef, keff).cpu().numpy()
+    ctx.set_pipeline(True)
+    ctx.set_graph_mode(True)
+    img = torch.empty_like(torch.from_numpy(ref).cuda())
+    for _ in range(3):
+        img.fill_(-3.0)
+        ctx.reconstruct(meas, img, "cross_scale", "bf16", K=K, Kmax=Kmax)
+        torch.cuda.synchronize()
+        assert np.array_equal(img.cpu().numpy(), ref)
+    ctx.set_graph_mode(False)
