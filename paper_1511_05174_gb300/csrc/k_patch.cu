@@ -35,19 +35,19 @@ __device__ __forceinline__ int level_index(const GeomDev &g, int l, int ly, int 
 // Phi = I, shot for coded aperture, 0 otherwise).
 __global__ void extract_kernel(GeomDev g, const float *__restrict__ meas, float *__restrict__ Y,
                                int64_t B, int M) {
-  // four consecutive rows m of one patch per thread (M and P are multiples of 4,
-  // so the four lie in one row of the patch)
-  const int64_t e4 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int M4 = M >> 2;
-  if (e4 >= B * M4) return;
-  const int64_t b = e4 / M4;
-  const int m = 4 * (int)(e4 - b * M4);
-  const int iy = (int)(b / g.nx), ix = (int)(b - (int64_t)iy * g.nx);
+  // thread (x, y) of a block: four consecutive rows m = 4x of patch
+  // blockIdx.x * blockDim.y + y (blockDim.x = M / 4; M and P are multiples of
+  // 4, so the four lie in one row of the patch); no 64-bit divisions
+  const int b = (int)(blockIdx.x * blockDim.y + threadIdx.y);  // B < 2^31 (launcher)
+  if (b >= B) return;
+  const int m = 4 * (int)threadIdx.x;
+  const int iy = b / g.nx, ix = b - iy * g.nx;
   const int oy = origin(iy, g.stride, g.H, g.P), ox = origin(ix, g.stride, g.W, g.P);
   const int PP = g.P * g.P;
   const int q = m / PP, r = m - q * PP, py = r / g.P, px = r - py * g.P;
   const float *src = meas + ((int64_t)q * g.H + oy + py) * g.W + ox + px;
-  reinterpret_cast<float4 *>(Y)[e4] = make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), __ldg(src + 3));
+  reinterpret_cast<float4 *>(Y + (int64_t)b * M)[threadIdx.x] =
+      make_float4(__ldg(src), __ldg(src + 1), __ldg(src + 2), __ldg(src + 3));
 }
 
 // Scalar variant for patch sides that are not a multiple of 4.
@@ -520,8 +520,10 @@ void launch_extract(const GeomDev &g, int sense_kind, int shots, const float *me
                     int64_t B, int M, cudaStream_t s) {
   (void)sense_kind; (void)shots;
   if (B * M == 0) return;
-  if (g.P % 4 == 0 && M % 4 == 0)
-    extract_kernel<<<blocks(B * M / 4, 256), 256, 0, s>>>(g, meas, Y, B, M);
+  if (g.P % 4 == 0 && M % 4 == 0 && M <= 1024 && B < ((int64_t)1 << 31) - 256) {
+    const int M4 = M / 4, per = M4 >= 256 ? 1 : 256 / M4;
+    extract_kernel<<<(unsigned)((B + per - 1) / per), dim3(M4, per), 0, s>>>(g, meas, Y, B, M);
+  }
   else
     extract1_kernel<<<blocks(B * M, 256), 256, 0, s>>>(g, meas, Y, B, M);
 }
