@@ -911,6 +911,45 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
 // Per-group shared memory: GrpSmem | p0[cap] | c[cap] | Q_C[cap][8] (its first
 // 64 words hold the parents' child ranges while the candidates are listed).
 // ---------------------------------------------------------------------------
+// x_hat = D0_Omega alpha for one patch, lanes s = 0 .. G-1 of its group each
+// writing float4 chunks s, s + G, ... of the row: the chosen rows in support
+// order, one FMA each from zero, as synth_kernel does (same values).  Not
+// inlined, so that the solver's loop does not hold its operands.
+static __device__ __noinline__ void synth_patch(const float *__restrict__ D0, int N0, float *__restrict__ xrow,
+                                                const float *W, const int *om, int k, int s, int G) {
+  constexpr int XS = 6;  // float4 chunks per lane per pass
+  const int n4 = N0 >> 2;
+  float4 *xb = reinterpret_cast<float4 *>(xrow);
+  for (int c0 = s; c0 < n4; c0 += G * XS) {
+    float4 acc[XS];
+#pragma unroll
+    for (int t = 0; t < XS; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+    for (int j = 0; j < k; ++j) {
+      const float aj = W[j];
+      const float4 *dr = reinterpret_cast<const float4 *>(D0 + (int64_t)om[j] * N0);
+      float4 d[XS];
+#pragma unroll
+      for (int t = 0; t < XS; ++t) {
+        const int ch = c0 + G * t;
+        d[t] = ch < n4 ? __ldg(dr + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int t = 0; t < XS; ++t) {
+        acc[t].x = fmaf(aj, d[t].x, acc[t].x);
+        acc[t].y = fmaf(aj, d[t].y, acc[t].y);
+        acc[t].z = fmaf(aj, d[t].z, acc[t].z);
+        acc[t].w = fmaf(aj, d[t].w, acc[t].w);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < XS; ++t) {
+      const int ch = c0 + G * t;
+      if (ch < n4) xb[ch] = acc[t];
+    }
+  }
+}
+
 __host__ __device__ __forceinline__ int qr8_q_floats(int cap) {
   return 8 * cap > 2 * CSP_MAX_K ? 8 * cap : 2 * CSP_MAX_K;
 }
@@ -1175,44 +1214,10 @@ omp_restricted_qr8_kernel(const float *__restrict__ Y, int M, const float *__res
       alpha[b * ldo + j] = (j < k) ? S.W[j] : 0.f;
     }
   }
-  // synthesis x_hat_b = D0_Omega alpha (Sec. IV) into Xh[b] when asked for: the
-  // chosen rows in support order, one FMA each from zero, as synth_kernel does
-  if (Xh && valid) {
-    constexpr int XS = 6;  // float4 chunks per lane per pass
-    const int n4 = N0 >> 2;
-    float4 *xb = reinterpret_cast<float4 *>(Xh + b * N0);
-    for (int c0 = s; c0 < n4; c0 += G * XS) {
-      float4 acc[XS];
-#pragma unroll
-      for (int t = 0; t < XS; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 2
-      for (int j = 0; j < k; ++j) {
-        const float aj = S.W[j];
-        const float4 *dr = reinterpret_cast<const float4 *>(D0 + (int64_t)S.om[j] * N0);
-        float4 d[XS];
-#pragma unroll
-        for (int t = 0; t < XS; ++t) {
-          const int ch = c0 + G * t;
-          d[t] = ch < n4 ? __ldg(dr + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int t = 0; t < XS; ++t) {
-          acc[t].x = fmaf(aj, d[t].x, acc[t].x);
-          acc[t].y = fmaf(aj, d[t].y, acc[t].y);
-          acc[t].z = fmaf(aj, d[t].z, acc[t].z);
-          acc[t].w = fmaf(aj, d[t].w, acc[t].w);
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < XS; ++t) {
-        const int ch = c0 + G * t;
-        if (ch < n4) xb[ch] = acc[t];
-      }
-    }
-  }
+  // synthesis x_hat_b = D0_Omega alpha (Sec. IV) into Xh[b] when asked for
+  if (Xh && valid) synth_patch(D0, N0, Xh + b * N0, S.W, S.om, k, s, G);
 }
 
-// ---------------------------------------------------------------------------
 // Restricted OMP in Gram-Schmidt form with the candidate state in registers.
 // Same iteration as omp_restricted_qr_kernel, but lane s of a group owns the
 // candidates c = s + G u (u < CPL) and keeps, per candidate, its atom index,
