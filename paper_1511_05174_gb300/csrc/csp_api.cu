@@ -821,6 +821,7 @@ void csp_destroy(csp_ctx *ctx) {
   for (auto e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->g_solve.exec) cudaGraphExecDestroy(ctx->g_solve.exec);
   if (ctx->g_recon.exec) cudaGraphExecDestroy(ctx->g_recon.exec);
+  if (ctx->g_host.exec) cudaGraphExecDestroy(ctx->g_host.exec);
   if (ctx->gstream) cudaStreamDestroy(ctx->gstream);
   if (ctx->aux) cudaStreamDestroy(ctx->aux);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
@@ -1128,7 +1129,7 @@ csp_status csp_set_graph_mode(csp_ctx *ctx, int on) {
   if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
   ctx->graph_mode = on != 0;
   if (!ctx->graph_mode)
-    for (csp_ctx::GraphSlot *g : {&ctx->g_solve, &ctx->g_recon})
+    for (csp_ctx::GraphSlot *g : {&ctx->g_solve, &ctx->g_recon, &ctx->g_host})
       if (g->exec) {
         cudaGraphExecDestroy(g->exec);
         g->exec = nullptr;
@@ -1217,6 +1218,35 @@ csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *prm, const
   };
   CSP_TRY(grow(ctx->h_meas, meas_n * 4));
   CSP_TRY(grow(ctx->h_img, img_n * 4));
+  // page-locked host buffers: in graph mode the copies join the recorded graph
+  auto pinned = [](const void *p) {
+    cudaPointerAttributes a;
+    const bool ok = cudaPointerGetAttributes(&a, p) == cudaSuccess && a.type == cudaMemoryTypeHost;
+    cudaGetLastError();
+    return ok;
+  };
+  if (ctx->graph_mode && !ctx->prof && pinned(meas_host) && pinned(image_host)) {
+    if (ctx->sense_kind == CSP_SENSE_DENSE)
+      return fail(ctx, CSP_ERR_UNSUPPORTED, "dense sensing has no measurement image to extract patches from");
+    CSP_TRY(check_solve_args(ctx, prm, ctx->B));
+    if (!ctx->lv[0].D) return fail(ctx, CSP_ERR_NOT_READY, "fine dictionary not loaded");
+    CSP_TRY(reconstruct_buffers(ctx, prm));
+    auto body = [&](cudaStream_t st) -> csp_status {
+      CSP_CUDA(ctx, cudaMemcpyAsync(ctx->h_meas.p, meas_host, meas_n * 4, cudaMemcpyHostToDevice, st));
+      CSP_TRY(reconstruct_core(ctx, prm, (const float *)ctx->h_meas.p, (float *)ctx->h_img.p, st));
+      CSP_CUDA(ctx, cudaMemcpyAsync(image_host, ctx->h_img.p, img_n * 4, cudaMemcpyDeviceToHost, st));
+      return CSP_OK;
+    };
+    csp_ctx::GraphKey key = graph_key(ctx, prm);
+    key.Y = meas_host;
+    key.B = ctx->B;
+    key.coef = image_host;
+    const csp_status st = run_graphed(ctx, ctx->g_host, key, s, body);
+    ctx->last_synth = st == CSP_OK && ctx->recon_synth;
+    CSP_TRY(st);
+    CSP_CUDA(ctx, cudaStreamSynchronize(s));
+    return CSP_OK;
+  }
   CSP_CUDA(ctx, cudaMemcpyAsync(ctx->h_meas.p, meas_host, meas_n * 4, cudaMemcpyHostToDevice, s));
   CSP_TRY(csp_reconstruct(ctx, prm, (const float *)ctx->h_meas.p, (float *)ctx->h_img.p, stream));
   CSP_CUDA(ctx, cudaMemcpyAsync(image_host, ctx->h_img.p, img_n * 4, cudaMemcpyDeviceToHost, s));

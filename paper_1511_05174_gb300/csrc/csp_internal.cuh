@@ -155,7 +155,7 @@ struct csp_ctx {
     GraphKey key{};
     cudaGraphExec_t exec = nullptr;
   };
-  GraphSlot g_solve, g_recon;  // csp_solve and csp_reconstruct
+  GraphSlot g_solve, g_recon, g_host;  // csp_solve, csp_reconstruct, csp_reconstruct_host (copies included)
   cudaStream_t gstream = nullptr;
   // second stream of the pipelined cross-scale solve (restricted level of the
   // first chunk beside the fused full-dictionary level of the second)

@@ -599,4 +599,12 @@ def test_reconstruct_at_size_pipelined():
         ctx.reconstruct(meas, img, "cross_scale", "bf16", K=K, Kmax=Kmax)
         torch.cuda.synchronize()
         assert np.array_equal(img.cpu().numpy(), ref)
+    # page-locked host buffers: the copies are recorded in the graph as well
+    meas_h = torch.from_numpy(np.ascontiguousarray(w.meas)).pin_memory()
+    img_h = torch.empty(ref.shape, dtype=torch.float32).pin_memory()
+    for _ in range(3):
+        img_h.fill_(-3.0)
+        ctx.reconstruct_host(meas_h, img_h, "cross_scale", "bf16", K=K, Kmax=Kmax)
+        assert np.array_equal(img_h.numpy(), ref)
+    assert ctx.stats()["synthesized"]
     ctx.set_graph_mode(False)
