@@ -1071,12 +1071,16 @@ omp_restricted_qr8_kernel(const float *__restrict__ Y, int M, const float *__res
       w[0] = h0.x; w[1] = h0.y; w[2] = h0.z; w[3] = h0.w;
       w[4] = h1.x; w[5] = h1.y; w[6] = h1.z; w[7] = h1.w;
     }
-    float ww = 0.f, wz = 0.f;
+    // two independent chains each (halves j < 4, j >= 4), then their sum
+    float ww0 = 0.f, ww1 = 0.f, wz0 = 0.f, wz1 = 0.f;
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      ww = fmaf(w[j], w[j], ww);
-      wz = fmaf(w[j], zr[j], wz);
+    for (int j = 0; j < 4; ++j) {
+      ww0 = fmaf(w[j], w[j], ww0);
+      ww1 = fmaf(w[j + 4], w[j + 4], ww1);
+      wz0 = fmaf(w[j], zr[j], wz0);
+      wz1 = fmaf(w[j + 4], zr[j + 4], wz1);
     }
+    const float ww = ww0 + ww1, wz = wz0 + wz1;
     const float d = aa - ww;
     const bool ok32 = f32 && aa > 0.f && d >= kTauPivot * aa;
     if (f32 && !ok32) {
@@ -1109,16 +1113,15 @@ omp_restricted_qr8_kernel(const float *__restrict__ Y, int M, const float *__res
         if (c < nc) {
           const int sc = (c >> 2) & 1;
           const float4 qa = Q4[2 * c + sc], qb = Q4[2 * c + 1 - sc];
-          float v = gpre[u];
-          v = fmaf(-w[0], qa.x, v);
-          v = fmaf(-w[1], qa.y, v);
-          v = fmaf(-w[2], qa.z, v);
-          v = fmaf(-w[3], qa.w, v);
-          v = fmaf(-w[4], qb.x, v);
-          v = fmaf(-w[5], qb.y, v);
-          v = fmaf(-w[6], qb.z, v);
-          v = fmaf(-w[7], qb.w, v);
-          v *= il;
+          // w . Q_C[c] as two chains of four, then G[q][c] minus it
+          float v0 = w[0] * qa.x, v1 = w[4] * qb.x;
+          v0 = fmaf(w[1], qa.y, v0);
+          v1 = fmaf(w[5], qb.y, v1);
+          v0 = fmaf(w[2], qa.z, v0);
+          v1 = fmaf(w[6], qb.z, v1);
+          v0 = fmaf(w[3], qa.w, v0);
+          v1 = fmaf(w[7], qb.w, v1);
+          float v = (gpre[u] - (v0 + v1)) * il;
           Q[8 * c + ((((k >> 2) ^ sc)) << 2) + kofs] = v;
           cc[c] = fmaf(-zk, v, cc[c]);
         }
@@ -1126,16 +1129,14 @@ omp_restricted_qr8_kernel(const float *__restrict__ Y, int M, const float *__res
       for (int c = s + 8 * G; c < nc; c += G) {
         const int sc = (c >> 2) & 1;
         const float4 qa = Q4[2 * c + sc], qb = Q4[2 * c + 1 - sc];
-        float v = __ldg(gram + (int64_t)q * T + S.cs[c]);
-        v = fmaf(-w[0], qa.x, v);
-        v = fmaf(-w[1], qa.y, v);
-        v = fmaf(-w[2], qa.z, v);
-        v = fmaf(-w[3], qa.w, v);
-        v = fmaf(-w[4], qb.x, v);
-        v = fmaf(-w[5], qb.y, v);
-        v = fmaf(-w[6], qb.z, v);
-        v = fmaf(-w[7], qb.w, v);
-        v *= il;
+        float v0 = w[0] * qa.x, v1 = w[4] * qb.x;
+        v0 = fmaf(w[1], qa.y, v0);
+        v1 = fmaf(w[5], qb.y, v1);
+        v0 = fmaf(w[2], qa.z, v0);
+        v1 = fmaf(w[6], qb.z, v1);
+        v0 = fmaf(w[3], qa.w, v0);
+        v1 = fmaf(w[7], qb.w, v1);
+        float v = (__ldg(gram + (int64_t)q * T + S.cs[c]) - (v0 + v1)) * il;
         Q[8 * c + ((((k >> 2) ^ sc)) << 2) + kofs] = v;
         cc[c] = fmaf(-zk, v, cc[c]);
       }
