@@ -486,11 +486,15 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
           }
         }
       }
-      float r2 = 0.f;
+      float r2x = 0.f, r2y = 0.f, r2z = 0.f, r2w = 0.f;  // four independent chains
 #pragma unroll
-      for (int t = 0; t < FZ_NCH; ++t)
-        r2 = fmaf(rv[t].x, rv[t].x, fmaf(rv[t].y, rv[t].y, fmaf(rv[t].z, rv[t].z, fmaf(rv[t].w, rv[t].w, r2))));
-      r2 = pair_sum(r2);
+      for (int t = 0; t < FZ_NCH; ++t) {
+        r2x = fmaf(rv[t].x, rv[t].x, r2x);
+        r2y = fmaf(rv[t].y, rv[t].y, r2y);
+        r2z = fmaf(rv[t].z, rv[t].z, r2z);
+        r2w = fmaf(rv[t].w, rv[t].w, r2w);
+      }
+      const float r2 = pair_sum((r2x + r2y) + (r2z + r2w));
       if (appended) {
         rsq = r2;
         ++k;
