@@ -229,9 +229,11 @@ csp_status csp_reconstruct(csp_ctx *ctx, const csp_solve_params *params, const f
 /* End-to-end reconstruction from HOST buffers: copies the measurement image
  * (layout as in csp_extract_patches) to the device, runs csp_reconstruct and
  * copies the image (float32 [planes][H][W]) back into image_host.  Per-patch
- * budgets are not accepted here (K_patch must be NULL).  In graph mode, with
- * page-locked host buffers, the copies are recorded in the graph with the rest
- * of the call.  Returns when the image is in host memory. */
+ * budgets are not accepted here (K_patch must be NULL).  A page-locked
+ * image_host is written directly by the overlap-add through its device mapping
+ * (over the host link, no staging copy); in graph mode, with a page-locked
+ * meas_host, the input copy is recorded in the graph with the rest of the call.
+ * Returns when the image is in host memory. */
 csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *params,
                                 const float *meas_host, float *image_host, void *stream);
 

@@ -1218,14 +1218,22 @@ csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *prm, const
   };
   CSP_TRY(grow(ctx->h_meas, meas_n * 4));
   CSP_TRY(grow(ctx->h_img, img_n * 4));
-  // page-locked host buffers: in graph mode the copies join the recorded graph
+  // page-locked host buffers: the overlap-add writes the image straight into
+  // the host buffer through its device mapping (over the host link, no staging
+  // copy), and in graph mode the input copy joins the recorded graph
   auto pinned = [](const void *p) {
     cudaPointerAttributes a;
     const bool ok = cudaPointerGetAttributes(&a, p) == cudaSuccess && a.type == cudaMemoryTypeHost;
     cudaGetLastError();
     return ok;
   };
-  if (ctx->graph_mode && !ctx->prof && pinned(meas_host) && pinned(image_host)) {
+  float *img_view = nullptr;
+  if (pinned(image_host) && cudaHostGetDevicePointer((void **)&img_view, image_host, 0) != cudaSuccess) {
+    cudaGetLastError();
+    img_view = nullptr;
+  }
+  float *img_out = img_view ? img_view : (float *)ctx->h_img.p;
+  if (ctx->graph_mode && !ctx->prof && pinned(meas_host)) {
     if (ctx->sense_kind == CSP_SENSE_DENSE)
       return fail(ctx, CSP_ERR_UNSUPPORTED, "dense sensing has no measurement image to extract patches from");
     CSP_TRY(check_solve_args(ctx, prm, ctx->B));
@@ -1233,8 +1241,8 @@ csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *prm, const
     CSP_TRY(reconstruct_buffers(ctx, prm));
     auto body = [&](cudaStream_t st) -> csp_status {
       CSP_CUDA(ctx, cudaMemcpyAsync(ctx->h_meas.p, meas_host, meas_n * 4, cudaMemcpyHostToDevice, st));
-      CSP_TRY(reconstruct_core(ctx, prm, (const float *)ctx->h_meas.p, (float *)ctx->h_img.p, st));
-      CSP_CUDA(ctx, cudaMemcpyAsync(image_host, ctx->h_img.p, img_n * 4, cudaMemcpyDeviceToHost, st));
+      CSP_TRY(reconstruct_core(ctx, prm, (const float *)ctx->h_meas.p, img_out, st));
+      if (!img_view) CSP_CUDA(ctx, cudaMemcpyAsync(image_host, ctx->h_img.p, img_n * 4, cudaMemcpyDeviceToHost, st));
       return CSP_OK;
     };
     csp_ctx::GraphKey key = graph_key(ctx, prm);
@@ -1248,8 +1256,8 @@ csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *prm, const
     return CSP_OK;
   }
   CSP_CUDA(ctx, cudaMemcpyAsync(ctx->h_meas.p, meas_host, meas_n * 4, cudaMemcpyHostToDevice, s));
-  CSP_TRY(csp_reconstruct(ctx, prm, (const float *)ctx->h_meas.p, (float *)ctx->h_img.p, stream));
-  CSP_CUDA(ctx, cudaMemcpyAsync(image_host, ctx->h_img.p, img_n * 4, cudaMemcpyDeviceToHost, s));
+  CSP_TRY(csp_reconstruct(ctx, prm, (const float *)ctx->h_meas.p, img_out, stream));
+  if (!img_view) CSP_CUDA(ctx, cudaMemcpyAsync(image_host, ctx->h_img.p, img_n * 4, cudaMemcpyDeviceToHost, s));
   CSP_CUDA(ctx, cudaStreamSynchronize(s));
   return CSP_OK;
 }
