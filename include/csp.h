@@ -231,9 +231,10 @@ csp_status csp_reconstruct(csp_ctx *ctx, const csp_solve_params *params, const f
  * copies the image (float32 [planes][H][W]) back into image_host.  Per-patch
  * budgets are not accepted here (K_patch must be NULL).  A page-locked
  * image_host is written directly by the overlap-add through its device mapping
- * (over the host link, no staging copy); in graph mode, with a page-locked
- * meas_host, the input copy is recorded in the graph with the rest of the call.
- * Returns when the image is in host memory. */
+ * (over the host link, no staging copy); a page-locked, 16-byte aligned
+ * meas_host is read by a copy kernel through its mapping; in graph mode, with a
+ * page-locked meas_host, the whole call is recorded in one graph.  Returns when
+ * the image is in host memory. */
 csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *params,
                                 const float *meas_host, float *image_host, void *stream);
 

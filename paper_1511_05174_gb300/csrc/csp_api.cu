@@ -1233,6 +1233,21 @@ csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *prm, const
     img_view = nullptr;
   }
   float *img_out = img_view ? img_view : (float *)ctx->h_img.p;
+  // a page-locked, 16-byte aligned meas_host is read once by a copy kernel
+  // through its device mapping (faster than a copy-engine transfer of this size)
+  const float *meas_view = nullptr;
+  if (pinned(meas_host) && (reinterpret_cast<uintptr_t>(meas_host) & 15) == 0 &&
+      cudaHostGetDevicePointer((void **)&meas_view, (void *)meas_host, 0) != cudaSuccess) {
+    cudaGetLastError();
+    meas_view = nullptr;
+  }
+  auto copy_in = [&](cudaStream_t st) -> csp_status {
+    if (meas_view) run(ctx, KK_EXTRACT, st, (int64_t)meas_n, [&] {
+      launch_copy_floats(meas_view, (float *)ctx->h_meas.p, (int64_t)meas_n, st);
+    });
+    else CSP_CUDA(ctx, cudaMemcpyAsync(ctx->h_meas.p, meas_host, meas_n * 4, cudaMemcpyHostToDevice, st));
+    return CSP_OK;
+  };
   if (ctx->graph_mode && !ctx->prof && pinned(meas_host)) {
     if (ctx->sense_kind == CSP_SENSE_DENSE)
       return fail(ctx, CSP_ERR_UNSUPPORTED, "dense sensing has no measurement image to extract patches from");
@@ -1240,7 +1255,7 @@ csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *prm, const
     if (!ctx->lv[0].D) return fail(ctx, CSP_ERR_NOT_READY, "fine dictionary not loaded");
     CSP_TRY(reconstruct_buffers(ctx, prm));
     auto body = [&](cudaStream_t st) -> csp_status {
-      CSP_CUDA(ctx, cudaMemcpyAsync(ctx->h_meas.p, meas_host, meas_n * 4, cudaMemcpyHostToDevice, st));
+      CSP_TRY(copy_in(st));
       CSP_TRY(reconstruct_core(ctx, prm, (const float *)ctx->h_meas.p, img_out, st));
       if (!img_view) CSP_CUDA(ctx, cudaMemcpyAsync(image_host, ctx->h_img.p, img_n * 4, cudaMemcpyDeviceToHost, st));
       return CSP_OK;
@@ -1255,7 +1270,7 @@ csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *prm, const
     CSP_CUDA(ctx, cudaStreamSynchronize(s));
     return CSP_OK;
   }
-  CSP_CUDA(ctx, cudaMemcpyAsync(ctx->h_meas.p, meas_host, meas_n * 4, cudaMemcpyHostToDevice, s));
+  CSP_TRY(copy_in(s));
   CSP_TRY(csp_reconstruct(ctx, prm, (const float *)ctx->h_meas.p, img_out, stream));
   if (!img_view) CSP_CUDA(ctx, cudaMemcpyAsync(image_host, ctx->h_img.p, img_n * 4, cudaMemcpyDeviceToHost, s));
   CSP_CUDA(ctx, cudaStreamSynchronize(s));

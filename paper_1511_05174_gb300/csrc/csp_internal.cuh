@@ -211,6 +211,9 @@ bool launch_aggregate_tiled(const GeomDev &g, const float *D0, int N0, const int
 void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *support,
                       const float *coef, const int8_t *k_eff, int Kmax, const int32_t *cover_y,
                       const int32_t *cover_x, float *Xh, float *img, cudaStream_t s);
+// Copy of n floats with a kernel (16-byte aligned pointers; the source may be a
+// page-locked host buffer's device mapping).
+void launch_copy_floats(const float *src, float *dst, int64_t n, cudaStream_t s);
 // The two passes of launch_aggregate: x_hat_p = D0 alpha_p into Xh [B][N0], then
 // the overlap-add of Xh into the image.
 void launch_synth(const GeomDev &g, const float *D0, int N0, const int32_t *support, const float *coef,

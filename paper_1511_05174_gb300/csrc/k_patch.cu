@@ -550,6 +550,24 @@ void launch_norms(const float *A, int T, int M, int Mp, float *inv_norm, __nv_bf
   norms_kernel<<<1, 1024, 0, s>>>(A, T, M, Mp, inv_norm, Abf);
 }
 
+// Copy of n floats (16-byte aligned source and destination), e.g. from a
+// page-locked host buffer through its device mapping: coalesced 16-byte loads,
+// many in flight, one pass over the source.
+__global__ void copy4_kernel(const float4 *__restrict__ src, float4 *__restrict__ dst, int64_t n4) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+void launch_copy_floats(const float *src, float *dst, int64_t n, cudaStream_t s) {
+  const int64_t n4 = n / 4;
+  if (n4 > 0) {
+    const int64_t want = (n4 + 255) / 256;
+    copy4_kernel<<<(unsigned)(want < 1216 ? want : 1216), 256, 0, s>>>(reinterpret_cast<const float4 *>(src),
+                                                                      reinterpret_cast<float4 *>(dst), n4);
+  }
+  if (n % 4) cudaMemcpyAsync(dst + 4 * n4, src + 4 * n4, (n % 4) * sizeof(float), cudaMemcpyDefault, s);
+}
+
 void launch_synth(const GeomDev &g, const float *D0, int N0, const int32_t *support, const float *coef,
                   const int8_t *k_eff, int Kmax, float *Xh, cudaStream_t s) {
   const int64_t B = (int64_t)g.nx * g.ny;
