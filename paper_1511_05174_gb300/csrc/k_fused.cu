@@ -19,16 +19,18 @@
 //           alpha, form r = y - A_Omega alpha, and write r back as the next
 //           BF16 tile (128-byte swizzle, the layout the MMA reads).
 // The FP32 rows of A (zero padded to 64, rows 68 words apart so that the rows
-// of different patches fall on different banks) stay in shared memory, so the
-// re-score, the Gram column and the residue read no global memory.  The two
-// threads of a patch own interleaved float4 chunks (2t and 2t + 1) of every
-// 64-vector.
+// of different patches fall on different banks) and their squared norms stay
+// in shared memory, so the re-score and the residue read no global memory;
+// the Gram column G[q][Omega] comes from the level's Gram matrix (L2) when
+// there is one, else from the shared rows.  The two threads of a patch own
+// interleaved float4 chunks (2t and 2t + 1) of every 64-vector.
 //
 // A CTA runs NGRP groups of 256 threads, each with its own tile of 128 patches,
 // its own half of the tensor memory and its own barriers, over one copy of
-// the atoms: while one group is in its scalar update the tensor cores and the
-// other group's epilogue proceed.  One launch covers every mosaic phase (each
-// CTA's tiles belong to one phase, whose atoms it loads).
+// the atoms; the second group starts one epilogue late, so that one group's
+// top-4 selection (integer pipe) runs beside the other's update (shared
+// memory).  One launch covers every mosaic phase (each CTA's tiles belong to
+// one phase, whose atoms it loads).
 //
 // Roles: thread 0 loads the BF16 atoms by TMA; warp 0 owns the tensor memory;
 // in each group, thread 0 issues the group's MMAs once the group barrier shows
