@@ -898,19 +898,6 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
   }
 }
 
-// ---------------------------------------------------------------------------
-// The Gram-Schmidt form for Kb <= 8 with Q_C stored by candidate: row c of
-// Q_C (its 8 entries <a_c, u_j>, zero beyond the chosen count) is 32 bytes,
-// its two 16-byte halves swapped when bit 2 of c is set so that the 8 lanes of
-// a group read 8 rows without bank conflicts.  A candidate's column update is
-// then two 16-byte loads and 8 FMAs against w held in registers; the new row
-// of L (w = Q_C[q]) is two broadcast loads; the argmax keeps the winner's slot
-// and finds its lane by ballot; ||w||^2 and <w, z> are formed by every lane
-// (z in registers), with no group reduction.  Same iteration, outputs and
-// FP64 / explicit-residual paths as omp_restricted_qr_kernel.
-// Per-group shared memory: GrpSmem | p0[cap] | c[cap] | Q_C[cap][8] (its first
-// 64 words hold the parents' child ranges while the candidates are listed).
-// ---------------------------------------------------------------------------
 // x_hat = D0_Omega alpha for one patch, lanes s = 0 .. G-1 of its group each
 // writing float4 chunks s, s + G, ... of the row: the chosen rows in support
 // order, one FMA each from zero, as synth_kernel does (same values).  Not
@@ -950,6 +937,21 @@ static __device__ __noinline__ void synth_patch(const float *__restrict__ D0, in
   }
 }
 
+// ---------------------------------------------------------------------------
+// The Gram-Schmidt form for Kb <= 8 with Q_C stored by candidate: row c of
+// Q_C (its 8 entries <a_c, u_j>, zero beyond the chosen count) is 32 bytes,
+// its two 16-byte halves swapped when bit 2 of c is set so that the 8 lanes of
+// a group read 8 rows without bank conflicts.  A candidate's column update is
+// then two 16-byte loads and 8 FMAs (two chains of four) against w held in
+// registers; the new row of L (w = Q_C[q]) is two broadcast loads; the group
+// argmax compares the score bits first and the indices only where scores tie,
+// and finds the winner's lane and slot by ballot; ||w||^2 and <w, z> are formed
+// by every lane (z in registers), with no group reduction.  Through
+// csp_reconstruct the kernel also writes x_hat = D0_Omega alpha (synth_patch).  Same iteration, outputs and
+// FP64 / explicit-residual paths as omp_restricted_qr_kernel.
+// Per-group shared memory: GrpSmem | p0[cap] | c[cap] | Q_C[cap][8] (its first
+// 64 words hold the parents' child ranges while the candidates are listed).
+// ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ int qr8_q_floats(int cap) {
   return 8 * cap > 2 * CSP_MAX_K ? 8 * cap : 2 * CSP_MAX_K;
 }
