@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the restricted-solver variant (0-9) instead of autotuning (profiling runs)")
     ap.add_argument("--serving-jobs", type=int, default=24, help="jobs per offered rate")
+    ap.add_argument("--sweep-q", default=None,
+                    help="comma-separated children-per-coarse-atom counts Q (e.g. 2,4,8,16): instead of the "
+                         "headline, time cross-scale and plain OMP and report PSNR for each Q (the link-size "
+                         "trade-off of Sec. III-E / Fig. 4 on synthetic data)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="one stream throughout (csp_set_pipeline off; profiling runs)")
     ap.add_argument("--top-form", type=int, default=None, choices=[1, 2],
@@ -362,10 +366,62 @@ def serving_bench(args, device, pool, mode, jobs_per_rate):
         srv.close()
 
 
+def q_sweep(args):
+    """Cross-scale vs plain OMP for several children-per-coarse-atom counts Q on
+    the synthetic workload (the coarse dictionary has T/Q atoms): patches/s of
+    csp_reconstruct (graph-replayed, L2 flushed between steps) and PSNR against
+    the synthetic ground truth.  One JSON line."""
+    import torch
+    import synthetic
+    from paper_1511_05174_gb300.context import Context
+
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    rows = []
+    for Q in [int(q) for q in args.sweep_q.split(",")]:
+        w = synthetic.make_workload(args.workload, links=args.links, Q=Q)
+        ctx = Context(0)
+        ctx.load_workload(w)
+        K = [int(k[0]) for k in w.K_levels]
+        meas_d = torch.from_numpy(w.meas).to(dev)
+        img = torch.empty((w.geometry.planes, w.geometry.H, w.geometry.W), dtype=torch.float32, device=dev)
+        Y = ctx.extract(meas_d)
+        ctx.autotune(Y, "cross_scale", args.precision, K=K, Kmax=K[0])
+        ctx.set_graph_mode(True)
+        row = {"Q": Q, "coarse_atoms": int(w.dicts[-1].shape[0]), "patches": int(w.n_patches)}
+        for mode in ("cross_scale", "plain"):
+            Km = K if mode == "cross_scale" else K[:1]
+            for _ in range(max(args.warmup, 3)):
+                ctx.reconstruct(meas_d, img, mode, args.precision, K=Km, Kmax=K[0])
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            torch.cuda.synchronize()
+            for a, b in ev:
+                flush.zero_()
+                a.record()
+                ctx.reconstruct(meas_d, img, mode, args.precision, K=Km, Kmax=K[0])
+                b.record()
+            torch.cuda.synchronize()
+            ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+            est = img.double().cpu().numpy()
+            mse = float(np.mean((w.truth - est) ** 2))
+            peak = float(w.truth.max() - w.truth.min())
+            row[mode] = {"patches_per_s": w.n_patches / (ms / 1e3), "ms_per_image": ms,
+                         "psnr_db": 10 * np.log10(peak * peak / mse)}
+        row["speedup"] = row["cross_scale"]["patches_per_s"] / row["plain"]["patches_per_s"]
+        rows.append(row)
+        ctx.close()
+    print(json.dumps({"sweep": "children per coarse atom (Q)", "workload": w.name, "precision": args.precision,
+                      "data": "synthetic (seeded)", "l2": "flushed between steps", "rows": rows}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.sweep_q:
+        q_sweep(args)
         return
 
     import torch

@@ -608,3 +608,17 @@ def test_reconstruct_at_size_pipelined():
         assert np.array_equal(img_h.numpy(), ref)
     assert ctx.stats()["synthesized"]
     ctx.set_graph_mode(False)
+
+
+@pytest.mark.parametrize("Q,prec", [(2, "fp32"), (8, "bf16"), (16, "fp32")])
+def test_cross_scale_other_link_sizes(Q, prec):
+    """Children per coarse atom Q = 2, 8, 16 (coarse dictionary of T/Q atoms,
+    uneven child counts), Bayer 64x64: supports and coefficients against the
+    oracle, and through csp_reconstruct the oracle's image."""
+    w = synthetic.make_workload("bayer", H=64, W=64, Q=Q)
+    g = run_gpu(w, "cross_scale", prec)
+    o, a, k, _ = oracle.cross_scale_omp(w)
+    rate, worst, bad = compare(w.dicts[0], g["sup"], g["coef"], g["keff"], o, a, k)
+    assert rate >= MATCH and worst <= REL_TOL, bad[:10]
+    img_o = oracle.aggregate(w, o, a, k)
+    assert abs(oracle.psnr(w.truth, g["img"]) - oracle.psnr(w.truth, img_o)) <= 0.05
