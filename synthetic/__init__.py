@@ -13,9 +13,11 @@ and here stand in for it.
 from .workloads import (  # noqa: F401
     Geometry,
     Sensing,
+    TrainingSet,
     Workload,
     WORKLOAD_NAMES,
     make_workload,
     make_independent_problems,
+    make_training_set,
     patch_count_1d,
 )

@@ -372,3 +372,53 @@ def make_independent_problems(B: int, M: int, T: int, K: int, seed: int = 0, sig
     Y = np.einsum("bk,bkm->bm", vals, A.astype(np.float64)[sup]) if B else np.zeros((0, M))
     Y = Y + sigma * r[3].standard_normal(Y.shape)
     return A, Y.astype(np.float32), sup.astype(np.int32)
+
+
+@dataclasses.dataclass
+class TrainingSet:
+    """Training signals for learning a cross-scale dictionary pair.
+
+    ``X`` [n, N0] float32 holds level-0 patch vectors x = D0_S s + e with
+    zero-tree supports S drawn through the scale links of ``parents`` (the
+    signal model of Sec. III-A) and s ~ N(0, 1).  ``dicts``/``parents`` are the
+    generating model (the learner never sees them).  ``u_low`` [T_low] and
+    ``u_high`` [T_high] are uniform numbers in [0, 1) for the random picks of
+    the initialisation heuristics."""
+
+    geometry: Geometry
+    X: np.ndarray
+    dicts: List[np.ndarray]
+    parents: List[np.ndarray]
+    K_high: int
+    K_low: int
+    u_low: np.ndarray
+    u_high: np.ndarray
+    sigma: float
+    seed: int
+
+
+def make_training_set(name: str = "denoise", n: int = 4096, seed: int = 0, T0: Optional[int] = None,
+                      sigma: Optional[float] = None, Q: int = 4) -> TrainingSet:
+    """Seeded two-scale training set with the patch shape, atom counts and
+    sparsities of workload ``name`` (``denoise``: 8x8 grey, T 256/64, K 4/2;
+    ``bayer``: 8x8 RGB, T 1024/256, K 8/4)."""
+    geo_kw, T0_def, K_lv, sigma_def, _ = _presets(name, "paper")
+    g = Geometry(**geo_kw)
+    if g.n_levels != 2 or K_lv is None:
+        raise ValueError("training sets are defined for the two-scale presets")
+    T0 = T0 or T0_def
+    sigma = sigma_def if sigma is None else sigma
+    ss = np.random.SeedSequence([seed, 0x6b737664]).spawn(_N_STREAMS)
+    rng = [np.random.default_rng(s) for s in ss]
+    dicts, parents = _build_dictionaries(g, T0, Q, "paper", rng[_S_DICT], rng[_S_SUBSET])
+    children = [_children(parents[0], dicts[1].shape[0])]
+    D0 = dicts[0].astype(np.float64)
+    X = np.zeros((n, D0.shape[1]))
+    for i in range(n):
+        S = _truth_support(rng[_S_SUPPORT], children, dicts[1].shape[0], K_lv)
+        X[i] = D0[S].T @ rng[_S_VALUES].standard_normal(len(S))
+    X += sigma * rng[_S_NOISE].standard_normal(X.shape)
+    u_low = rng[_S_CODES].random(dicts[1].shape[0])
+    u_high = rng[_S_CODES].random(T0)
+    return TrainingSet(g, X.astype(np.float32), dicts, parents, int(K_lv[0]), int(K_lv[1]),
+                       u_low, u_high, sigma, seed)
