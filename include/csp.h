@@ -238,6 +238,67 @@ csp_status csp_reconstruct(csp_ctx *ctx, const csp_solve_params *params, const f
 csp_status csp_reconstruct_host(csp_ctx *ctx, const csp_solve_params *params,
                                 const float *meas_host, float *image_host, void *stream);
 
+/* ---- Dictionary learning: modified K-SVD -----------------------------------
+ * Sec. II ("Dictionary learning"): K-SVD alternates sparse coding of the
+ * training signals with an atom-by-atom dictionary update.  Sec. III
+ * ("Learning cross-scale sparse models"): Step 1 runs K-SVD on the
+ * downsampled signals W x_i (csp_downsample) with plain OMP; Step 2 runs
+ * K-SVD on the x_i with the coding restricted to the children of each
+ * signal's coarse support (csp_solve, CSP_MODE_CROSS_SCALE).  Sec. III
+ * ("Initialization of dictionary"): heuristics 1-2 (csp_ksvd_init_atoms) and
+ * 3-4 (replace_unused of csp_ksvd_update).  These calls need no sensing
+ * operator and, except csp_downsample, no geometry; they use the context's
+ * device, workspace and memory budget. */
+
+/* W of Sec. III-A for training signals: X_low[i] = W_level x_i (box average
+ * over the level's factor blocks).  X: DEVICE float32 [N][N_0] level-0 patch
+ * vectors of the geometry's layout; X_low: DEVICE float32 [N][N_level].
+ * Requires geometry.  Stream-ordered. */
+csp_status csp_downsample(csp_ctx *ctx, int level, const float *X, int64_t N, float *X_low, void *stream);
+
+/* One dictionary-update sweep of K-SVD.  Atoms k = 0 .. T-1 are visited in
+ * order; visiting k: E_k = the residuals r_i = x_i - D s_i of the signals
+ * whose support holds k, each with alpha_ik d_k added back; d_k becomes the
+ * leading left singular vector of E_k (the dominant eigenvector of E_k E_k^T,
+ * found by the power method from the old d_k to an FP32 fixed point), signed
+ * so that <d_new, d_old> >= 0; alpha_ik becomes <e_i, d_k>; the residuals
+ * follow.  An atom with E_k = 0 keeps its value.
+ * D: DEVICE float32 [T][M] (atom-major), updated in place.
+ * X: DEVICE float32 [N][M] training signals.
+ * support / coef: DEVICE [N][Kmax] as csp_solve writes them (atom ids into D,
+ *   -1 padded; coef updated in place); k_eff: DEVICE int8 [N].  A support
+ *   must not repeat an atom.
+ * replace_unused = 1: an atom with no users becomes the normalised signal of
+ *   largest residual norm among the eligible ones (ties: lowest index), and
+ *   that signal is not picked again in this sweep (heuristics 3-4).  Eligible:
+ *   every signal of nonzero norm, or, with repl_parent (DEVICE int32 [T], the
+ *   coarse parent of each atom) and repl_support (DEVICE int32 [N][Kc], coarse
+ *   supports, -1 padded), the signals whose coarse support holds the atom's
+ *   parent.  replace_unused = 0: unused atoms keep their value.
+ * err_out: DEVICE float32 [1] or NULL; receives ||X - D S||_F^2 after the sweep.
+ * Limits: 1 <= M <= 192 (else CSP_ERR_UNSUPPORTED), T <= 32768,
+ *   N * Kmax < 2^31.  Errors found on the device (k_eff outside [0, Kmax],
+ *   atom id outside [0, T), a repeated atom) return CSP_ERR_INVALID before D
+ *   or coef change.  Deterministic.  Synchronous: returns when the sweep is
+ *   complete (work is ordered after earlier work on `stream`). */
+csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X, int64_t N,
+                           const int32_t *support, float *coef, const int8_t *k_eff, int Kmax,
+                           int replace_unused, const int32_t *repl_parent, const int32_t *repl_support,
+                           int Kc, float *err_out, void *stream);
+
+/* Initialisation picks of the modified K-SVD.  Atom t = x_i / ||x_i|| with
+ * i = item floor(u_t n) of a pool of n signals in ascending order: all N
+ * signals when parent is NULL (heuristic 1, the coarse dictionary from W X);
+ * else the signals whose coarse support (support_low DEVICE int32 [N][Kc],
+ * keff_low DEVICE int8 [N]) holds parent[t] (heuristic 2: the children of
+ * coarse atom k from X restricted to Omega_k), all N when that pool is empty.
+ * D: DEVICE float32 [T][M] (written; an atom whose pick is a zero signal keeps
+ * its value).  X: DEVICE float32 [N][M].  parent: DEVICE int32 [T] in
+ * [0, T_low).  u: DEVICE float64 [T], uniform in [0, 1).  Synchronous. */
+csp_status csp_ksvd_init_atoms(csp_ctx *ctx, float *D, int M, int T, const float *X, int64_t N,
+                               const int32_t *parent, const int32_t *support_low, const int8_t *keff_low,
+                               int Kc, int T_low, const double *u, void *stream);
+
 /* ---- Serving: continuous batching of reconstruction jobs -----------------
  * Not part of the paper's method: a request loop around csp_solve.  A server
  * owns one CUDA device, a device-memory budget for in-flight jobs and a

@@ -120,6 +120,7 @@ def ksvd_update(D: np.ndarray, X: np.ndarray, omega: np.ndarray, alpha: np.ndarr
         U, s, _ = np.linalg.svd(E.T, full_matrices=False)  # E^T = M x n
         if s[0] == 0.0:
             A[I, J] = E @ D[k]
+            R[I] = E - A[I, J][:, None] * D[k][None, :]
             continue
         u = U[:, 0]
         if u @ D[k] < 0.0:

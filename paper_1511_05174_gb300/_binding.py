@@ -39,7 +39,8 @@ EXPORTS = ("csp_create", "csp_destroy", "csp_last_error", "csp_set_geometry", "c
            "csp_server_create", "csp_server_destroy", "csp_server_last_error", "csp_server_add_model",
            "csp_submit", "csp_poll", "csp_wait", "csp_job_info_get", "csp_job_release",
            "csp_server_pause", "csp_set_aggregate_path", "csp_set_top_level_form",
-           "csp_set_wait_test", "csp_set_graph_mode", "csp_set_pipeline", "csp_reconstruct")
+           "csp_set_wait_test", "csp_set_graph_mode", "csp_set_pipeline", "csp_reconstruct",
+           "csp_downsample", "csp_ksvd_update", "csp_ksvd_init_atoms")
 
 
 class csp_geometry(ctypes.Structure):
@@ -150,6 +151,9 @@ def load_library(path: str = LIB_PATH):
         "csp_job_info_get": (i, [vp, ctypes.c_uint64, ctypes.POINTER(csp_job_info)]),
         "csp_job_release": (i, [vp, ctypes.c_uint64]),
         "csp_server_pause": (i, [vp, i]),
+        "csp_downsample": (i, [vp, i, vp, ctypes.c_int64, vp, vp]),
+        "csp_ksvd_update": (i, [vp, vp, i, i, vp, ctypes.c_int64, vp, vp, vp, i, i, vp, vp, i, vp, vp]),
+        "csp_ksvd_init_atoms": (i, [vp, vp, i, i, vp, ctypes.c_int64, vp, vp, vp, i, i, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -347,3 +351,20 @@ def csp_job_release(srv, job_id: int) -> None:
 
 def csp_server_pause(srv, paused: bool) -> None:
     check_server(load_library().csp_server_pause(srv, int(bool(paused))), srv)
+
+
+def csp_downsample(ctx, level: int, X_ptr: int, N: int, X_low_ptr: int, stream: int = 0) -> None:
+    check(load_library().csp_downsample(ctx, level, X_ptr, N, X_low_ptr, stream), ctx)
+
+
+def csp_ksvd_update(ctx, D_ptr: int, M: int, T: int, X_ptr: int, N: int, sup_ptr: int, coef_ptr: int,
+                    keff_ptr: int, Kmax: int, replace_unused: int, parent_ptr, rsup_ptr, Kc: int, err_ptr,
+                    stream: int = 0) -> None:
+    check(load_library().csp_ksvd_update(ctx, D_ptr, M, T, X_ptr, N, sup_ptr, coef_ptr, keff_ptr, Kmax,
+                                         replace_unused, parent_ptr, rsup_ptr, Kc, err_ptr, stream), ctx)
+
+
+def csp_ksvd_init_atoms(ctx, D_ptr: int, M: int, T: int, X_ptr: int, N: int, parent_ptr, sup_low_ptr,
+                        keff_low_ptr, Kc: int, T_low: int, u_ptr: int, stream: int = 0) -> None:
+    check(load_library().csp_ksvd_init_atoms(ctx, D_ptr, M, T, X_ptr, N, parent_ptr, sup_low_ptr, keff_low_ptr,
+                                             Kc, T_low, u_ptr, stream), ctx)

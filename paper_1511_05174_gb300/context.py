@@ -227,6 +227,49 @@ class Context:
         b.csp_reconstruct(self._ctx, p, meas.data_ptr(), img.data_ptr(), _stream_ptr(stream, self.device))
         return img
 
+    # ---- dictionary learning (modified K-SVD) -------------------------------
+    def downsample(self, level: int, X: torch.Tensor, out: Optional[torch.Tensor] = None,
+                   stream=None) -> torch.Tensor:
+        """W_level applied to level-0 vectors X [N, N0] (csp_downsample)."""
+        X = X.contiguous()
+        assert X.dtype == torch.float32 and X.is_cuda
+        fy, fx, sy, sx = self.geometry[5][level]
+        n_low = X.shape[1] // (fy * fx * sy * sx)
+        if out is None:
+            out = torch.empty((X.shape[0], n_low), dtype=torch.float32, device=self.device)
+        b.csp_downsample(self._ctx, level, X.data_ptr(), X.shape[0], out.data_ptr(), _stream_ptr(stream, self.device))
+        return out
+
+    def ksvd_update(self, D: torch.Tensor, X: torch.Tensor, sup: torch.Tensor, coef: torch.Tensor,
+                    keff: torch.Tensor, replace_unused: bool = False, repl_parent: Optional[torch.Tensor] = None,
+                    repl_support: Optional[torch.Tensor] = None, err_out: Optional[torch.Tensor] = None,
+                    stream=None) -> None:
+        """One K-SVD dictionary-update sweep in place on D [T, M] and coef
+        [N, Kmax] (csp_ksvd_update); err_out (float32 [1]) receives
+        ||X - D S||_F^2 after the sweep."""
+        for t in (D, X, sup, coef, keff):
+            assert t.is_cuda and t.is_contiguous()
+        T, M = D.shape
+        Kc = int(repl_support.shape[1]) if repl_support is not None else 0
+        b.csp_ksvd_update(self._ctx, D.data_ptr(), int(M), int(T), X.data_ptr(), int(X.shape[0]), sup.data_ptr(),
+                          coef.data_ptr(), keff.data_ptr(), int(sup.shape[1]), int(bool(replace_unused)),
+                          repl_parent.data_ptr() if repl_parent is not None else None,
+                          repl_support.data_ptr() if repl_support is not None else None, Kc,
+                          err_out.data_ptr() if err_out is not None else None, _stream_ptr(stream, self.device))
+
+    def ksvd_init_atoms(self, D: torch.Tensor, X: torch.Tensor, u: torch.Tensor,
+                        parent: Optional[torch.Tensor] = None, sup_low: Optional[torch.Tensor] = None,
+                        keff_low: Optional[torch.Tensor] = None, T_low: int = 0, stream=None) -> None:
+        """Initialisation picks (csp_ksvd_init_atoms); u: float64 [T] on the device."""
+        assert u.dtype == torch.float64 and u.is_cuda
+        T, M = D.shape
+        Kc = int(sup_low.shape[1]) if sup_low is not None else 0
+        b.csp_ksvd_init_atoms(self._ctx, D.data_ptr(), int(M), int(T), X.data_ptr(), int(X.shape[0]),
+                              parent.data_ptr() if parent is not None else None,
+                              sup_low.data_ptr() if sup_low is not None else None,
+                              keff_low.data_ptr() if keff_low is not None else None, Kc, int(T_low),
+                              u.data_ptr(), _stream_ptr(stream, self.device))
+
     def reconstruct_host(self, meas: np.ndarray, img: np.ndarray, mode: str = "cross_scale",
                          precision: str = "fp32", K: Sequence[int] = (), Kmax: Optional[int] = None,
                          stream=None) -> np.ndarray:

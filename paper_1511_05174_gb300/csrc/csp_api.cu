@@ -109,7 +109,7 @@ csp_status ws_get_t(csp_ctx *ctx, Workspace &W, int slot, size_t count, T **out)
 
 const char *const kKernelNames[KK_COUNT] = {"extract", "downsample", "prepare", "omp_init", "proxy_fp32",
                                             "proxy_bf16", "omp_update", "restricted", "aggregate", "lift",
-                                            "omp_fused"};
+                                            "omp_fused", "ksvd_sort", "ksvd_sweep"};
 
 cudaEvent_t pool_event(csp_ctx *ctx) {
   if (!ctx->ev_pool.empty()) {
@@ -160,6 +160,7 @@ enum Slot {
   WS_LV_Y = WS_LV_KEFF + CSP_MAX_LEVELS,
   WS_XH = WS_LV_Y + CSP_MAX_LEVELS,
   WS_SCRATCH, WS_LIFT, WS_LIFTBF, WS_PPC_A, WS_PPC_INV, WS_PART, WS_KEYS,
+  WS_KS_R, WS_KS_RN2, WS_KS_XN2, WS_KS_TAKEN, WS_KS_HIST, WS_KS_OFF, WS_KS_SEG, WS_KS_ERR,
   WS_COUNT
 };
 
@@ -784,6 +785,40 @@ using csp::graph_key;
 using csp::reconstruct_core;
 using csp::reconstruct_buffers;
 
+namespace csp {
+// Support checks and the by-atom sort of a [N][K] support array (K-SVD sweep
+// and initialisation); synchronises `s` to read the device checks.
+csp_status ksvd_sort(csp_ctx *ctx, const float *D, int M, int T, const float *X, int N, const int32_t *sup,
+                     const float *coef, const int8_t *keff, int K, bool resid, int **off, int32_t **seg,
+                     float **R, float **rn2, float **xn2, cudaStream_t s) {
+  const int C = ksvd_chunks(N);
+  int *hist = nullptr;
+  unsigned *err = nullptr;
+  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_HIST, (size_t)std::max(C, 1) * T, &hist));
+  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_OFF, (size_t)T + 1, off));
+  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_SEG, (size_t)std::max<int64_t>((int64_t)N * K, 1), seg));
+  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_ERR, 1, &err));
+  if (resid) {
+    CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_R, (size_t)std::max(N, 1) * M, R));
+    CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_RN2, (size_t)std::max(N, 1), rn2));
+    CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_XN2, (size_t)std::max(N, 1), xn2));
+  }
+  CSP_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(unsigned), s));
+  run(ctx, KK_KSVD_SORT, s, 1, [&] {
+    launch_ksvd_sort(D, M, T, X, N, sup, coef, keff, K, resid ? *R : nullptr, resid ? *rn2 : nullptr,
+                     resid ? *xn2 : nullptr, hist, *off, *seg, err, s);
+  });
+  CSP_CUDA(ctx, cudaGetLastError());
+  unsigned herr = 0;
+  CSP_CUDA(ctx, cudaMemcpyAsync(&herr, err, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CSP_CUDA(ctx, cudaStreamSynchronize(s));
+  if (herr & 1) return fail(ctx, CSP_ERR_INVALID, "k_eff outside [0, K]");
+  if (herr & 2) return fail(ctx, CSP_ERR_INVALID, "support entry outside [0, T)");
+  if (herr & 4) return fail(ctx, CSP_ERR_INVALID, "an atom appears twice in one support");
+  return CSP_OK;
+}
+}  // namespace csp
+
 extern "C" {
 
 csp_status csp_create(csp_ctx **out, int device, size_t mem_budget_bytes) {
@@ -1390,6 +1425,92 @@ csp_status csp_profile_read(csp_ctx *ctx, csp_kernel_time *out, int cap, int *n_
   if (n_out) *n_out = n;
   if (reset)
     for (int k = 0; k < KK_COUNT; ++k) { ctx->launches[k] = 0; ctx->prof_ms[k] = 0.0; }
+  return CSP_OK;
+}
+
+// ---- Dictionary learning ----
+
+csp_status csp_downsample(csp_ctx *ctx, int level, const float *X, int64_t N, float *X_low, void *stream) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (!ctx->has_geom) return fail(ctx, CSP_ERR_NOT_READY, "geometry not set");
+  if (level < 1 || level >= ctx->geom.n_levels) return fail(ctx, CSP_ERR_INVALID, "level must be in 1 .. n_levels - 1");
+  if (N < 0 || N > INT32_MAX) return fail(ctx, CSP_ERR_INVALID, "N out of range");
+  if (N > 0 && (!X || !X_low)) return fail(ctx, CSP_ERR_INVALID, "NULL buffer");
+  DeviceGuard dg(ctx->device);
+  run(ctx, KK_DOWNSAMPLE, (cudaStream_t)stream, N, [&] {
+    launch_downsample(ctx->gd, level, X, X_low, N, (cudaStream_t)stream);
+  });
+  CSP_CUDA(ctx, cudaGetLastError());
+  return CSP_OK;
+}
+
+
+csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X, int64_t N, const int32_t *support,
+                           float *coef, const int8_t *k_eff, int Kmax, int replace_unused,
+                           const int32_t *repl_parent, const int32_t *repl_support, int Kc, float *err_out,
+                           void *stream) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (M < 1 || M > 192) return fail(ctx, M < 1 ? CSP_ERR_INVALID : CSP_ERR_UNSUPPORTED, "M must be in 1 .. 192");
+  if (T < 1 || T > 32768) return fail(ctx, CSP_ERR_INVALID, "T must be in 1 .. 32768");
+  if (Kmax < 1 || Kmax > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "Kmax must be in 1 .. CSP_MAX_K");
+  if (N < 0 || N * Kmax > INT32_MAX) return fail(ctx, CSP_ERR_INVALID, "N * Kmax must be below 2^31");
+  if (replace_unused != 0 && replace_unused != 1) return fail(ctx, CSP_ERR_INVALID, "replace_unused must be 0 or 1");
+  if ((repl_parent == nullptr) != (repl_support == nullptr))
+    return fail(ctx, CSP_ERR_INVALID, "repl_parent and repl_support go together");
+  if (repl_support && (Kc < 1 || N * Kc > INT32_MAX)) return fail(ctx, CSP_ERR_INVALID, "Kc out of range");
+  if (!D || (N > 0 && (!X || !support || !coef || !k_eff))) return fail(ctx, CSP_ERR_INVALID, "NULL buffer");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = (int)N;
+  int *off = nullptr;
+  int32_t *seg = nullptr;
+  float *R = nullptr, *rn2 = nullptr, *xn2 = nullptr;
+  uint8_t *taken = nullptr;
+  CSP_TRY(ksvd_sort(ctx, D, M, T, X, n, support, coef, k_eff, Kmax, true, &off, &seg, &R, &rn2, &xn2, s));
+  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_TAKEN, (size_t)std::max(n, 1), &taken));
+  CSP_CUDA(ctx, cudaMemsetAsync(taken, 0, (size_t)std::max(n, 1), s));
+  cudaError_t le = cudaSuccess;
+  run(ctx, KK_KSVD_SWEEP, s, 1, [&] {
+    le = launch_ksvd_sweep(D, M, T, X, n, coef, Kmax, off, seg, R, rn2, xn2, taken, replace_unused, repl_parent,
+                           repl_support, Kc, s);
+  });
+  if (le != cudaSuccess) return fail(ctx, CSP_ERR_CUDA, std::string("K-SVD sweep launch: ") + cudaGetErrorString(le));
+  if (err_out) {
+    if (n > 0) launch_ksvd_sum(rn2, n, err_out, s);
+    else CSP_CUDA(ctx, cudaMemsetAsync(err_out, 0, sizeof(float), s));
+  }
+  CSP_CUDA(ctx, cudaGetLastError());
+  CSP_CUDA(ctx, cudaStreamSynchronize(s));
+  return CSP_OK;
+}
+
+csp_status csp_ksvd_init_atoms(csp_ctx *ctx, float *D, int M, int T, const float *X, int64_t N,
+                               const int32_t *parent, const int32_t *support_low, const int8_t *keff_low, int Kc,
+                               int T_low, const double *u, void *stream) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (M < 1 || T < 1) return fail(ctx, CSP_ERR_INVALID, "M and T must be positive");
+  if (N < 1 || N > INT32_MAX) return fail(ctx, CSP_ERR_INVALID, "N must be in 1 .. 2^31 - 1");
+  if (!D || !X || !u) return fail(ctx, CSP_ERR_INVALID, "NULL buffer");
+  if (parent && (!support_low || !keff_low || Kc < 1 || Kc > CSP_MAX_K || T_low < 1 || T_low > 32768 ||
+                 N * Kc > INT32_MAX))
+    return fail(ctx, CSP_ERR_INVALID, "parent needs support_low, keff_low, Kc in 1 .. CSP_MAX_K and T_low");
+  DeviceGuard dg(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int *off = nullptr;
+  int32_t *seg = nullptr;
+  if (parent) {
+    // parent[t] must name a coarse atom: checked on the host copy
+    std::vector<int32_t> hp(T);
+    CSP_CUDA(ctx, cudaMemcpyAsync(hp.data(), parent, (size_t)T * 4, cudaMemcpyDeviceToHost, s));
+    CSP_CUDA(ctx, cudaStreamSynchronize(s));
+    for (int t = 0; t < T; ++t)
+      if (hp[t] < 0 || hp[t] >= T_low) return fail(ctx, CSP_ERR_INVALID, "parent entry outside [0, T_low)");
+    CSP_TRY(ksvd_sort(ctx, nullptr, M, T_low, nullptr, (int)N, support_low, nullptr, keff_low, Kc, false, &off, &seg,
+                      nullptr, nullptr, nullptr, s));
+  }
+  run(ctx, KK_KSVD_SORT, s, 1, [&] { launch_ksvd_init(D, M, T, X, (int)N, parent, off, seg, Kc, u, s); });
+  CSP_CUDA(ctx, cudaGetLastError());
+  CSP_CUDA(ctx, cudaStreamSynchronize(s));
   return CSP_OK;
 }
 

@@ -90,7 +90,7 @@ struct Workspace {
 
 enum KernelKind {
   KK_EXTRACT, KK_DOWNSAMPLE, KK_PREP, KK_INIT, KK_PROXY_FP32, KK_PROXY_BF16, KK_UPDATE, KK_RESTRICTED,
-  KK_AGGREGATE, KK_LIFT, KK_FUSED, KK_COUNT
+  KK_AGGREGATE, KK_LIFT, KK_FUSED, KK_KSVD_SORT, KK_KSVD_SWEEP, KK_COUNT
 };
 struct ProfRec {
   int kind;
@@ -315,6 +315,27 @@ bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
 void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
                           const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int32_t *child_off,
                           const int32_t *child_idx, int cap, int64_t B, float *Ac, float *invc, cudaStream_t s);
+
+// ---- K-SVD dictionary update and initialisation (k_ksvd.cu) ----
+// Shared memory of the sweep kernel for dimension M (M <= 192).
+size_t ksvd_sweep_smem_bytes(int M);
+// Counting chunks of N signals (rows of the [chunks][T] histogram).
+int ksvd_chunks(int64_t N);
+// Residuals R = X - D S, their squared norms rn2 and those of X (xn2), support
+// checks (err bits 1: k_eff range, 2: atom range, 4: repeated atom) and the
+// stable counting sort of the support slots by atom: off[T + 1], seg[slots].
+// R == nullptr: checks and sort only (D, X, coef, rn2, xn2 unused).
+void launch_ksvd_sort(const float *D, int M, int T, const float *X, int N, const int32_t *sup, const float *coef,
+                      const int8_t *keff, int Kmax, float *R, float *rn2, float *xn2, int *hist, int *off,
+                      int32_t *seg, unsigned *err, cudaStream_t s);
+// The sequential atom sweep (one thread-block cluster).
+cudaError_t launch_ksvd_sweep(float *D, int M, int T, const float *X, int N, float *coef, int Kmax, const int *off,
+                              const int32_t *seg, float *R, float *rn2, const float *xn2, uint8_t *taken, int replace,
+                              const int32_t *rparent, const int32_t *rsup, int Kc, cudaStream_t s);
+void launch_ksvd_sum(const float *rn2, int N, float *out, cudaStream_t s);
+// Initialisation picks; off == nullptr: from all N signals.
+void launch_ksvd_init(float *D, int M, int T, const float *X, int N, const int32_t *parent, const int *off,
+                      const int32_t *seg, int Kc, const double *u, cudaStream_t s);
 
 // ---- solve entry points shared by csp_solve and the serving engine (csp_api.cu) ----
 csp_status prepare_model(csp_ctx *ctx, cudaStream_t s);                       // effective dictionaries etc.
