@@ -276,7 +276,7 @@ csp_status csp_downsample(csp_ctx *ctx, int level, const float *X, int64_t N, fl
  *   supports, -1 padded), the signals whose coarse support holds the atom's
  *   parent.  replace_unused = 0: unused atoms keep their value.
  * err_out: DEVICE float32 [1] or NULL; receives ||X - D S||_F^2 after the sweep.
- * Limits: 1 <= M <= 192 (else CSP_ERR_UNSUPPORTED), T <= 32768,
+ * Limits: 1 <= M <= 192 and T <= 4096 (else CSP_ERR_UNSUPPORTED),
  *   N * Kmax < 2^31.  Errors found on the device (k_eff outside [0, Kmax],
  *   atom id outside [0, T), a repeated atom) return CSP_ERR_INVALID before D
  *   or coef change.  Deterministic.  Synchronous: returns when the sweep is
@@ -285,6 +285,12 @@ csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X,
                            const int32_t *support, float *coef, const int8_t *k_eff, int Kmax,
                            int replace_unused, const int32_t *repl_parent, const int32_t *repl_support,
                            int Kc, float *err_out, void *stream);
+
+/* Counters of the last csp_ksvd_update on this context: power_steps = the
+ * power-method steps summed over the visited atoms (a step is one product
+ * with E_k E_k^T; at most 1000 per atom), replaced = atoms replaced by
+ * heuristics 3-4.  Either pointer may be NULL. */
+csp_status csp_ksvd_stats_get(csp_ctx *ctx, int64_t *power_steps, int64_t *replaced);
 
 /* Initialisation picks of the modified K-SVD.  Atom t = x_i / ||x_i|| with
  * i = item floor(u_t n) of a pool of n signals in ascending order: all N

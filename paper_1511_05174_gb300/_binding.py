@@ -40,7 +40,7 @@ EXPORTS = ("csp_create", "csp_destroy", "csp_last_error", "csp_set_geometry", "c
            "csp_submit", "csp_poll", "csp_wait", "csp_job_info_get", "csp_job_release",
            "csp_server_pause", "csp_set_aggregate_path", "csp_set_top_level_form",
            "csp_set_wait_test", "csp_set_graph_mode", "csp_set_pipeline", "csp_reconstruct",
-           "csp_downsample", "csp_ksvd_update", "csp_ksvd_init_atoms")
+           "csp_downsample", "csp_ksvd_update", "csp_ksvd_init_atoms", "csp_ksvd_stats_get")
 
 
 class csp_geometry(ctypes.Structure):
@@ -154,6 +154,7 @@ def load_library(path: str = LIB_PATH):
         "csp_downsample": (i, [vp, i, vp, ctypes.c_int64, vp, vp]),
         "csp_ksvd_update": (i, [vp, vp, i, i, vp, ctypes.c_int64, vp, vp, vp, i, i, vp, vp, i, vp, vp]),
         "csp_ksvd_init_atoms": (i, [vp, vp, i, i, vp, ctypes.c_int64, vp, vp, vp, i, i, vp, vp]),
+        "csp_ksvd_stats_get": (i, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -368,3 +369,9 @@ def csp_ksvd_init_atoms(ctx, D_ptr: int, M: int, T: int, X_ptr: int, N: int, par
                         keff_low_ptr, Kc: int, T_low: int, u_ptr: int, stream: int = 0) -> None:
     check(load_library().csp_ksvd_init_atoms(ctx, D_ptr, M, T, X_ptr, N, parent_ptr, sup_low_ptr, keff_low_ptr,
                                              Kc, T_low, u_ptr, stream), ctx)
+
+
+def csp_ksvd_stats_get(ctx):
+    steps, rep = ctypes.c_int64(), ctypes.c_int64()
+    check(load_library().csp_ksvd_stats_get(ctx, ctypes.byref(steps), ctypes.byref(rep)), ctx)
+    return int(steps.value), int(rep.value)

@@ -257,6 +257,10 @@ class Context:
                           repl_support.data_ptr() if repl_support is not None else None, Kc,
                           err_out.data_ptr() if err_out is not None else None, _stream_ptr(stream, self.device))
 
+    def ksvd_stats(self):
+        """(power-method steps, replaced atoms) of the last ksvd_update."""
+        return b.csp_ksvd_stats_get(self._ctx)
+
     def ksvd_init_atoms(self, D: torch.Tensor, X: torch.Tensor, u: torch.Tensor,
                         parent: Optional[torch.Tensor] = None, sup_low: Optional[torch.Tensor] = None,
                         keff_low: Optional[torch.Tensor] = None, T_low: int = 0, stream=None) -> None:

@@ -160,7 +160,7 @@ enum Slot {
   WS_LV_Y = WS_LV_KEFF + CSP_MAX_LEVELS,
   WS_XH = WS_LV_Y + CSP_MAX_LEVELS,
   WS_SCRATCH, WS_LIFT, WS_LIFTBF, WS_PPC_A, WS_PPC_INV, WS_PART, WS_KEYS,
-  WS_KS_R, WS_KS_RN2, WS_KS_XN2, WS_KS_TAKEN, WS_KS_HIST, WS_KS_OFF, WS_KS_SEG, WS_KS_ERR,
+  WS_KS_R, WS_KS_RN2, WS_KS_XN2, WS_KS_TAKEN, WS_KS_HIST, WS_KS_OFF, WS_KS_SEG, WS_KS_ERR, WS_KS_STATS,
   WS_COUNT
 };
 
@@ -789,13 +789,13 @@ namespace csp {
 // Support checks and the by-atom sort of a [N][K] support array (K-SVD sweep
 // and initialisation); synchronises `s` to read the device checks.
 csp_status ksvd_sort(csp_ctx *ctx, const float *D, int M, int T, const float *X, int N, const int32_t *sup,
-                     const float *coef, const int8_t *keff, int K, bool resid, int **off, int32_t **seg,
+                     const float *coef, const int8_t *keff, int K, int split, bool resid, int **off, int32_t **seg,
                      float **R, float **rn2, float **xn2, cudaStream_t s) {
   const int C = ksvd_chunks(N);
   int *hist = nullptr;
   unsigned *err = nullptr;
-  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_HIST, (size_t)std::max(C, 1) * T, &hist));
-  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_OFF, (size_t)T + 1, off));
+  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_HIST, (size_t)std::max(C, 1) * T * split, &hist));
+  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_OFF, (size_t)T * split + 1, off));
   CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_SEG, (size_t)std::max<int64_t>((int64_t)N * K, 1), seg));
   CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_ERR, 1, &err));
   if (resid) {
@@ -805,7 +805,7 @@ csp_status ksvd_sort(csp_ctx *ctx, const float *D, int M, int T, const float *X,
   }
   CSP_CUDA(ctx, cudaMemsetAsync(err, 0, sizeof(unsigned), s));
   run(ctx, KK_KSVD_SORT, s, 1, [&] {
-    launch_ksvd_sort(D, M, T, X, N, sup, coef, keff, K, resid ? *R : nullptr, resid ? *rn2 : nullptr,
+    launch_ksvd_sort(D, M, T, X, N, sup, coef, keff, K, split, resid ? *R : nullptr, resid ? *rn2 : nullptr,
                      resid ? *xn2 : nullptr, hist, *off, *seg, err, s);
   });
   CSP_CUDA(ctx, cudaGetLastError());
@@ -1451,7 +1451,8 @@ csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X,
                            void *stream) {
   if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
   if (M < 1 || M > 192) return fail(ctx, M < 1 ? CSP_ERR_INVALID : CSP_ERR_UNSUPPORTED, "M must be in 1 .. 192");
-  if (T < 1 || T > 32768) return fail(ctx, CSP_ERR_INVALID, "T must be in 1 .. 32768");
+  if (T < 1) return fail(ctx, CSP_ERR_INVALID, "T must be positive");
+  if (T > 4096) return fail(ctx, CSP_ERR_UNSUPPORTED, "T must be at most 4096");
   if (Kmax < 1 || Kmax > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "Kmax must be in 1 .. CSP_MAX_K");
   if (N < 0 || N * Kmax > INT32_MAX) return fail(ctx, CSP_ERR_INVALID, "N * Kmax must be below 2^31");
   if (replace_unused != 0 && replace_unused != 1) return fail(ctx, CSP_ERR_INVALID, "replace_unused must be 0 or 1");
@@ -1466,21 +1467,35 @@ csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X,
   int32_t *seg = nullptr;
   float *R = nullptr, *rn2 = nullptr, *xn2 = nullptr;
   uint8_t *taken = nullptr;
-  CSP_TRY(ksvd_sort(ctx, D, M, T, X, n, support, coef, k_eff, Kmax, true, &off, &seg, &R, &rn2, &xn2, s));
+  CSP_TRY(ksvd_sort(ctx, D, M, T, X, n, support, coef, k_eff, Kmax, ksvd_owner_split(), true, &off, &seg, &R, &rn2,
+                    &xn2, s));
+  unsigned long long *st = nullptr;
   CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_TAKEN, (size_t)std::max(n, 1), &taken));
+  CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_STATS, 2, &st));
   CSP_CUDA(ctx, cudaMemsetAsync(taken, 0, (size_t)std::max(n, 1), s));
   cudaError_t le = cudaSuccess;
   run(ctx, KK_KSVD_SWEEP, s, 1, [&] {
     le = launch_ksvd_sweep(D, M, T, X, n, coef, Kmax, off, seg, R, rn2, xn2, taken, replace_unused, repl_parent,
-                           repl_support, Kc, s);
+                           repl_support, Kc, st, s);
   });
   if (le != cudaSuccess) return fail(ctx, CSP_ERR_CUDA, std::string("K-SVD sweep launch: ") + cudaGetErrorString(le));
   if (err_out) {
     if (n > 0) launch_ksvd_sum(rn2, n, err_out, s);
     else CSP_CUDA(ctx, cudaMemsetAsync(err_out, 0, sizeof(float), s));
   }
+  unsigned long long hst[2] = {0, 0};
+  CSP_CUDA(ctx, cudaMemcpyAsync(hst, st, sizeof(hst), cudaMemcpyDeviceToHost, s));
   CSP_CUDA(ctx, cudaGetLastError());
   CSP_CUDA(ctx, cudaStreamSynchronize(s));
+  ctx->ksvd_steps = (int64_t)hst[0];
+  ctx->ksvd_replaced = (int64_t)hst[1];
+  return CSP_OK;
+}
+
+csp_status csp_ksvd_stats_get(csp_ctx *ctx, int64_t *power_steps, int64_t *replaced) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (power_steps) *power_steps = ctx->ksvd_steps;
+  if (replaced) *replaced = ctx->ksvd_replaced;
   return CSP_OK;
 }
 
@@ -1505,8 +1520,8 @@ csp_status csp_ksvd_init_atoms(csp_ctx *ctx, float *D, int M, int T, const float
     CSP_CUDA(ctx, cudaStreamSynchronize(s));
     for (int t = 0; t < T; ++t)
       if (hp[t] < 0 || hp[t] >= T_low) return fail(ctx, CSP_ERR_INVALID, "parent entry outside [0, T_low)");
-    CSP_TRY(ksvd_sort(ctx, nullptr, M, T_low, nullptr, (int)N, support_low, nullptr, keff_low, Kc, false, &off, &seg,
-                      nullptr, nullptr, nullptr, s));
+    CSP_TRY(ksvd_sort(ctx, nullptr, M, T_low, nullptr, (int)N, support_low, nullptr, keff_low, Kc, 1, false, &off,
+                      &seg, nullptr, nullptr, nullptr, s));
   }
   run(ctx, KK_KSVD_SORT, s, 1, [&] { launch_ksvd_init(D, M, T, X, (int)N, parent, off, seg, Kc, u, s); });
   CSP_CUDA(ctx, cudaGetLastError());

@@ -164,6 +164,7 @@ struct csp_ctx {
   bool pipeline = true;        // csp_set_pipeline
   bool recon_synth = false;    // the recorded / last csp_reconstruct fused the synthesis
   bool last_synth = false;     // reported by csp_solve_stats_get
+  int64_t ksvd_steps = 0, ksvd_replaced = 0;  // last csp_ksvd_update (csp_ksvd_stats_get)
   std::vector<csp::ProfRec> pending;
   std::vector<cudaEvent_t> ev_pool;
   // All device allocations (for the memory budget and destroy).
@@ -319,19 +320,25 @@ void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const 
 // ---- K-SVD dictionary update and initialisation (k_ksvd.cu) ----
 // Shared memory of the sweep kernel for dimension M (M <= 192).
 size_t ksvd_sweep_smem_bytes(int M);
-// Counting chunks of N signals (rows of the [chunks][T] histogram).
+// Ranks of the sweep's cluster: the sort for the sweep splits every atom's
+// slots by owner rank i mod ksvd_owner_split().
+int ksvd_owner_split();
+// Counting chunks of N signals (rows of the [chunks][T * split] histogram).
 int ksvd_chunks(int64_t N);
 // Residuals R = X - D S, their squared norms rn2 and those of X (xn2), support
 // checks (err bits 1: k_eff range, 2: atom range, 4: repeated atom) and the
-// stable counting sort of the support slots by atom: off[T + 1], seg[slots].
+// stable counting sort of the support slots by key atom * split + i % split:
+// off[T * split + 1], seg[slots] (ascending i within a key).
 // R == nullptr: checks and sort only (D, X, coef, rn2, xn2 unused).
 void launch_ksvd_sort(const float *D, int M, int T, const float *X, int N, const int32_t *sup, const float *coef,
-                      const int8_t *keff, int Kmax, float *R, float *rn2, float *xn2, int *hist, int *off,
+                      const int8_t *keff, int Kmax, int split, float *R, float *rn2, float *xn2, int *hist, int *off,
                       int32_t *seg, unsigned *err, cudaStream_t s);
-// The sequential atom sweep (one thread-block cluster).
+// The sequential atom sweep (one thread-block cluster); stats[0] = power-method
+// steps, stats[1] = replaced atoms.
 cudaError_t launch_ksvd_sweep(float *D, int M, int T, const float *X, int N, float *coef, int Kmax, const int *off,
                               const int32_t *seg, float *R, float *rn2, const float *xn2, uint8_t *taken, int replace,
-                              const int32_t *rparent, const int32_t *rsup, int Kc, cudaStream_t s);
+                              const int32_t *rparent, const int32_t *rsup, int Kc, unsigned long long *stats,
+                              cudaStream_t s);
 void launch_ksvd_sum(const float *rn2, int N, float *out, cudaStream_t s);
 // Initialisation picks; off == nullptr: from all N signals.
 void launch_ksvd_init(float *D, int M, int T, const float *X, int N, const int32_t *parent, const int *off,

@@ -1464,7 +1464,8 @@ template <typename F>
 bool dispatch_gram(int M, int width, F &&f) {
   if (M % 4 || M > 256) return false;
   const int G = gram_group(M, width);
-  const int nch = (M / 4 + G - 1) / G;
+  int nch = (M / 4 + G - 1) / G;  // chunks of four elements per lane; lanes past M hold zeros
+  if (nch == 3) nch = 4;          // (instantiated for 1, 2 and 4 chunks)
   using std::integral_constant;
   switch (G * 8 + nch) {
     case 4 * 8 + 1: f(integral_constant<int, 4>{}, integral_constant<int, 1>{}); break;

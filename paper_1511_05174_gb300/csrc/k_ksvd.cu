@@ -27,12 +27,12 @@
 //                        on global memory).
 //  4. ksvd_sweep_kernel  one thread-block cluster visits the atoms in order.
 //     Per atom: each CTA accumulates C_r = sum e_i e_i^T over the users it
-//     owns (i mod CL == rank), the partial Gram matrices meet through
-//     distributed shared memory (reduce-scatter, then all-gather, fixed rank
-//     order), every CTA runs the same power iteration on C = E_k E_k^T from
-//     d_old (identical inputs, identical result), and each CTA updates the
-//     coefficients and residuals of its own users.  Ownership by signal keeps
-//     every residual with one CTA, so atoms need two cluster barriers each.
+//     owns (i mod CL == rank); the power method on C = E_k E_k^T = sum_r C_r
+//     from d_old multiplies each C_r locally and adds the kCL products through
+//     distributed shared memory in rank order (one cluster barrier per step,
+//     identical vectors and decisions on every rank); each CTA then updates
+//     the coefficients and residuals of its own users.  Ownership by signal
+//     keeps every residual with one CTA: successive atoms exchange nothing else.
 //  5. ksvd_sum_kernel    ||X - D S||_F^2 after the sweep (optional).
 
 #include <cooperative_groups.h>
@@ -50,7 +50,6 @@ namespace {
 
 constexpr int kChunk = 256;       // signals per counting chunk
 constexpr int kCL = 8;            // CTAs of the sweep's cluster
-constexpr int kNB = 32;           // columns e_i staged per batch
 constexpr int kMaxIt = 1000;      // power-iteration cap per atom
 constexpr float kTol2 = 1.6e-11f; // converged when ||v_new - v||^2 <= (4e-6)^2
 
@@ -71,11 +70,12 @@ __device__ __forceinline__ float warp_sum(float s) {
 // 4 = an atom repeated within one support.  R == nullptr: counts and checks only.
 __global__ void ksvd_prep_kernel(const float *__restrict__ D, int M, int T, const float *__restrict__ X, int N,
                                  const int32_t *__restrict__ sup, const float *__restrict__ coef,
-                                 const int8_t *__restrict__ keff, int Kmax, float *__restrict__ R,
+                                 const int8_t *__restrict__ keff, int Kmax, int split, float *__restrict__ R,
                                  float *__restrict__ rn2, float *__restrict__ xn2, int *__restrict__ hist,
                                  unsigned *err) {
   extern __shared__ int h[];
-  for (int t = threadIdx.x; t < T; t += blockDim.x) h[t] = 0;
+  const int nkeys = T * split;
+  for (int t = threadIdx.x; t < nkeys; t += blockDim.x) h[t] = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int i0 = blockIdx.x * kChunk, i1 = min(N, i0 + kChunk);
@@ -90,7 +90,7 @@ __global__ void ksvd_prep_kernel(const float *__restrict__ D, int M, int T, cons
         bool dup = false;
         for (int j = 0; j < lane; ++j) dup |= sup[(size_t)i * Kmax + j] == a;
         if (dup) e |= 4;
-        atomicAdd(&h[a], 1);
+        atomicAdd(&h[a * split + i % split], 1);
       }
     }
     e = __reduce_or_sync(0xffffffffu, e);
@@ -113,10 +113,11 @@ __global__ void ksvd_prep_kernel(const float *__restrict__ D, int M, int T, cons
     if (lane == 0) { rn2[i] = rs; xn2[i] = xs; }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < T; t += blockDim.x) hist[(size_t)blockIdx.x * T + t] = h[t];
+  for (int t = threadIdx.x; t < nkeys; t += blockDim.x) hist[(size_t)blockIdx.x * nkeys + t] = h[t];
 }
 
-// 2. hist[c][t] <- users of atom t in chunks before c; off[t] = first slot of atom t.
+// 2. hist[c][t] <- slots of key t in chunks before c; off[t] = first slot of key t
+// (T here counts keys: atoms x owner ranks).
 __global__ void __launch_bounds__(1024) ksvd_scan_kernel(int *__restrict__ hist, int C, int T, int *__restrict__ off) {
   __shared__ int wsum[32];
   __shared__ int carry;
@@ -159,13 +160,14 @@ __global__ void __launch_bounds__(1024) ksvd_scan_kernel(int *__restrict__ hist,
   if (threadIdx.x == 0) off[T] = carry;
 }
 
-// 3. Stable counting sort of the slots q = i * Kmax + j by atom (one warp per chunk).
+// 3. Stable counting sort of the slots q = i * Kmax + j by key a * split + i % split
+// (atom a, owner rank i mod split; one warp per chunk).
 __global__ void ksvd_fill_kernel(const int32_t *__restrict__ sup, const int8_t *__restrict__ keff, int N, int Kmax,
-                                 int T, const int *__restrict__ hist, const int *__restrict__ off,
+                                 int T, int split, const int *__restrict__ hist, const int *__restrict__ off,
                                  int32_t *__restrict__ seg) {
   extern __shared__ int base[];
-  const int lane = threadIdx.x;
-  for (int t = lane; t < T; t += 32) base[t] = off[t] + hist[(size_t)blockIdx.x * T + t];
+  const int lane = threadIdx.x, nkeys = T * split;
+  for (int t = lane; t < nkeys; t += 32) base[t] = off[t] + hist[(size_t)blockIdx.x * nkeys + t];
   __syncwarp();
   const int i0 = blockIdx.x * kChunk, i1 = min(N, i0 + kChunk);
   const int q1 = i1 * Kmax;
@@ -177,7 +179,7 @@ __global__ void ksvd_fill_kernel(const int32_t *__restrict__ sup, const int8_t *
       const int k = keff[i];
       if (k >= 0 && k <= Kmax && j < k) {
         a = sup[q];
-        if (a < 0 || a >= T) a = -1;
+        a = (a < 0 || a >= T) ? -1 : a * split + i % split;
       }
     }
     const unsigned peers = __match_any_sync(0xffffffffu, a);
@@ -192,6 +194,28 @@ __global__ void ksvd_fill_kernel(const int32_t *__restrict__ sup, const int8_t *
   }
 }
 
+// TR consecutive floats of shared memory at p (16-byte aligned for TR % 4 == 0,
+// 8-byte aligned for TR % 2 == 0) with the widest loads that fit.
+template <int TR>
+__device__ __forceinline__ void lds_run(float (&o)[TR], const float *p) {
+  if constexpr (TR % 4 == 0) {
+#pragma unroll
+    for (int t = 0; t < TR / 4; ++t) {
+      const float4 v = reinterpret_cast<const float4 *>(p)[t];
+      o[4 * t] = v.x; o[4 * t + 1] = v.y; o[4 * t + 2] = v.z; o[4 * t + 3] = v.w;
+    }
+  } else if constexpr (TR % 2 == 0) {
+#pragma unroll
+    for (int t = 0; t < TR / 2; ++t) {
+      const float2 v = reinterpret_cast<const float2 *>(p)[t];
+      o[2 * t] = v.x; o[2 * t + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int t = 0; t < TR; ++t) o[t] = p[t];
+  }
+}
+
 struct SweepArgs {
   float *D;
   int M, T;
@@ -199,65 +223,106 @@ struct SweepArgs {
   int N;
   float *coef;
   int Kmax;
-  const int *off;
-  const int32_t *seg;
+  const int *off;          // [T * kCL + 1]: slots of (atom k, owner rank r) at off[k * kCL + r] ..
+  const int32_t *seg;      // slot ids q = i * Kmax + j, ascending i within each (k, r)
   float *R, *rn2;
   const float *xn2;
   uint8_t *taken;
   int replace;
   const int32_t *rparent, *rsup;
   int Kc;
+  unsigned long long *stats;  // [0] power-method steps, [1] replaced atoms
 };
 
 __host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
 
-// Shared-memory floats of the sweep for dimension M with `nt` threads.
-__host__ __device__ inline int sweep_smem_floats(int M, int MP, int nt) {
-  const int MM = M * M, RB = (MM + kCL - 1) / kCL;
-  return pad4(MM) + pad4(RB) + kNB * MP + 3 * pad4(M) + 128 + nt + 64;
+// Stage capacity (floats) of the e_i columns: kNB-free sizing by dimension.
+__host__ __device__ constexpr int stage_floats(int side) { return side == 16 ? 16384 : 12288; }
+
+// Shared-memory floats of the sweep: this rank's partial C ([M][M + 1]), the
+// exchanged products C_r v (2 x M),
+// share, the staged columns, the vectors and the slot lists.
+__host__ __device__ inline int sweep_smem_floats(int M, int MP, int side) {
+  const int CCP = pad4(M * (M + 1)), RB = 2 * pad4(M);
+  const int NB = stage_floats(side) / MP;
+  return CCP + RB + stage_floats(side) + 10 * pad4(M) + 128 + 6 * NB;
 }
 
 // 4. The sweep.  Threads form a SIDE x SIDE grid; thread (ty, tx) accumulates
 // the TR x TR tile of C at rows ty*TR.., columns tx*TR.. (SIDE*TR >= M).
+// Rank r of the cluster owns the signals i with i mod kCL == r: it reads and
+// writes only their residuals and coefficients, so the visits of successive
+// atoms need no exchange beyond the Gram matrix.
 template <int SIDE, int TR>
 __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepArgs a) {
   constexpr int NT = SIDE * SIDE, NW = NT / 32, MP = SIDE * TR;
+  constexpr int NB = stage_floats(SIDE) / MP;     // columns staged at once
   cg::cluster_group cl = cg::this_cluster();
-  const int rank = (int)cl.block_rank(), CL = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
   extern __shared__ float4 smem4[];
   float *sm = reinterpret_cast<float *>(smem4);
-  const int M = a.M, MM = M * M, RB = (MM + CL - 1) / CL, Kmax = a.Kmax;
-  float *Cb = sm;                        // [M][M] partial, then full E_k E_k^T
-  float *red = Cb + pad4(MM);            // [RB] this CTA's share of the reduced matrix
-  float *stage = red + pad4((MM + kCL - 1) / kCL);  // [kNB][MP] staged e_i
-  float *dold = stage + kNB * MP;        // [M] atom before the visit
-  float *v = dold + pad4(M);             // [M] power-iteration vector
-  float *y = v + pad4(M);                // [M] C v
-  float *scal = y + pad4(M);             // [128] flags, per-warp argmax scratch
-  int *ents = reinterpret_cast<int *>(scal + 128);  // [NT] compacted slots
-  int *wcnt = ents + NT;                 // [NW + 1]
+  const int M = a.M, LDC = M + 1, CCP = pad4(M * LDC), Kmax = a.Kmax;
+  float *Cb = sm;                        // [M][M + 1] this rank's partial C_r = sum e_i e_i^T
+  float *yx = Cb + CCP;                  // [2][pad4(M)] C_r v of the last two steps (read by all ranks)
+  float *stage = yx + 2 * pad4(M);       // [NB][MP] e_i of the staged users
+  float *dold0 = stage + stage_floats(SIDE), *dold1 = dold0 + pad4(M);  // atom before the visit (2 buffers)
+  float *const vb0 = dold0 + 2 * pad4(M), *const vb1 = dold0 + 3 * pad4(M);  // power-method vectors
+  float *ysum = dold0 + 4 * pad4(M);     // [M] C v = sum over ranks of C_r v
+  float *dd = dold0 + 5 * pad4(M);       // [M] squared change of each component
+  float *yp = dold0 + 6 * pad4(M);       // [4][M] partial sums of C v
+  float *scal = dold0 + 10 * pad4(M);    // [128] flags, per-warp argmax scratch
+  int *ents0 = reinterpret_cast<int *>(scal + 128), *ents1 = ents0 + NB;  // staged slot ids (2 buffers)
+  float *als0 = reinterpret_cast<float *>(ents1 + NB), *als1 = als0 + NB;  // their coefficients before the visit
+  int *rows0 = reinterpret_cast<int *>(als1 + NB), *rows1 = rows0 + NB;     // their signals i = q / Kmax
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int ty = tid / SIDE, tx = tid - ty * SIDE, r0 = ty * TR, c0 = tx * TR;
-  int *iflag = reinterpret_cast<int *>(scal);   // [0] converged, [1] zero matrix
-  float *slotv = scal + 8;                      // best replacement candidate of this CTA
+  float *slotv = scal + 8;                      // best replacement candidate of this rank
   int *sloti = reinterpret_cast<int *>(scal + 9);
   float *wv = scal + 32;                        // [32] per-warp best residual norm
   int *wi = reinterpret_cast<int *>(scal + 64); // [32] ... and its signal
+  unsigned long long steps = 0, replaced = 0;
+  unsigned gstep = 0;                   // power-method steps of this sweep (product buffer parity)
 
+  for (int q = tid; q < stage_floats(SIDE); q += NT) stage[q] = 0.f;  // padding rows stay zero
+  {  // slot ids, coefficients and atom of the first visit
+    const int br = a.off[rank], nr = a.off[rank + 1] - br;
+    for (int c = tid; c < min(nr, min(NB, NT)); c += NT) {
+      ents0[c] = a.seg[br + c];
+      als0[c] = a.coef[ents0[c]];
+      rows0[c] = ents0[c] / Kmax;
+    }
+    for (int m = tid; m < M; m += NT) dold0[m] = a.D[m];
+  }
+  __syncthreads();
   for (int k = 0; k < a.T; ++k) {
-    const int base = a.off[k], n = a.off[k + 1] - base;
-    for (int m = tid; m < M; m += NT) dold[m] = a.D[(size_t)k * M + m];
-    for (int q = tid; q < kNB * MP; q += NT) stage[q] = 0.f;
-    __syncthreads();
+    const int kb = a.off[k * kCL], nk = a.off[(k + 1) * kCL] - kb;
+    const int br = a.off[k * kCL + rank], nr = a.off[k * kCL + rank + 1] - br;
+    float *dold = (k & 1) ? dold1 : dold0;
+    int *ents = (k & 1) ? ents1 : ents0;
+    float *als = (k & 1) ? als1 : als0;
+    int *rows = (k & 1) ? rows1 : rows0;
+    // Prefetch of the next visit's slot ids, coefficients and atom: none of
+    // them changes during this visit (a slot belongs to one atom, D[k + 1] is
+    // written only by its own visit).  Stored after this visit.
+    int pq = -1;
+    float pa = 0.f, pd = 0.f;
+    if (k + 1 < a.T) {
+      const int br1 = a.off[(k + 1) * kCL + rank], nr1 = a.off[(k + 1) * kCL + rank + 1] - br1;
+      if (tid < min(nr1, NB)) {
+        pq = a.seg[br1 + tid];
+        pa = a.coef[pq];
+      }
+      if (tid < M) pd = a.D[(size_t)(k + 1) * M + tid];
+    }
 
-    if (n == 0) {
+    if (nk == 0) {
       // Heuristics 3 / 4: the unused atom becomes the eligible signal with the
       // largest residual norm (ties: lowest index); the signal is then taken.
-      if (!a.replace) continue;
+      if (!a.replace) goto next;
       float bv = -1.f;
       int bi = -1;
       const int pk = a.rparent ? a.rparent[k] : -1;
-      for (int i = rank + CL * tid; i < a.N; i += CL * NT) {
+      for (int i = rank + kCL * tid; i < a.N; i += kCL * NT) {
         if (a.taken[i] || !(a.xn2[i] > 0.f)) continue;
         if (a.rparent) {
           bool ok = false;
@@ -289,14 +354,15 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
       cl.sync();
       float gv = -1.f;
       int gi = -1;
-      for (int q = 0; q < CL; ++q) {
+      for (int q = 0; q < kCL; ++q) {
         const float ov = *cl.map_shared_rank(slotv, q);
         const int oi = *cl.map_shared_rank(sloti, q);
         if (oi >= 0 && (ov > gv || (ov == gv && (gi < 0 || oi < gi)))) { gv = ov; gi = oi; }
       }
       cl.sync();
       if (gi >= 0) {
-        if (tid == 0 && gi % CL == rank) a.taken[gi] = 1;
+        ++replaced;
+        if (tid == 0 && gi % kCL == rank) a.taken[gi] = 1;
         if (rank == 0 && warp == 0) {
           float s = 0.f;
           for (int m = lane; m < M; m += 32) {
@@ -307,159 +373,231 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
           for (int m = lane; m < M; m += 32) a.D[(size_t)k * M + m] = a.X[(size_t)gi * M + m] / nrm;
         }
       }
-      __syncthreads();
-      continue;
+      goto next;
     }
 
-    // ---- partial C over the users this CTA owns, in slot order ----
+    {  // ---- partial C = sum e_i e_i^T over this rank's users, in slot order ----
+    // e_i = r_i + alpha_ik d_old for staged columns 0 .. nb-1: a warp per
+    // column, SU columns' loads in flight per warp.
+    auto stage_cols = [&](int nb) {
+      constexpr int SU = NT >= 1024 ? 2 : 4, PL = (MP + 31) / 32;
+      for (int cb = warp; cb < nb; cb += SU * NW) {
+        float e[SU][PL];
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+          const int c = cb + u * NW;
+          const float *rr = a.R + (size_t)rows[c < nb ? c : 0] * M;
+          const float al = als[c < nb ? c : 0];
+#pragma unroll
+          for (int t = 0; t < PL; ++t) {
+            const int m = lane + 32 * t;
+            e[u][t] = (c < nb && m < M) ? fmaf(al, dold[m], rr[m]) : 0.f;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < SU; ++u) {
+          const int c = cb + u * NW;
+          if (c < nb)
+#pragma unroll
+            for (int t = 0; t < PL; ++t) {
+              const int m = lane + 32 * t;
+              if (m < M) stage[c * MP + m] = e[u][t];
+            }
+        }
+      }
+    };
     float acc[TR][TR];
 #pragma unroll
     for (int i = 0; i < TR; ++i)
 #pragma unroll
       for (int j = 0; j < TR; ++j) acc[i][j] = 0.f;
-    for (int p0 = 0; p0 < n; p0 += NT) {
-      const int p = p0 + tid;
-      int e = -1;
-      if (p < n) {
-        const int q = a.seg[base + p];
-        if ((q / Kmax) % CL == rank) e = q;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, e >= 0);
-      if (lane == 0) wcnt[warp] = __popc(bal);
-      __syncthreads();
-      if (tid == 0) {
-        int s = 0;
-        for (int w = 0; w < NW; ++w) { const int c = wcnt[w]; wcnt[w] = s; s += c; }
-        wcnt[NW] = s;
+    for (int b0 = 0; b0 < nr; b0 += NB) {
+      const int nb = min(NB, nr - b0);
+      for (int c = (b0 == 0 ? NT : 0) + tid; c < nb; c += NT) {   // the first NT of batch 0 are prefetched
+        const int q = a.seg[br + b0 + c];
+        ents[c] = q;
+        als[c] = a.coef[q];
+        rows[c] = q / Kmax;
       }
       __syncthreads();
-      if (e >= 0) ents[wcnt[warp] + __popc(bal & lanemask_lt())] = e;
+      stage_cols(nb);
       __syncthreads();
-      const int cnt = wcnt[NW];
-      for (int b0 = 0; b0 < cnt; b0 += kNB) {
-        const int nb = min(kNB, cnt - b0);
-        for (int q = tid; q < nb * M; q += NT) {
-          const int c = q / M, m = q - c * M;
-          const int s = ents[b0 + c];
-          const int i = s / Kmax;
-          stage[c * MP + m] = fmaf(a.coef[s], dold[m], a.R[(size_t)i * M + m]);
-        }
-        __syncthreads();
-        for (int c = 0; c < nb; ++c) {
-          const float *ec = stage + c * MP;
-          float er[TR], ek[TR];
+#pragma unroll 2
+      for (int c = 0; c < nb; ++c) {
+        const float *ec = stage + c * MP;
+        float er[TR], ek[TR];
+        lds_run<TR>(er, ec + r0);
+        lds_run<TR>(ek, ec + c0);
 #pragma unroll
-          for (int t = 0; t < TR; ++t) { er[t] = ec[r0 + t]; ek[t] = ec[c0 + t]; }
+        for (int i = 0; i < TR; ++i)
 #pragma unroll
-          for (int i = 0; i < TR; ++i)
-#pragma unroll
-            for (int j = 0; j < TR; ++j) acc[i][j] = fmaf(er[i], ek[j], acc[i][j]);
-        }
-        __syncthreads();
+          for (int j = 0; j < TR; ++j) acc[i][j] = fmaf(er[i], ek[j], acc[i][j]);
       }
+      if (b0 + NB < nr) __syncthreads();   // the last batch stays staged for the update
     }
 #pragma unroll
     for (int i = 0; i < TR; ++i)
 #pragma unroll
       for (int j = 0; j < TR; ++j)
-        if (r0 + i < M && c0 + j < M) Cb[(r0 + i) * M + c0 + j] = acc[i][j];
+        if (r0 + i < M && c0 + j < M) Cb[(r0 + i) * LDC + c0 + j] = acc[i][j];
 
-    // ---- C = sum over ranks (reduce-scatter, all-gather) ----
-    cl.sync();
-    {
-      const int e0 = rank * RB, e1 = min(MM, e0 + RB);
-      for (int el = e0 + tid; el < e1; el += NT) {
-        float s = 0.f;
-        for (int q = 0; q < CL; ++q) s += cl.map_shared_rank(Cb, q)[el];
-        red[el - e0] = s;
-      }
-    }
-    cl.sync();
-    for (int el = tid; el < MM; el += NT) {
-      const int q = el / RB;
-      Cb[el] = cl.map_shared_rank(red, q)[el - q * RB];
-    }
-    for (int m = tid; m < M; m += NT) v[m] = dold[m];
+    for (int m = tid; m < M; m += NT) vb0[m] = dold[m];
     __syncthreads();
 
-    // ---- leading eigenvector of C by the power method from d_old ----
+    // ---- leading eigenvector of C = sum_r C_r by the power method from d_old ----
+    // The ranks never form C: step t computes C_r v_t locally (thread (part,
+    // r) sums column range `part` of row r, read as column r of the symmetric
+    // C_r: consecutive lanes, consecutive banks), publishes it, and after one
+    // cluster barrier every rank adds the kCL products in rank order, so all
+    // ranks hold the same y = C v_t and take the same decisions.  v_{t+1} =
+    // y / ||y||; the change ||v_{t+1} - v_t||^2 is summed one step later; stop
+    // when it is <= kTol2.  The two product buffers alternate by step, so a
+    // rank may overwrite one only after every rank has passed the barrier that
+    // follows its reads (the alternation runs on across visits).
+    int cur = 0;
+    bool zero = false;
+    constexpr int PARTS = NT / MP >= 4 ? 4 : (NT / MP >= 2 ? 2 : 1);
+    const int CW = (M + PARTS - 1) / PARTS;
     for (int it = 0; it < kMaxIt; ++it) {
-      for (int r = warp; r < M; r += NW) {
-        float s = 0.f;
-        for (int c = lane; c < M; c += 32) s = fmaf(Cb[r * M + c], v[c], s);
-        s = warp_sum(s);
-        if (lane == 0) y[r] = s;
-      }
-      __syncthreads();
-      if (warp == 0) {
-        float s = 0.f;
-        for (int m = lane; m < M; m += 32) s = fmaf(y[m], y[m], s);
-        s = warp_sum(s);
-        int conv = 0, zero = 0;
-        if (!(s > 0.f)) {
-          zero = 1;
-        } else {
-          const float inv = 1.f / sqrtf(s);
-          float d2 = 0.f;
-          for (int m = lane; m < M; m += 32) {
-            const float nv = y[m] * inv;
-            const float d = nv - v[m];
-            d2 = fmaf(d, d, d2);
-            v[m] = nv;
-          }
-          d2 = warp_sum(d2);
-          conv = d2 <= kTol2;
+      const float *v = cur ? vb1 : vb0;
+      float *vn = cur ? vb0 : vb1;
+      float *yo = yx + (gstep & 1) * pad4(M);
+      ++gstep;
+      for (int t = tid; t < PARTS * M; t += NT) {
+        const int part = t / M, r = t - part * M;
+        const int ca = part * CW, cz = min(M, ca + CW);
+        float s0 = 0.f, s1 = 0.f;
+        int c = ca;
+        for (; c + 1 < cz; c += 2) {
+          s0 = fmaf(Cb[c * LDC + r], v[c], s0);
+          s1 = fmaf(Cb[(c + 1) * LDC + r], v[c + 1], s1);
         }
-        if (lane == 0) { iflag[0] = conv; iflag[1] = zero; }
+        if (c < cz) s0 = fmaf(Cb[c * LDC + r], v[c], s0);
+        yp[part * M + r] = s0 + s1;
       }
       __syncthreads();
-      const bool stop = iflag[0] | iflag[1];
+      for (int m = tid; m < M; m += NT) {
+        float ym = yp[m];
+#pragma unroll
+        for (int q = 1; q < PARTS; ++q) ym += yp[q * M + m];
+        yo[m] = ym;
+      }
+      cl.sync();
+      for (int m = tid; m < M; m += NT) {
+        float ym = 0.f;
+#pragma unroll
+        for (int q = 0; q < kCL; ++q) ym += cl.map_shared_rank(yo, q)[m];
+        ysum[m] = ym;
+      }
       __syncthreads();
-      if (stop) break;
+      float ss = 0.f, d2 = 0.f;
+      for (int m = lane; m < M; m += 32) {
+        ss = fmaf(ysum[m], ysum[m], ss);
+        if (it) d2 += dd[m];
+      }
+      ss = warp_sum(ss);
+      d2 = warp_sum(d2);
+      if (it && d2 <= kTol2) { steps += it; break; }   // v_t is converged
+      if (!(ss > 0.f)) { zero = true; steps += it; break; }
+      const float inv = 1.f / sqrtf(ss);
+      __syncthreads();                                  // every warp has read dd
+      for (int m = tid; m < M; m += NT) {
+        const float nv = ysum[m] * inv;
+        const float d = nv - v[m];
+        dd[m] = d * d;
+        vn[m] = nv;
+      }
+      __syncthreads();
+      cur ^= 1;
+      if (it == kMaxIt - 1) steps += kMaxIt;
     }
-    if (warp == 0) {  // sign: <d_new, d_old> >= 0
+    float *v = zero ? dold : (cur ? vb1 : vb0);
+    {  // sign: <d_new, d_old> >= 0 (every warp computes it; all agree)
       float s = 0.f;
       for (int m = lane; m < M; m += 32) s = fmaf(v[m], dold[m], s);
       s = warp_sum(s);
-      if (s < 0.f)
-        for (int m = lane; m < M; m += 32) v[m] = -v[m];
+      if (s < 0.f) {
+        __syncthreads();
+        for (int m = tid; m < M; m += NT) v[m] = -v[m];
+      }
+      __syncthreads();
     }
-    __syncthreads();
     if (rank == 0)
       for (int m = tid; m < M; m += NT) a.D[(size_t)k * M + m] = v[m];
 
-    // ---- coefficients E_k^T d_k and residuals of the users this CTA owns ----
-    for (int p = warp; p < n; p += NW) {
-      const int q = a.seg[base + p];
-      const int i = q / Kmax;
-      if (i % CL != rank) continue;
-      const float al = a.coef[q];
-      float ev[(MP + 31) / 32];
-      float s = 0.f;
+    // ---- coefficients E_k^T d_k and residuals of this rank's users ----
+    // A warp per column, four columns in flight per warp.
+    auto update_cols = [&](int nbat) {
+      for (int cb = warp; cb < nbat; cb += 4 * NW) {
+        float dt[4] = {0.f, 0.f, 0.f, 0.f}, rs[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int t = 0; t < (MP + 31) / 32; ++t) {
-        const int m = lane + 32 * t;
-        ev[t] = 0.f;
-        if (m < M) {
-          ev[t] = fmaf(al, dold[m], a.R[(size_t)i * M + m]);
-          s = fmaf(ev[t], v[m], s);
+        for (int u = 0; u < 4; ++u) {
+          const int c = cb + u * NW;
+          if (c < nbat) {
+            const float *ec = stage + c * MP;
+            for (int m = lane; m < M; m += 32) dt[u] = fmaf(ec[m], v[m], dt[u]);
+          }
         }
-      }
-      const float an = warp_sum(s);
-      float rs = 0.f;
 #pragma unroll
-      for (int t = 0; t < (MP + 31) / 32; ++t) {
-        const int m = lane + 32 * t;
-        if (m < M) {
-          const float r = fmaf(-an, v[m], ev[t]);
-          a.R[(size_t)i * M + m] = r;
-          rs = fmaf(r, r, rs);
+        for (int u = 0; u < 4; ++u) dt[u] = warp_sum(dt[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = cb + u * NW;
+          if (c < nbat) {
+            const float *ec = stage + c * MP;
+            float *ri = a.R + (size_t)rows[c] * M;
+            for (int m = lane; m < M; m += 32) {
+              const float r = fmaf(-dt[u], v[m], ec[m]);
+              ri[m] = r;
+              rs[u] = fmaf(r, r, rs[u]);
+            }
+          }
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) rs[u] = warp_sum(rs[u]);
+        if (lane == 0)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int c = cb + u * NW;
+            if (c < nbat) {
+              a.coef[ents[c]] = dt[u];
+              a.rn2[rows[c]] = rs[u];
+            }
+          }
       }
-      rs = warp_sum(rs);
-      if (lane == 0) { a.coef[q] = an; a.rn2[i] = rs; }
+    };
+    if (nr > NB) {   // restage batch by batch
+      for (int b0 = 0; b0 < nr; b0 += NB) {
+        const int nb = min(NB, nr - b0);
+        __syncthreads();
+        for (int c = tid; c < nb; c += NT) {
+          const int q = a.seg[br + b0 + c];
+          ents[c] = q;
+          als[c] = a.coef[q];
+          rows[c] = q / Kmax;
+        }
+        __syncthreads();
+        stage_cols(nb);
+        __syncthreads();
+        update_cols(nb);
+      }
+    } else {         // all users still staged from the Gram pass
+      update_cols(nr);
     }
+    }  // visit
+  next:
+    __syncthreads();   // this visit is done with every buffer
+    if (tid < NB) {
+      ((k & 1) ? ents0 : ents1)[tid] = pq;
+      ((k & 1) ? als0 : als1)[tid] = pa;
+      ((k & 1) ? rows0 : rows1)[tid] = pq >= 0 ? pq / Kmax : 0;
+    }
+    if (tid < M) ((k & 1) ? dold0 : dold1)[tid] = pd;
     __syncthreads();
+  }
+  if (rank == 0 && tid == 0 && a.stats) {
+    a.stats[0] = steps;
+    a.stats[1] = replaced;
   }
   cl.sync();  // no CTA leaves while another may still read its shared memory
 }
@@ -518,7 +656,7 @@ __global__ void ksvd_init_kernel(float *__restrict__ D, int M, int T, const floa
 template <int SIDE, int TR>
 cudaError_t launch_sweep_t(const SweepArgs &a, cudaStream_t s) {
   constexpr int NT = SIDE * SIDE;
-  const size_t smem = (size_t)sweep_smem_floats(a.M, SIDE * TR, NT) * 4;
+  const size_t smem = (size_t)sweep_smem_floats(a.M, SIDE * TR, SIDE) * 4;
   cudaError_t e = cudaFuncSetAttribute(ksvd_sweep_kernel<SIDE, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -539,36 +677,40 @@ cudaError_t launch_sweep_t(const SweepArgs &a, cudaStream_t s) {
 
 }  // namespace
 
+int ksvd_owner_split() { return kCL; }
+
 size_t ksvd_sweep_smem_bytes(int M) {
-  if (M <= 16) return (size_t)sweep_smem_floats(M, 16, 256) * 4;
-  if (M <= 32) return (size_t)sweep_smem_floats(M, 32, 256) * 4;
-  if (M <= 48) return (size_t)sweep_smem_floats(M, 48, 256) * 4;
-  if (M <= 64) return (size_t)sweep_smem_floats(M, 64, 256) * 4;
-  if (M <= 128) return (size_t)sweep_smem_floats(M, 128, 256) * 4;
-  return (size_t)sweep_smem_floats(M, 192, 1024) * 4;
+  if (M <= 16) return (size_t)sweep_smem_floats(M, 16, 16) * 4;
+  if (M <= 32) return (size_t)sweep_smem_floats(M, 32, 16) * 4;
+  if (M <= 48) return (size_t)sweep_smem_floats(M, 48, 16) * 4;
+  if (M <= 64) return (size_t)sweep_smem_floats(M, 64, 16) * 4;
+  if (M <= 128) return (size_t)sweep_smem_floats(M, 128, 16) * 4;
+  return (size_t)sweep_smem_floats(M, 192, 32) * 4;
 }
 
 int ksvd_chunks(int64_t N) { return (int)((N + kChunk - 1) / kChunk); }
 
 void launch_ksvd_sort(const float *D, int M, int T, const float *X, int N, const int32_t *sup, const float *coef,
-                      const int8_t *keff, int Kmax, float *R, float *rn2, float *xn2, int *hist, int *off,
+                      const int8_t *keff, int Kmax, int split, float *R, float *rn2, float *xn2, int *hist, int *off,
                       int32_t *seg, unsigned *err, cudaStream_t s) {
-  const int C = ksvd_chunks(N);
+  const int C = ksvd_chunks(N), nkeys = T * split;
   if (C > 0) {
-    cudaFuncSetAttribute(ksvd_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, T * 4);
-    ksvd_prep_kernel<<<C, 256, (size_t)T * 4, s>>>(D, M, T, X, N, sup, coef, keff, Kmax, R, rn2, xn2, hist, err);
+    cudaFuncSetAttribute(ksvd_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, nkeys * 4);
+    ksvd_prep_kernel<<<C, 256, (size_t)nkeys * 4, s>>>(D, M, T, X, N, sup, coef, keff, Kmax, split, R, rn2, xn2,
+                                                         hist, err);
   }
-  ksvd_scan_kernel<<<1, 1024, 0, s>>>(hist, C, T, off);
+  ksvd_scan_kernel<<<1, 1024, 0, s>>>(hist, C, nkeys, off);
   if (C > 0) {
-    cudaFuncSetAttribute(ksvd_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, T * 4);
-    ksvd_fill_kernel<<<C, 32, (size_t)T * 4, s>>>(sup, keff, N, Kmax, T, hist, off, seg);
+    cudaFuncSetAttribute(ksvd_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, nkeys * 4);
+    ksvd_fill_kernel<<<C, 32, (size_t)nkeys * 4, s>>>(sup, keff, N, Kmax, T, split, hist, off, seg);
   }
 }
 
 cudaError_t launch_ksvd_sweep(float *D, int M, int T, const float *X, int N, float *coef, int Kmax, const int *off,
                               const int32_t *seg, float *R, float *rn2, const float *xn2, uint8_t *taken, int replace,
-                              const int32_t *rparent, const int32_t *rsup, int Kc, cudaStream_t s) {
-  SweepArgs a{D, M, T, X, N, coef, Kmax, off, seg, R, rn2, xn2, taken, replace, rparent, rsup, Kc};
+                              const int32_t *rparent, const int32_t *rsup, int Kc, unsigned long long *stats,
+                              cudaStream_t s) {
+  SweepArgs a{D, M, T, X, N, coef, Kmax, off, seg, R, rn2, xn2, taken, replace, rparent, rsup, Kc, stats};
   if (M <= 16) return launch_sweep_t<16, 1>(a, s);
   if (M <= 32) return launch_sweep_t<16, 2>(a, s);
   if (M <= 48) return launch_sweep_t<16, 3>(a, s);

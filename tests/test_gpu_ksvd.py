@@ -104,6 +104,8 @@ def test_sweep_is_deterministic_and_leaves_unused_atoms():
     np.testing.assert_array_equal(a[1], b[1])
     assert a[2] == b[2]
     np.testing.assert_array_equal(a[0][5], D0[5])
+    steps, replaced = ctx.ksvd_stats()
+    assert replaced == 0 and 127 <= steps <= 1000 * 127
 
 
 def test_unused_atoms_are_replaced_like_the_oracle():
@@ -117,6 +119,7 @@ def test_unused_atoms_are_replaced_like_the_oracle():
     assert [k for k, _ in rep] == unused
     ctx = _ctx()
     Dg, Ag, _ = _gpu_update(ctx, D0, X, om, al, ke, replace=True)
+    assert ctx.ksvd_stats()[1] == len(unused)
     for k, i in rep:
         np.testing.assert_allclose(Dg[k], X[i] / np.linalg.norm(X[i].astype(np.float64)), atol=1e-6)
     assert np.max(np.abs(Dg - Do)) <= ATOL_D

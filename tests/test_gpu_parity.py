@@ -27,6 +27,7 @@ SMALL = {
     "video": dict(name="video", H=48, W=48, T0=1024),
     "inpaint": dict(name="inpaint", H=64, W=56, T0=512),
     "cs_dense": dict(name="cs_dense", H=64, W=72, T0=512),
+    "rgb_identity": dict(name="bayer", H=48, W=48),   # Phi = I on RGB: M = 192 at the fine scale
 }
 
 
@@ -35,6 +36,10 @@ def _workload(key, links="paper", **kw):
     name = spec.pop("name")
     spec.update(kw)
     w = synthetic.make_workload(name, links=links, **spec)
+    if key == "rgb_identity":
+        rng = np.random.default_rng(9)
+        w.sensing = synthetic.Sensing("identity")
+        w.meas = (w.truth + w.sigma * rng.standard_normal(w.truth.shape)).astype(np.float32)
     if key == "denoise_ragged":
         w.geometry.stride = 3   # (72 - 8) % 3 != 0: clamped last origin on x
         B = w.n_patches
@@ -397,7 +402,7 @@ def test_restricted_dependent_candidate_falls_back_to_fp64(variant):
 
 
 @pytest.mark.parametrize("variant", list(range(10)))
-@pytest.mark.parametrize("key", ["bayer", "lightfield", "denoise_ragged", "video"])
+@pytest.mark.parametrize("key", ["bayer", "lightfield", "denoise_ragged", "video", "rgb_identity"])
 def test_restricted_variants_agree_with_oracle(key, variant):
     """Every restricted-solver variant the autotuner may pick meets the parity
     bar: L2-cooperative (0), shared-memory staged (1), Gram-matrix proxy with
