@@ -55,6 +55,11 @@ def parse():
                     help="comma-separated children-per-coarse-atom counts Q (e.g. 2,4,8,16): instead of the "
                          "headline, time cross-scale and plain OMP and report PSNR for each Q (the link-size "
                          "trade-off of Sec. III-E / Fig. 4 on synthetic data)")
+    ap.add_argument("--ksvd", action="store_true",
+                    help="instead of the headline, time the modified K-SVD (Sec. III, learning cross-scale "
+                         "models) on a synthetic training set shaped like --workload: one Step-2 iteration "
+                         "(zero-tree coding + dictionary-update sweep) against one plain K-SVD iteration")
+    ap.add_argument("--ksvd-signals", type=int, default=65536, help="training signals of --ksvd")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="one stream throughout (csp_set_pipeline off; profiling runs)")
     ap.add_argument("--top-form", type=int, default=None, choices=[1, 2],
@@ -415,6 +420,104 @@ def q_sweep(args):
                       "data": "synthetic (seeded)", "l2": "flushed between steps", "rows": rows}))
 
 
+def ksvd_bench(args):
+    """Modified K-SVD on a seeded training set with the patch shape, atom counts
+    and sparsities of the workload: time of one Step-2 iteration (zero-tree
+    coding of every signal, csp_solve cross-scale, then one dictionary-update
+    sweep, csp_ksvd_update) and of one plain K-SVD iteration (plain OMP over all
+    fine atoms, then the same sweep) on the same dictionaries, CUDA events,
+    FP32 coding.  The sweep visits the atoms in order inside one thread-block
+    cluster; its roofline is FP32 FMA work (Gram matrices, power steps,
+    residual updates) against the peak of the cluster's SMs.  The oracle's
+    sweep (FP64 CPU, the same inputs) is timed once beside it.  One JSON line."""
+    import torch
+    import synthetic
+    import oracle  # noqa: F401  (the CPU baseline below)
+    from oracle import ksvd as oksvd
+    from paper_1511_05174_gb300.context import Context
+    from paper_1511_05174_gb300.ksvd import ModifiedKSVD
+
+    dev = torch.device("cuda", 0)
+    ts = synthetic.make_training_set(args.workload, args.ksvd_signals, seed=0)
+    g = ts.geometry
+    mk = ModifiedKSVD(g.P, g.plane_grid, g.level_factors, ts.parents[0], ts.K_high, ts.K_low)
+    X = torch.from_numpy(ts.X).to(dev)
+    t0 = time.perf_counter()
+    D_low, D_high, sup_low, keff_low, el, eh = mk.fit(X, ts.u_low, ts.u_high, 2, 2)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
+    plain = Context(0)
+    plain.set_geometry(g.P, g.P, g.plane_grid, g.P, g.P, [(1, 1, 1, 1)])
+    plain.set_sensing("identity")
+    n, N0 = X.shape
+    T = D_high.shape[0]
+    err = torch.zeros(1, dtype=torch.float32, device=dev)
+
+    def one(kind):
+        Dw = D_high.clone()
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        a.record()
+        if kind == "cross_scale":
+            sup, coef, keff = mk.code_high(Dw, D_low, X)
+        else:
+            plain.load_dictionary(0, Dw)
+            sup, coef, keff = plain.solve(X, mode="plain", precision="fp32", K=(ts.K_high,))
+        b.record()
+        ctx = mk.fine if kind == "cross_scale" else plain
+        ctx.profile(True)
+        ctx.profile_read(reset=True)
+        if kind == "cross_scale":
+            ctx.ksvd_update(Dw, X, sup, coef, keff, True, mk.parent_dev, sup_low, err)
+        else:
+            ctx.ksvd_update(Dw, X, sup, coef, keff, True, err_out=err)
+        c.record()
+        torch.cuda.synchronize()
+        prof = ctx.profile_read(reset=True)
+        ctx.profile(False)
+        return a.elapsed_time(b), b.elapsed_time(c), prof, ctx.ksvd_stats(), (sup, coef, keff)
+
+    res = {}
+    for kind in ("cross_scale", "plain"):
+        for _ in range(max(args.warmup, 1)):
+            one(kind)
+        runs = [one(kind) for _ in range(max(args.steps, 1))]
+        code = sorted(r[0] for r in runs)[len(runs) // 2]
+        upd = sorted(r[1] for r in runs)[len(runs) // 2]
+        sweep_ms = sorted(r[2]["ksvd_sweep"][1] for r in runs)[len(runs) // 2]
+        steps, replaced = runs[-1][3]
+        res[kind] = {"coding_ms": code, "update_ms": upd, "iteration_ms": code + upd, "sweep_kernel_ms": sweep_ms,
+                     "power_steps": steps, "replaced_atoms": replaced, "last": runs[-1][4]}
+    # algorithmic FP32 work of the Step-2 sweep: Gram matrices n_k M^2, power steps M^2 each, residual
+    # and coefficient updates 4 M per slot (2 FLOP per FMA)
+    sup, coef, keff = res["cross_scale"].pop("last")
+    res["plain"].pop("last")
+    slots = int(keff.to(torch.int64).sum())
+    flops = 2.0 * (slots * N0 * N0 + res["cross_scale"]["power_steps"] * N0 * N0 + 2 * slots * N0)
+    achieved = flops / (res["cross_scale"]["sweep_kernel_ms"] / 1e3) / 1e12
+    cluster_peak = 8 * 128 * 2 * 2.070e9 / 1e12
+    # CPU oracle of the same sweep (FP64), once
+    s_np, c_np, k_np = sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy()
+    t1 = time.perf_counter()
+    oksvd.ksvd_update(D_high.cpu().numpy(), ts.X, s_np, c_np, k_np, True, ts.parents[0], sup_low.cpu().numpy())
+    cpu_s = time.perf_counter() - t1
+    out = {
+        "metric": "modified K-SVD iteration time (Step 2: zero-tree coding + dictionary update)",
+        "value": res["cross_scale"]["iteration_ms"], "unit": "ms", "higher_is_better": False,
+        "workload": f"training set shaped like {args.workload}: {n} signals of dimension {N0}, "
+                    f"T {T}/{D_low.shape[0]}, K {ts.K_high}/{ts.K_low}",
+        "data": "synthetic (seeded two-scale model)",
+        "step2": res["cross_scale"], "plain_ksvd": res["plain"],
+        "training_speedup": res["plain"]["iteration_ms"] / res["cross_scale"]["iteration_ms"],
+        "fit_2x2_s": fit_s, "err_low": el, "err_high": eh,
+        "roofline": {"kernel": "ksvd_sweep", "bound": "alu", "achieved": achieved, "peak": cluster_peak,
+                     "peak_source": "derived: 8 SMs (one cluster) x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "unit": "TFLOP/s", "frac": achieved / cluster_peak, "traffic": None},
+        "cpu_baseline": {"value": cpu_s * 1e3, "unit": "ms per sweep", "cores": 1, "kind": "oracle",
+                         "sample": "the same sweep (all signals and atoms), FP64 numpy"},
+    }
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -422,6 +525,9 @@ def main():
         return
     if args.sweep_q:
         q_sweep(args)
+        return
+    if args.ksvd:
+        ksvd_bench(args)
         return
 
     import torch

@@ -53,28 +53,33 @@ def residuals(D: np.ndarray, X: np.ndarray, omega: np.ndarray, alpha: np.ndarray
     """R [N, M] with r_i = x_i - sum_j alpha_ij d_{omega_ij} (j < k_eff_i)."""
     D = np.asarray(D, np.float64)
     R = np.array(X, np.float64, copy=True)
-    for i in range(R.shape[0]):
-        k = int(k_eff[i])
-        if k:
-            R[i] -= np.asarray(alpha[i, :k], np.float64) @ D[omega[i, :k]]
+    valid = np.arange(omega.shape[1])[None, :] < np.asarray(k_eff).reshape(-1, 1)
+    for i0 in range(0, R.shape[0], 4096):      # blocks of signals bound the [n, K, M] temporary
+        v = valid[i0:i0 + 4096]
+        a = np.where(v, np.asarray(alpha[i0:i0 + 4096], np.float64), 0.0)
+        idx = np.where(v, omega[i0:i0 + 4096], 0)
+        R[i0:i0 + 4096] -= np.einsum("nk,nkm->nm", a, D[idx])
     return R
 
 
 def atom_users(omega: np.ndarray, k_eff: np.ndarray, T: int):
     """For every atom k, the (signal i, slot j) pairs with omega[i, j] = k, i ascending."""
-    users: List[list] = [[] for _ in range(T)]
-    for i in range(omega.shape[0]):
-        for j in range(int(k_eff[i])):
-            users[int(omega[i, j])].append((i, j))
-    return users
+    valid = np.arange(omega.shape[1])[None, :] < np.asarray(k_eff).reshape(-1, 1)
+    I, J = np.nonzero(valid)                       # row-major: i ascending
+    atoms = np.asarray(omega)[I, J]
+    order = np.argsort(atoms, kind="stable")
+    cuts = np.searchsorted(atoms[order], np.arange(T + 1))
+    return [list(zip(I[order[cuts[k]:cuts[k + 1]]].tolist(), J[order[cuts[k]:cuts[k + 1]]].tolist()))
+            for k in range(T)]
 
 
-def _eligible(i: int, k: int, taken, X_norm2, repl_parent, repl_support) -> bool:
-    if taken[i] or X_norm2[i] <= 0.0:
-        return False
-    if repl_parent is None:
-        return True
-    return int(repl_parent[k]) in set(int(a) for a in repl_support[i] if a >= 0)
+def _eligible(k: int, taken, X_norm2, repl_parent, repl_support) -> np.ndarray:
+    """Signals that may replace unused atom k: not yet taken, nonzero, and (with
+    coarse parents) holding atom k's parent in their coarse support."""
+    ok = ~taken & (X_norm2 > 0.0)
+    if repl_parent is not None:
+        ok &= np.any(np.asarray(repl_support) == int(repl_parent[k]), axis=1)
+    return ok
 
 
 def ksvd_update(D: np.ndarray, X: np.ndarray, omega: np.ndarray, alpha: np.ndarray,
@@ -105,10 +110,8 @@ def ksvd_update(D: np.ndarray, X: np.ndarray, omega: np.ndarray, alpha: np.ndarr
             if not replace_unused:
                 continue
             err = np.einsum("ij,ij->i", R, R)
-            best, best_i = -1.0, -1
-            for i in range(X.shape[0]):        # first maximum = lowest index
-                if _eligible(i, k, taken, X_norm2, repl_parent, repl_support) and err[i] > best:
-                    best, best_i = err[i], i
+            ok = _eligible(k, taken, X_norm2, repl_parent, repl_support)
+            best_i = int(np.argmax(np.where(ok, err, -1.0))) if ok.any() else -1  # first maximum
             if best_i >= 0:
                 D[k] = X[best_i] / np.sqrt(X_norm2[best_i])
                 taken[best_i] = True
