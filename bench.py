@@ -484,9 +484,9 @@ def ksvd_bench(args):
         code = sorted(r[0] for r in runs)[len(runs) // 2]
         upd = sorted(r[1] for r in runs)[len(runs) // 2]
         sweep_ms = sorted(r[2]["ksvd_sweep"][1] for r in runs)[len(runs) // 2]
-        steps, replaced = runs[-1][3]
+        steps, replaced, ranks = runs[-1][3]
         res[kind] = {"coding_ms": code, "update_ms": upd, "iteration_ms": code + upd, "sweep_kernel_ms": sweep_ms,
-                     "power_steps": steps, "replaced_atoms": replaced, "last": runs[-1][4]}
+                     "power_steps": steps, "replaced_atoms": replaced, "cluster_ranks": ranks, "last": runs[-1][4]}
     # algorithmic FP32 work of the Step-2 sweep: Gram matrices n_k M^2, power steps M^2 each, residual
     # and coefficient updates 4 M per slot (2 FLOP per FMA)
     sup, coef, keff = res["cross_scale"].pop("last")
@@ -494,7 +494,8 @@ def ksvd_bench(args):
     slots = int(keff.to(torch.int64).sum())
     flops = 2.0 * (slots * N0 * N0 + res["cross_scale"]["power_steps"] * N0 * N0 + 2 * slots * N0)
     achieved = flops / (res["cross_scale"]["sweep_kernel_ms"] / 1e3) / 1e12
-    cluster_peak = 8 * 128 * 2 * 2.070e9 / 1e12
+    ranks = res["cross_scale"]["cluster_ranks"]
+    cluster_peak = ranks * 128 * 2 * 2.070e9 / 1e12
     # CPU oracle of the same sweep (FP64), once
     s_np, c_np, k_np = sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy()
     t1 = time.perf_counter()
@@ -510,7 +511,7 @@ def ksvd_bench(args):
         "training_speedup": res["plain"]["iteration_ms"] / res["cross_scale"]["iteration_ms"],
         "fit_2x2_s": fit_s, "err_low": el, "err_high": eh,
         "roofline": {"kernel": "ksvd_sweep", "bound": "alu", "achieved": achieved, "peak": cluster_peak,
-                     "peak_source": "derived: 8 SMs (one cluster) x 128 FP32 lanes x 2 x 2.07 GHz",
+                     "peak_source": f"derived: {ranks} SMs (one cluster) x 128 FP32 lanes x 2 x 2.07 GHz",
                      "unit": "TFLOP/s", "frac": achieved / cluster_peak, "traffic": None},
         "cpu_baseline": {"value": cpu_s * 1e3, "unit": "ms per sweep", "cores": 1, "kind": "oracle",
                          "sample": "the same sweep (all signals and atoms), FP64 numpy"},

@@ -289,8 +289,9 @@ csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X,
 /* Counters of the last csp_ksvd_update on this context: power_steps = the
  * power-method steps summed over the visited atoms (a step is one product
  * with E_k E_k^T; at most 1000 per atom), replaced = atoms replaced by
- * heuristics 3-4.  Either pointer may be NULL. */
-csp_status csp_ksvd_stats_get(csp_ctx *ctx, int64_t *power_steps, int64_t *replaced);
+ * heuristics 3-4, ranks = thread blocks of the sweep's cluster (16 where the
+ * device holds such a cluster, else 8).  Any pointer may be NULL. */
+csp_status csp_ksvd_stats_get(csp_ctx *ctx, int64_t *power_steps, int64_t *replaced, int64_t *ranks);
 
 /* Initialisation picks of the modified K-SVD.  Atom t = x_i / ||x_i|| with
  * i = item floor(u_t n) of a pool of n signals in ascending order: all N

@@ -154,7 +154,8 @@ def load_library(path: str = LIB_PATH):
         "csp_downsample": (i, [vp, i, vp, ctypes.c_int64, vp, vp]),
         "csp_ksvd_update": (i, [vp, vp, i, i, vp, ctypes.c_int64, vp, vp, vp, i, i, vp, vp, i, vp, vp]),
         "csp_ksvd_init_atoms": (i, [vp, vp, i, i, vp, ctypes.c_int64, vp, vp, vp, i, i, vp, vp]),
-        "csp_ksvd_stats_get": (i, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
+        "csp_ksvd_stats_get": (i, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.POINTER(ctypes.c_int64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -372,6 +373,6 @@ def csp_ksvd_init_atoms(ctx, D_ptr: int, M: int, T: int, X_ptr: int, N: int, par
 
 
 def csp_ksvd_stats_get(ctx):
-    steps, rep = ctypes.c_int64(), ctypes.c_int64()
-    check(load_library().csp_ksvd_stats_get(ctx, ctypes.byref(steps), ctypes.byref(rep)), ctx)
-    return int(steps.value), int(rep.value)
+    steps, rep, ranks = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    check(load_library().csp_ksvd_stats_get(ctx, ctypes.byref(steps), ctypes.byref(rep), ctypes.byref(ranks)), ctx)
+    return int(steps.value), int(rep.value), int(ranks.value)

@@ -258,7 +258,7 @@ class Context:
                           err_out.data_ptr() if err_out is not None else None, _stream_ptr(stream, self.device))
 
     def ksvd_stats(self):
-        """(power-method steps, replaced atoms) of the last ksvd_update."""
+        """(power-method steps, replaced atoms, cluster ranks) of the last ksvd_update."""
         return b.csp_ksvd_stats_get(self._ctx)
 
     def ksvd_init_atoms(self, D: torch.Tensor, X: torch.Tensor, u: torch.Tensor,

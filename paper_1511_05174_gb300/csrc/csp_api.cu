@@ -1467,16 +1467,16 @@ csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X,
   int32_t *seg = nullptr;
   float *R = nullptr, *rn2 = nullptr, *xn2 = nullptr;
   uint8_t *taken = nullptr;
-  CSP_TRY(ksvd_sort(ctx, D, M, T, X, n, support, coef, k_eff, Kmax, ksvd_owner_split(), true, &off, &seg, &R, &rn2,
-                    &xn2, s));
+  const int split = ksvd_owner_split(M, T);
+  CSP_TRY(ksvd_sort(ctx, D, M, T, X, n, support, coef, k_eff, Kmax, split, true, &off, &seg, &R, &rn2, &xn2, s));
   unsigned long long *st = nullptr;
   CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_TAKEN, (size_t)std::max(n, 1), &taken));
   CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_STATS, 2, &st));
   CSP_CUDA(ctx, cudaMemsetAsync(taken, 0, (size_t)std::max(n, 1), s));
   cudaError_t le = cudaSuccess;
   run(ctx, KK_KSVD_SWEEP, s, 1, [&] {
-    le = launch_ksvd_sweep(D, M, T, X, n, coef, Kmax, off, seg, R, rn2, xn2, taken, replace_unused, repl_parent,
-                           repl_support, Kc, st, s);
+    le = launch_ksvd_sweep(D, M, T, X, n, coef, Kmax, split, off, seg, R, rn2, xn2, taken, replace_unused,
+                           repl_parent, repl_support, Kc, st, s);
   });
   if (le != cudaSuccess) return fail(ctx, CSP_ERR_CUDA, std::string("K-SVD sweep launch: ") + cudaGetErrorString(le));
   if (err_out) {
@@ -1489,13 +1489,15 @@ csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X,
   CSP_CUDA(ctx, cudaStreamSynchronize(s));
   ctx->ksvd_steps = (int64_t)hst[0];
   ctx->ksvd_replaced = (int64_t)hst[1];
+  ctx->ksvd_ranks = split;
   return CSP_OK;
 }
 
-csp_status csp_ksvd_stats_get(csp_ctx *ctx, int64_t *power_steps, int64_t *replaced) {
+csp_status csp_ksvd_stats_get(csp_ctx *ctx, int64_t *power_steps, int64_t *replaced, int64_t *ranks) {
   if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
   if (power_steps) *power_steps = ctx->ksvd_steps;
   if (replaced) *replaced = ctx->ksvd_replaced;
+  if (ranks) *ranks = ctx->ksvd_ranks;
   return CSP_OK;
 }
 

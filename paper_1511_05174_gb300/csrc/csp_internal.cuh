@@ -164,7 +164,7 @@ struct csp_ctx {
   bool pipeline = true;        // csp_set_pipeline
   bool recon_synth = false;    // the recorded / last csp_reconstruct fused the synthesis
   bool last_synth = false;     // reported by csp_solve_stats_get
-  int64_t ksvd_steps = 0, ksvd_replaced = 0;  // last csp_ksvd_update (csp_ksvd_stats_get)
+  int64_t ksvd_steps = 0, ksvd_replaced = 0, ksvd_ranks = 0;  // last csp_ksvd_update (csp_ksvd_stats_get)
   std::vector<csp::ProfRec> pending;
   std::vector<cudaEvent_t> ev_pool;
   // All device allocations (for the memory budget and destroy).
@@ -318,11 +318,9 @@ void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const 
                           const int32_t *child_idx, int cap, int64_t B, float *Ac, float *invc, cudaStream_t s);
 
 // ---- K-SVD dictionary update and initialisation (k_ksvd.cu) ----
-// Shared memory of the sweep kernel for dimension M (M <= 192).
-size_t ksvd_sweep_smem_bytes(int M);
-// Ranks of the sweep's cluster: the sort for the sweep splits every atom's
-// slots by owner rank i mod ksvd_owner_split().
-int ksvd_owner_split();
+// Ranks of the sweep's cluster (16 when such a cluster fits, else 8): the sort
+// for the sweep splits every atom's slots by owner rank i mod this count.
+int ksvd_owner_split(int M, int T);
 // Counting chunks of N signals (rows of the [chunks][T * split] histogram).
 int ksvd_chunks(int64_t N);
 // Residuals R = X - D S, their squared norms rn2 and those of X (xn2), support
@@ -335,10 +333,10 @@ void launch_ksvd_sort(const float *D, int M, int T, const float *X, int N, const
                       int32_t *seg, unsigned *err, cudaStream_t s);
 // The sequential atom sweep (one thread-block cluster); stats[0] = power-method
 // steps, stats[1] = replaced atoms.
-cudaError_t launch_ksvd_sweep(float *D, int M, int T, const float *X, int N, float *coef, int Kmax, const int *off,
-                              const int32_t *seg, float *R, float *rn2, const float *xn2, uint8_t *taken, int replace,
-                              const int32_t *rparent, const int32_t *rsup, int Kc, unsigned long long *stats,
-                              cudaStream_t s);
+cudaError_t launch_ksvd_sweep(float *D, int M, int T, const float *X, int N, float *coef, int Kmax, int split,
+                              const int *off, const int32_t *seg, float *R, float *rn2, const float *xn2,
+                              uint8_t *taken, int replace, const int32_t *rparent, const int32_t *rsup, int Kc,
+                              unsigned long long *stats, cudaStream_t s);
 void launch_ksvd_sum(const float *rn2, int N, float *out, cudaStream_t s);
 // Initialisation picks; off == nullptr: from all N signals.
 void launch_ksvd_init(float *D, int M, int T, const float *X, int N, const int32_t *parent, const int *off,

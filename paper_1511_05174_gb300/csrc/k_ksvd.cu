@@ -28,7 +28,7 @@
 //  4. ksvd_sweep_kernel  one thread-block cluster visits the atoms in order.
 //     Per atom: each CTA accumulates C_r = sum e_i e_i^T over the users it
 //     owns (i mod CL == rank); the power method on C = E_k E_k^T = sum_r C_r
-//     from d_old multiplies each C_r locally and adds the kCL products through
+//     from d_old multiplies each C_r locally and adds the CL products through
 //     distributed shared memory in rank order (one cluster barrier per step,
 //     identical vectors and decisions on every rank); each CTA then updates
 //     the coefficients and residuals of its own users.  Ownership by signal
@@ -49,7 +49,6 @@ namespace csp {
 namespace {
 
 constexpr int kChunk = 256;       // signals per counting chunk
-constexpr int kCL = 8;            // CTAs of the sweep's cluster
 constexpr int kMaxIt = 1000;      // power-iteration cap per atom
 constexpr float kTol2 = 1.6e-11f; // converged when ||v_new - v||^2 <= (4e-6)^2
 
@@ -223,7 +222,7 @@ struct SweepArgs {
   int N;
   float *coef;
   int Kmax;
-  const int *off;          // [T * kCL + 1]: slots of (atom k, owner rank r) at off[k * kCL + r] ..
+  const int *off;          // [T * CL + 1]: slots of (atom k, owner rank r) at off[k * CL + r] ..
   const int32_t *seg;      // slot ids q = i * Kmax + j, ascending i within each (k, r)
   float *R, *rn2;
   const float *xn2;
@@ -234,26 +233,24 @@ struct SweepArgs {
   unsigned long long *stats;  // [0] power-method steps, [1] replaced atoms
 };
 
-__host__ __device__ constexpr int pad4(int n) { return (n + 3) & ~3; }
 
 // Stage capacity (floats) of the e_i columns: kNB-free sizing by dimension.
 __host__ __device__ constexpr int stage_floats(int side) { return side == 16 ? 16384 : 12288; }
 
-// Shared-memory floats of the sweep: this rank's partial C ([M][M + 1]), the
-// exchanged products C_r v (2 x M),
+// Shared-memory floats of the sweep: the products C_q v received from every
+// rank q (2 x CL x MP),
 // share, the staged columns, the vectors and the slot lists.
-__host__ __device__ inline int sweep_smem_floats(int M, int MP, int side) {
-  const int CCP = pad4(M * (M + 1)), RB = 2 * pad4(M);
+__host__ __device__ inline int sweep_smem_floats(int MP, int side, int CL) {
   const int NB = stage_floats(side) / MP;
-  return CCP + RB + stage_floats(side) + 10 * pad4(M) + 128 + 6 * NB;
+  return 2 * CL * MP + stage_floats(side) + 8 * MP + 128 + 6 * NB;
 }
 
 // 4. The sweep.  Threads form a SIDE x SIDE grid; thread (ty, tx) accumulates
 // the TR x TR tile of C at rows ty*TR.., columns tx*TR.. (SIDE*TR >= M).
-// Rank r of the cluster owns the signals i with i mod kCL == r: it reads and
+// Rank r of the cluster owns the signals i with i mod CL == r: it reads and
 // writes only their residuals and coefficients, so the visits of successive
 // atoms need no exchange beyond the Gram matrix.
-template <int SIDE, int TR>
+template <int SIDE, int TR, int CL>
 __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepArgs a) {
   constexpr int NT = SIDE * SIDE, NW = NT / 32, MP = SIDE * TR;
   constexpr int NB = stage_floats(SIDE) / MP;     // columns staged at once
@@ -261,16 +258,15 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
   const int rank = (int)cl.block_rank();
   extern __shared__ float4 smem4[];
   float *sm = reinterpret_cast<float *>(smem4);
-  const int M = a.M, LDC = M + 1, CCP = pad4(M * LDC), Kmax = a.Kmax;
-  float *Cb = sm;                        // [M][M + 1] this rank's partial C_r = sum e_i e_i^T
-  float *yx = Cb + CCP;                  // [2][pad4(M)] C_r v of the last two steps (read by all ranks)
-  float *stage = yx + 2 * pad4(M);       // [NB][MP] e_i of the staged users
-  float *dold0 = stage + stage_floats(SIDE), *dold1 = dold0 + pad4(M);  // atom before the visit (2 buffers)
-  float *const vb0 = dold0 + 2 * pad4(M), *const vb1 = dold0 + 3 * pad4(M);  // power-method vectors
-  float *ysum = dold0 + 4 * pad4(M);     // [M] C v = sum over ranks of C_r v
-  float *dd = dold0 + 5 * pad4(M);       // [M] squared change of each component
-  float *yp = dold0 + 6 * pad4(M);       // [4][M] partial sums of C v
-  float *scal = dold0 + 10 * pad4(M);    // [128] flags, per-warp argmax scratch
+  const int M = a.M, Kmax = a.Kmax;
+  float *rx = sm;                        // [2][CL][MP] C_q v pushed by every rank q (two step parities)
+  float *stage = rx + 2 * CL * MP;       // [NB][MP] e_i of the staged users
+  float *dold0 = stage + stage_floats(SIDE), *dold1 = dold0 + MP;  // atom before the visit (2 buffers)
+  float *const vb0 = dold0 + 2 * MP, *const vb1 = dold0 + 3 * MP;  // power-method vectors (zero past M)
+  float *yl = dold0 + 4 * MP;            // [MP] this rank's C_r v
+  float *ysum = dold0 + 5 * MP;          // [MP] C v
+  float *dd = dold0 + 6 * MP;            // [MP] squared change of each component
+  float *scal = dold0 + 8 * MP;          // [128] flags, per-warp argmax scratch
   int *ents0 = reinterpret_cast<int *>(scal + 128), *ents1 = ents0 + NB;  // staged slot ids (2 buffers)
   float *als0 = reinterpret_cast<float *>(ents1 + NB), *als1 = als0 + NB;  // their coefficients before the visit
   int *rows0 = reinterpret_cast<int *>(als1 + NB), *rows1 = rows0 + NB;     // their signals i = q / Kmax
@@ -284,6 +280,7 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
   unsigned gstep = 0;                   // power-method steps of this sweep (product buffer parity)
 
   for (int q = tid; q < stage_floats(SIDE); q += NT) stage[q] = 0.f;  // padding rows stay zero
+  for (int q = tid; q < 2 * MP; q += NT) vb0[q] = 0.f;                 // entries past M stay zero
   {  // slot ids, coefficients and atom of the first visit
     const int br = a.off[rank], nr = a.off[rank + 1] - br;
     for (int c = tid; c < min(nr, min(NB, NT)); c += NT) {
@@ -295,8 +292,8 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
   }
   __syncthreads();
   for (int k = 0; k < a.T; ++k) {
-    const int kb = a.off[k * kCL], nk = a.off[(k + 1) * kCL] - kb;
-    const int br = a.off[k * kCL + rank], nr = a.off[k * kCL + rank + 1] - br;
+    const int kb = a.off[k * CL], nk = a.off[(k + 1) * CL] - kb;
+    const int br = a.off[k * CL + rank], nr = a.off[k * CL + rank + 1] - br;
     float *dold = (k & 1) ? dold1 : dold0;
     int *ents = (k & 1) ? ents1 : ents0;
     float *als = (k & 1) ? als1 : als0;
@@ -307,7 +304,7 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
     int pq = -1;
     float pa = 0.f, pd = 0.f;
     if (k + 1 < a.T) {
-      const int br1 = a.off[(k + 1) * kCL + rank], nr1 = a.off[(k + 1) * kCL + rank + 1] - br1;
+      const int br1 = a.off[(k + 1) * CL + rank], nr1 = a.off[(k + 1) * CL + rank + 1] - br1;
       if (tid < min(nr1, NB)) {
         pq = a.seg[br1 + tid];
         pa = a.coef[pq];
@@ -322,7 +319,7 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
       float bv = -1.f;
       int bi = -1;
       const int pk = a.rparent ? a.rparent[k] : -1;
-      for (int i = rank + kCL * tid; i < a.N; i += kCL * NT) {
+      for (int i = rank + CL * tid; i < a.N; i += CL * NT) {
         if (a.taken[i] || !(a.xn2[i] > 0.f)) continue;
         if (a.rparent) {
           bool ok = false;
@@ -354,7 +351,8 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
       cl.sync();
       float gv = -1.f;
       int gi = -1;
-      for (int q = 0; q < kCL; ++q) {
+#pragma unroll 1
+      for (int q = 0; q < CL; ++q) {
         const float ov = *cl.map_shared_rank(slotv, q);
         const int oi = *cl.map_shared_rank(sloti, q);
         if (oi >= 0 && (ov > gv || (ov == gv && (gi < 0 || oi < gi)))) { gv = ov; gi = oi; }
@@ -362,7 +360,7 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
       cl.sync();
       if (gi >= 0) {
         ++replaced;
-        if (tid == 0 && gi % kCL == rank) a.taken[gi] = 1;
+        if (tid == 0 && gi % CL == rank) a.taken[gi] = 1;
         if (rank == 0 && warp == 0) {
           float s = 0.f;
           for (int m = lane; m < M; m += 32) {
@@ -435,58 +433,58 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
       }
       if (b0 + NB < nr) __syncthreads();   // the last batch stays staged for the update
     }
-#pragma unroll
-    for (int i = 0; i < TR; ++i)
-#pragma unroll
-      for (int j = 0; j < TR; ++j)
-        if (r0 + i < M && c0 + j < M) Cb[(r0 + i) * LDC + c0 + j] = acc[i][j];
+    // acc now holds this thread's tile of C_r (zero past M) and stays in registers
 
     for (int m = tid; m < M; m += NT) vb0[m] = dold[m];
     __syncthreads();
 
     // ---- leading eigenvector of C = sum_r C_r by the power method from d_old ----
-    // The ranks never form C: step t computes C_r v_t locally (thread (part,
-    // r) sums column range `part` of row r, read as column r of the symmetric
-    // C_r: consecutive lanes, consecutive banks), publishes it, and after one
-    // cluster barrier every rank adds the kCL products in rank order, so all
-    // ranks hold the same y = C v_t and take the same decisions.  v_{t+1} =
-    // y / ||y||; the change ||v_{t+1} - v_t||^2 is summed one step later; stop
-    // when it is <= kTol2.  The two product buffers alternate by step, so a
-    // rank may overwrite one only after every rank has passed the barrier that
-    // follows its reads (the alternation runs on across visits).
+    // The ranks never form C.  Step t: every thread multiplies its register
+    // tile of C_r with v_t, the tile rows are summed across the row's SIDE
+    // threads (shuffles), each rank pushes its C_r v_t into every rank's
+    // receive slot (distributed shared memory stores), and after one cluster
+    // barrier every rank adds the CL products in rank order: all ranks hold
+    // the same y = C v_t and take the same decisions.  v_{t+1} = y / ||y||;
+    // the change ||v_{t+1} - v_t||^2 is summed one step later; stop when it is
+    // <= kTol2.  Receive slots alternate by step (the alternation runs on across
+    // visits), so a rank writes a slot only after every rank has passed the
+    // barrier that follows its reads of it.
     int cur = 0;
     bool zero = false;
-    constexpr int PARTS = NT / MP >= 4 ? 4 : (NT / MP >= 2 ? 2 : 1);
-    const int CW = (M + PARTS - 1) / PARTS;
     for (int it = 0; it < kMaxIt; ++it) {
       const float *v = cur ? vb1 : vb0;
       float *vn = cur ? vb0 : vb1;
-      float *yo = yx + (gstep & 1) * pad4(M);
+      float *rxp = rx + (gstep & 1) * CL * MP;
       ++gstep;
-      for (int t = tid; t < PARTS * M; t += NT) {
-        const int part = t / M, r = t - part * M;
-        const int ca = part * CW, cz = min(M, ca + CW);
-        float s0 = 0.f, s1 = 0.f;
-        int c = ca;
-        for (; c + 1 < cz; c += 2) {
-          s0 = fmaf(Cb[c * LDC + r], v[c], s0);
-          s1 = fmaf(Cb[(c + 1) * LDC + r], v[c + 1], s1);
+      {
+        float vv[TR], py[TR];
+        lds_run<TR>(vv, v + c0);
+#pragma unroll
+        for (int i = 0; i < TR; ++i) {
+          float t = 0.f;
+#pragma unroll
+          for (int j = 0; j < TR; ++j) t = fmaf(acc[i][j], vv[j], t);
+          py[i] = t;
         }
-        if (c < cz) s0 = fmaf(Cb[c * LDC + r], v[c], s0);
-        yp[part * M + r] = s0 + s1;
+#pragma unroll
+        for (int i = 0; i < TR; ++i)
+#pragma unroll
+          for (int o = SIDE / 2; o; o >>= 1) py[i] += __shfl_xor_sync(0xffffffffu, py[i], o);
+        if (tx == 0)
+#pragma unroll
+          for (int i = 0; i < TR; ++i)
+            if (r0 + i < M) yl[r0 + i] = py[i];
       }
       __syncthreads();
-      for (int m = tid; m < M; m += NT) {
-        float ym = yp[m];
-#pragma unroll
-        for (int q = 1; q < PARTS; ++q) ym += yp[q * M + m];
-        yo[m] = ym;
+      for (int t = tid; t < CL * M; t += NT) {
+        const int q = t / M, m = t - q * M;
+        cl.map_shared_rank(rxp, q)[rank * MP + m] = yl[m];
       }
       cl.sync();
       for (int m = tid; m < M; m += NT) {
         float ym = 0.f;
-#pragma unroll
-        for (int q = 0; q < kCL; ++q) ym += cl.map_shared_rank(yo, q)[m];
+#pragma unroll 4
+        for (int q = 0; q < CL; ++q) ym += rxp[q * MP + m];
         ysum[m] = ym;
       }
       __syncthreads();
@@ -653,39 +651,76 @@ __global__ void ksvd_init_kernel(float *__restrict__ D, int M, int T, const floa
   for (int m = lane; m < M; m += 32) D[(size_t)t * M + m] = X[(size_t)i * M + m] / nrm;
 }
 
-template <int SIDE, int TR>
-cudaError_t launch_sweep_t(const SweepArgs &a, cudaStream_t s) {
+template <int SIDE, int TR, int CL>
+cudaLaunchConfig_t sweep_config(int M, cudaLaunchAttribute *at, cudaStream_t s, cudaError_t *e) {
   constexpr int NT = SIDE * SIDE;
-  const size_t smem = (size_t)sweep_smem_floats(a.M, SIDE * TR, SIDE) * 4;
-  cudaError_t e = cudaFuncSetAttribute(ksvd_sweep_kernel<SIDE, TR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
+  const size_t smem = (size_t)sweep_smem_floats(SIDE * TR, SIDE, CL) * 4;
+  *e = cudaFuncSetAttribute(ksvd_sweep_kernel<SIDE, TR, CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (*e == cudaSuccess && CL > 8)
+    *e = cudaFuncSetAttribute(ksvd_sweep_kernel<SIDE, TR, CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(kCL);
+  cfg.gridDim = dim3(CL);
   cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
-  cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = kCL;
+  at[0].val.clusterDim.x = CL;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, ksvd_sweep_kernel<SIDE, TR>, a);
+  return cfg;
+}
+
+// Whether one cluster of CL CTAs of this shape can be resident on the device.
+template <int SIDE, int TR, int CL>
+bool sweep_fits(int M) {
+  cudaLaunchAttribute at[1];
+  cudaError_t e;
+  cudaLaunchConfig_t cfg = sweep_config<SIDE, TR, CL>(M, at, nullptr, &e);
+  int n = 0;
+  if (e != cudaSuccess || cudaOccupancyMaxActiveClusters(&n, ksvd_sweep_kernel<SIDE, TR, CL>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return n >= 1;
+}
+
+template <int SIDE, int TR, int CL>
+cudaError_t launch_sweep_t(const SweepArgs &a, cudaStream_t s) {
+  cudaLaunchAttribute at[1];
+  cudaError_t e;
+  cudaLaunchConfig_t cfg = sweep_config<SIDE, TR, CL>(a.M, at, s, &e);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchKernelEx(&cfg, ksvd_sweep_kernel<SIDE, TR, CL>, a);
+}
+
+template <int CL>
+cudaError_t launch_sweep_cl(const SweepArgs &a, cudaStream_t s) {
+  const int M = a.M;
+  if (M <= 16) return launch_sweep_t<16, 1, CL>(a, s);
+  if (M <= 32) return launch_sweep_t<16, 2, CL>(a, s);
+  if (M <= 48) return launch_sweep_t<16, 3, CL>(a, s);
+  if (M <= 64) return launch_sweep_t<16, 4, CL>(a, s);
+  if (M <= 128) return launch_sweep_t<16, 8, CL>(a, s);
+  return launch_sweep_t<32, 6, CL>(a, s);
+}
+
+bool sweep_fits_16(int M) {
+  if (M <= 16) return sweep_fits<16, 1, 16>(M);
+  if (M <= 32) return sweep_fits<16, 2, 16>(M);
+  if (M <= 48) return sweep_fits<16, 3, 16>(M);
+  if (M <= 64) return sweep_fits<16, 4, 16>(M);
+  if (M <= 128) return sweep_fits<16, 8, 16>(M);
+  return sweep_fits<32, 6, 16>(M);
 }
 
 }  // namespace
 
-int ksvd_owner_split() { return kCL; }
-
-size_t ksvd_sweep_smem_bytes(int M) {
-  if (M <= 16) return (size_t)sweep_smem_floats(M, 16, 16) * 4;
-  if (M <= 32) return (size_t)sweep_smem_floats(M, 32, 16) * 4;
-  if (M <= 48) return (size_t)sweep_smem_floats(M, 48, 16) * 4;
-  if (M <= 64) return (size_t)sweep_smem_floats(M, 64, 16) * 4;
-  if (M <= 128) return (size_t)sweep_smem_floats(M, 128, 16) * 4;
-  return (size_t)sweep_smem_floats(M, 192, 32) * 4;
+int ksvd_owner_split(int M, int T) {
+  // Sixteen ranks (a non-portable cluster) when one fits on the device and the
+  // sort's shared histogram (T x 16 counters) stays within 128 KB; else eight.
+  return (T * 16 <= 32768 && sweep_fits_16(M)) ? 16 : 8;
 }
 
 int ksvd_chunks(int64_t N) { return (int)((N + kChunk - 1) / kChunk); }
@@ -706,17 +741,12 @@ void launch_ksvd_sort(const float *D, int M, int T, const float *X, int N, const
   }
 }
 
-cudaError_t launch_ksvd_sweep(float *D, int M, int T, const float *X, int N, float *coef, int Kmax, const int *off,
-                              const int32_t *seg, float *R, float *rn2, const float *xn2, uint8_t *taken, int replace,
-                              const int32_t *rparent, const int32_t *rsup, int Kc, unsigned long long *stats,
-                              cudaStream_t s) {
+cudaError_t launch_ksvd_sweep(float *D, int M, int T, const float *X, int N, float *coef, int Kmax, int split,
+                              const int *off, const int32_t *seg, float *R, float *rn2, const float *xn2,
+                              uint8_t *taken, int replace, const int32_t *rparent, const int32_t *rsup, int Kc,
+                              unsigned long long *stats, cudaStream_t s) {
   SweepArgs a{D, M, T, X, N, coef, Kmax, off, seg, R, rn2, xn2, taken, replace, rparent, rsup, Kc, stats};
-  if (M <= 16) return launch_sweep_t<16, 1>(a, s);
-  if (M <= 32) return launch_sweep_t<16, 2>(a, s);
-  if (M <= 48) return launch_sweep_t<16, 3>(a, s);
-  if (M <= 64) return launch_sweep_t<16, 4>(a, s);
-  if (M <= 128) return launch_sweep_t<16, 8>(a, s);
-  return launch_sweep_t<32, 6>(a, s);
+  return split == 16 ? launch_sweep_cl<16>(a, s) : launch_sweep_cl<8>(a, s);
 }
 
 void launch_ksvd_sum(const float *rn2, int N, float *out, cudaStream_t s) {
