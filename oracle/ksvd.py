@@ -37,6 +37,13 @@ Readings where the passages are silent (each listed in the design notes):
   Signals with a zero norm are never picked.
 * Random picks (initialisation) are passed in as uniform numbers u in [0, 1):
   the pick from an ordered list of n items is item floor(u n).
+
+Approximate update (an option; Rubinstein, Zibulevsky and Elad, "Efficient
+implementation of the K-SVD algorithm using Batch Orthogonal Matching
+Pursuit", 2008): instead of the leading singular vector, one alternating step
+from the current coefficients -- d_k = E_k^T alpha_k / ||E_k^T alpha_k||, then
+alpha_k = E_k d_k -- each half minimises ||E_k - alpha d^T||_F over its own
+variable, so the error never grows.  E_k^T alpha_k = 0 keeps the atom.
 """
 
 from __future__ import annotations
@@ -85,7 +92,7 @@ def _eligible(k: int, taken, X_norm2, repl_parent, repl_support) -> np.ndarray:
 def ksvd_update(D: np.ndarray, X: np.ndarray, omega: np.ndarray, alpha: np.ndarray,
                 k_eff: np.ndarray, replace_unused: bool = False,
                 repl_parent: Optional[np.ndarray] = None,
-                repl_support: Optional[np.ndarray] = None):
+                repl_support: Optional[np.ndarray] = None, approximate: bool = False):
     """One dictionary-update sweep of K-SVD over atoms k = 0 .. T-1 in order.
 
     D: [T, M] atoms (rows); X: [N, M] training signals; omega/alpha [N, Kmax]
@@ -94,6 +101,8 @@ def ksvd_update(D: np.ndarray, X: np.ndarray, omega: np.ndarray, alpha: np.ndarr
     ([T], coarse parent of each atom) and repl_support ([N, Kc] coarse
     supports, -1 padded) only signals whose coarse support holds the atom's
     parent may replace it (heuristic 4), else any signal (heuristic 3).
+    approximate: the one-step update from the current coefficients (module
+    docstring) instead of the singular vector.
     Returns (D_new [T, M], alpha_new [N, Kmax], replaced: list of (k, i))."""
     D = np.array(D, np.float64, copy=True)
     A = np.array(alpha, np.float64, copy=True)
@@ -120,6 +129,15 @@ def ksvd_update(D: np.ndarray, X: np.ndarray, omega: np.ndarray, alpha: np.ndarr
         I = np.array([u[0] for u in us])
         J = np.array([u[1] for u in us])
         E = R[I] + A[I, J][:, None] * D[k][None, :]        # rows e_i, [n, M]
+        if approximate:
+            g = E.T @ A[I, J]                              # E_k^T alpha_k
+            ng = np.linalg.norm(g)
+            u = g / ng if ng > 0.0 else D[k].copy()
+            a = E @ u
+            D[k] = u
+            A[I, J] = a
+            R[I] = E - a[:, None] * u[None, :]
+            continue
         U, s, _ = np.linalg.svd(E.T, full_matrices=False)  # E^T = M x n
         if s[0] == 0.0:
             A[I, J] = E @ D[k]
@@ -193,7 +211,7 @@ def restricted_coding(D_high: np.ndarray, X: np.ndarray, parent: np.ndarray, T_l
 
 def modified_ksvd(X: np.ndarray, X_low: np.ndarray, parent: np.ndarray, K_low: int, K_high: int,
                   u_low: np.ndarray, u_high: np.ndarray, iters_low: int, iters_high: int,
-                  replace_unused: bool = True, nthreads: int = 0):
+                  replace_unused: bool = True, nthreads: int = 0, approximate: bool = False):
     """Sec. III, learning cross-scale models: Step 1 (K-SVD on W X from heuristic 1), Step 2 (K-SVD on X
     from heuristic 2 with the coding restricted to f(Omega_low)).
 
@@ -206,13 +224,13 @@ def modified_ksvd(X: np.ndarray, X_low: np.ndarray, parent: np.ndarray, K_low: i
     err_low = []
     for _ in range(iters_low):
         o, a, k, _ = omp_batch([D_low] * n, X_low, K_low, nthreads=nthreads)
-        D_low, a, _ = ksvd_update(D_low, X_low, o, a, k, replace_unused)
+        D_low, a, _ = ksvd_update(D_low, X_low, o, a, k, replace_unused, approximate=approximate)
         err_low.append(float(np.sum(residuals(D_low, X_low, o, a, k) ** 2)))
     om_low, _, ke_low, _ = omp_batch([D_low] * n, X_low, K_low, nthreads=nthreads)
     D_high = init_children(X, parent, om_low, ke_low, T_low, u_high)
     err_high = []
     for _ in range(iters_high):
         o, a, k, _ = restricted_coding(D_high, X, parent, T_low, om_low, ke_low, K_high, nthreads)
-        D_high, a, _ = ksvd_update(D_high, X, o, a, k, replace_unused, parent, om_low)
+        D_high, a, _ = ksvd_update(D_high, X, o, a, k, replace_unused, parent, om_low, approximate)
         err_high.append(float(np.sum(residuals(D_high, X, o, a, k) ** 2)))
     return D_low, D_high, om_low, ke_low, err_low, err_high

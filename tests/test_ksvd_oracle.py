@@ -195,3 +195,43 @@ def test_modified_ksvd_reduces_error_and_keeps_zero_tree_supports():
     for i in range(len(X)):
         allowed = set(np.flatnonzero(np.isin(parent, om_low[i, :ke_low[i]])))
         assert set(o[i, :k[i]]) <= allowed
+
+
+def test_approximate_update_is_exact_on_rank_one_and_never_grows_the_error():
+    """Approximate update (one alternating step from the current coefficients):
+    on rank-one users it gives the singular vector like the exact update; on
+    general data each visit minimises the error over d for fixed alpha and
+    over alpha for fixed d, so the objective never grows, and it stays at or
+    above the exact update's (Eckart-Young bound per visit)."""
+    rng = np.random.default_rng(8)
+    N, M, T = 40, 7, 5
+    G = rng.standard_normal((T, M))
+    G /= np.linalg.norm(G, axis=1, keepdims=True)
+    k_of = np.arange(N) % T
+    c = rng.uniform(0.5, 2.0, N) * rng.choice([-1, 1], N)
+    X = c[:, None] * G[k_of]
+    D0 = G + 0.3 * rng.standard_normal((T, M))
+    D0 /= np.linalg.norm(D0, axis=1, keepdims=True)
+    om = k_of[:, None].astype(np.int32)
+    al = c[:, None] * np.sum(D0[k_of] * G[k_of], axis=1, keepdims=True)   # alpha = <x, d0>
+    Da, Aa, _ = ksvd.ksvd_update(D0, X, om, al, np.ones(N, np.int32), approximate=True)
+    De, Ae, _ = ksvd.ksvd_update(D0, X, om, al, np.ones(N, np.int32))
+    np.testing.assert_allclose(Da, De, atol=1e-12)
+    np.testing.assert_allclose(Aa, Ae, atol=1e-12)
+
+    N, M, T, K = 150, 6, 12, 3
+    D, X, om, al, ke = _random_problem(rng, N, M, T, K)
+    before = _objective(D, X, om, al, ke)
+    Da, Aa, _ = ksvd.ksvd_update(D, X, om, al, ke, approximate=True)
+    after = _objective(Da, X, om, Aa, ke)
+    assert after <= before * (1 + 1e-12)
+    np.testing.assert_allclose(np.linalg.norm(Da, axis=1), 1.0, atol=1e-12)
+    # one visit alone: approximate error >= exact error (exact is optimal)
+    users = np.array([i for i in range(N) if 0 in om[i, :ke[i]]])
+    sl = np.array([list(om[i]).index(0) for i in users])
+    E = np.stack([X[i] - sum(al[i, j] * D[om[i, j]] for j in range(ke[i]) if om[i, j] != 0) for i in users])
+    lam = scipy.linalg.eigvalsh(E.T @ E)[-1]
+    D1, A1, _ = ksvd.ksvd_update(D[:1], E, np.zeros((len(users), 1), np.int32), al[users, sl][:, None],
+                                 np.ones(len(users), np.int32), approximate=True)
+    e1 = float(np.sum((E - A1[:, :1] * D1[0]) ** 2))
+    assert e1 >= float(np.sum(E * E)) - lam - 1e-9
