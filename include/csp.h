@@ -263,6 +263,11 @@ csp_status csp_downsample(csp_ctx *ctx, int level, const float *X, int64_t N, fl
  * found by the power method from the old d_k to an FP32 fixed point), signed
  * so that <d_new, d_old> >= 0; alpha_ik becomes <e_i, d_k>; the residuals
  * follow.  An atom with E_k = 0 keeps its value.
+ * approximate = 1 replaces the singular vector by one alternating step from
+ *   the current coefficients (Rubinstein, Zibulevsky and Elad 2008, "Efficient
+ *   implementation of the K-SVD algorithm using Batch OMP"): d_k = E_k^T
+ *   alpha_k / ||E_k^T alpha_k|| (kept when zero), then alpha_ik = <e_i, d_k>;
+ *   the error never grows.  0 = the exact update.
  * D: DEVICE float32 [T][M] (atom-major), updated in place.
  * X: DEVICE float32 [N][M] training signals.
  * support / coef: DEVICE [N][Kmax] as csp_solve writes them (atom ids into D,
@@ -283,8 +288,8 @@ csp_status csp_downsample(csp_ctx *ctx, int level, const float *X, int64_t N, fl
  *   complete (work is ordered after earlier work on `stream`). */
 csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X, int64_t N,
                            const int32_t *support, float *coef, const int8_t *k_eff, int Kmax,
-                           int replace_unused, const int32_t *repl_parent, const int32_t *repl_support,
-                           int Kc, float *err_out, void *stream);
+                           int replace_unused, int approximate, const int32_t *repl_parent,
+                           const int32_t *repl_support, int Kc, float *err_out, void *stream);
 
 /* Counters of the last csp_ksvd_update on this context: power_steps = the
  * power-method steps summed over the visited atoms (a step is one product

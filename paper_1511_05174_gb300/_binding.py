@@ -152,7 +152,7 @@ def load_library(path: str = LIB_PATH):
         "csp_job_release": (i, [vp, ctypes.c_uint64]),
         "csp_server_pause": (i, [vp, i]),
         "csp_downsample": (i, [vp, i, vp, ctypes.c_int64, vp, vp]),
-        "csp_ksvd_update": (i, [vp, vp, i, i, vp, ctypes.c_int64, vp, vp, vp, i, i, vp, vp, i, vp, vp]),
+        "csp_ksvd_update": (i, [vp, vp, i, i, vp, ctypes.c_int64, vp, vp, vp, i, i, i, vp, vp, i, vp, vp]),
         "csp_ksvd_init_atoms": (i, [vp, vp, i, i, vp, ctypes.c_int64, vp, vp, vp, i, i, vp, vp]),
         "csp_ksvd_stats_get": (i, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                    ctypes.POINTER(ctypes.c_int64)]),
@@ -360,10 +360,11 @@ def csp_downsample(ctx, level: int, X_ptr: int, N: int, X_low_ptr: int, stream: 
 
 
 def csp_ksvd_update(ctx, D_ptr: int, M: int, T: int, X_ptr: int, N: int, sup_ptr: int, coef_ptr: int,
-                    keff_ptr: int, Kmax: int, replace_unused: int, parent_ptr, rsup_ptr, Kc: int, err_ptr,
-                    stream: int = 0) -> None:
+                    keff_ptr: int, Kmax: int, replace_unused: int, approximate: int, parent_ptr, rsup_ptr, Kc: int,
+                    err_ptr, stream: int = 0) -> None:
     check(load_library().csp_ksvd_update(ctx, D_ptr, M, T, X_ptr, N, sup_ptr, coef_ptr, keff_ptr, Kmax,
-                                         replace_unused, parent_ptr, rsup_ptr, Kc, err_ptr, stream), ctx)
+                                         replace_unused, approximate, parent_ptr, rsup_ptr, Kc, err_ptr, stream),
+          ctx)
 
 
 def csp_ksvd_init_atoms(ctx, D_ptr: int, M: int, T: int, X_ptr: int, N: int, parent_ptr, sup_low_ptr,

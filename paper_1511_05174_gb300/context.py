@@ -243,16 +243,18 @@ class Context:
     def ksvd_update(self, D: torch.Tensor, X: torch.Tensor, sup: torch.Tensor, coef: torch.Tensor,
                     keff: torch.Tensor, replace_unused: bool = False, repl_parent: Optional[torch.Tensor] = None,
                     repl_support: Optional[torch.Tensor] = None, err_out: Optional[torch.Tensor] = None,
-                    stream=None) -> None:
+                    stream=None, approximate: bool = False) -> None:
         """One K-SVD dictionary-update sweep in place on D [T, M] and coef
         [N, Kmax] (csp_ksvd_update); err_out (float32 [1]) receives
-        ||X - D S||_F^2 after the sweep."""
+        ||X - D S||_F^2 after the sweep; approximate: one alternating step per
+        atom instead of the singular vector."""
         for t in (D, X, sup, coef, keff):
             assert t.is_cuda and t.is_contiguous()
         T, M = D.shape
         Kc = int(repl_support.shape[1]) if repl_support is not None else 0
         b.csp_ksvd_update(self._ctx, D.data_ptr(), int(M), int(T), X.data_ptr(), int(X.shape[0]), sup.data_ptr(),
                           coef.data_ptr(), keff.data_ptr(), int(sup.shape[1]), int(bool(replace_unused)),
+                          int(bool(approximate)),
                           repl_parent.data_ptr() if repl_parent is not None else None,
                           repl_support.data_ptr() if repl_support is not None else None, Kc,
                           err_out.data_ptr() if err_out is not None else None, _stream_ptr(stream, self.device))

@@ -1446,7 +1446,7 @@ csp_status csp_downsample(csp_ctx *ctx, int level, const float *X, int64_t N, fl
 
 
 csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X, int64_t N, const int32_t *support,
-                           float *coef, const int8_t *k_eff, int Kmax, int replace_unused,
+                           float *coef, const int8_t *k_eff, int Kmax, int replace_unused, int approximate,
                            const int32_t *repl_parent, const int32_t *repl_support, int Kc, float *err_out,
                            void *stream) {
   if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
@@ -1456,6 +1456,7 @@ csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X,
   if (Kmax < 1 || Kmax > CSP_MAX_K) return fail(ctx, CSP_ERR_INVALID, "Kmax must be in 1 .. CSP_MAX_K");
   if (N < 0 || N * Kmax > INT32_MAX) return fail(ctx, CSP_ERR_INVALID, "N * Kmax must be below 2^31");
   if (replace_unused != 0 && replace_unused != 1) return fail(ctx, CSP_ERR_INVALID, "replace_unused must be 0 or 1");
+  if (approximate != 0 && approximate != 1) return fail(ctx, CSP_ERR_INVALID, "approximate must be 0 or 1");
   if ((repl_parent == nullptr) != (repl_support == nullptr))
     return fail(ctx, CSP_ERR_INVALID, "repl_parent and repl_support go together");
   if (repl_support && (Kc < 1 || N * Kc > INT32_MAX)) return fail(ctx, CSP_ERR_INVALID, "Kc out of range");
@@ -1476,7 +1477,7 @@ csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X,
   cudaError_t le = cudaSuccess;
   run(ctx, KK_KSVD_SWEEP, s, 1, [&] {
     le = launch_ksvd_sweep(D, M, T, X, n, coef, Kmax, split, off, seg, R, rn2, xn2, taken, replace_unused,
-                           repl_parent, repl_support, Kc, st, s);
+                           repl_parent, repl_support, Kc, st, approximate, s);
   });
   if (le != cudaSuccess) return fail(ctx, CSP_ERR_CUDA, std::string("K-SVD sweep launch: ") + cudaGetErrorString(le));
   if (err_out) {

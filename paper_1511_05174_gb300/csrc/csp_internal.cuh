@@ -332,11 +332,11 @@ void launch_ksvd_sort(const float *D, int M, int T, const float *X, int N, const
                       const int8_t *keff, int Kmax, int split, float *R, float *rn2, float *xn2, int *hist, int *off,
                       int32_t *seg, unsigned *err, cudaStream_t s);
 // The sequential atom sweep (one thread-block cluster); stats[0] = power-method
-// steps, stats[1] = replaced atoms.
+// steps, stats[1] = replaced atoms; approx = 1: one alternating step per atom.
 cudaError_t launch_ksvd_sweep(float *D, int M, int T, const float *X, int N, float *coef, int Kmax, int split,
                               const int *off, const int32_t *seg, float *R, float *rn2, const float *xn2,
                               uint8_t *taken, int replace, const int32_t *rparent, const int32_t *rsup, int Kc,
-                              unsigned long long *stats, cudaStream_t s);
+                              unsigned long long *stats, int approx, cudaStream_t s);
 void launch_ksvd_sum(const float *rn2, int N, float *out, cudaStream_t s);
 // Initialisation picks; off == nullptr: from all N signals.
 void launch_ksvd_init(float *D, int M, int T, const float *X, int N, const int32_t *parent, const int *off,

@@ -231,6 +231,7 @@ struct SweepArgs {
   const int32_t *rparent, *rsup;
   int Kc;
   unsigned long long *stats;  // [0] power-method steps, [1] replaced atoms
+  int approx;                 // 1: one alternating step from the current coefficients
 };
 
 
@@ -409,6 +410,7 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
     for (int i = 0; i < TR; ++i)
 #pragma unroll
       for (int j = 0; j < TR; ++j) acc[i][j] = 0.f;
+    float ya = 0.f;   // approximate update: (E_r^T alpha_r)[tid], over this rank's users in slot order
     for (int b0 = 0; b0 < nr; b0 += NB) {
       const int nb = min(NB, nr - b0);
       for (int c = (b0 == 0 ? NT : 0) + tid; c < nb; c += NT) {   // the first NT of batch 0 are prefetched
@@ -420,6 +422,10 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
       __syncthreads();
       stage_cols(nb);
       __syncthreads();
+      if (a.approx) {
+        if (tid < M)
+          for (int c = 0; c < nb; ++c) ya = fmaf(stage[c * MP + tid], als[c], ya);
+      } else
 #pragma unroll 2
       for (int c = 0; c < nb; ++c) {
         const float *ec = stage + c * MP;
@@ -435,8 +441,43 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
     }
     // acc now holds this thread's tile of C_r (zero past M) and stays in registers
 
+    // y = sum over ranks of yl (rank order) into ysum: push yl into every rank's
+    // receive slot of this step's parity, one cluster barrier, local sums.
+    auto reduce_ranks = [&]() {
+      float *rxp = rx + (gstep & 1) * CL * MP;
+      ++gstep;
+      for (int t = tid; t < CL * M; t += NT) {
+        const int q = t / M, m = t - q * M;
+        cl.map_shared_rank(rxp, q)[rank * MP + m] = yl[m];
+      }
+      cl.sync();
+      for (int m = tid; m < M; m += NT) {
+        float ym = 0.f;
+#pragma unroll 4
+        for (int q = 0; q < CL; ++q) ym += rxp[q * MP + m];
+        ysum[m] = ym;
+      }
+      __syncthreads();
+    };
+
     for (int m = tid; m < M; m += NT) vb0[m] = dold[m];
     __syncthreads();
+    float *v = vb0;
+    if (a.approx) {
+      // ---- approximate update: d_k = E_k^T alpha_k / ||.|| (no sign rule) ----
+      if (tid < M) yl[tid] = ya;
+      __syncthreads();
+      reduce_ranks();
+      float ss = 0.f;
+      for (int m = lane; m < M; m += 32) ss = fmaf(ysum[m], ysum[m], ss);
+      ss = warp_sum(ss);
+      if (ss > 0.f) {
+        const float inv = 1.f / sqrtf(ss);
+        for (int m = tid; m < M; m += NT) vb0[m] = ysum[m] * inv;
+      }
+      steps += 1;
+      __syncthreads();
+    } else {
 
     // ---- leading eigenvector of C = sum_r C_r by the power method from d_old ----
     // The ranks never form C.  Step t: every thread multiplies its register
@@ -454,8 +495,6 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
     for (int it = 0; it < kMaxIt; ++it) {
       const float *v = cur ? vb1 : vb0;
       float *vn = cur ? vb0 : vb1;
-      float *rxp = rx + (gstep & 1) * CL * MP;
-      ++gstep;
       {
         float vv[TR], py[TR];
         lds_run<TR>(vv, v + c0);
@@ -476,18 +515,7 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
             if (r0 + i < M) yl[r0 + i] = py[i];
       }
       __syncthreads();
-      for (int t = tid; t < CL * M; t += NT) {
-        const int q = t / M, m = t - q * M;
-        cl.map_shared_rank(rxp, q)[rank * MP + m] = yl[m];
-      }
-      cl.sync();
-      for (int m = tid; m < M; m += NT) {
-        float ym = 0.f;
-#pragma unroll 4
-        for (int q = 0; q < CL; ++q) ym += rxp[q * MP + m];
-        ysum[m] = ym;
-      }
-      __syncthreads();
+      reduce_ranks();
       float ss = 0.f, d2 = 0.f;
       for (int m = lane; m < M; m += 32) {
         ss = fmaf(ysum[m], ysum[m], ss);
@@ -509,7 +537,7 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
       cur ^= 1;
       if (it == kMaxIt - 1) steps += kMaxIt;
     }
-    float *v = zero ? dold : (cur ? vb1 : vb0);
+    v = zero ? dold : (cur ? vb1 : vb0);
     {  // sign: <d_new, d_old> >= 0 (every warp computes it; all agree)
       float s = 0.f;
       for (int m = lane; m < M; m += 32) s = fmaf(v[m], dold[m], s);
@@ -520,6 +548,7 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
       }
       __syncthreads();
     }
+    }  // exact update
     if (rank == 0)
       for (int m = tid; m < M; m += NT) a.D[(size_t)k * M + m] = v[m];
 
@@ -744,8 +773,8 @@ void launch_ksvd_sort(const float *D, int M, int T, const float *X, int N, const
 cudaError_t launch_ksvd_sweep(float *D, int M, int T, const float *X, int N, float *coef, int Kmax, int split,
                               const int *off, const int32_t *seg, float *R, float *rn2, const float *xn2,
                               uint8_t *taken, int replace, const int32_t *rparent, const int32_t *rsup, int Kc,
-                              unsigned long long *stats, cudaStream_t s) {
-  SweepArgs a{D, M, T, X, N, coef, Kmax, off, seg, R, rn2, xn2, taken, replace, rparent, rsup, Kc, stats};
+                              unsigned long long *stats, int approx, cudaStream_t s) {
+  SweepArgs a{D, M, T, X, N, coef, Kmax, off, seg, R, rn2, xn2, taken, replace, rparent, rsup, Kc, stats, approx};
   return split == 16 ? launch_sweep_cl<16>(a, s) : launch_sweep_cl<8>(a, s);
 }
 

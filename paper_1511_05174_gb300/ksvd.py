@@ -28,7 +28,8 @@ class ModifiedKSVD:
     and the scale links parent[j] (coarse atom of fine atom j)."""
 
     def __init__(self, P: int, plane_grid: Sequence[int], level_factors, parent: np.ndarray, K_high: int,
-                 K_low: int, device: int = 0, precision: str = "fp32", replace_unused: bool = True):
+                 K_low: int, device: int = 0, precision: str = "fp32", replace_unused: bool = True,
+                 approximate: bool = False):
         if len(level_factors) != 2:
             raise ValueError("two scales")
         fy, fx, sy, sx = level_factors[1]
@@ -39,6 +40,7 @@ class ModifiedKSVD:
         self.K_high, self.K_low = int(K_high), int(K_low)
         self.precision = precision
         self.replace = bool(replace_unused)
+        self.approximate = bool(approximate)   # one alternating step per atom instead of the SVD
         Ly, Lx = int(plane_grid[0]), int(plane_grid[1])
         self.fine = Context(device)          # both scales; Step 2 coding and W
         self.fine.set_geometry(P, P, (Ly, Lx), P, P, level_factors)
@@ -66,7 +68,8 @@ class ModifiedKSVD:
         for _ in range(iters_low):
             self.coarse.load_dictionary(0, D_low)
             sup, coef, keff = self.coarse.solve(X_low, mode="plain", precision=self.precision, K=(self.K_low,))
-            self.coarse.ksvd_update(D_low, X_low, sup, coef, keff, self.replace, err_out=err)
+            self.coarse.ksvd_update(D_low, X_low, sup, coef, keff, self.replace, err_out=err,
+                                    approximate=self.approximate)
             err_low.append(float(err.item()))
         self.coarse.load_dictionary(0, D_low)
         sup_low, _, keff_low = self.coarse.solve(X_low, mode="plain", precision=self.precision, K=(self.K_low,))
@@ -75,7 +78,8 @@ class ModifiedKSVD:
                                   self.parent_dev, sup_low, keff_low, T_low)
         for _ in range(iters_high):
             sup, coef, keff = self.code_high(D_high, D_low, X)
-            self.fine.ksvd_update(D_high, X, sup, coef, keff, self.replace, self.parent_dev, sup_low, err_out=err)
+            self.fine.ksvd_update(D_high, X, sup, coef, keff, self.replace, self.parent_dev, sup_low, err_out=err,
+                                  approximate=self.approximate)
             err_high.append(float(err.item()))
         return D_low, D_high, sup_low, keff_low, err_low, err_high
 

@@ -43,7 +43,7 @@ def _problem(N, M, T, K, seed, perturb=0.15, sigma=0.01):
     return D0, Y, om.astype(np.int32), al.astype(np.float32), ke.astype(np.int8)
 
 
-def _gpu_update(ctx, D0, X, om, al, ke, replace=False, parent=None, rsup=None):
+def _gpu_update(ctx, D0, X, om, al, ke, replace=False, parent=None, rsup=None, approximate=False):
     dev = ctx.device
     D = torch.from_numpy(D0.copy()).to(dev)
     Xd = torch.from_numpy(np.ascontiguousarray(X, np.float32)).to(dev)
@@ -53,7 +53,7 @@ def _gpu_update(ctx, D0, X, om, al, ke, replace=False, parent=None, rsup=None):
     err = torch.zeros(1, dtype=torch.float32, device=dev)
     p = torch.from_numpy(parent.astype(np.int32)).to(dev) if parent is not None else None
     r = torch.from_numpy(rsup.astype(np.int32)).to(dev) if rsup is not None else None
-    ctx.ksvd_update(D, Xd, sup, coef, keff, replace, p, r, err)
+    ctx.ksvd_update(D, Xd, sup, coef, keff, replace, p, r, err, approximate=approximate)
     torch.cuda.synchronize()
     return D.cpu().numpy(), coef.cpu().numpy(), float(err.item())
 
@@ -80,6 +80,22 @@ def test_sweep_matches_oracle(N, M, T, K):
     assert np.all(Ag[~mask] == al[~mask])            # padded slots untouched
     assert e_g == pytest.approx(e_o, rel=RTOL_E)
     np.testing.assert_allclose(np.linalg.norm(Dg, axis=1), 1.0, atol=1e-5)
+
+
+@pytest.mark.parametrize("N,M,T,K", [(3001, 16, 32, 3), (3001, 64, 128, 5), (1500, 192, 256, 6), (1200, 100, 160, 4)])
+def test_approximate_sweep_matches_oracle(N, M, T, K):
+    """The approximate update (one alternating step per atom) against the
+    oracle's approximate update: same bar as the exact sweep."""
+    D0, X, om, al, ke = _problem(N, M, T, K, seed=M + T + 1, perturb=0.3)
+    Do, Ao, _ = oksvd.ksvd_update(D0, X, om, al, ke, approximate=True)
+    e_o = float(np.sum(oksvd.residuals(Do, X, om, Ao, ke) ** 2))
+    ctx = _ctx()
+    Dg, Ag, e_g = _gpu_update(ctx, D0, X, om, al, ke, approximate=True)
+    assert np.max(np.abs(Dg - Do)) <= ATOL_D
+    mask = np.arange(om.shape[1])[None, :] < ke[:, None]
+    assert np.max(np.abs(np.where(mask, Ag - Ao, 0.0))) <= RTOL_A * np.max(np.abs(Ao[mask]))
+    assert e_g == pytest.approx(e_o, rel=RTOL_E)
+    assert ctx.ksvd_stats()[0] == T     # one exchange per visited atom
 
 
 def _drop_atoms(om, ke, unused, T, seed):
@@ -199,7 +215,8 @@ def test_downsample_is_W():
     mk.close()
 
 
-def test_modified_ksvd_tracks_the_oracle():
+@pytest.mark.parametrize("approximate", [False, True])
+def test_modified_ksvd_tracks_the_oracle(approximate):
     """Steps 1 and 2 end to end: every sweep lowers the error, the final
     errors are within 2 % of the oracle's run (the FP32 coding may break near
     ties differently), and Step-2 supports stay in f(Omega_low)."""
@@ -207,13 +224,15 @@ def test_modified_ksvd_tracks_the_oracle():
     g = ts.geometry
     X = ts.X
     from paper_1511_05174_gb300.ksvd import ModifiedKSVD
-    mk = ModifiedKSVD(g.P, g.plane_grid, g.level_factors, ts.parents[0], ts.K_high, ts.K_low)
+    mk = ModifiedKSVD(g.P, g.plane_grid, g.level_factors, ts.parents[0], ts.K_high, ts.K_low,
+                      approximate=approximate)
     Xd = torch.from_numpy(X).to(mk.dev)
     D_low, D_high, sup_low, keff_low, el, eh = mk.fit(Xd, ts.u_low, ts.u_high, 4, 4)
     assert np.all(np.diff(el) < 0) and np.all(np.diff(eh) < 0)
     X_low = oracle.W_down(X.astype(np.float64), g, 1)
     _, _, _, _, el_o, eh_o = oksvd.modified_ksvd(X.astype(np.float64), X_low, ts.parents[0], ts.K_low,
-                                                 ts.K_high, ts.u_low, ts.u_high, 4, 4)
+                                                 ts.K_high, ts.u_low, ts.u_high, 4, 4,
+                                                 approximate=approximate)
     assert el[-1] == pytest.approx(el_o[-1], rel=0.02)
     assert eh[-1] == pytest.approx(eh_o[-1], rel=0.02)
     sup, _, keff = mk.code_high(D_high, D_low, Xd)
