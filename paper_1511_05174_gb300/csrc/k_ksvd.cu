@@ -516,17 +516,21 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
       }
       __syncthreads();
       reduce_ranks();
-      float ss = 0.f, d2 = 0.f;
-      for (int m = lane; m < M; m += 32) {
-        ss = fmaf(ysum[m], ysum[m], ss);
-        if (it) d2 += dd[m];
+      if (warp == 0) {   // ||y||^2 and the last step's change, published to the CTA
+        float s2 = 0.f, c2 = 0.f;
+        for (int m = lane; m < M; m += 32) {
+          s2 = fmaf(ysum[m], ysum[m], s2);
+          if (it) c2 += dd[m];
+        }
+        s2 = warp_sum(s2);
+        c2 = warp_sum(c2);
+        if (lane == 0) { scal[0] = s2; scal[1] = c2; }
       }
-      ss = warp_sum(ss);
-      d2 = warp_sum(d2);
+      __syncthreads();
+      const float ss = scal[0], d2 = scal[1];
       if (it && d2 <= kTol2) { steps += it; break; }   // v_t is converged
       if (!(ss > 0.f)) { zero = true; steps += it; break; }
       const float inv = 1.f / sqrtf(ss);
-      __syncthreads();                                  // every warp has read dd
       for (int m = tid; m < M; m += NT) {
         const float nv = ysum[m] * inv;
         const float d = nv - v[m];
