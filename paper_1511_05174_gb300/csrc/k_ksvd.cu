@@ -266,7 +266,6 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
   float *const vb0 = dold0 + 2 * MP, *const vb1 = dold0 + 3 * MP;  // power-method vectors (zero past M)
   float *yl = dold0 + 4 * MP;            // [MP] this rank's C_r v
   float *ysum = dold0 + 5 * MP;          // [MP] C v
-  float *dd = dold0 + 6 * MP;            // [MP] squared change of each component
   float *scal = dold0 + 8 * MP;          // [128] flags, per-warp argmax scratch
   int *ents0 = reinterpret_cast<int *>(scal + 128), *ents1 = ents0 + NB;  // staged slot ids (2 buffers)
   float *als0 = reinterpret_cast<float *>(ents1 + NB), *als1 = als0 + NB;  // their coefficients before the visit
@@ -486,10 +485,9 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
     // receive slot (distributed shared memory stores), and after one cluster
     // barrier every rank adds the CL products in rank order: all ranks hold
     // the same y = C v_t and take the same decisions.  v_{t+1} = y / ||y||;
-    // the change ||v_{t+1} - v_t||^2 is summed one step later; stop when it is
-    // <= kTol2.  Receive slots alternate by step (the alternation runs on across
-    // visits), so a rank writes a slot only after every rank has passed the
-    // barrier that follows its reads of it.
+    // stop when ||v_{t+1} - v_t||^2 <= kTol2.  Receive slots alternate by step
+    // (the alternation runs on across visits), so a rank writes a slot only
+    // after every rank has passed the barrier that follows its reads of it.
     int cur = 0;
     bool zero = false;
     for (int it = 0; it < kMaxIt; ++it) {
@@ -516,29 +514,28 @@ __global__ void __launch_bounds__(SIDE *SIDE, 1) ksvd_sweep_kernel(const SweepAr
       }
       __syncthreads();
       reduce_ranks();
-      if (warp == 0) {   // ||y||^2 and the last step's change, published to the CTA
+      if (warp == 0) {   // ||y||^2 and the change to the next vector, published to the CTA
         float s2 = 0.f, c2 = 0.f;
-        for (int m = lane; m < M; m += 32) {
-          s2 = fmaf(ysum[m], ysum[m], s2);
-          if (it) c2 += dd[m];
-        }
+        for (int m = lane; m < M; m += 32) s2 = fmaf(ysum[m], ysum[m], s2);
         s2 = warp_sum(s2);
-        c2 = warp_sum(c2);
+        if (s2 > 0.f) {
+          const float inv = 1.f / sqrtf(s2);
+          for (int m = lane; m < M; m += 32) {
+            const float d = ysum[m] * inv - v[m];
+            c2 = fmaf(d, d, c2);
+          }
+          c2 = warp_sum(c2);
+        }
         if (lane == 0) { scal[0] = s2; scal[1] = c2; }
       }
       __syncthreads();
       const float ss = scal[0], d2 = scal[1];
-      if (it && d2 <= kTol2) { steps += it; break; }   // v_t is converged
       if (!(ss > 0.f)) { zero = true; steps += it; break; }
       const float inv = 1.f / sqrtf(ss);
-      for (int m = tid; m < M; m += NT) {
-        const float nv = ysum[m] * inv;
-        const float d = nv - v[m];
-        dd[m] = d * d;
-        vn[m] = nv;
-      }
+      for (int m = tid; m < M; m += NT) vn[m] = ysum[m] * inv;
       __syncthreads();
       cur ^= 1;
+      if (d2 <= kTol2) { steps += it + 1; break; }     // v_{t+1} is converged
       if (it == kMaxIt - 1) steps += kMaxIt;
     }
     v = zero ? dold : (cur ? vb1 : vb0);
