@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "csp_internal.cuh"
+#include "ksvd.cuh"
 
 using namespace csp;
 
@@ -1468,7 +1469,7 @@ csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X,
   int32_t *seg = nullptr;
   float *R = nullptr, *rn2 = nullptr, *xn2 = nullptr;
   uint8_t *taken = nullptr;
-  const int split = ksvd_owner_split(M, T);
+  const int split = ksvd_owner_split(M, T, approximate != 0);
   CSP_TRY(ksvd_sort(ctx, D, M, T, X, n, support, coef, k_eff, Kmax, split, true, &off, &seg, &R, &rn2, &xn2, s));
   unsigned long long *st = nullptr;
   CSP_TRY(ws_get_t(ctx, ctx->wsp, WS_KS_TAKEN, (size_t)std::max(n, 1), &taken));

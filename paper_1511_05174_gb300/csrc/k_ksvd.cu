@@ -41,6 +41,7 @@
 #include <stdint.h>
 
 #include "csp_internal.cuh"
+#include "ksvd.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -733,25 +734,30 @@ cudaError_t launch_sweep_cl(const SweepArgs &a, cudaStream_t s) {
   if (M <= 48) return launch_sweep_t<16, 3, CL>(a, s);
   if (M <= 64) return launch_sweep_t<16, 4, CL>(a, s);
   if (M <= 128) return launch_sweep_t<16, 8, CL>(a, s);
-  return launch_sweep_t<32, 6, CL>(a, s);
+  // M <= 192: the exact update's Gram tiles favour 256 threads with 12 x 12
+  // tiles; the approximate update (no Gram) favours 1024 threads (more warps
+  // in flight for staging and the column updates)
+  return a.approx ? launch_sweep_t<32, 6, CL>(a, s) : launch_sweep_t<16, 12, CL>(a, s);
 }
 
-bool sweep_fits_16(int M) {
+bool sweep_fits_16(int M, bool approx) {
   if (M <= 16) return sweep_fits<16, 1, 16>(M);
   if (M <= 32) return sweep_fits<16, 2, 16>(M);
   if (M <= 48) return sweep_fits<16, 3, 16>(M);
   if (M <= 64) return sweep_fits<16, 4, 16>(M);
   if (M <= 128) return sweep_fits<16, 8, 16>(M);
-  return sweep_fits<32, 6, 16>(M);
+  return approx ? sweep_fits<32, 6, 16>(M) : sweep_fits<16, 12, 16>(M);
 }
 
 }  // namespace
 
-int ksvd_owner_split(int M, int T) {
+int ksvd_owner_split(int M, int T, bool approx) {
   // Sixteen ranks (a non-portable cluster) when one fits on the device and the
   // sort's shared histogram (T x 16 counters) stays within 128 KB; else eight.
-  return (T * 16 <= 32768 && sweep_fits_16(M)) ? 16 : 8;
+  return (T * 16 <= 32768 && sweep_fits_16(M, approx)) ? 16 : 8;
 }
+
+int ksvd_owner_split(int M, int T) { return ksvd_owner_split(M, T, false); }
 
 int ksvd_chunks(int64_t N) { return (int)((N + kChunk - 1) / kChunk); }
 
