@@ -260,7 +260,8 @@ csp_status csp_downsample(csp_ctx *ctx, int level, const float *X, int64_t N, fl
  * order; visiting k: E_k = the residuals r_i = x_i - D s_i of the signals
  * whose support holds k, each with alpha_ik d_k added back; d_k becomes the
  * leading left singular vector of E_k (the dominant eigenvector of E_k E_k^T,
- * found by the power method from the old d_k to an FP32 fixed point), signed
+ * found in FP32 by the power method from the old d_k until a step moves the
+ * vector by at most 4e-6, at most 1000 steps), signed
  * so that <d_new, d_old> >= 0; alpha_ik becomes <e_i, d_k>; the residuals
  * follow.  An atom with E_k = 0 keeps its value.
  * approximate = 1 replaces the singular vector by one alternating step from
@@ -293,7 +294,8 @@ csp_status csp_ksvd_update(csp_ctx *ctx, float *D, int M, int T, const float *X,
 
 /* Counters of the last csp_ksvd_update on this context: power_steps = the
  * power-method steps summed over the visited atoms (a step is one product
- * with E_k E_k^T; at most 1000 per atom), replaced = atoms replaced by
+ * with E_k E_k^T; at most 1000 per atom; the approximate update counts one
+ * product E_k^T alpha_k per atom), replaced = atoms replaced by
  * heuristics 3-4, ranks = thread blocks of the sweep's cluster (16 where the
  * device holds such a cluster, else 8).  Any pointer may be NULL. */
 csp_status csp_ksvd_stats_get(csp_ctx *ctx, int64_t *power_steps, int64_t *replaced, int64_t *ranks);
