@@ -293,3 +293,18 @@ def test_full_size_sweep_properties():
     assert (w[-1] - w[-2]) / w[-1] > 0.1
     np.testing.assert_allclose(Dn[T - 1], u, atol=1e-4)
     np.testing.assert_allclose([c_np[i, j] for i, j in users], E @ Dn[T - 1], atol=1e-4 * np.abs(E).max())
+
+
+@pytest.mark.parametrize("approximate", [False, True])
+@pytest.mark.parametrize("N,M,T,K", [(20000, 16, 4, 2), (20000, 64, 6, 2), (6000, 192, 6, 2)])
+def test_sweep_with_many_users_per_rank(N, M, T, K, approximate):
+    """Thousands of users per atom: each rank's slot list exceeds the prefetch
+    (one slot per thread) and the staging capacity, so the batch loads and the
+    restaging of the coefficient update run."""
+    D0, X, om, al, ke = _problem(N, M, T, K, seed=N + M, perturb=0.2)
+    Do, Ao, _ = oksvd.ksvd_update(D0, X, om, al, ke, approximate=approximate)
+    ctx = _ctx()
+    Dg, Ag, _ = _gpu_update(ctx, D0, X, om, al, ke, approximate=approximate)
+    assert np.max(np.abs(Dg - Do)) <= ATOL_D
+    mask = np.arange(om.shape[1])[None, :] < ke[:, None]
+    assert np.max(np.abs(np.where(mask, Ag - Ao, 0.0))) <= RTOL_A * np.max(np.abs(Ao[mask]))
