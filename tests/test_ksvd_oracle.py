@@ -235,3 +235,32 @@ def test_approximate_update_is_exact_on_rank_one_and_never_grows_the_error():
                                  np.ones(len(users), np.int32), approximate=True)
     e1 = float(np.sum((E - A1[:, :1] * D1[0]) ** 2))
     assert e1 >= float(np.sum(E * E)) - lam - 1e-9
+
+
+def test_step2_coding_is_the_fine_step_of_algorithm_2():
+    """Reading R26: Step 2's coding (OMP over the children of Step 1's coarse
+    supports) equals the finer level of Algorithm 2 run on the same pair of
+    dictionaries (which recomputes the coarse supports from W x)."""
+    ts = synthetic.make_training_set("denoise", 300, seed=9, T0=64)
+    g = ts.geometry
+    X = ts.X.astype(np.float64)
+    X_low = oracle.W_down(X, g, 1)
+    D_high, D_low = ts.dicts[0].astype(np.float64), ts.dicts[1].astype(np.float64)
+    parent = ts.parents[0]
+    om_low, _, ke_low, _ = oracle.omp_batch([D_low] * len(X), X_low, ts.K_low)
+    o, a, k, _ = ksvd.restricted_coding(D_high, X, parent, D_low.shape[0], om_low, ke_low, ts.K_high)
+
+    class W:  # the two-level identity problem of these signals, one "patch" per signal
+        pass
+    w = W()
+    w.geometry = g
+    w.sensing = synthetic.Sensing("identity")
+    w.dicts = [D_high, D_low]
+    w.parents = [parent]
+    w.n_levels = 2
+    w.K_levels = [np.full(len(X), ts.K_high, np.int32), np.full(len(X), ts.K_low, np.int32)]
+    o2, a2, k2, _ = oracle.cross_scale_omp(w, Y=X)
+    np.testing.assert_array_equal(k, k2)
+    for i in range(len(X)):
+        assert list(o[i, :k[i]]) == list(o2[i, :k2[i]])
+        np.testing.assert_allclose(a[i, :k[i]], a2[i, :k2[i]], rtol=1e-12, atol=1e-12)
