@@ -25,7 +25,7 @@ Passages followed (arXiv 1511.05174):
   the least-represented training signal, for a fine atom the least-represented
   signal of X|Omega_k of its parent k.
 
-Readings where the passages are silent (each listed in the design notes):
+Readings taken where the passages are silent:
 
 * Sign of the singular vector: the one with <d_new, d_old> >= 0 (an SVD fixes
   it only up to sign; this keeps an atom's sign across sweeps).

@@ -16,7 +16,7 @@ Workloads (sizes follow the configurations this library is measured on):
                     patches, stride 4, D 1024x8192, three scales, K in [8, 20]
                     drawn per patch.
 
-Two readings of the scale links exist:
+Three readings of the scale links exist:
 
 * ``links="paper"`` (default): each coarser level has T/Q atoms (Q = 4), made by
   box-downsampling a seeded subset of the finer atoms and renormalising; every
@@ -26,6 +26,14 @@ Two readings of the scale links exist:
 * ``links="literal"``: every level keeps all T atoms (downsampled and
   renormalised) and each atom is linked to its own downsampled copy, i.e. the
   identity map; the coarse sparsity equals the fine one.
+* ``links="model"``: dictionaries built so that the signal model of
+  Sec. III-A holds exactly -- coarse atoms are unit Gaussian, fine atom i is a
+  child of coarse atom i // Q (block rule of Sec. III-B) whose box-downsampled,
+  renormalised copy is its parent (parent structure plus a detail in the null
+  space of W), and the truth codes are sign-coherent within each subtree so a
+  tile's coarse code W x never cancels.  The solver's coarser budgets are
+  ceil(1.5 K_l) of the truth's (capped by the finer budget): a patch that
+  straddles tiles mixes several tiles' coarse codes.
 
 Vector layout of a patch at any level: index ``((ly * Lx + lx) * Py + py) * Px + px``
 for plane-grid position (ly, lx) (colour channel, frame or view) and pixel
@@ -106,6 +114,7 @@ class Workload:
     sigma: float
     seed: int
     links: str
+    tile_codes: Optional[list] = None  # per P x P tile of the truth, raster order: (support, values)
 
     @property
     def n_patches(self) -> int:
@@ -158,7 +167,59 @@ def _rel_factor(g: Geometry, l: int) -> Tuple[int, int, int, int]:
     return r  # type: ignore[return-value]
 
 
-def _build_dictionaries(g: Geometry, T0: int, Q: int, links: str, rng_dict, rng_subset):
+def _up_rel(V: np.ndarray, shape_fine: Tuple[int, int, int, int], f: Tuple[int, int, int, int]) -> np.ndarray:
+    """Nearest-neighbour upsampling of rows of V (patch vectors of the coarser
+    level) to the finer level of ``shape_fine`` by factors f (U of Sec. III-A)."""
+    Ly, Lx, Py, Px = shape_fine
+    fy, fx, sy, sx = f
+    T = V.shape[0]
+    X = V.reshape(T, Ly // fy, 1, Lx // fx, 1, Py // sy, 1, Px // sx, 1)
+    X = np.broadcast_to(X, (T, Ly // fy, fy, Lx // fx, fx, Py // sy, sy, Px // sx, sx))
+    return X.reshape(T, -1).copy()
+
+
+def _build_model_dictionaries(g: Geometry, T0: int, Q: int, rho: float, rng_dict):
+    """Dictionaries that satisfy the signal model of Sec. III-A exactly.
+
+    The coarsest level holds T0 / Q^(L-1) unit-norm Gaussian atoms.  Going one
+    level finer, atom i is a child of coarse atom floor(i / Q) (the block rule
+    of Sec. III-B) and equals sqrt(rho) * U c_p / ||U c_p|| + sqrt(1 - rho) * n_i,
+    n_i a unit Gaussian direction in the null space of the level's box
+    downsampler W (I - U W projects onto it, since U W replaces each block by its
+    mean).  The two parts are orthogonal, so every atom has unit norm, and
+    W d_i is proportional to c_p: the downsampled, renormalised child IS its
+    parent.  A K-sparse fine code whose support lies in the children of K_low
+    coarse atoms therefore gives a coarse signal W x that is K_low-sparse over
+    the coarse dictionary (property 2), with the fine support inside f of the
+    coarse one (property 3).  rho is the share of an atom's energy carried by
+    its parent's (block-constant) structure."""
+    if not 0.0 < rho < 1.0:
+        raise ValueError("rho must lie in (0, 1)")
+    L = g.n_levels
+    T_top = T0 // Q ** (L - 1)
+    if T_top * Q ** (L - 1) != T0:
+        raise ValueError("T must be divisible by Q^(levels - 1)")
+    dicts = [None] * L
+    parents: List[np.ndarray] = [None] * (L - 1)
+    dicts[L - 1] = _unit_gaussian(rng_dict, T_top, g.level_dim(L - 1))
+    for l in range(L - 2, -1, -1):
+        f = _rel_factor(g, l)
+        shape = g.level_shape(l)
+        Tl = dicts[l + 1].shape[0] * Q
+        parent = (np.arange(Tl) // Q).astype(np.int32)
+        up = _up_rel(dicts[l + 1], shape, f)[parent]
+        up /= np.linalg.norm(up, axis=1, keepdims=True)
+        G = rng_dict.standard_normal((Tl, g.level_dim(l)))
+        n = G - _up_rel(_box_down(G, shape, f), shape, f)
+        n /= np.linalg.norm(n, axis=1, keepdims=True)
+        dicts[l] = np.sqrt(rho) * up + np.sqrt(1.0 - rho) * n
+        parents[l] = parent
+    return [d.astype(np.float32) for d in dicts], parents
+
+
+def _build_dictionaries(g: Geometry, T0: int, Q: int, links: str, rng_dict, rng_subset, rho: float = 0.5):
+    if links == "model":
+        return _build_model_dictionaries(g, T0, Q, rho, rng_dict)
     L = g.n_levels
     dicts = [_unit_gaussian(rng_dict, T0, g.level_dim(0))]
     parents: List[np.ndarray] = []
@@ -203,22 +264,43 @@ def _truth_support(rng, children: List[List[np.ndarray]], T_top: int, K_lv: Sequ
     return S
 
 
-def _truth_image(g: Geometry, D0: np.ndarray, children, T_top, K_tile_levels, rng_sup, rng_val):
+def _coarsest_ancestor(parents: List[np.ndarray]) -> np.ndarray:
+    """For every fine atom, its ancestor at the coarsest level."""
+    a = np.arange(len(parents[0]) if parents else 0)
+    for p in parents:
+        a = p[a]
+    return a
+
+
+def _truth_image(g: Geometry, D0: np.ndarray, children, T_top, K_tile_levels, rng_sup, rng_val,
+                 ancestor: Optional[np.ndarray] = None):
+    """Ground truth: non-overlapping P x P tiles, each D0 s with a zero-tree
+    support.  Values are N(0, 1); with ``ancestor`` (the coarsest ancestor of
+    each fine atom) the values are sign-coherent: every atom of a subtree takes
+    its root's random sign and an |N(0, 1)| magnitude, so the coarse code that
+    W x aggregates from the children never cancels and every ancestor of the
+    fine support stays in the coarse support (property 3 of Sec. III-A)."""
     Ly, Lx = g.plane_grid
     P = g.P
     if g.H % P or g.W % P:
         raise ValueError("image extent must be a multiple of the patch side")
     ty, tx = g.H // P, g.W // P
     img = np.zeros((Ly * Lx, g.H, g.W))
+    codes = []
     t = 0
     for by in range(ty):
         for bx in range(tx):
             S = _truth_support(rng_sup, children, T_top, [k[t] for k in K_tile_levels])
             s = rng_val.standard_normal(len(S))
+            if ancestor is not None and len(S):
+                roots, inv = np.unique(ancestor[S], return_inverse=True)
+                sign = np.where(rng_val.random(len(roots)) < 0.5, -1.0, 1.0)
+                s = np.abs(s) * sign[inv]
             x = (D0[S].astype(np.float64).T @ s) if len(S) else np.zeros(D0.shape[1])
             img[:, by * P:(by + 1) * P, bx * P:(bx + 1) * P] = x.reshape(Ly * Lx, P, P)
+            codes.append((S, s))
             t += 1
-    return img
+    return img, codes
 
 
 def _simulate_camera(sensing: Sensing, truth: np.ndarray, sigma: float, rng_noise) -> np.ndarray:
@@ -247,15 +329,15 @@ def _presets(name: str, links: str):
     if name == "denoise":
         geo = dict(kind="image", H=64, W=64, plane_grid=(1, 1), P=8, stride=8,
                    level_factors=[(1, 1, 1, 1), (1, 1, 2, 2)])
-        return geo, 256, [4, 2] if links == "paper" else [4, 4], 0.01, "identity"
+        return geo, 256, [4, 2] if links != "literal" else [4, 4], 0.01, "identity"
     if name == "bayer":
         geo = dict(kind="image", H=512, W=512, plane_grid=(1, 3), P=8, stride=2,
                    level_factors=[(1, 1, 1, 1), (1, 1, 2, 2)])
-        return geo, 1024, [8, 4] if links == "paper" else [8, 8], 0.005, "bayer_rggb"
+        return geo, 1024, [8, 4] if links != "literal" else [8, 8], 0.005, "bayer_rggb"
     if name == "video":
         geo = dict(kind="video", H=256, W=256, plane_grid=(1, 8), P=8, stride=4,
                    level_factors=[(1, 1, 1, 1), (1, 1, 2, 2), (1, 2, 2, 2)])
-        return geo, 4096, [16, 8, 4] if links == "paper" else [16, 16, 16], 0.005, "coded_exposure"
+        return geo, 4096, [16, 8, 4] if links != "literal" else [16, 16, 16], 0.005, "coded_exposure"
     if name == "lightfield":
         geo = dict(kind="lightfield", H=256, W=256, plane_grid=(4, 4), P=8, stride=4,
                    level_factors=[(1, 1, 1, 1), (2, 2, 1, 1), (2, 2, 2, 2)])
@@ -265,16 +347,17 @@ def _presets(name: str, links: str):
         # per-pixel retention mask is a one-frame coded exposure y = c * x
         geo = dict(kind="image", H=512, W=512, plane_grid=(1, 1), P=8, stride=4,
                    level_factors=[(1, 1, 1, 1), (1, 1, 2, 2)])
-        return geo, 1024, [8, 4] if links == "paper" else [8, 8], 0.005, "coded_exposure"
+        return geo, 1024, [8, 4] if links != "literal" else [8, 8], 0.005, "coded_exposure"
     if name == "cs_dense":
         # compressive sensing of each patch with one dense Gaussian Phi (32 x 64)
         geo = dict(kind="image", H=128, W=128, plane_grid=(1, 1), P=8, stride=4,
                    level_factors=[(1, 1, 1, 1), (1, 1, 2, 2)])
-        return geo, 512, [6, 3] if links == "paper" else [6, 6], 0.005, "dense"
+        return geo, 512, [6, 3] if links != "literal" else [6, 6], 0.005, "dense"
     raise ValueError(f"unknown workload {name!r}; expected one of {WORKLOAD_NAMES}")
 
 
 DENSE_M = 32  # measurements per patch of the dense-Phi workload
+MODEL_RHO = 0.5  # links="model": share of a fine atom's energy in its parent's structure
 
 
 def _patch_origins(extent: int, P: int, stride: int) -> np.ndarray:
@@ -299,7 +382,7 @@ def _simulate_patches(phi: np.ndarray, truth: np.ndarray, g: Geometry, sigma: fl
 def make_workload(name: str, seed: int = 0, links: str = "paper", H: Optional[int] = None,
                   W: Optional[int] = None, T0: Optional[int] = None, sigma: Optional[float] = None,
                   Q: int = 4, K_range: Tuple[int, int] = (8, 20), shots: int = 4,
-                  dict_seed: Optional[int] = None) -> Workload:
+                  dict_seed: Optional[int] = None, rho: float = MODEL_RHO) -> Workload:
     """Build one seeded workload.  ``H``/``W``/``T0``/``sigma`` override the
     full-size preset (tests use small images); everything else keeps the
     preset's structure.  ``dict_seed`` (default: ``seed``) seeds the
@@ -319,7 +402,7 @@ def make_workload(name: str, seed: int = 0, links: str = "paper", H: Optional[in
         dss = np.random.SeedSequence(dict_seed).spawn(_N_STREAMS)
         rng[_S_DICT], rng[_S_SUBSET] = np.random.default_rng(dss[_S_DICT]), np.random.default_rng(dss[_S_SUBSET])
 
-    dicts, parents = _build_dictionaries(g, T0, Q, links, rng[_S_DICT], rng[_S_SUBSET])
+    dicts, parents = _build_dictionaries(g, T0, Q, links, rng[_S_DICT], rng[_S_SUBSET], rho)
     L = g.n_levels
     children = [_children(parents[l], dicts[l + 1].shape[0]) for l in range(L - 1)]
 
@@ -329,12 +412,15 @@ def make_workload(name: str, seed: int = 0, links: str = "paper", H: Optional[in
         k_lo, k_hi = K_range
         Kp = rng[_S_KPATCH].integers(k_lo, k_hi + 1, size=B)
         Kt = rng[_S_KPATCH].integers(k_lo, k_hi + 1, size=n_tiles)
-        div = (lambda K, l: -(-K // (2 ** l))) if links == "paper" else (lambda K, l: K)
+        div = (lambda K, l: -(-K // (2 ** l))) if links != "literal" else (lambda K, l: K)
         K_levels = [np.asarray(div(Kp, l), np.int32) for l in range(L)]
         K_tile = [np.asarray(div(Kt, l), np.int32) for l in range(L)]
     else:
         K_levels = [np.full(B, k, np.int32) for k in K_lv]
         K_tile = [np.full(n_tiles, k, np.int32) for k in K_lv]
+    if links == "model":  # the solver's coarser budgets exceed the truth's (off-grid patches mix tiles)
+        K_levels = [K_levels[0]] + [np.minimum(K_levels[l - 1], -(-3 * K_levels[l] // 2)).astype(np.int32)
+                                    for l in range(1, L)]
 
     if skind == "coded_exposure":
         codes = (rng[_S_CODES].random((g.planes, g.H, g.W)) < 0.5).astype(np.uint8)
@@ -347,12 +433,13 @@ def make_workload(name: str, seed: int = 0, links: str = "paper", H: Optional[in
         codes = None
     sensing = Sensing(skind, codes)
 
-    truth = _truth_image(g, dicts[0], children, dicts[-1].shape[0], K_tile, rng[_S_SUPPORT], rng[_S_VALUES])
+    truth, tile_codes = _truth_image(g, dicts[0], children, dicts[-1].shape[0], K_tile, rng[_S_SUPPORT],
+                                     rng[_S_VALUES], _coarsest_ancestor(parents) if links == "model" else None)
     if skind == "dense":  # per-patch measurements [B, M]
         meas = _simulate_patches(codes, truth, g, sigma, rng[_S_NOISE])
     else:
         meas = _simulate_camera(sensing, truth, sigma, rng[_S_NOISE])
-    return Workload(name, g, sensing, dicts, parents, K_levels, truth, meas, sigma, seed, links)
+    return Workload(name, g, sensing, dicts, parents, K_levels, truth, meas, sigma, seed, links, tile_codes)
 
 
 def make_independent_problems(B: int, M: int, T: int, K: int, seed: int = 0, sigma: float = 0.0,

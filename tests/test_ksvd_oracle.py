@@ -238,9 +238,10 @@ def test_approximate_update_is_exact_on_rank_one_and_never_grows_the_error():
 
 
 def test_step2_coding_is_the_fine_step_of_algorithm_2():
-    """Reading R26: Step 2's coding (OMP over the children of Step 1's coarse
-    supports) equals the finer level of Algorithm 2 run on the same pair of
-    dictionaries (which recomputes the coarse supports from W x)."""
+    """Step 2's coarse supports are those of Step 1's final coding (plain OMP
+    on W x against the learned D_low): Step 2's coding (OMP over the children
+    of those supports) then equals the finer level of Algorithm 2 run on the
+    same pair of dictionaries, which recomputes the coarse supports from W x."""
     ts = synthetic.make_training_set("denoise", 300, seed=9, T0=64)
     g = ts.geometry
     X = ts.X.astype(np.float64)
@@ -264,3 +265,26 @@ def test_step2_coding_is_the_fine_step_of_algorithm_2():
     for i in range(len(X)):
         assert list(o[i, :k[i]]) == list(o2[i, :k2[i]])
         np.testing.assert_allclose(a[i, :k[i]], a2[i, :k2[i]], rtol=1e-12, atol=1e-12)
+
+
+def test_zero_error_matrix_keeps_the_atom():
+    """E_k = 0: every user of atom k is represented exactly without it (here
+    x_i = d_1 with coefficient 0 on d_0).  The update keeps d_0 unchanged (no
+    singular vector exists; any unit vector would fit), sets its coefficients
+    to E_k^T d_k = 0 and leaves the residuals at zero; atom 1's visit then sees
+    the rank-one matrix of its users and keeps d_1 (the signals are d_1)."""
+    rng = np.random.default_rng(31)
+    D = rng.standard_normal((2, 12))
+    D /= np.linalg.norm(D, axis=1, keepdims=True)
+    X = np.stack([D[1] * c for c in (1.0, -2.0, 0.5)])
+    om = np.tile(np.array([[0, 1]], np.int32), (3, 1))
+    al = np.stack([[0.0, 1.0], [0.0, -2.0], [0.0, 0.5]])
+    ke = np.full(3, 2, np.int32)
+    for approx in (False, True):
+        Dn, An, rep = ksvd.ksvd_update(D, X, om, al, ke, approximate=approx)
+        assert rep == []
+        np.testing.assert_array_equal(Dn[0], D[0])
+        np.testing.assert_array_equal(An[:, 0], 0.0)
+        np.testing.assert_allclose(Dn[1], D[1], atol=1e-12)
+        np.testing.assert_allclose(An[:, 1], [1.0, -2.0, 0.5], atol=1e-12)
+        np.testing.assert_allclose(ksvd.residuals(Dn, X, om, An, ke), 0.0, atol=1e-12)

@@ -424,3 +424,52 @@ def test_fine_support_lies_in_predicted_set():
             allowed = set(np.concatenate([ch[p] for p in o_c[b, :k_c[b]]]).tolist()) if k_c[b] else set()
             assert set(o_f[b, :k_f[b]].tolist()) <= allowed
             assert k_f[b] == min(int(w.K_levels[l][b]), len(allowed))
+
+
+# ---------------------------------------------------------------- per-patch operators
+
+@pytest.mark.parametrize("name,H", [("bayer", 24), ("inpaint", 24), ("video", 16)])
+def test_per_patch_operator_selection_equals_direct_construction(name, H):
+    """Sec. III-C, y_p = Phi_p x_p: the oracle hands every patch the effective
+    dictionary of its own operator (Bayer: one per mosaic phase (oy % 2, ox % 2),
+    shared by the patches of that phase; per-pixel codes: one per patch).  At
+    stride 1 every phase occurs; the oracle's plain and cross-scale OMP must equal
+    OMP against Phi_p U_l D^(l) written out densely for each patch on its own,
+    from its origin, with no sharing between patches."""
+    kw = dict(T0=256) if name == "video" else {}
+    w = synthetic.make_workload(name, H=H, W=H, **kw)
+    w.geometry.stride = 1
+    B = w.n_patches
+    w.K_levels = [np.full(B, int(k[0]), np.int32) for k in w.K_levels]
+    g, s = w.geometry, w.sensing
+    Y = oracle.extract_patches(w)
+    oy, ox = oracle.patch_grid(g)
+    assert {(int(a) % 2, int(b) % 2) for a, b in zip(oy, ox)} == {(0, 0), (0, 1), (1, 0), (1, 1)}
+
+    def level_mats(l):
+        D = w.dicts[l].astype(np.float64)
+        UD = oracle.U_up(D, g, l) if l else D
+        return [UD @ oracle.sensing_matrix(s, g, int(oy[b]), int(ox[b])).T for b in range(B)]
+
+    o, a, k, _ = oracle.plain_omp(w, Y=Y)
+    o2, a2, k2, _ = oracle.omp_batch(level_mats(0), Y, w.K_levels[0])
+    np.testing.assert_array_equal(k, k2)
+    np.testing.assert_array_equal(o, o2)
+    np.testing.assert_allclose(a, a2, rtol=1e-9, atol=1e-12)
+
+    # Algorithm 2 level by level with the directly built operators (P_low form)
+    L = w.n_levels
+    om, ke = None, None
+    for l in range(L - 1, -1, -1):
+        mats = level_mats(l)
+        if l == L - 1:
+            om, al, ke, _ = oracle.omp_batch(mats, Y, w.K_levels[l])
+            continue
+        ch = oracle.children_lists(w.parents[l], w.dicts[l + 1].shape[0])
+        C = [np.sort(np.concatenate([ch[p] for p in om[b, :ke[b]]])) for b in range(B)]
+        om, al, ke, _ = oracle.omp_batch([mats[b][C[b]] for b in range(B)], Y, w.K_levels[l])
+        om = np.array([[C[b][j] if j >= 0 else -1 for j in om[b]] for b in range(B)], np.int32)
+    o, a, k, _ = oracle.cross_scale_omp(w, Y=Y, coarse_form="p_low")
+    np.testing.assert_array_equal(k, ke)
+    np.testing.assert_array_equal(o[:, :om.shape[1]], om)
+    np.testing.assert_allclose(a[:, :al.shape[1]], al, rtol=1e-9, atol=1e-12)
