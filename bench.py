@@ -3,10 +3,16 @@
 
 Workload: Bayer RGGB demosaicing of a 512x512 RGB synthetic image, 8x8x3
 patches at stride 2 (253 x 253 = 64,009 patches), fine dictionary 192 x 1024,
-64 measurements per patch, K = 8 (coarse scale 48 x 256, K_low = 4, links by
-nearest downsampled atom).  One step = the whole hot path on that image:
-patch extraction -> solve (cross-scale for the headline value; plain OMP
-reported beside it) -> overlap-add aggregation.
+64 measurements per patch, K = 8.  Default link reading "model": the coarse
+dictionary (48 x 256) is the box-downsampled fine atoms (each coarse atom the
+renormalised 2x2 downsample of its Q = 4 children), so the signal model of
+Sec. III-A holds exactly and the two forms reach matched PSNR; the coarse
+budget is K_low = 6 (truth codes use 4 coarse atoms per tile; patches that
+straddle tiles mix their coarse codes).  One step = the whole hot path on that
+image: patch extraction -> solve (cross-scale for the headline value; plain OMP
+reported beside it) -> overlap-add aggregation.  After the timing, both forms'
+codes of every patch are compared with the FP64 oracle (support-set match,
+per-patch relative L2, image PSNR against the oracle's image).
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
 on a bounded sample of the same workload instead.
@@ -33,7 +39,13 @@ import numpy as np  # noqa: E402
 METRIC = "patches/s cross-scale vs full OMP on one GB300 at matched PSNR; p50/p99 job latency"
 UNIT = "patches/s"
 L2_FLUSH_BYTES = 512 << 20
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+FP32_LANES_PER_SM = 128
+MAX_SM_GHZ = 2.070
+
+
+def fp32_peak_tflops(sms: int) -> float:
+    """FP32 CUDA-core peak: SMs x FP32 lanes x 2 (FMA) x maximum SM clock."""
+    return sms * FP32_LANES_PER_SM * 2 * MAX_SM_GHZ * 1e9 / 1e12
 
 
 def parse():
@@ -43,7 +55,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="bayer")
-    ap.add_argument("--links", default="paper", choices=["paper", "literal"])
+    ap.add_argument("--links", default="model", choices=["model", "paper", "literal"],
+                    help="scale-link reading of the synthetic model (model: Sec. III-A holds exactly; "
+                         "paper: coarse atoms = downsampled subset, nearest-parent links; literal: identity links)")
+    ap.add_argument("--accuracy-sample", type=int, default=70000,
+                    help="largest number of patches compared with the oracle per form (a seeded sample above it)")
     ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -75,6 +91,10 @@ def workload_config(w, args):
         "dictionaries": [f"{d.shape[1]}x{d.shape[0]}" for d in w.dicts],
         "K": [int(k[0]) for k in w.K_levels],
         "links": args.links,
+        "reading": {"model": "coarse atoms = downsampled children (Sec. III-A exact), block links, "
+                             "sign-coherent codes; coarse budgets 1.5x the truth's",
+                    "paper": "coarse atoms = downsampled subset of T/4 fine atoms, nearest-parent links",
+                    "literal": "coarse atoms = every downsampled fine atom, identity links"}[args.links],
         "seed": int(w.seed),
         "l2": "flushed between steps (512 MiB write)",
         "parallelism": "replicas (one image per GPU)",
@@ -278,31 +298,99 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(w, seconds=12.0):
-    """The oracle as it stands, on all host threads, over a sample of patches
-    sized to about `seconds` of CPU time (cross-scale and plain)."""
+def cpu_baseline(w, gpu_codes=None, sample_cap=70000, seconds=6.0):
+    """The oracle as it stands on the host cores: both forms on all threads over
+    the whole image (a seeded sample of `sample_cap` patches when the image has
+    more), cross-scale on one thread over a sample sized to about `seconds`.
+    The oracle's codes of the all-thread runs are then compared with the GPU's
+    (`gpu_codes`, see `accuracy`).  Returns (cpu_baseline dict, accuracy dict)."""
     import oracle
 
     cores = oracle.num_threads()
     Y = oracle.extract_patches(w)
+    B = w.n_patches
+    sample = None if B <= sample_cap else np.sort(np.random.default_rng(3).choice(B, sample_cap, replace=False))
+    n_all = B if sample is None else len(sample)
+    runs = {}
+    for mode, fn in (("cross_scale", oracle.cross_scale_omp), ("plain", oracle.plain_omp)):
+        t0 = time.perf_counter()
+        res = fn(w, Y=Y, patches=sample, nthreads=cores)
+        runs[mode] = (n_all / (time.perf_counter() - t0), res)
     rng = np.random.default_rng(2)
+    sel = np.sort(rng.choice(B, min(64, B), replace=False))
+    t0 = time.perf_counter()
+    oracle.cross_scale_omp(w, Y=Y, patches=sel, nthreads=1)
+    dt = time.perf_counter() - t0
+    n1 = int(min(B, max(len(sel), len(sel) * seconds / max(dt, 1e-6))))
+    sel = np.sort(rng.choice(B, n1, replace=False))
+    t0 = time.perf_counter()
+    oracle.cross_scale_omp(w, Y=Y, patches=sel, nthreads=1)
+    one = n1 / (time.perf_counter() - t0)
+    what = "every patch of the image" if sample is None else f"{n_all} seeded random patches"
+    cpu = {"value": runs["cross_scale"][0], "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"{what} (cross-scale solve; extraction and aggregation excluded); plain OMP on the same "
+                     f"patches: {runs['plain'][0]:.1f} patches/s",
+           "plain": {"value": runs["plain"][0], "unit": UNIT, "cores": cores},
+           "one_core": {"value": one, "unit": UNIT, "cores": 1, "sample": f"{n1} random patches, cross-scale solve"}}
+    acc = None
+    if gpu_codes:
+        acc = accuracy(w, gpu_codes, {m: runs[m][1] for m in runs}, sample)
+    return cpu, acc
+
+
+def _synth(D0, sup, coef, keff):
+    """x_hat_p = D0_|Omega alpha_p for every patch (FP64), [B, N0]."""
+    D = D0.astype(np.float64)
+    B, Km = sup.shape
+    out = np.zeros((B, D.shape[1]))
+    valid = np.arange(Km)[None, :] < np.asarray(keff).reshape(-1, 1)
+    for b0 in range(0, B, 4096):
+        v = valid[b0:b0 + 4096]
+        idx = np.where(v, sup[b0:b0 + 4096], 0)
+        a = np.where(v, coef[b0:b0 + 4096].astype(np.float64), 0.0)
+        out[b0:b0 + 4096] = np.einsum("bk,bkn->bn", a, D[idx])
+    return out
+
+
+def accuracy(w, results, oracle_codes, sample):
+    """Error of each form's GPU result against the FP64 oracle on the same
+    patches: support-set match rate (and in selection order), the relative L2
+    of x_hat_p = D_|Omega alpha_p per patch (over matching patches and over all),
+    and the GPU image's PSNR beside the oracle image's.  `results[mode]` =
+    (sup, coef, keff, image) of the GPU, `oracle_codes[mode]` = the oracle's
+    (omega, alpha, k_eff, rsq) on the patches `sample` (None: all)."""
+    import oracle
+
+    B = w.n_patches
+    sel = np.arange(B) if sample is None else sample
     out = {}
-    for form, fn in (("cross_scale", oracle.cross_scale_omp), ("plain", oracle.plain_omp)):
-        n = 256
-        sel = np.sort(rng.choice(w.n_patches, n, replace=False))
-        t0 = time.perf_counter()
-        fn(w, Y=Y, patches=sel, nthreads=cores)
-        dt = time.perf_counter() - t0
-        n2 = int(min(w.n_patches, max(n, n * (seconds / 2) / max(dt, 1e-6))))
-        sel = np.sort(rng.choice(w.n_patches, n2, replace=False))
-        t0 = time.perf_counter()
-        fn(w, Y=Y, patches=sel, nthreads=cores)
-        dt = time.perf_counter() - t0
-        out[form] = (n2 / dt, n2)
-    return {"value": out["cross_scale"][0], "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{out['cross_scale'][1]} random patches (cross-scale solve; extraction and "
-                      f"aggregation excluded); plain OMP: {out['plain'][0]:.1f} patches/s on "
-                      f"{out['plain'][1]} patches"}
+    for mode in ("cross_scale", "plain"):
+        sup, coef, keff, img = results[mode]
+        o, a, k, _ = oracle_codes[mode]
+        sup, coef, keff = sup[sel], coef[sel], keff[sel].astype(np.int64)
+        km = max(o.shape[1], sup.shape[1])
+        same_k = keff == k
+        set_match = np.array([same_k[i] and set(sup[i, :keff[i]].tolist()) == set(o[i, :k[i]].tolist())
+                              for i in range(len(sel))])
+        ord_match = np.array([same_k[i] and list(sup[i, :keff[i]]) == list(o[i, :k[i]]) for i in range(len(sel))])
+        xg = _synth(w.dicts[0], sup, coef, keff)
+        xo = _synth(w.dicts[0], np.pad(o, ((0, 0), (0, km - o.shape[1])), constant_values=0)[:, :km],
+                    np.pad(a, ((0, 0), (0, km - a.shape[1]))), k)
+        rel = np.linalg.norm(xg - xo, axis=1) / np.maximum(np.linalg.norm(xo, axis=1), 1e-30)
+        row = {"patches_compared": int(len(sel)), "support_match": float(set_match.mean()),
+               "support_match_ordered": float(ord_match.mean()),
+               "rel_l2_max_on_match": float(rel[set_match].max()) if set_match.any() else None,
+               "rel_l2_median_all": float(np.median(rel)), "rel_l2_max_all": float(rel.max()),
+               "psnr_db": oracle.psnr(w.truth, img)}
+        if sample is None:
+            row["oracle_psnr_db"] = oracle.psnr(w.truth, oracle.aggregate(w, o, a, k))
+            row["psnr_minus_oracle_db"] = row["psnr_db"] - row["oracle_psnr_db"]
+        out[mode] = row
+    if sample is None:
+        out["oracle_psnr_gap_plain_minus_cross_db"] = out["plain"]["oracle_psnr_db"] - out["cross_scale"]["oracle_psnr_db"]
+    out["gpu_psnr_gap_plain_minus_cross_db"] = out["plain"]["psnr_db"] - out["cross_scale"]["psnr_db"]
+    out["bar"] = "support sets identical on >= 99.9 % of patches, rel L2 <= 1e-4 on those; PSNR within 0.05 dB"
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -311,7 +399,7 @@ def cpu_baseline(w, seconds=12.0):
 SERVING_RATES = (10, 20, 50, 100, 200)  # offered jobs/s
 
 
-def serving_pool(kinds=("denoise", "bayer", "video"), per_kind=4, seed=0, lo=128, hi=2048):
+def serving_pool(kinds=("denoise", "bayer", "video"), per_kind=4, seed=0, lo=128, hi=2048, links="model"):
     """Distinct jobs of each kind (own seed, own coded-exposure mask), sides
     uniform in [lo, hi] (multiples of 8); one model (dictionaries and links)
     per kind.  Returns [(kind, workload)]."""
@@ -322,7 +410,7 @@ def serving_pool(kinds=("denoise", "bayer", "video"), per_kind=4, seed=0, lo=128
         for i in range(per_kind):
             side = int(rng.integers(lo // 8, hi // 8 + 1)) * 8
             pool.append((kind, synthetic.make_workload(kind, seed=1000 + 10 * i + len(pool), H=side, W=side,
-                                                       dict_seed=0)))
+                                                       dict_seed=0, links=links)))
     return pool
 
 
@@ -669,11 +757,13 @@ def main():
                          else (1900.0, "fallback"))
             achieved = per_s / 1e12
         else:
-            peak, src = FP32_PEAK_TFLOPS, "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            peak = fp32_peak_tflops(sms)
+            src = f"derived: {sms} SM x {FP32_LANES_PER_SM} FP32 lanes x 2 x {MAX_SM_GHZ} GHz"
             achieved = per_s / 1e12
         roofline = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "peak_source": src,
                     "unit": unit, "frac": achieved / peak if peak else None,
-                    "traffic": read_traffic(dom, w.name),
+                    "traffic": read_traffic(dom, workload_config(w, args)["workload"]),
                     "avg_launch_us": 1e3 * tot_ms / n_launch, "launches_per_step": n_launch / args.steps}
 
     gpu_launches = int(sum(v[0] for v in cs_prof.values()))
@@ -705,18 +795,29 @@ def main():
         peak = float(w.truth.max() - w.truth.min())
         return 10 * np.log10(peak * peak / mse)
 
+    # the codes of both forms (the same context and settings solve the image once
+    # more, from the solve's own CUDA graph) for the comparison with the oracle
+    gpu_codes = {}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ctx.extract(meas_d, Y)
+        for mode, im in (("cross_scale", cs_img), ("plain", pl_img)):
+            ctx.solve(Y, mode, args.precision, K=K if mode == "cross_scale" else K[:1], Kmax=Kmax,
+                      out=(sup, coef, keff))
+            torch.cuda.synchronize()
+            gpu_codes[mode] = (sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy().astype(np.int64), im)
+
     serving = None
     if not args.no_serving:
-        pool = serving_pool()
+        pool = serving_pool(links=args.links)
         serving = {"pool": [{"kind": k, "side": int(w.geometry.H), "patches": int(w.n_patches)} for k, w in pool],
                    "precision": args.precision, "n_streams": 2, "per_gpu": True,
                    "note": "Poisson arrivals; each job drawn uniformly from the pool; host buffers in and out"}
         for mode in ("cross_scale", "plain"):
             serving[mode] = serving_bench(args, local, pool, mode, args.serving_jobs)
 
-    cpu = None
+    cpu, acc = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(w)
+        cpu, acc = cpu_baseline(w, gpu_codes, args.accuracy_sample)
 
     if rank == 0:
         line = {
@@ -742,6 +843,7 @@ def main():
                           "kernels": kernels_plain},
             "speedup_cross_scale_vs_plain": value / plain_value,
             "psnr_db": {"cross_scale": psnr(cs_img), "plain": psnr(pl_img)},
+            "accuracy_vs_oracle": acc,
             "solve_stats": {"cross_scale": cs_stats, "plain": pl_stats},
             "kernels": kernels,
             "roofline": roofline,

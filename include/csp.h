@@ -203,10 +203,12 @@ csp_status csp_aggregate(csp_ctx *ctx, const int32_t *support, const float *coef
  * synthesis scratch is a fixed 16 MiB array (4,194,304 floats) in the
  * library's device image, held by every GPU that loads the library until the
  * process exits.  Requires B * N0 <= 4,194,304 (N0 = fine patch dimension),
- * else CSP_ERR_INVALID with a message.  Calls no cudaMalloc/cudaFree.  The
- * first call on each device looks up the array's device address with that
- * device current; make that first call before any stream capture.  All calls
- * share the array: calls whose work overlaps on the GPU race on it. */
+ * else CSP_ERR_INVALID with a message.  Calls no cudaMalloc/cudaFree.
+ * csp_create looks up the array's device address (once per device, with that
+ * device current), which is when the driver reserves its memory; should that
+ * lookup have failed, the first call on the device repeats it, and that first
+ * call should then come before any stream capture.  All calls share the array:
+ * calls whose work overlaps on the GPU race on it. */
 csp_status csp_aggregate_noalloc(csp_ctx *ctx, const int32_t *support, const float *coef,
                                  const int8_t *k_eff, int64_t B, int Kmax, float *image_out,
                                  void *stream);

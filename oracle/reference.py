@@ -248,9 +248,22 @@ def plain_omp(w, Y: Optional[np.ndarray] = None, patches: Optional[np.ndarray] =
     if Y is None:
         Y = extract_patches(w)
     sel = np.arange(Y.shape[0]) if patches is None else np.asarray(patches)
-    Yl, mats = _level_subset(w, 0, Y, sel, "p_low")
     Kp = w.K_levels[0][sel] if K is None else np.broadcast_to(K, sel.shape)
-    return omp_batch(mats, Yl, Kp, nthreads=nthreads)
+    # chunks of patches bound the memory of per-patch effective dictionaries;
+    # every problem is solved on its own, so chunking changes no result
+    chunk = 512 if w.sensing.kind in ("coded_exposure",) else max(len(sel), 1)
+    outs = []
+    for c0 in range(0, len(sel), chunk):
+        Yl, mats = _level_subset(w, 0, Y, sel[c0:c0 + chunk], "p_low")
+        outs.append(omp_batch(mats, Yl, Kp[c0:c0 + chunk], nthreads=nthreads))
+    if len(outs) == 1:
+        return outs[0]
+    if not outs:
+        return omp_batch([], np.zeros((0, Y.shape[1])), Kp)
+    Kmax = max(o[0].shape[1] for o in outs)
+    return (np.concatenate([np.pad(o[0], ((0, 0), (0, Kmax - o[0].shape[1])), constant_values=-1) for o in outs]),
+            np.concatenate([np.pad(o[1], ((0, 0), (0, Kmax - o[1].shape[1]))) for o in outs]),
+            np.concatenate([o[2] for o in outs]), np.concatenate([o[3] for o in outs]))
 
 
 def _level_subset(w, l, Y, sel, form):

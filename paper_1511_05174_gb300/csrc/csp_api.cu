@@ -844,6 +844,7 @@ csp_status csp_create(csp_ctx **out, int device, size_t mem_budget_bytes) {
     return fail(nullptr, CSP_ERR_OOM, m);
   }
   cudaMemset(ctx->wsp.stats_dev, 0, 8 * sizeof(int64_t));
+  csp::noalloc_setup(device);  // the no-alloc aggregation's scratch address, once per device
   *out = ctx;
   return CSP_OK;
 }

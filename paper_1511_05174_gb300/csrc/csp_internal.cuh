@@ -209,6 +209,10 @@ inline bool aggregate_use_tiled(int path, const GeomDev &g, int N0, int Kmax) {
 bool launch_aggregate_tiled(const GeomDev &g, const float *D0, int N0, const int32_t *support, const float *coef,
                             const int8_t *k_eff, int Kmax, const int32_t *cover_y, const int32_t *cover_x, float *img,
                             cudaStream_t s);
+// Set-up of csp_aggregate_noalloc on `dev` (current): looks up its scratch
+// array's device address once per device.
+void noalloc_setup(int dev);
+
 void launch_aggregate(const GeomDev &g, const float *D0, int N0, const int32_t *support,
                       const float *coef, const int8_t *k_eff, int Kmax, const int32_t *cover_y,
                       const int32_t *cover_x, float *Xh, float *img, cudaStream_t s);

@@ -10,7 +10,11 @@
 // held in a fixed array in the library's device image instead.
 //
 // The array holds kNoAllocScratchFloats floats (16 MiB) and exists on every
-// GPU that loads this library, until the process exits.  Calls are limited to
+// GPU that loads this library, until the process exits.  Its device address is
+// looked up when a context is created on the device (csp_create), which is also
+// when the driver loads the array's module and reserves the memory; if that
+// lookup failed, the entry point's first call on the device repeats it, and
+// such a first call should then come before any stream capture.  Calls are limited to
 // B * N0 <= kNoAllocScratchFloats.  All calls share the array: calls whose
 // work overlaps on the GPU (different streams, or different contexts on the
 // same device) race on it.  The array keeps the last call's contents; every
@@ -32,7 +36,26 @@ __device__ __align__(256) float g_noalloc_scratch[kNoAllocScratchFloats];
 constexpr int kMaxDevices = 64;
 float *g_scratch_addr[kMaxDevices] = {};
 
+// Looks up (once per device, with `dev` current) the device address of the
+// scratch array.  Looking it up loads the array's module, which is when the
+// driver reserves its 16 MiB; csp_create calls this so that the memory is
+// taken at set-up and no later call of the entry point allocates anything.
+cudaError_t scratch_lookup(int dev) {
+  if (g_scratch_addr[dev]) return cudaSuccess;
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e == cudaSuccess && p) g_scratch_addr[dev] = static_cast<float *>(p);
+  return e == cudaSuccess && !p ? cudaErrorInvalidSymbol : e;
+}
+
 }  // namespace
+
+namespace csp {
+void noalloc_setup(int dev) {
+  if (dev < 0 || dev >= kMaxDevices) return;
+  if (scratch_lookup(dev) != cudaSuccess) cudaGetLastError();  // the entry point retries and reports
+}
+}  // namespace csp
 
 extern "C" csp_status csp_aggregate_noalloc(csp_ctx *ctx, const int32_t *support, const float *coef,
                                            const int8_t *k_eff, int64_t B, int Kmax, float *image_out,
@@ -58,11 +81,9 @@ extern "C" csp_status csp_aggregate_noalloc(csp_ctx *ctx, const int32_t *support
   if (cudaGetDevice(&prev) != cudaSuccess) return fail(CSP_ERR_CUDA, "cudaGetDevice failed");
   if (prev != dev && cudaSetDevice(dev) != cudaSuccess) return fail(CSP_ERR_CUDA, "cudaSetDevice failed");
   csp_status st = CSP_OK;
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) st = fail(CSP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    else g_scratch_addr[dev] = static_cast<float *>(p);
+  if (!g_scratch_addr[dev]) {  // normally done by csp_create; retried here if that lookup failed
+    const cudaError_t e = scratch_lookup(dev);
+    if (e != cudaSuccess) st = fail(CSP_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
   }
   if (st == CSP_OK) {
     csp::launch_aggregate(ctx->gd, ctx->lv[0].D, N0, support, coef, k_eff, Kmax, ctx->cover_y, ctx->cover_x,

@@ -1,0 +1,146 @@
+"""Full-size parity: every patch of the benchmark's workloads against the FP64
+oracle, in the launch configuration the benchmark times.
+
+The benchmark's step is csp_reconstruct in graph mode after the autotuner has
+picked the restricted-solver variant and the full-dictionary form, with the
+two-stream pipeline on.  Here the same context settings solve the image with
+csp_solve (graph-recorded, then replayed), and all patches are compared with
+the oracle: support sets identical on >= 99.9 % of patches, on those the
+reconstruction D_|Omega alpha within 1e-4 relative L2 (Algorithm 1 for plain,
+Algorithm 2 for cross-scale).  The image that csp_reconstruct writes must equal
+the overlap-add of those codes (Sec. IV) and its PSNR must lie within 0.05 dB of
+the oracle image's."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+from _gpu_util import budgets, compare
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-4
+MATCH = 0.999
+_ORACLE = {}
+
+
+def _oracle(w, key, mode, patches=None):
+    k = (key, mode, None if patches is None else len(patches))
+    if k not in _ORACLE:
+        Y = oracle.extract_patches(w)
+        fn = oracle.plain_omp if mode == "plain" else oracle.cross_scale_omp
+        _ORACLE[k] = fn(w, Y=Y, patches=patches)
+    return _ORACLE[k]
+
+
+_W = {}
+
+
+def _workload(name, links):
+    if (name, links) not in _W:
+        _W[(name, links)] = synthetic.make_workload(name, links=links)
+    return _W[(name, links)]
+
+
+def _bench_context(w, prec):
+    """A context set up as the benchmark sets it: workload loaded, warm-up
+    reconstructions, the autotuner's picks for the cross-scale solve, graph
+    mode on (the pipeline is on by default)."""
+    from paper_1511_05174_gb300.context import Context
+    ctx = Context(0)
+    ctx.load_workload(w)
+    meas = torch.from_numpy(np.ascontiguousarray(w.meas)).cuda()
+    Y = ctx.extract(meas)
+    Kc, K_patch, Kmax = budgets(w, "cross_scale")
+    tune = ctx.autotune(Y, "cross_scale", prec, K=Kc, K_patch=K_patch, Kmax=Kmax)
+    ctx.set_graph_mode(True)
+    return ctx, meas, Y, tune
+
+
+def _solve_replayed(ctx, Y, mode, prec, w):
+    K, K_patch, Kmax = budgets(w, mode)
+    B = Y.shape[0]
+    out = (torch.empty((B, Kmax), dtype=torch.int32, device="cuda"),
+           torch.empty((B, Kmax), dtype=torch.float32, device="cuda"),
+           torch.empty((B,), dtype=torch.int8, device="cuda"))
+    res = None
+    for _ in range(2):  # record, then replay into the cleared buffers
+        for t in out:
+            t.fill_(-5)
+        ctx.solve(Y, mode, prec, K=K, K_patch=K_patch, Kmax=Kmax, out=out)
+        torch.cuda.synchronize()
+        cur = [t.cpu().numpy() for t in out]
+        if res is not None:
+            for a, b in zip(res, cur):
+                assert np.array_equal(a, b)
+        res = cur
+    return res[0], res[1], res[2].astype(np.int64)
+
+
+@pytest.mark.parametrize("links", ["model", "paper"])
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+def test_bayer_512_every_patch(prec, links):
+    """Bayer RGGB 512 x 512 (64,009 patches, D 192 x 1024): both forms, every
+    patch, and the reconstructed image of the benchmark's own call."""
+    w = _workload("bayer", links)
+    ctx, meas, Y, tune = _bench_context(w, prec)
+    img = torch.empty((w.geometry.planes, w.geometry.H, w.geometry.W), dtype=torch.float32, device="cuda")
+    for mode in ("cross_scale", "plain"):
+        sup, coef, keff = _solve_replayed(ctx, Y, mode, prec, w)
+        o, a, k, _ = _oracle(w, links, mode)
+        rate, worst, bad = compare(w.dicts[0], sup, coef, keff, o, a, k)
+        assert rate >= MATCH, (mode, rate, bad[:10])
+        assert worst <= REL_TOL, (mode, worst)
+        K, _, Kmax = budgets(w, mode)
+        for _ in range(3):  # record, replay, replay
+            img.fill_(-3.0)
+            ctx.reconstruct(meas, img, mode, prec, K=K, Kmax=Kmax)
+        torch.cuda.synchronize()
+        got = img.cpu().numpy().astype(np.float64)
+        ref_gpu = oracle.aggregate(w, sup, coef.astype(np.float64), keff)
+        assert np.abs(got - ref_gpu).max() <= 1e-5 * np.abs(ref_gpu).max()
+        img_o = oracle.aggregate(w, o, a, k)
+        assert abs(oracle.psnr(w.truth, got) - oracle.psnr(w.truth, img_o)) <= 0.05, mode
+    ctx.set_graph_mode(False)
+
+
+def test_bayer_512_model_reading_matched_psnr():
+    """On the model reading (Sec. III-A's three properties hold exactly) the
+    oracle's cross-scale image is within 0.1 dB of its plain image: the
+    cross-scale speed comes at matched PSNR (the GPU images are tied to these
+    by the test above)."""
+    w = _workload("bayer", "model")
+    p = {}
+    for mode in ("cross_scale", "plain"):
+        o, a, k, _ = _oracle(w, "model", mode)
+        p[mode] = oracle.psnr(w.truth, oracle.aggregate(w, o, a, k))
+    assert p["plain"] - p["cross_scale"] <= 0.1, p
+
+
+@pytest.mark.parametrize("name,links,plain_sample", [
+    ("video", "model", None), ("video", "paper", None),
+    ("lightfield", "model", 600), ("lightfield", "paper", 600),
+])
+def test_three_scale_every_patch(name, links, plain_sample):
+    """Video (coded exposure, D 512 x 4096, three scales) and light field
+    (coded aperture, D 1024 x 8192, K in [8, 20] per patch): every patch of the
+    cross-scale solve; plain OMP on every video patch and on a seeded sample of
+    light-field patches (K up to 20 over 8,192 atoms is slow in FP64)."""
+    w = _workload(name, links)
+    ctx, meas, Y, tune = _bench_context(w, "bf16")
+    sup, coef, keff = _solve_replayed(ctx, Y, "cross_scale", "bf16", w)
+    o, a, k, _ = _oracle(w, links, "cross_scale")
+    rate, worst, bad = compare(w.dicts[0], sup, coef, keff, o, a, k)
+    assert rate >= MATCH and worst <= REL_TOL, ("cross_scale", rate, worst, bad[:10])
+    assert ctx.stats()["overflow"] == 0
+    sample = None
+    if plain_sample:
+        sample = np.sort(np.random.default_rng(0).choice(w.n_patches, plain_sample, replace=False))
+    sup, coef, keff = _solve_replayed(ctx, Y, "plain", "bf16", w)
+    o, a, k, _ = _oracle(w, links, "plain", sample)
+    sel = np.arange(w.n_patches) if sample is None else sample
+    rate, worst, bad = compare(w.dicts[0], sup[sel], coef[sel], keff[sel], o, a, k)
+    assert rate >= MATCH and worst <= REL_TOL, ("plain", rate, worst, sel[bad[:10]])
+    ctx.set_graph_mode(False)

@@ -55,11 +55,14 @@ def test_extract_is_exact(key):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("links", ["paper", "model"])
 @pytest.mark.parametrize("key", list(SMALL))
-def test_plain_parity(key, prec):
+def test_plain_parity(key, links, prec):
     """BF16: tensor-core proxy (tcgen05) with the top candidates re-scored in
-    FP32 -- held to the same support bar as the FP32 path."""
-    w = _workload(key)
+    FP32 -- held to the same support bar as the FP32 path.  The model reading's
+    fine atoms come in coherent sibling groups (they share their parent's
+    structure)."""
+    w = _workload(key, links=links)
     # video: per-patch Phi, the lifted proxy runs at dimension 512 (eight K blocks)
     g = run_gpu(w, "plain", prec)
     o, a, k, _ = oracle.plain_omp(w)
@@ -69,7 +72,7 @@ def test_plain_parity(key, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
-@pytest.mark.parametrize("links", ["paper", "literal"])
+@pytest.mark.parametrize("links", ["paper", "literal", "model"])
 @pytest.mark.parametrize("key", list(SMALL))
 def test_cross_scale_parity(key, links, prec):
     w = _workload(key, links=links)

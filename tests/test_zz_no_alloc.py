@@ -46,6 +46,28 @@ def test_noalloc_aggregate_matches_aggregate_twice():
         assert np.abs(o - r).max() <= 1e-5 * scale, call
 
 
+def test_noalloc_first_call_on_a_fresh_context_takes_no_device_memory():
+    """Free device memory (cudaMemGetInfo) is the same before and after the
+    entry point's first call on a freshly created context: the scratch array is
+    reserved when the context is created, and the call itself allocates
+    nothing."""
+    w = synthetic.make_workload("bayer", H=48, W=48)
+    ctx = Context(0)
+    ctx.load_workload(w)
+    sup, coef, keff = _codes(w, ctx, 0)
+    ref = ctx.aggregate(sup, coef, keff)   # loads the aggregation kernels
+    out = torch.full_like(ref, float("nan"))
+    stream = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        b.csp_aggregate_noalloc(ctx._ctx, sup.data_ptr(), coef.data_ptr(), keff.data_ptr(), sup.shape[0],
+                                sup.shape[1], out.data_ptr(), stream)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+    assert torch.equal(out, ref)
+
+
 @pytest.mark.parametrize("name,kw", [
     ("bayer", dict(H=64, W=72)),
     ("denoise", dict(H=64, W=72)),
