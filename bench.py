@@ -243,6 +243,16 @@ def algorithmic(kind, w, prof_launches, stats, B, steps, M):
         iters = int(np.max(w.K_levels[-1 if cross else 0]))
         launches = max(prof_launches[kind][0] / steps, 1.0)
         return 2.0 * dim * T * B * iters / launches, "TFLOP/s", ("tensor" if kind == "proxy_bf16" else "alu")
+    if kind == "omp_fused":
+        # the tensor-core proxy of every iteration of the full-dictionary level (coarsest level
+        # in cross-scale mode): 2 Mp T flops per patch per iteration, Mp = M padded to 64
+        cross = bool(prof_launches.get("restricted"))
+        lvl = -1 if cross else 0
+        T = w.dicts[lvl].shape[0]
+        dim = (M + 63) // 64 * 64
+        iters = int(np.max(w.K_levels[lvl]))
+        launches = max(prof_launches[kind][0] / steps, 1.0)
+        return 2.0 * dim * T * B * iters / launches, "TFLOP/s", "tensor"
     if kind == "restricted":
         per_step = max(prof_launches.get("restricted", (1,))[0] / steps, 1.0)
         flops = 2.0 * M * stats.get("restricted_scores", 0)

@@ -27,7 +27,7 @@ _ORACLE = {}
 
 
 def _oracle(w, key, mode, patches=None):
-    k = (key, mode, None if patches is None else len(patches))
+    k = (w.name, key, mode, None if patches is None else len(patches))
     if k not in _ORACLE:
         Y = oracle.extract_patches(w)
         fn = oracle.plain_omp if mode == "plain" else oracle.cross_scale_omp
