@@ -403,9 +403,10 @@ csp_status csp_job_release(csp_server *srv, uint64_t job_id);
  * fastest for this context and reports the times; then, with that variant,
  * times the two forms of the full-dictionary level (csp_set_top_level_form)
  * where the fused form applies and keeps the faster.  Synchronises `stream`. */
-#define CSP_TUNE_VARIANTS 10 /* 0: L2-cooperative, 1: shared-memory staged, 2-4: Gram-matrix proxy, 5-7: Gram-Schmidt
+#define CSP_TUNE_VARIANTS 11 /* 0: L2-cooperative, 1: shared-memory staged, 2-4: Gram-matrix proxy, 5-7: Gram-Schmidt
                                 form, each narrow to wide; 8-9: Gram-Schmidt form with the candidates' state in
-                                registers, 8 and 16 lanes per patch */
+                                registers, 8 and 16 lanes per patch; 10: Gram-Schmidt form, one thread per patch
+                                (budgets <= 8, at most 32 candidates; else as 6) */
 typedef struct csp_tune_result {
     int restricted_variant;            /* chosen variant index                      */
     double ms[CSP_TUNE_VARIANTS];      /* solve time per variant (ms)               */

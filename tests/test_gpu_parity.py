@@ -374,7 +374,7 @@ def test_exactly_dependent_atom_ends_the_patch():
     assert rate == 1.0 and worst <= REL_TOL
 
 
-@pytest.mark.parametrize("variant", list(range(10)))
+@pytest.mark.parametrize("variant", list(range(11)))
 def test_restricted_dependent_candidate_falls_back_to_fp64(variant):
     """Fine step of Algorithm 2 whose candidate set holds an exactly dependent
     atom (a_2 = a_0 + a_1, integer atoms): every restricted variant rejects it
@@ -404,7 +404,7 @@ def test_restricted_dependent_candidate_falls_back_to_fp64(variant):
     assert rate == 1.0 and worst <= REL_TOL
 
 
-@pytest.mark.parametrize("variant", list(range(10)))
+@pytest.mark.parametrize("variant", list(range(11)))
 @pytest.mark.parametrize("key", ["bayer", "lightfield", "denoise_ragged", "video", "rgb_identity"])
 def test_restricted_variants_agree_with_oracle(key, variant):
     """Every restricted-solver variant the autotuner may pick meets the parity
@@ -502,7 +502,7 @@ def test_autotune_picks_a_variant():
     Y = ctx.extract(torch.from_numpy(w.meas).cuda())
     K, K_patch, Kmax = budgets(w, "cross_scale")
     r = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
-    assert r["restricted_variant"] in range(10) and all(t > 0 for t in r["ms"])
+    assert r["restricted_variant"] in range(11) and all(t > 0 for t in r["ms"])
     assert r["ms"][r["restricted_variant"]] == min(r["ms"])
     # the BF16 Bayer coarse level (T = 256, M = 64, K = 4) has both full-dictionary forms
     r2 = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
@@ -630,3 +630,36 @@ def test_cross_scale_other_link_sizes(Q, prec):
     assert rate >= MATCH and worst <= REL_TOL, bad[:10]
     img_o = oracle.aggregate(w, o, a, k)
     assert abs(oracle.psnr(w.truth, g["img"]) - oracle.psnr(w.truth, img_o)) <= 0.05
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("key", ["bayer", "denoise", "denoise_ragged", "cs_dense", "rgb_identity"])
+def test_thread_per_patch_variant_on_model_reading(key, prec):
+    """Restricted variant 10 (one thread per patch, candidates in registers,
+    Q_C in shared memory) on the model reading, where every candidate set fits
+    it (|f(Omega)| = 4 K_low <= 32, K <= 8): supports and coefficients against
+    the oracle, and csp_reconstruct (which then synthesizes x_hat in the same
+    kernel) equal to extract + solve + aggregate, bit for bit."""
+    from paper_1511_05174_gb300.context import Context
+    w = _workload(key, links="model")
+    assert max(int(np.max(k)) for k in w.K_levels) <= 8
+    ctx = Context(0)
+    ctx.load_workload(w)
+    ctx.set_kernel_variant(10)
+    meas = torch.from_numpy(np.ascontiguousarray(w.meas)).cuda()
+    Y = meas.contiguous() if w.sensing.kind == "dense" else ctx.extract(meas)
+    K, K_patch, Kmax = budgets(w, "cross_scale")
+    sup, coef, keff = ctx.solve(Y, "cross_scale", prec, K=K, K_patch=K_patch, Kmax=Kmax)
+    o, a, k, _ = oracle.cross_scale_omp(w)
+    rate, worst, bad = compare(w.dicts[0], sup.cpu().numpy(), coef.cpu().numpy(),
+                               keff.cpu().numpy().astype(np.int64), o, a, k)
+    assert rate >= MATCH and worst <= REL_TOL, bad[:10]
+    assert ctx.stats()["overflow"] == 0
+    if w.sensing.kind == "dense" or K_patch is not None:
+        return
+    ref = ctx.aggregate(sup, coef, keff).cpu().numpy()
+    img = torch.full_like(torch.from_numpy(ref).cuda(), -3.0)
+    ctx.reconstruct(meas, img, "cross_scale", prec, K=K, Kmax=Kmax)
+    torch.cuda.synchronize()
+    assert ctx.stats()["synthesized"]
+    assert np.array_equal(img.cpu().numpy(), ref)
