@@ -61,6 +61,7 @@ constexpr int FZ_KMAX = 8;       // largest K of the fused form
 constexpr int FZ_GT = 256;       // threads of a group: a pair per patch
 constexpr int FZ_NCH = 8;        // float4 chunks per thread of a pair
 constexpr int FZ_MAXPH = kMaxPhases;
+constexpr int FZ_HCOLS_MAX = 128;  // accumulator columns per epilogue thread (half of T <= 256)
 
 __host__ __device__ constexpr int ftri(int i) { return i * (i + 1) / 2; }
 
@@ -298,6 +299,7 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
     store_rbf(r_bf, p, h, rv);
     const uint32_t imask = (1u << idx_bits) - 1u;
     const uint32_t smask = 0x7fffffffu & ~imask;
+    const uint32_t gmask = smask & ~15u;
     const int hcols = T / 2;
     // with two groups, group 1 starts once group 0 has finished its first
     // epilogue, so that one group's epilogue (integer-pipe bound) runs beside
@@ -326,23 +328,24 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
       group_bar(bar_id);
       if (*flag) break;
       tc_fence_after();
-      uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;  // two independent chains
-      for (int c0 = 0; c0 < hcols; c0 += 16) {
-        uint32_t v[16];
-        tmem_ld16_nowait(tm + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ehalf * hcols + c0), v);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int base = ehalf * hcols + c0;  // T is a multiple of 64: every column is an atom
-        const uint32_t cb = imask - (uint32_t)base;
+      // 16-column chunks (T is a multiple of 64: every column is an atom), the
+      // next chunk's TMEM load in flight while this one is reduced
+      uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+      {
+        const uint32_t taddr = tm + ((uint32_t)(quad * 32) << 16) + (uint32_t)(ehalf * hcols);
+        uint32_t v[2][16];
+        tmem_ld16_nowait(taddr, v[0]);
+        tmem_wait_ld16(v[0]);
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-          top4_insert((v[i] & smask) | (cb - (uint32_t)i), a0, a1, a2, a3);
-          top4_insert((v[i + 1] & smask) | (cb - (uint32_t)(i + 1)), b0, b1, b2, b3);
+        for (int c = 0; c < FZ_HCOLS_MAX / 16; ++c) {
+          if (c * 16 >= hcols) break;
+          const bool more = (c + 1) * 16 < hcols;
+          if (more) tmem_ld16_nowait(taddr + (uint32_t)((c + 1) * 16), v[(c + 1) & 1]);
+          const int base = ehalf * hcols + c * 16;
+          chunk_top4<16, false>(v[c & 1], 16, gmask, imask - (uint32_t)base, a0, a1, a2, a3);
+          if (more) tmem_wait_ld16(v[(c + 1) & 1]);
         }
       }
-      top4_insert(b0, a0, a1, a2, a3);
-      top4_insert(b1, a0, a1, a2, a3);
-      top4_insert(b2, a0, a1, a2, a3);
-      top4_insert(b3, a0, a1, a2, a3);
       tc_fence_before();
       if (ehalf == 1) cand4[erow] = make_uint4(a0, a1, a2, a3);
       group_bar(bar_id);
@@ -410,31 +413,53 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
         }
       }
       __syncwarp();
-      // projection (scalar work on h == 0): w = L^{-1} V, pivot, z_k, alpha = L^{-T} z
+      // projection (scalar work on h == 0): w = L^{-1} V, pivot, z_k, alpha = L^{-T} z;
+      // the substitutions run on registers (static indices, predicated on k) so
+      // that their dependent chains hold no shared-memory round trip
       bool ok32 = false;
       if (f32 && h == 0) {
+        float wv[FZ_KMAX];
         float ww = 0.f, wz = 0.f;
-        for (int i = 0; i < k; ++i) {
-          float sacc = Vp[i];
-          for (int j = 0; j < i; ++j) sacc = fmaf(-Lp[ftri(i) + j], Wp[j], sacc);
-          const float w = sacc * Linv[i];
-          Wp[i] = w;
-          ww = fmaf(w, w, ww);
-          wz = fmaf(w, zp[i], wz);
+#pragma unroll
+        for (int i = 0; i < FZ_KMAX; ++i) {
+          wv[i] = 0.f;
+          if (i < k) {
+            float sacc = Vp[i];
+#pragma unroll
+            for (int j = 0; j < i; ++j) sacc = fmaf(-Lp[ftri(i) + j], wv[j], sacc);
+            wv[i] = sacc * Linv[i];
+            ww = fmaf(wv[i], wv[i], ww);
+            wz = fmaf(wv[i], zp[i], wz);
+          }
         }
         const float d = aa - ww;
         ok32 = aa > 0.f && d >= kTauPivot * aa;
         if (ok32) {
           const float lkk = sqrtf(d), il = 1.f / lkk;
-          for (int j = 0; j < k; ++j) Lp[ftri(k) + j] = Wp[j];
+          const float zk = (bq - wz) * il;
+#pragma unroll
+          for (int j = 0; j < FZ_KMAX; ++j)
+            if (j < k) Lp[ftri(k) + j] = wv[j];
           Lp[ftri(k) + k] = lkk;
           Linv[k] = il;
-          zp[k] = (bq - wz) * il;
-          for (int i = k; i >= 0; --i) {
-            float sacc = zp[i];
-            for (int j = i + 1; j <= k; ++j) sacc = fmaf(-Lp[ftri(j) + i], Wp[j], sacc);
-            Wp[i] = sacc * Linv[i];
+          zp[k] = zk;
+          // alpha_i = (z_i - sum_{j > i} L[j][i] alpha_j) / L_ii, i = k .. 0, with
+          // row k of L = (w, lkk) and the earlier rows from shared memory
+          float al[FZ_KMAX];
+#pragma unroll
+          for (int i = FZ_KMAX - 1; i >= 0; --i) {
+            al[i] = 0.f;
+            if (i <= k) {
+              float sacc = i == k ? zk : zp[i];
+#pragma unroll
+              for (int j = i + 1; j < FZ_KMAX; ++j)
+                if (j <= k) sacc = fmaf(-(j == k ? wv[i] : Lp[ftri(j) + i]), al[j], sacc);
+              al[i] = sacc * (i == k ? il : Linv[i]);
+            }
           }
+#pragma unroll
+          for (int i = 0; i < FZ_KMAX; ++i)
+            if (i <= k) Wp[i] = al[i];
         } else {
           atomicAdd((unsigned long long *)&stats[0], 1ull);
         }

@@ -1247,7 +1247,8 @@ omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__res
                           int cap, const int32_t *__restrict__ omega_up, int ldo_up,
                           const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                           int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
-                          int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
+                          int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T,
+                          const float *__restrict__ D0, int N0, float *__restrict__ Xh) {
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
@@ -1433,6 +1434,8 @@ omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__res
       alpha[b * ldo + j] = (j < k) ? S.W[j] : 0.f;
     }
   }
+  // synthesis x_hat_b = D0_Omega alpha (Sec. IV) into Xh[b] when asked for
+  if (Xh && valid) synth_patch(D0, N0, Xh + b * N0, S.W, S.om, k, s, G);
 }
 
 inline unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -1538,10 +1541,14 @@ bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, con
                                const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx,
                                int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
                                const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
-                               int8_t *k_eff, int64_t *stats, const float *gram, int T, cudaStream_t s) {
+                               int8_t *k_eff, int64_t *stats, const float *gram, int T, const float *D0, int N0,
+                               float *Xh, bool *synthesized, cudaStream_t s) {
+  *synthesized = false;
   if (M % 4 || M > 8 * G || Kb > 8 || (G != 8 && G != 16)) return false;
   const int per_g = (cap + G - 1) / G;
   if (per_g > 8) return false;
+  const bool synth = Xh && D0 && N0 > 0 && N0 % 4 == 0;
+  *synthesized = synth;
   if (n == 0) return true;
   const int CPL = per_g <= 2 ? 2 : (per_g <= 4 ? 4 : 8);
   const int per_cta = WV_WARPS * (32 / G);
@@ -1550,7 +1557,7 @@ bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, con
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kern<<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up,
                                                       ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats,
-                                                      gram, T);
+                                                      gram, T, D0, N0, synth ? Xh : nullptr);
   };
   switch ((G == 8 ? 0 : 100) + CPL) {
     case 2: go(omp_restricted_reg_kernel<8, 2, 8>); break;

@@ -760,10 +760,11 @@ bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
     variant = 6;  // shape outside the one-thread form: the shared-memory Gram-Schmidt form
   }
   if (variant >= 8) {  // 8, 9: Gram-Schmidt form with register-resident candidates, 8 / 16 lanes per patch
+    bool sy = false;
     if (launch_omp_restricted_reg(variant == 8 ? 8 : 16, Y, M, A, inv_norm, ids, n, child_off, child_idx, cap,
                                   omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T,
-                                  s))
-      return false;
+                                  D0, N0, Xh, &sy, s))
+      return sy;
     variant = 6;  // shape outside the register form: the shared-memory Gram-Schmidt form
   }
   if (variant >= 2)  // 2-4: Gram proxy p0 - G alpha; 5-7: Gram-Schmidt form; narrow to wide lane groups

@@ -16,10 +16,13 @@
 //           TMEM accumulators of NT columns, released by tcgen05.commit;
 //   warps 2-9  epilogue: warps w and w + 4 share TMEM lane quadrant w % 4
 //           (thread <-> patch) and split each accumulator's columns in two
-//           halves; every thread keeps the four largest 32-bit packed keys
-//           (|score| bits above, T-complement of the atom index below, so ties
-//           go to the lowest index) with a branch-free min/max network in two
-//           independent chains; the halves merge through shared memory.
+//           halves; every thread reduces its columns 32 at a time (the next
+//           chunk's TMEM load in flight): the chunk's two best keys (|score|
+//           bits, complemented position) by a min/max pair per column, then
+//           these as 32-bit packed keys (|score| bits above, T-complement of
+//           the atom index below, so ties go to the lowest index) into the
+//           running four best with a branch-free network; the halves merge
+//           through shared memory.
 // The kTopP candidates per patch are re-scored in FP32 by the update kernel,
 // which excludes atoms already chosen.
 //
@@ -41,6 +44,7 @@ constexpr int TC_M = 128;
 constexpr int TC_EPI_WARPS = 8;                    // two per TMEM lane quadrant
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 constexpr int TC_MAX_STAGES = 8;
+constexpr int TC_HCOLS_MAX = 64;                   // accumulator columns per epilogue thread and tile
 
 struct TcLayout {
   int kb;       // 64-element K blocks
@@ -186,7 +190,8 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
     // per-patch norms (per-patch Phi): scores scaled by 1/||Phi_p U d_i|| of this thread's patch
     const int64_t wi_row = tile0 + row;
     const float *prow = (pinv && wi_row < n) ? pinv + (ids ? (int64_t)ids[wi_row] : wi_row) * (int64_t)T : nullptr;
-    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0, b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+    const uint32_t gmask = smask & ~31u;
+    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
     bool ok = true;
     for (int j = 0; j < n_at && ok; ++j) {
       const int a = j & 1;
@@ -194,41 +199,34 @@ proxy_tc_kernel(const __grid_constant__ CUtensorMap tmR, const __grid_constant__
       ok = __all_sync(0xffffffffu, ok);
       if (!ok) break;
       tc_fence_after();
-      for (int c0 = 0; c0 < hcols; c0 += 64) {
-        uint32_t v[64];
-        const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * nt + half * hcols + c0);
-        tmem_ld32_nowait(taddr, v);
-        tmem_ld32_nowait(taddr + 32, v + 32);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int base = (j0 + j) * nt + half * hcols + c0;
-        const uint32_t c = imask - (uint32_t)base;
+      // 32-column chunks, the next one's TMEM load in flight while this one is reduced
+      const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(a * nt + half * hcols);
+      uint32_t v[2][32];
+      tmem_ld32_nowait(taddr, v[0]);
+      tmem_wait_ld32(v[0]);
+#pragma unroll
+      for (int c = 0; c < TC_HCOLS_MAX / 32; ++c) {
+        if (c * 32 >= hcols) break;
+        const bool more = (c + 1) * 32 < hcols;
+        if (more) tmem_ld32_nowait(taddr + (uint32_t)((c + 1) * 32), v[(c + 1) & 1]);
+        uint32_t(&cur)[32] = v[c & 1];
+        const int base = (j0 + j) * nt + half * hcols + c * 32;
         if (pinv) {
 #pragma unroll
-          for (int i = 0; i < 64; ++i) {
+          for (int i = 0; i < 32; ++i) {
             const float pv = (prow && base + i < T) ? __ldg(prow + base + i) : 0.f;
-            v[i] = __float_as_uint(fabsf(__uint_as_float(v[i])) * pv);
+            cur[i] = __float_as_uint(fabsf(__uint_as_float(cur[i])) * pv);
           }
         }
-        if (base + 64 <= T) {
-#pragma unroll
-          for (int i = 0; i < 64; i += 2) {
-            top4_insert((v[i] & smask) | (c - (uint32_t)i), a0, a1, a2, a3);
-            top4_insert((v[i + 1] & smask) | (c - (uint32_t)(i + 1)), b0, b1, b2, b3);
-          }
-        } else {
-#pragma unroll
-          for (int i = 0; i < 64; ++i)
-            if (base + i < T) top4_insert((v[i] & smask) | (c - (uint32_t)i), a0, a1, a2, a3);
-        }
+        const uint32_t cb = imask - (uint32_t)base;
+        if (base + 32 <= T) chunk_top4<32, false>(cur, 32, gmask, cb, a0, a1, a2, a3);
+        else chunk_top4<32, true>(cur, T - base, gmask, cb, a0, a1, a2, a3);
+        if (more) tmem_wait_ld32(v[(c + 1) & 1]);
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty + a);
     }
-    top4_insert(b0, a0, a1, a2, a3);
-    top4_insert(b1, a0, a1, a2, a3);
-    top4_insert(b2, a0, a1, a2, a3);
-    top4_insert(b3, a0, a1, a2, a3);
     if (half == 1) {
       merge[row * 4 + 0] = a0;
       merge[row * 4 + 1] = a1;

@@ -134,6 +134,68 @@ __device__ __forceinline__ void top4_insert(uint32_t x, uint32_t &k0, uint32_t &
   k3 = max(k3, l2);
 }
 
+// Waits for this thread's TMEM loads; the 32 registers pass through the wait
+// so that no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_wait_ld32(uint32_t *r) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+        "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]),
+        "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+        "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+      :
+      : "memory");
+}
+
+// Waits for this thread's TMEM loads, 16 registers passed through as above.
+__device__ __forceinline__ void tmem_wait_ld16(uint32_t *r) {
+  asm volatile(
+      "tcgen05.wait::ld.sync.aligned;"
+      : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+        "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+      :
+      : "memory");
+}
+
+// Candidate keys of one chunk of N (16 or 32) accumulator columns (columns
+// base .. base+N-1 of the dictionary, `lim` of them real atoms).  Each column's
+// key is its |score| bits with the low log2(N) bits replaced by its
+// complemented position in the chunk (larger score first, then the lower
+// column); the chunk's two largest keys (two interleaved chains: three integer
+// operations a column) are turned into global keys -- |score| bits above
+// idx_bits, complemented atom index below (cb = imask - base) -- and inserted
+// into the running top four.  The result holds the true top four of all
+// columns seen unless three of them share a chunk; the update kernels re-score
+// the candidates in FP32.  gmask must clear the low max(idx_bits, log2 N) bits.
+template <int N, bool RAGGED>
+__device__ __forceinline__ void chunk_top4(const uint32_t (&v)[N], int lim, uint32_t gmask, uint32_t cb,
+                                           uint32_t &k0, uint32_t &k1, uint32_t &k2, uint32_t &k3) {
+  static_assert(N == 16 || N == 32, "chunks of 16 or 32 columns");
+  constexpr uint32_t pm = (uint32_t)N - 1u;
+  const uint32_t lm = 0x7fffffffu & ~pm;
+  uint32_t h0 = 0, l0 = 0, h1 = 0, l1 = 0;
+#pragma unroll
+  for (int i = 0; i < N; i += 2) {
+    uint32_t x = (v[i] & lm) | (pm - (uint32_t)i);
+    uint32_t y = (v[i + 1] & lm) | (pm - (uint32_t)(i + 1));
+    if (RAGGED) {
+      x = i < lim ? x : 0u;
+      y = i + 1 < lim ? y : 0u;
+    }
+    const uint32_t t = min(h0, x);
+    h0 = max(h0, x);
+    l0 = max(l0, t);
+    const uint32_t u = min(h1, y);
+    h1 = max(h1, y);
+    l1 = max(l1, u);
+  }
+  const uint32_t h = max(h0, h1), l = max(min(h0, h1), max(l0, l1));
+  const uint32_t gh = h ? ((h & gmask) | (cb - pm + (h & pm))) : 0u;
+  const uint32_t gl = l ? ((l & gmask) | (cb - pm + (l & pm))) : 0u;
+  top4_insert(gh, k0, k1, k2, k3);
+  top4_insert(gl, k0, k1, k2, k3);
+}
+
 }  // namespace tc
 
 // 2-D BF16 tensor map over `rows` rows of `inner` elements, box 64 x box_rows,
