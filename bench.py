@@ -469,10 +469,25 @@ def serving_bench(args, device, pool, mode, jobs_per_rate):
             lat = np.array([i["t_done"] - i["t_submit"] for i in infos]) * 1e3
             span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
             patches = sum(i["patches"] for i in infos)
+
+            def med(f):
+                return float(np.median([f(i) for i in infos]))
+            stages = {  # medians over the jobs (device stages are per batch)
+                "wait_ms": med(lambda i: 1e3 * (i["t_admit"] - i["t_submit"])),
+                "enqueue_ms": med(lambda i: i["enqueue_ms"]),
+                "copy_in_ms": med(lambda i: i["copy_in_ms"]), "solve_ms": med(lambda i: i["solve_ms"]),
+                "aggregate_ms": med(lambda i: i["aggregate_ms"]), "copy_out_ms": med(lambda i: i["copy_out_ms"]),
+                "admit_to_gpu_done_ms": med(lambda i: 1e3 * (i["t_gpu_done"] - i["t_admit"])),
+                "host_out_ms": med(lambda i: i["host_out_ms"]),
+                "device_ms_per_job": float(np.sum([(i["copy_in_ms"] + i["solve_ms"] + i["aggregate_ms"]
+                                                    + i["copy_out_ms"]) / max(i["batch_jobs"], 1) for i in infos])
+                                           / len(infos)),
+            }
             rates.append({"offered_jobs_per_s": rate, "jobs": len(infos), "value": patches / span, "unit": UNIT,
                           "jobs_per_s": len(infos) / span, "latency_ms_p50": float(np.percentile(lat, 50)),
                           "latency_ms_p99": float(np.percentile(lat, 99)),
-                          "mean_batch_jobs": float(np.mean([i["batch_jobs"] for i in infos]))})
+                          "mean_batch_jobs": float(np.mean([i["batch_jobs"] for i in infos])),
+                          "stages_median": stages})
         return rates
     finally:
         srv.close()

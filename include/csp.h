@@ -364,6 +364,16 @@ typedef struct csp_job_info {
     int batch_jobs;             /* jobs coalesced into this job's batch                    */
     int64_t batch_patches;
     csp_status status;          /* CSP_OK, CSP_ERR_NOT_READY while queued/running, or error */
+    /* Stage times of the job's batch (milliseconds; shared by the jobs of one batch):
+     * enqueue_ms   host time the scheduler spent staging inputs and enqueueing the batch;
+     * copy_in_ms   device: host-to-device copies, patch extraction and code blocks;
+     * solve_ms     device: the solve (with per-patch operator builds for per-pixel Phi);
+     * aggregate_ms device: synthesis and overlap-add of the batch's images;
+     * copy_out_ms  device: device-to-host copies of the images;
+     * t_gpu_done   seconds on the server's clock when the scheduler saw the batch complete;
+     * host_out_ms  host copy of this job's image into the caller's buffer (0 when the
+     *              device wrote it there directly). */
+    double enqueue_ms, copy_in_ms, solve_ms, aggregate_ms, copy_out_ms, t_gpu_done, host_out_ms;
 } csp_job_info;
 
 csp_status csp_server_create(csp_server **out, const csp_server_config *cfg);
@@ -405,8 +415,8 @@ csp_status csp_job_release(csp_server *srv, uint64_t job_id);
  * where the fused form applies and keeps the faster.  Synchronises `stream`. */
 #define CSP_TUNE_VARIANTS 11 /* 0: L2-cooperative, 1: shared-memory staged, 2-4: Gram-matrix proxy, 5-7: Gram-Schmidt
                                 form, each narrow to wide; 8-9: Gram-Schmidt form with the candidates' state in
-                                registers, 8 and 16 lanes per patch; 10: Gram-Schmidt form, one thread per patch
-                                (budgets <= 8, at most 32 candidates; else as 6) */
+                                registers, 8, 16 and 4 lanes per patch (8-10; budgets <= 8, at most 8 candidates a
+                                lane; else as 6) */
 typedef struct csp_tune_result {
     int restricted_variant;            /* chosen variant index                      */
     double ms[CSP_TUNE_VARIANTS];      /* solve time per variant (ms)               */

@@ -295,8 +295,9 @@ bool launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const
                                 const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
                                 int8_t *k_eff, int64_t *stats, const float *gram, int T, const float *D0, int N0,
                                 float *Xh, cudaStream_t s);
-// Gram-Schmidt form with the candidates' state in registers (G = 8 or 16 lanes
-// per patch); false (nothing launched) when M > 8 G, Kb > 8 or cap > 8 G.
+// Gram-Schmidt form with the candidates' state in registers (G = 4, 8 or 16
+// lanes per patch); false (nothing launched) when M > 16 G (G = 4) or 8 G,
+// Kb > 8 or cap > 8 G.
 // With Xh (and D0, N0) it also writes x_hat_p = D0_Omega alpha_p; *synthesized
 // tells whether it did.
 bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, const float *inv_norm,
@@ -309,15 +310,6 @@ bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, con
 void launch_gram(const float *A, int T, int M, float *Gm, cudaStream_t s);
 // variant 0: rows from L2 every pass (cooperative groups); 1: rows staged in shared memory;
 // 2: proxy from the Gram matrix + exact re-score of the best three (falls back to 0 without gram).
-// Restricted OMP, Gram-Schmidt form, one thread per patch (k_thread.cu): Kb <= 8,
-// cap <= 32, shared Gram matrix.  Returns false (nothing launched) outside that
-// shape; *synthesized tells whether it wrote x_hat into Xh.
-bool launch_omp_restricted_thread(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids,
-                                  int64_t n, const int32_t *child_off, const int32_t *child_idx, int cap,
-                                  const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int8_t *Kp,
-                                  int Kuni, int Kb, int32_t *omega, float *alpha, int ldo, int8_t *k_eff,
-                                  int64_t *stats, const float *gram, int T, const float *D0, int N0, float *Xh,
-                                  bool *synthesized, cudaStream_t s);
 bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, const float *inv_norm,
                            const int32_t *ids, int64_t n, const int32_t *child_off,
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,

@@ -1225,13 +1225,17 @@ omp_restricted_qr8_kernel(const float *__restrict__ Y, int M, const float *__res
 // Same iteration as omp_restricted_qr_kernel, but lane s of a group owns the
 // candidates c = s + G u (u < CPL) and keeps, per candidate, its atom index,
 // 1/||a_c||, the correlation c_c = <a_c, r> and its row of Q_C = A_C^T U
-// (KM >= Kb entries, zero beyond the chosen count) in registers.  Per
-// iteration: the argmax over the group, the owner of q publishes its row of
-// Q_C (w, the new row of L) through shared memory, every lane updates its own
-// candidates from G[q][c] (one load wave), so the only shared-memory traffic
-// is the k-vector w.  FP64 fallback, the explicit residual near the FP32
-// floor and the outputs are those of the shared-memory form.
-// M <= 8 G (two float4 chunks of y per lane for p0 = A_C^T y).
+// (8 >= Kb entries) in registers.  Per iteration: the argmax over the group,
+// the owner of q publishes its row of Q_C (w, the new row of L) through shared
+// memory, every lane updates its own candidates from G[q][c] (one load wave),
+// so the only shared-memory traffic is the k-vector w.  A patch that is still
+// active at iteration `it` has chosen exactly `it` atoms, so the iteration loop
+// is unrolled: in each copy the count is a compile-time constant, the dot
+// products w . Q_C[c] have exactly `it` terms and the new column of Q_C is a
+// plain register write.  FP64 fallback, the explicit residual near the FP32
+// floor and the outputs are those of the shared-memory form; with Xh the group
+// also writes x_hat = D0_Omega alpha (synth_patch).
+// M <= 4 G NCH (NCH float4 chunks of y per lane for p0 = A_C^T y).
 // Per-group shared memory: GrpSmem | p0[cap] | parents' child ranges [2 x CSP_MAX_K].
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ int reg_group_bytes(int Kb, int cap) {
@@ -1239,8 +1243,8 @@ __host__ __device__ __forceinline__ int reg_group_bytes(int Kb, int cap) {
   return (bytes + 127) / 128 * 128 + 16;
 }
 
-template <int G, int CPL, int KM>
-__global__ void __launch_bounds__(WV_WARPS * 32, 4)
+template <int G, int CPL, int NCH>
+__global__ void __launch_bounds__(WV_WARPS * 32, CPL >= 6 ? 3 : 4)  // 6-8 candidates a lane: up to 168 registers
 omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                           const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
                           const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx,
@@ -1249,6 +1253,7 @@ omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__res
                           int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
                           int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T,
                           const float *__restrict__ D0, int N0, float *__restrict__ Xh) {
+  constexpr int KM = 8;
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
@@ -1269,11 +1274,11 @@ omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__res
   const float *yrow = Y + b * M;
   const float4 *y4 = reinterpret_cast<const float4 *>(yrow);
   // candidates, their inverse norms and p0 = A_C^T y (group-cooperative, in shared memory)
-  float4 yv[2];
-  load_chunks<G, 2>(yv, yrow, nv, s, valid);
-  const int nc = gram_setup<G, 2>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
-                                  inv_norm, stats, M, A, yv, p0);
-  const float ysq = gsum<G>(dotc<2>(yv, yv));
+  float4 yv[NCH];
+  load_chunks<G, NCH>(yv, yrow, nv, s, valid);
+  const int nc = gram_setup<G, NCH>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
+                                    inv_norm, stats, M, A, yv, p0);
+  const float ysq = gsum<G>(dotc<NCH>(yv, yv));
   // this lane's candidates into registers (u < ucnt: a bound uniform over the warp, <= CPL)
   const int ucnt = __reduce_max_sync(kFull, (nc + G - 1) / G);
   int cs[CPL];
@@ -1288,12 +1293,18 @@ omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__res
 #pragma unroll
     for (int j = 0; j < KM; ++j) Q[u][j] = 0.f;
   }
+  float zr[KM];  // z_j of the chosen atoms (registers; row it of z is written at iteration it)
+#pragma unroll
+  for (int j = 0; j < KM; ++j) zr[j] = 0.f;
   float rsq = ysq;
   bool act = valid && Kpb > 0;
   uint8_t fl = 0;  // bit 1: FP64 from here on
   int k = 0, scored = 0;
   const int Kw = __reduce_max_sync(kFull, Kpb);
-  for (int it = 0; it < Kw; ++it) {
+#pragma unroll
+  for (int it = 0; it < KM; ++it) {
+    // an active patch has chosen exactly `it` atoms here (k == it)
+    if (it >= Kw) break;
     act = act && k < Kpb && !(rsq <= kEpsR32 * ysq);
     if (!__any_sync(kFull, act)) break;
     if (act) ++scored;
@@ -1308,64 +1319,65 @@ omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__res
     best = gmax<G>(best);
     if (act && !best) act = false;  // candidate set exhausted
     const int q = act ? key_idx(best) : 0;
+    const bool f32 = act && !(fl & 2);
     // G[q][C] (row q: G is symmetric) and G[q][q], issued first
     float gpre[CPL];
 #pragma unroll
-    for (int u = 0; u < CPL; ++u) gpre[u] = (u < ucnt && act && cs[u] >= 0) ? __ldg(gram + (int64_t)q * T + cs[u]) : 0.f;
-    const float aa = act ? __ldg(gram + (int64_t)q * T + q) : 0.f;
-    // the owner of q: no longer eligible; publishes its row of Q_C and p0_q
+    for (int u = 0; u < CPL; ++u)
+      gpre[u] = (u < ucnt && f32 && cs[u] >= 0) ? __ldg(gram + (int64_t)q * T + cs[u]) : 0.f;
+    const float aa = f32 ? __ldg(gram + (int64_t)q * T + q) : 0.f;
+    // the owner of q: no longer eligible; publishes its row of Q_C and its correlation
 #pragma unroll
     for (int u = 0; u < CPL; ++u)
       if (u < ucnt && act && cs[u] == q) {
         inv[u] = -1.f;
 #pragma unroll
-        for (int j = 0; j < KM; ++j)
-          if (j < k) S.V[j] = Q[u][j];
-        S.misc[1] = s + G * u;
+        for (int j = 0; j < it; ++j) S.V[j] = Q[u][j];
+        S.V[Kb] = cc[u];  // V holds Kb + 1 entries; w uses the first it < Kb
       }
     __syncwarp();
-    const bool f32 = act && !(fl & 2);
-    // new row of L: w_j = <u_j, a_q>
+    // new row of L: w_j = <u_j, a_q>, j < it; z_it = c_q / L_kk (c_q = <a_q, y> - w.z)
     float w[KM];
-    float ww = 0.f, wz = 0.f;
+    float ww0 = 0.f, ww1 = 0.f;
 #pragma unroll
-    for (int j = 0; j < KM; ++j) {
-      const bool o = f32 && j < k;
-      w[j] = o ? S.V[j] : 0.f;
-      ww = fmaf(w[j], w[j], ww);
-      wz = fmaf(w[j], o ? S.z[j] : 0.f, wz);
+    for (int j = 0; j < it; ++j) {
+      w[j] = f32 ? S.V[j] : 0.f;
+      if (j & 1) ww1 = fmaf(w[j], w[j], ww1);
+      else ww0 = fmaf(w[j], w[j], ww0);
     }
-    const float d = aa - ww;
+    const float cq = S.V[Kb];
+    const float d = aa - (ww0 + ww1);
     const bool ok32 = f32 && aa > 0.f && d >= kTauPivot * aa;
     if (f32 && !ok32) {
       fl |= 2;
       if (s == 0) atomicAdd((unsigned long long *)&stats[0], 1ull);
     }
     if (ok32) {
-      const float lkk = sqrtf(d);
-      const float il = 1.f / lkk;
-      const float zk = (p0[S.misc[1]] - wz) * il;
+      const float il = rsqrtf(d);  // d >= kTauPivot aa > 0
+      const float lkk = d * il;
+      const float zk = cq * il;
       if (s == 0) {
 #pragma unroll
-        for (int j = 0; j < KM; ++j)
-          if (j < k) S.L[tri(k) + j] = w[j];
-        S.L[tri(k) + k] = lkk;
-        S.Linv[k] = il;
-        S.z[k] = zk;
-        S.om[k] = q;
-        S.colp[k] = A + (int64_t)q * M;
+        for (int j = 0; j < it; ++j) S.L[tri(it) + j] = w[j];
+        S.L[tri(it) + it] = lkk;
+        S.Linv[it] = il;
+        S.z[it] = zk;
+        S.om[it] = q;
+        S.colp[it] = A + (int64_t)q * M;
       }
-      // column k of Q_C and the correlations
+      zr[it] = zk;
+      // column `it` of Q_C and the correlations
 #pragma unroll
       for (int u = 0; u < CPL; ++u)
         if (u < ucnt && cs[u] >= 0) {
-          float v = gpre[u];
+          float v0 = gpre[u], v1 = 0.f;
 #pragma unroll
-          for (int j = 0; j < KM; ++j) v = fmaf(-w[j], Q[u][j], v);
-          v *= il;
-#pragma unroll
-          for (int j = 0; j < KM; ++j)
-            if (j == k) Q[u][j] = v;
+          for (int j = 0; j < it; ++j) {
+            if (j & 1) v1 = fmaf(-w[j], Q[u][j], v1);
+            else v0 = fmaf(-w[j], Q[u][j], v0);
+          }
+          const float v = (v0 + v1) * il;
+          Q[u][it] = v;
           cc[u] = fmaf(-zk, v, cc[u]);
         }
       rsq = rsq - zk * zk;
@@ -1544,13 +1556,16 @@ bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, con
                                int8_t *k_eff, int64_t *stats, const float *gram, int T, const float *D0, int N0,
                                float *Xh, bool *synthesized, cudaStream_t s) {
   *synthesized = false;
-  if (M % 4 || M > 8 * G || Kb > 8 || (G != 8 && G != 16)) return false;
+  if (M % 4 || Kb > 8 || (G != 4 && G != 8 && G != 16)) return false;
+  // float4 chunks of y per lane: 4 lanes take M <= 64 (4 chunks), 8 and 16 lanes two chunks
+  const int nch = G == 4 ? 4 : 2;
+  if (M > 4 * G * nch) return false;
   const int per_g = (cap + G - 1) / G;
-  if (per_g > 8) return false;
+  const int CPL = per_g <= 2 ? 2 : (per_g <= 3 ? 3 : (per_g <= 4 ? 4 : (per_g <= 6 ? 6 : (per_g <= 8 ? 8 : 0))));
+  if (!CPL) return false;
   const bool synth = Xh && D0 && N0 > 0 && N0 % 4 == 0;
   *synthesized = synth;
   if (n == 0) return true;
-  const int CPL = per_g <= 2 ? 2 : (per_g <= 4 ? 4 : 8);
   const int per_cta = WV_WARPS * (32 / G);
   const size_t sm = (size_t)reg_group_bytes(Kb, cap) * per_cta;
   auto go = [&](auto kern) {
@@ -1559,13 +1574,22 @@ bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, con
                                                       ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats,
                                                       gram, T, D0, N0, synth ? Xh : nullptr);
   };
-  switch ((G == 8 ? 0 : 100) + CPL) {
-    case 2: go(omp_restricted_reg_kernel<8, 2, 8>); break;
-    case 4: go(omp_restricted_reg_kernel<8, 4, 8>); break;
-    case 8: go(omp_restricted_reg_kernel<8, 8, 8>); break;
-    case 102: go(omp_restricted_reg_kernel<16, 2, 8>); break;
-    case 104: go(omp_restricted_reg_kernel<16, 4, 8>); break;
-    case 108: go(omp_restricted_reg_kernel<16, 8, 8>); break;
+  switch (G * 100 + CPL) {
+    case 402: go(omp_restricted_reg_kernel<4, 2, 4>); break;
+    case 403: go(omp_restricted_reg_kernel<4, 3, 4>); break;
+    case 404: go(omp_restricted_reg_kernel<4, 4, 4>); break;
+    case 406: go(omp_restricted_reg_kernel<4, 6, 4>); break;
+    case 408: go(omp_restricted_reg_kernel<4, 8, 4>); break;
+    case 802: go(omp_restricted_reg_kernel<8, 2, 2>); break;
+    case 803: go(omp_restricted_reg_kernel<8, 3, 2>); break;
+    case 804: go(omp_restricted_reg_kernel<8, 4, 2>); break;
+    case 806: go(omp_restricted_reg_kernel<8, 6, 2>); break;
+    case 808: go(omp_restricted_reg_kernel<8, 8, 2>); break;
+    case 1602: go(omp_restricted_reg_kernel<16, 2, 2>); break;
+    case 1603: go(omp_restricted_reg_kernel<16, 3, 2>); break;
+    case 1604: go(omp_restricted_reg_kernel<16, 4, 2>); break;
+    case 1606: go(omp_restricted_reg_kernel<16, 6, 2>); break;
+    case 1608: go(omp_restricted_reg_kernel<16, 8, 2>); break;
     default: return false;
   }
   return true;

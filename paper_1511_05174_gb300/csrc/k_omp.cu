@@ -752,16 +752,10 @@ bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            cudaStream_t s, const float *D0, int N0, float *Xh) {
   if (n == 0) return false;
   if (variant >= 2 && (!gram || a_pstride || cpos)) variant = 0;  // the Gram variants need the level's shared Gram matrix
-  if (variant == 10) {  // Gram-Schmidt form, one thread per patch (Kb <= 8, |C| <= 32)
+  if (variant >= 8) {  // 8, 9, 10: Gram-Schmidt form with register-resident candidates, 8 / 16 / 4 lanes per patch
     bool sy = false;
-    if (launch_omp_restricted_thread(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up, keff_up,
-                                     Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T, D0, N0, Xh, &sy, s))
-      return sy;
-    variant = 6;  // shape outside the one-thread form: the shared-memory Gram-Schmidt form
-  }
-  if (variant >= 8) {  // 8, 9: Gram-Schmidt form with register-resident candidates, 8 / 16 lanes per patch
-    bool sy = false;
-    if (launch_omp_restricted_reg(variant == 8 ? 8 : 16, Y, M, A, inv_norm, ids, n, child_off, child_idx, cap,
+    if (launch_omp_restricted_reg(variant == 8 ? 8 : (variant == 9 ? 16 : 4), Y, M, A, inv_norm, ids, n, child_off,
+                                  child_idx, cap,
                                   omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T,
                                   D0, N0, Xh, &sy, s))
       return sy;

@@ -46,7 +46,8 @@ struct Job {
   float *image_host = nullptr;
   std::vector<uint8_t> codes;
   size_t meas_floats = 0, img_floats = 0, bytes = 0;
-  double t_submit = 0, t_admit = 0, t_done = 0;
+  double t_submit = 0, t_admit = 0, t_done = 0, t_gpu_done = 0;
+  double enqueue_ms = 0, stage_ms[4] = {0, 0, 0, 0}, host_out_ms = 0;  // stages: copy-in, solve, aggregate, copy-out
   int batch_jobs = 0;
   int64_t batch_patches = 0;
   csp_status status = CSP_ERR_NOT_READY;
@@ -58,6 +59,7 @@ struct Job {
 struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
+  cudaEvent_t tev[5] = {};  // timing events at the batch's stage boundaries
   Workspace W;              // solver workspace, kept at its high-water mark
   bool busy = false;
   std::vector<Job *> jobs;
@@ -203,6 +205,7 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
     sl.dev = nullptr;
     return e;
   }
+  cudaEventRecord(sl.tev[0], s);
   uint8_t *D = static_cast<uint8_t *>(sl.dev), *Hs = sl.host;
   auto dp = [&](size_t o) { return D + o; };
   auto hp = [&](size_t o) { return Hs + o; };
@@ -244,6 +247,7 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
   }
   PatchSet ps;
   ps.B = Bt;
+  cudaEventRecord(sl.tev[1], s);
   if (bayer) {
     int32_t *ids = (int32_t *)hp(h_ids);
     int64_t n = 0;
@@ -275,7 +279,8 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
     // one solve over every patch of the batch
     return cudaErrorUnknown;
   }
-  // outputs: overlap-add and copy-out job by job
+  cudaEventRecord(sl.tev[2], s);
+  // outputs: overlap-add job by job, then the copies out
   for (size_t k = 0; k < sl.jobs.size(); ++k) {
     Job *j = sl.jobs[k];
     const JobLayout &L = jl[k];
@@ -285,10 +290,29 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
                                           keff + j->off, Kmax, dcy, dcx, img, s))
       launch_aggregate(j->gd, m.ctx->lv[0].D, m.N0, sup + j->off * Kmax, coef + j->off * Kmax, keff + j->off, Kmax,
                        dcy, dcx, xh, img, s);
-    if ((e = cudaMemcpyAsync(j->h_img, img, j->img_floats * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
   }
+  cudaEventRecord(sl.tev[3], s);
+  for (size_t k = 0; k < sl.jobs.size(); ++k) {
+    Job *j = sl.jobs[k];
+    if ((e = cudaMemcpyAsync(j->h_img, dp(jl[k].d_img), j->img_floats * 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return e;
+  }
+  cudaEventRecord(sl.tev[4], s);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   return cudaEventRecord(sl.ev, s);
+}
+
+// Stage times of a completed batch into its jobs (device events; host times
+// were recorded by the scheduler).
+void batch_stage_times(Slot &sl) {
+  float ms[4] = {0, 0, 0, 0};
+  for (int i = 0; i < 4; ++i)
+    if (cudaEventElapsedTime(&ms[i], sl.tev[i], sl.tev[i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms[i] = 0.f;
+    }
+  for (Job *j : sl.jobs)
+    for (int i = 0; i < 4; ++i) j->stage_ms[i] = ms[i];
 }
 
 // Called with the server lock held, after the batch's work has completed
@@ -324,9 +348,15 @@ void scheduler(csp_server *srv) {
       if (q == cudaSuccess) {
         // images from the pinned staging area to the callers' buffers, without
         // the lock (the slot stays busy and its jobs not done meanwhile)
+        const double tg = now_s();
+        batch_stage_times(sl);
         lk.unlock();
-        for (Job *j : sl.jobs)
+        for (Job *j : sl.jobs) {
+          const double t0 = now_s();
           if (j->image_host && j->h_img) std::memcpy(j->image_host, j->h_img, j->img_floats * 4);
+          j->t_gpu_done = tg;
+          j->host_out_ms = 1e3 * (now_s() - t0);
+        }
         lk.lock();
       }
       release_batch(srv, sl, q == cudaSuccess ? CSP_OK : CSP_ERR_CUDA);
@@ -366,6 +396,8 @@ void scheduler(csp_server *srv) {
       }
       lk.unlock();  // submitters may queue while the batch is being enqueued
       const cudaError_t e = launch_batch(srv, sl);
+      const double te = 1e3 * (now_s() - t);
+      for (Job *j : sl.jobs) j->enqueue_ms = te;
       lk.lock();
       if (e != cudaSuccess) {
         cudaGetLastError();
@@ -412,6 +444,7 @@ csp_status csp_server_create(csp_server **out, const csp_server_config *cfg) {
   for (Slot &sl : srv->slots) {
     cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+    for (cudaEvent_t &e : sl.tev) cudaEventCreate(&e);
     sl.W.owner = srv->alloc_ctx;
     void *st = nullptr;
     cudaMalloc(&st, 8 * sizeof(int64_t));
@@ -439,6 +472,7 @@ void csp_server_destroy(csp_server *srv) {
     cudaStreamSynchronize(sl.stream);
     cudaStreamDestroy(sl.stream);
     cudaEventDestroy(sl.ev);
+    for (cudaEvent_t e : sl.tev) cudaEventDestroy(e);
     cudaFree(sl.W.stats_dev);
     if (sl.host) cudaFreeHost(sl.host);
     sl.W.ws.clear();  // buffers are owned (and freed) by alloc_ctx
@@ -603,6 +637,13 @@ csp_status csp_job_info_get(csp_server *srv, uint64_t job_id, csp_job_info *out)
   out->batch_jobs = j->batch_jobs;
   out->batch_patches = j->batch_patches;
   out->status = j->status;
+  out->enqueue_ms = j->enqueue_ms;
+  out->copy_in_ms = j->stage_ms[0];
+  out->solve_ms = j->stage_ms[1];
+  out->aggregate_ms = j->stage_ms[2];
+  out->copy_out_ms = j->stage_ms[3];
+  out->t_gpu_done = j->t_gpu_done;
+  out->host_out_ms = j->host_out_ms;
   return CSP_OK;
 }
 

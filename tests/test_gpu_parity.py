@@ -632,20 +632,21 @@ def test_cross_scale_other_link_sizes(Q, prec):
     assert abs(oracle.psnr(w.truth, g["img"]) - oracle.psnr(w.truth, img_o)) <= 0.05
 
 
+@pytest.mark.parametrize("variant", [8, 9, 10])
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("key", ["bayer", "denoise", "denoise_ragged", "cs_dense", "rgb_identity"])
-def test_thread_per_patch_variant_on_model_reading(key, prec):
-    """Restricted variant 10 (one thread per patch, candidates in registers,
-    Q_C in shared memory) on the model reading, where every candidate set fits
-    it (|f(Omega)| = 4 K_low <= 32, K <= 8): supports and coefficients against
-    the oracle, and csp_reconstruct (which then synthesizes x_hat in the same
-    kernel) equal to extract + solve + aggregate, bit for bit."""
+def test_register_variants_on_model_reading(key, prec, variant):
+    """Restricted variants 8, 9, 10 (candidates' state in registers, 8, 16 and
+    4 lanes per patch, iteration loop unrolled) on the model reading, where
+    every candidate set fits them (|f(Omega)| = 4 K_low, K <= 8): supports and
+    coefficients against the oracle, and csp_reconstruct (which then synthesizes
+    x_hat in the same kernel) equal to extract + solve + aggregate, bit for bit."""
     from paper_1511_05174_gb300.context import Context
     w = _workload(key, links="model")
     assert max(int(np.max(k)) for k in w.K_levels) <= 8
     ctx = Context(0)
     ctx.load_workload(w)
-    ctx.set_kernel_variant(10)
+    ctx.set_kernel_variant(variant)
     meas = torch.from_numpy(np.ascontiguousarray(w.meas)).cuda()
     Y = meas.contiguous() if w.sensing.kind == "dense" else ctx.extract(meas)
     K, K_patch, Kmax = budgets(w, "cross_scale")
