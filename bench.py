@@ -66,7 +66,6 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the restricted-solver variant (0-9) instead of autotuning (profiling runs)")
-    ap.add_argument("--serving-jobs", type=int, default=24, help="jobs per offered rate")
     ap.add_argument("--sweep-q", default=None,
                     help="comma-separated children-per-coarse-atom counts Q (e.g. 2,4,8,16): instead of the "
                          "headline, time cross-scale and plain OMP and report PSNR for each Q (the link-size "
@@ -406,7 +405,8 @@ def accuracy(w, results, oracle_codes, sample):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
-SERVING_RATES = (10, 20, 50, 100, 200)  # offered jobs/s
+SERVING_RATES = {"cross_scale": (5, 10, 20, 30, 50, 100, 200), "plain": (1, 2, 5, 10)}  # offered jobs/s
+SERVING_JOBS = {"cross_scale": 32, "plain": 12}  # jobs per offered rate
 
 
 def serving_pool(kinds=("denoise", "bayer", "video"), per_kind=4, seed=0, lo=128, hi=2048, links="model"):
@@ -422,6 +422,48 @@ def serving_pool(kinds=("denoise", "bayer", "video"), per_kind=4, seed=0, lo=128
             pool.append((kind, synthetic.make_workload(kind, seed=1000 + 10 * i + len(pool), H=side, W=side,
                                                        dict_seed=0, links=links)))
     return pool
+
+
+def standalone_job_ms(device, pool, mode, precision, reps=3):
+    """Device time of each pool job alone through csp_reconstruct (device
+    buffers, default kernel choices as the server's models use them): the
+    extraction, the solve and the overlap-add, best of `reps`, CUDA events.
+    Returns [ms] in pool order."""
+    import torch
+    from paper_1511_05174_gb300.context import Context
+
+    from paper_1511_05174_gb300 import _binding as b
+
+    dev = torch.device("cuda", device)
+    out = []
+    for kind, w in pool:
+        ctx = Context(device, mem_budget_bytes=48 << 30)  # whole-image per-patch operators beyond it: skipped
+        ctx.load_workload(w)
+        K = [int(k[0]) for k in w.K_levels]
+        Km = K if mode == "cross_scale" else K[:1]
+        meas = torch.from_numpy(np.ascontiguousarray(w.meas)).to(dev)
+        img = torch.empty((w.geometry.planes, w.geometry.H, w.geometry.W), dtype=torch.float32, device=dev)
+        try:
+            ctx.reconstruct(meas, img, mode, precision, K=Km, Kmax=K[0])
+        except b.CspError as e:
+            if e.status != b.CSP_ERR_OOM:
+                raise
+            out.append(None)
+            ctx.close()
+            continue
+        best = float("inf")
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.reconstruct(meas, img, mode, precision, K=Km, Kmax=K[0])
+            b.record()
+            torch.cuda.synchronize()
+            best = min(best, a.elapsed_time(b))
+        out.append(best)
+        ctx.close()
+        del meas, img
+        torch.cuda.empty_cache()
+    return out
 
 
 def serving_bench(args, device, pool, mode, jobs_per_rate):
@@ -463,7 +505,7 @@ def serving_bench(args, device, pool, mode, jobs_per_rate):
         run(range(len(pool)))  # warm-up: every job once (workspaces, pools, staging)
         rng = np.random.default_rng(1)
         rates = []
-        for rate in SERVING_RATES:
+        for rate in SERVING_RATES[mode]:
             order = rng.integers(0, len(pool), size=jobs_per_rate)
             infos = run(order, rng.exponential(1.0 / rate, size=jobs_per_rate))
             lat = np.array([i["t_done"] - i["t_submit"] for i in infos]) * 1e3
@@ -838,7 +880,16 @@ def main():
                    "precision": args.precision, "n_streams": 2, "per_gpu": True,
                    "note": "Poisson arrivals; each job drawn uniformly from the pool; host buffers in and out"}
         for mode in ("cross_scale", "plain"):
-            serving[mode] = serving_bench(args, local, pool, mode, args.serving_jobs)
+            alone = standalone_job_ms(local, pool, mode, args.precision)
+            fit = [t for t in alone if t is not None]
+            serving[mode] = {"rates": serving_bench(args, local, pool, mode, SERVING_JOBS[mode]),
+                             "standalone_device_ms": [None if t is None else round(t, 3) for t in alone],
+                             "standalone_jobs_per_s": len(fit) / (sum(fit) / 1e3) if fit else None,
+                             "standalone_note": "each pool job alone through csp_reconstruct on device buffers "
+                                                "(extraction, solve, overlap-add), default kernel choices, 48 GiB "
+                                                "budget (null: the whole image's per-patch operators exceed it; the "
+                                                "server builds them slice by slice); jobs/s = jobs that fit / their "
+                                                "summed device time"}
 
     cpu, acc = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -407,10 +407,11 @@ csp_status csp_job_release(csp_server *srv, uint64_t job_id);
  * or its Gram-Schmidt form, which updates the correlations per appended atom
  * and solves for alpha once -- each with 4, 8 or 16 lanes per patch for
  * M <= 64, twice that for larger M; the Gram-Schmidt form also with each
- * lane's candidates held in registers, 8 or 16 lanes per patch).  csp_autotune runs
- * csp_solve once per variant on the given batch (same arguments as
- * csp_solve, outputs overwritten), times each with CUDA events, keeps the
- * fastest for this context and reports the times; then, with that variant,
+ * lane's candidates held in registers, 8, 16 or 4 lanes per patch).  csp_autotune
+ * runs csp_solve once per variant on the given batch (same arguments as
+ * csp_solve, outputs overwritten), then times three more runs with CUDA events
+ * and takes the fastest, keeps the fastest variant for this context and reports
+ * the times; then, with that variant,
  * times the two forms of the full-dictionary level (csp_set_top_level_form)
  * where the fused form applies and keeps the faster.  Synchronises `stream`. */
 #define CSP_TUNE_VARIANTS 11 /* 0: L2-cooperative, 1: shared-memory staged, 2-4: Gram-matrix proxy, 5-7: Gram-Schmidt
@@ -431,9 +432,11 @@ csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const floa
                         csp_tune_result *out);
 
 /* Pin the restricted-solver variant (0 .. CSP_TUNE_VARIANTS - 1), e.g. from a
- * stored csp_tune_result.  Variants 8-9 run as variant 6 where M > 8 x lanes,
- * Kb > 8 or more than 8 candidates per lane.  Variants 2-9 fall back to 0 on levels whose Gram
- * matrix was not kept (T^2 floats above 256 MiB or beyond the memory budget).
+ * stored csp_tune_result (a new context starts with variant 8).  Variants 8-10
+ * run as variant 6 where M is above 8 x lanes (16 x lanes with 4 lanes), Kb > 8
+ * or more than 8 candidates per lane.  Variants 2-10 fall back to 0 on levels
+ * whose Gram matrix was not kept (T^2 floats above 256 MiB or beyond the memory
+ * budget) and on per-pixel operators.
  * Errors: CSP_ERR_INVALID for an unknown variant. */
 csp_status csp_set_kernel_variant(csp_ctx *ctx, int restricted_variant);
 
@@ -446,7 +449,8 @@ csp_status csp_set_kernel_variant(csp_ctx *ctx, int restricted_variant);
 csp_status csp_set_aggregate_path(csp_ctx *ctx, int path);
 
 /* Form of the full-dictionary OMP (plain OMP; the coarsest level of
- * cross-scale OMP): 0 automatic (form 1 unless csp_autotune chose form 2),
+ * cross-scale OMP): 0 automatic (the default: form 2 wherever it applies, else
+ * form 1; csp_autotune replaces it by the faster form it measured),
  * 1 one launch per iteration for the proxy and one for the update, 2 fused:
  * all iterations of 128 patches in one CTA with residuals and factors on
  * chip (shared effective dictionary with T <= 256, a multiple of 64, M <= 64,

@@ -132,7 +132,7 @@ struct csp_ctx {
   int64_t launches[csp::KK_COUNT] = {};
   double prof_ms[csp::KK_COUNT] = {};
   bool prof = false;
-  int restricted_variant = 2;  // restricted-OMP kernel variant (see launch_omp_restricted)
+  int restricted_variant = 8;  // restricted-OMP kernel variant (see launch_omp_restricted)
   int aggregate_path = 0;      // 0 automatic, 1 two-pass (synthesis scratch), 2 fused shared-memory tiles
   int top_form = 0;            // full-dictionary level: 0 automatic, 1 per-iteration kernels, 2 fused kernel
   bool wait_test = false;      // test hook: the tensor-core proxy loads no atom tiles (its waits expire)
