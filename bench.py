@@ -432,7 +432,7 @@ def standalone_job_ms(device, pool, mode, precision, reps=3):
     import torch
     from paper_1511_05174_gb300.context import Context
 
-    from paper_1511_05174_gb300 import _binding as b
+    from paper_1511_05174_gb300 import _binding as binding
 
     dev = torch.device("cuda", device)
     out = []
@@ -445,20 +445,20 @@ def standalone_job_ms(device, pool, mode, precision, reps=3):
         img = torch.empty((w.geometry.planes, w.geometry.H, w.geometry.W), dtype=torch.float32, device=dev)
         try:
             ctx.reconstruct(meas, img, mode, precision, K=Km, Kmax=K[0])
-        except b.CspError as e:
-            if e.status != b.CSP_ERR_OOM:
+        except binding.CspError as e:
+            if e.status != binding.CSP_ERR_OOM:
                 raise
             out.append(None)
             ctx.close()
             continue
         best = float("inf")
         for _ in range(reps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
             ctx.reconstruct(meas, img, mode, precision, K=Km, Kmax=K[0])
-            b.record()
+            ev1.record()
             torch.cuda.synchronize()
-            best = min(best, a.elapsed_time(b))
+            best = min(best, ev0.elapsed_time(ev1))
         out.append(best)
         ctx.close()
         del meas, img

@@ -421,10 +421,10 @@ csp_status csp_job_release(csp_server *srv, uint64_t job_id);
 typedef struct csp_tune_result {
     int restricted_variant;            /* chosen variant index                      */
     double ms[CSP_TUNE_VARIANTS];      /* solve time per variant (ms)               */
-    int top_level_form;                /* chosen full-dictionary form (1 or 2), see
+    int top_level_form;                /* chosen full-dictionary form (1, 2 or 3), see
                                           csp_set_top_level_form                     */
-    double ms_top[2];                  /* solve time with form 1 and form 2 (0 when
-                                          form 2 does not apply)                     */
+    double ms_top[3];                  /* solve time with forms 1, 2 and 3 (0 when a
+                                          form does not apply)                       */
 } csp_tune_result;
 
 csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const float *Y, int64_t B,
@@ -450,13 +450,19 @@ csp_status csp_set_aggregate_path(csp_ctx *ctx, int path);
 
 /* Form of the full-dictionary OMP (plain OMP; the coarsest level of
  * cross-scale OMP): 0 automatic (the default: form 2 wherever it applies, else
- * form 1; csp_autotune replaces it by the faster form it measured),
+ * form 1; csp_autotune replaces it by the fastest form it measured),
  * 1 one launch per iteration for the proxy and one for the update, 2 fused:
  * all iterations of 128 patches in one CTA with residuals and factors on
  * chip (shared effective dictionary with T <= 256, a multiple of 64, M <= 64,
- * K <= 8, BF16 precision; other shapes use form 1).  The two forms select the
- * same atoms (same tensor-core proxy, FP32 re-score of its four best) and
- * differ in FP32 rounding only.  CSP_ERR_INVALID for another value. */
+ * K <= 8, BF16 precision; other shapes use form 1), 3 the Gram form (the
+ * "Batch-OMP" form of Sec. III-C's cost terms, no residual): the correlations
+ * P0 = Y A^T once by an FP32 GEMM, then every iteration from the level's Gram
+ * matrix G = A A^T with all atoms as candidates -- the proxy c = P0 - Q_C z,
+ * Q_C = A^T U updated by one Gram row per appended atom -- in FP32 at every
+ * precision (shared dictionary kept with its Gram matrix, T <= 256, K <= 8,
+ * M <= 256; other shapes use forms 2 or 1).  Forms 1 and 2 select the same
+ * atoms (same tensor-core proxy, FP32 re-score of its best four); form 3 scores
+ * every atom in FP32.  CSP_ERR_INVALID for another value. */
 csp_status csp_set_top_level_form(csp_ctx *ctx, int form);
 
 /* Test hook for failure detection (not part of the method).  on != 0: the

@@ -71,7 +71,7 @@ class csp_kernel_time(ctypes.Structure):
 
 class csp_tune_result(ctypes.Structure):
     _fields_ = [("restricted_variant", ctypes.c_int), ("ms", ctypes.c_double * TUNE_VARIANTS),
-                ("top_level_form", ctypes.c_int), ("ms_top", ctypes.c_double * 2)]
+                ("top_level_form", ctypes.c_int), ("ms_top", ctypes.c_double * 3)]
 
 
 class csp_server_config(ctypes.Structure):

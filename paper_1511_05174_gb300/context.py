@@ -182,7 +182,8 @@ class Context:
         b.csp_set_wait_test(self._ctx, on)
 
     def set_top_level_form(self, form: int) -> None:
-        """0 automatic, 1 per-iteration kernels, 2 fused full-dictionary kernel."""
+        """0 automatic, 1 per-iteration kernels, 2 fused full-dictionary kernel,
+        3 Gram form (correlation GEMM once, Gram-Schmidt iteration over every atom)."""
         b.csp_set_top_level_form(self._ctx, form)
 
     def set_aggregate_path(self, path: int) -> None:

@@ -110,7 +110,7 @@ csp_status ws_get_t(csp_ctx *ctx, Workspace &W, int slot, size_t count, T **out)
 
 const char *const kKernelNames[KK_COUNT] = {"extract", "downsample", "prepare", "omp_init", "proxy_fp32",
                                             "proxy_bf16", "omp_update", "restricted", "aggregate", "lift",
-                                            "omp_fused", "ksvd_sort", "ksvd_sweep"};
+                                            "omp_fused", "ksvd_sort", "ksvd_sweep", "full_gram"};
 
 cudaEvent_t pool_event(csp_ctx *ctx) {
   if (!ctx->ev_pool.empty()) {
@@ -160,7 +160,7 @@ enum Slot {
   WS_LV_OMEGA, WS_LV_ALPHA = WS_LV_OMEGA + CSP_MAX_LEVELS, WS_LV_KEFF = WS_LV_ALPHA + CSP_MAX_LEVELS,
   WS_LV_Y = WS_LV_KEFF + CSP_MAX_LEVELS,
   WS_XH = WS_LV_Y + CSP_MAX_LEVELS,
-  WS_SCRATCH, WS_LIFT, WS_LIFTBF, WS_PPC_A, WS_PPC_INV, WS_PART, WS_KEYS,
+  WS_SCRATCH, WS_LIFT, WS_LIFTBF, WS_PPC_A, WS_PPC_INV, WS_PART, WS_KEYS, WS_P0,
   WS_KS_R, WS_KS_RN2, WS_KS_XN2, WS_KS_TAKEN, WS_KS_HIST, WS_KS_OFF, WS_KS_SEG, WS_KS_ERR, WS_KS_STATS,
   WS_COUNT
 };
@@ -376,12 +376,30 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
     }
   }
 
-  // full-dictionary OMP at the top level (the only level in plain mode): all
-  // iterations in one fused kernel when the dictionary is small and shared
+  // full-dictionary OMP at the top level (the only level in plain mode), form 3:
+  // the Gram form -- correlations P0 = Y A^T once (FP32 GEMM), then every
+  // iteration from the level's Gram matrix with all atoms as candidates
   bool fused_done = false;
-  {
+  if (ctx->top_form == 3) {
     const LevelData &L = ctx->lv[top];
-    const bool want = ctx->top_form != 1;  // 0 (automatic) and 2: the fused form wherever it applies
+    bool ok = !L.per_patch && full_gram_supported(L.M, L.T, Kb[top]);
+    for (int ph = 0; ph < nph; ++ph) ok = ok && L.G[ph] != nullptr;
+    if (ok) {
+      float *P0 = nullptr;
+      CSP_TRY(ws_get_t(ctx, W, WS_P0, (size_t)B * L.T, &P0));
+      for (int ph = 0; ph < nph; ++ph)
+        run(ctx, KK_FULL_GRAM, s, n_of(ph), [&] {
+          launch_omp_full_gram(Yl[top], L.M, L.A[ph], L.inv_norm[ph], ids_of(ph), n_of(ph), prm->K_patch[top],
+                               prm->K[top], Kb[top], lv_om[top], lv_al[top], ldo[top], lv_ke[top], W.stats_dev,
+                               L.G[ph], L.T, P0, s);
+        });
+      fused_done = true;
+    }
+  }
+  // otherwise all iterations in one fused kernel when the dictionary is small and shared
+  if (!fused_done) {
+    const LevelData &L = ctx->lv[top];
+    const bool want = ctx->top_form == 0 || ctx->top_form == 2;  // automatic and 2: fused wherever it applies
     if (want && bf16 && !L.per_patch && L.Mp == 64 && fused_top_supported(L.M, L.T, Kb[top])) {
       const float *Aph[kMaxPhases] = {}, *Iph[kMaxPhases] = {};
       const __nv_bfloat16 *Bph[kMaxPhases] = {};
@@ -1363,14 +1381,18 @@ csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const floa
   const int Ktop = params->K_patch[nl - 1] ? params->Kmax : params->K[nl - 1];
   const bool fusable = params->precision == CSP_PREC_BF16 && !LT.per_patch && LT.Mp == 64 &&
                        fused_top_supported(LT.M, LT.T, Ktop);
-  for (int form = 1; form <= (fusable ? 2 : 1) && st == CSP_OK; ++form) {
+  bool gramable = !LT.per_patch && full_gram_supported(LT.M, LT.T, Ktop);
+  for (int ph = 0; ph < kMaxPhases; ++ph) gramable = gramable && (!LT.A[ph] || LT.G[ph]);
+  out->ms_top[2] = 0.0;
+  for (int form = 1; form <= 3 && st == CSP_OK; ++form) {
+    if ((form == 2 && !fusable) || (form == 3 && !gramable)) continue;
     ctx->top_form = form;
     float ms = 0.f;
     st = time_solve(&ms);
     if (st != CSP_OK) break;
     out->ms_top[form - 1] = ms;
+    if (ms < out->ms_top[out->top_level_form - 1]) out->top_level_form = form;
   }
-  if (st == CSP_OK && fusable) out->top_level_form = out->ms_top[1] < out->ms_top[0] ? 2 : 1;
   ctx->top_form = st == CSP_OK ? out->top_level_form : saved_form;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1385,7 +1407,7 @@ csp_status csp_set_wait_test(csp_ctx *ctx, int on) {
 
 csp_status csp_set_top_level_form(csp_ctx *ctx, int form) {
   if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
-  if (form < 0 || form > 2) return fail(ctx, CSP_ERR_INVALID, "unknown full-dictionary form");
+  if (form < 0 || form > 3) return fail(ctx, CSP_ERR_INVALID, "unknown full-dictionary form");
   ctx->top_form = form;
   return CSP_OK;
 }

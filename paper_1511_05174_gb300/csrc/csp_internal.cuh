@@ -90,7 +90,7 @@ struct Workspace {
 
 enum KernelKind {
   KK_EXTRACT, KK_DOWNSAMPLE, KK_PREP, KK_INIT, KK_PROXY_FP32, KK_PROXY_BF16, KK_UPDATE, KK_RESTRICTED,
-  KK_AGGREGATE, KK_LIFT, KK_FUSED, KK_KSVD_SORT, KK_KSVD_SWEEP, KK_COUNT
+  KK_AGGREGATE, KK_LIFT, KK_FUSED, KK_KSVD_SORT, KK_KSVD_SWEEP, KK_FULL_GRAM, KK_COUNT
 };
 struct ProfRec {
   int kind;
@@ -134,7 +134,8 @@ struct csp_ctx {
   bool prof = false;
   int restricted_variant = 8;  // restricted-OMP kernel variant (see launch_omp_restricted)
   int aggregate_path = 0;      // 0 automatic, 1 two-pass (synthesis scratch), 2 fused shared-memory tiles
-  int top_form = 0;            // full-dictionary level: 0 automatic, 1 per-iteration kernels, 2 fused kernel
+  int top_form = 0;            // full-dictionary level: 0 automatic, 1 per-iteration kernels, 2 fused kernel,
+                               // 3 Gram form (P0 GEMM + Gram-Schmidt iteration over every atom)
   bool wait_test = false;      // test hook: the tensor-core proxy loads no atom tiles (its waits expire)
   // CUDA graphs of the last csp_solve and csp_reconstruct (csp_set_graph_mode):
   // replayed while the call and the context's buffers are unchanged
@@ -310,6 +311,17 @@ bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, con
 void launch_gram(const float *A, int T, int M, float *Gm, cudaStream_t s);
 // variant 0: rows from L2 every pass (cooperative groups); 1: rows staged in shared memory;
 // 2: proxy from the Gram matrix + exact re-score of the best three (falls back to 0 without gram).
+// P0 = Y A^T (FP32) for the patches ids[0..n): P0[b][a] = <a_a, y_b>.
+void launch_p0_gemm(const float *Y, int M, const float *A, int T, const int32_t *ids, int64_t n, float *P0,
+                    cudaStream_t s);
+// Full-dictionary level in the Gram form (form 3): P0 = Y A^T once, then the
+// register-resident Gram-Schmidt iteration with every atom a candidate (32
+// lanes per patch; T <= 256, Kb <= 8, M <= 256); needs the level's Gram matrix
+// and P0 scratch of n x T floats.  False when the shape does not fit.
+bool full_gram_supported(int M, int T, int Kb);
+bool launch_omp_full_gram(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids, int64_t n,
+                          const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo, int8_t *k_eff,
+                          int64_t *stats, const float *gram, int T, float *P0, cudaStream_t s);
 bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, const float *inv_norm,
                            const int32_t *ids, int64_t n, const int32_t *child_off,
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,

@@ -1252,7 +1252,8 @@ omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__res
                           const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                           int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
                           int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T,
-                          const float *__restrict__ D0, int N0, float *__restrict__ Xh) {
+                          const float *__restrict__ D0, int N0, float *__restrict__ Xh,
+                          const float *__restrict__ p0full) {
   constexpr int KM = 8;
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
@@ -1270,14 +1271,27 @@ omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__res
   const int64_t b = valid ? (ids ? __ldg(ids + wi) : wi) : 0;
   int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
   Kpb = Kpb < Kb ? Kpb : Kb;
-  const int kup = valid ? keff_up[b] : 0;
   const float *yrow = Y + b * M;
   const float4 *y4 = reinterpret_cast<const float4 *>(yrow);
   // candidates, their inverse norms and p0 = A_C^T y (group-cooperative, in shared memory)
   float4 yv[NCH];
   load_chunks<G, NCH>(yv, yrow, nv, s, valid);
-  const int nc = gram_setup<G, NCH>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
-                                    inv_norm, stats, M, A, yv, p0);
+  int nc;
+  if (p0full) {
+    // full-dictionary level (the Gram form of Algorithm 1): every atom is a
+    // candidate, p0 comes from the precomputed correlations P0[b] = A y_b
+    nc = valid ? (T < cap ? T : cap) : 0;
+    for (int c = s; c < nc; c += G) {
+      S.cs[c] = c;
+      S.invn[c] = __ldg(inv_norm + c);
+      p0[c] = __ldg(p0full + b * (int64_t)T + c);
+    }
+    __syncwarp();
+  } else {
+    const int kup = valid ? keff_up[b] : 0;
+    nc = gram_setup<G, NCH>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg, inv_norm,
+                            stats, M, A, yv, p0);
+  }
   const float ysq = gsum<G>(dotc<NCH>(yv, yv));
   // this lane's candidates into registers (u < ucnt: a bound uniform over the warp, <= CPL)
   const int ucnt = __reduce_max_sync(kFull, (nc + G - 1) / G);
@@ -1572,7 +1586,7 @@ bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, con
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kern<<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up,
                                                       ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats,
-                                                      gram, T, D0, N0, synth ? Xh : nullptr);
+                                                      gram, T, D0, N0, synth ? Xh : nullptr, nullptr);
   };
   switch (G * 100 + CPL) {
     case 402: go(omp_restricted_reg_kernel<4, 2, 4>); break;
@@ -1591,6 +1605,36 @@ bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, con
     case 1606: go(omp_restricted_reg_kernel<16, 6, 2>); break;
     case 1608: go(omp_restricted_reg_kernel<16, 8, 2>); break;
     default: return false;
+  }
+  return true;
+}
+
+bool full_gram_supported(int M, int T, int Kb) { return M % 4 == 0 && M <= 256 && T >= 1 && T <= 256 && Kb <= 8; }
+
+bool launch_omp_full_gram(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids, int64_t n,
+                          const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo, int8_t *k_eff,
+                          int64_t *stats, const float *gram, int T, float *P0, cudaStream_t s) {
+  if (!full_gram_supported(M, T, Kb) || !gram || !P0) return false;
+  if (n == 0) return true;
+  launch_p0_gemm(Y, M, A, T, ids, n, P0, s);
+  constexpr int G = 32;
+  const int per_g = (T + G - 1) / G;
+  const int CPL = per_g <= 2 ? 2 : (per_g <= 4 ? 4 : 8);
+  const int per_cta = WV_WARPS * (32 / G);
+  const size_t sm = (size_t)reg_group_bytes(Kb, T) * per_cta;
+  auto go = [&](auto kern) {
+    if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kern<<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n, nullptr, nullptr, T, nullptr, 0,
+                                                      nullptr, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T,
+                                                      nullptr, 0, nullptr, P0);
+  };
+  switch ((M <= 128 ? 10 : 20) + CPL) {
+    case 12: go(omp_restricted_reg_kernel<32, 2, 1>); break;
+    case 14: go(omp_restricted_reg_kernel<32, 4, 1>); break;
+    case 18: go(omp_restricted_reg_kernel<32, 8, 1>); break;
+    case 22: go(omp_restricted_reg_kernel<32, 2, 2>); break;
+    case 24: go(omp_restricted_reg_kernel<32, 4, 2>); break;
+    default: go(omp_restricted_reg_kernel<32, 8, 2>); break;
   }
   return true;
 }

@@ -732,6 +732,102 @@ void launch_proxy_fp32(const float *R, int M, const float *A, const float *inv_n
   if (kk) proxy_keys_kernel<<<blocks(n, 256), 256, 0, s>>>(kk, ids, n, cand);
 }
 
+// P0 = Y A^T for the patches ids[0..n) (all correlations <a_i, y_b> of a
+// shared dictionary: the starting point of the Gram form of the full-dictionary
+// level).  The GEMM of proxy_fp32_kernel (128 patches x 128 atoms per CTA, 8 x 8
+// per thread, contraction in double-buffered chunks of 16) with an epilogue that
+// stores the FP32 products row by row: P0[b][a], b the patch id.
+__global__ void __launch_bounds__(256)
+p0_gemm_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A, int T,
+               const int32_t *__restrict__ ids, int64_t n, float *__restrict__ P0) {
+  __shared__ __align__(16) float Rs[2 * PF_KC * PF_LD];
+  __shared__ __align__(16) float As[2 * PF_KC * PF_LD];
+  __shared__ int64_t Pb[PF_TP];
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  const int64_t p0 = (int64_t)blockIdx.x * PF_TP;
+  const int a0 = blockIdx.y * PF_TA;
+  for (int p = tid; p < PF_TP; p += 256) {
+    const int64_t pi = p0 + p;
+    Pb[p] = pi < n ? (ids ? ids[pi] : pi) : -1;
+  }
+  __syncthreads();
+  const int lrow = tid >> 1, lk = (tid & 1) * 8;
+  const bool rrow_ok = Pb[lrow] >= 0;
+  const float *rrow = Y + (rrow_ok ? Pb[lrow] : 0) * (int64_t)M;
+  const bool arow_ok = a0 + lrow < T;
+  const float *arow = A + (arow_ok ? a0 + lrow : 0) * (int64_t)M;
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  float4 gr[2], ga[2];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = k0 + lk + 4 * h;
+      gr[h] = (rrow_ok && k < M) ? __ldg(reinterpret_cast<const float4 *>(rrow + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      ga[h] = (arow_ok && k < M) ? __ldg(reinterpret_cast<const float4 *>(arow + k)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  auto stash = [&](int buf) {
+    float *rs = Rs + buf * PF_KC * PF_LD, *as = As + buf * PF_KC * PF_LD;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lk + 4 * h;
+      rs[(k + 0) * PF_LD + lrow] = gr[h].x;
+      rs[(k + 1) * PF_LD + lrow] = gr[h].y;
+      rs[(k + 2) * PF_LD + lrow] = gr[h].z;
+      rs[(k + 3) * PF_LD + lrow] = gr[h].w;
+      as[(k + 0) * PF_LD + lrow] = ga[h].x;
+      as[(k + 1) * PF_LD + lrow] = ga[h].y;
+      as[(k + 2) * PF_LD + lrow] = ga[h].z;
+      as[(k + 3) * PF_LD + lrow] = ga[h].w;
+    }
+  };
+  load(0);
+  stash(0);
+  __syncthreads();
+  int buf = 0;
+  for (int k0 = 0; k0 < M; k0 += PF_KC) {
+    const bool more = k0 + PF_KC < M;
+    if (more) load(k0 + PF_KC);
+    const float *rs = Rs + buf * PF_KC * PF_LD, *as = As + buf * PF_KC * PF_LD;
+#pragma unroll 4
+    for (int kk = 0; kk < PF_KC; ++kk) {
+      const float4 r0 = *reinterpret_cast<const float4 *>(rs + kk * PF_LD + ty * 8);
+      const float4 r1 = *reinterpret_cast<const float4 *>(rs + kk * PF_LD + ty * 8 + 4);
+      const float4 x0 = *reinterpret_cast<const float4 *>(as + kk * PF_LD + tx * 8);
+      const float4 x1 = *reinterpret_cast<const float4 *>(as + kk * PF_LD + tx * 8 + 4);
+      const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+      const float av[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(rv[i], av[j], acc[i][j]);
+    }
+    if (more) stash(buf ^ 1);
+    __syncthreads();
+    buf ^= 1;
+  }
+  // rows of 8 consecutive atoms per thread: two float4 stores when the row is whole
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int64_t b = Pb[ty * 8 + i];
+    if (b < 0) continue;
+    const int a = a0 + tx * 8;
+    float *dst = P0 + b * (int64_t)T + a;
+    if (a + 8 <= T && (T & 3) == 0) {
+      reinterpret_cast<float4 *>(dst)[0] = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+      reinterpret_cast<float4 *>(dst)[1] = make_float4(acc[i][4], acc[i][5], acc[i][6], acc[i][7]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        if (a + j < T) dst[j] = acc[i][j];
+    }
+  }
+}
+
 // (G, NCH) of the restricted kernel: wide groups (one candidate per lane).
 template <typename F>
 bool dispatch_group_wide(int M, F &&f) {
@@ -741,6 +837,13 @@ bool dispatch_group_wide(int M, F &&f) {
   else if (M <= 256) f(std::integral_constant<int, 32>{}, std::integral_constant<int, 2>{});
   else return false;
   return true;
+}
+
+void launch_p0_gemm(const float *Y, int M, const float *A, int T, const int32_t *ids, int64_t n, float *P0,
+                    cudaStream_t s) {
+  if (n == 0) return;
+  const dim3 grid((unsigned)((n + PF_TP - 1) / PF_TP), (unsigned)((T + PF_TA - 1) / PF_TA));
+  p0_gemm_kernel<<<grid, 256, 0, s>>>(Y, M, A, T, ids, n, P0);
 }
 
 bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, const float *inv_norm,

@@ -149,12 +149,15 @@ def test_independent_problems_nonunit_norms(B, M, T, K, prec):
     assert rate >= MATCH and worst <= REL_TOL, bad[:10]
 
 
-@pytest.mark.parametrize("form", [1, 2])
-@pytest.mark.parametrize("B,M,T,K", [(1000, 64, 256, 6), (777, 64, 192, 5), (300, 16, 64, 3), (129, 32, 128, 8)])
+@pytest.mark.parametrize("form", [1, 2, 3])
+@pytest.mark.parametrize("B,M,T,K", [(1000, 64, 256, 6), (777, 64, 192, 5), (300, 16, 64, 3), (129, 32, 128, 8),
+                                     (200, 128, 100, 7)])
 def test_full_dictionary_forms_agree_with_oracle(B, M, T, K, form):
     """The fused full-dictionary kernel (form 2: every iteration of 128 patches
-    in one CTA) and the per-iteration kernels (form 1), BF16 proxy with FP32
-    re-score, against the oracle; ragged tiles, per-patch budgets."""
+    in one CTA), the per-iteration kernels (form 1), BF16 proxy with FP32
+    re-score, and the Gram form (form 3: correlation GEMM once, Gram-Schmidt
+    iteration over every atom in FP32), against the oracle; ragged tiles
+    (patches and atoms), per-patch budgets."""
     from paper_1511_05174_gb300.context import Context
     A, Y, _ = synthetic.make_independent_problems(B, M, T, K, seed=5, sigma=0.05)
     Kp = np.random.default_rng(6).integers(0, K + 1, size=B).astype(np.int8)
@@ -167,7 +170,8 @@ def test_full_dictionary_forms_agree_with_oracle(B, M, T, K, form):
     sup, coef, keff = ctx.solve(torch.from_numpy(Y).cuda(), "plain", "bf16", K=[K],
                                 K_patch=[torch.from_numpy(Kp).cuda()], Kmax=K)
     prof = ctx.profile_read()
-    assert ("omp_fused" in prof) == (form == 2)
+    assert ("omp_fused" in prof) == (form == 2 and T % 64 == 0 and M <= 64)
+    assert ("full_gram" in prof) == (form == 3)
     o, a, k, _ = oracle.omp_batch([A] * len(Y), Y, [int(x) for x in Kp])
     rate, worst, bad = compare(A, sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy().astype(int), o, a, k)
     assert rate >= MATCH and worst <= REL_TOL, bad[:10]
@@ -504,9 +508,9 @@ def test_autotune_picks_a_variant():
     r = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
     assert r["restricted_variant"] in range(11) and all(t > 0 for t in r["ms"])
     assert r["ms"][r["restricted_variant"]] == min(r["ms"])
-    # the BF16 Bayer coarse level (T = 256, M = 64, K = 4) has both full-dictionary forms
+    # the BF16 Bayer coarse level (T = 256, M = 64, K = 4) has all three full-dictionary forms
     r2 = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
-    assert r2["top_level_form"] in (1, 2) and r2["ms_top"][0] > 0 and r2["ms_top"][1] > 0
+    assert r2["top_level_form"] in (1, 2, 3) and all(t > 0 for t in r2["ms_top"])  # form 3 applies too
     assert r2["ms_top"][r2["top_level_form"] - 1] == min(r2["ms_top"])
 
 
@@ -664,3 +668,38 @@ def test_register_variants_on_model_reading(key, prec, variant):
     torch.cuda.synchronize()
     assert ctx.stats()["synthesized"]
     assert np.array_equal(img.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("key,links", [("bayer", "model"), ("bayer", "paper"), ("denoise", "model"),
+                                       ("rgb_identity", "model"), ("cs_dense", "model"), ("denoise_ragged", "paper")])
+def test_gram_form_of_the_coarse_level(key, links, prec):
+    """Form 3 (Gram form) at the coarsest level of Algorithm 2: supports and
+    coefficients against the oracle, and csp_reconstruct in graph mode equal to
+    the three calls."""
+    from paper_1511_05174_gb300.context import Context
+    w = _workload(key, links=links)
+    ctx = Context(0)
+    ctx.load_workload(w)
+    ctx.set_top_level_form(3)
+    ctx.profile(True)
+    meas = torch.from_numpy(np.ascontiguousarray(w.meas)).cuda()
+    Y = meas.contiguous() if w.sensing.kind == "dense" else ctx.extract(meas)
+    K, K_patch, Kmax = budgets(w, "cross_scale")
+    sup, coef, keff = ctx.solve(Y, "cross_scale", prec, K=K, K_patch=K_patch, Kmax=Kmax)
+    assert "full_gram" in ctx.profile_read()
+    o, a, k, _ = oracle.cross_scale_omp(w)
+    rate, worst, bad = compare(w.dicts[0], sup.cpu().numpy(), coef.cpu().numpy(),
+                               keff.cpu().numpy().astype(np.int64), o, a, k)
+    assert rate >= MATCH and worst <= REL_TOL, bad[:10]
+    if w.sensing.kind == "dense" or K_patch is not None:
+        return
+    ref = ctx.aggregate(sup, coef, keff).cpu().numpy()
+    img = torch.full_like(torch.from_numpy(ref).cuda(), -3.0)
+    ctx.set_graph_mode(True)
+    for _ in range(2):
+        img.fill_(-3.0)
+        ctx.reconstruct(meas, img, "cross_scale", prec, K=K, Kmax=Kmax)
+        torch.cuda.synchronize()
+        assert np.array_equal(img.cpu().numpy(), ref)
+    ctx.set_graph_mode(False)
