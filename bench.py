@@ -75,6 +75,9 @@ def parse():
                          "models) on a synthetic training set shaped like --workload: one Step-2 iteration "
                          "(zero-tree coding + dictionary-update sweep) against one plain K-SVD iteration")
     ap.add_argument("--ksvd-signals", type=int, default=65536, help="training signals of --ksvd")
+    ap.add_argument("--uneven", action="store_true",
+                    help="instead of the headline, time the light-field workload with per-patch budgets K in [8, 20] "
+                         "with the work order off and on (sorted by budget, persistent warps on a work queue)")
     ap.add_argument("--no-pipeline", action="store_true",
                     help="one stream throughout (csp_set_pipeline off; profiling runs)")
     ap.add_argument("--top-form", type=int, default=None, choices=[1, 2],
@@ -696,6 +699,71 @@ def ksvd_bench(args):
     print(json.dumps(out))
 
 
+def uneven_bench(args):
+    """Uneven per-patch work: the light-field workload (4 coded-aperture shots
+    of 4 x 4 views, 3,969 patches, D 1024 x 8192, K drawn per patch in [8, 20],
+    three scales) solved with per-patch budgets, cross-scale and plain, with the
+    work order off (static grids in patch order) and on (patches sorted by
+    budget, largest first; restricted levels on persistent warps fed by a work
+    queue).  CUDA graph replay, L2 flushed between steps; per-kernel times from
+    a one-stream pass with graph replay off.  One JSON line."""
+    import torch
+    import synthetic
+    from paper_1511_05174_gb300.context import Context
+
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    w = synthetic.make_workload("lightfield", links=args.links)
+    ctx = Context(0)
+    ctx.load_workload(w)
+    Y = ctx.extract(torch.from_numpy(np.ascontiguousarray(w.meas)).to(dev))
+    B = w.n_patches
+    out = {"workload": f"lightfield_coded_aperture_{w.geometry.H}x{w.geometry.W}x{w.geometry.planes}_patch8_stride4",
+           "patches": int(B), "K_range": [int(w.K_levels[0].min()), int(w.K_levels[0].max())],
+           "links": args.links, "precision": args.precision, "data": "synthetic (seeded)", "l2": "flushed between steps"}
+    for mode in ("cross_scale", "plain"):
+        levels = w.K_levels if mode == "cross_scale" else w.K_levels[:1]
+        Kmax = int(max(int(k.max()) for k in levels))
+        K_patch = [torch.from_numpy(k.astype(np.int8)).to(dev) for k in levels]
+        K = [Kmax] * len(levels)
+        tune = ctx.autotune(Y, mode, args.precision, K=K, K_patch=K_patch, Kmax=Kmax)
+        row = {"restricted_variant": tune["restricted_variant"], "top_level_form": tune["top_level_form"]}
+        outs = {}
+        for order in (0, 1):
+            ctx.set_work_order(order)
+            ctx.set_graph_mode(True)
+            for _ in range(max(args.warmup, 3)):
+                res = ctx.solve(Y, mode, args.precision, K=K, K_patch=K_patch, Kmax=Kmax)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            torch.cuda.synchronize()
+            for a, b in ev:
+                flush.zero_()
+                a.record()
+                res = ctx.solve(Y, mode, args.precision, K=K, K_patch=K_patch, Kmax=Kmax)
+                b.record()
+            torch.cuda.synchronize()
+            ms = sorted(a.elapsed_time(b) for a, b in ev)
+            outs[order] = [t.cpu().numpy() for t in res]
+            ctx.set_graph_mode(False)
+            ctx.profile_read(reset=True)
+            ctx.profile(True)
+            for _ in range(args.steps):
+                flush.zero_()
+                ctx.solve(Y, mode, args.precision, K=K, K_patch=K_patch, Kmax=Kmax)
+            torch.cuda.synchronize()
+            prof = ctx.profile_read(reset=True)
+            ctx.profile(False)
+            row["sorted_queue" if order else "static"] = {
+                "ms_median": ms[len(ms) // 2], "ms_min": ms[0], "patches_per_s": B / (ms[len(ms) // 2] / 1e3),
+                "kernels_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()}}
+        ctx.set_work_order(0)
+        row["identical_results"] = all(np.array_equal(a, b) for a, b in zip(outs[0], outs[1]))
+        row["speedup_sorted_queue"] = row["static"]["ms_median"] / row["sorted_queue"]["ms_median"]
+        out[mode] = row
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -706,6 +774,9 @@ def main():
         return
     if args.ksvd:
         ksvd_bench(args)
+        return
+    if args.uneven:
+        uneven_bench(args)
         return
 
     import torch

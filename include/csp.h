@@ -465,6 +465,18 @@ csp_status csp_set_aggregate_path(csp_ctx *ctx, int path);
  * every atom in FP32.  CSP_ERR_INVALID for another value. */
 csp_status csp_set_top_level_form(csp_ctx *ctx, int form);
 
+/* Work order of solves with per-patch budgets (K_patch of level 0 given) on
+ * one operator group (not Bayer phases): 0 (default) every level runs a static
+ * grid over the patches in their order; 1 the patches are first sorted by
+ * their level-0 budget, largest first (a counting sort on the device), every
+ * level takes them in that order, and the restricted Gram and Gram-Schmidt
+ * kernels (variants 2-7) run persistent warps that take the next group of
+ * patches from a work queue with one atomic add -- long problems start first
+ * and warps that finish early take more (uneven K across patches, Sec. IV
+ * light fields; scheduling only: every patch's result is the same).  Nothing
+ * in the queue waits.  CSP_ERR_INVALID for another value. */
+csp_status csp_set_work_order(csp_ctx *ctx, int order);
+
 /* Test hook for failure detection (not part of the method).  on != 0: the
  * tensor-core proxy's TMA producer issues no atom-tile loads, so the MMA
  * thread's bounded mbarrier wait expires (after about 2 s), the kernel records

@@ -39,7 +39,7 @@ EXPORTS = ("csp_create", "csp_destroy", "csp_last_error", "csp_set_geometry", "c
            "csp_server_create", "csp_server_destroy", "csp_server_last_error", "csp_server_add_model",
            "csp_submit", "csp_poll", "csp_wait", "csp_job_info_get", "csp_job_release",
            "csp_server_pause", "csp_set_aggregate_path", "csp_set_top_level_form",
-           "csp_set_wait_test", "csp_set_graph_mode", "csp_set_pipeline", "csp_reconstruct",
+           "csp_set_wait_test", "csp_set_graph_mode", "csp_set_pipeline", "csp_set_work_order", "csp_reconstruct",
            "csp_downsample", "csp_ksvd_update", "csp_ksvd_init_atoms", "csp_ksvd_stats_get")
 
 
@@ -141,6 +141,7 @@ def load_library(path: str = LIB_PATH):
         "csp_set_wait_test": (i, [vp, i]),
         "csp_set_graph_mode": (i, [vp, i]),
         "csp_set_pipeline": (i, [vp, i]),
+        "csp_set_work_order": (i, [vp, i]),
         "csp_profile_enable": (i, [vp, i]),
         "csp_profile_read": (i, [vp, ctypes.POINTER(csp_kernel_time), i, ctypes.POINTER(ctypes.c_int), i]),
         "csp_server_create": (i, [ctypes.POINTER(vp), ctypes.POINTER(csp_server_config)]),
@@ -276,6 +277,10 @@ def csp_set_graph_mode(ctx, on: bool) -> None:
 
 def csp_set_pipeline(ctx, on: bool) -> None:
     check(load_library().csp_set_pipeline(ctx, int(bool(on))), ctx)
+
+
+def csp_set_work_order(ctx, order: int) -> None:
+    check(load_library().csp_set_work_order(ctx, int(order)), ctx)
 
 
 def csp_set_wait_test(ctx, on: bool) -> None:

@@ -177,6 +177,11 @@ class Context:
         """Pipelined cross-scale solve on two streams (see csp_set_pipeline)."""
         b.csp_set_pipeline(self._ctx, on)
 
+    def set_work_order(self, order: int) -> None:
+        """0 static grids in patch order; 1 patches sorted by budget (largest
+        first) and the restricted levels on a work queue (csp_set_work_order)."""
+        b.csp_set_work_order(self._ctx, order)
+
     def set_wait_test(self, on: bool) -> None:
         """Failure-detection test hook (see csp_set_wait_test)."""
         b.csp_set_wait_test(self._ctx, on)

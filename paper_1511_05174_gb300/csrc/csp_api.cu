@@ -160,7 +160,7 @@ enum Slot {
   WS_LV_OMEGA, WS_LV_ALPHA = WS_LV_OMEGA + CSP_MAX_LEVELS, WS_LV_KEFF = WS_LV_ALPHA + CSP_MAX_LEVELS,
   WS_LV_Y = WS_LV_KEFF + CSP_MAX_LEVELS,
   WS_XH = WS_LV_Y + CSP_MAX_LEVELS,
-  WS_SCRATCH, WS_LIFT, WS_LIFTBF, WS_PPC_A, WS_PPC_INV, WS_PART, WS_KEYS, WS_P0,
+  WS_SCRATCH, WS_LIFT, WS_LIFTBF, WS_PPC_A, WS_PPC_INV, WS_PART, WS_KEYS, WS_P0, WS_ORDER, WS_ORDER_CNT, WS_QUEUE,
   WS_KS_R, WS_KS_RN2, WS_KS_XN2, WS_KS_TAKEN, WS_KS_HIST, WS_KS_OFF, WS_KS_SEG, WS_KS_ERR, WS_KS_STATS,
   WS_COUNT
 };
@@ -344,7 +344,21 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
   // phase groups
   const bool phased = ps.phase_ids != nullptr;
   const int nph = phased ? 4 : 1;
-  auto ids_of = [&](int ph) -> const int32_t * { return phased ? ps.phase_ids + ps.phase_start[ph] : nullptr; };
+  // work order (csp_set_work_order): with per-patch budgets and one operator
+  // group, every level takes the patches sorted by the finest budget, largest
+  // first, and the restricted levels pull them from a work queue
+  const int32_t *order = nullptr;
+  unsigned long long *queue = nullptr;
+  if (ctx->work_order == 1 && !phased && prm->K_patch[0]) {
+    int32_t *ord = nullptr;
+    int *cnt = nullptr;
+    CSP_TRY(ws_get_t(ctx, W, WS_ORDER, (size_t)B, &ord));
+    CSP_TRY(ws_get_t(ctx, W, WS_ORDER_CNT, (size_t)2 * (CSP_MAX_K + 1), &cnt));
+    CSP_TRY(ws_get_t(ctx, W, WS_QUEUE, (size_t)1, &queue));
+    run(ctx, KK_PREP, s, B, [&] { launch_sort_by_budget(prm->K_patch[0], B, ord, cnt, s); });
+    order = ord;
+  }
+  auto ids_of = [&](int ph) -> const int32_t * { return phased ? ps.phase_ids + ps.phase_start[ph] : order; };
   auto n_of = [&](int ph) -> int64_t { return phased ? ps.phase_start[ph + 1] - ps.phase_start[ph] : B; };
 
   // per-level measurement vectors (Phi = I: y_l = W_l y)
@@ -737,6 +751,7 @@ csp_ctx::GraphKey graph_key(const csp_ctx *ctx, const csp_solve_params *prm) {
   key.wait_test = ctx->wait_test;
   key.pipeline = ctx->pipeline;
   key.aggregate_path = ctx->aggregate_path;
+  key.work_order = ctx->work_order;
   return key;
 }
 
@@ -1397,6 +1412,13 @@ csp_status csp_autotune(csp_ctx *ctx, const csp_solve_params *params, const floa
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return st;
+}
+
+csp_status csp_set_work_order(csp_ctx *ctx, int order) {
+  if (!ctx) return fail(nullptr, CSP_ERR_INVALID, "ctx is NULL");
+  if (order < 0 || order > 1) return fail(ctx, CSP_ERR_INVALID, "unknown work order");
+  ctx->work_order = order;
+  return CSP_OK;
 }
 
 csp_status csp_set_wait_test(csp_ctx *ctx, int on) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <algorithm>
 #include <cuda_bf16.h>
 #include <stdint.h>
 
@@ -134,6 +135,7 @@ struct csp_ctx {
   bool prof = false;
   int restricted_variant = 8;  // restricted-OMP kernel variant (see launch_omp_restricted)
   int aggregate_path = 0;      // 0 automatic, 1 two-pass (synthesis scratch), 2 fused shared-memory tiles
+  int work_order = 0;          // 0 patch order on static grids; 1 sorted by budget, restricted levels on a work queue
   int top_form = 0;            // full-dictionary level: 0 automatic, 1 per-iteration kernels, 2 fused kernel,
                                // 3 Gram form (P0 GEMM + Gram-Schmidt iteration over every atom)
   bool wait_test = false;      // test hook: the tensor-core proxy loads no atom tiles (its waits expire)
@@ -150,7 +152,7 @@ struct csp_ctx {
     float *coef;     // csp_reconstruct: the output image
     int8_t *keff;
     uint64_t version;
-    int restricted_variant, top_form, wait_test, pipeline, aggregate_path;
+    int restricted_variant, top_form, wait_test, pipeline, aggregate_path, work_order;
   };
   struct GraphSlot {
     GraphKey key{};
@@ -295,7 +297,7 @@ bool launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const
                                 int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
                                 const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
                                 int8_t *k_eff, int64_t *stats, const float *gram, int T, const float *D0, int N0,
-                                float *Xh, cudaStream_t s);
+                                float *Xh, cudaStream_t s, unsigned long long *queue = nullptr);
 // Gram-Schmidt form with the candidates' state in registers (G = 4, 8 or 16
 // lanes per patch); false (nothing launched) when M > 16 G (G = 4) or 8 G,
 // Kb > 8 or cap > 8 G.
@@ -328,7 +330,12 @@ bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
                            const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, bool cpos,
-                           cudaStream_t s, const float *D0 = nullptr, int N0 = 0, float *Xh = nullptr);
+                           cudaStream_t s, const float *D0 = nullptr, int N0 = 0, float *Xh = nullptr,
+                           unsigned long long *queue = nullptr);
+// Work order: ids[0..n) = the patches 0..n-1 sorted by budget K[b] (int8,
+// 0..CSP_MAX_K), largest first; `counts` is scratch of 2 x (CSP_MAX_K + 1) ints.
+// Patches of equal budget keep no particular order.
+void launch_sort_by_budget(const int8_t *K, int64_t n, int32_t *ids, int *counts, cudaStream_t s);
 // Per-pixel coded exposure, restricted level l: rows of the effective
 // dictionary for the candidates f(Omega_up) of every patch only, in candidate
 // order ([B][cap][M], row c of patch b = a_{cs_c} for that patch's codes) and

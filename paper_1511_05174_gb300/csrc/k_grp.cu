@@ -444,7 +444,7 @@ __device__ int gram_setup(bool valid, int s, int64_t b, int kup, const int32_t *
   return nc;
 }
 
-template <int G, int NCH>
+template <int G, int NCH, bool PERSIST>
 __global__ void __launch_bounds__(WV_WARPS * 32, 5)
 omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                            const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
@@ -452,11 +452,14 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
                            int cap, const int32_t *__restrict__ omega_up, int ldo_up,
                            const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                            int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
-                           int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
+                           int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T,
+    unsigned long long *__restrict__ queue) {
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
-  const int64_t wbase = ((int64_t)blockIdx.x * WV_WARPS + wib) * NG;
+  // one group of NG patches starting at wbase; a static grid runs it once per
+  // warp, the persistent form pulls the next group from the work queue
+  auto body = [&](const int64_t wbase) {
   if (wbase >= n) return;  // whole warp
   const int64_t wi = wbase + g;
   const bool valid = wi < n;
@@ -663,6 +666,19 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
       alpha[b * ldo + j] = (j < k) ? S.W[j] : 0.f;
     }
   }
+  };
+  if (!PERSIST) {
+    body(((int64_t)blockIdx.x * WV_WARPS + wib) * NG);
+    return;
+  }
+  for (;;) {  // each warp takes the next NG patches with one atomic add; nothing waits
+    unsigned long long w = 0ull;
+    if (lane == 0) w = atomicAdd(queue, (unsigned long long)NG);
+    w = __shfl_sync(kFull, w, 0);
+    if ((int64_t)w >= n) break;
+    body((int64_t)w);
+    __syncwarp();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -687,7 +703,7 @@ __host__ __device__ __forceinline__ int qr_group_bytes(int Kb, int cap) {
   return (bytes + 127) / 128 * 128 + 16;  // groups start on different bank offsets
 }
 
-template <int G, int NCH>
+template <int G, int NCH, bool PERSIST>
 __global__ void __launch_bounds__(WV_WARPS * 32, 5)
 omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                          const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
@@ -695,11 +711,14 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
                          int cap, const int32_t *__restrict__ omega_up, int ldo_up,
                          const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                          int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
-                         int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T) {
+                         int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T,
+    unsigned long long *__restrict__ queue) {
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
-  const int64_t wbase = ((int64_t)blockIdx.x * WV_WARPS + wib) * NG;
+  // one group of NG patches starting at wbase; a static grid runs it once per
+  // warp, the persistent form pulls the next group from the work queue
+  auto body = [&](const int64_t wbase) {
   if (wbase >= n) return;  // whole warp
   const int64_t wi = wbase + g;
   const bool valid = wi < n;
@@ -895,6 +914,19 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
       omega[b * ldo + j] = (j < k) ? S.om[j] : -1;
       alpha[b * ldo + j] = (j < k) ? S.W[j] : 0.f;
     }
+  }
+  };
+  if (!PERSIST) {
+    body(((int64_t)blockIdx.x * WV_WARPS + wib) * NG);
+    return;
+  }
+  for (;;) {  // each warp takes the next NG patches with one atomic add; nothing waits
+    unsigned long long w = 0ull;
+    if (lane == 0) w = atomicAdd(queue, (unsigned long long)NG);
+    w = __shfl_sync(kFull, w, 0);
+    if ((int64_t)w >= n) break;
+    body((int64_t)w);
+    __syncwarp();
   }
 }
 
@@ -1536,7 +1568,7 @@ bool launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const
                                 int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
                                 const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
                                 int8_t *k_eff, int64_t *stats, const float *gram, int T, const float *D0, int N0,
-                                float *Xh, cudaStream_t s) {
+                                float *Xh, cudaStream_t s, unsigned long long *queue) {
   const bool qr8 = qr && Kb <= 8;  // Q_C stored by candidate
   const bool synth = qr8 && Xh && D0 && N0 > 0 && N0 % 4 == 0;
   if (n == 0) return synth;
@@ -1554,11 +1586,22 @@ bool launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const
                                                         k_eff, stats, gram, T, D0, N0, synth ? Xh : nullptr);
       return;
     }
-    auto kern = qr ? omp_restricted_qr_kernel<GG, NCH> : omp_restricted_gram_kernel<GG, NCH>;
+    auto kern = queue ? (qr ? omp_restricted_qr_kernel<GG, NCH, true> : omp_restricted_gram_kernel<GG, NCH, true>)
+                      : (qr ? omp_restricted_qr_kernel<GG, NCH, false> : omp_restricted_gram_kernel<GG, NCH, false>);
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    kern<<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up,
-                                                      ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats,
-                                                      gram, T);
+    unsigned grid = blocks(n, per_cta);
+    if (queue) {  // persistent: as many CTAs as fit at once, fed by the work queue
+      int per_sm = 0, dev = 0;
+      cudaGetDevice(&dev);
+      int sms = 1;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WV_WARPS * 32, sm) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+      grid = std::min<unsigned>(grid, (unsigned)(per_sm * sms));
+      cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s);
+    }
+    kern<<<grid, WV_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up,
+                                         keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T, queue);
   });
   return synth;
 }

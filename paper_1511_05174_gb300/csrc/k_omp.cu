@@ -839,6 +839,49 @@ bool dispatch_group_wide(int M, F &&f) {
   return true;
 }
 
+// ---- work order: counting sort of the patches by budget, largest first ----
+__global__ void budget_hist_kernel(const int8_t *__restrict__ K, int64_t n, int *__restrict__ hist) {
+  __shared__ int h[CSP_MAX_K + 1];
+  for (int i = threadIdx.x; i <= CSP_MAX_K; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    int k = K[b];
+    k = k < 0 ? 0 : (k > CSP_MAX_K ? CSP_MAX_K : k);
+    atomicAdd(&h[k], 1);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= CSP_MAX_K; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// cursor[k] = number of patches with a larger budget (the start of bucket k)
+__global__ void budget_scan_kernel(int *__restrict__ hist, int *__restrict__ cursor) {
+  if (threadIdx.x != 0) return;
+  int acc = 0;
+  for (int k = CSP_MAX_K; k >= 0; --k) {
+    cursor[k] = acc;
+    acc += hist[k];
+  }
+}
+
+__global__ void budget_scatter_kernel(const int8_t *__restrict__ K, int64_t n, int *__restrict__ cursor,
+                                      int32_t *__restrict__ ids) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    int k = K[b];
+    k = k < 0 ? 0 : (k > CSP_MAX_K ? CSP_MAX_K : k);
+    ids[atomicAdd(&cursor[k], 1)] = (int32_t)b;
+  }
+}
+
+void launch_sort_by_budget(const int8_t *K, int64_t n, int32_t *ids, int *counts, cudaStream_t s) {
+  if (n == 0) return;
+  cudaMemsetAsync(counts, 0, sizeof(int) * 2 * (CSP_MAX_K + 1), s);
+  const unsigned g = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
+  budget_hist_kernel<<<g, 256, 0, s>>>(K, n, counts);
+  budget_scan_kernel<<<1, 32, 0, s>>>(counts, counts + CSP_MAX_K + 1);
+  budget_scatter_kernel<<<g, 256, 0, s>>>(K, n, counts + CSP_MAX_K + 1, ids);
+}
+
 void launch_p0_gemm(const float *Y, int M, const float *A, int T, const int32_t *ids, int64_t n, float *P0,
                     cudaStream_t s) {
   if (n == 0) return;
@@ -852,7 +895,7 @@ bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
                            const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, bool cpos,
-                           cudaStream_t s, const float *D0, int N0, float *Xh) {
+                           cudaStream_t s, const float *D0, int N0, float *Xh, unsigned long long *queue) {
   if (n == 0) return false;
   if (variant >= 2 && (!gram || a_pstride || cpos)) variant = 0;  // the Gram variants need the level's shared Gram matrix
   if (variant >= 8) {  // 8, 9, 10: Gram-Schmidt form with register-resident candidates, 8 / 16 / 4 lanes per patch
@@ -867,7 +910,7 @@ bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
   if (variant >= 2)  // 2-4: Gram proxy p0 - G alpha; 5-7: Gram-Schmidt form; narrow to wide lane groups
     return launch_omp_restricted_gram((variant - 2) % 3, variant >= 5, Y, M, A, inv_norm, ids, n, child_off,
                                       child_idx, cap, omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo,
-                                      k_eff, stats, gram, T, D0, N0, Xh, s);
+                                      k_eff, stats, gram, T, D0, N0, Xh, s, queue);
   if (variant == 0) {
     const int G = group_size(M);
     const int per_cta = GRP_WARPS * (32 / G);

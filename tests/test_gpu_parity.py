@@ -703,3 +703,31 @@ def test_gram_form_of_the_coarse_level(key, links, prec):
         torch.cuda.synchronize()
         assert np.array_equal(img.cpu().numpy(), ref)
     ctx.set_graph_mode(False)
+
+
+@pytest.mark.parametrize("variant", [2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("links", ["paper", "model"])
+def test_work_order_sorted_queue_equals_static(links, variant):
+    """Per-patch budgets K in [8, 20] (light field): with the work order (patches
+    sorted by budget, restricted levels on persistent warps fed by a work queue)
+    every patch's result equals the static grid's bit for bit, and both meet
+    the oracle; also recorded in a CUDA graph and replayed."""
+    from paper_1511_05174_gb300.context import Context
+    w = _workload("lightfield", links=links)
+    K, K_patch, Kmax = budgets(w, "cross_scale")
+    assert K_patch is not None
+    ctx = Context(0)
+    ctx.load_workload(w)
+    ctx.set_kernel_variant(variant)
+    Y = ctx.extract(torch.from_numpy(np.ascontiguousarray(w.meas)).cuda())
+    ref = [t.cpu().numpy() for t in ctx.solve(Y, "cross_scale", "fp32", K=K, K_patch=K_patch, Kmax=Kmax)]
+    ctx.set_work_order(1)
+    ctx.set_graph_mode(True)
+    for _ in range(3):
+        got = [t.cpu().numpy() for t in ctx.solve(Y, "cross_scale", "fp32", K=K, K_patch=K_patch, Kmax=Kmax)]
+        for a, b in zip(ref, got):
+            assert np.array_equal(a, b)
+    ctx.set_graph_mode(False)
+    o, a, k, _ = oracle.cross_scale_omp(w)
+    rate, worst, bad = compare(w.dicts[0], got[0], got[1], got[2].astype(np.int64), o, a, k)
+    assert rate >= MATCH and worst <= REL_TOL, bad[:10]
