@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-only", action="store_true", help="run the serving measurement alone (no headline)")
     ap.add_argument("--variant", type=int, default=None,
                     help="pin the restricted-solver variant (0-9) instead of autotuning (profiling runs)")
     ap.add_argument("--sweep-q", default=None,
@@ -409,7 +410,7 @@ def accuracy(w, results, oracle_codes, sample):
 # our arm
 # ----------------------------------------------------------------------------
 SERVING_RATES = {"cross_scale": (5, 10, 20, 30, 50, 100, 200), "plain": (1, 2, 5, 10)}  # offered jobs/s
-SERVING_JOBS = {"cross_scale": 32, "plain": 12}  # jobs per offered rate
+SERVING_JOBS = {"cross_scale": 48, "plain": 12}  # jobs per offered rate
 
 
 def serving_pool(kinds=("denoise", "bayer", "video"), per_kind=4, seed=0, lo=128, hi=2048, links="model"):
@@ -528,11 +529,24 @@ def serving_bench(args, device, pool, mode, jobs_per_rate):
                                                     + i["copy_out_ms"]) / max(i["batch_jobs"], 1) for i in infos])
                                            / len(infos)),
             }
+            by_kind = {}
+            for kind in sorted({k for k, _ in pool}):
+                sel = [inf for inf, i in zip(infos, order) if pool[i][0] == kind]
+                if not sel:
+                    continue
+                by_kind[kind] = {
+                    "jobs": len(sel),
+                    "latency_ms_median": float(np.median([1e3 * (i["t_done"] - i["t_submit"]) for i in sel])),
+                    "solve_ms_median": float(np.median([i["solve_ms"] for i in sel])),
+                    "copy_in_ms_median": float(np.median([i["copy_in_ms"] for i in sel])),
+                    "admit_to_gpu_done_ms_median": float(np.median([1e3 * (i["t_gpu_done"] - i["t_admit"])
+                                                                    for i in sel])),
+                    "mean_batch_jobs": float(np.mean([i["batch_jobs"] for i in sel]))}
             rates.append({"offered_jobs_per_s": rate, "jobs": len(infos), "value": patches / span, "unit": UNIT,
                           "jobs_per_s": len(infos) / span, "latency_ms_p50": float(np.percentile(lat, 50)),
                           "latency_ms_p99": float(np.percentile(lat, 99)),
                           "mean_batch_jobs": float(np.mean([i["batch_jobs"] for i in infos])),
-                          "stages_median": stages})
+                          "stages_median": stages, "by_kind": by_kind})
         return rates
     finally:
         srv.close()
@@ -777,6 +791,18 @@ def main():
         return
     if args.uneven:
         uneven_bench(args)
+        return
+    if args.serving_only:
+        import torch
+        pool = serving_pool(links=args.links)
+        out = {"pool": [{"kind": k, "side": int(w.geometry.H), "patches": int(w.n_patches)} for k, w in pool]}
+        for mode in ("cross_scale", "plain"):
+            alone = standalone_job_ms(0, pool, mode, args.precision)
+            fit = [t for t in alone if t is not None]
+            out[mode] = {"rates": serving_bench(args, 0, pool, mode, SERVING_JOBS[mode]),
+                         "standalone_device_ms": [None if t is None else round(t, 3) for t in alone],
+                         "standalone_jobs_per_s": len(fit) / (sum(fit) / 1e3) if fit else None}
+        print(json.dumps(out))
         return
 
     import torch

@@ -501,6 +501,9 @@ csp_status csp_server_add_model(csp_server *srv, const csp_model_desc *d, int *m
     csp_destroy(m.ctx);
     return st;
   };
+  // no two-stream pipeline inside a batch: the slots' streams overlap batches,
+  // and the model context's second stream would be shared by every slot
+  m.ctx->pipeline = false;
   csp_geometry g = d->geom;
   g.H = g.W = g.P;  // a one-patch template: the image extent is per job
   csp_status st = csp_set_geometry(m.ctx, &g);
