@@ -414,10 +414,11 @@ csp_status csp_job_release(csp_server *srv, uint64_t job_id);
  * the times; then, with that variant,
  * times the two forms of the full-dictionary level (csp_set_top_level_form)
  * where the fused form applies and keeps the faster.  Synchronises `stream`. */
-#define CSP_TUNE_VARIANTS 11 /* 0: L2-cooperative, 1: shared-memory staged, 2-4: Gram-matrix proxy, 5-7: Gram-Schmidt
-                                form, each narrow to wide; 8-9: Gram-Schmidt form with the candidates' state in
-                                registers, 8, 16 and 4 lanes per patch (8-10; budgets <= 8, at most 8 candidates a
-                                lane; else as 6) */
+#define CSP_TUNE_VARIANTS 14 /* 0: L2-cooperative, 1: shared-memory staged, 2-4: Gram-matrix proxy, 5-7: Gram-Schmidt
+                                form, each narrow to wide; 8-10: Gram-Schmidt form with the candidates' state in
+                                registers, 8, 16 and 4 lanes per patch (budgets <= 8, at most 8 candidates a
+                                lane; else as 6); 11-13: as 8-10 with each patch's Gram block G[C][C] staged in
+                                shared memory (at most 32 candidates, 16 with 16 lanes; else as 6) */
 typedef struct csp_tune_result {
     int restricted_variant;            /* chosen variant index                      */
     double ms[CSP_TUNE_VARIANTS];      /* solve time per variant (ms)               */

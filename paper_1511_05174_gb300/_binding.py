@@ -25,7 +25,7 @@ SENSE = {"identity": 0, "bayer_rggb": 1, "coded_exposure": 2, "coded_aperture": 
 MODE = {"plain": 0, "cross_scale": 1}
 PREC = {"fp32": 0, "bf16": 1}
 
-TUNE_VARIANTS = 11  # CSP_TUNE_VARIANTS
+TUNE_VARIANTS = 14  # CSP_TUNE_VARIANTS
 STATUS_NAMES = {0: "CSP_OK", -1: "CSP_ERR_INVALID", -2: "CSP_ERR_OOM", -3: "CSP_ERR_NOT_READY",
                 -4: "CSP_ERR_CUDA", -5: "CSP_ERR_TIMEOUT", -6: "CSP_ERR_UNSUPPORTED"}
 

@@ -483,7 +483,7 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
       }
       run(ctx, KK_FUSED, s, B, [&] {
         fused_done = launch_omp_fused_tc(Yl[top], L.M, Aph, Iph, Bph, Gph, nph, phased ? ps.phase_start : nullptr, L.Mp,
-                                         L.T, phased ? ps.phase_ids : nullptr, B, prm->K_patch[top], prm->K[top],
+                                         L.T, phased ? ps.phase_ids : order, B, prm->K_patch[top], prm->K[top],
                                          Kb[top], lv_om[top], lv_al[top], ldo[top], lv_ke[top], W.stats_dev,
                                          (unsigned long long *)(W.stats_dev + 4), s);
       });
@@ -531,7 +531,7 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
     st.k_eff = lv_ke[top];
     const int64_t a_ps = pp ? (int64_t)L.T * L.M : 0, inv_ps = pp ? (int64_t)L.T : 0;
     run(ctx, KK_INIT, s, B, [&] {
-      launch_omp_init(Yl[top], B, L.M, (bf16 && !pp) ? L.Mp : 0, phased ? ps.phase_ids : nullptr, st, s);
+      launch_omp_init(Yl[top], B, L.M, (bf16 && !pp) ? L.Mp : 0, phased ? ps.phase_ids : order, st, s);
     });
     bool maps_ok = true;
     for (int it = 0; it < Kb[top]; ++it) {
@@ -587,7 +587,7 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
             ids_of(ph), n_of(ph), L.child_off, L.child_idx, cap, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1],
             prm->K_patch[l], prm->K[l], Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], W.stats_dev, L.G[ph], L.T,
             L.per_patch ? (int64_t)cap * L.M : 0, L.per_patch ? (int64_t)cap : 0, L.per_patch, s,
-            l == 0 ? ctx->lv[0].D : nullptr, ctx->lv[0].N, l == 0 ? Xh : nullptr);
+            l == 0 ? ctx->lv[0].D : nullptr, ctx->lv[0].N, l == 0 ? Xh : nullptr, queue);
         if (l == 0) synth_all = synth_all && sy;
       });
   }

@@ -302,13 +302,14 @@ bool launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const
 // lanes per patch); false (nothing launched) when M > 16 G (G = 4) or 8 G,
 // Kb > 8 or cap > 8 G.
 // With Xh (and D0, N0) it also writes x_hat_p = D0_Omega alpha_p; *synthesized
-// tells whether it did.
+// tells whether it did.  stage_gram: each patch's Gram block G[C][C] is gathered
+// into shared memory at set-up (cap <= 32; false when it does not fit).
 bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, const float *inv_norm,
                                const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx,
                                int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
                                const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
                                int8_t *k_eff, int64_t *stats, const float *gram, int T, const float *D0, int N0,
-                               float *Xh, bool *synthesized, cudaStream_t s);
+                               float *Xh, bool *synthesized, cudaStream_t s, bool stage_gram = false);
 // Gram matrix A A^T ([T][T] FP32) of an effective dictionary.
 void launch_gram(const float *A, int T, int M, float *Gm, cudaStream_t s);
 // variant 0: rows from L2 every pass (cooperative groups); 1: rows staged in shared memory;

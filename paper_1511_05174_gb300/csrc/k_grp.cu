@@ -1270,12 +1270,14 @@ omp_restricted_qr8_kernel(const float *__restrict__ Y, int M, const float *__res
 // M <= 4 G NCH (NCH float4 chunks of y per lane for p0 = A_C^T y).
 // Per-group shared memory: GrpSmem | p0[cap] | parents' child ranges [2 x CSP_MAX_K].
 // ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ int reg_group_bytes(int Kb, int cap) {
-  const int bytes = grp_smem_bytes(Kb, cap) + up16(4 * cap) + 8 * CSP_MAX_K;
+__host__ __device__ __forceinline__ int reg_group_bytes(int Kb, int cap, bool gs = false) {
+  const int bytes = grp_smem_bytes(Kb, cap) + up16(4 * cap) + 8 * CSP_MAX_K + (gs ? up16(4 * cap * cap) : 0);
   return (bytes + 127) / 128 * 128 + 16;
 }
 
-template <int G, int CPL, int NCH>
+// GS: the patch's Gram block G[C][C] is gathered into shared memory once, after
+// the candidates are listed, so that no iteration waits on a load of G[q][C].
+template <int G, int CPL, int NCH, bool GS = false>
 __global__ void __launch_bounds__(WV_WARPS * 32, CPL >= 6 ? 3 : 4)  // 6-8 candidates a lane: up to 168 registers
 omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                           const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
@@ -1294,11 +1296,12 @@ omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__res
   if (wbase >= n) return;  // whole warp
   const int64_t wi = wbase + g;
   const bool valid = wi < n;
-  char *gbase = smem_raw + (size_t)(wib * NG + g) * reg_group_bytes(Kb, cap);
+  char *gbase = smem_raw + (size_t)(wib * NG + g) * reg_group_bytes(Kb, cap, GS);
   const GrpSmem S = carve(gbase, Kb, cap);
   float *p0 = reinterpret_cast<float *>(gbase + grp_smem_bytes(Kb, cap));
   int *pstart = reinterpret_cast<int *>(gbase + grp_smem_bytes(Kb, cap) + up16(4 * cap));
   int *pbeg = pstart + CSP_MAX_K;
+  float *Gcc = reinterpret_cast<float *>(gbase + grp_smem_bytes(Kb, cap) + up16(4 * cap) + 8 * CSP_MAX_K);
   const int nv = M >> 2;
   const int64_t b = valid ? (ids ? __ldg(ids + wi) : wi) : 0;
   int Kpb = valid ? (Kp ? (int)Kp[b] : Kuni) : 0;
@@ -1325,6 +1328,24 @@ omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__res
                             stats, M, A, yv, p0);
   }
   const float ysq = gsum<G>(dotc<NCH>(yv, yv));
+  if (GS) {  // Gram block of the candidates: Gcc[i * cap + j] = G[C_i][C_j], all loads in flight first
+    constexpr int GB = 8;
+    const int ncw = __reduce_max_sync(kFull, nc);
+    for (int e0 = 0; e0 < ncw * ncw; e0 += GB * G) {
+      float v[GB];
+#pragma unroll
+      for (int t = 0; t < GB; ++t) {
+        const int e = e0 + s + t * G, i = e / ncw, j = e - i * ncw;
+        v[t] = (e < ncw * ncw && i < nc && j < nc) ? __ldg(gram + (int64_t)S.cs[i] * T + S.cs[j]) : 0.f;
+      }
+#pragma unroll
+      for (int t = 0; t < GB; ++t) {
+        const int e = e0 + s + t * G, i = e / ncw, j = e - i * ncw;
+        if (e < ncw * ncw && i < nc && j < nc) Gcc[i * cap + j] = v[t];
+      }
+    }
+    __syncwarp();
+  }
   // this lane's candidates into registers (u < ucnt: a bound uniform over the warp, <= CPL)
   const int ucnt = __reduce_max_sync(kFull, (nc + G - 1) / G);
   int cs[CPL];
@@ -1366,13 +1387,15 @@ omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__res
     if (act && !best) act = false;  // candidate set exhausted
     const int q = act ? key_idx(best) : 0;
     const bool f32 = act && !(fl & 2);
-    // G[q][C] (row q: G is symmetric) and G[q][q], issued first
     float gpre[CPL];
+    float aa = 0.f;
+    if (!GS) {  // G[q][C] (row q: G is symmetric) and G[q][q], issued first
 #pragma unroll
-    for (int u = 0; u < CPL; ++u)
-      gpre[u] = (u < ucnt && f32 && cs[u] >= 0) ? __ldg(gram + (int64_t)q * T + cs[u]) : 0.f;
-    const float aa = f32 ? __ldg(gram + (int64_t)q * T + q) : 0.f;
-    // the owner of q: no longer eligible; publishes its row of Q_C and its correlation
+      for (int u = 0; u < CPL; ++u)
+        gpre[u] = (u < ucnt && f32 && cs[u] >= 0) ? __ldg(gram + (int64_t)q * T + cs[u]) : 0.f;
+      aa = f32 ? __ldg(gram + (int64_t)q * T + q) : 0.f;
+    }
+    // the owner of q: no longer eligible; publishes its row of Q_C, its correlation and its slot
 #pragma unroll
     for (int u = 0; u < CPL; ++u)
       if (u < ucnt && act && cs[u] == q) {
@@ -1380,8 +1403,15 @@ omp_restricted_reg_kernel(const float *__restrict__ Y, int M, const float *__res
 #pragma unroll
         for (int j = 0; j < it; ++j) S.V[j] = Q[u][j];
         S.V[Kb] = cc[u];  // V holds Kb + 1 entries; w uses the first it < Kb
+        S.misc[1] = s + G * u;
       }
     __syncwarp();
+    if (GS) {  // the row of the winner's slot in the staged Gram block
+      const float *gr = Gcc + (f32 ? S.misc[1] : 0) * cap;
+#pragma unroll
+      for (int u = 0; u < CPL; ++u) gpre[u] = (u < ucnt && f32 && cs[u] >= 0) ? gr[s + G * u] : 0.f;
+      aa = f32 ? gr[S.misc[1]] : 0.f;
+    }
     // new row of L: w_j = <u_j, a_q>, j < it; z_it = c_q / L_kk (c_q = <a_q, y> - w.z)
     float w[KM];
     float ww0 = 0.f, ww1 = 0.f;
@@ -1611,7 +1641,7 @@ bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, con
                                int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
                                const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
                                int8_t *k_eff, int64_t *stats, const float *gram, int T, const float *D0, int N0,
-                               float *Xh, bool *synthesized, cudaStream_t s) {
+                               float *Xh, bool *synthesized, cudaStream_t s, bool stage_gram) {
   *synthesized = false;
   if (M % 4 || Kb > 8 || (G != 4 && G != 8 && G != 16)) return false;
   // float4 chunks of y per lane: 4 lanes take M <= 64 (4 chunks), 8 and 16 lanes two chunks
@@ -1621,17 +1651,20 @@ bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, con
   const int CPL = per_g <= 2 ? 2 : (per_g <= 3 ? 3 : (per_g <= 4 ? 4 : (per_g <= 6 ? 6 : (per_g <= 8 ? 8 : 0))));
   if (!CPL) return false;
   const bool synth = Xh && D0 && N0 > 0 && N0 % 4 == 0;
+  // the staged Gram block needs cap^2 floats per patch: up to 32 candidates
+  const bool gs = stage_gram && cap <= 32;
+  if (stage_gram && !gs) return false;
   *synthesized = synth;
   if (n == 0) return true;
   const int per_cta = WV_WARPS * (32 / G);
-  const size_t sm = (size_t)reg_group_bytes(Kb, cap) * per_cta;
+  const size_t sm = (size_t)reg_group_bytes(Kb, cap, gs) * per_cta;
   auto go = [&](auto kern) {
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     kern<<<blocks(n, per_cta), WV_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up,
                                                       ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats,
                                                       gram, T, D0, N0, synth ? Xh : nullptr, nullptr);
   };
-  switch (G * 100 + CPL) {
+  switch ((gs ? 10000 : 0) + G * 100 + CPL) {
     case 402: go(omp_restricted_reg_kernel<4, 2, 4>); break;
     case 403: go(omp_restricted_reg_kernel<4, 3, 4>); break;
     case 404: go(omp_restricted_reg_kernel<4, 4, 4>); break;
@@ -1647,6 +1680,15 @@ bool launch_omp_restricted_reg(int G, const float *Y, int M, const float *A, con
     case 1604: go(omp_restricted_reg_kernel<16, 4, 2>); break;
     case 1606: go(omp_restricted_reg_kernel<16, 6, 2>); break;
     case 1608: go(omp_restricted_reg_kernel<16, 8, 2>); break;
+    case 10402: go(omp_restricted_reg_kernel<4, 2, 4, true>); break;
+    case 10403: go(omp_restricted_reg_kernel<4, 3, 4, true>); break;
+    case 10404: go(omp_restricted_reg_kernel<4, 4, 4, true>); break;
+    case 10406: go(omp_restricted_reg_kernel<4, 6, 4, true>); break;
+    case 10408: go(omp_restricted_reg_kernel<4, 8, 4, true>); break;
+    case 10802: go(omp_restricted_reg_kernel<8, 2, 2, true>); break;
+    case 10803: go(omp_restricted_reg_kernel<8, 3, 2, true>); break;
+    case 10804: go(omp_restricted_reg_kernel<8, 4, 2, true>); break;
+    case 11602: go(omp_restricted_reg_kernel<16, 2, 2, true>); break;
     default: return false;
   }
   return true;

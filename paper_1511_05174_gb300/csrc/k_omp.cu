@@ -898,12 +898,13 @@ bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            cudaStream_t s, const float *D0, int N0, float *Xh, unsigned long long *queue) {
   if (n == 0) return false;
   if (variant >= 2 && (!gram || a_pstride || cpos)) variant = 0;  // the Gram variants need the level's shared Gram matrix
-  if (variant >= 8) {  // 8, 9, 10: Gram-Schmidt form with register-resident candidates, 8 / 16 / 4 lanes per patch
+  if (variant >= 8) {  // 8-10 (11-13 with the Gram block staged): register-resident candidates, 8 / 16 / 4 lanes
     bool sy = false;
-    if (launch_omp_restricted_reg(variant == 8 ? 8 : (variant == 9 ? 16 : 4), Y, M, A, inv_norm, ids, n, child_off,
+    const int vv = variant >= 11 ? variant - 3 : variant;
+    if (launch_omp_restricted_reg(vv == 8 ? 8 : (vv == 9 ? 16 : 4), Y, M, A, inv_norm, ids, n, child_off,
                                   child_idx, cap,
                                   omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T,
-                                  D0, N0, Xh, &sy, s))
+                                  D0, N0, Xh, &sy, s, variant >= 11))
       return sy;
     variant = 6;  // shape outside the register form: the shared-memory Gram-Schmidt form
   }

@@ -117,14 +117,21 @@ def test_psnr_matches_oracle(mode, prec):
     assert abs(oracle.psnr(w.truth, g["img"]) - oracle.psnr(w.truth, img_o)) <= 0.05
 
 
-def test_bayer_all_four_phases():
-    """Stride 1 puts patch origins on every RGGB phase."""
-    w = synthetic.make_workload("bayer", H=24, W=24)
+@pytest.mark.parametrize("prec,form", [("fp32", 0), ("bf16", 1), ("bf16", 2), ("bf16", 3)])
+def test_bayer_all_four_phases(prec, form):
+    """Stride 1 puts patch origins on every RGGB phase: the patches of a phase
+    are a non-identity subset of the grid, so every full-dictionary form runs
+    with a permuted patch order (and the BF16 proxy with its sorted-position
+    residual tile)."""
+    from paper_1511_05174_gb300.context import Context
+    w = synthetic.make_workload("bayer", H=40, W=40)
     w.geometry.stride = 1
     B = w.n_patches
     w.K_levels = [np.full(B, int(k[0]), np.int32) for k in w.K_levels]
     for mode, fn in (("plain", oracle.plain_omp), ("cross_scale", oracle.cross_scale_omp)):
-        g = run_gpu(w, mode)
+        ctx = Context(0)
+        ctx.set_top_level_form(form)
+        g = run_gpu(w, mode, prec, ctx=ctx)
         o, a, k, _ = fn(w)
         rate, worst, bad = compare(w.dicts[0], g["sup"], g["coef"], g["keff"], o, a, k)
         assert rate >= MATCH and worst <= REL_TOL, (mode, bad[:10])
@@ -378,7 +385,7 @@ def test_exactly_dependent_atom_ends_the_patch():
     assert rate == 1.0 and worst <= REL_TOL
 
 
-@pytest.mark.parametrize("variant", list(range(11)))
+@pytest.mark.parametrize("variant", list(range(14)))
 def test_restricted_dependent_candidate_falls_back_to_fp64(variant):
     """Fine step of Algorithm 2 whose candidate set holds an exactly dependent
     atom (a_2 = a_0 + a_1, integer atoms): every restricted variant rejects it
@@ -408,7 +415,7 @@ def test_restricted_dependent_candidate_falls_back_to_fp64(variant):
     assert rate == 1.0 and worst <= REL_TOL
 
 
-@pytest.mark.parametrize("variant", list(range(11)))
+@pytest.mark.parametrize("variant", list(range(14)))
 @pytest.mark.parametrize("key", ["bayer", "lightfield", "denoise_ragged", "video", "rgb_identity"])
 def test_restricted_variants_agree_with_oracle(key, variant):
     """Every restricted-solver variant the autotuner may pick meets the parity
@@ -506,7 +513,7 @@ def test_autotune_picks_a_variant():
     Y = ctx.extract(torch.from_numpy(w.meas).cuda())
     K, K_patch, Kmax = budgets(w, "cross_scale")
     r = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
-    assert r["restricted_variant"] in range(11) and all(t > 0 for t in r["ms"])
+    assert r["restricted_variant"] in range(14) and all(t > 0 for t in r["ms"])
     assert r["ms"][r["restricted_variant"]] == min(r["ms"])
     # the BF16 Bayer coarse level (T = 256, M = 64, K = 4) has all three full-dictionary forms
     r2 = ctx.autotune(Y, "cross_scale", "bf16", K=K, K_patch=K_patch, Kmax=Kmax)
@@ -636,12 +643,13 @@ def test_cross_scale_other_link_sizes(Q, prec):
     assert abs(oracle.psnr(w.truth, g["img"]) - oracle.psnr(w.truth, img_o)) <= 0.05
 
 
-@pytest.mark.parametrize("variant", [8, 9, 10])
+@pytest.mark.parametrize("variant", [8, 9, 10, 11, 12, 13])
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("key", ["bayer", "denoise", "denoise_ragged", "cs_dense", "rgb_identity"])
 def test_register_variants_on_model_reading(key, prec, variant):
-    """Restricted variants 8, 9, 10 (candidates' state in registers, 8, 16 and
-    4 lanes per patch, iteration loop unrolled) on the model reading, where
+    """Restricted variants 8-13 (candidates' state in registers, 8, 16 and 4
+    lanes per patch, iteration loop unrolled; 11-13 with each patch's Gram
+    block staged in shared memory) on the model reading, where
     every candidate set fits them (|f(Omega)| = 4 K_low, K <= 8): supports and
     coefficients against the oracle, and csp_reconstruct (which then synthesizes
     x_hat in the same kernel) equal to extract + solve + aggregate, bit for bit."""
@@ -705,13 +713,16 @@ def test_gram_form_of_the_coarse_level(key, links, prec):
     ctx.set_graph_mode(False)
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("variant", [2, 3, 4, 5, 6, 7, 8])
 @pytest.mark.parametrize("links", ["paper", "model"])
-def test_work_order_sorted_queue_equals_static(links, variant):
+def test_work_order_sorted_queue_equals_static(links, variant, prec):
     """Per-patch budgets K in [8, 20] (light field): with the work order (patches
     sorted by budget, restricted levels on persistent warps fed by a work queue)
     every patch's result equals the static grid's bit for bit, and both meet
-    the oracle; also recorded in a CUDA graph and replayed."""
+    the oracle; also recorded in a CUDA graph and replayed.  BF16 runs the
+    full-dictionary level's tensor-core proxy on the sorted-position residual
+    tile."""
     from paper_1511_05174_gb300.context import Context
     w = _workload("lightfield", links=links)
     K, K_patch, Kmax = budgets(w, "cross_scale")
@@ -720,11 +731,11 @@ def test_work_order_sorted_queue_equals_static(links, variant):
     ctx.load_workload(w)
     ctx.set_kernel_variant(variant)
     Y = ctx.extract(torch.from_numpy(np.ascontiguousarray(w.meas)).cuda())
-    ref = [t.cpu().numpy() for t in ctx.solve(Y, "cross_scale", "fp32", K=K, K_patch=K_patch, Kmax=Kmax)]
+    ref = [t.cpu().numpy() for t in ctx.solve(Y, "cross_scale", prec, K=K, K_patch=K_patch, Kmax=Kmax)]
     ctx.set_work_order(1)
     ctx.set_graph_mode(True)
     for _ in range(3):
-        got = [t.cpu().numpy() for t in ctx.solve(Y, "cross_scale", "fp32", K=K, K_patch=K_patch, Kmax=Kmax)]
+        got = [t.cpu().numpy() for t in ctx.solve(Y, "cross_scale", prec, K=K, K_patch=K_patch, Kmax=Kmax)]
         for a, b in zip(ref, got):
             assert np.array_equal(a, b)
     ctx.set_graph_mode(False)
