@@ -193,8 +193,11 @@ void launch_norms(const float *A, int T, int M, int Mp, float *inv_norm, __nv_bf
 void launch_effective_dict_dense(const GeomDev &g, const float *phi, int level, const float *D, int T, int N,
                                  float *A, int M, cudaStream_t s);
 void launch_patch_codes(const GeomDev &g, const uint8_t *codes, int64_t B, uint8_t *pc, cudaStream_t s);
-void launch_effective_dict_pp(const GeomDev &g, const uint8_t *pc, int level, const float *D, int T, int N,
-                              float *A, int64_t B, cudaStream_t s);
+// Per-patch effective dictionaries of level l and their inverse row norms in
+// one pass per patch (-1 for rows at or below 1e-12 of the largest norm); the
+// norms of launch_inv_row_norms.  scratch: 4 bytes.
+void launch_effective_dict_pp_norms(const GeomDev &g, const uint8_t *pc, int level, const float *D, int T, int N,
+                                    float *A, float *inv, unsigned int *scratch, int64_t B, cudaStream_t s);
 void launch_inv_row_norms(const float *A, int64_t rows, int M, float *inv, unsigned int *scratch, cudaStream_t s);
 void launch_bf16_rows(const float *D, int T, int N, int Np, __nv_bfloat16 *out, cudaStream_t s);
 void launch_lift(const GeomDev &g, const uint8_t *pc, int level, const float *R, int64_t B, float *Z,
@@ -317,10 +320,11 @@ void launch_gram(const float *A, int T, int M, float *Gm, cudaStream_t s);
 // P0 = Y A^T (FP32) for the patches ids[0..n): P0[b][a] = <a_a, y_b>.
 void launch_p0_gemm(const float *Y, int M, const float *A, int T, const int32_t *ids, int64_t n, float *P0,
                     cudaStream_t s);
-// Full-dictionary level in the Gram form (form 3): P0 = Y A^T once, then the
-// register-resident Gram-Schmidt iteration with every atom a candidate (32
-// lanes per patch; T <= 256, Kb <= 8, M <= 256); needs the level's Gram matrix
-// and P0 scratch of n x T floats.  False when the shape does not fit.
+// Full-dictionary level in the Gram form (form 3), after launch_p0_gemm has
+// written P0 = Y A^T: the register-resident Gram-Schmidt iteration with every
+// atom a candidate (32 lanes per patch; T <= 256, Kb <= 8, M <= 256); needs the
+// level's Gram matrix; P0 holds T floats per patch id.  False when the shape
+// does not fit.
 bool full_gram_supported(int M, int T, int Kb);
 bool launch_omp_full_gram(const float *Y, int M, const float *A, const float *inv_norm, const int32_t *ids, int64_t n,
                           const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo, int8_t *k_eff,

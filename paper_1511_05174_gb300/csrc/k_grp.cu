@@ -1701,7 +1701,6 @@ bool launch_omp_full_gram(const float *Y, int M, const float *A, const float *in
                           int64_t *stats, const float *gram, int T, float *P0, cudaStream_t s) {
   if (!full_gram_supported(M, T, Kb) || !gram || !P0) return false;
   if (n == 0) return true;
-  launch_p0_gemm(Y, M, A, T, ids, n, P0, s);
   constexpr int G = 32;
   const int per_g = (T + G - 1) / G;
   const int CPL = per_g <= 2 ? 2 : (per_g <= 4 ? 4 : 8);

@@ -130,28 +130,52 @@ __global__ void patch_codes_kernel(GeomDev g, const uint8_t *__restrict__ codes,
   pc[e] = codes[((int64_t)t * g.H + oy + py) * g.W + ox + px];
 }
 
-// Per-patch effective dictionaries for per-pixel coded exposure (plane grid
-// 1 x F frames): A_p[i][m] = (Phi_p U_l d_i)[m] = sum_t pc_p[t][py][px]
-// d_i[level index of (t, py, px)], one thread per (patch, atom, pixel).  Only
-// the patch-local code blocks are read, so patches of different images can
-// share one launch.
-__global__ void effective_dict_pp_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l,
-                                         const float *__restrict__ D, int T, int N, float *__restrict__ A,
-                                         int64_t B) {
+
+// Per-pixel coded exposure: the full per-patch effective dictionary of level l,
+// a_i = Phi_p U_l d_i, and its row norms, one CTA per patch: the patch's code block is
+// turned once into a table of level-element offsets (off[t][m] = the element of
+// frame t, pixel m at level l, -1 where the code is 0) in shared memory; then a
+// warp per atom row writes a_i[m] = sum_t d_i[off[t][m]] (frames in order) for
+// m = lane, lane + 32, ... and the row's norm in the order
+// of row_norms_kernel (per-lane FMA chain over its elements, then the xor tree),
+// with the running maximum of the norms in *mx.  The index arithmetic is done
+// once per patch instead of once per element and frame.
+__global__ void __launch_bounds__(256)
+effective_dict_pp_rows_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const float *__restrict__ D, int T,
+                              int N, float *__restrict__ A, float *__restrict__ nrm, unsigned int *mx, int64_t B) {
+  extern __shared__ int pp_off[];  // [F][M]
+  const int64_t b = blockIdx.x;
+  if (b >= B) return;
   const int M = g.P * g.P, F = g.Lx;
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= B * T * M) return;
-  const int m = (int)(e % M);
-  const int64_t bi = e / M;
-  const int i = (int)(bi % T);
-  const int64_t b = bi / T;
-  const int py = m / g.P, px = m - py * g.P;
-  const float *d = D + (int64_t)i * N;
-  const uint8_t *c = pc + b * (int64_t)F * M;
-  float v = 0.f;
-  for (int t = 0; t < F; ++t)
-    if (c[t * M + m]) v += d[level_index(g, l, 0, t, py, px)];
-  A[e] = v;
+  const uint8_t *cb = pc + b * (int64_t)F * M;
+  for (int e = threadIdx.x; e < F * M; e += blockDim.x) {
+    const int t = e / M, m = e - t * M, py = m / g.P, px = m - py * g.P;
+    pp_off[e] = cb[e] ? level_index(g, l, 0, t, py, px) : -1;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned int wmax = 0u;
+  for (int i = warp; i < T; i += nw) {
+    const float *d = D + (int64_t)i * N;
+    float *row = A + (b * T + i) * (int64_t)M;
+    float sq = 0.f;
+    for (int m = lane; m < M; m += 32) {
+      float v = 0.f;
+      for (int t = 0; t < F; ++t) {
+        const int o = pp_off[t * M + m];
+        if (o >= 0) v += __ldg(d + o);
+      }
+      row[m] = v;
+      sq = fmaf(v, v, sq);
+    }
+    for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) {
+      const float r = sqrtf(sq);
+      nrm[b * T + i] = r;
+      wmax = max(wmax, __float_as_uint(r));
+    }
+  }
+  if (lane == 0 && wmax) atomicMax(mx, wmax);
 }
 
 // Candidate rows of per-pixel coded exposure at a restricted level: one CTA
@@ -160,7 +184,7 @@ __global__ void effective_dict_pp_kernel(GeomDev g, const uint8_t *__restrict__ 
 // cap) and tabulates, per (frame t, pixel m), the offset of the level element
 // d[level index of (t, m)] when the patch's code there is 1 (-1 otherwise);
 // then a warp per candidate c writes a_c[m] = sum_t pc_p[t][m] d_c[...] -- the
-// arithmetic and order of effective_dict_pp_kernel -- and 1/||a_c|| (-1 for a
+// arithmetic and order of effective_dict_pp_rows_kernel -- and 1/||a_c|| (-1 for a
 // zero row), the norm reduced as in row_norms_kernel.
 __global__ void __launch_bounds__(256)
 pp_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const float *__restrict__ D, int N, int M,
@@ -656,11 +680,15 @@ void launch_patch_codes(const GeomDev &g, const uint8_t *codes, int64_t B, uint8
   patch_codes_kernel<<<blocks(n, 256), 256, 0, s>>>(g, codes, B, pc);
 }
 
-void launch_effective_dict_pp(const GeomDev &g, const uint8_t *pc, int level, const float *D, int T, int N,
-                              float *A, int64_t B, cudaStream_t s) {
-  const int64_t n = B * T * (int64_t)(g.P * g.P);
-  if (n == 0) return;
-  effective_dict_pp_kernel<<<blocks(n, 256), 256, 0, s>>>(g, pc, level, D, T, N, A, B);
+void launch_effective_dict_pp_norms(const GeomDev &g, const uint8_t *pc, int level, const float *D, int T, int N,
+                                    float *A, float *inv, unsigned int *scratch, int64_t B, cudaStream_t s) {
+  if (B * T == 0) return;
+  const size_t sm = sizeof(int) * (size_t)g.Lx * g.P * g.P;
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(effective_dict_pp_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaMemsetAsync(scratch, 0, sizeof(unsigned int), s);
+  effective_dict_pp_rows_kernel<<<(unsigned)B, 256, sm, s>>>(g, pc, level, D, T, N, A, inv, scratch, B);
+  inv_norms_kernel<<<blocks(B * T, 256), 256, 0, s>>>(inv, B * T, scratch);
 }
 
 void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
