@@ -243,6 +243,130 @@ pp_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const flo
   }
 }
 
+// Per-pixel coded exposure in time-bin form.  At level l the frames t of one
+// time bin k (t / fx = k, fx the level's frame factor) all send pixel m to the
+// same level element k S + s(m) (S = the level's pixels per frame, s(m) the
+// element of m's pixel), so a row of the effective dictionary is
+//   a_i[m] = sum_k c_k(m) d_i[k S + s(m)],   k = 0 .. F / fx - 1 in order,
+// with c_k(m) the number of frames of bin k whose code at m is 1: the operator
+// Phi_p U_l of the patch applied to d_i, the frame sums of one bin taken as
+// one multiply-add.  A lane keeps s and c_k of its pixels m = lane + 32 j in
+// registers for the whole patch, so the loop over rows does one load and one
+// FMA per (pixel, bin) and no index arithmetic.
+template <int NB, int MPL>
+struct PpBins {
+  int s[MPL];
+  float c[MPL][NB];
+};
+
+template <int NB, int MPL>
+__device__ __forceinline__ void pp_bins_setup(const GeomDev &g, int l, const uint8_t *__restrict__ cb, int M, int nb,
+                                              int lane, PpBins<NB, MPL> &t) {
+  const int fx = g.f[l][1], sy = g.f[l][2], sx = g.f[l][3], Pxl = g.P / sx;
+#pragma unroll
+  for (int j = 0; j < MPL; ++j) {
+    const int m = lane + 32 * j;
+    const bool ok = m < M;
+    const int py = ok ? m / g.P : 0, px = ok ? m - py * g.P : 0;
+    t.s[j] = (py / sy) * Pxl + px / sx;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      int n = 0;
+      if (ok && k < nb)
+        for (int u = 0; u < fx; ++u) n += cb[(k * fx + u) * M + m] ? 1 : 0;
+      t.c[j][k] = (float)n;
+    }
+  }
+}
+
+// Writes row[m] = a[m] for the lane's pixels and returns the lane's partial
+// sum of squares (FMA chain in pixel order, as row_norms_kernel).
+template <int NB, int MPL>
+__device__ __forceinline__ float pp_bins_row(const float *__restrict__ d, int S, int nb, int M, int lane,
+                                             const PpBins<NB, MPL> &t, float *__restrict__ row) {
+  float sq = 0.f;
+#pragma unroll
+  for (int j = 0; j < MPL; ++j) {
+    float x[NB];
+#pragma unroll
+    for (int k = 0; k < NB; ++k) x[k] = k < nb ? __ldg(d + k * S + t.s[j]) : 0.f;
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < NB; ++k) v = fmaf(t.c[j][k], x[k], v);
+    const int m = lane + 32 * j;
+    if (m < M) {
+      row[m] = v;
+      sq = fmaf(v, v, sq);
+    }
+  }
+  return sq;
+}
+
+// The full per-patch effective dictionary of level l and its row norms in
+// time-bin form: one CTA per patch, a warp per atom row, two rows in flight.
+template <int NB, int MPL>
+__global__ void __launch_bounds__(256)
+pp_bins_rows_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const float *__restrict__ D, int T, int N,
+                    int S, int nb, float *__restrict__ A, float *__restrict__ nrm, unsigned int *mx, int64_t B) {
+  const int64_t b = blockIdx.x;
+  if (b >= B) return;
+  const int M = g.P * g.P;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  PpBins<NB, MPL> t;
+  pp_bins_setup<NB, MPL>(g, l, pc + b * (int64_t)g.Lx * M, M, nb, lane, t);
+  unsigned int wmax = 0u;
+#pragma unroll 2
+  for (int i = warp; i < T; i += nw) {
+    float sq = pp_bins_row<NB, MPL>(D + (int64_t)i * N, S, nb, M, lane, t, A + (b * T + i) * (int64_t)M);
+    for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) {
+      const float r = sqrtf(sq);
+      nrm[b * T + i] = r;
+      wmax = max(wmax, __float_as_uint(r));
+    }
+  }
+  if (lane == 0 && wmax) atomicMax(mx, wmax);
+}
+
+// Candidate rows of a restricted level in time-bin form (the candidate list
+// and the outputs of pp_candidates_kernel, the row arithmetic of
+// pp_bins_rows_kernel).
+template <int NB, int MPL>
+__global__ void __launch_bounds__(256)
+pp_bins_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const float *__restrict__ D, int N,
+                          int M, int S, int nb, const int32_t *__restrict__ omega_up, int ldo_up,
+                          const int8_t *__restrict__ keff_up, const int32_t *__restrict__ child_off,
+                          const int32_t *__restrict__ child_idx, int cap, int64_t B, float *__restrict__ Ac,
+                          float *__restrict__ invc) {
+  extern __shared__ int cs[];  // [cap] candidate atoms
+  __shared__ int s_nc;
+  const int64_t b = blockIdx.x;
+  if (b >= B) return;
+  if (threadIdx.x == 0) {
+    const int kup = keff_up[b];
+    int nc = 0;
+    for (int j = 0; j < kup && nc < cap; ++j) {
+      const int p = omega_up[b * ldo_up + j];
+      for (int i = child_off[p]; i < child_off[p + 1] && nc < cap; ++i) cs[nc++] = child_idx[i];
+    }
+    s_nc = nc;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  PpBins<NB, MPL> t;
+  pp_bins_setup<NB, MPL>(g, l, pc + b * (int64_t)g.Lx * M, M, nb, lane, t);
+  __syncthreads();
+  const int nc = s_nc;
+#pragma unroll 2
+  for (int c = warp; c < nc; c += nw) {
+    float sq = pp_bins_row<NB, MPL>(D + (int64_t)cs[c] * N, S, nb, M, lane, t, Ac + (b * cap + c) * (int64_t)M);
+    for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0) {
+      const float nrm = sqrtf(sq);
+      invc[b * cap + c] = nrm > 0.f ? 1.f / nrm : -1.f;
+    }
+  }
+}
+
 // Dense Phi (the same for every patch): a_i = Phi U_l d_i, one thread per
 // (atom i, measurement m), the level-0 patch index n = (plane, py, px) mapped
 // to its level-l element by U_l (nearest replication).
@@ -680,21 +804,104 @@ void launch_patch_codes(const GeomDev &g, const uint8_t *codes, int64_t B, uint8
   patch_codes_kernel<<<blocks(n, 256), 256, 0, s>>>(g, codes, B, pc);
 }
 
+// Time-bin form of a per-pixel level: bins per pixel, level pixels per frame,
+// and the template instance (bins rounded up to 1, 2, 4, 8 or 16; pixels per
+// lane 1, 2 or 4), or false when the shape needs the general kernels.
+struct PpShape {
+  int nb, S, NB, MPL;
+};
+
+bool pp_shape(const GeomDev &g, int level, int M, PpShape &p) {
+  p.nb = g.Lx / g.f[level][1];
+  p.S = (g.P / g.f[level][2]) * (g.P / g.f[level][3]);
+  p.NB = p.nb <= 1 ? 1 : p.nb <= 2 ? 2 : p.nb <= 4 ? 4 : p.nb <= 8 ? 8 : p.nb <= 16 ? 16 : 0;
+  p.MPL = M <= 32 ? 1 : M <= 64 ? 2 : M <= 128 ? 4 : 0;
+  return p.NB && p.MPL && g.Ly == 1;
+}
+
+template <int NB, int MPL>
+void launch_pp_bins_rows(const GeomDev &g, const uint8_t *pc, int level, const float *D, int T, int N,
+                         const PpShape &p, float *A, float *nrm, unsigned int *mx, int64_t B, cudaStream_t s) {
+  pp_bins_rows_kernel<NB, MPL><<<(unsigned)B, 256, 0, s>>>(g, pc, level, D, T, N, p.S, p.nb, A, nrm, mx, B);
+}
+
+template <int NB>
+void launch_pp_bins_rows_m(const GeomDev &g, const uint8_t *pc, int level, const float *D, int T, int N,
+                           const PpShape &p, float *A, float *nrm, unsigned int *mx, int64_t B, cudaStream_t s) {
+  if (p.MPL == 1) launch_pp_bins_rows<NB, 1>(g, pc, level, D, T, N, p, A, nrm, mx, B, s);
+  else if (p.MPL == 2) launch_pp_bins_rows<NB, 2>(g, pc, level, D, T, N, p, A, nrm, mx, B, s);
+  else launch_pp_bins_rows<NB, 4>(g, pc, level, D, T, N, p, A, nrm, mx, B, s);
+}
+
 void launch_effective_dict_pp_norms(const GeomDev &g, const uint8_t *pc, int level, const float *D, int T, int N,
                                     float *A, float *inv, unsigned int *scratch, int64_t B, cudaStream_t s) {
   if (B * T == 0) return;
-  const size_t sm = sizeof(int) * (size_t)g.Lx * g.P * g.P;
-  if (sm > 48 * 1024)
-    cudaFuncSetAttribute(effective_dict_pp_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaMemsetAsync(scratch, 0, sizeof(unsigned int), s);
-  effective_dict_pp_rows_kernel<<<(unsigned)B, 256, sm, s>>>(g, pc, level, D, T, N, A, inv, scratch, B);
+  PpShape p;
+  if (pp_shape(g, level, g.P * g.P, p)) {
+    switch (p.NB) {
+      case 1: launch_pp_bins_rows_m<1>(g, pc, level, D, T, N, p, A, inv, scratch, B, s); break;
+      case 2: launch_pp_bins_rows_m<2>(g, pc, level, D, T, N, p, A, inv, scratch, B, s); break;
+      case 4: launch_pp_bins_rows_m<4>(g, pc, level, D, T, N, p, A, inv, scratch, B, s); break;
+      case 8: launch_pp_bins_rows_m<8>(g, pc, level, D, T, N, p, A, inv, scratch, B, s); break;
+      default: launch_pp_bins_rows_m<16>(g, pc, level, D, T, N, p, A, inv, scratch, B, s); break;
+    }
+  } else {
+    const size_t sm = sizeof(int) * (size_t)g.Lx * g.P * g.P;
+    if (sm > 48 * 1024)
+      cudaFuncSetAttribute(effective_dict_pp_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    effective_dict_pp_rows_kernel<<<(unsigned)B, 256, sm, s>>>(g, pc, level, D, T, N, A, inv, scratch, B);
+  }
   inv_norms_kernel<<<blocks(B * T, 256), 256, 0, s>>>(inv, B * T, scratch);
+}
+
+template <int NB, int MPL>
+void launch_pp_bins_cand(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
+                         const PpShape &p, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
+                         const int32_t *child_off, const int32_t *child_idx, int cap, int64_t B, float *Ac,
+                         float *invc, cudaStream_t s) {
+  const size_t sm = sizeof(int) * (size_t)cap;
+  if (sm > 48 * 1024)
+    cudaFuncSetAttribute(pp_bins_candidates_kernel<NB, MPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  pp_bins_candidates_kernel<NB, MPL><<<(unsigned)B, 256, sm, s>>>(g, pc, level, D, N, M, p.S, p.nb, omega_up, ldo_up,
+                                                                  keff_up, child_off, child_idx, cap, B, Ac, invc);
+}
+
+template <int NB>
+void launch_pp_bins_cand_m(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
+                           const PpShape &p, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
+                           const int32_t *child_off, const int32_t *child_idx, int cap, int64_t B, float *Ac,
+                           float *invc, cudaStream_t s) {
+  if (p.MPL == 1)
+    launch_pp_bins_cand<NB, 1>(g, pc, level, D, N, M, p, omega_up, ldo_up, keff_up, child_off, child_idx, cap, B, Ac,
+                               invc, s);
+  else if (p.MPL == 2)
+    launch_pp_bins_cand<NB, 2>(g, pc, level, D, N, M, p, omega_up, ldo_up, keff_up, child_off, child_idx, cap, B, Ac,
+                               invc, s);
+  else
+    launch_pp_bins_cand<NB, 4>(g, pc, level, D, N, M, p, omega_up, ldo_up, keff_up, child_off, child_idx, cap, B, Ac,
+                               invc, s);
 }
 
 void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
                           const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int32_t *child_off,
                           const int32_t *child_idx, int cap, int64_t B, float *Ac, float *invc, cudaStream_t s) {
   if (B == 0) return;
+  PpShape p;
+  if (pp_shape(g, level, M, p)) {
+#define CSP_PP_CAND(nb_)                                                                                         \
+  launch_pp_bins_cand_m<nb_>(g, pc, level, D, N, M, p, omega_up, ldo_up, keff_up, child_off, child_idx, cap, B, Ac, \
+                             invc, s)
+    switch (p.NB) {
+      case 1: CSP_PP_CAND(1); break;
+      case 2: CSP_PP_CAND(2); break;
+      case 4: CSP_PP_CAND(4); break;
+      case 8: CSP_PP_CAND(8); break;
+      default: CSP_PP_CAND(16); break;
+    }
+#undef CSP_PP_CAND
+    return;
+  }
   const size_t sm = sizeof(int) * ((size_t)g.Lx * M + cap);
   if (sm > 48 * 1024) cudaFuncSetAttribute(pp_candidates_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   pp_candidates_kernel<<<(unsigned)B, 256, sm, s>>>(g, pc, level, D, N, M, omega_up, ldo_up, keff_up, child_off,
