@@ -278,19 +278,20 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
     float *Wp = reinterpret_cast<float *>(gb + lay.W) + p * lay.vs;
     auto arow = [&](int i) -> const float * { return a_fp + i * FZ_AS; };
     int fb_misc = 0;
-    // y and r: this thread's chunks, zero padded
+    // r (= y at the start): this thread's chunks, zero padded.  y itself is not
+    // kept: the residual is updated by the change of alpha, and z_k comes from
+    // the FP32 correlation <a_q, r> of the chosen atom
     const float *yrow = Y + b * M;
-    float4 yv[FZ_NCH], rv[FZ_NCH];
+    float4 rv[FZ_NCH];
 #pragma unroll
     for (int t = 0; t < FZ_NCH; ++t) {
       const int m0 = 4 * (2 * t + h);
-      yv[t] = (valid && m0 < M) ? __ldg(reinterpret_cast<const float4 *>(yrow + m0)) : make_float4(0.f, 0.f, 0.f, 0.f);
-      rv[t] = yv[t];
+      rv[t] = (valid && m0 < M) ? __ldg(reinterpret_cast<const float4 *>(yrow + m0)) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     float ysq = 0.f;
 #pragma unroll
     for (int t = 0; t < FZ_NCH; ++t)
-      ysq = fmaf(yv[t].x, yv[t].x, fmaf(yv[t].y, yv[t].y, fmaf(yv[t].z, yv[t].z, fmaf(yv[t].w, yv[t].w, ysq))));
+      ysq = fmaf(rv[t].x, rv[t].x, fmaf(rv[t].y, rv[t].y, fmaf(rv[t].z, rv[t].z, fmaf(rv[t].w, rv[t].w, ysq))));
     ysq = pair_sum(ysq);
     float rsq = ysq;
     int k = 0;
@@ -365,6 +366,7 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
       // ---- update: a thread pair per patch ----
       act = act && k < Kpb && !(rsq <= kEpsR32 * ysq);
       unsigned long long best = 0ull;
+      float cq = 0.f;  // <a_q, r> of the chosen atom
       const uint4 ck = cand4[p];
       const uint32_t keys[4] = {ck.x, ck.y, ck.z, ck.w};
       int ci[4];
@@ -382,7 +384,10 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
         const float inv = ci[c] >= 0 ? s_inv[ci[c]] : -1.f;
         if (act && ci[c] >= 0 && inv > 0.f && !taken) {
           const unsigned long long kk = pack_key(fabsf(sc[c]) * inv, ci[c]);
-          best = kk > best ? kk : best;
+          if (kk > best) {
+            best = kk;
+            cq = sc[c];
+          }
         }
       }
       if (act && !best) {  // no eligible candidate
@@ -399,7 +404,6 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
         for (int j = 0; j < FZ_KMAX; ++j) vr[j] = (f32 && h == 0 && j < k) ? __ldg(Gm + (int64_t)q * T + omp[j]) : 0.f;
       }
       const float aa = s_nrm[q];
-      const float bq = pair_sum(half_dot(aq, h, yv));
       if (Gm) {
 #pragma unroll
         for (int j = 0; j < FZ_KMAX; ++j)
@@ -419,7 +423,7 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
       bool ok32 = false;
       if (f32 && h == 0) {
         float wv[FZ_KMAX];
-        float ww = 0.f, wz = 0.f;
+        float ww = 0.f;
 #pragma unroll
         for (int i = 0; i < FZ_KMAX; ++i) {
           wv[i] = 0.f;
@@ -429,14 +433,14 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
             for (int j = 0; j < i; ++j) sacc = fmaf(-Lp[ftri(i) + j], wv[j], sacc);
             wv[i] = sacc * Linv[i];
             ww = fmaf(wv[i], wv[i], ww);
-            wz = fmaf(wv[i], zp[i], wz);
           }
         }
         const float d = aa - ww;
         ok32 = aa > 0.f && d >= kTauPivot * aa;
         if (ok32) {
           const float lkk = sqrtf(d), il = 1.f / lkk;
-          const float zk = (bq - wz) * il;
+          // z_k = <u_k, y> = <a_q, r> / L_kk (r is orthogonal to the chosen atoms)
+          const float zk = cq * il;
 #pragma unroll
           for (int j = 0; j < FZ_KMAX; ++j)
             if (j < k) Lp[ftri(k) + j] = wv[j];
@@ -457,9 +461,14 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
               al[i] = sacc * (i == k ? il : Linv[i]);
             }
           }
+          // the residual moves by A_Omega (alpha' - alpha): the differences go to
+          // Vp (free once the Gram column is used)
 #pragma unroll
           for (int i = 0; i < FZ_KMAX; ++i)
-            if (i <= k) Wp[i] = al[i];
+            if (i <= k) {
+              Vp[i] = i < k ? al[i] - Wp[i] : al[i];
+              Wp[i] = al[i];
+            }
         } else {
           atomicAdd((unsigned long long *)&stats[0], 1ull);
         }
@@ -475,6 +484,8 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
         S.W = Wp;
         S.colp = cp;
         fb_misc = csp::grp::fp64_projection(M, yrow, S, k, aq) ? 1 : 0;
+        if (fb_misc)  // alpha from scratch: the residual is recomputed from y
+          for (int j = 0; j <= k; ++j) Vp[j] = Wp[j];
       }
       const bool app64 = __shfl_sync(0xffffffffu, fb_misc, lane & ~1) != 0 && go64;
       const bool appended = ok32 || app64;
@@ -491,17 +502,21 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
         if (h == 0 && k < Kpb) atomicAdd((unsigned long long *)&stats[1], 1ull);
       }
       __syncwarp();
-      // residue r = y - A_Omega alpha
+      // residue r = y - A_Omega alpha' = r - A_Omega (alpha' - alpha) with the
+      // differences in Vp (after the FP64 solve: y - A_Omega alpha')
       if (appended && h == 0) omp[k] = q;
       __syncwarp();
-      const int kr = __reduce_max_sync(0xffffffffu, appended ? k + 1 : 0);
-      if (appended) {
+      if (app64) {
 #pragma unroll
-        for (int t = 0; t < FZ_NCH; ++t) rv[t] = yv[t];
+        for (int t = 0; t < FZ_NCH; ++t) {
+          const int m0 = 4 * (2 * t + h);
+          rv[t] = m0 < M ? __ldg(reinterpret_cast<const float4 *>(yrow + m0)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
       }
+      const int kr = __reduce_max_sync(0xffffffffu, appended ? k + 1 : 0);
       for (int j = 0; j < kr; ++j) {
         if (appended && j <= k) {
-          const float aj = Wp[j];
+          const float aj = Vp[j];
           const float4 *c4 = reinterpret_cast<const float4 *>(arow(omp[j]));
 #pragma unroll
           for (int t = 0; t < FZ_NCH; ++t) {
