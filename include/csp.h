@@ -366,7 +366,8 @@ typedef struct csp_job_info {
     csp_status status;          /* CSP_OK, CSP_ERR_NOT_READY while queued/running, or error */
     /* Stage times of the job's batch (milliseconds; shared by the jobs of one batch):
      * enqueue_ms   host time the scheduler spent staging inputs and enqueueing the batch;
-     * copy_in_ms   device: host-to-device copies, patch extraction and code blocks;
+     * copy_in_ms   device: host-to-device copies (the measurements straight from the
+     *              caller's buffer), patch extraction and code blocks;
      * solve_ms     device: the solve (with per-patch operator builds for per-pixel Phi);
      * aggregate_ms device: synthesis and overlap-add of the batch's images;
      * copy_out_ms  device: device-to-host copies of the images;
@@ -411,9 +412,13 @@ csp_status csp_job_release(csp_server *srv, uint64_t job_id);
  * runs csp_solve once per variant on the given batch (same arguments as
  * csp_solve, outputs overwritten), then times three more runs with CUDA events
  * and takes the fastest, keeps the fastest variant for this context and reports
- * the times; then, with that variant,
- * times the two forms of the full-dictionary level (csp_set_top_level_form)
- * where the fused form applies and keeps the faster.  Synchronises `stream`. */
+ * the times; then, with that variant, times the forms of the full-dictionary
+ * level (csp_set_top_level_form) that apply and keeps the fastest.  A
+ * cross-scale batch of the context's own patch grid (B = the grid's patch
+ * count) is timed with the synthesis x_hat_p = D0 alpha_p of every patch into
+ * workspace scratch, as csp_reconstruct runs it (inside the finest restricted
+ * kernel for the variants that write it, else by the synthesis kernel), since
+ * the variants differ there too.  Synchronises `stream`. */
 #define CSP_TUNE_VARIANTS 14 /* 0: L2-cooperative, 1: shared-memory staged, 2-4: Gram-matrix proxy, 5-7: Gram-Schmidt
                                 form, each narrow to wide; 8-10: Gram-Schmidt form with the candidates' state in
                                 registers, 8, 16 and 4 lanes per patch (budgets <= 8, at most 8 candidates a

@@ -64,7 +64,7 @@ struct Slot {
   bool busy = false;
   std::vector<Job *> jobs;
   void *dev = nullptr;      // the batch's device memory (stream-ordered allocation)
-  uint8_t *host = nullptr;  // pinned staging of the batch's inputs and outputs
+  uint8_t *host = nullptr;  // pinned staging of the batch's codes, cover ranges, ids and images
   size_t host_cap = 0;
   size_t reserved = 0;
 };
@@ -184,14 +184,14 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
   const size_t o_inv = ce ? dv.take<float>((size_t)slice * m.ctx->lv[top].T) : 0;
   const size_t o_scr = dv.take<unsigned int>(4);
   const size_t o_ids = dv.take<int32_t>((size_t)Bt), h_ids = hs.take<int32_t>((size_t)Bt);
-  struct JobLayout { size_t d_meas, d_codes, d_img, d_cov, h_meas, h_codes, h_img, h_cov; };
+  struct JobLayout { size_t d_meas, d_codes, d_img, d_cov, h_codes, h_img, h_cov; };
   std::vector<JobLayout> jl(sl.jobs.size());
   for (size_t k = 0; k < sl.jobs.size(); ++k) {
     const Job *j = sl.jobs[k];
     const size_t cov = 2 * (size_t)(j->H + j->W);
     jl[k] = {dv.take<float>(j->meas_floats), dv.take<uint8_t>(j->codes.size()), dv.take<float>(j->img_floats),
-             dv.take<int32_t>(cov), hs.take<float>(j->meas_floats), hs.take<uint8_t>(j->codes.size()),
-             hs.take<float>(j->img_floats), hs.take<int32_t>(cov)};
+             dv.take<int32_t>(cov), hs.take<uint8_t>(j->codes.size()), hs.take<float>(j->img_floats),
+             hs.take<int32_t>(cov)};
   }
   cudaError_t e;
   if (sl.host_cap < hs.off) {
@@ -218,8 +218,10 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
   for (size_t k = 0; k < sl.jobs.size(); ++k) {
     Job *j = sl.jobs[k];
     const JobLayout &L = jl[k];
-    std::memcpy(hp(L.h_meas), j->meas_host, j->meas_floats * 4);
-    if ((e = cudaMemcpyAsync(dp(L.d_meas), hp(L.h_meas), j->meas_floats * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    // the measurements straight from the caller's buffer (it stays alive until
+    // the job is done): one driver-staged copy instead of a host copy into the
+    // pinned area followed by a device copy
+    if ((e = cudaMemcpyAsync(dp(L.d_meas), j->meas_host, j->meas_floats * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess)
       return e;
     launch_extract(j->gd, m.sense_kind, 0, (const float *)dp(L.d_meas), Y + j->off * m.M, j->B, m.M, s);
     if (ce) {
@@ -347,7 +349,10 @@ void scheduler(csp_server *srv) {
       if (q == cudaErrorNotReady) continue;
       if (q == cudaSuccess) {
         // images from the pinned staging area to the callers' buffers, without
-        // the lock (the slot stays busy and its jobs not done meanwhile)
+        // the lock (the slot stays busy and its jobs not done meanwhile).  A
+        // device-to-host copy straight into the caller's pageable buffer here
+        // was slower for small jobs in the mix: the scheduler thread waited in
+        // it while other batches ran.
         const double tg = now_s();
         batch_stage_times(sl);
         lk.unlock();
