@@ -178,6 +178,39 @@ effective_dict_pp_rows_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, 
   if (lane == 0 && wmax) atomicMax(mx, wmax);
 }
 
+// The candidate atoms f(Omega_up) of patch b in the order of the restricted
+// kernels (parents in support order, each parent's children in link order, at
+// most cap), listed by one warp: lane j takes parent j of each group of 32, and an
+// inclusive scan of the children counts gives each parent its first slot.
+// Returns the number listed (all lanes).
+__device__ __forceinline__ int list_candidates_warp(int64_t b, const int32_t *__restrict__ omega_up, int ldo_up,
+                                                    const int8_t *__restrict__ keff_up,
+                                                    const int32_t *__restrict__ child_off,
+                                                    const int32_t *__restrict__ child_idx, int cap, int *cs,
+                                                    int lane) {
+  const int kup = keff_up[b];
+  int base = 0;
+  for (int j0 = 0; j0 < kup && base < cap; j0 += 32) {
+    const int j = j0 + lane;
+    int lo = 0, cnt = 0;
+    if (j < kup) {
+      const int p = omega_up[b * ldo_up + j];
+      lo = child_off[p];
+      cnt = child_off[p + 1] - lo;
+    }
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    const int first = base + inc - cnt;
+    for (int i = 0; i < cnt && first + i < cap; ++i) cs[first + i] = child_idx[lo + i];
+    base += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  return base < cap ? base : cap;
+}
+
 // Candidate rows of per-pixel coded exposure at a restricted level: one CTA
 // per patch.  The CTA lists f(Omega_up) in the order of the restricted kernels
 // (parents in support order, each parent's children in link order, at most
@@ -203,14 +236,9 @@ pp_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const flo
     const int t = e / M, m = e - t * M, py = m / g.P, px = m - py * g.P;
     off[e] = cb[e] ? level_index(g, l, 0, t, py, px) : -1;
   }
-  if (threadIdx.x == 0) {
-    const int kup = keff_up[b];
-    int nc = 0;
-    for (int j = 0; j < kup && nc < cap; ++j) {
-      const int p = omega_up[b * ldo_up + j];
-      for (int i = child_off[p]; i < child_off[p + 1] && nc < cap; ++i) cs[nc++] = child_idx[i];
-    }
-    s_nc = nc;
+  if (threadIdx.x < 32) {
+    const int nc = list_candidates_warp(b, omega_up, ldo_up, keff_up, child_off, child_idx, cap, cs, threadIdx.x);
+    if (threadIdx.x == 0) s_nc = nc;
   }
   __syncthreads();
   const int nc = s_nc;
@@ -250,119 +278,169 @@ pp_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const flo
 //   a_i[m] = sum_k c_k(m) d_i[k S + s(m)],   k = 0 .. F / fx - 1 in order,
 // with c_k(m) the number of frames of bin k whose code at m is 1: the operator
 // Phi_p U_l of the patch applied to d_i, the frame sums of one bin taken as
-// one multiply-add.  A lane keeps s and c_k of its pixels m = lane + 32 j in
-// registers for the whole patch, so the loop over rows does one load and one
-// FMA per (pixel, bin) and no index arithmetic.
+// one multiply-add.  A lane keeps the element offsets and counts of its pixels
+// m = lane + 32 j in registers for the whole patch, so a row costs one load and
+// one FMA per (pixel, bin) and no index arithmetic.  Bins past the level's
+// count (the template rounds it up) and pixels past M get count 0 and a valid
+// offset (s(m), or 0), so the loads need no guard.
 template <int NB, int MPL>
 struct PpBins {
-  int s[MPL];
+  int off[MPL][NB];
   float c[MPL][NB];
 };
 
 template <int NB, int MPL>
-__device__ __forceinline__ void pp_bins_setup(const GeomDev &g, int l, const uint8_t *__restrict__ cb, int M, int nb,
-                                              int lane, PpBins<NB, MPL> &t) {
+__device__ __forceinline__ void pp_bins_setup(const GeomDev &g, int l, const uint8_t *__restrict__ cb, int M, int S,
+                                              int nb, int lane, PpBins<NB, MPL> &t) {
   const int fx = g.f[l][1], sy = g.f[l][2], sx = g.f[l][3], Pxl = g.P / sx;
 #pragma unroll
   for (int j = 0; j < MPL; ++j) {
     const int m = lane + 32 * j;
     const bool ok = m < M;
     const int py = ok ? m / g.P : 0, px = ok ? m - py * g.P : 0;
-    t.s[j] = (py / sy) * Pxl + px / sx;
+    const int sm = (py / sy) * Pxl + px / sx;
 #pragma unroll
     for (int k = 0; k < NB; ++k) {
       int n = 0;
       if (ok && k < nb)
         for (int u = 0; u < fx; ++u) n += cb[(k * fx + u) * M + m] ? 1 : 0;
+      t.off[j][k] = (k < nb ? k * S : 0) + sm;
       t.c[j][k] = (float)n;
     }
   }
 }
 
-// Writes row[m] = a[m] for the lane's pixels and returns the lane's partial
-// sum of squares (FMA chain in pixel order, as row_norms_kernel).
+// The lane's pixels of one row: v[j] = a[lane + 32 j].
 template <int NB, int MPL>
-__device__ __forceinline__ float pp_bins_row(const float *__restrict__ d, int S, int nb, int M, int lane,
-                                             const PpBins<NB, MPL> &t, float *__restrict__ row) {
-  float sq = 0.f;
+__device__ __forceinline__ void pp_bins_eval(const float *__restrict__ d, const PpBins<NB, MPL> &t,
+                                             float (&v)[MPL]) {
+  float x[MPL][NB];
+#pragma unroll
+  for (int j = 0; j < MPL; ++j)
+#pragma unroll
+    for (int k = 0; k < NB; ++k) x[j][k] = __ldg(d + t.off[j][k]);
 #pragma unroll
   for (int j = 0; j < MPL; ++j) {
-    float x[NB];
+    v[j] = 0.f;
 #pragma unroll
-    for (int k = 0; k < NB; ++k) x[k] = k < nb ? __ldg(d + k * S + t.s[j]) : 0.f;
-    float v = 0.f;
-#pragma unroll
-    for (int k = 0; k < NB; ++k) v = fmaf(t.c[j][k], x[k], v);
-    const int m = lane + 32 * j;
-    if (m < M) {
-      row[m] = v;
-      sq = fmaf(v, v, sq);
-    }
+    for (int k = 0; k < NB; ++k) v[j] = fmaf(t.c[j][k], x[j][k], v[j]);
   }
-  return sq;
 }
 
+// Warp sums of eight values at once: lane l ends with the sum over all lanes of
+// q[r], r = 4 (l >> 4 & 1) + 2 (l >> 3 & 1) + (l >> 2 & 1) -- three halving
+// exchanges and two plain ones, nine shuffles for eight sums.
+__device__ __forceinline__ float warp_sum8(const float (&q)[8], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+  float h4[4], h2[2];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const float send = b4 ? q[u] : q[u + 4], keep = b4 ? q[u + 4] : q[u];
+    h4[u] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const float send = b3 ? h4[u] : h4[u + 2], keep = b3 ? h4[u + 2] : h4[u];
+    h2[u] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float h = (b2 ? h2[1] : h2[0]) + __shfl_xor_sync(0xffffffffu, b2 ? h2[0] : h2[1], 4);
+  h += __shfl_xor_sync(0xffffffffu, h, 2);
+  h += __shfl_xor_sync(0xffffffffu, h, 1);
+  return h;
+}
+
+__device__ __forceinline__ int sum8_row(int lane) { return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1); }
+
 // The full per-patch effective dictionary of level l and its row norms in
-// time-bin form: one CTA per patch, a warp per atom row, two rows in flight.
+// time-bin form: one warp per patch (eight patches per CTA), rows taken in
+// groups of eight (r0 + u, u < 8), written, and their eight squared norms
+// reduced together.  A warp per patch, not a CTA: the per-patch set-up (the
+// bins of the lane's pixels) is done once and no barrier is needed.
 template <int NB, int MPL>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 pp_bins_rows_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const float *__restrict__ D, int T, int N,
                     int S, int nb, float *__restrict__ A, float *__restrict__ nrm, unsigned int *mx, int64_t B) {
-  const int64_t b = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (b >= B) return;
   const int M = g.P * g.P;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   PpBins<NB, MPL> t;
-  pp_bins_setup<NB, MPL>(g, l, pc + b * (int64_t)g.Lx * M, M, nb, lane, t);
+  pp_bins_setup<NB, MPL>(g, l, pc + b * (int64_t)g.Lx * M, M, S, nb, lane, t);
   unsigned int wmax = 0u;
-#pragma unroll 2
-  for (int i = warp; i < T; i += nw) {
-    float sq = pp_bins_row<NB, MPL>(D + (int64_t)i * N, S, nb, M, lane, t, A + (b * T + i) * (int64_t)M);
-    for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    if (lane == 0) {
-      const float r = sqrtf(sq);
+  float *Ab = A + b * (int64_t)T * M;
+  for (int r0 = 0; r0 < T; r0 += 8) {
+    float q[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int i = r0 + u;
+      q[u] = 0.f;
+      if (i < T) {
+        float v[MPL];
+        pp_bins_eval<NB, MPL>(D + (int64_t)i * N, t, v);
+        float *row = Ab + (int64_t)i * M;
+#pragma unroll
+        for (int j = 0; j < MPL; ++j) {
+          if (lane + 32 * j < M) row[lane + 32 * j] = v[j];
+          q[u] = fmaf(v[j], v[j], q[u]);
+        }
+      }
+    }
+    const float tot = warp_sum8(q, lane);
+    const int i = r0 + sum8_row(lane);
+    if ((lane & 3) == 0 && i < T) {
+      const float r = sqrtf(tot);
       nrm[b * T + i] = r;
       wmax = max(wmax, __float_as_uint(r));
     }
   }
+  // the largest norm: one global atomic per patch
+  wmax = __reduce_max_sync(0xffffffffu, wmax);
   if (lane == 0 && wmax) atomicMax(mx, wmax);
 }
 
 // Candidate rows of a restricted level in time-bin form (the candidate list
-// and the outputs of pp_candidates_kernel, the row arithmetic of
-// pp_bins_rows_kernel).
+// and the outputs of pp_candidates_kernel, the row arithmetic and grouping of
+// pp_bins_rows_kernel): one warp per patch, its candidate list in its own
+// slice of shared memory.
 template <int NB, int MPL>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 pp_bins_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const float *__restrict__ D, int N,
                           int M, int S, int nb, const int32_t *__restrict__ omega_up, int ldo_up,
                           const int8_t *__restrict__ keff_up, const int32_t *__restrict__ child_off,
                           const int32_t *__restrict__ child_idx, int cap, int64_t B, float *__restrict__ Ac,
                           float *__restrict__ invc) {
-  extern __shared__ int cs[];  // [cap] candidate atoms
-  __shared__ int s_nc;
-  const int64_t b = blockIdx.x;
+  extern __shared__ int cs_all[];  // [warps][cap] candidate atoms
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (b >= B) return;
-  if (threadIdx.x == 0) {
-    const int kup = keff_up[b];
-    int nc = 0;
-    for (int j = 0; j < kup && nc < cap; ++j) {
-      const int p = omega_up[b * ldo_up + j];
-      for (int i = child_off[p]; i < child_off[p + 1] && nc < cap; ++i) cs[nc++] = child_idx[i];
-    }
-    s_nc = nc;
-  }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int *cs = cs_all + warp * cap;
+  const int nc = list_candidates_warp(b, omega_up, ldo_up, keff_up, child_off, child_idx, cap, cs, lane);
   PpBins<NB, MPL> t;
-  pp_bins_setup<NB, MPL>(g, l, pc + b * (int64_t)g.Lx * M, M, nb, lane, t);
-  __syncthreads();
-  const int nc = s_nc;
-#pragma unroll 2
-  for (int c = warp; c < nc; c += nw) {
-    float sq = pp_bins_row<NB, MPL>(D + (int64_t)cs[c] * N, S, nb, M, lane, t, Ac + (b * cap + c) * (int64_t)M);
-    for (int o = 16; o; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-    if (lane == 0) {
-      const float nrm = sqrtf(sq);
-      invc[b * cap + c] = nrm > 0.f ? 1.f / nrm : -1.f;
+  pp_bins_setup<NB, MPL>(g, l, pc + b * (int64_t)g.Lx * M, M, S, nb, lane, t);
+  __syncwarp();
+  float *Ab = Ac + b * (int64_t)cap * M;
+  for (int r0 = 0; r0 < nc; r0 += 8) {
+    float q[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = r0 + u;
+      q[u] = 0.f;
+      if (c < nc) {
+        float v[MPL];
+        pp_bins_eval<NB, MPL>(D + (int64_t)cs[c] * N, t, v);
+        float *row = Ab + (int64_t)c * M;
+#pragma unroll
+        for (int j = 0; j < MPL; ++j) {
+          if (lane + 32 * j < M) row[lane + 32 * j] = v[j];
+          q[u] = fmaf(v[j], v[j], q[u]);
+        }
+      }
+    }
+    const float tot = warp_sum8(q, lane);
+    const int c = r0 + sum8_row(lane);
+    if ((lane & 3) == 0 && c < nc) {
+      const float r = sqrtf(tot);
+      invc[b * cap + c] = r > 0.f ? 1.f / r : -1.f;
     }
   }
 }
@@ -822,7 +900,8 @@ bool pp_shape(const GeomDev &g, int level, int M, PpShape &p) {
 template <int NB, int MPL>
 void launch_pp_bins_rows(const GeomDev &g, const uint8_t *pc, int level, const float *D, int T, int N,
                          const PpShape &p, float *A, float *nrm, unsigned int *mx, int64_t B, cudaStream_t s) {
-  pp_bins_rows_kernel<NB, MPL><<<(unsigned)B, 256, 0, s>>>(g, pc, level, D, T, N, p.S, p.nb, A, nrm, mx, B);
+  pp_bins_rows_kernel<NB, MPL><<<(unsigned)((B + 7) / 8), 256, 0, s>>>(g, pc, level, D, T, N, p.S, p.nb, A, nrm,
+                                                                        mx, B);
 }
 
 template <int NB>
@@ -860,11 +939,11 @@ void launch_pp_bins_cand(const GeomDev &g, const uint8_t *pc, int level, const f
                          const PpShape &p, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
                          const int32_t *child_off, const int32_t *child_idx, int cap, int64_t B, float *Ac,
                          float *invc, cudaStream_t s) {
-  const size_t sm = sizeof(int) * (size_t)cap;
+  const size_t sm = sizeof(int) * 8 * (size_t)cap;  // eight warps' candidate lists
   if (sm > 48 * 1024)
     cudaFuncSetAttribute(pp_bins_candidates_kernel<NB, MPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  pp_bins_candidates_kernel<NB, MPL><<<(unsigned)B, 256, sm, s>>>(g, pc, level, D, N, M, p.S, p.nb, omega_up, ldo_up,
-                                                                  keff_up, child_off, child_idx, cap, B, Ac, invc);
+  pp_bins_candidates_kernel<NB, MPL><<<(unsigned)((B + 7) / 8), 256, sm, s>>>(
+      g, pc, level, D, N, M, p.S, p.nb, omega_up, ldo_up, keff_up, child_off, child_idx, cap, B, Ac, invc);
 }
 
 template <int NB>
@@ -888,7 +967,7 @@ void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const 
                           const int32_t *child_idx, int cap, int64_t B, float *Ac, float *invc, cudaStream_t s) {
   if (B == 0) return;
   PpShape p;
-  if (pp_shape(g, level, M, p)) {
+  if (pp_shape(g, level, M, p) && (size_t)cap * 32 <= 200 * 1024) {  // eight lists of cap atoms in shared memory
 #define CSP_PP_CAND(nb_)                                                                                         \
   launch_pp_bins_cand_m<nb_>(g, pc, level, D, N, M, p, omega_up, ldo_up, keff_up, child_off, child_idx, cap, B, Ac, \
                              invc, s)
