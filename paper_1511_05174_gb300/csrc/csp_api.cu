@@ -160,7 +160,7 @@ enum Slot {
   WS_LV_OMEGA, WS_LV_ALPHA = WS_LV_OMEGA + CSP_MAX_LEVELS, WS_LV_KEFF = WS_LV_ALPHA + CSP_MAX_LEVELS,
   WS_LV_Y = WS_LV_KEFF + CSP_MAX_LEVELS,
   WS_XH = WS_LV_Y + CSP_MAX_LEVELS,
-  WS_SCRATCH, WS_LIFT, WS_LIFTBF, WS_PPC_A, WS_PPC_INV, WS_PART, WS_KEYS, WS_P0, WS_ORDER, WS_ORDER_CNT, WS_QUEUE,
+  WS_SCRATCH, WS_LIFT, WS_LIFTBF, WS_PPC_A, WS_PPC_INV, WS_PPC_G, WS_PART, WS_KEYS, WS_P0, WS_ORDER, WS_ORDER_CNT, WS_QUEUE,
   WS_KS_R, WS_KS_RN2, WS_KS_XN2, WS_KS_TAKEN, WS_KS_HIST, WS_KS_OFF, WS_KS_SEG, WS_KS_ERR, WS_KS_STATS,
   WS_COUNT
 };
@@ -573,14 +573,17 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
   for (int l = top - 1; l >= 0; --l) {
     const LevelData &L = ctx->lv[l];
     const int cap = std::max(1, L.max_children * Kb[l + 1]);
-    float *Ac = nullptr, *invc = nullptr;
+    float *Ac = nullptr, *invc = nullptr, *Gpp = nullptr;
     if (L.per_patch) {
-      // per-patch Phi: rows of this level's effective dictionary for each patch's candidates only
+      // per-patch Phi: rows of this level's effective dictionary for each patch's
+      // candidates only, with their Gram block for the Gram-Schmidt variants
       CSP_TRY(ws_get_t(ctx, W, WS_PPC_A, (size_t)B * cap * L.M, &Ac));
       CSP_TRY(ws_get_t(ctx, W, WS_PPC_INV, (size_t)B * cap, &invc));
+      if (ctx->restricted_variant >= 2) CSP_TRY(ws_get_t(ctx, W, WS_PPC_G, (size_t)B * cap * cap, &Gpp));
       run(ctx, KK_PREP, s, B, [&] {
-        launch_pp_candidates(ctx->gd, ps.pcodes, l, L.D, L.N, L.M, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1],
-                             L.child_off, L.child_idx, cap, B, Ac, invc, s);
+        if (!launch_pp_candidates(ctx->gd, ps.pcodes, l, L.D, L.N, L.M, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1],
+                                  L.child_off, L.child_idx, cap, B, Ac, invc, s, Gpp))
+          Gpp = nullptr;
       });
     }
     for (int ph = 0; ph < nph; ++ph)
@@ -590,7 +593,7 @@ csp_status solve_core(csp_ctx *ctx, const PatchSet &ps, Workspace &W, const csp_
             ids_of(ph), n_of(ph), L.child_off, L.child_idx, cap, lv_om[l + 1], ldo[l + 1], lv_ke[l + 1],
             prm->K_patch[l], prm->K[l], Kb[l], lv_om[l], lv_al[l], ldo[l], lv_ke[l], W.stats_dev, L.G[ph], L.T,
             L.per_patch ? (int64_t)cap * L.M : 0, L.per_patch ? (int64_t)cap : 0, L.per_patch, s,
-            l == 0 ? ctx->lv[0].D : nullptr, ctx->lv[0].N, l == 0 ? Xh : nullptr, queue);
+            l == 0 ? ctx->lv[0].D : nullptr, ctx->lv[0].N, l == 0 ? Xh : nullptr, queue, Gpp);
         if (l == 0) synth_all = synth_all && sy;
       });
   }

@@ -294,13 +294,20 @@ void launch_omp_update_wave(const float *Y, int M, const float *A, const float *
                             int64_t *stats, const float *gram, int T, int64_t a_pstride, int64_t inv_pstride,
                             cudaStream_t s);
 // width 0, 1, 2: 4, 8, 16 lanes per patch for M <= 64 (doubled per doubling of M, at most 32);
-// qr: Gram-Schmidt form (correlations updated per appended atom) instead of p0 - G alpha
+// qr: Gram-Schmidt form (correlations updated per appended atom) instead of p0 - G alpha.
+// gpp: per-patch candidate rows (A, inv_norm with strides a_pstride, inv_pstride)
+// and Gram blocks ([B][cap][cap], candidate order) instead of the level's shared
+// Gram matrix; the Gram-Schmidt form with Q_C in shared memory runs then.
+// Shared memory of one CTA of launch_omp_restricted_gram for these arguments
+// (pp: per-patch Gram blocks).
+size_t restricted_gram_smem(int width, bool qr, int M, int Kb, int cap, bool pp);
 bool launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const float *A, const float *inv_norm,
                                 const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx,
                                 int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
                                 const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
                                 int8_t *k_eff, int64_t *stats, const float *gram, int T, const float *D0, int N0,
-                                float *Xh, cudaStream_t s, unsigned long long *queue = nullptr);
+                                float *Xh, cudaStream_t s, unsigned long long *queue = nullptr,
+                                const float *gpp = nullptr, int64_t a_pstride = 0, int64_t inv_pstride = 0);
 // Gram-Schmidt form with the candidates' state in registers (G = 4, 8 or 16
 // lanes per patch); false (nothing launched) when M > 16 G (G = 4) or 8 G,
 // Kb > 8 or cap > 8 G.
@@ -336,7 +343,7 @@ bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, c
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
                            const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, bool cpos,
                            cudaStream_t s, const float *D0 = nullptr, int N0 = 0, float *Xh = nullptr,
-                           unsigned long long *queue = nullptr);
+                           unsigned long long *queue = nullptr, const float *gpp = nullptr);
 // Work order: ids[0..n) = the patches 0..n-1 sorted by budget K[b] (int8,
 // 0..CSP_MAX_K), largest first; `counts` is scratch of 2 x (CSP_MAX_K + 1) ints.
 // Patches of equal budget keep no particular order.
@@ -345,9 +352,13 @@ void launch_sort_by_budget(const int8_t *K, int64_t n, int32_t *ids, int *counts
 // dictionary for the candidates f(Omega_up) of every patch only, in candidate
 // order ([B][cap][M], row c of patch b = a_{cs_c} for that patch's codes) and
 // their inverse norms ([B][cap]); read by launch_omp_restricted(cpos = true).
-void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
+// With Gpp it also writes each patch's Gram block of those rows ([B][cap][cap],
+// G[i][j] = <a_i, a_j> for i, j < |C|) and returns true; false when the shape
+// has no such form (Gpp then untouched).
+bool launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
                           const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int32_t *child_off,
-                          const int32_t *child_idx, int cap, int64_t B, float *Ac, float *invc, cudaStream_t s);
+                          const int32_t *child_idx, int cap, int64_t B, float *Ac, float *invc, cudaStream_t s,
+                          float *Gpp = nullptr);
 
 // ---- K-SVD dictionary update and initialisation (k_ksvd.cu) ----
 // Ranks of the sweep's cluster (16 when such a cluster fits, else 8): the sort

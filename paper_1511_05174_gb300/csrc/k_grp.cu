@@ -409,12 +409,14 @@ __device__ int list_candidates(bool valid, int s, int64_t b, int kup, const int3
 
 // The candidate list (list_candidates), the candidates' inverse norms, and
 // p0 = A_C^T y (8 rows per load wave where registers allow, else 4).  Returns
-// |C|.  Warp-collective.
-template <int G, int NCH>
+// |C|.  Warp-collective.  PP: per-patch rows, candidate c of patch b at
+// A + b a_pstride + c M, its inverse norm at inv_norm[b inv_pstride + c].
+template <int G, int NCH, bool PP = false>
 __device__ int gram_setup(bool valid, int s, int64_t b, int kup, const int32_t *__restrict__ omega_up, int ldo_up,
                           const int32_t *__restrict__ child_off, const int32_t *__restrict__ child_idx, int cap,
                           const GrpSmem &S, int *pstart, int *pbeg, const float *__restrict__ inv_norm,
-                          int64_t *stats, int M, const float *__restrict__ A, const float4 (&yv)[NCH], float *p0) {
+                          int64_t *stats, int M, const float *__restrict__ A, const float4 (&yv)[NCH], float *p0,
+                          int64_t a_pstride = 0, int64_t inv_pstride = 0) {
   const int nv = M >> 2;
   const int nc = list_candidates<G>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
                                     stats);
@@ -426,12 +428,13 @@ __device__ int gram_setup(bool valid, int s, int64_t b, int kup, const int32_t *
   for (int c0 = 0; c0 < ncw; c0 += RBP) {
     const int ci = c0 + s;
     const bool oi = s < RBP && ci < nc;
-    const float iv = oi ? __ldg(inv_norm + S.cs[ci]) : -1.f;
+    const float iv = oi ? __ldg(PP ? inv_norm + b * inv_pstride + ci : inv_norm + S.cs[ci]) : -1.f;
     float4 a[RBP][NCH];
 #pragma unroll
     for (int u = 0; u < RBP; ++u) {
       const bool o = c0 + u < nc;
-      load_chunks<G, NCH>(a[u], A + (int64_t)(o ? S.cs[c0 + u] : 0) * M, nv, s, o);
+      const float *row = PP ? A + b * a_pstride + (int64_t)(o ? c0 + u : 0) * M : A + (int64_t)(o ? S.cs[c0 + u] : 0) * M;
+      load_chunks<G, NCH>(a[u], row, nv, s, o);
     }
     if (oi) S.invn[ci] = iv;
 #pragma unroll
@@ -453,7 +456,8 @@ omp_restricted_gram_kernel(const float *__restrict__ Y, int M, const float *__re
                            const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                            int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
                            int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T,
-    unsigned long long *__restrict__ queue) {
+    unsigned long long *__restrict__ queue, const float *__restrict__ = nullptr, int64_t = 0,
+    int64_t = 0) {  // the trailing per-patch arguments of omp_restricted_qr_kernel, unused
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
@@ -703,7 +707,11 @@ __host__ __device__ __forceinline__ int qr_group_bytes(int Kb, int cap) {
   return (bytes + 127) / 128 * 128 + 16;  // groups start on different bank offsets
 }
 
-template <int G, int NCH, bool PERSIST>
+// PP: per-patch candidate rows (per-pixel Phi): candidate c of patch b has its
+// row at A + b a_pstride + c M, its inverse norm at inv_norm[b inv_pstride + c],
+// and the patch's Gram block G_C at gpp + b cap^2 (row i at i cap, in the order
+// of the candidate list); chosen atoms are tracked by their slot.
+template <int G, int NCH, bool PERSIST, bool PP = false>
 __global__ void __launch_bounds__(WV_WARPS * 32, 5)
 omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__restrict__ A,
                          const float *__restrict__ inv_norm, const int32_t *__restrict__ ids, int64_t n,
@@ -712,7 +720,8 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
                          const int8_t *__restrict__ keff_up, const int8_t *__restrict__ Kp, int Kuni,
                          int Kb, int32_t *__restrict__ omega, float *__restrict__ alpha, int ldo,
                          int8_t *__restrict__ k_eff, int64_t *stats, const float *__restrict__ gram, int T,
-    unsigned long long *__restrict__ queue) {
+    unsigned long long *__restrict__ queue, const float *__restrict__ gpp = nullptr, int64_t a_pstride = 0,
+    int64_t inv_pstride = 0) {
   constexpr int NG = 32 / G;
   extern __shared__ __align__(16) char smem_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, s = lane & (G - 1), g = lane / G;
@@ -740,8 +749,16 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
   const float *yrow = Y + b * M;
   float4 yv[NCH];
   load_chunks<G, NCH>(yv, yrow, nv, s, valid);
-  const int nc = gram_setup<G, NCH>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart, pbeg,
-                                   inv_norm, stats, M, A, yv, p0);
+  const int nc = gram_setup<G, NCH, PP>(valid, s, b, kup, omega_up, ldo_up, child_off, child_idx, cap, S, pstart,
+                                       pbeg, inv_norm, stats, M, A, yv, p0, a_pstride, inv_pstride);
+  const float *gb = PP ? gpp + b * (int64_t)cap * cap : nullptr;  // this patch's Gram block
+  // G[q][C_c], with q in slot qs; and the row of atom q
+  auto gqc = [&](int q, int qs, int c) -> float {
+    return PP ? __ldg(gb + qs * cap + c) : __ldg(gram + (int64_t)q * T + S.cs[c]);
+  };
+  auto rowq = [&](int q, int qs) -> const float * {
+    return PP ? A + b * a_pstride + (int64_t)qs * M : A + (int64_t)q * M;
+  };
   // lane steps over the candidates (c = s + u G) any group of this warp needs, at most 8
   const int ucnt = min(8, __reduce_max_sync(kFull, (nc + G - 1) / G));
   for (int c = s; c < nc; c += G) cc[c] = p0[c];
@@ -782,9 +799,9 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
     for (int u = 0; u < 8; ++u) {
       if (u >= ucnt) break;  // ucnt is uniform over the warp
       const int c = s + u * G;
-      gpre[u] = (act && c < nc) ? __ldg(gram + (int64_t)q * T + S.cs[c]) : 0.f;
+      gpre[u] = (act && c < nc) ? gqc(q, qs, c) : 0.f;
     }
-    const float aa = act ? __ldg(gram + (int64_t)q * T + q) : 0.f;
+    const float aa = act ? (PP ? __ldg(gb + qs * cap + qs) : __ldg(gram + (int64_t)q * T + q)) : 0.f;
     const bool f32 = act && !(fl & 2);
     // new row of L: w_j = <u_j, a_q> = Q_C[q][j]
     float ww = 0.f, wz = 0.f;
@@ -813,8 +830,8 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
         S.L[tri(k) + k] = lkk;
         S.Linv[k] = il;
         S.z[k] = zk;
-        S.om[k] = q;
-        S.colp[k] = A + (int64_t)q * M;
+        S.om[k] = PP ? qs : q;
+        S.colp[k] = rowq(q, qs);
         p0c[k] = p0[qs];
       }
     }
@@ -834,7 +851,7 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
         }
       }
       for (int c = s + 8 * G; c < nc; c += G) {
-        float v = __ldg(gram + (int64_t)q * T + S.cs[c]);
+        float v = gqc(q, qs, c);
         for (int j = 0; j < k; ++j) v = fmaf(-S.W[j], Qc[j * ldg + c], v);
         v *= il;
         Qc[k * ldg + c] = v;
@@ -844,7 +861,7 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
     }
     // FP64 from scratch for the patches whose FP32 pivot failed (now or before)
     const bool go64 = act && !ok32;
-    if (go64 && s == 0) S.misc[0] = fp64_projection(M, yrow, S, k, A + (int64_t)q * M) ? 1 : 0;
+    if (go64 && s == 0) S.misc[0] = fp64_projection(M, yrow, S, k, rowq(q, qs)) ? 1 : 0;
     __syncwarp();
     const bool app64 = go64 && S.misc[0] != 0;
     // q depends on the chosen columns: alpha of the chosen ones from the FP32
@@ -853,14 +870,15 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
     if (__any_sync(kFull, restore))
       grp_backsub<G>(restore, s, k - 1, __reduce_max_sync(kFull, restore ? k - 1 : 0), S);
     if (app64 && s == 0) {
-      S.om[k] = q;
-      S.colp[k] = A + (int64_t)q * M;
+      S.om[k] = PP ? qs : q;
+      S.colp[k] = rowq(q, qs);
     }
     __syncwarp();
     if (app64)  // correlations c = p0 - G[C][Omega] alpha from the Gram rows of the chosen atoms
       for (int c = s; c < nc; c += G) {
         float v = p0[c];
-        for (int j = 0; j <= k; ++j) v = fmaf(-S.W[j], __ldg(gram + (int64_t)S.om[j] * T + S.cs[c]), v);
+        for (int j = 0; j <= k; ++j)
+          v = fmaf(-S.W[j], PP ? __ldg(gb + S.om[j] * cap + c) : __ldg(gram + (int64_t)S.om[j] * T + S.cs[c]), v);
         cc[c] = v;
       }
     // ||r||^2 formed explicitly in FP64 mode and near the FP32 floor
@@ -911,7 +929,7 @@ omp_restricted_qr_kernel(const float *__restrict__ Y, int M, const float *__rest
       k_eff[b] = (int8_t)k;
     }
     for (int j = s; j < ldo; j += G) {
-      omega[b * ldo + j] = (j < k) ? S.om[j] : -1;
+      omega[b * ldo + j] = (j < k) ? (PP ? S.cs[S.om[j]] : S.om[j]) : -1;
       alpha[b * ldo + j] = (j < k) ? S.W[j] : 0.f;
     }
   }
@@ -1593,13 +1611,22 @@ void launch_omp_update_wave(const float *Y, int M, const float *A, const float *
   });
 }
 
+size_t restricted_gram_smem(int width, bool qr, int M, int Kb, int cap, bool pp) {
+  const bool qr8 = qr && Kb <= 8 && !pp;
+  const int per_cta = WV_WARPS * (32 / gram_group(M, width));
+  return (size_t)(qr8 ? qr8_group_bytes(Kb, cap) : (qr || pp ? qr_group_bytes(Kb, cap) : gram_group_bytes(Kb, cap))) *
+         per_cta;
+}
+
 bool launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const float *A, const float *inv_norm,
                                 const int32_t *ids, int64_t n, const int32_t *child_off, const int32_t *child_idx,
                                 int cap, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
                                 const int8_t *Kp, int Kuni, int Kb, int32_t *omega, float *alpha, int ldo,
                                 int8_t *k_eff, int64_t *stats, const float *gram, int T, const float *D0, int N0,
-                                float *Xh, cudaStream_t s, unsigned long long *queue) {
-  const bool qr8 = qr && Kb <= 8;  // Q_C stored by candidate
+                                float *Xh, cudaStream_t s, unsigned long long *queue, const float *gpp,
+                                int64_t a_pstride, int64_t inv_pstride) {
+  if (gpp) qr = true;  // per-patch Gram blocks: the Gram-Schmidt form with Q_C in shared memory
+  const bool qr8 = qr && Kb <= 8 && !gpp;  // Q_C stored by candidate
   const bool synth = qr8 && Xh && D0 && N0 > 0 && N0 % 4 == 0;
   if (n == 0) return synth;
   const int per_cta = WV_WARPS * (32 / gram_group(M, width));
@@ -1616,8 +1643,9 @@ bool launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const
                                                         k_eff, stats, gram, T, D0, N0, synth ? Xh : nullptr);
       return;
     }
-    auto kern = queue ? (qr ? omp_restricted_qr_kernel<GG, NCH, true> : omp_restricted_gram_kernel<GG, NCH, true>)
-                      : (qr ? omp_restricted_qr_kernel<GG, NCH, false> : omp_restricted_gram_kernel<GG, NCH, false>);
+    auto kern = gpp ? (queue ? omp_restricted_qr_kernel<GG, NCH, true, true> : omp_restricted_qr_kernel<GG, NCH, false, true>)
+                : queue ? (qr ? omp_restricted_qr_kernel<GG, NCH, true> : omp_restricted_gram_kernel<GG, NCH, true>)
+                        : (qr ? omp_restricted_qr_kernel<GG, NCH, false> : omp_restricted_gram_kernel<GG, NCH, false>);
     if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     unsigned grid = blocks(n, per_cta);
     if (queue) {  // persistent: as many CTAs as fit at once, fed by the work queue
@@ -1631,7 +1659,8 @@ bool launch_omp_restricted_gram(int width, bool qr, const float *Y, int M, const
       cudaMemsetAsync(queue, 0, sizeof(unsigned long long), s);
     }
     kern<<<grid, WV_WARPS * 32, sm, s>>>(Y, M, A, inv_norm, ids, n, child_off, child_idx, cap, omega_up, ldo_up,
-                                         keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T, queue);
+                                         keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats, gram, T, queue, gpp,
+                                         a_pstride, inv_pstride);
   });
   return synth;
 }

@@ -889,15 +889,30 @@ void launch_p0_gemm(const float *Y, int M, const float *A, int T, const int32_t 
   p0_gemm_kernel<<<grid, 256, 0, s>>>(Y, M, A, T, ids, n, P0);
 }
 
+constexpr size_t kMaxSmemPerCta = 227 * 1024;  // dynamic shared memory of one CTA at most (opt-in)
+
 bool launch_omp_restricted(int variant, const float *Y, int M, const float *A, const float *inv_norm,
                            const int32_t *ids, int64_t n, const int32_t *child_off,
                            const int32_t *child_idx, int cap, const int32_t *omega_up, int ldo_up,
                            const int8_t *keff_up, const int8_t *Kp, int Kuni, int Kb,
                            int32_t *omega, float *alpha, int ldo, int8_t *k_eff, int64_t *stats,
                            const float *gram, int T, int64_t a_pstride, int64_t inv_pstride, bool cpos,
-                           cudaStream_t s, const float *D0, int N0, float *Xh, unsigned long long *queue) {
+                           cudaStream_t s, const float *D0, int N0, float *Xh, unsigned long long *queue,
+                           const float *gpp) {
   if (n == 0) return false;
+  if (gpp && cpos && variant >= 2) {
+    // per-patch rows with their Gram blocks: the Gram-Schmidt form, the variant's
+    // lane width or the narrowest wider one whose shared memory fits
+    for (int width = variant >= 8 ? 1 : (variant - 2) % 3; width <= 2; ++width)
+      if (restricted_gram_smem(width, true, M, Kb, cap, true) <= kMaxSmemPerCta)
+        return launch_omp_restricted_gram(width, true, Y, M, A, inv_norm, ids, n, child_off, child_idx, cap,
+                                          omega_up, ldo_up, keff_up, Kp, Kuni, Kb, omega, alpha, ldo, k_eff, stats,
+                                          nullptr, T, D0, N0, Xh, s, queue, gpp, a_pstride, inv_pstride);
+  }
   if (variant >= 2 && (!gram || a_pstride || cpos)) variant = 0;  // the Gram variants need the level's shared Gram matrix
+  if (variant >= 2 && variant < 8 && restricted_gram_smem((variant - 2) % 3, variant >= 5, M, Kb, cap, false) >
+                                         kMaxSmemPerCta)
+    variant = 0;  // candidate sets too large for the Gram forms' shared memory
   if (variant >= 8) {  // 8-10 (11-13 with the Gram block staged): register-resident candidates, 8 / 16 / 4 lanes
     bool sy = false;
     const int vv = variant >= 11 ? variant - 3 : variant;

@@ -401,19 +401,24 @@ pp_bins_rows_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const floa
 // Candidate rows of a restricted level in time-bin form (the candidate list
 // and the outputs of pp_candidates_kernel, the row arithmetic and grouping of
 // pp_bins_rows_kernel): one warp per patch, its candidate list in its own
-// slice of shared memory.
-template <int NB, int MPL>
+// slice of shared memory.  GRAM: the rows also go to shared memory ([cap][M + 1]
+// per warp) and the warp writes the patch's Gram block G[i][j] = <a_i, a_j>
+// (i, j < |C|, FMA chain over m in order) to Gpp + b cap^2, each lane a 4 x 4
+// tile of the upper triangle at a time, mirrored.
+template <int NB, int MPL, bool GRAM>
 __global__ void __launch_bounds__(256, 2)
 pp_bins_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, const float *__restrict__ D, int N,
                           int M, int S, int nb, const int32_t *__restrict__ omega_up, int ldo_up,
                           const int8_t *__restrict__ keff_up, const int32_t *__restrict__ child_off,
                           const int32_t *__restrict__ child_idx, int cap, int64_t B, float *__restrict__ Ac,
-                          float *__restrict__ invc) {
-  extern __shared__ int cs_all[];  // [warps][cap] candidate atoms
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t b = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+                          float *__restrict__ invc, float *__restrict__ Gpp) {
+  extern __shared__ int cs_all[];  // [warps][cap] candidate atoms | GRAM: [warps][cap][M + 1] rows
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwc = blockDim.x >> 5;
+  const int64_t b = (int64_t)blockIdx.x * nwc + warp;
   if (b >= B) return;
   int *cs = cs_all + warp * cap;
+  const int ldr = M + 1;
+  float *Rs = reinterpret_cast<float *>(cs_all + nwc * cap) + (size_t)warp * cap * ldr;
   const int nc = list_candidates_warp(b, omega_up, ldo_up, keff_up, child_off, child_idx, cap, cs, lane);
   PpBins<NB, MPL> t;
   pp_bins_setup<NB, MPL>(g, l, pc + b * (int64_t)g.Lx * M, M, S, nb, lane, t);
@@ -431,7 +436,10 @@ pp_bins_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, cons
         float *row = Ab + (int64_t)c * M;
 #pragma unroll
         for (int j = 0; j < MPL; ++j) {
-          if (lane + 32 * j < M) row[lane + 32 * j] = v[j];
+          if (lane + 32 * j < M) {
+            row[lane + 32 * j] = v[j];
+            if (GRAM) Rs[c * ldr + lane + 32 * j] = v[j];
+          }
           q[u] = fmaf(v[j], v[j], q[u]);
         }
       }
@@ -441,6 +449,52 @@ pp_bins_candidates_kernel(GeomDev g, const uint8_t *__restrict__ pc, int l, cons
     if ((lane & 3) == 0 && c < nc) {
       const float r = sqrtf(tot);
       invc[b * cap + c] = r > 0.f ? 1.f / r : -1.f;
+    }
+  }
+  if (GRAM) {
+    __syncwarp();
+    float *Gb = Gpp + b * (int64_t)cap * cap;
+    const int nt = (nc + 3) >> 2, ntile = nt * (nt + 1) / 2;
+    for (int tix = lane; tix < ntile; tix += 32) {
+      int ti = 0, rem = tix;  // tile (ti, tj), ti <= tj, row-major over the upper triangle
+      while (rem >= nt - ti) {
+        rem -= nt - ti;
+        ++ti;
+      }
+      const int tj = ti + rem;
+      float acc[4][4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
+      int ri[4], rj[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ri[u] = min(4 * ti + u, nc - 1) * ldr;  // rows past |C| repeat the last one (not written)
+        rj[u] = min(4 * tj + u, nc - 1) * ldr;
+      }
+      for (int m = 0; m < M; ++m) {
+        float x[4], y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          x[u] = Rs[ri[u] + m];
+          y[u] = Rs[rj[u] + m];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(x[u], y[v], acc[u][v]);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int i = 4 * ti + u, j = 4 * tj + v;
+          if (i < nc && j < nc && i <= j) {
+            Gb[i * cap + j] = acc[u][v];
+            Gb[j * cap + i] = acc[u][v];
+          }
+        }
     }
   }
 }
@@ -934,43 +988,55 @@ void launch_effective_dict_pp_norms(const GeomDev &g, const uint8_t *pc, int lev
   inv_norms_kernel<<<blocks(B * T, 256), 256, 0, s>>>(inv, B * T, scratch);
 }
 
+// Shared memory of one warp of pp_bins_candidates_kernel: its candidate list
+// and, with the Gram block, its rows.
+size_t pp_cand_warp_bytes(int cap, int M, bool gram) {
+  return sizeof(int) * (size_t)cap + (gram ? sizeof(float) * (size_t)cap * (M + 1) : 0);
+}
+constexpr size_t kPpCandSmem = 200 * 1024;  // shared memory of one CTA at most
+
 template <int NB, int MPL>
 void launch_pp_bins_cand(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
                          const PpShape &p, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
                          const int32_t *child_off, const int32_t *child_idx, int cap, int64_t B, float *Ac,
-                         float *invc, cudaStream_t s) {
-  const size_t sm = sizeof(int) * 8 * (size_t)cap;  // eight warps' candidate lists
-  if (sm > 48 * 1024)
-    cudaFuncSetAttribute(pp_bins_candidates_kernel<NB, MPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  pp_bins_candidates_kernel<NB, MPL><<<(unsigned)((B + 7) / 8), 256, sm, s>>>(
-      g, pc, level, D, N, M, p.S, p.nb, omega_up, ldo_up, keff_up, child_off, child_idx, cap, B, Ac, invc);
+                         float *invc, cudaStream_t s, float *Gpp) {
+  const size_t per = pp_cand_warp_bytes(cap, M, Gpp != nullptr);
+  const int nw = (int)std::max<size_t>(1, std::min<size_t>(8, kPpCandSmem / per));  // warps (patches) per CTA
+  const size_t sm = per * nw;
+  auto kern = Gpp ? pp_bins_candidates_kernel<NB, MPL, true> : pp_bins_candidates_kernel<NB, MPL, false>;
+  if (sm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  kern<<<(unsigned)((B + nw - 1) / nw), 32 * nw, sm, s>>>(g, pc, level, D, N, M, p.S, p.nb, omega_up, ldo_up,
+                                                          keff_up, child_off, child_idx, cap, B, Ac, invc, Gpp);
 }
 
 template <int NB>
 void launch_pp_bins_cand_m(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
                            const PpShape &p, const int32_t *omega_up, int ldo_up, const int8_t *keff_up,
                            const int32_t *child_off, const int32_t *child_idx, int cap, int64_t B, float *Ac,
-                           float *invc, cudaStream_t s) {
+                           float *invc, cudaStream_t s, float *Gpp) {
   if (p.MPL == 1)
     launch_pp_bins_cand<NB, 1>(g, pc, level, D, N, M, p, omega_up, ldo_up, keff_up, child_off, child_idx, cap, B, Ac,
-                               invc, s);
+                               invc, s, Gpp);
   else if (p.MPL == 2)
     launch_pp_bins_cand<NB, 2>(g, pc, level, D, N, M, p, omega_up, ldo_up, keff_up, child_off, child_idx, cap, B, Ac,
-                               invc, s);
+                               invc, s, Gpp);
   else
     launch_pp_bins_cand<NB, 4>(g, pc, level, D, N, M, p, omega_up, ldo_up, keff_up, child_off, child_idx, cap, B, Ac,
-                               invc, s);
+                               invc, s, Gpp);
 }
 
-void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
+bool launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const float *D, int N, int M,
                           const int32_t *omega_up, int ldo_up, const int8_t *keff_up, const int32_t *child_off,
-                          const int32_t *child_idx, int cap, int64_t B, float *Ac, float *invc, cudaStream_t s) {
-  if (B == 0) return;
+                          const int32_t *child_idx, int cap, int64_t B, float *Ac, float *invc, cudaStream_t s,
+                          float *Gpp) {
   PpShape p;
-  if (pp_shape(g, level, M, p) && (size_t)cap * 32 <= 200 * 1024) {  // eight lists of cap atoms in shared memory
+  const bool bins = pp_shape(g, level, M, p) && pp_cand_warp_bytes(cap, M, false) <= kPpCandSmem;
+  if (Gpp && !(bins && pp_cand_warp_bytes(cap, M, true) <= kPpCandSmem)) Gpp = nullptr;  // no Gram form here
+  if (B == 0) return Gpp != nullptr;
+  if (bins) {
 #define CSP_PP_CAND(nb_)                                                                                         \
   launch_pp_bins_cand_m<nb_>(g, pc, level, D, N, M, p, omega_up, ldo_up, keff_up, child_off, child_idx, cap, B, Ac, \
-                             invc, s)
+                             invc, s, Gpp)
     switch (p.NB) {
       case 1: CSP_PP_CAND(1); break;
       case 2: CSP_PP_CAND(2); break;
@@ -979,12 +1045,13 @@ void launch_pp_candidates(const GeomDev &g, const uint8_t *pc, int level, const 
       default: CSP_PP_CAND(16); break;
     }
 #undef CSP_PP_CAND
-    return;
+    return Gpp != nullptr;
   }
   const size_t sm = sizeof(int) * ((size_t)g.Lx * M + cap);
   if (sm > 48 * 1024) cudaFuncSetAttribute(pp_candidates_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   pp_candidates_kernel<<<(unsigned)B, 256, sm, s>>>(g, pc, level, D, N, M, omega_up, ldo_up, keff_up, child_off,
                                                     child_idx, cap, B, Ac, invc);
+  return false;
 }
 
 void launch_inv_row_norms(const float *A, int64_t rows, int M, float *inv, unsigned int *scratch, cudaStream_t s) {
