@@ -420,7 +420,9 @@ def test_restricted_dependent_candidate_falls_back_to_fp64(variant):
 def test_restricted_variants_agree_with_oracle(key, variant):
     """Every restricted-solver variant the autotuner may pick meets the parity
     bar: L2-cooperative (0), shared-memory staged (1), Gram-matrix proxy with
-    narrow, middle and wide lane groups (2, 3, 4), its Gram-Schmidt form (5, 6, 7)."""
+    narrow, middle and wide lane groups (2, 3, 4), its Gram-Schmidt form (5, 6, 7),
+    the register forms (8-13).  On the per-pixel-Phi video workload variants 2-13
+    run the Gram-Schmidt form on the per-patch Gram blocks of the candidate rows."""
     from paper_1511_05174_gb300.context import Context
     w = _workload(key)
     o, a, k, _ = oracle.cross_scale_omp(w)
