@@ -270,6 +270,16 @@ def algorithmic(kind, w, prof_launches, stats, B, steps, M):
         return 4.0 * g.planes * g.H * g.W + B * (K * 8 + 1), "GB/s", "hbm"
     if kind == "extract":
         return 4.0 * B * M + 4.0 * w.meas.size, "GB/s", "hbm"
+    if kind == "full_gram":
+        # the Gram form of the full-dictionary level: per patch and appended atom k
+        # (k = 0 .. K-1) a new column of Q over all T atoms (T k FMAs) and the
+        # correlation update (T FMAs): T K (K + 1) flops per patch
+        cross = bool(prof_launches.get("restricted"))
+        lvl = -1 if cross else 0
+        T = w.dicts[lvl].shape[0]
+        K = int(np.max(w.K_levels[lvl]))
+        launches = max(prof_launches[kind][0] / steps, 1.0)
+        return float(T) * K * (K + 1) * B / launches, "TFLOP/s", "alu"
     return None, None, None
 
 
