@@ -373,20 +373,46 @@ omp_fused_tc_kernel(const __grid_constant__ FzArgs args, const float *__restrict
       float sc[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) ci[c] = keys[c] ? (int)(imask - (keys[c] & imask)) : -1;
+      // A clear winner needs no re-score of the other three.  Each BF16 score
+      // |<a^, r^>| (a^ the BF16 rounding of the unit atom, r^ of r, unit roundoff
+      // 2^-8) lies within 2^-7 ||r|| of |<a, r>| / ||a||; a key's truncated low bits
+      // put it at most a factor 1 + 2^(idx_bits - 23) below its score.  A top key
+      // whose score leads the second (with twice that slack) by more than
+      // 2^-5 ||r|| -- twice the 2^-6 the two errors can close -- is the strict FP32
+      // argmax over every atom, the atom the full re-score would choose.  When a
+      // whole warp's patches are clear (or done), only the winners' correlations
+      // are formed, with the arithmetic of the full path (same results).
+      bool clear = !act;
+      const float inv0 = ci[0] >= 0 ? s_inv[ci[0]] : -1.f;
+      if (act && ci[0] >= 0 && inv0 > 0.f) {
+        const float s1 = __uint_as_float(keys[0] & smask), s2 = __uint_as_float(keys[1] & smask);
+        const float slack = 1.f + __uint_as_float((uint32_t)(127 + idx_bits - 22) << 23);
+        bool taken0 = false;
+        for (int j = 0; j < k; ++j) taken0 |= (omp[j] == ci[0]);
+        clear = !taken0 && s1 - s2 * slack > 0.03125f * sqrtf(rsq);
+      }
+      if (__all_sync(0xffffffffu, clear)) {
+        const float s0 = pair_sum(half_dot(arow(ci[0] >= 0 ? ci[0] : 0), h, rv));
+        if (act) {
+          best = pack_key(fabsf(s0) * inv0, ci[0]);
+          cq = s0;
+        }
+      } else {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) sc[c] = half_dot(arow(ci[c] >= 0 ? ci[c] : 0), h, rv);
+        for (int c = 0; c < 4; ++c) sc[c] = half_dot(arow(ci[c] >= 0 ? ci[c] : 0), h, rv);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        sc[c] = pair_sum(sc[c]);
-        bool taken = false;
-        if (act && ci[c] >= 0)
-          for (int j = 0; j < k; ++j) taken |= (omp[j] == ci[c]);
-        const float inv = ci[c] >= 0 ? s_inv[ci[c]] : -1.f;
-        if (act && ci[c] >= 0 && inv > 0.f && !taken) {
-          const unsigned long long kk = pack_key(fabsf(sc[c]) * inv, ci[c]);
-          if (kk > best) {
-            best = kk;
-            cq = sc[c];
+        for (int c = 0; c < 4; ++c) {
+          sc[c] = pair_sum(sc[c]);
+          bool taken = false;
+          if (act && ci[c] >= 0)
+            for (int j = 0; j < k; ++j) taken |= (omp[j] == ci[c]);
+          const float inv = ci[c] >= 0 ? s_inv[ci[c]] : -1.f;
+          if (act && ci[c] >= 0 && inv > 0.f && !taken) {
+            const unsigned long long kk = pack_key(fabsf(sc[c]) * inv, ci[c]);
+            if (kk > best) {
+              best = kk;
+              cq = sc[c];
+            }
           }
         }
       }
