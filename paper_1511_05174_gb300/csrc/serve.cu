@@ -137,7 +137,8 @@ size_t model_patch_bytes(const Model &m) {
 }
 
 // Coded exposure: bytes of one patch's effective dictionary (and norms) of the
-// full-dictionary level, plus the candidate rows of the restricted levels.
+// full-dictionary level, plus the candidate rows (and their Gram blocks) of the
+// restricted levels.
 size_t model_pp_bytes(const Model &m) {
   if (m.sense_kind != CSP_SENSE_CODED_EXPOSURE) return 0;
   const csp_solve_params &p = m.params;
@@ -147,6 +148,7 @@ size_t model_pp_bytes(const Model &m) {
   for (int l = 0; l + 1 < nl; ++l) {
     const int cap = std::max(1, m.ctx->lv[l].max_children * (p.K[l + 1] > 0 ? p.K[l + 1] : p.Kmax));
     b += ((size_t)cap * m.M + cap) * 4 + 32;
+    if (m.ctx->restricted_variant >= 2) b += (size_t)cap * cap * 4;  // the candidates' Gram block
   }
   return b;
 }
