@@ -50,7 +50,7 @@ typedef int csp_status;
 #define CSP_ERR_NOT_READY   -3   /* a required load/set call has not been made */
 #define CSP_ERR_CUDA        -4   /* a CUDA runtime call failed */
 #define CSP_ERR_TIMEOUT     -5   /* a bounded wait expired */
-#define CSP_ERR_UNSUPPORTED -6   /* valid request this build does not implement */
+#define CSP_ERR_UNSUPPORTED -6   /* valid request the library does not implement   */
 
 #define CSP_MAX_LEVELS 4
 #define CSP_MAX_K      32        /* largest sparsity per level */
