@@ -550,6 +550,7 @@ def serving_bench(args, device, pool, mode, jobs_per_rate):
                 "wait_ms": med(lambda i: 1e3 * (i["t_admit"] - i["t_submit"])),
                 "enqueue_ms": med(lambda i: i["enqueue_ms"]),
                 "copy_in_ms": med(lambda i: i["copy_in_ms"]), "solve_ms": med(lambda i: i["solve_ms"]),
+                "operator_build_ms": med(lambda i: i["build_ms"]),
                 "aggregate_ms": med(lambda i: i["aggregate_ms"]), "copy_out_ms": med(lambda i: i["copy_out_ms"]),
                 "admit_to_gpu_done_ms": med(lambda i: 1e3 * (i["t_gpu_done"] - i["t_admit"])),
                 "host_out_ms": med(lambda i: i["host_out_ms"]),
@@ -566,7 +567,10 @@ def serving_bench(args, device, pool, mode, jobs_per_rate):
                     "jobs": len(sel),
                     "latency_ms_median": float(np.median([1e3 * (i["t_done"] - i["t_submit"]) for i in sel])),
                     "solve_ms_median": float(np.median([i["solve_ms"] for i in sel])),
+                    "operator_build_ms_median": float(np.median([i["build_ms"] for i in sel])),
                     "copy_in_ms_median": float(np.median([i["copy_in_ms"] for i in sel])),
+                    "aggregate_ms_median": float(np.median([i["aggregate_ms"] for i in sel])),
+                    "copy_out_ms_median": float(np.median([i["copy_out_ms"] for i in sel])),
                     "admit_to_gpu_done_ms_median": float(np.median([1e3 * (i["t_gpu_done"] - i["t_admit"])
                                                                     for i in sel])),
                     "mean_batch_jobs": float(np.mean([i["batch_jobs"] for i in sel]))}

@@ -369,12 +369,14 @@ typedef struct csp_job_info {
      * copy_in_ms   device: host-to-device copies (the measurements straight from the
      *              caller's buffer), patch extraction and code blocks;
      * solve_ms     device: the solve (with per-patch operator builds for per-pixel Phi);
+     * build_ms     device: of solve_ms, the builds of the per-patch operators of the
+     *              full-dictionary level (coded exposure; 0 otherwise);
      * aggregate_ms device: synthesis and overlap-add of the batch's images;
      * copy_out_ms  device: device-to-host copies of the images;
      * t_gpu_done   seconds on the server's clock when the scheduler saw the batch complete;
      * host_out_ms  host copy of this job's image into the caller's buffer (0 when the
      *              device wrote it there directly). */
-    double enqueue_ms, copy_in_ms, solve_ms, aggregate_ms, copy_out_ms, t_gpu_done, host_out_ms;
+    double enqueue_ms, copy_in_ms, solve_ms, aggregate_ms, copy_out_ms, t_gpu_done, host_out_ms, build_ms;
 } csp_job_info;
 
 csp_status csp_server_create(csp_server **out, const csp_server_config *cfg);

@@ -95,7 +95,7 @@ class csp_job_info(ctypes.Structure):
                 ("t_done", ctypes.c_double), ("batch_jobs", ctypes.c_int), ("batch_patches", ctypes.c_int64),
                 ("status", ctypes.c_int), ("enqueue_ms", ctypes.c_double), ("copy_in_ms", ctypes.c_double),
                 ("solve_ms", ctypes.c_double), ("aggregate_ms", ctypes.c_double), ("copy_out_ms", ctypes.c_double),
-                ("t_gpu_done", ctypes.c_double), ("host_out_ms", ctypes.c_double)]
+                ("t_gpu_done", ctypes.c_double), ("host_out_ms", ctypes.c_double), ("build_ms", ctypes.c_double)]
 
 
 class CspError(RuntimeError):

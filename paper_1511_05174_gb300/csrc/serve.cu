@@ -48,6 +48,7 @@ struct Job {
   size_t meas_floats = 0, img_floats = 0, bytes = 0;
   double t_submit = 0, t_admit = 0, t_done = 0, t_gpu_done = 0;
   double enqueue_ms = 0, stage_ms[4] = {0, 0, 0, 0}, host_out_ms = 0;  // stages: copy-in, solve, aggregate, copy-out
+  double build_ms = 0;  // per-patch operator builds within the solve (coded exposure)
   int batch_jobs = 0;
   int64_t batch_patches = 0;
   csp_status status = CSP_ERR_NOT_READY;
@@ -60,6 +61,8 @@ struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   cudaEvent_t tev[5] = {};  // timing events at the batch's stage boundaries
+  std::vector<cudaEvent_t> bev;  // around each operator-slice build (pairs), created on demand
+  int nbev = 0;                  // pairs recorded for the current batch
   Workspace W;              // solver workspace, kept at its high-water mark
   bool busy = false;
   std::vector<Job *> jobs;
@@ -264,9 +267,17 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
     if ((e = cudaMemcpyAsync(dp(o_ids), ids, (size_t)n * 4, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
     ps.phase_ids = (const int32_t *)dp(o_ids);
   }
+  sl.nbev = 0;
   if (ce) {
     // slice by slice: per-patch operators, then the solve of those patches
     for (int64_t off = 0; off < Bt; off += slice) {
+      const int pe = 2 * sl.nbev;  // timing pair of this slice's build
+      while ((int)sl.bev.size() < pe + 2) {
+        cudaEvent_t ev = nullptr;
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return e;
+        sl.bev.push_back(ev);
+      }
+      cudaEventRecord(sl.bev[pe], s);
       PatchSet pss;
       pss.B = std::min(slice, Bt - off);
       pss.pcodes = dp(o_pc) + off * codes_pp;
@@ -275,6 +286,8 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
       if (build_patch_dicts_for(m.ctx, top, pss.pcodes, pss.B, pss.A_pp[top], pss.inv_pp[top],
                                 (unsigned int *)dp(o_scr), s) != CSP_OK)
         return cudaErrorUnknown;
+      cudaEventRecord(sl.bev[pe + 1], s);
+      ++sl.nbev;
       if (solve_patchset(m.ctx, pss, sl.W, &m.params, Y + off * m.M, sup + off * Kmax, coef + off * Kmax,
                          keff + off, s) != CSP_OK)
         return cudaErrorUnknown;
@@ -315,8 +328,19 @@ void batch_stage_times(Slot &sl) {
       cudaGetLastError();
       ms[i] = 0.f;
     }
-  for (Job *j : sl.jobs)
+  float build = 0.f;
+  for (int p = 0; p < sl.nbev; ++p) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, sl.bev[2 * p], sl.bev[2 * p + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      t = 0.f;
+    }
+    build += t;
+  }
+  for (Job *j : sl.jobs) {
     for (int i = 0; i < 4; ++i) j->stage_ms[i] = ms[i];
+    j->build_ms = build;
+  }
 }
 
 // Called with the server lock held, after the batch's work has completed
@@ -480,6 +504,7 @@ void csp_server_destroy(csp_server *srv) {
     cudaStreamDestroy(sl.stream);
     cudaEventDestroy(sl.ev);
     for (cudaEvent_t e : sl.tev) cudaEventDestroy(e);
+    for (cudaEvent_t e : sl.bev) cudaEventDestroy(e);
     cudaFree(sl.W.stats_dev);
     if (sl.host) cudaFreeHost(sl.host);
     sl.W.ws.clear();  // buffers are owned (and freed) by alloc_ctx
@@ -654,6 +679,7 @@ csp_status csp_job_info_get(csp_server *srv, uint64_t job_id, csp_job_info *out)
   out->copy_out_ms = j->stage_ms[3];
   out->t_gpu_done = j->t_gpu_done;
   out->host_out_ms = j->host_out_ms;
+  out->build_ms = j->build_ms;
   return CSP_OK;
 }
 

@@ -129,7 +129,7 @@ class Server:
                 "batch_jobs": i.batch_jobs, "batch_patches": i.batch_patches, "status": i.status,
                 "enqueue_ms": i.enqueue_ms, "copy_in_ms": i.copy_in_ms, "solve_ms": i.solve_ms,
                 "aggregate_ms": i.aggregate_ms, "copy_out_ms": i.copy_out_ms, "t_gpu_done": i.t_gpu_done,
-                "host_out_ms": i.host_out_ms}
+                "host_out_ms": i.host_out_ms, "build_ms": i.build_ms}
 
     def release(self, job_id: int) -> None:
         b.csp_job_release(self._srv, job_id)

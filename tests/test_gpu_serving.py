@@ -50,6 +50,10 @@ def test_mixed_batch_equals_alone(name, kw, prec):
         assert info["patches"] == w.n_patches
         assert info["batch_patches"] >= info["patches"] and info["batch_jobs"] >= 1
         assert info["t_submit"] <= info["t_admit"] <= info["t_done"]
+        # stage times: the per-patch operator builds are part of the solve, and
+        # only coded-exposure jobs have them
+        assert 0.0 <= info["build_ms"] <= info["solve_ms"] + 1e-3
+        assert (info["build_ms"] > 0.0) == (name == "video")
 
 
 def test_video_job_in_slices_equals_alone():
@@ -58,8 +62,11 @@ def test_video_job_in_slices_equals_alone():
     w = _w("video", 256, 256, seed=3, T0=1024)
     with Server(0, mem_budget_bytes=1 << 30) as srv:
         mid = srv.add_workload_model(w, "cross_scale", "fp32")
-        img = srv.result(srv.submit(mid, w.meas, 256, 256, codes=w.sensing.codes), 120).copy()
+        j = srv.submit(mid, w.meas, 256, 256, codes=w.sensing.codes)
+        img = srv.result(j, 120).copy()
+        info = srv.info(j)
     assert np.array_equal(img, _alone(w, "cross_scale", "fp32"))
+    assert 0.0 < info["build_ms"] <= info["solve_ms"] + 1e-3  # every slice's build counted
 
 
 def test_two_models_interleaved():
