@@ -319,6 +319,34 @@ cudaError_t launch_batch(csp_server *srv, Slot &sl) {
   return cudaEventRecord(sl.ev, s);
 }
 
+// Host copy of a finished image into the caller's buffer.  One thread copies at
+// about 20 GB/s on the host of a GB300, so images above 4 MB are copied by up to
+// four threads (chunks of at least 2 MB; the last one by the calling thread).
+void host_copy(void *dst, const void *src, size_t bytes) {
+  constexpr size_t kMin = size_t(4) << 20, kChunk = size_t(2) << 20;
+  const int nt = bytes < kMin ? 1 : (int)std::min<size_t>(4, bytes / kChunk);
+  if (nt <= 1) {
+    std::memcpy(dst, src, bytes);
+    return;
+  }
+  const size_t part = (bytes / nt + 63) & ~size_t(63);
+  std::vector<std::thread> th;
+  th.reserve(nt - 1);
+  for (int t = 0; t + 1 < nt; ++t) {
+    auto copy = [=] {
+      std::memcpy(static_cast<char *>(dst) + t * part, static_cast<const char *>(src) + t * part, part);
+    };
+    try {
+      th.emplace_back(copy);
+    } catch (...) {  // no thread to be had: this chunk inline
+      copy();
+    }
+  }
+  const size_t last = (size_t)(nt - 1) * part;
+  std::memcpy(static_cast<char *>(dst) + last, static_cast<const char *>(src) + last, bytes - last);
+  for (std::thread &x : th) x.join();
+}
+
 // Stage times of a completed batch into its jobs (device events; host times
 // were recorded by the scheduler).
 void batch_stage_times(Slot &sl) {
@@ -384,7 +412,7 @@ void scheduler(csp_server *srv) {
         lk.unlock();
         for (Job *j : sl.jobs) {
           const double t0 = now_s();
-          if (j->image_host && j->h_img) std::memcpy(j->image_host, j->h_img, j->img_floats * 4);
+          if (j->image_host && j->h_img) host_copy(j->image_host, j->h_img, j->img_floats * 4);
           j->t_gpu_done = tg;
           j->host_out_ms = 1e3 * (now_s() - t0);
         }
