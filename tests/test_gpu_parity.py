@@ -415,6 +415,36 @@ def test_restricted_dependent_candidate_falls_back_to_fp64(variant):
     assert rate == 1.0 and worst <= REL_TOL
 
 
+@pytest.mark.parametrize("variant", [0, 2, 6, 8, 12])
+def test_per_pixel_dependent_candidate_falls_back_to_fp64(variant):
+    """The dependent-atom case above on per-pixel Phi: a one-frame coded exposure
+    whose codes are all 1 (so every patch's effective rows are the atoms
+    themselves), 40 patches in one row of the image.  The restricted level takes
+    each patch's candidate rows and, for variants >= 2, their per-patch Gram
+    blocks; the FP64 rebuild reads the rows of the patch's own slots.  k_eff = 2
+    and least-squares coefficients, as in the oracle."""
+    from paper_1511_05174_gb300.context import Context
+    rng = np.random.default_rng(13)
+    A = rng.integers(-3, 4, size=(3, 64)).astype(np.float32)
+    A[2] = A[0] + A[1]
+    Y = np.stack([A[0] + 0.5 * A[1] + 0.01 * rng.standard_normal(64) for _ in range(40)]).astype(np.float32)
+    coarse = A[:1].reshape(1, 4, 2, 4, 2).mean(axis=(2, 4)).reshape(1, 16).astype(np.float32)
+    ctx = Context(0)
+    ctx.set_geometry(8, 320, (1, 1), 8, 8, [(1, 1, 1, 1), (1, 1, 2, 2)])
+    ctx.set_sensing("coded_exposure", np.ones((1, 8, 320), np.uint8))
+    ctx.load_dictionary(0, A)
+    ctx.load_dictionary(1, coarse)
+    ctx.load_links(0, np.zeros(3, np.int32))
+    ctx.set_kernel_variant(variant)
+    sup, coef, keff = ctx.solve(torch.from_numpy(Y).cuda(), "cross_scale", "fp32", K=[3, 1], Kmax=3)
+    o, a, k, _ = oracle.omp_batch([A] * len(Y), Y, 3)
+    assert np.all(k == 2)
+    assert np.all(keff.cpu().numpy() == 2)
+    assert ctx.stats()["fp64_fallbacks"] >= 1
+    rate, worst, bad = compare(A, sup.cpu().numpy(), coef.cpu().numpy(), keff.cpu().numpy().astype(int), o, a, k)
+    assert rate == 1.0 and worst <= REL_TOL
+
+
 @pytest.mark.parametrize("variant", list(range(14)))
 @pytest.mark.parametrize("key", ["bayer", "lightfield", "denoise_ragged", "video", "rgb_identity"])
 def test_restricted_variants_agree_with_oracle(key, variant):
